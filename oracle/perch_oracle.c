@@ -1,0 +1,459 @@
+/*
+ * PERCH CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, obviously correct restatement of what the successor-evaluation
+ * path computes (Narayanan & Likhachev, "PERCH: Perception via Search for
+ * Multi-Object Recognition and Localization"). Only the tests, the smoke check
+ * and the benchmark's CPU-baseline leg may load this library; the product
+ * path never does. It shares no code, header or table with the CUDA library.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fno-fast-math [-fopenmp] -shared -fPIC.
+ * Every float operation below is one IEEE binary32 operation rounded to
+ * nearest-even (no contraction into FMA), so the result is fixed by the
+ * arithmetic contract written out next to each step.
+ *
+ * What is computed, per the paper:
+ *   - observed cloud I (Sec. III-A notation): valid depth pixels back-projected
+ *     through the pinhole model;
+ *   - rendered clouds R_j (Sec. III-A): z-buffer render of objects
+ *     O_1..O_j, each at a 3-DoF table pose (x, y, yaw) (Sec. III);
+ *   - explanation indicator, Eq. (1): p is unexplained by C iff every point
+ *     of C is farther than delta;
+ *   - decomposed edge cost, Sec. IV-A / Eq. (2):
+ *       dJr  = #{p in dR_i unexplained by I}
+ *       dJo  = #{q in I n V(O_i) unexplained by dR_i}
+ *       resid= #{q in I - V_K unexplained by R_K}   (only when i = K)
+ *   - monotone constraint R_{i-1} subset R_i of Eq. (3): the child is invalid
+ *     when any of its pixels lies strictly in front of the parent's render;
+ *   - undecomposed J = J_o + J_r of Sec. III-B (used to pin the K = 1 case).
+ *
+ * Readings where the paper is silent (it only says "render"):
+ *   - pinhole with pixel centres at integer (u, v); depth = camera-frame Z;
+ *   - vertices snapped to 1/16 pixel (round half to even);
+ *   - exact integer edge functions, coverage of pixel centres with the
+ *     top-left tie rule; front faces only (positive signed area);
+ *   - 1/z interpolated with the screen-space barycentrics, z-buffer keeps
+ *     the minimum z;
+ *   - a triangle with a vertex at z_c <= 0.05 m, a vertex beyond 2048 px, or
+ *     an extent of 1024 px or more is dropped and counted ("culled");
+ *   - distances are measured in the camera frame; "explained" is d^2 <= delta^2
+ *     (Eq. (1) calls a point unexplained only when the distance exceeds delta);
+ *   - V(O) is an inscribed vertical cylinder about the object origin, the
+ *     conservative volume the paper names in Sec. III-A.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+  int32_t n_verts, n_tris;
+  const float* verts;   /* n_verts x 3, object frame, z up */
+  const int32_t* tris;  /* n_tris x 3 */
+  float vol_r, vol_zlo, vol_zhi; /* V(O): inscribed cylinder */
+} or_mesh;
+
+typedef struct { uint16_t mesh, iyaw; int16_t ix, iy; } or_obj;
+
+typedef struct {
+  int32_t W, H;
+  float fx, fy, cx, cy;
+  float T_wc[12];       /* camera -> world, row-major 3x4 */
+  const float* xs; int32_t nx;
+  const float* ys; int32_t ny;
+  const float* cos_sin; int32_t n_yaw; /* (cos, sin) per yaw */
+  const or_mesh* meshes; int32_t n_mesh;
+  float delta;
+} or_world;
+
+/* record: dJr, dJo, resid, viol, n_new, flags */
+enum { OR_DJR = 0, OR_DJO, OR_RESID, OR_VIOL, OR_NNEW, OR_FLAGS, OR_REC };
+#define OR_FLAG_CULLED 1u
+#define OR_FLAG_INVALID 2u
+
+/* ------------------------------------------------------------------ camera */
+typedef struct {
+  float Rcw[9], tcw[3];  /* world -> camera */
+  float Rwc[9], twc[3];  /* camera -> world */
+  float* rx;             /* (u - cx) / fx, per column */
+  float* ry;             /* (v - cy) / fy, per row */
+  float delta2;
+} or_cam;
+
+static int cam_init(const or_world* w, or_cam* c) {
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) c->Rwc[r * 3 + k] = w->T_wc[r * 4 + k];
+    c->twc[r] = w->T_wc[r * 4 + 3];
+  }
+  /* R_cw is the exact transpose; t_cw = -R_wc^T t_wc in double, then rounded */
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) c->Rcw[r * 3 + k] = c->Rwc[k * 3 + r];
+    double acc = (double)c->Rwc[0 * 3 + r] * (double)c->twc[0];
+    acc = acc + (double)c->Rwc[1 * 3 + r] * (double)c->twc[1];
+    acc = acc + (double)c->Rwc[2 * 3 + r] * (double)c->twc[2];
+    c->tcw[r] = (float)(-acc);
+  }
+  c->rx = (float*)malloc(sizeof(float) * (size_t)w->W);
+  c->ry = (float*)malloc(sizeof(float) * (size_t)w->H);
+  if (!c->rx || !c->ry) { free(c->rx); free(c->ry); return -1; }
+  for (int u = 0; u < w->W; ++u) c->rx[u] = (float)(((double)u - (double)w->cx) / (double)w->fx);
+  for (int v = 0; v < w->H; ++v) c->ry[v] = (float)(((double)v - (double)w->cy) / (double)w->fy);
+  c->delta2 = (float)((double)w->delta * (double)w->delta);
+  return 0;
+}
+
+static void cam_free(or_cam* c) { free(c->rx); free(c->ry); }
+
+/* ------------------------------------------------------------ rasteriser */
+typedef struct { int64_t X, Y; float iz; int bad; } or_vtx;
+
+/* object frame -> world (yaw then translation) -> camera -> pixel, snapped */
+static or_vtx transform_vertex(const or_world* w, const or_cam* c, const float* v,
+                               float x, float y, float cs, float sn) {
+  or_vtx o;
+  float t1 = cs * v[0], t2 = sn * v[1];
+  float xw = (t1 - t2) + x;
+  float t3 = sn * v[0], t4 = cs * v[1];
+  float yw = (t3 + t4) + y;
+  float zw = v[2];
+  float cam[3];
+  for (int r = 0; r < 3; ++r) {
+    float a = c->Rcw[r * 3 + 0] * xw;
+    float b = c->Rcw[r * 3 + 1] * yw;
+    float d = c->Rcw[r * 3 + 2] * zw;
+    cam[r] = ((a + b) + d) + c->tcw[r];
+  }
+  o.bad = !(cam[2] > 0.05f);
+  float qx = cam[0] / cam[2], qy = cam[1] / cam[2];
+  float u = w->fx * qx, vv = w->fy * qy;
+  u = u + w->cx;
+  vv = vv + w->cy;
+  if (!(fabsf(u) <= 2048.0f) || !(fabsf(vv) <= 2048.0f)) o.bad = 1;
+  if (o.bad) { o.X = o.Y = 0; o.iz = 0.0f; return o; }
+  o.X = (int64_t)lrintf(16.0f * u);
+  o.Y = (int64_t)lrintf(16.0f * vv);
+  o.iz = 1.0f / cam[2];
+  return o;
+}
+
+/* signed edge function of edge a->b at point P (exact integers); positive
+ * on the inner side of a front-facing triangle */
+static int64_t edge_fn(int64_t Xa, int64_t Ya, int64_t Xb, int64_t Yb, int64_t Px, int64_t Py) {
+  return (Yb - Ya) * (Px - Xa) - (Xb - Xa) * (Py - Ya);
+}
+
+/* top-left tie rule for front faces in this orientation */
+static int owns_edge(int64_t Xa, int64_t Ya, int64_t Xb, int64_t Yb) {
+  int64_t dy = Yb - Ya, dx = Xb - Xa;
+  return dy > 0 || (dy == 0 && dx < 0);
+}
+
+static int64_t floordiv16(int64_t a) { return a >= 0 ? a / 16 : -((-a + 15) / 16); }
+static int64_t ceildiv16(int64_t a) { return -floordiv16(-a); }
+
+/* render one object into zbuf (min), counting culled triangles */
+static void render_object(const or_world* w, const or_cam* c, or_obj o, float* zbuf, int64_t* culled) {
+  const or_mesh* m = &w->meshes[o.mesh];
+  float x = w->xs[o.ix], y = w->ys[o.iy];
+  float cs = w->cos_sin[2 * o.iyaw], sn = w->cos_sin[2 * o.iyaw + 1];
+  for (int t = 0; t < m->n_tris; ++t) {
+    or_vtx v[3];
+    int bad = 0;
+    for (int k = 0; k < 3; ++k) {
+      v[k] = transform_vertex(w, c, m->verts + 3 * (size_t)m->tris[3 * t + k], x, y, cs, sn);
+      bad |= v[k].bad;
+    }
+    if (bad) { (*culled)++; continue; }
+    int64_t A = edge_fn(v[0].X, v[0].Y, v[1].X, v[1].Y, v[2].X, v[2].Y);
+    if (A <= 0) continue; /* back-facing or degenerate */
+    int64_t xmin = v[0].X, xmax = v[0].X, ymin = v[0].Y, ymax = v[0].Y;
+    for (int k = 1; k < 3; ++k) {
+      if (v[k].X < xmin) xmin = v[k].X;
+      if (v[k].X > xmax) xmax = v[k].X;
+      if (v[k].Y < ymin) ymin = v[k].Y;
+      if (v[k].Y > ymax) ymax = v[k].Y;
+    }
+    if (xmax - xmin >= 16384 || ymax - ymin >= 16384) { (*culled)++; continue; }
+    int64_t px0 = ceildiv16(xmin), px1 = floordiv16(xmax);
+    int64_t py0 = ceildiv16(ymin), py1 = floordiv16(ymax);
+    if (px0 < 0) px0 = 0;
+    if (py0 < 0) py0 = 0;
+    if (px1 > w->W - 1) px1 = w->W - 1;
+    if (py1 > w->H - 1) py1 = w->H - 1;
+    int own12 = owns_edge(v[1].X, v[1].Y, v[2].X, v[2].Y);
+    int own20 = owns_edge(v[2].X, v[2].Y, v[0].X, v[0].Y);
+    int own01 = owns_edge(v[0].X, v[0].Y, v[1].X, v[1].Y);
+    float invA = 1.0f / (float)A;
+    for (int64_t py = py0; py <= py1; ++py) {
+      for (int64_t px = px0; px <= px1; ++px) {
+        int64_t Px = 16 * px, Py = 16 * py;
+        int64_t w0 = edge_fn(v[1].X, v[1].Y, v[2].X, v[2].Y, Px, Py);
+        int64_t w1 = edge_fn(v[2].X, v[2].Y, v[0].X, v[0].Y, Px, Py);
+        int64_t w2 = edge_fn(v[0].X, v[0].Y, v[1].X, v[1].Y, Px, Py);
+        int in0 = w0 > 0 || (w0 == 0 && own12);
+        int in1 = w1 > 0 || (w1 == 0 && own20);
+        int in2 = w2 > 0 || (w2 == 0 && own01);
+        if (!(in0 && in1 && in2)) continue;
+        float b0 = (float)w0 * invA, b1 = (float)w1 * invA, b2 = (float)w2 * invA;
+        float s0 = b0 * v[0].iz, s1 = b1 * v[1].iz, s2 = b2 * v[2].iz;
+        float iz = (s0 + s1) + s2;
+        float z = 1.0f / iz;
+        float* dst = &zbuf[py * w->W + px];
+        if (z < *dst) *dst = z;
+      }
+    }
+  }
+}
+
+static void render_scene(const or_world* w, const or_cam* c, const or_obj* objs, int n,
+                         float* zbuf, int64_t* culled) {
+  for (int64_t i = 0; i < (int64_t)w->W * w->H; ++i) zbuf[i] = INFINITY;
+  for (int k = 0; k < n; ++k) render_object(w, c, objs[k], zbuf, culled);
+}
+
+/* ------------------------------------------------------------ point sets */
+typedef struct { float x, y, z; } or_pt;
+
+static or_pt pixel_point(const or_cam* c, int u, int v, float z) {
+  or_pt p = {c->rx[u] * z, c->ry[v] * z, z};
+  return p;
+}
+
+static or_pt cam_to_world(const or_cam* c, or_pt p) {
+  float o[3];
+  for (int r = 0; r < 3; ++r) {
+    float a = c->Rwc[r * 3 + 0] * p.x;
+    float b = c->Rwc[r * 3 + 1] * p.y;
+    float d = c->Rwc[r * 3 + 2] * p.z;
+    o[r] = ((a + b) + d) + c->twc[r];
+  }
+  or_pt q = {o[0], o[1], o[2]};
+  return q;
+}
+
+static float dist2(or_pt a, or_pt b) {
+  float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  float sx = dx * dx, sy = dy * dy, sz = dz * dz;
+  return (sx + sy) + sz;
+}
+
+/* Eq. (1): p is explained by C iff some point of C lies within delta */
+static int explained(or_pt p, const or_pt* C, int64_t n, float delta2) {
+  for (int64_t i = 0; i < n; ++i)
+    if (dist2(p, C[i]) <= delta2) return 1;
+  return 0;
+}
+
+/* V(O): inscribed vertical cylinder of the object's mesh at its pose */
+static int in_volume(const or_world* w, or_obj o, or_pt qw) {
+  const or_mesh* m = &w->meshes[o.mesh];
+  float r2 = (float)((double)m->vol_r * (double)m->vol_r);
+  float dx = qw.x - w->xs[o.ix], dy = qw.y - w->ys[o.iy];
+  float sx = dx * dx, sy = dy * dy;
+  float d2 = sx + sy;
+  return d2 <= r2 && m->vol_zlo <= qw.z && qw.z <= m->vol_zhi;
+}
+
+typedef struct { or_pt* cam; or_pt* world; int64_t n; } or_cloud;
+
+/* observed cloud I: every pixel with a finite positive depth */
+static int observed_cloud(const or_world* w, const or_cam* c, const float* depth, or_cloud* I) {
+  int64_t n = 0, N = (int64_t)w->W * w->H;
+  I->cam = (or_pt*)malloc(sizeof(or_pt) * (size_t)(N > 0 ? N : 1));
+  I->world = (or_pt*)malloc(sizeof(or_pt) * (size_t)(N > 0 ? N : 1));
+  if (!I->cam || !I->world) { free(I->cam); free(I->world); return -1; }
+  for (int v = 0; v < w->H; ++v)
+    for (int u = 0; u < w->W; ++u) {
+      float d = depth[(int64_t)v * w->W + u];
+      if (!(d > 0.0f) || !isfinite(d)) continue;
+      I->cam[n] = pixel_point(c, u, v, d);
+      I->world[n] = cam_to_world(c, I->cam[n]);
+      n++;
+    }
+  I->n = n;
+  return 0;
+}
+
+/* valid pixels of a z-buffer as camera-frame points */
+static int64_t zbuf_points(const or_world* w, const or_cam* c, const float* z, or_pt* out) {
+  int64_t n = 0;
+  for (int v = 0; v < w->H; ++v)
+    for (int u = 0; u < w->W; ++u) {
+      float d = z[(int64_t)v * w->W + u];
+      if (isfinite(d)) out[n++] = pixel_point(c, u, v, d);
+    }
+  return n;
+}
+
+/* ------------------------------------------------------------ edge cost */
+/* One MSGT edge (Eq. (3), Eq. (4)): parent render zp, child object o. */
+static void edge_cost(const or_world* w, const or_cam* c, const or_cloud* I,
+                      const or_obj* parent, int n_parent, const float* zp, or_obj o,
+                      int K_total, float* zc, or_pt* pts, int32_t* rec) {
+  int64_t N = (int64_t)w->W * w->H, culled = 0;
+  for (int64_t i = 0; i < N; ++i) zc[i] = INFINITY;
+  render_object(w, c, o, zc, &culled);
+  int64_t viol = 0, n_new = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    if (!isfinite(zc[i])) continue;
+    if (!isfinite(zp[i])) n_new++;         /* dR: child visible, parent empty */
+    else if (zc[i] < zp[i]) viol++;        /* child occludes the parent's render */
+  }
+  uint32_t flags = culled ? OR_FLAG_CULLED : 0u;
+  memset(rec, 0, sizeof(int32_t) * OR_REC);
+  rec[OR_VIOL] = (int32_t)viol;
+  rec[OR_NNEW] = (int32_t)n_new;
+  if (viol > 0) { rec[OR_FLAGS] = (int32_t)(flags | OR_FLAG_INVALID); return; }
+  rec[OR_FLAGS] = (int32_t)flags;
+
+  /* dR_{j+1} as camera-frame points */
+  int64_t nd = 0;
+  for (int v = 0; v < w->H; ++v)
+    for (int u = 0; u < w->W; ++u) {
+      int64_t i = (int64_t)v * w->W + u;
+      if (isfinite(zc[i]) && !isfinite(zp[i])) pts[nd++] = pixel_point(c, u, v, zc[i]);
+    }
+  int64_t djr = 0;
+  for (int64_t k = 0; k < nd; ++k)
+    if (!explained(pts[k], I->cam, I->n, c->delta2)) djr++;
+  int64_t djo = 0;
+  for (int64_t k = 0; k < I->n; ++k)
+    if (in_volume(w, o, I->world[k]) && !explained(I->cam[k], pts, nd, c->delta2)) djo++;
+  rec[OR_DJR] = (int32_t)djr;
+  rec[OR_DJO] = (int32_t)djo;
+
+  if (n_parent + 1 == K_total) {
+    /* residual(K): observed points outside V_K unexplained by R_K */
+    for (int64_t i = 0; i < N; ++i) zc[i] = (zc[i] < zp[i]) ? zc[i] : zp[i];
+    int64_t nr = zbuf_points(w, c, zc, pts);
+    int64_t resid = 0;
+    for (int64_t k = 0; k < I->n; ++k) {
+      int inside = in_volume(w, o, I->world[k]);
+      for (int j = 0; j < n_parent && !inside; ++j) inside = in_volume(w, parent[j], I->world[k]);
+      if (inside) continue;
+      if (!explained(I->cam[k], pts, nr, c->delta2)) resid++;
+    }
+    rec[OR_RESID] = (int32_t)resid;
+  }
+}
+
+/* ================================================================ exports */
+
+/* z-buffer render of n objects (min z; +inf where empty). Returns the
+ * number of culled triangles, or -1 on allocation failure. */
+int64_t or_render(const or_world* w, const or_obj* objs, int32_t n, float* zbuf) {
+  or_cam c;
+  if (cam_init(w, &c)) return -1;
+  int64_t culled = 0;
+  render_scene(w, &c, objs, n, zbuf, &culled);
+  cam_free(&c);
+  return culled;
+}
+
+/* observed cloud I in camera and world frames; returns |I| (arrays must hold
+ * W*H points of 3 floats) */
+int64_t or_observed(const or_world* w, const float* depth, float* cam_xyz, float* world_xyz) {
+  or_cam c;
+  if (cam_init(w, &c)) return -1;
+  or_cloud I;
+  if (observed_cloud(w, &c, depth, &I)) { cam_free(&c); return -1; }
+  for (int64_t k = 0; k < I.n; ++k) {
+    cam_xyz[3 * k] = I.cam[k].x; cam_xyz[3 * k + 1] = I.cam[k].y; cam_xyz[3 * k + 2] = I.cam[k].z;
+    world_xyz[3 * k] = I.world[k].x; world_xyz[3 * k + 1] = I.world[k].y; world_xyz[3 * k + 2] = I.world[k].z;
+  }
+  int64_t n = I.n;
+  free(I.cam); free(I.world); cam_free(&c);
+  return n;
+}
+
+/* Eq. (1) over explicit clouds: out[k] = 1 iff P[k] is unexplained by Q */
+int32_t or_unexplained(const float* P, int64_t np, const float* Q, int64_t nq, float delta, int32_t* out) {
+  float d2 = (float)((double)delta * (double)delta);
+  for (int64_t k = 0; k < np; ++k) {
+    or_pt p = {P[3 * k], P[3 * k + 1], P[3 * k + 2]};
+    int ex = 0;
+    for (int64_t i = 0; i < nq && !ex; ++i) {
+      or_pt q = {Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]};
+      ex = dist2(p, q) <= d2;
+    }
+    out[k] = !ex;
+  }
+  return 0;
+}
+
+/* Undecomposed explanation cost of Sec. III-B for a full assignment:
+ * out[0] = J_o (observed points unexplained by R_K), out[1] = J_r. */
+int32_t or_cost_J(const or_world* w, const float* depth, const or_obj* objs, int32_t K, int64_t* out) {
+  or_cam c;
+  if (cam_init(w, &c)) return -1;
+  or_cloud I;
+  if (observed_cloud(w, &c, depth, &I)) { cam_free(&c); return -1; }
+  int64_t N = (int64_t)w->W * w->H, culled = 0;
+  float* z = (float*)malloc(sizeof(float) * (size_t)N);
+  or_pt* R = (or_pt*)malloc(sizeof(or_pt) * (size_t)N);
+  if (!z || !R) { free(z); free(R); free(I.cam); free(I.world); cam_free(&c); return -1; }
+  render_scene(w, &c, objs, K, z, &culled);
+  int64_t nr = zbuf_points(w, &c, z, R);
+  int64_t jo = 0, jr = 0;
+  for (int64_t k = 0; k < I.n; ++k) jo += !explained(I.cam[k], R, nr, c.delta2);
+  for (int64_t k = 0; k < nr; ++k) jr += !explained(R[k], I.cam, I.n, c.delta2);
+  out[0] = jo; out[1] = jr;
+  free(z); free(R); free(I.cam); free(I.world); cam_free(&c);
+  return 0;
+}
+
+/* Edge costs for a batch of successors. parents: n_par x k_max objects,
+ * parent_len[i] of them used; hypothesis h adds hyps[h] to parent
+ * hyp_parent[h]; K_total = objects in a complete scene. recs: n_hyp x 6. */
+int32_t or_eval_batch(const or_world* w, const float* depth,
+                      const or_obj* parents, const int32_t* parent_len, int32_t n_par, int32_t k_max,
+                      const int32_t* hyp_parent, const or_obj* hyps, int64_t n_hyp,
+                      int32_t K_total, int32_t* recs, int32_t n_threads) {
+  or_cam c;
+  if (cam_init(w, &c)) return -1;
+  or_cloud I;
+  if (observed_cloud(w, &c, depth, &I)) { cam_free(&c); return -1; }
+  int64_t N = (int64_t)w->W * w->H;
+  float* zp = (float*)malloc(sizeof(float) * (size_t)N * (size_t)(n_par > 0 ? n_par : 1));
+  if (!zp) { free(I.cam); free(I.world); cam_free(&c); return -1; }
+  for (int32_t p = 0; p < n_par; ++p) {
+    int64_t culled = 0;
+    render_scene(w, &c, parents + (int64_t)p * k_max, parent_len[p], zp + (int64_t)p * N, &culled);
+  }
+  int err = 0;
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+  (void)n_threads;
+#endif
+#pragma omp parallel
+  {
+    float* zc = (float*)malloc(sizeof(float) * (size_t)N);
+    or_pt* pts = (or_pt*)malloc(sizeof(or_pt) * (size_t)N);
+    if (!zc || !pts) {
+#pragma omp atomic write
+      err = 1;
+    } else {
+#pragma omp for schedule(dynamic, 1)
+      for (int64_t h = 0; h < n_hyp; ++h) {
+        int32_t p = hyp_parent[h];
+        edge_cost(w, &c, &I, parents + (int64_t)p * k_max, parent_len[p], zp + (int64_t)p * N,
+                  hyps[h], K_total, zc, pts, recs + h * OR_REC);
+      }
+    }
+    free(zc); free(pts);
+  }
+  free(zp); free(I.cam); free(I.world); cam_free(&c);
+  return err ? -1 : 0;
+}
+
+int32_t or_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

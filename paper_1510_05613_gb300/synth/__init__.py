@@ -1,0 +1,447 @@
+"""Seeded synthetic PERCH workloads: procedural meshes, pose grids, camera,
+ground-truth scenes and simulated noisy depth observations.
+
+This module is input generation only. It holds none of the method's
+arithmetic (no z-buffer rendering, no explanation cost, no search): both the
+CPU oracle and the CUDA library consume what it produces. The observation is
+made by a double-precision ray caster (``sensor.c``), a different algorithm
+from the fixed-point rasteriser the method uses.
+
+The paper's own data (the occlusion dataset of its Sec. V-A, 36 CAD models)
+is not available, so procedural tabletop objects with the shapes and sizes of
+the workloads below stand in for it. The problem statement (Sec. III) fixes the
+structure: known object models, known object count and types, 3-DoF poses
+(x, y, yaw) on a table, a known sensor pose and intrinsics, and an observed
+cloud containing only object points.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SENSOR_SRC = os.path.join(_HERE, "sensor.c")
+_SENSOR_LIB = os.path.join(_HERE, "libperch_sensor.so")
+
+# ---------------------------------------------------------------------------
+# counter-based random numbers (SplitMix64, Steele/Lea/Flood 2014)
+# ---------------------------------------------------------------------------
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Values ``offset .. offset+n-1`` of the SplitMix64 stream of ``seed``."""
+    with np.errstate(over="ignore"):
+        i = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Doubles in [0, 1) from the top 53 bits of SplitMix64."""
+    return (splitmix64(seed, n, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def normal(seed: int, n: int) -> np.ndarray:
+    """Standard normals by Box-Muller over two interleaved uniform streams."""
+    u = uniform(seed, 2 * n)
+    u1 = 1.0 - u[0::2]  # in (0, 1]
+    u2 = u[1::2]
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+def substream(seed: int, tag: int) -> int:
+    """Independent seed for a named sub-stream of a scene's seed."""
+    return int(splitmix64(seed * 7919 + tag, 1)[0])
+
+
+# ---------------------------------------------------------------------------
+# procedural meshes (object frame: z up, base on z = 0, CCW seen from outside)
+# ---------------------------------------------------------------------------
+@dataclass
+class Mesh:
+    name: str
+    verts: np.ndarray  # float32 (V, 3)
+    tris: np.ndarray  # int32 (T, 3)
+    vol_r: float  # V(O): inscribed vertical cylinder about the object origin
+    vol_zlo: float
+    vol_zhi: float
+
+    @property
+    def n_verts(self) -> int:
+        return int(self.verts.shape[0])
+
+    @property
+    def n_tris(self) -> int:
+        return int(self.tris.shape[0])
+
+    @property
+    def footprint_radius(self) -> float:
+        v = self.verts.astype(np.float64)
+        return float(np.sqrt((v[:, 0] ** 2 + v[:, 1] ** 2).max()))
+
+
+def _orient_outward(verts: np.ndarray, tris: np.ndarray, centre) -> np.ndarray:
+    """Make every triangle's normal point away from ``centre`` (valid for
+    star-shaped, here convex, solids)."""
+    v = verts.astype(np.float64)
+    a, b, c = v[tris[:, 0]], v[tris[:, 1]], v[tris[:, 2]]
+    n = np.cross(b - a, c - a)
+    out = ((a + b + c) / 3.0) - np.asarray(centre, np.float64)
+    flip = (n * out).sum(1) < 0
+    t = tris.copy()
+    t[flip, 1], t[flip, 2] = tris[flip, 2], tris[flip, 1]
+    return t
+
+
+def _weld(points: np.ndarray, tris: np.ndarray, decimals: int = 9):
+    key = np.round(points, decimals)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    inv = inv.reshape(-1)
+    new_pts = points[first]
+    new_tris = inv[tris]
+    keep = (new_tris[:, 0] != new_tris[:, 1]) & (new_tris[:, 1] != new_tris[:, 2]) & (new_tris[:, 0] != new_tris[:, 2])
+    return new_pts, new_tris[keep]
+
+
+def box_mesh(a: float, b: float, h: float, n: int, name: str = "box") -> Mesh:
+    """Box of size a x b x h (x, y, z), every face split into n x n quads."""
+    pts, tris = [], []
+    size = np.array([a, b, h])
+    lo = np.array([-a / 2, -b / 2, 0.0])
+    # (normal axis, sign, u axis, v axis) with u x v = sign * normal
+    faces = [(2, 1, 0, 1), (2, -1, 1, 0), (0, 1, 1, 2), (0, -1, 2, 1), (1, 1, 2, 0), (1, -1, 0, 2)]
+    for ax, sg, ua, va in faces:
+        base = len(pts)
+        for j in range(n + 1):
+            for i in range(n + 1):
+                p = np.zeros(3)
+                p[ax] = 1.0 if sg > 0 else 0.0
+                p[ua] = i / n
+                p[va] = j / n
+                pts.append(lo + p * size)
+        for j in range(n):
+            for i in range(n):
+                q00 = base + j * (n + 1) + i
+                q10, q01, q11 = q00 + 1, q00 + n + 1, q00 + n + 2
+                tris.append((q00, q10, q11))
+                tris.append((q00, q11, q01))
+    P, T = _weld(np.array(pts), np.array(tris, np.int64))
+    T = _orient_outward(P, T, (0.0, 0.0, h / 2))
+    r = 0.9 * min(a, b) / 2
+    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h)
+
+
+def cylinder_mesh(R: float, h: float, n_seg: int, n_rings: int, name: str = "cylinder") -> Mesh:
+    """Closed n-gon cylinder: side split into n_rings bands, fan caps."""
+    pts = []
+    for l in range(n_rings + 1):
+        z = h * l / n_rings
+        for k in range(n_seg):
+            phi = 2.0 * math.pi * k / n_seg
+            pts.append((R * math.cos(phi), R * math.sin(phi), z))
+    top_c = len(pts); pts.append((0.0, 0.0, h))
+    bot_c = len(pts); pts.append((0.0, 0.0, 0.0))
+    tris = []
+    for l in range(n_rings):
+        for k in range(n_seg):
+            a = l * n_seg + k
+            b = l * n_seg + (k + 1) % n_seg
+            c = (l + 1) * n_seg + (k + 1) % n_seg
+            d = (l + 1) * n_seg + k
+            tris.append((a, b, c)); tris.append((a, c, d))
+    for k in range(n_seg):
+        tris.append((top_c, n_rings * n_seg + k, n_rings * n_seg + (k + 1) % n_seg))
+        tris.append((bot_c, (k + 1) % n_seg, k))
+    P, T = np.array(pts), np.array(tris, np.int64)
+    T = _orient_outward(P, T, (0.0, 0.0, h / 2))
+    r = 0.9 * R * math.cos(math.pi / n_seg)
+    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h)
+
+
+def _spow(x, e):
+    return np.sign(x) * np.abs(x) ** e
+
+
+def superquadric_mesh(a1: float, a2: float, a3: float, e1: float, e2: float,
+                      n_eta: int, n_omega: int, name: str = "superquadric") -> Mesh:
+    """Superquadric x = a1 C(eta)^e1 C(w)^e2, y = a2 C(eta)^e1 S(w)^e2,
+    z = a3 S(eta)^e1 (signed powers), shifted so its base sits on z = 0."""
+    etas = np.linspace(-math.pi / 2, math.pi / 2, n_eta + 1)[1:-1]
+    oms = np.linspace(-math.pi, math.pi, n_omega, endpoint=False)
+    E, O = np.meshgrid(etas, oms, indexing="ij")
+    x = a1 * _spow(np.cos(E), e1) * _spow(np.cos(O), e2)
+    y = a2 * _spow(np.cos(E), e1) * _spow(np.sin(O), e2)
+    z = a3 * _spow(np.sin(E), e1) + a3
+    pts = list(np.stack([x, y, z], -1).reshape(-1, 3))
+    nr = len(etas)
+    bot = len(pts); pts.append((0.0, 0.0, 0.0))
+    top = len(pts); pts.append((0.0, 0.0, 2 * a3))
+    tris = []
+    for l in range(nr - 1):
+        for k in range(n_omega):
+            a = l * n_omega + k
+            b = l * n_omega + (k + 1) % n_omega
+            c = (l + 1) * n_omega + (k + 1) % n_omega
+            d = (l + 1) * n_omega + k
+            tris.append((a, b, c)); tris.append((a, c, d))
+    for k in range(n_omega):
+        tris.append((bot, k, (k + 1) % n_omega))
+        tris.append((top, (nr - 1) * n_omega + k, (nr - 1) * n_omega + (k + 1) % n_omega))
+    P, T = np.array(pts, np.float64), np.array(tris, np.int64)
+    T = _orient_outward(P, T, (0.0, 0.0, a3))
+    # inscribed cylinder: |z - a3| <= 0.8 a3; cross-section radius shrinks
+    # with |z|, take it at the first tessellated ring beyond 0.8 a3, and the
+    # n_omega-gon chord factor, then shrink by 10%.
+    zr = np.abs(z[:, 0] - a3)
+    beyond = zr[zr >= 0.8 * a3]
+    zb = beyond.min() if beyond.size else a3
+    s = min(1.0, zb / a3)
+    rho = max(0.0, 1.0 - s ** (2.0 / e1)) ** (e1 / 2.0)
+    r = 0.9 * min(a1, a2) * rho * math.cos(math.pi / n_omega)
+    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.2 * a3, 1.8 * a3)
+
+
+# ---------------------------------------------------------------------------
+# camera, pose grid
+# ---------------------------------------------------------------------------
+@dataclass
+class Camera:
+    W: int
+    H: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    T_wc: np.ndarray  # float32 (3, 4): camera -> world, row-major
+
+    @property
+    def fxfycxcy(self) -> np.ndarray:
+        return np.array([self.fx, self.fy, self.cx, self.cy], np.float32)
+
+
+def look_at(eye, target, up=(0.0, 0.0, 1.0)) -> np.ndarray:
+    """Camera->world (3x4, float32) for an OpenCV camera (x right, y down,
+    z forward) at ``eye`` looking at ``target``."""
+    eye, target, up = (np.asarray(v, np.float64) for v in (eye, target, up))
+    zc = target - eye; zc /= np.linalg.norm(zc)
+    xc = np.cross(zc, up); xc /= np.linalg.norm(xc)
+    yc = np.cross(zc, xc)
+    T = np.zeros((3, 4))
+    T[:, 0], T[:, 1], T[:, 2], T[:, 3] = xc, yc, zc, eye
+    return T.astype(np.float32)
+
+
+@dataclass
+class PoseGrid:
+    xs: np.ndarray  # float32 (nx,)
+    ys: np.ndarray  # float32 (ny,)
+    cos_sin: np.ndarray  # float32 (n_yaw, 2)
+
+    @property
+    def nx(self): return int(self.xs.shape[0])
+
+    @property
+    def ny(self): return int(self.ys.shape[0])
+
+    @property
+    def n_yaw(self): return int(self.cos_sin.shape[0])
+
+    @property
+    def n_poses(self): return self.nx * self.ny * self.n_yaw
+
+
+def pose_grid(x0: float, step: float, n: int, n_yaw: int) -> PoseGrid:
+    xs = np.array([x0 + step * k for k in range(n)], np.float64).astype(np.float32)
+    th = [2.0 * math.pi * k / n_yaw for k in range(n_yaw)]
+    cs = np.array([[math.cos(t), math.sin(t)] for t in th], np.float64).astype(np.float32)
+    return PoseGrid(xs, xs.copy(), cs)
+
+
+# object record used by every layer: (mesh, ix, iy, iyaw)
+OBJ_DTYPE = np.dtype([("mesh", np.uint16), ("iyaw", np.uint16), ("ix", np.int16), ("iy", np.int16)])
+
+
+def objs(rows) -> np.ndarray:
+    """Object records from (mesh, ix, iy, iyaw) tuples."""
+    a = np.zeros(len(rows), OBJ_DTYPE)
+    for i, (m, ix, iy, k) in enumerate(rows):
+        a[i] = (m, k, ix, iy)
+    return a
+
+
+def all_hypotheses(grid: PoseGrid, meshes_ids) -> np.ndarray:
+    """Every (mesh, ix, iy, iyaw) on the grid for the given mesh ids."""
+    m = np.asarray(list(meshes_ids), np.int64)
+    M, X, Y, K = np.meshgrid(m, np.arange(grid.nx), np.arange(grid.ny), np.arange(grid.n_yaw), indexing="ij")
+    a = np.zeros(M.size, OBJ_DTYPE)
+    a["mesh"], a["ix"], a["iy"], a["iyaw"] = M.ravel(), X.ravel(), Y.ravel(), K.ravel()
+    return a
+
+
+# ---------------------------------------------------------------------------
+# sensor simulation
+# ---------------------------------------------------------------------------
+_sensor = None
+
+
+def _load_sensor():
+    global _sensor
+    if _sensor is None:
+        if (not os.path.exists(_SENSOR_LIB)) or os.path.getmtime(_SENSOR_LIB) < os.path.getmtime(_SENSOR_SRC):
+            build_sensor()
+        lib = ctypes.CDLL(_SENSOR_LIB)
+        lib.synth_raycast.restype = ctypes.c_int
+        lib.synth_raycast.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long, ctypes.c_void_p]
+        _sensor = lib
+    return _sensor
+
+
+def build_sensor() -> str:
+    tmp = _SENSOR_LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SENSOR_SRC, "-lm"])
+    os.replace(tmp, _SENSOR_LIB)
+    return _SENSOR_LIB
+
+
+def place(mesh: Mesh, grid: PoseGrid, ix: int, iy: int, iyaw: int) -> np.ndarray:
+    """World-frame triangle soup (T, 3, 3) of a placed mesh, in double."""
+    v = mesh.verts.astype(np.float64)
+    c, s = float(grid.cos_sin[iyaw, 0]), float(grid.cos_sin[iyaw, 1])
+    w = np.empty_like(v)
+    w[:, 0] = c * v[:, 0] - s * v[:, 1] + float(grid.xs[ix])
+    w[:, 1] = s * v[:, 0] + c * v[:, 1] + float(grid.ys[iy])
+    w[:, 2] = v[:, 2]
+    return w[mesh.tris]
+
+
+def raycast_depth(cam: Camera, meshes, grid: PoseGrid, scene) -> np.ndarray:
+    """Noise-free sensor depth (float64, H x W, 0 = no return)."""
+    soups = [place(meshes[int(o["mesh"])], grid, int(o["ix"]), int(o["iy"]), int(o["iyaw"])) for o in scene]
+    tris = np.ascontiguousarray(np.concatenate(soups, 0) if soups else np.zeros((0, 3, 3)), np.float64)
+    T = np.ascontiguousarray(cam.T_wc.astype(np.float64))
+    out = np.zeros((cam.H, cam.W), np.float64)
+    rc = _load_sensor().synth_raycast(cam.W, cam.H, cam.fx, cam.fy, cam.cx, cam.cy,
+                                      T.ctypes.data, tris.ctypes.data, tris.shape[0], out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("synth_raycast failed")
+    return out
+
+
+def observe(cam: Camera, meshes, grid: PoseGrid, scene, sigma: float, dropout: float, seed: int) -> np.ndarray:
+    """Simulated observation: ray-cast depth + N(0, sigma^2) on z, then each
+    pixel dropped (set to 0 = missing) with probability ``dropout``."""
+    d = raycast_depth(cam, meshes, grid, scene)
+    n = d.size
+    noise = normal(substream(seed, 1), n).reshape(d.shape)
+    drop = uniform(substream(seed, 2), n).reshape(d.shape) < dropout
+    valid = d > 0
+    d = np.where(valid, d + sigma * noise, 0.0)
+    d[drop] = 0.0
+    d[d <= 0] = 0.0
+    return d.astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+@dataclass
+class Workload:
+    name: str
+    cam: Camera
+    meshes: list
+    grid: PoseGrid
+    delta: float
+    gt: np.ndarray  # OBJ_DTYPE (K,)
+    depth: np.ndarray  # float32 (H, W) observation
+    sigma: float = 0.0
+    dropout: float = 0.0
+    seed: int = 0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def K(self) -> int:
+        return int(self.gt.shape[0])
+
+    @property
+    def mesh_multiset(self):
+        return sorted(int(m) for m in self.gt["mesh"])
+
+
+def sample_scene(meshes, grid: PoseGrid, mesh_ids, seed: int, margin: float = 0.005,
+                 max_tries: int = 100000) -> np.ndarray:
+    """Ground-truth objects on the pose grid whose circumscribed footprint
+    circles are disjoint (no interpenetration)."""
+    k = len(mesh_ids)
+    u = uniform(substream(seed, 3), 3 * k * max_tries)
+    pos = 0
+    for _ in range(max_tries):
+        rows = []
+        for m in mesh_ids:
+            ix = min(int(u[pos] * grid.nx), grid.nx - 1)
+            iy = min(int(u[pos + 1] * grid.ny), grid.ny - 1)
+            iyaw = min(int(u[pos + 2] * grid.n_yaw), grid.n_yaw - 1)
+            pos += 3
+            rows.append((m, ix, iy, iyaw))
+        ok = True
+        for i in range(k):
+            for j in range(i + 1, k):
+                mi, mj = rows[i], rows[j]
+                dx = float(grid.xs[mi[1]]) - float(grid.xs[mj[1]])
+                dy = float(grid.ys[mi[2]]) - float(grid.ys[mj[2]])
+                rr = meshes[mi[0]].footprint_radius + meshes[mj[0]].footprint_radius + margin
+                if dx * dx + dy * dy < rr * rr:
+                    ok = False
+        if ok:
+            return objs(rows)
+    raise RuntimeError("could not sample a non-interpenetrating scene")
+
+
+def camera_c1() -> Camera:
+    return Camera(160, 120, 140.0, 140.0, 79.5, 59.5, look_at((0.0, -1.0, 1.0), (0.0, 0.0, 0.0)))
+
+
+def camera_c2() -> Camera:
+    return Camera(640, 480, 525.0, 525.0, 319.5, 239.5, look_at((0.0, -1.0, 1.0), (0.0, 0.0, 0.0)))
+
+
+def meshes_c1():
+    return [box_mesh(0.10, 0.06, 0.15, 9), cylinder_mesh(0.04, 0.12, 64, 15)]
+
+
+def meshes_c2():
+    return [box_mesh(0.10, 0.06, 0.15, 29), cylinder_mesh(0.04, 0.12, 128, 38),
+            superquadric_mesh(0.04, 0.04, 0.07, 0.5, 1.0, 51, 100)]
+
+
+def workload_c1(scene: int = 0, grid: PoseGrid | None = None) -> Workload:
+    """160x120, fx=fy=140, box (~1k triangles) + cylinder (~2k), poses on a
+    10x10 grid at 5 cm x 8 yaws, sigma = 2 mm, 5% dropout, delta = 1 cm, K = 2."""
+    seed = 1000 * 1 + scene
+    cam, meshes = camera_c1(), meshes_c1()
+    grid = grid or pose_grid(-0.225, 0.05, 10, 8)
+    gt = sample_scene(meshes, grid, [0, 1], seed)
+    depth = observe(cam, meshes, grid, gt, 0.002, 0.05, seed)
+    return Workload("c1", cam, meshes, grid, 0.01, gt, depth, 0.002, 0.05, seed)
+
+
+def workload_c2(scene: int = 0, grid: PoseGrid | None = None) -> Workload:
+    """640x480, fx=fy=525, box / cylinder / superquadric (eps1=0.5, eps2=1)
+    of ~10k triangles each, poses on a 50x50 grid at 2 cm x 16 yaws,
+    sigma = 3 mm, 5% dropout, delta = 1 cm, K = 3."""
+    seed = 1000 * 2 + scene
+    cam, meshes = camera_c2(), meshes_c2()
+    grid = grid or pose_grid(-0.49, 0.02, 50, 16)
+    gt = sample_scene(meshes, grid, [0, 1, 2], seed)
+    depth = observe(cam, meshes, grid, gt, 0.003, 0.05, seed)
+    return Workload("c2", cam, meshes, grid, 0.01, gt, depth, 0.003, 0.05, seed)

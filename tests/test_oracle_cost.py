@@ -1,0 +1,168 @@
+"""Pins of the oracle's explanation cost (Eq. (1), Sec. III-B, Sec. IV-A /
+Eq. (2), Eq. (3), Eq. (4)).
+
+Each test fixes a value from outside the oracle: exact-delta ties of the
+indicator, float64 brute force, the K = 1 identity between the decomposed and
+the undecomposed cost, the zero-cost ground-truth path on a noise-free
+observation, and the empty-observation / infinite-delta special cases.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1510_05613_gb300 import synth
+
+
+def test_indicator_exact_delta_ties():
+    # Eq. (1): unexplained only when the distance EXCEEDS delta
+    P = np.array([[0, 0, 0], [0, 0, 0], [0, 0, 0]], np.float32)
+    # (0.375, 0.5, 0): d^2 = 0.390625 = 0.625^2 exactly in binary32
+    assert oracle.unexplained(P[:1], np.array([[0.375, 0.5, 0.0]], np.float32), 0.625).tolist() == [0]
+    assert oracle.unexplained(P[:1], np.array([[0.0, 0.0, 0.5]], np.float32), 0.5).tolist() == [0]
+    nxt = np.nextafter(np.float32(0.5), np.float32(1.0))
+    assert oracle.unexplained(P[:1], np.array([[0.0, nxt, 0.0]], np.float32), 0.5).tolist() == [1]
+    # empty cloud: min over nothing is +inf, so everything is unexplained
+    assert oracle.unexplained(P, np.zeros((0, 3), np.float32), 1.0).tolist() == [1, 1, 1]
+
+
+def test_indicator_matches_float64_brute_force():
+    rng = np.random.default_rng(11)
+    P = rng.uniform(-0.1, 0.1, (400, 3)).astype(np.float32)
+    Q = rng.uniform(-0.1, 0.1, (300, 3)).astype(np.float32)
+    delta = 0.02
+    got = oracle.unexplained(P, Q, delta)
+    d2 = ((P[:, None, :].astype(np.float64) - Q[None, :, :].astype(np.float64)) ** 2).sum(-1)
+    mind = d2.min(1)
+    clear = np.abs(mind - delta * delta) > 1e-9  # away from the rounding band
+    assert clear.sum() > 390
+    assert np.array_equal(got[clear], (mind[clear] > delta * delta).astype(np.int32))
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return synth.workload_c1()
+
+
+def test_k1_decomposition_equals_undecomposed_cost(c1):
+    """For K = 1 the decomposition of Sec. IV-A is exact: dJr = J_r and
+    dJo + residual(1) = J_o (dR_1 = R_1, V_1 = V(O_1))."""
+    w = oracle.World.of(c1)
+    rng = np.random.default_rng(5)
+    hyps = synth.all_hypotheses(c1.grid, [0, 1])
+    pick = hyps[rng.choice(len(hyps), 40, replace=False)]
+    # include the ground-truth poses (dense overlaps with the observation)
+    pick = np.concatenate([pick, c1.gt])
+    recs = oracle.eval_batch(w, c1.depth, [pick[:0]], np.zeros(len(pick), np.int32), pick, 1)
+    nonzero = 0
+    for h, r in zip(pick, recs):
+        jo, jr = oracle.cost_J(w, c1.depth, np.array([h]))
+        assert r[3] == 0  # nothing to occlude under an empty parent
+        assert r[0] == jr and r[1] + r[2] == jo, (h, r, jo, jr)
+        nonzero += (r[1] > 0) + (r[2] > 0)
+    assert nonzero > 10
+
+
+def _noise_free(w, gt):
+    z, _ = oracle.render(w, gt)
+    return np.where(np.isfinite(z), z, 0).astype(np.float32)
+
+
+def _path_costs(w, depth, order, K):
+    recs = []
+    for j in range(len(order)):
+        r = oracle.eval_batch(w, depth, [order[:j]], np.zeros(1, np.int32), order[j:j + 1], K)[0]
+        recs.append(r)
+    return recs
+
+
+def test_ground_truth_path_has_zero_cost_on_noise_free_observation(c1):
+    """Observation = render of the ground truth itself: along an order in
+    which no object occludes an earlier one, every edge is valid and costs 0."""
+    w = oracle.World.of(c1)
+    depth = _noise_free(w, c1.gt)
+    found = False
+    for perm in itertools.permutations(range(c1.K)):
+        order = c1.gt[list(perm)]
+        recs = _path_costs(w, depth, order, c1.K)
+        if all(r[3] == 0 for r in recs):
+            found = True
+            for r in recs:
+                assert r[0] == 0 and r[1] == 0 and r[2] == 0, r
+                assert r[4] > 0
+    assert found
+
+
+def test_c2_ground_truth_path_zero_cost():
+    wl = synth.workload_c2()
+    w = oracle.World.of(wl)
+    depth = _noise_free(w, wl.gt)
+    best = None
+    for perm in itertools.permutations(range(wl.K)):
+        recs = _path_costs(w, depth, wl.gt[list(perm)], wl.K)
+        if all(r[3] == 0 for r in recs):
+            best = recs
+            break
+    assert best is not None
+    assert all(r[0] == 0 and r[1] == 0 and r[2] == 0 for r in best)
+
+
+def test_empty_observation_special_case(c1):
+    """I empty: every rendered point is unexplained (dJr = |dR|); nothing to
+    count on the observed side (dJo = residual = 0)."""
+    w = oracle.World.of(c1)
+    depth = np.zeros_like(c1.depth)
+    hyps = synth.all_hypotheses(c1.grid, [0, 1])[::97]
+    recs = oracle.eval_batch(w, depth, [c1.gt[:1]], np.zeros(len(hyps), np.int32), hyps, 2)
+    valid = recs[:, 3] == 0
+    assert valid.sum() > 5
+    assert np.array_equal(recs[valid, 0], recs[valid, 4])
+    assert np.all(recs[valid, 1] == 0) and np.all(recs[valid, 2] == 0)
+
+
+def test_infinite_delta_special_case(c1):
+    """delta -> infinity: everything is explained by any non-empty cloud."""
+    w = oracle.World.of(c1, delta=1000.0)
+    hyps = synth.all_hypotheses(c1.grid, [0, 1])[::53]
+    recs = oracle.eval_batch(w, c1.depth, [c1.gt[:1]], np.zeros(len(hyps), np.int32), hyps, 2)
+    valid = recs[:, 3] == 0
+    assert valid.sum() > 5
+    assert np.all(recs[valid, 0] == 0)
+    # dJo is zero whenever dR is non-empty; residual zero since R_K is non-empty
+    assert np.all(recs[valid & (recs[:, 4] > 0), 1] == 0)
+    assert np.all(recs[valid, 2] == 0)
+
+
+def test_monotone_constraint(c1):
+    """Eq. (3): a child that would occlude the parent's render is invalid;
+    re-placing a parent's object exactly is valid with an empty dR."""
+    w = oracle.World.of(c1)
+    parent = c1.gt[:1]
+    same = oracle.eval_batch(w, c1.depth, [parent], np.zeros(1, np.int32), parent, 2)[0]
+    assert same[3] == 0 and same[4] == 0
+    # every pose of the other object in front of / behind the parent
+    hyps = synth.all_hypotheses(c1.grid, [1])
+    recs = oracle.eval_batch(w, c1.depth, [parent], np.zeros(len(hyps), np.int32), hyps, 2)
+    zp, _ = oracle.render(w, parent)
+    n_checked = 0
+    for h, r in zip(hyps[::37], recs[::37]):
+        zc, _ = oracle.render(w, np.array([h]))
+        both = np.isfinite(zc) & np.isfinite(zp)
+        v = int((zc[both] < zp[both]).sum())
+        assert r[3] == v
+        if v > 0:
+            assert r[5] & oracle.FLAG_INVALID and r[0] == r[1] == r[2] == 0
+            n_checked += 1
+        else:
+            assert r[4] == int((np.isfinite(zc) & ~np.isfinite(zp)).sum())
+    assert n_checked > 0
+
+
+def test_residual_only_at_last_level(c1):
+    w = oracle.World.of(c1)
+    hyps = synth.all_hypotheses(c1.grid, [1])[::41]
+    r_mid = oracle.eval_batch(w, c1.depth, [c1.gt[:0]], np.zeros(len(hyps), np.int32), hyps, 2)
+    assert np.all(r_mid[:, 2] == 0)
+    r_last = oracle.eval_batch(w, c1.depth, [c1.gt[:1]], np.zeros(len(hyps), np.int32), hyps, 2)
+    assert (r_last[r_last[:, 3] == 0, 2] > 0).any()
