@@ -1,0 +1,188 @@
+/*
+ * perch.h -- C ABI of the GB300 PERCH successor-evaluation library.
+ *
+ * PERCH (Narayanan & Likhachev, "PERCH: Perception via Search for
+ * Multi-Object Recognition and Localization") localises K known objects on a
+ * table by searching the Monotone Scene Generation Tree (MSGT, Sec. IV-A).
+ * This library evaluates MSGT successors in bulk on one GPU: it z-buffer
+ * renders each (object, x, y, yaw) hypothesis over its parent scene and counts
+ * the explanation edge cost of Eq. (4). It also runs the tree search of
+ * Sec. IV-B over those evaluations.
+ *
+ * Conventions for every entry point:
+ *   - returns a perch_status (0 = PERCH_OK); never aborts or exits; the
+ *     message of the last failure is available from perch_last_error();
+ *   - host input buffers are owned by the caller and are copied (or fully
+ *     consumed) before the call returns; nothing keeps a caller pointer;
+ *   - all device memory the library allocates is owned by the context and
+ *     released by perch_destroy();
+ *   - a context is not thread-safe; use one context per host thread;
+ *   - world frame: z up, table plane z = 0; camera frame: x right, y down,
+ *     z forward (pinhole, pixel centres at integer (u, v), depth = camera Z);
+ *   - all floating-point arithmetic on the evaluation path is IEEE binary32
+ *     with round-to-nearest-even and no fused multiply-add, in the operation
+ *     order the oracle in oracle/ states, so results are bit-exact with it.
+ */
+#ifndef PERCH_H_
+#define PERCH_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PERCH_OK = 0,
+  PERCH_E_ARG = -1,     /* invalid argument (null pointer, bad size, bad index) */
+  PERCH_E_CUDA = -2,    /* a CUDA call failed; the message names it */
+  PERCH_E_OOM = -3,     /* device or host allocation failed */
+  PERCH_E_STATE = -4,   /* call order: meshes / pose grid / observation missing */
+  PERCH_E_TIMEOUT = -5, /* search limit reached; best solution so far returned */
+  PERCH_E_RANGE = -6    /* a hypothesis does not fit the renderer's tile limit */
+} perch_status;
+
+typedef struct perch_ctx perch_ctx;
+
+/* Triangle mesh of one object type (Sec. III: "3D models of N unique
+ * objects"). Object frame: z up, base on z = 0, origin on the vertical axis the
+ * yaw turns about. Triangles are counter-clockwise seen from outside. V(O),
+ * the conservative object volume of Sec. III-A, is the inscribed vertical
+ * cylinder of radius vol_r about the origin between heights vol_zlo..vol_zhi. */
+typedef struct {
+  const float* verts;   /* n_verts x 3 */
+  int32_t n_verts;
+  const int32_t* tris;  /* n_tris x 3 vertex indices */
+  int32_t n_tris;
+  float vol_r, vol_zlo, vol_zhi;
+} perch_mesh;
+
+/* One object state O = (ID, x, y, theta) of Sec. III-A, as indices into the
+ * pose grid: x = xs[ix], y = ys[iy], (cos, sin) = cos_sin[iyaw]. 8 bytes. */
+typedef struct {
+  uint16_t mesh;
+  uint16_t iyaw;
+  int16_t ix, iy;
+} perch_obj;
+
+/* Result for one successor (24 bytes). For a valid child (viol == 0) the edge
+ * cost of Eq. (4) is djr + djo + resid:
+ *   djr   = #{p in dR unexplained by I}             (Sec. IV-A, dJ_r)
+ *   djo   = #{q in I n V(O) unexplained by dR}       (Sec. IV-A, dJ_o)
+ *   resid = #{q in I - V_K unexplained by R_K} on edges into level K, else 0
+ *   viol  = #{pixels where the child lies strictly in front of the parent};
+ *           viol > 0 means the child breaks R_{j} subset R_{j+1} (Eq. (3)) and
+ *           is not a successor: its cost fields are then 0
+ *   n_new = |dR|, the child's pixels where the parent render is empty
+ *   flags = bit 0: a triangle of the child was culled (near plane / guard
+ *           band); bit 1: invalid (viol > 0). */
+typedef struct {
+  int32_t djr, djo, resid, viol, n_new;
+  uint32_t flags;
+} perch_cost;
+
+#define PERCH_FLAG_CULLED 1u
+#define PERCH_FLAG_INVALID 2u
+
+/* Create a context on CUDA device `device`. `cuda_stream` (a cudaStream_t,
+ * may be NULL) is the stream all work is issued on; with NULL the context
+ * creates and owns a non-blocking stream. */
+int perch_create(perch_ctx** out, int device, void* cuda_stream);
+
+/* Release every device buffer and the owned stream. NULL is accepted. */
+int perch_destroy(perch_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none). The string
+ * stays valid until the next call on the context. */
+const char* perch_last_error(const perch_ctx* ctx);
+
+/* Upload n object meshes (Sec. III: the known 3D models). Replaces any
+ * previous meshes. Meshes are split into meshlets on the host (at most 64
+ * vertices and 64 triangles each). Errors: PERCH_E_ARG for empty meshes,
+ * out-of-range indices or n < 1. */
+int perch_load_meshes(perch_ctx* ctx, const perch_mesh* meshes, int32_t n);
+
+/* Discretised 3-DoF poses (Sec. III; Sec. V-B discretises x, y and yaw):
+ * xs[nx], ys[ny] in metres, cos_sin[2 * n_yaw] = (cos, sin) per yaw. The
+ * tables are used as given (no trigonometry on the device). */
+int perch_set_pose_grid(perch_ctx* ctx, const float* xs, int32_t nx, const float* ys,
+                        int32_t ny, const float* cos_sin, int32_t n_yaw);
+
+/* Set the observation (Sec. III: the input cloud I and the sensor pose):
+ * depth[H * W] in metres, row-major, 0 (or non-finite) = missing;
+ * fxfycxcy = pinhole intrinsics; T_world_cam = row-major 3x4 camera-to-world
+ * transform; delta = the sensor-noise threshold of Eq. (1), in metres.
+ * Builds the observed cloud and its delta-grid index on the device. Requires
+ * meshes and the pose grid (PERCH_E_STATE otherwise). */
+int perch_set_observation(perch_ctx* ctx, const float* depth, int32_t W, int32_t H,
+                          const float fxfycxcy[4], const float T_world_cam[12], float delta);
+
+/* Evaluate n_hyp MSGT successors (Eq. (3), Eq. (4)).
+ * parents: n_par partial assignments, parent i = parents[i * parent_stride ..
+ *          + parent_len[i]) (parent_len may be 0: the root);
+ * hyp_parent[h] in [0, n_par): the parent hypothesis h extends;
+ * hyp[h]: the object added; K_total: objects in a complete scene (the
+ *          residual term is added when parent_len + 1 == K_total);
+ * out[n_hyp]: results.
+ * All pointers are host pointers; the call returns when out is written.
+ * Errors: PERCH_E_ARG (bad index / length), PERCH_E_STATE (no observation),
+ * PERCH_E_RANGE (a hypothesis larger than the tile limit). */
+int perch_eval_successors(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride,
+                          const int32_t* parent_len, int32_t n_par, const int32_t* hyp_parent,
+                          const perch_obj* hyp, int64_t n_hyp, int32_t K_total, perch_cost* out);
+
+/* Same as perch_eval_successors, but parents, parent_len, hyp_parent, hyp and
+ * out are DEVICE pointers (e.g. torch tensors on the context's device) and
+ * the work is only enqueued on the context's stream; out is valid once that
+ * stream reaches this point. Indices are not validated on the host (an
+ * out-of-range parent or pose index sets PERCH_FLAG bit 31 in that record's
+ * flags and zeroes the rest). */
+int perch_eval_successors_dev(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride,
+                              const int32_t* parent_len, int32_t n_par, const int32_t* hyp_parent,
+                              const perch_obj* hyp, int64_t n_hyp, int32_t K_total, perch_cost* out);
+
+/* z-buffer render (min depth, +inf where empty) of n objects into
+ * depth_out[H * W] (host pointer), the R_j of Sec. III-A. Returns the number
+ * of culled triangles in *n_culled (may be NULL). */
+int perch_render(perch_ctx* ctx, const perch_obj* objs, int32_t n, float* depth_out,
+                 int64_t* n_culled);
+
+/* Tree search (Sec. IV-B, Alg. 1 with the admissible h0 = 0; w = 1 gives
+ * uniform-cost search). mesh_multiset[K]: the types of the K objects in the
+ * scene (Sec. III: known number and types). batch_states: states expanded
+ * per device launch (>= 1). Stops at optimality or at time_limit_s /
+ * max_expansions (0 = none) and then returns PERCH_E_TIMEOUT with the best
+ * goal found so far (or cost -1 if none). */
+typedef struct {
+  int32_t K;
+  const uint16_t* mesh_multiset;
+  float w;
+  int32_t batch_states;
+  double time_limit_s;
+  int64_t max_expansions;
+} perch_search_params;
+
+typedef struct {
+  perch_obj objs[16];   /* the goal state, sorted by (mesh, ix, iy, iyaw) */
+  int32_t n_objs;
+  int64_t cost;         /* sum of edge costs along the returned path */
+  int64_t expansions;   /* states expanded */
+  int64_t successors;   /* hypotheses evaluated */
+  double seconds;
+  int32_t proven_optimal;
+} perch_result;
+
+int perch_search(perch_ctx* ctx, const perch_search_params* params, perch_result* result);
+
+/* Device time of the most recent evaluation (perch_eval_successors or
+ * perch_eval_successors_dev), measured with CUDA events recorded on the
+ * context's stream around its two phases: prep_ms = parent z-buffers and
+ * residual sets, eval_ms = the per-hypothesis evaluation kernel. Waits for
+ * those events. Either pointer may be NULL. PERCH_E_STATE if no evaluation
+ * has been issued yet. */
+int perch_last_timing(perch_ctx* ctx, float* prep_ms, float* eval_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PERCH_H_ */

@@ -1,0 +1,602 @@
+// C-ABI entry points of the PERCH successor-evaluation library (host side).
+//
+// Owns the context's device memory and orchestrates the kernels in
+// perch_kernels.cu. Host arithmetic that feeds the device (camera transform,
+// squared thresholds) is done in double and rounded once to binary32, as the
+// arithmetic contract in include/perch.h states; this file is compiled with
+// -ffp-contract=off so no fused multiply-add changes those roundings.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "perch_internal.h"
+#include "perch_ctx.h"
+
+using namespace perch;
+
+// ------------------------------------------------------------------ helpers
+cudaError_t DevBuf::ensure(size_t bytes) {
+  if (bytes <= cap) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  size_t nb = std::max<size_t>(bytes, 256);
+  cudaError_t e = cudaMalloc(&p, nb);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    return e;
+  }
+  cap = nb;
+  return cudaSuccess;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+}
+
+int perch_ctx::fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  err = buf;
+  return code;
+}
+
+int perch_ctx::cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PERCH_OK;
+  cudaGetLastError();
+  if (e == cudaErrorMemoryAllocation) return fail(PERCH_E_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(PERCH_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+Geometry perch_ctx::geometry() const {
+  Geometry g;
+  g.meshes = meshes.as<DevMesh>();
+  g.n_mesh = n_mesh;
+  g.ml_verts = ml_verts.as<float4>();
+  g.ml_info = ml_info.as<int4>();
+  g.ml_tris = ml_tris.as<uint32_t>();
+  g.xs = xs.as<float>();
+  g.ys = ys.as<float>();
+  g.cs = cs.as<float2>();
+  g.nx = nx;
+  g.ny = ny;
+  g.n_yaw = n_yaw;
+  g.pose_bbox = pose_bbox.as<int4>();
+  g.rx = rx.as<float>();
+  g.ry = ry.as<float>();
+  return g;
+}
+
+#define CK(expr, what)                          \
+  do {                                          \
+    int rc_ = ctx->cuda((expr), what);          \
+    if (rc_ != PERCH_OK) return rc_;            \
+  } while (0)
+
+static float ordered_to_float(int i) {
+  int b = i >= 0 ? i : i ^ 0x7fffffff;
+  float f;
+  std::memcpy(&f, &b, 4);
+  return f;
+}
+
+// screen boxes of every (mesh, pose); sets the shared-memory tile size
+int perch_ctx::ensure_bbox() {
+  perch_ctx* ctx = this;
+  if (bbox_valid) return PERCH_OK;
+  if (!has_cam || n_mesh == 0 || nx == 0) return PERCH_OK;
+  const long long n = (long long)n_mesh * nx * ny * n_yaw;
+  CK(pose_bbox.ensure(sizeof(int4) * n), "alloc pose boxes");
+  CK(scratch_small.ensure(64), "alloc");
+  int* d = scratch_small.as<int>();
+  CK(cudaMemsetAsync(d, 0, 3 * sizeof(int), stream), "memset");
+  CK(launch_pose_bbox(cam, geometry(), pose_bbox.as<int4>(), d, d + 2, stream), "pose_bbox kernel");
+  int h[3];
+  CK(cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, stream), "copy pose boxes");
+  CK(cudaStreamSynchronize(stream), "pose_bbox sync");
+  if (h[2]) return fail(PERCH_E_RANGE, "a (mesh, pose) projects behind the near plane or far off-screen");
+  if (!eval_tile_fits(device, std::max(h[0], 1), std::max(h[1], 1)))
+    return fail(PERCH_E_RANGE, "object screen box %dx%d does not fit in shared memory", h[0], h[1]);
+  tile_w = std::max(h[0], 1);
+  tile_h = std::max(h[1], 1);
+  bbox_valid = true;
+  return PERCH_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+int perch_create(perch_ctx** out, int device, void* cuda_stream) {
+  if (!out) return PERCH_E_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return PERCH_E_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return PERCH_E_CUDA;
+  perch_ctx* ctx = new (std::nothrow) perch_ctx();
+  if (!ctx) return PERCH_E_OOM;
+  ctx->device = device;
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return PERCH_E_CUDA;
+    }
+    ctx->own_stream = true;
+  }
+  *out = ctx;
+  return PERCH_OK;
+}
+
+int perch_destroy(perch_ctx* ctx) {
+  if (!ctx) return PERCH_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (DevBuf* b : ctx->all_buffers()) b->release();
+  for (int k = 0; k < 3; ++k)
+    if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return PERCH_OK;
+}
+
+const char* perch_last_error(const perch_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int perch_load_meshes(perch_ctx* ctx, const perch_mesh* meshes, int32_t n) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (!meshes || n < 1 || n > 65535) return ctx->fail(PERCH_E_ARG, "need 1..65535 meshes, got %d", n);
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  std::vector<DevMesh> dm(n);
+  std::vector<float4> verts;
+  std::vector<int4> info;
+  std::vector<uint32_t> tris;
+  int max_ml = 0, max_tris = 0;
+  for (int i = 0; i < n; ++i) {
+    const perch_mesh& m = meshes[i];
+    if (!m.verts || !m.tris || m.n_verts < 3 || m.n_tris < 1)
+      return ctx->fail(PERCH_E_ARG, "mesh %d: empty or null arrays", i);
+    if (!(m.vol_r >= 0.0f) || !std::isfinite(m.vol_zlo) || !std::isfinite(m.vol_zhi))
+      return ctx->fail(PERCH_E_ARG, "mesh %d: bad volume parameters", i);
+    DevMesh& d = dm[i];
+    d.n_tris = m.n_tris;
+    d.n_verts = m.n_verts;
+    d.vol_r2 = (float)((double)m.vol_r * (double)m.vol_r);
+    d.vol_zlo = m.vol_zlo;
+    d.vol_zhi = m.vol_zhi;
+    for (int k = 0; k < 3; ++k) {
+      d.lo[k] = INFINITY;
+      d.hi[k] = -INFINITY;
+    }
+    for (int v = 0; v < m.n_verts; ++v)
+      for (int k = 0; k < 3; ++k) {
+        float x = m.verts[3 * v + k];
+        if (!std::isfinite(x)) return ctx->fail(PERCH_E_ARG, "mesh %d: non-finite vertex %d", i, v);
+        d.lo[k] = std::min(d.lo[k], x);
+        d.hi[k] = std::max(d.hi[k], x);
+      }
+    // greedy meshlets in triangle order: <= 64 vertices, <= 64 triangles
+    d.meshlet_begin = (int)info.size();
+    std::vector<int> local(m.n_verts, -1);
+    std::vector<int> cur_v;
+    std::vector<uint32_t> cur_t;
+    auto flush = [&]() {
+      if (cur_t.empty()) return;
+      int4 in = make_int4((int)verts.size(), (int)cur_v.size(), (int)tris.size(), (int)cur_t.size());
+      for (int gv : cur_v) {
+        verts.push_back(make_float4(m.verts[3 * gv], m.verts[3 * gv + 1], m.verts[3 * gv + 2], 0.0f));
+        local[gv] = -1;
+      }
+      tris.insert(tris.end(), cur_t.begin(), cur_t.end());
+      info.push_back(in);
+      cur_v.clear();
+      cur_t.clear();
+    };
+    for (int t = 0; t < m.n_tris; ++t) {
+      int idx[3];
+      for (int k = 0; k < 3; ++k) {
+        idx[k] = m.tris[3 * t + k];
+        if (idx[k] < 0 || idx[k] >= m.n_verts)
+          return ctx->fail(PERCH_E_ARG, "mesh %d: triangle %d has vertex index %d out of range", i, t, idx[k]);
+      }
+      int need = 0;
+      for (int k = 0; k < 3; ++k) {
+        bool dup = false;
+        for (int j = 0; j < k; ++j) dup |= idx[j] == idx[k];
+        if (!dup && local[idx[k]] < 0) need++;
+      }
+      if ((int)cur_v.size() + need > kMeshletMaxVerts || (int)cur_t.size() + 1 > kMeshletMaxTris) flush();
+      uint32_t pk = 0;
+      for (int k = 0; k < 3; ++k) {
+        if (local[idx[k]] < 0) {
+          local[idx[k]] = (int)cur_v.size();
+          cur_v.push_back(idx[k]);
+        }
+        pk |= (uint32_t)local[idx[k]] << (8 * k);
+      }
+      cur_t.push_back(pk);
+    }
+    flush();
+    d.meshlet_count = (int)info.size() - d.meshlet_begin;
+    max_ml = std::max(max_ml, d.meshlet_count);
+    max_tris = std::max(max_tris, m.n_tris);
+  }
+  CK(ctx->meshes.ensure(sizeof(DevMesh) * n), "alloc meshes");
+  CK(ctx->ml_verts.ensure(sizeof(float4) * verts.size()), "alloc meshlet vertices");
+  CK(ctx->ml_info.ensure(sizeof(int4) * info.size()), "alloc meshlets");
+  CK(ctx->ml_tris.ensure(sizeof(uint32_t) * tris.size()), "alloc meshlet triangles");
+  CK(cudaMemcpyAsync(ctx->meshes.p, dm.data(), sizeof(DevMesh) * n, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  CK(cudaMemcpyAsync(ctx->ml_verts.p, verts.data(), sizeof(float4) * verts.size(), cudaMemcpyHostToDevice,
+                     ctx->stream), "copy");
+  CK(cudaMemcpyAsync(ctx->ml_info.p, info.data(), sizeof(int4) * info.size(), cudaMemcpyHostToDevice, ctx->stream),
+     "copy");
+  CK(cudaMemcpyAsync(ctx->ml_tris.p, tris.data(), sizeof(uint32_t) * tris.size(), cudaMemcpyHostToDevice,
+                     ctx->stream), "copy");
+  CK(cudaStreamSynchronize(ctx->stream), "load meshes");
+  ctx->h_meshes = dm;
+  ctx->n_mesh = n;
+  ctx->max_meshlets = max_ml;
+  ctx->max_tris = max_tris;
+  ctx->bbox_valid = false;
+  return ctx->ensure_bbox();
+}
+
+int perch_set_pose_grid(perch_ctx* ctx, const float* xs, int32_t nx, const float* ys, int32_t ny,
+                        const float* cos_sin, int32_t n_yaw) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (!xs || !ys || !cos_sin || nx < 1 || ny < 1 || n_yaw < 1 || nx > 32767 || ny > 32767 || n_yaw > 65535)
+    return ctx->fail(PERCH_E_ARG, "pose grid: bad sizes %d x %d x %d", nx, ny, n_yaw);
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(ctx->xs.ensure(4 * nx), "alloc");
+  CK(ctx->ys.ensure(4 * ny), "alloc");
+  CK(ctx->cs.ensure(8 * n_yaw), "alloc");
+  CK(cudaMemcpyAsync(ctx->xs.p, xs, 4 * nx, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  CK(cudaMemcpyAsync(ctx->ys.p, ys, 4 * ny, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  CK(cudaMemcpyAsync(ctx->cs.p, cos_sin, 8 * n_yaw, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  CK(cudaStreamSynchronize(ctx->stream), "set pose grid");
+  ctx->nx = nx;
+  ctx->ny = ny;
+  ctx->n_yaw = n_yaw;
+  ctx->bbox_valid = false;
+  return ctx->ensure_bbox();
+}
+
+int perch_set_observation(perch_ctx* ctx, const float* depth, int32_t W, int32_t H, const float fxfycxcy[4],
+                          const float T_world_cam[12], float delta) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (!depth || !fxfycxcy || !T_world_cam || W < 1 || H < 1 || (long long)W * H > (1LL << 28))
+    return ctx->fail(PERCH_E_ARG, "observation: bad image %d x %d or null pointer", W, H);
+  if (!(delta > 0.0f) || !std::isfinite(delta)) return ctx->fail(PERCH_E_ARG, "delta must be finite and > 0");
+  if (!(fxfycxcy[0] > 0.0f) || !(fxfycxcy[1] > 0.0f)) return ctx->fail(PERCH_E_ARG, "focal lengths must be > 0");
+  if (ctx->n_mesh == 0 || ctx->nx == 0) return ctx->fail(PERCH_E_STATE, "load meshes and the pose grid first");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  ctx->has_obs = false;
+  Camera& c = ctx->cam;
+  c.W = W;
+  c.H = H;
+  c.fx = fxfycxcy[0];
+  c.fy = fxfycxcy[1];
+  c.cx = fxfycxcy[2];
+  c.cy = fxfycxcy[3];
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) c.Rwc[r * 3 + k] = T_world_cam[r * 4 + k];
+    c.twc[r] = T_world_cam[r * 4 + 3];
+  }
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) c.Rcw[r * 3 + k] = c.Rwc[k * 3 + r];
+    double acc = (double)c.Rwc[0 * 3 + r] * (double)c.twc[0];
+    acc = acc + (double)c.Rwc[1 * 3 + r] * (double)c.twc[1];
+    acc = acc + (double)c.Rwc[2 * 3 + r] * (double)c.twc[2];
+    c.tcw[r] = (float)(-acc);
+  }
+  c.delta = delta;
+  c.delta2 = (float)((double)delta * (double)delta);
+  ctx->has_cam = true;
+  ctx->bbox_valid = false;
+
+  const int npx = W * H;
+  const int nblk = (npx + 255) / 256;
+  CK(ctx->depth.ensure(4 * (size_t)npx), "alloc depth");
+  CK(ctx->rx.ensure(4 * (size_t)W), "alloc");
+  CK(ctx->ry.ensure(4 * (size_t)H), "alloc");
+  CK(ctx->blockcnt.ensure(4 * ((size_t)nblk + 1)), "alloc");
+  CK(ctx->scan_tmp.ensure(4 * ((size_t)npx / 1024 + 2 + 4096)), "alloc");
+  CK(ctx->cam_pts.ensure(16 * (size_t)npx), "alloc");
+  CK(ctx->world_pts.ensure(16 * (size_t)npx), "alloc");
+  CK(ctx->scratch_small.ensure(64), "alloc");
+  CK(cudaMemcpyAsync(ctx->depth.p, depth, 4 * (size_t)npx, cudaMemcpyHostToDevice, ctx->stream), "copy depth");
+  CK(launch_rays(c, ctx->rx.as<float>(), ctx->ry.as<float>(), ctx->stream), "rays kernel");
+  int binit[10] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN, INT_MAX, INT_MAX, INT_MIN, INT_MIN};
+  int* bounds = ctx->scratch_small.as<int>();
+  CK(cudaMemcpyAsync(bounds, binit, sizeof binit, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  int* offs = ctx->blockcnt.as<int>();
+  CK(ctx->blockoff.ensure(4 * ((size_t)nblk + 1)), "alloc");
+  CK(launch_obs_count(ctx->depth.as<float>(), W, H, offs, ctx->stream), "obs count kernel");
+  CK(launch_exclusive_scan(offs, ctx->blockoff.as<int>(), nblk, ctx->scan_tmp.as<int>(), ctx->stream), "scan");
+  CK(launch_obs_write(ctx->depth.as<float>(), c, ctx->rx.as<float>(), ctx->ry.as<float>(), ctx->blockoff.as<int>(),
+                      ctx->cam_pts.as<float4>(), ctx->world_pts.as<float4>(), bounds, ctx->stream),
+     "obs write kernel");
+  int hb[11];
+  CK(cudaMemcpyAsync(hb, bounds, 10 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "copy");
+  CK(cudaMemcpyAsync(hb + 10, ctx->blockoff.as<int>() + nblk, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+     "copy");
+  CK(cudaStreamSynchronize(ctx->stream), "observation sync");
+  const int n = hb[10];
+  ObsIndex& o = ctx->obs;
+  std::memset(&o, 0, sizeof o);
+  o.n = n;
+  if (n > 0) {
+    float lo[3], hi[3], wlo[2], whi[2];
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = ordered_to_float(hb[k]);
+      hi[k] = ordered_to_float(hb[3 + k]);
+    }
+    for (int k = 0; k < 2; ++k) {
+      wlo[k] = ordered_to_float(hb[6 + k]);
+      whi[k] = ordered_to_float(hb[8 + k]);
+    }
+    // 3D camera-frame grid, cells >= 1.02 delta (Eq. (1) neighbourhood = 3x3x3)
+    double h = 1.02 * (double)delta;
+    long long cells;
+    int dims[3];
+    for (;;) {
+      cells = 1;
+      for (int k = 0; k < 3; ++k) {
+        dims[k] = (int)std::floor(((double)hi[k] - lo[k]) / h) + 3;
+        cells *= dims[k];
+      }
+      if (cells <= (16LL << 20)) break;
+      h *= 1.25;
+    }
+    o.g3x = (float)(lo[0] - h);
+    o.g3y = (float)(lo[1] - h);
+    o.g3z = (float)(lo[2] - h);
+    o.inv3 = (float)(1.0 / h);
+    o.n3x = dims[0];
+    o.n3y = dims[1];
+    o.n3z = dims[2];
+    // 2D world grid for V(O) candidates
+    double g2 = 0.01;
+    int d2[2];
+    for (;;) {
+      for (int k = 0; k < 2; ++k) d2[k] = (int)std::floor(((double)whi[k] - wlo[k]) / g2) + 3;
+      if ((long long)d2[0] * d2[1] <= (4LL << 20)) break;
+      g2 *= 1.5;
+    }
+    o.g2x = (float)(wlo[0] - g2);
+    o.g2y = (float)(wlo[1] - g2);
+    o.inv2 = (float)(1.0 / g2);
+    o.n2x = d2[0];
+    o.n2y = d2[1];
+    const long long c2 = (long long)d2[0] * d2[1];
+    const long long cmax = std::max(cells, c2);
+    CK(ctx->keys.ensure(4 * (size_t)n), "alloc");
+    CK(ctx->counts.ensure(4 * ((size_t)cmax + 1)), "alloc");
+    CK(ctx->cursor.ensure(4 * ((size_t)cmax + 1)), "alloc");
+    CK(ctx->start3.ensure(4 * ((size_t)cells + 1)), "alloc");
+    CK(ctx->start2.ensure(4 * ((size_t)c2 + 1)), "alloc");
+    CK(ctx->obs3.ensure(16 * (size_t)n), "alloc");
+    CK(ctx->world2.ensure(16 * (size_t)n), "alloc");
+    CK(ctx->cam2.ensure(16 * (size_t)n), "alloc");
+    CK(ctx->scan_tmp.ensure(4 * ((size_t)cmax / 1024 + 2)), "alloc");
+    // bucket the camera-frame cloud
+    CK(cudaMemsetAsync(ctx->counts.p, 0, 4 * (size_t)cells, ctx->stream), "memset");
+    CK(launch_grid3_keys(ctx->cam_pts.as<float4>(), n, o.g3x, o.g3y, o.g3z, o.inv3, o.n3x, o.n3y, o.n3z,
+                         ctx->keys.as<int>(), ctx->counts.as<int>(), ctx->stream), "grid3 keys");
+    CK(launch_exclusive_scan(ctx->counts.as<int>(), ctx->start3.as<int>(), (int)cells, ctx->scan_tmp.as<int>(),
+                             ctx->stream), "scan3");
+    CK(cudaMemcpyAsync(ctx->cursor.p, ctx->start3.p, 4 * (size_t)cells, cudaMemcpyDeviceToDevice, ctx->stream),
+       "copy");
+    CK(launch_scatter(ctx->keys.as<int>(), n, ctx->cursor.as<int>(), ctx->cam_pts.as<float4>(),
+                      ctx->obs3.as<float4>(), nullptr, nullptr, ctx->stream), "scatter3");
+    // bucket the world-frame cloud (with its camera-frame copy)
+    CK(cudaMemsetAsync(ctx->counts.p, 0, 4 * (size_t)c2, ctx->stream), "memset");
+    CK(launch_grid2_keys(ctx->world_pts.as<float4>(), n, o.g2x, o.g2y, o.inv2, o.n2x, o.n2y, ctx->keys.as<int>(),
+                         ctx->counts.as<int>(), ctx->stream), "grid2 keys");
+    CK(launch_exclusive_scan(ctx->counts.as<int>(), ctx->start2.as<int>(), (int)c2, ctx->scan_tmp.as<int>(),
+                             ctx->stream), "scan2");
+    CK(cudaMemcpyAsync(ctx->cursor.p, ctx->start2.p, 4 * (size_t)c2, cudaMemcpyDeviceToDevice, ctx->stream),
+       "copy");
+    CK(launch_scatter(ctx->keys.as<int>(), n, ctx->cursor.as<int>(), ctx->world_pts.as<float4>(),
+                      ctx->world2.as<float4>(), ctx->cam_pts.as<float4>(), ctx->cam2.as<float4>(), ctx->stream),
+       "scatter2");
+    o.cam3 = ctx->obs3.as<float4>();
+    o.start3 = ctx->start3.as<int>();
+    o.world2 = ctx->world2.as<float4>();
+    o.cam2 = ctx->cam2.as<float4>();
+    o.start2 = ctx->start2.as<int>();
+  }
+  int rc = ctx->ensure_bbox();
+  if (rc != PERCH_OK) return rc;
+  CK(cudaStreamSynchronize(ctx->stream), "observation index");
+  ctx->has_obs = true;
+  return PERCH_OK;
+}
+
+}  // extern "C"
+
+// Enqueue parent preparation and successor evaluation for device-resident
+// batch arrays (no host synchronisation).
+int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const int32_t* d_plen, int n_par,
+                            const int32_t* d_hp, const perch_obj* d_hyp, long long n_hyp, int K_total,
+                            perch_cost* d_out) {
+  perch_ctx* ctx = this;
+  const size_t npx = (size_t)cam.W * cam.H;
+  CK(parent_z.ensure(4 * npx * std::max(n_par, 1)), "alloc parent z-buffers");
+  CK(uset.ensure(4 * (size_t)std::max(obs.n, 1) * std::max(n_par, 1)), "alloc U sets");
+  CK(uset_count.ensure(4 * (size_t)std::max(n_par, 1)), "alloc");
+  Batch b;
+  b.parents = d_parents;
+  b.parent_stride = parent_stride;
+  b.parent_len = d_plen;
+  b.n_par = n_par;
+  b.parent_z = parent_z.as<float>();
+  b.uset = uset.as<int>();
+  b.uset_count = uset_count.as<int>();
+  b.uset_stride = std::max(obs.n, 1);
+  b.hyp_parent = d_hp;
+  b.hyp = d_hyp;
+  b.n_hyp = n_hyp;
+  b.K_total = K_total;
+  b.out = d_out;
+  b.tile_w = tile_w;
+  b.tile_h = tile_h;
+  const Geometry g = geometry();
+  if (!ev[0])
+    for (int k = 0; k < 3; ++k) CK(cudaEventCreate(&ev[k]), "cudaEventCreate");
+  CK(cudaEventRecord(ev[0], stream), "event");
+  CK(launch_fill_u32(parent_z.as<uint32_t>(), kInfBits, (long long)npx * n_par, stream), "clear parents");
+  CK(cudaMemsetAsync(uset_count.p, 0, 4 * (size_t)std::max(n_par, 1), stream), "memset");
+  CK(launch_render_parents(cam, g, b, max_meshlets, nullptr, stream), "render parents");
+  CK(launch_uset(cam, g, obs, b, stream), "U sets");
+  CK(cudaEventRecord(ev[1], stream), "event");
+  CK(launch_eval(cam, g, obs, b, stream), "eval kernel");
+  CK(cudaEventRecord(ev[2], stream), "event");
+  timed = true;
+  return PERCH_OK;
+}
+
+static int check_obj(perch_ctx* ctx, const perch_obj& o, const char* what, long long i) {
+  if (o.mesh >= ctx->n_mesh || o.ix < 0 || o.ix >= ctx->nx || o.iy < 0 || o.iy >= ctx->ny || o.iyaw >= ctx->n_yaw)
+    return ctx->fail(PERCH_E_ARG, "%s %lld: object (%d, %d, %d, %d) outside meshes / pose grid", what, i, o.mesh,
+                     o.ix, o.iy, o.iyaw);
+  return PERCH_OK;
+}
+
+extern "C" {
+
+int perch_eval_successors(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride, const int32_t* parent_len,
+                          int32_t n_par, const int32_t* hyp_parent, const perch_obj* hyp, int64_t n_hyp,
+                          int32_t K_total, perch_cost* out) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (!ctx->has_obs) return ctx->fail(PERCH_E_STATE, "set an observation first");
+  if (n_hyp < 0 || n_hyp > 0x7fffffffLL) return ctx->fail(PERCH_E_ARG, "n_hyp out of range");
+  if (n_hyp == 0) return PERCH_OK;
+  if (!parent_len || !hyp_parent || !hyp || !out || n_par < 1 || parent_stride < 0 || K_total < 1 ||
+      (parent_stride > 0 && !parents))
+    return ctx->fail(PERCH_E_ARG, "null pointer or bad sizes");
+  if (n_par > 65535 || (long long)n_par * std::max(parent_stride, 1) > 65535)
+    return ctx->fail(PERCH_E_ARG, "too many parents in one batch (n_par x stride <= 65535)");
+  for (int i = 0; i < n_par; ++i) {
+    if (parent_len[i] < 0 || parent_len[i] > parent_stride || parent_len[i] >= K_total)
+      return ctx->fail(PERCH_E_ARG, "parent %d: length %d outside [0, min(stride, K_total - 1)]", i, parent_len[i]);
+    for (int k = 0; k < parent_len[i]; ++k) {
+      int rc = check_obj(ctx, parents[(long long)i * parent_stride + k], "parent object", i);
+      if (rc) return rc;
+    }
+  }
+  for (long long h = 0; h < n_hyp; ++h) {
+    if (hyp_parent[h] < 0 || hyp_parent[h] >= n_par)
+      return ctx->fail(PERCH_E_ARG, "hypothesis %lld: parent %d out of range", h, hyp_parent[h]);
+    int rc = check_obj(ctx, hyp[h], "hypothesis", h);
+    if (rc) return rc;
+  }
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const size_t pbytes = sizeof(perch_obj) * std::max<size_t>((size_t)n_par * parent_stride, 1);
+  CK(ctx->b_parents.ensure(pbytes), "alloc");
+  CK(ctx->b_plen.ensure(4 * (size_t)n_par), "alloc");
+  CK(ctx->b_hp.ensure(4 * (size_t)n_hyp), "alloc");
+  CK(ctx->b_hyp.ensure(sizeof(perch_obj) * (size_t)n_hyp), "alloc");
+  CK(ctx->b_out.ensure(sizeof(perch_cost) * (size_t)n_hyp), "alloc");
+  if (parent_stride > 0)
+    CK(cudaMemcpyAsync(ctx->b_parents.p, parents, sizeof(perch_obj) * (size_t)n_par * parent_stride,
+                       cudaMemcpyHostToDevice, ctx->stream), "copy parents");
+  CK(cudaMemcpyAsync(ctx->b_plen.p, parent_len, 4 * (size_t)n_par, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  CK(cudaMemcpyAsync(ctx->b_hp.p, hyp_parent, 4 * (size_t)n_hyp, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  CK(cudaMemcpyAsync(ctx->b_hyp.p, hyp, sizeof(perch_obj) * (size_t)n_hyp, cudaMemcpyHostToDevice, ctx->stream),
+     "copy");
+  int rc = ctx->enqueue_eval(ctx->b_parents.as<perch_obj>(), parent_stride, ctx->b_plen.as<int32_t>(), n_par,
+                             ctx->b_hp.as<int32_t>(), ctx->b_hyp.as<perch_obj>(), n_hyp, K_total,
+                             ctx->b_out.as<perch_cost>());
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(out, ctx->b_out.p, sizeof(perch_cost) * (size_t)n_hyp, cudaMemcpyDeviceToHost, ctx->stream),
+     "copy results");
+  CK(cudaStreamSynchronize(ctx->stream), "eval");
+  return PERCH_OK;
+}
+
+int perch_eval_successors_dev(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride,
+                              const int32_t* parent_len, int32_t n_par, const int32_t* hyp_parent,
+                              const perch_obj* hyp, int64_t n_hyp, int32_t K_total, perch_cost* out) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (!ctx->has_obs) return ctx->fail(PERCH_E_STATE, "set an observation first");
+  if (n_hyp < 0 || n_hyp > 0x7fffffffLL) return ctx->fail(PERCH_E_ARG, "n_hyp out of range");
+  if (n_hyp == 0) return PERCH_OK;
+  if (!parent_len || !hyp_parent || !hyp || !out || n_par < 1 || parent_stride < 0 || K_total < 1 ||
+      (parent_stride > 0 && !parents))
+    return ctx->fail(PERCH_E_ARG, "null pointer or bad sizes");
+  if (n_par > 65535 || (long long)n_par * std::max(parent_stride, 1) > 65535)
+    return ctx->fail(PERCH_E_ARG, "too many parents in one batch (n_par x stride <= 65535)");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  return ctx->enqueue_eval(parents, parent_stride, parent_len, n_par, hyp_parent, hyp, n_hyp, K_total, out);
+}
+
+int perch_last_timing(perch_ctx* ctx, float* prep_ms, float* eval_ms) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (!ctx->timed) return ctx->fail(PERCH_E_STATE, "no evaluation issued yet");
+  CK(cudaEventSynchronize(ctx->ev[2]), "event sync");
+  float a = 0.0f, b = 0.0f;
+  CK(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]), "event time");
+  CK(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]), "event time");
+  if (prep_ms) *prep_ms = a;
+  if (eval_ms) *eval_ms = b;
+  return PERCH_OK;
+}
+
+int perch_render(perch_ctx* ctx, const perch_obj* objs, int32_t n, float* depth_out, int64_t* n_culled) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (!ctx->has_cam) return ctx->fail(PERCH_E_STATE, "set an observation (camera) first");
+  if (!depth_out || n < 0 || n > 65535 || (n > 0 && !objs)) return ctx->fail(PERCH_E_ARG, "bad arguments");
+  for (int i = 0; i < n; ++i) {
+    int rc = check_obj(ctx, objs[i], "object", i);
+    if (rc) return rc;
+  }
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const size_t npx = (size_t)ctx->cam.W * ctx->cam.H;
+  CK(ctx->parent_z.ensure(4 * npx), "alloc");
+  CK(ctx->b_parents.ensure(sizeof(perch_obj) * std::max(n, 1)), "alloc");
+  CK(ctx->b_plen.ensure(4), "alloc");
+  CK(ctx->scratch_small.ensure(64), "alloc");
+  if (n > 0)
+    CK(cudaMemcpyAsync(ctx->b_parents.p, objs, sizeof(perch_obj) * n, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  CK(cudaMemcpyAsync(ctx->b_plen.p, &n, 4, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  unsigned long long* culled = reinterpret_cast<unsigned long long*>(ctx->scratch_small.as<int>() + 8);
+  CK(cudaMemsetAsync(culled, 0, 8, ctx->stream), "memset");
+  CK(launch_fill_u32(ctx->parent_z.as<uint32_t>(), kInfBits, (long long)npx, ctx->stream), "clear");
+  Batch b;
+  std::memset(&b, 0, sizeof b);
+  b.parents = ctx->b_parents.as<perch_obj>();
+  b.parent_stride = std::max(n, 1);
+  b.parent_len = ctx->b_plen.as<int32_t>();
+  b.n_par = 1;
+  b.parent_z = ctx->parent_z.as<float>();
+  CK(launch_render_parents(ctx->cam, ctx->geometry(), b, ctx->max_meshlets, culled, ctx->stream), "render");
+  unsigned long long hc = 0;
+  CK(cudaMemcpyAsync(depth_out, ctx->parent_z.p, 4 * npx, cudaMemcpyDeviceToHost, ctx->stream), "copy depth");
+  CK(cudaMemcpyAsync(&hc, culled, 8, cudaMemcpyDeviceToHost, ctx->stream), "copy");
+  CK(cudaStreamSynchronize(ctx->stream), "render");
+  if (n_culled) *n_culled = (int64_t)hc;
+  return PERCH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Context object behind the opaque perch_ctx handle (library-internal).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "perch_internal.h"
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes);  // grow-only; contents are not preserved
+  void release();
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+struct perch_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+
+  // object meshes, split into meshlets
+  int n_mesh = 0, max_meshlets = 0, max_tris = 0;
+  std::vector<perch::DevMesh> h_meshes;
+  DevBuf meshes, ml_verts, ml_info, ml_tris;
+
+  // pose grid
+  int nx = 0, ny = 0, n_yaw = 0;
+  DevBuf xs, ys, cs;
+
+  // camera, observation and its indices
+  bool has_cam = false, has_obs = false;
+  perch::Camera cam{};
+  perch::ObsIndex obs{};
+  DevBuf depth, rx, ry, blockcnt, blockoff, scan_tmp, cam_pts, world_pts, keys, counts, cursor;
+  DevBuf start3, start2, obs3, world2, cam2, scratch_small;
+
+  // screen box of every (mesh, pose) and the tile it needs
+  DevBuf pose_bbox;
+  bool bbox_valid = false;
+  int tile_w = 0, tile_h = 0;
+
+  // per-batch buffers
+  DevBuf parent_z, uset, uset_count;
+  DevBuf b_parents, b_plen, b_hp, b_hyp, b_out;
+
+  // events around the phases of the last evaluation
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool timed = false;
+
+  std::vector<DevBuf*> all_buffers() {
+    return {&meshes, &ml_verts, &ml_info, &ml_tris, &xs, &ys, &cs, &depth, &rx, &ry, &blockcnt, &blockoff,
+            &scan_tmp, &cam_pts, &world_pts, &keys, &counts, &cursor, &start3, &start2, &obs3, &world2, &cam2,
+            &scratch_small, &pose_bbox, &parent_z, &uset, &uset_count, &b_parents, &b_plen, &b_hp, &b_hyp,
+            &b_out};
+  }
+
+  int fail(int code, const char* fmt, ...);
+  int cuda(cudaError_t e, const char* what);
+  perch::Geometry geometry() const;
+  int ensure_bbox();
+  int enqueue_eval(const perch_obj* d_parents, int parent_stride, const int32_t* d_plen, int n_par,
+                   const int32_t* d_hp, const perch_obj* d_hyp, long long n_hyp, int K_total, perch_cost* d_out);
+};

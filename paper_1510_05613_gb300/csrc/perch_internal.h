@@ -1,0 +1,113 @@
+// Internal declarations of the PERCH CUDA library (shared by its own
+// translation units only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "perch.h"
+
+namespace perch {
+
+constexpr uint32_t kInfBits = 0x7f800000u;  // +inf: empty z-buffer pixel
+constexpr uint32_t kFlagBadIndex = 0x80000000u;
+constexpr int kMeshletMaxVerts = 64;
+constexpr int kMeshletMaxTris = 64;
+constexpr int kEvalThreads = 256;
+constexpr int kEvalWarps = kEvalThreads / 32;
+constexpr float kNearZ = 0.05f;   // cull: vertex depth at or below this
+constexpr float kGuard = 2048.0f; // cull: |u| or |v| beyond this (pixels)
+constexpr int kMaxExtent = 16384; // cull: snapped extent (1/16 px) at or above
+
+// Camera constants, derived on the host from the caller's intrinsics and
+// camera-to-world pose (double arithmetic, rounded once to binary32).
+struct Camera {
+  int W, H;
+  float fx, fy, cx, cy;
+  float Rcw[9], tcw[3];  // world -> camera
+  float Rwc[9], twc[3];  // camera -> world
+  float delta, delta2;
+};
+
+// One object type after meshlet splitting.
+struct DevMesh {
+  int meshlet_begin, meshlet_count;
+  int n_tris, n_verts;
+  float vol_r2, vol_zlo, vol_zhi;
+  float lo[3], hi[3];  // object-frame bounding box
+};
+
+// Observed cloud with its two spatial indices.
+struct ObsIndex {
+  int n;
+  // camera-frame points bucketed by a 3D grid of cell >= delta (Eq. (1) query)
+  const float4* cam3;  // x, y, z, pixel index (int bits)
+  const int* start3;   // n_cells3 + 1
+  float g3x, g3y, g3z, inv3;
+  int n3x, n3y, n3z;
+  // the same points bucketed by a 2D world (x, y) grid (V(O) candidates)
+  const float4* world2;  // x_w, y_w, z_w, -
+  const float4* cam2;    // x_c, y_c, z_c, pixel index (int bits)
+  const int* start2;     // n_cells2 + 1
+  float g2x, g2y, inv2;
+  int n2x, n2y;
+};
+
+struct Geometry {
+  const DevMesh* meshes;
+  int n_mesh;
+  const float4* ml_verts;   // meshlet vertex positions (object frame)
+  const int4* ml_info;      // vtx offset, n_vtx, tri offset, n_tri
+  const uint32_t* ml_tris;  // 3 x 8-bit local indices
+  const float* xs;
+  const float* ys;
+  const float2* cs;
+  int nx, ny, n_yaw;
+  const int4* pose_bbox;  // per (mesh, ix, iy, iyaw): x0, y0, w, h in pixels
+  const float* rx;        // ray slope per column
+  const float* ry;        // ray slope per row
+};
+
+struct Batch {
+  const perch_obj* parents;
+  int parent_stride;
+  const int32_t* parent_len;
+  int n_par;
+  float* parent_z;      // n_par x H x W
+  int* uset;            // n_par x uset_stride indices into the 2D-sorted cloud
+  int* uset_count;      // n_par
+  int uset_stride;
+  const int32_t* hyp_parent;
+  const perch_obj* hyp;
+  long long n_hyp;
+  int K_total;
+  perch_cost* out;
+  int tile_w, tile_h;
+};
+
+// kernels.cu launchers (all asynchronous on `s`)
+cudaError_t launch_fill_u32(uint32_t* p, uint32_t v, long long n, cudaStream_t s);
+cudaError_t launch_obs_count(const float* depth, int W, int H, int* block_counts, cudaStream_t s);
+cudaError_t launch_exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t s);
+cudaError_t launch_obs_write(const float* depth, const Camera& cam, const float* rx, const float* ry,
+                             const int* block_offsets, float4* cam_pts, float4* world_pts,
+                             int* bounds, cudaStream_t s);
+cudaError_t launch_grid3_keys(const float4* cam_pts, int n, float g3x, float g3y, float g3z, float inv3,
+                              int n3x, int n3y, int n3z, int* keys, int* counts, cudaStream_t s);
+cudaError_t launch_grid2_keys(const float4* world_pts, int n, float g2x, float g2y, float inv2,
+                              int n2x, int n2y, int* keys, int* counts, cudaStream_t s);
+cudaError_t launch_scatter(const int* keys, int n, int* cursor, const float4* a_in, float4* a_out,
+                           const float4* b_in, float4* b_out, cudaStream_t s);
+cudaError_t launch_rays(const Camera& cam, float* rx, float* ry, cudaStream_t s);
+cudaError_t launch_pose_bbox(const Camera& cam, const Geometry& g, int4* bbox, int* max_wh, int* bad,
+                             cudaStream_t s);
+cudaError_t launch_render_parents(const Camera& cam, const Geometry& g, const Batch& b, int max_tris,
+                                  unsigned long long* culled, cudaStream_t s);
+cudaError_t launch_uset(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                        cudaStream_t s);
+cudaError_t launch_eval(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                        cudaStream_t s);
+size_t eval_smem_bytes(int tile_w, int tile_h);
+bool eval_tile_fits(int device, int tile_w, int tile_h);
+
+}  // namespace perch

@@ -1,0 +1,214 @@
+"""Thin ctypes binding of libperch.so (include/perch.h), same names.
+
+Argument marshalling only: every step of successor evaluation and search runs
+in the CUDA library. If the library is missing or fails to load this module
+raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libperch.so")
+
+PERCH_OK, PERCH_E_ARG, PERCH_E_CUDA, PERCH_E_OOM, PERCH_E_STATE, PERCH_E_TIMEOUT, PERCH_E_RANGE = 0, -1, -2, -3, -4, -5, -6
+FLAG_CULLED, FLAG_INVALID, FLAG_BAD_INDEX = 1, 2, 1 << 31
+
+OBJ = np.dtype([("mesh", np.uint16), ("iyaw", np.uint16), ("ix", np.int16), ("iy", np.int16)])
+COST = np.dtype([("djr", np.int32), ("djo", np.int32), ("resid", np.int32), ("viol", np.int32),
+                 ("n_new", np.int32), ("flags", np.uint32)])
+
+# names exported by the library (include/perch.h)
+EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_meshes", "perch_set_pose_grid",
+           "perch_set_observation", "perch_eval_successors", "perch_eval_successors_dev", "perch_render",
+           "perch_search", "perch_last_timing")
+
+
+class perch_mesh(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("n_verts", ctypes.c_int32), ("tris", ctypes.c_void_p),
+                ("n_tris", ctypes.c_int32), ("vol_r", ctypes.c_float), ("vol_zlo", ctypes.c_float),
+                ("vol_zhi", ctypes.c_float)]
+
+
+class perch_obj(ctypes.Structure):
+    _fields_ = [("mesh", ctypes.c_uint16), ("iyaw", ctypes.c_uint16), ("ix", ctypes.c_int16), ("iy", ctypes.c_int16)]
+
+
+class perch_search_params(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("mesh_multiset", ctypes.c_void_p), ("w", ctypes.c_float),
+                ("batch_states", ctypes.c_int32), ("time_limit_s", ctypes.c_double),
+                ("max_expansions", ctypes.c_int64)]
+
+
+class perch_result(ctypes.Structure):
+    _fields_ = [("objs", perch_obj * 16), ("n_objs", ctypes.c_int32), ("cost", ctypes.c_int64),
+                ("expansions", ctypes.c_int64), ("successors", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("proven_optimal", ctypes.c_int32)]
+
+
+class PerchError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"perch error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libperch.so (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not built: run paper_1510_05613_gb300/build.py (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, F = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    sig = {
+        "perch_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, P], ctypes.c_int),
+        "perch_destroy": ([P], ctypes.c_int),
+        "perch_last_error": ([P], ctypes.c_char_p),
+        "perch_load_meshes": ([P, P, I32], ctypes.c_int),
+        "perch_set_pose_grid": ([P, P, I32, P, I32, P, I32], ctypes.c_int),
+        "perch_set_observation": ([P, P, I32, I32, P, P, F], ctypes.c_int),
+        "perch_eval_successors": ([P, P, I32, P, I32, P, P, I64, I32, P], ctypes.c_int),
+        "perch_eval_successors_dev": ([P, P, I32, P, I32, P, P, I64, I32, P], ctypes.c_int),
+        "perch_render": ([P, P, I32, P, P], ctypes.c_int),
+        "perch_search": ([P, P, P], ctypes.c_int),
+        "perch_last_timing": ([P, P, P], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes, fn.restype = args, res
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return a.ctypes.data if a is not None and a.size else None
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class Perch:
+    """One library context (device memory, stream) on one GPU."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        rc = self.lib.perch_create(ctypes.byref(h), device, stream)
+        if rc != PERCH_OK:
+            raise PerchError(rc, "perch_create failed")
+        self.h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.perch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, ok=(PERCH_OK,)):
+        if rc not in ok:
+            raise PerchError(rc, self.lib.perch_last_error(self.h).decode())
+        return rc
+
+    # -- setup ---------------------------------------------------------
+    def perch_load_meshes(self, meshes):
+        arr = (perch_mesh * len(meshes))()
+        keep = []
+        for i, m in enumerate(meshes):
+            v, t = _c(m.verts, np.float32), _c(m.tris, np.int32)
+            keep += [v, t]
+            arr[i] = perch_mesh(v.ctypes.data, m.n_verts, t.ctypes.data, m.n_tris, m.vol_r, m.vol_zlo, m.vol_zhi)
+        return self._check(self.lib.perch_load_meshes(self.h, ctypes.addressof(arr), len(meshes)))
+
+    def perch_set_pose_grid(self, grid):
+        xs, ys, cs = _c(grid.xs, np.float32), _c(grid.ys, np.float32), _c(grid.cos_sin, np.float32)
+        return self._check(self.lib.perch_set_pose_grid(self.h, xs.ctypes.data, len(xs), ys.ctypes.data, len(ys),
+                                                        cs.ctypes.data, cs.shape[0]))
+
+    def perch_set_observation(self, depth, fxfycxcy, T_world_cam, delta: float):
+        d = _c(depth, np.float32)
+        H, W = d.shape
+        k = _c(fxfycxcy, np.float32)
+        T = _c(T_world_cam, np.float32).reshape(-1)
+        return self._check(self.lib.perch_set_observation(self.h, d.ctypes.data, W, H, k.ctypes.data, T.ctypes.data,
+                                                          delta))
+
+    def setup(self, workload):
+        """Meshes, pose grid and observation of a synth.Workload."""
+        self.perch_load_meshes(workload.meshes)
+        self.perch_set_pose_grid(workload.grid)
+        self.perch_set_observation(workload.depth, workload.cam.fxfycxcy, workload.cam.T_wc, workload.delta)
+        self.H, self.W = workload.depth.shape
+
+    # -- evaluation ----------------------------------------------------
+    @staticmethod
+    def pack_parents(parents):
+        stride = max([1] + [len(p) for p in parents])
+        P = np.zeros((max(1, len(parents)), stride), OBJ)
+        plen = np.zeros(max(1, len(parents)), np.int32)
+        for i, p in enumerate(parents):
+            p = np.asarray(p, OBJ)
+            P[i, :len(p)] = p
+            plen[i] = len(p)
+        return P, plen, stride
+
+    def perch_eval_successors(self, parents, hyp_parent, hyps, K_total: int):
+        """Host arrays in, structured COST array out. ``parents``: list of
+        object arrays (partial assignments)."""
+        P, plen, stride = self.pack_parents(parents)
+        hp = _c(hyp_parent, np.int32)
+        h = _c(hyps, OBJ)
+        out = np.zeros(len(h), COST)
+        self._check(self.lib.perch_eval_successors(self.h, P.ctypes.data, stride, plen.ctypes.data, len(plen),
+                                                   _ptr(hp), _ptr(h), len(h), K_total, _ptr(out)))
+        return out
+
+    def perch_eval_successors_dev(self, parents_t, stride: int, plen_t, hyp_parent_t, hyps_t, K_total: int, out_t):
+        """Device buffers (torch tensors) in and out; enqueued on the context's stream."""
+        return self._check(self.lib.perch_eval_successors_dev(
+            self.h, parents_t.data_ptr(), stride, plen_t.data_ptr(), plen_t.numel(), hyp_parent_t.data_ptr(),
+            hyps_t.data_ptr(), hyp_parent_t.numel(), K_total, out_t.data_ptr()))
+
+    def perch_render(self, objs):
+        o = _c(objs, OBJ)
+        out = np.empty((self.H, self.W), np.float32)
+        n = ctypes.c_int64(0)
+        self._check(self.lib.perch_render(self.h, _ptr(o), len(o), out.ctypes.data, ctypes.byref(n)))
+        return out, int(n.value)
+
+    def perch_last_timing(self):
+        """(prep_ms, eval_ms) of the last evaluation, from CUDA events."""
+        a, b = ctypes.c_float(0), ctypes.c_float(0)
+        self._check(self.lib.perch_last_timing(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return float(a.value), float(b.value)
+
+    def perch_search(self, mesh_multiset, w: float = 1.0, batch_states: int = 8, time_limit_s: float = 0.0,
+                     max_expansions: int = 0):
+        ms = _c(mesh_multiset, np.uint16)
+        p = perch_search_params(len(ms), ms.ctypes.data, w, batch_states, time_limit_s, max_expansions)
+        r = perch_result()
+        rc = self.lib.perch_search(self.h, ctypes.byref(p), ctypes.byref(r))
+        self._check(rc, ok=(PERCH_OK, PERCH_E_TIMEOUT))
+        objs = np.array([(r.objs[i].mesh, r.objs[i].iyaw, r.objs[i].ix, r.objs[i].iy) for i in range(r.n_objs)], OBJ)
+        key = tuple(sorted((int(o["mesh"]), int(o["ix"]), int(o["iy"]), int(o["iyaw"])) for o in objs))
+        return {"cost": int(r.cost), "key": key, "objs": objs, "expansions": int(r.expansions),
+                "successors": int(r.successors), "seconds": float(r.seconds),
+                "proven_optimal": bool(r.proven_optimal), "status": rc}
+
+
+def records(out) -> np.ndarray:
+    """COST structured array -> (n, 6) int64 (djr, djo, resid, viol, n_new, flags)."""
+    return np.stack([out[f].astype(np.int64) for f in COST.names], 1)

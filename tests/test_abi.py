@@ -1,0 +1,61 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and
+loads, exports every function include/perch.h declares, the binding's
+structures match the header's layouts, and calls fail cleanly without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1510_05613_gb300 import perch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "perch.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(perch.LIB_PATH):
+        from paper_1510_05613_gb300 import build
+        build.build()
+    return perch.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(perch_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_binding_names():
+    assert declared_functions() == sorted(perch.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts():
+    assert ctypes.sizeof(perch.perch_obj) == 8 == perch.OBJ.itemsize
+    assert perch.COST.itemsize == 24
+    assert ctypes.sizeof(perch.perch_mesh) == 40
+    assert ctypes.sizeof(perch.perch_result) == 16 * 8 + 4 + 4 + 8 * 4 + 4 + 4
+
+
+def test_null_context_and_null_args_are_rejected(lib):
+    assert lib.perch_destroy(None) == perch.PERCH_OK
+    assert lib.perch_load_meshes(None, None, 0) == perch.PERCH_E_ARG
+    assert lib.perch_eval_successors(None, None, 0, None, 0, None, None, 0, 1, None) == perch.PERCH_E_ARG
+    assert lib.perch_search(None, None, None) == perch.PERCH_E_ARG
+    assert lib.perch_create(None, 0, None) == perch.PERCH_E_ARG
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.perch_create(ctypes.byref(h), 0, None) == perch.PERCH_E_CUDA
+    assert not h.value

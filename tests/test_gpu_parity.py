@@ -1,0 +1,226 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer records (dJr, dJo, residual, violations, |dR|, flags) must be
+bit-exact; rendered depths are compared bit for bit as well (the north-star
+tolerance for depths is 1e-4 m, and the arithmetic contract makes them equal).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import search
+from paper_1510_05613_gb300 import perch, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _recs(out):
+    r = perch.records(out)
+    r[:, 5] &= 0x7FFFFFFF
+    return r
+
+
+@pytest.fixture(scope="module")
+def c1():
+    wl = synth.workload_c1()
+    p = perch.Perch(0)
+    p.setup(wl)
+    return wl, p, oracle.World.of(wl)
+
+
+@pytest.fixture(scope="module")
+def c2():
+    wl = synth.workload_c2()
+    p = perch.Perch(0)
+    p.setup(wl)
+    return wl, p, oracle.World.of(wl)
+
+
+def _compare(wl, p, w, parents, hp, hyps, K):
+    got = _recs(p.perch_eval_successors(parents, hp, hyps, K))
+    exp = oracle.eval_batch(w, wl.depth, parents, hp, hyps, K)
+    bad = np.nonzero((got != exp).any(1))[0]
+    assert bad.size == 0, f"{bad.size} mismatches, first {hyps[bad[:3]]}: gpu {got[bad[:3]]} oracle {exp[bad[:3]]}"
+    return got
+
+
+def test_render_bit_exact_c1(c1):
+    wl, p, w = c1
+    for objs in (wl.gt, wl.gt[:1], wl.gt[::-1]):
+        z, culled = p.perch_render(objs)
+        ze, ce = oracle.render(w, objs)
+        assert culled == ce
+        assert np.array_equal(z.view(np.uint32), ze.view(np.uint32))
+
+
+def test_render_bit_exact_c2(c2):
+    wl, p, w = c2
+    z, culled = p.perch_render(wl.gt)
+    ze, ce = oracle.render(w, wl.gt)
+    assert culled == ce
+    assert np.array_equal(z.view(np.uint32), ze.view(np.uint32))
+    fin = np.isfinite(ze)
+    assert np.max(np.abs(z[fin] - ze[fin])) <= 1e-4
+
+
+def test_c1_level0_all_hypotheses(c1):
+    wl, p, w = c1
+    hyps = synth.all_hypotheses(wl.grid, [0, 1])
+    got = _compare(wl, p, w, [wl.gt[:0]], np.zeros(len(hyps), np.int32), hyps, wl.K)
+    assert (got[:, 0] > 0).any() and (got[:, 1] > 0).any()
+
+
+def test_c1_last_level_with_residual(c1):
+    wl, p, w = c1
+    parents = [wl.gt[:1], wl.gt[1:2]]
+    h0 = synth.all_hypotheses(wl.grid, [int(wl.gt[1]["mesh"])])
+    h1 = synth.all_hypotheses(wl.grid, [int(wl.gt[0]["mesh"])])
+    hyps = np.concatenate([h0, h1])
+    hp = np.concatenate([np.zeros(len(h0), np.int32), np.ones(len(h1), np.int32)])
+    got = _compare(wl, p, w, parents, hp, hyps, wl.K)
+    assert (got[:, 2] > 0).any() and (got[:, 3] > 0).any()
+
+
+def test_c1_mixed_parents_and_levels(c1):
+    wl, p, w = c1
+    rng = np.random.default_rng(0)
+    allh = synth.all_hypotheses(wl.grid, [0, 1])
+    parents = [wl.gt[:0], wl.gt[:1], allh[rng.choice(len(allh), 1)], allh[rng.choice(len(allh), 1)]]
+    n = 700
+    hyps = allh[rng.choice(len(allh), n)]
+    hp = rng.integers(0, len(parents), n).astype(np.int32)
+    _compare(wl, p, w, parents, hp, hyps, 2)
+    # the same batch with K = 3 (no residual anywhere) and K = 1 from the root
+    _compare(wl, p, w, parents, hp, hyps, 3)
+    _compare(wl, p, w, [wl.gt[:0]], np.zeros(200, np.int32), hyps[:200], 1)
+
+
+def test_c2_sampled_all_levels(c2):
+    wl, p, w = c2
+    rng = np.random.default_rng(1)
+    allh = synth.all_hypotheses(wl.grid, [0, 1, 2])
+    # near the ground truth (overlapping the observation) and uniform
+    near = []
+    for o in wl.gt:
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for k in (0, 3, 8):
+                    near.append((int(o["mesh"]), int(o["ix"]) + dx, int(o["iy"]) + dy, (int(o["iyaw"]) + k) % 16))
+    hyps = np.concatenate([synth.objs(near), allh[rng.choice(len(allh), 120)]])
+    parents = [wl.gt[:0], wl.gt[:1], wl.gt[:2]]
+    hp = np.repeat(np.arange(3, dtype=np.int32), len(hyps))
+    got = _compare(wl, p, w, parents, hp, np.tile(hyps, 3), 3)
+    assert (got[:, 1] > 0).any() and (got[:, 2] > 0).any()
+
+
+def test_c2_bench_launch_sampled(c2):
+    """The full-size batch the benchmark times (root 120k + level-1 80k +
+    level-2 40k hypotheses, one launch): sampled records against the oracle,
+    invariants on all of them."""
+    wl, p, w = c2
+    from bench import c2_batch
+    parents, hp, hyps = c2_batch(wl)
+    got = _recs(p.perch_eval_successors(parents, hp, hyps, wl.K))
+    assert got.shape == (len(hyps), 6)
+    # invariants on every record
+    inval = got[:, 3] > 0
+    assert np.all((got[:, 5] & 2 > 0) == inval)
+    assert np.all(got[inval, :3] == 0)
+    assert np.all(got[~inval, 0] <= got[~inval, 4])
+    assert np.all(got[hp == 0, 3] == 0) and np.all(got[hp != 2, 2] == 0)
+    # sampled exact parity
+    rng = np.random.default_rng(2)
+    idx = np.sort(rng.choice(len(hyps), 150, replace=False))
+    exp = oracle.eval_batch(w, wl.depth, parents, hp[idx], hyps[idx], wl.K)
+    assert np.array_equal(got[idx], exp)
+
+
+def test_empty_observation_and_huge_delta():
+    wl = synth.workload_c1()
+    allh = synth.all_hypotheses(wl.grid, [0, 1])[::7]
+    for depth, delta in ((np.zeros_like(wl.depth), 0.01), (wl.depth, 5.0)):
+        p = perch.Perch(0)
+        p.perch_load_meshes(wl.meshes)
+        p.perch_set_pose_grid(wl.grid)
+        p.perch_set_observation(depth, wl.cam.fxfycxcy, wl.cam.T_wc, delta)
+        w = oracle.World(wl.cam, wl.meshes, wl.grid, delta)
+        parents = [wl.gt[:0], wl.gt[:1]]
+        hp = np.arange(len(allh), dtype=np.int32) % 2
+        got = _recs(p.perch_eval_successors(parents, hp, allh, 2))
+        exp = oracle.eval_batch(w, depth, parents, hp, allh, 2)
+        assert np.array_equal(got, exp)
+        p.close()
+
+
+def test_offscreen_and_ragged_pose_grid():
+    """A pose grid reaching past the image edge (partly and fully off-screen
+    objects) and an odd number of poses."""
+    wl = synth.workload_c1()
+    grid = synth.pose_grid(-0.9, 0.13, 13, 5)
+    p = perch.Perch(0)
+    p.perch_load_meshes(wl.meshes)
+    p.perch_set_pose_grid(grid)
+    p.perch_set_observation(wl.depth, wl.cam.fxfycxcy, wl.cam.T_wc, wl.delta)
+    w = oracle.World(wl.cam, wl.meshes, grid, wl.delta)
+    hyps = synth.all_hypotheses(grid, [0, 1])
+    parent = synth.objs([(0, 6, 6, 0)])
+    hp = np.arange(len(hyps), dtype=np.int32) % 2
+    got = _recs(p.perch_eval_successors([parent[:0], parent], hp, hyps, 2))
+    exp = oracle.eval_batch(w, wl.depth, [parent[:0], parent], hp, hyps, 2)
+    assert np.array_equal(got, exp)
+    assert (got[:, 4] == 0).any()  # some hypotheses fully off-screen
+    p.close()
+
+
+def test_device_pointer_entry_point(c1):
+    import torch
+    wl, p, w = c1
+    hyps = synth.all_hypotheses(wl.grid, [0, 1])[::3]
+    P, plen, stride = perch.Perch.pack_parents([wl.gt[:1]])
+    dev = torch.device("cuda:0")
+    tP = torch.from_numpy(P.view(np.int16).reshape(-1).copy()).to(dev)
+    tplen = torch.from_numpy(plen).to(dev)
+    thp = torch.zeros(len(hyps), dtype=torch.int32, device=dev)
+    th = torch.from_numpy(np.ascontiguousarray(hyps).view(np.int16).reshape(-1).copy()).to(dev)
+    tout = torch.zeros(len(hyps) * 6, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    p.perch_eval_successors_dev(tP, stride, tplen, thp, th, 2, tout)
+    torch.cuda.synchronize()
+    got = tout.cpu().numpy().reshape(-1, 6).astype(np.int64)
+    exp = oracle.eval_batch(w, wl.depth, [wl.gt[:1]], np.zeros(len(hyps), np.int32), hyps, 2)
+    assert np.array_equal(got, exp)
+
+
+def test_argument_errors(c1):
+    wl, p, w = c1
+    hyps = synth.all_hypotheses(wl.grid, [0])[:4]
+    with pytest.raises(perch.PerchError) as e:
+        p.perch_eval_successors([wl.gt[:0]], np.array([0, 0, 0, 5], np.int32), hyps, 2)
+    assert e.value.code == perch.PERCH_E_ARG
+    bad = hyps.copy()
+    bad["ix"][1] = 99
+    with pytest.raises(perch.PerchError):
+        p.perch_eval_successors([wl.gt[:0]], np.zeros(4, np.int32), bad, 2)
+    with pytest.raises(perch.PerchError):  # parent as long as the full scene
+        p.perch_eval_successors([wl.gt], np.zeros(4, np.int32), hyps, 2)
+    assert len(p.perch_eval_successors([wl.gt[:0]], np.zeros(0, np.int32), hyps[:0], 2)) == 0
+
+
+def test_search_matches_oracle_exhaustive_small_c1():
+    grid = synth.pose_grid(-0.15, 0.1, 4, 4)
+    wl = synth.workload_c1(scene=3, grid=grid)
+    p = perch.Perch(0)
+    p.setup(wl)
+    w = oracle.World.of(wl)
+    ex_cost, ex_key = search.exhaustive(w, wl.depth, wl.grid, wl.mesh_multiset)
+    for B in (1, 3, 64):
+        r = p.perch_search(wl.mesh_multiset, batch_states=B)
+        assert r["proven_optimal"] and (r["cost"], r["key"]) == (ex_cost, ex_key)
+    p.close()
+
+
+def test_search_matches_oracle_ucs_full_c1(c1):
+    wl, p, w = c1
+    cost, key, _ = search.uniform_cost_search(w, wl.depth, wl.grid, wl.mesh_multiset)
+    r = p.perch_search(wl.mesh_multiset, batch_states=16)
+    assert r["proven_optimal"] and (r["cost"], r["key"]) == (cost, key)
