@@ -219,10 +219,16 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream: torch's default stream has the NULL handle, which the
+    # library would read as "create your own stream"
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
 
     wl = synth.workload_c2()
     parents, hp, hyps = c2_batch(wl)
+    if args.max_hyps and args.max_hyps < len(hyps):  # reduced batch (profiling case)
+        keep = np.linspace(0, len(hyps) - 1, args.max_hyps).astype(np.int64)
+        hp, hyps = hp[keep], hyps[keep]
     n_hyp = len(hyps)
     p = perch.Perch(local, stream=stream.cuda_stream)
     p.setup(wl)
@@ -278,11 +284,15 @@ def run_ours(args):
     achieved = ops / eval_s / 1e12
 
     # end to end through the C ABI with host buffers (pinned)
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    def pin(a):
+        a = np.ascontiguousarray(a)
+        t = torch.from_numpy(a.view(np.uint8).reshape(-1)).pin_memory()
+        return t.numpy().view(a.dtype).reshape(a.shape)
+
     h_depth = pin(wl.depth)
     h_hyps, h_hp = pin(hyps), pin(hp)
     e2e_t = []
-    for k in range(2 + max(2, args.steps // 2)):
+    for k in range(0 if args.no_e2e else 2 + max(2, args.steps // 2)):
         t0 = time.perf_counter()
         p.perch_set_observation(h_depth, wl.cam.fxfycxcy, wl.cam.T_wc, wl.delta)
         out = p.perch_eval_successors(parents, h_hp, h_hyps, wl.K)
@@ -290,6 +300,8 @@ def run_ours(args):
         if k >= 2:
             e2e_t.append(t1 - t0)
     e2e_bytes_in = h_depth.nbytes + h_hyps.nbytes + h_hp.nbytes + P.nbytes + plen.nbytes
+    if not e2e_t:
+        out, e2e_t = np.zeros(n_hyp, perch.COST), [float("nan")]
     e2e = {"value": ws * n_hyp / statistics.mean(e2e_t), "unit": UNIT, "h2d_bytes_per_step": int(e2e_bytes_in),
            "d2h_bytes_per_step": int(out.nbytes),
            "includes": "perch_set_observation (depth upload, cloud + grid build) + perch_eval_successors "
@@ -350,6 +362,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-search", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--max-hyps", type=int, default=0, help="evenly subsample the batch (profiling case)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
