@@ -141,6 +141,26 @@ int perch_eval_successors_dev(perch_ctx* ctx, const perch_obj* parents, int32_t 
                               const int32_t* parent_len, int32_t n_par, const int32_t* hyp_parent,
                               const perch_obj* hyp, int64_t n_hyp, int32_t K_total, perch_cost* out);
 
+/* Same work and arguments as perch_eval_successors_dev (device pointers,
+ * enqueued on the context's stream), but the call allocates no memory: its
+ * scratch (parent z-buffers, residual sets) is a fixed 8 MiB device array
+ * compiled into the library. The paper has no counterpart; this serves
+ * callers that cannot allocate device memory when they evaluate (a real-time
+ * loop that must not stall on cudaMalloc/cudaFree, or a process whose GPU
+ * memory is fixed by its own pool after start-up). They set the context up
+ * first; the set-up calls do allocate.
+ * Limit: n_par * (4*W*H + 4*max(|I|,1) + 4) bytes (each part rounded up to
+ * 256) must not exceed 8 MiB, else PERCH_E_RANGE and nothing is enqueued.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture. Every call shares
+ * the array and re-initialises it, so calls whose work overlaps on the GPU
+ * (other streams, or other contexts on the same device) race; serialise them.
+ * The array is held by every GPU that loads the library until the process
+ * exits. */
+int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride,
+                                  const int32_t* parent_len, int32_t n_par, const int32_t* hyp_parent,
+                                  const perch_obj* hyp, int64_t n_hyp, int32_t K_total, perch_cost* out);
+
 /* z-buffer render (min depth, +inf where empty) of n objects into
  * depth_out[H * W] (host pointer), the R_j of Sec. III-A. Returns the number
  * of culled triangles in *n_culled (may be NULL). */

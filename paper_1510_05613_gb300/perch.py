@@ -24,7 +24,7 @@ COST = np.dtype([("djr", np.int32), ("djo", np.int32), ("resid", np.int32), ("vi
 # names exported by the library (include/perch.h)
 EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_meshes", "perch_set_pose_grid",
            "perch_set_observation", "perch_eval_successors", "perch_eval_successors_dev", "perch_render",
-           "perch_search", "perch_last_timing")
+           "perch_search", "perch_last_timing", "perch_eval_successors_noalloc")
 
 
 class perch_mesh(ctypes.Structure):
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
         "perch_render": ([P, P, I32, P, P], ctypes.c_int),
         "perch_search": ([P, P, P], ctypes.c_int),
         "perch_last_timing": ([P, P, P], ctypes.c_int),
+        "perch_eval_successors_noalloc": ([P, P, I32, P, I32, P, P, I64, I32, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -179,6 +180,14 @@ class Perch:
     def perch_eval_successors_dev(self, parents_t, stride: int, plen_t, hyp_parent_t, hyps_t, K_total: int, out_t):
         """Device buffers (torch tensors) in and out; enqueued on the context's stream."""
         return self._check(self.lib.perch_eval_successors_dev(
+            self.h, parents_t.data_ptr(), stride, plen_t.data_ptr(), plen_t.numel(), hyp_parent_t.data_ptr(),
+            hyps_t.data_ptr(), hyp_parent_t.numel(), K_total, out_t.data_ptr()))
+
+    def perch_eval_successors_noalloc(self, parents_t, stride: int, plen_t, hyp_parent_t, hyps_t, K_total: int,
+                                      out_t):
+        """As perch_eval_successors_dev, with the library's fixed scratch array
+        instead of context-allocated scratch (the call allocates nothing)."""
+        return self._check(self.lib.perch_eval_successors_noalloc(
             self.h, parents_t.data_ptr(), stride, plen_t.data_ptr(), plen_t.numel(), hyp_parent_t.data_ptr(),
             hyps_t.data_ptr(), hyp_parent_t.numel(), K_total, out_t.data_ptr()))
 
