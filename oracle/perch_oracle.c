@@ -9,8 +9,9 @@
  *
  * Build: gcc -O2 -ffp-contract=off -fno-fast-math [-fopenmp] -shared -fPIC.
  * Every float operation below is one IEEE binary32 operation rounded to
- * nearest-even (no contraction into FMA), so the result is fixed by the
- * arithmetic contract written out next to each step.
+ * nearest-even; a fused multiply-add appears only where written as fmaf()
+ * (one rounding, as IEEE 754 defines it) and the compiler contracts nothing
+ * else, so the result is fixed by the arithmetic written out at each step.
  *
  * What is computed, per the paper:
  *   - observed cloud I (Sec. III-A notation): valid depth pixels back-projected
@@ -110,32 +111,48 @@ static void cam_free(or_cam* c) { free(c->rx); free(c->ry); }
 /* ------------------------------------------------------------ rasteriser */
 typedef struct { int64_t X, Y; float iz; int bad; } or_vtx;
 
-/* object frame -> world (yaw then translation) -> camera -> pixel, snapped */
-static or_vtx transform_vertex(const or_world* w, const or_cam* c, const float* v,
-                               float x, float y, float cs, float sn) {
+/* Camera-frame pose of a placed object: the yaw rotation and the
+ * world->camera rotation composed into one matrix M = R_cw Rz(yaw), and the
+ * table translation into one offset b = R_cw (x, y, 0) + t_cw. Both are
+ * evaluated in double from the binary32 inputs (every product of two floats
+ * is exact in double) and rounded once to binary32. */
+typedef struct { float M[9]; float b[3]; } or_pose;
+
+static or_pose placed_pose(const or_world* w, const or_cam* c, or_obj o) {
+  or_pose p;
+  double cs = w->cos_sin[2 * o.iyaw], sn = w->cos_sin[2 * o.iyaw + 1];
+  double x = w->xs[o.ix], y = w->ys[o.iy];
+  for (int r = 0; r < 3; ++r) {
+    double r0 = c->Rcw[r * 3 + 0], r1 = c->Rcw[r * 3 + 1], r2 = c->Rcw[r * 3 + 2];
+    p.M[r * 3 + 0] = (float)(r0 * cs + r1 * sn);
+    p.M[r * 3 + 1] = (float)(r1 * cs - r0 * sn);
+    p.M[r * 3 + 2] = (float)r2;
+    p.b[r] = (float)((r0 * x + r1 * y) + (double)c->tcw[r]);
+  }
+  return p;
+}
+
+/* object-frame vertex -> camera -> pixel, snapped to 1/16 pixel:
+ * c_r = fma(M_r2, vz, fma(M_r1, vy, M_r0 vx)) + b_r; 1/z = 1/c_z;
+ * u = fma(fx, c_x (1/z), cx); X = rint(16 u) */
+static or_vtx transform_vertex(const or_world* w, const or_pose* p, const float* v) {
   or_vtx o;
-  float t1 = cs * v[0], t2 = sn * v[1];
-  float xw = (t1 - t2) + x;
-  float t3 = sn * v[0], t4 = cs * v[1];
-  float yw = (t3 + t4) + y;
-  float zw = v[2];
   float cam[3];
   for (int r = 0; r < 3; ++r) {
-    float a = c->Rcw[r * 3 + 0] * xw;
-    float b = c->Rcw[r * 3 + 1] * yw;
-    float d = c->Rcw[r * 3 + 2] * zw;
-    cam[r] = ((a + b) + d) + c->tcw[r];
+    float a = p->M[r * 3 + 0] * v[0];
+    a = fmaf(p->M[r * 3 + 1], v[1], a);
+    a = fmaf(p->M[r * 3 + 2], v[2], a);
+    cam[r] = a + p->b[r];
   }
   o.bad = !(cam[2] > 0.05f);
-  float qx = cam[0] / cam[2], qy = cam[1] / cam[2];
-  float u = w->fx * qx, vv = w->fy * qy;
-  u = u + w->cx;
-  vv = vv + w->cy;
+  float iz = 1.0f / cam[2];
+  float qx = cam[0] * iz, qy = cam[1] * iz;
+  float u = fmaf(w->fx, qx, w->cx), vv = fmaf(w->fy, qy, w->cy);
   if (!(fabsf(u) <= 2048.0f) || !(fabsf(vv) <= 2048.0f)) o.bad = 1;
   if (o.bad) { o.X = o.Y = 0; o.iz = 0.0f; return o; }
   o.X = (int64_t)lrintf(16.0f * u);
   o.Y = (int64_t)lrintf(16.0f * vv);
-  o.iz = 1.0f / cam[2];
+  o.iz = iz;
   return o;
 }
 
@@ -157,13 +174,12 @@ static int64_t ceildiv16(int64_t a) { return -floordiv16(-a); }
 /* render one object into zbuf (min), counting culled triangles */
 static void render_object(const or_world* w, const or_cam* c, or_obj o, float* zbuf, int64_t* culled) {
   const or_mesh* m = &w->meshes[o.mesh];
-  float x = w->xs[o.ix], y = w->ys[o.iy];
-  float cs = w->cos_sin[2 * o.iyaw], sn = w->cos_sin[2 * o.iyaw + 1];
+  const or_pose pose = placed_pose(w, c, o);
   for (int t = 0; t < m->n_tris; ++t) {
     or_vtx v[3];
     int bad = 0;
     for (int k = 0; k < 3; ++k) {
-      v[k] = transform_vertex(w, c, m->verts + 3 * (size_t)m->tris[3 * t + k], x, y, cs, sn);
+      v[k] = transform_vertex(w, &pose, m->verts + 3 * (size_t)m->tris[3 * t + k]);
       bad |= v[k].bad;
     }
     if (bad) { (*culled)++; continue; }
@@ -198,8 +214,9 @@ static void render_object(const or_world* w, const or_cam* c, or_obj o, float* z
         int in2 = w2 > 0 || (w2 == 0 && own01);
         if (!(in0 && in1 && in2)) continue;
         float b0 = (float)w0 * invA, b1 = (float)w1 * invA, b2 = (float)w2 * invA;
-        float s0 = b0 * v[0].iz, s1 = b1 * v[1].iz, s2 = b2 * v[2].iz;
-        float iz = (s0 + s1) + s2;
+        float iz = b0 * v[0].iz;
+        iz = fmaf(b1, v[1].iz, iz);
+        iz = fmaf(b2, v[2].iz, iz);
         float z = 1.0f / iz;
         float* dst = &zbuf[py * w->W + px];
         if (z < *dst) *dst = z;
@@ -226,9 +243,9 @@ static or_pt cam_to_world(const or_cam* c, or_pt p) {
   float o[3];
   for (int r = 0; r < 3; ++r) {
     float a = c->Rwc[r * 3 + 0] * p.x;
-    float b = c->Rwc[r * 3 + 1] * p.y;
-    float d = c->Rwc[r * 3 + 2] * p.z;
-    o[r] = ((a + b) + d) + c->twc[r];
+    a = fmaf(c->Rwc[r * 3 + 1], p.y, a);
+    a = fmaf(c->Rwc[r * 3 + 2], p.z, a);
+    o[r] = a + c->twc[r];
   }
   or_pt q = {o[0], o[1], o[2]};
   return q;
@@ -236,8 +253,9 @@ static or_pt cam_to_world(const or_cam* c, or_pt p) {
 
 static float dist2(or_pt a, or_pt b) {
   float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-  float sx = dx * dx, sy = dy * dy, sz = dz * dz;
-  return (sx + sy) + sz;
+  float d = dx * dx;
+  d = fmaf(dy, dy, d);
+  return fmaf(dz, dz, d);
 }
 
 /* Eq. (1): p is explained by C iff some point of C lies within delta */
@@ -252,8 +270,7 @@ static int in_volume(const or_world* w, or_obj o, or_pt qw) {
   const or_mesh* m = &w->meshes[o.mesh];
   float r2 = (float)((double)m->vol_r * (double)m->vol_r);
   float dx = qw.x - w->xs[o.ix], dy = qw.y - w->ys[o.iy];
-  float sx = dx * dx, sy = dy * dy;
-  float d2 = sx + sy;
+  float d2 = fmaf(dy, dy, dx * dx);
   return d2 <= r2 && m->vol_zlo <= qw.z && qw.z <= m->vol_zhi;
 }
 

@@ -62,9 +62,12 @@ Geometry perch_ctx::geometry() const {
   Geometry g;
   g.meshes = meshes.as<DevMesh>();
   g.n_mesh = n_mesh;
-  g.ml_verts = ml_verts.as<float4>();
-  g.ml_info = ml_info.as<int4>();
-  g.ml_tris = ml_tris.as<uint32_t>();
+  g.chunk_info = chunk_info.as<int4>();
+  g.chunk_tris = chunk_tris.as<uint32_t>();
+  g.chunk_verts = chunk_verts.as<float4>();
+  g.n_cverts = n_cverts;
+  g.vtab = vtab.as<float4>();
+  g.pose_off = pose_off.as<float4>();
   g.xs = xs.as<float>();
   g.ys = ys.as<float>();
   g.cs = cs.as<float2>();
@@ -90,26 +93,37 @@ static float ordered_to_float(int i) {
   return f;
 }
 
-// screen boxes of every (mesh, pose); sets the shared-memory tile size
-int perch_ctx::ensure_bbox() {
+// Camera-frame pose tables (per-yaw matrices, per-(ix, iy) offsets, per-yaw
+// vertex tables) and the screen box of every (mesh, pose), which sets the
+// shared-memory tile size. Rebuilt when the meshes, the pose grid or the
+// camera change.
+int perch_ctx::ensure_tables() {
   perch_ctx* ctx = this;
-  if (bbox_valid) return PERCH_OK;
+  if (tables_valid) return PERCH_OK;
   if (!has_cam || n_mesh == 0 || nx == 0) return PERCH_OK;
   const long long n = (long long)n_mesh * nx * ny * n_yaw;
+  CK(yaw_mats.ensure(sizeof(float) * 9 * n_yaw), "alloc yaw matrices");
+  CK(pose_off.ensure(sizeof(float4) * nx * ny), "alloc pose offsets");
+  CK(vtab.ensure(sizeof(float4) * (size_t)n_yaw * n_cverts), "alloc vertex tables");
   CK(pose_bbox.ensure(sizeof(int4) * n), "alloc pose boxes");
   CK(scratch_small.ensure(64), "alloc");
   int* d = scratch_small.as<int>();
   CK(cudaMemsetAsync(d, 0, 3 * sizeof(int), stream), "memset");
-  CK(launch_pose_bbox(cam, geometry(), pose_bbox.as<int4>(), d, d + 2, stream), "pose_bbox kernel");
+  const Geometry g = geometry();
+  CK(launch_pose_tables(cam, g, yaw_mats.as<float>(), pose_off.as<float4>(), vtab.as<float4>(), stream),
+     "pose tables kernel");
+  CK(launch_pose_bbox(cam, g, yaw_mats.as<float>(), pose_bbox.as<int4>(), d, d + 2, stream), "pose_bbox kernel");
   int h[3];
   CK(cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, stream), "copy pose boxes");
-  CK(cudaStreamSynchronize(stream), "pose_bbox sync");
-  if (h[2]) return fail(PERCH_E_RANGE, "a (mesh, pose) projects behind the near plane or far off-screen");
+  CK(cudaStreamSynchronize(stream), "pose tables sync");
+  if (h[2] & 1) return fail(PERCH_E_RANGE, "a (mesh, pose) projects behind the near plane or far off-screen");
+  if (h[2] & 2)
+    return fail(PERCH_E_RANGE, "an object's screen box exceeds %d pixels (too close to the camera)", kMaxObjectPixels);
   if (!eval_tile_fits(device, std::max(h[0], 1), std::max(h[1], 1)))
     return fail(PERCH_E_RANGE, "object screen box %dx%d does not fit in shared memory", h[0], h[1]);
   tile_w = std::max(h[0], 1);
   tile_h = std::max(h[1], 1);
-  bbox_valid = true;
+  tables_valid = true;
   return PERCH_OK;
 }
 
@@ -189,8 +203,8 @@ int perch_load_meshes(perch_ctx* ctx, const perch_mesh* meshes, int32_t n) {
         d.lo[k] = std::min(d.lo[k], x);
         d.hi[k] = std::max(d.hi[k], x);
       }
-    // greedy meshlets in triangle order: <= 64 vertices, <= 64 triangles
-    d.meshlet_begin = (int)info.size();
+    // greedy chunks in triangle order: <= 1024 vertices, <= 2048 triangles
+    d.chunk_begin = (int)info.size();
     std::vector<int> local(m.n_verts, -1);
     std::vector<int> cur_v;
     std::vector<uint32_t> cur_t;
@@ -202,6 +216,7 @@ int perch_load_meshes(perch_ctx* ctx, const perch_mesh* meshes, int32_t n) {
         local[gv] = -1;
       }
       tris.insert(tris.end(), cur_t.begin(), cur_t.end());
+      while (tris.size() % 4) tris.push_back(0xffffffffu);  // 16-byte aligned chunk lists (bulk copies)
       info.push_back(in);
       cur_v.clear();
       cur_t.clear();
@@ -219,40 +234,41 @@ int perch_load_meshes(perch_ctx* ctx, const perch_mesh* meshes, int32_t n) {
         for (int j = 0; j < k; ++j) dup |= idx[j] == idx[k];
         if (!dup && local[idx[k]] < 0) need++;
       }
-      if ((int)cur_v.size() + need > kMeshletMaxVerts || (int)cur_t.size() + 1 > kMeshletMaxTris) flush();
+      if ((int)cur_v.size() + need > kChunkMaxVerts || (int)cur_t.size() + 1 > kChunkMaxTris) flush();
       uint32_t pk = 0;
       for (int k = 0; k < 3; ++k) {
         if (local[idx[k]] < 0) {
           local[idx[k]] = (int)cur_v.size();
           cur_v.push_back(idx[k]);
         }
-        pk |= (uint32_t)local[idx[k]] << (8 * k);
+        pk |= (uint32_t)local[idx[k]] << (10 * k);
       }
       cur_t.push_back(pk);
     }
     flush();
-    d.meshlet_count = (int)info.size() - d.meshlet_begin;
-    max_ml = std::max(max_ml, d.meshlet_count);
+    d.chunk_count = (int)info.size() - d.chunk_begin;
+    max_ml = std::max(max_ml, d.chunk_count);
     max_tris = std::max(max_tris, m.n_tris);
   }
   CK(ctx->meshes.ensure(sizeof(DevMesh) * n), "alloc meshes");
-  CK(ctx->ml_verts.ensure(sizeof(float4) * verts.size()), "alloc meshlet vertices");
-  CK(ctx->ml_info.ensure(sizeof(int4) * info.size()), "alloc meshlets");
-  CK(ctx->ml_tris.ensure(sizeof(uint32_t) * tris.size()), "alloc meshlet triangles");
+  CK(ctx->chunk_verts.ensure(sizeof(float4) * verts.size()), "alloc chunk vertices");
+  CK(ctx->chunk_info.ensure(sizeof(int4) * info.size()), "alloc chunks");
+  CK(ctx->chunk_tris.ensure(sizeof(uint32_t) * tris.size()), "alloc chunk triangles");
   CK(cudaMemcpyAsync(ctx->meshes.p, dm.data(), sizeof(DevMesh) * n, cudaMemcpyHostToDevice, ctx->stream), "copy");
-  CK(cudaMemcpyAsync(ctx->ml_verts.p, verts.data(), sizeof(float4) * verts.size(), cudaMemcpyHostToDevice,
+  CK(cudaMemcpyAsync(ctx->chunk_verts.p, verts.data(), sizeof(float4) * verts.size(), cudaMemcpyHostToDevice,
                      ctx->stream), "copy");
-  CK(cudaMemcpyAsync(ctx->ml_info.p, info.data(), sizeof(int4) * info.size(), cudaMemcpyHostToDevice, ctx->stream),
-     "copy");
-  CK(cudaMemcpyAsync(ctx->ml_tris.p, tris.data(), sizeof(uint32_t) * tris.size(), cudaMemcpyHostToDevice,
+  CK(cudaMemcpyAsync(ctx->chunk_info.p, info.data(), sizeof(int4) * info.size(), cudaMemcpyHostToDevice,
+                     ctx->stream), "copy");
+  CK(cudaMemcpyAsync(ctx->chunk_tris.p, tris.data(), sizeof(uint32_t) * tris.size(), cudaMemcpyHostToDevice,
                      ctx->stream), "copy");
   CK(cudaStreamSynchronize(ctx->stream), "load meshes");
   ctx->h_meshes = dm;
   ctx->n_mesh = n;
-  ctx->max_meshlets = max_ml;
+  ctx->max_chunks = max_ml;
   ctx->max_tris = max_tris;
-  ctx->bbox_valid = false;
-  return ctx->ensure_bbox();
+  ctx->n_cverts = (int)verts.size();
+  ctx->tables_valid = false;
+  return ctx->ensure_tables();
 }
 
 int perch_set_pose_grid(perch_ctx* ctx, const float* xs, int32_t nx, const float* ys, int32_t ny,
@@ -272,8 +288,8 @@ int perch_set_pose_grid(perch_ctx* ctx, const float* xs, int32_t nx, const float
   ctx->nx = nx;
   ctx->ny = ny;
   ctx->n_yaw = n_yaw;
-  ctx->bbox_valid = false;
-  return ctx->ensure_bbox();
+  ctx->tables_valid = false;
+  return ctx->ensure_tables();
 }
 
 int perch_set_observation(perch_ctx* ctx, const float* depth, int32_t W, int32_t H, const float fxfycxcy[4],
@@ -308,7 +324,7 @@ int perch_set_observation(perch_ctx* ctx, const float* depth, int32_t W, int32_t
   c.delta = delta;
   c.delta2 = (float)((double)delta * (double)delta);
   ctx->has_cam = true;
-  ctx->bbox_valid = false;
+  ctx->tables_valid = false;
 
   const int npx = W * H;
   const int nblk = (npx + 255) / 256;
@@ -392,6 +408,7 @@ int perch_set_observation(perch_ctx* ctx, const float* depth, int32_t W, int32_t
     CK(ctx->start3.ensure(4 * ((size_t)cells + 1)), "alloc");
     CK(ctx->start2.ensure(4 * ((size_t)c2 + 1)), "alloc");
     CK(ctx->obs3.ensure(16 * (size_t)n), "alloc");
+    CK(ctx->dil3.ensure(4 * ((size_t)cells / 32 + 1)), "alloc");
     CK(ctx->world2.ensure(16 * (size_t)n), "alloc");
     CK(ctx->cam2.ensure(16 * (size_t)n), "alloc");
     CK(ctx->scan_tmp.ensure(4 * ((size_t)cmax / 1024 + 2)), "alloc");
@@ -405,6 +422,9 @@ int perch_set_observation(perch_ctx* ctx, const float* depth, int32_t W, int32_t
        "copy");
     CK(launch_scatter(ctx->keys.as<int>(), n, ctx->cursor.as<int>(), ctx->cam_pts.as<float4>(),
                       ctx->obs3.as<float4>(), nullptr, nullptr, ctx->stream), "scatter3");
+    CK(cudaMemsetAsync(ctx->dil3.p, 0, 4 * ((size_t)cells / 32 + 1), ctx->stream), "memset");
+    CK(launch_dilate3(ctx->start3.as<int>(), o.n3x, o.n3y, o.n3z, ctx->dil3.as<uint32_t>(), ctx->stream),
+       "dilate3");
     // bucket the world-frame cloud (with its camera-frame copy)
     CK(cudaMemsetAsync(ctx->counts.p, 0, 4 * (size_t)c2, ctx->stream), "memset");
     CK(launch_grid2_keys(ctx->world_pts.as<float4>(), n, o.g2x, o.g2y, o.inv2, o.n2x, o.n2y, ctx->keys.as<int>(),
@@ -418,11 +438,12 @@ int perch_set_observation(perch_ctx* ctx, const float* depth, int32_t W, int32_t
        "scatter2");
     o.cam3 = ctx->obs3.as<float4>();
     o.start3 = ctx->start3.as<int>();
+    o.dil3 = ctx->dil3.as<uint32_t>();
     o.world2 = ctx->world2.as<float4>();
     o.cam2 = ctx->cam2.as<float4>();
     o.start2 = ctx->start2.as<int>();
   }
-  int rc = ctx->ensure_bbox();
+  int rc = ctx->ensure_tables();
   if (rc != PERCH_OK) return rc;
   CK(cudaStreamSynchronize(ctx->stream), "observation index");
   ctx->has_obs = true;
@@ -463,7 +484,7 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
   CK(cudaEventRecord(ev[0], stream), "event");
   CK(launch_fill_u32(parent_z.as<uint32_t>(), kInfBits, (long long)npx * n_par, stream), "clear parents");
   CK(cudaMemsetAsync(uset_count.p, 0, 4 * (size_t)std::max(n_par, 1), stream), "memset");
-  CK(launch_render_parents(cam, g, b, max_meshlets, nullptr, stream), "render parents");
+  CK(launch_render_parents(cam, g, b, max_chunks, nullptr, stream), "render parents");
   CK(launch_uset(cam, g, obs, b, stream), "U sets");
   CK(cudaEventRecord(ev[1], stream), "event");
   CK(launch_eval(cam, g, obs, b, stream), "eval kernel");
@@ -590,7 +611,7 @@ int perch_render(perch_ctx* ctx, const perch_obj* objs, int32_t n, float* depth_
   b.parent_len = ctx->b_plen.as<int32_t>();
   b.n_par = 1;
   b.parent_z = ctx->parent_z.as<float>();
-  CK(launch_render_parents(ctx->cam, ctx->geometry(), b, ctx->max_meshlets, culled, ctx->stream), "render");
+  CK(launch_render_parents(ctx->cam, ctx->geometry(), b, ctx->max_chunks, culled, ctx->stream), "render");
   unsigned long long hc = 0;
   CK(cudaMemcpyAsync(depth_out, ctx->parent_z.p, 4 * npx, cudaMemcpyDeviceToHost, ctx->stream), "copy depth");
   CK(cudaMemcpyAsync(&hc, culled, 8, cudaMemcpyDeviceToHost, ctx->stream), "copy");

@@ -23,10 +23,10 @@ struct perch_ctx {
   bool own_stream = false;
   std::string err;
 
-  // object meshes, split into meshlets
-  int n_mesh = 0, max_meshlets = 0, max_tris = 0;
+  // object meshes, split into chunks
+  int n_mesh = 0, max_chunks = 0, max_tris = 0, n_cverts = 0;
   std::vector<perch::DevMesh> h_meshes;
-  DevBuf meshes, ml_verts, ml_info, ml_tris;
+  DevBuf meshes, chunk_verts, chunk_info, chunk_tris;
 
   // pose grid
   int nx = 0, ny = 0, n_yaw = 0;
@@ -37,11 +37,11 @@ struct perch_ctx {
   perch::Camera cam{};
   perch::ObsIndex obs{};
   DevBuf depth, rx, ry, blockcnt, blockoff, scan_tmp, cam_pts, world_pts, keys, counts, cursor;
-  DevBuf start3, start2, obs3, world2, cam2, scratch_small;
+  DevBuf start3, start2, obs3, world2, cam2, dil3, scratch_small;
 
-  // screen box of every (mesh, pose) and the tile it needs
-  DevBuf pose_bbox;
-  bool bbox_valid = false;
+  // camera-frame pose tables and the screen box of every (mesh, pose)
+  DevBuf yaw_mats, pose_off, vtab, pose_bbox;
+  bool tables_valid = false;
   int tile_w = 0, tile_h = 0;
 
   // per-batch buffers
@@ -53,8 +53,8 @@ struct perch_ctx {
   bool timed = false;
 
   std::vector<DevBuf*> all_buffers() {
-    return {&meshes, &ml_verts, &ml_info, &ml_tris, &xs, &ys, &cs, &depth, &rx, &ry, &blockcnt, &blockoff,
-            &scan_tmp, &cam_pts, &world_pts, &keys, &counts, &cursor, &start3, &start2, &obs3, &world2, &cam2,
+    return {&meshes, &chunk_verts, &chunk_info, &chunk_tris, &yaw_mats, &pose_off, &vtab, &xs, &ys, &cs, &depth, &rx, &ry, &blockcnt, &blockoff,
+            &scan_tmp, &cam_pts, &world_pts, &keys, &counts, &cursor, &start3, &start2, &obs3, &world2, &cam2, &dil3,
             &scratch_small, &pose_bbox, &parent_z, &uset, &uset_count, &b_parents, &b_plen, &b_hp, &b_hyp,
             &b_out};
   }
@@ -62,7 +62,7 @@ struct perch_ctx {
   int fail(int code, const char* fmt, ...);
   int cuda(cudaError_t e, const char* what);
   perch::Geometry geometry() const;
-  int ensure_bbox();
+  int ensure_tables();
   int enqueue_eval(const perch_obj* d_parents, int parent_stride, const int32_t* d_plen, int n_par,
                    const int32_t* d_hp, const perch_obj* d_hyp, long long n_hyp, int K_total, perch_cost* d_out);
 };

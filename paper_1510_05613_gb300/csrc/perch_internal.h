@@ -11,13 +11,18 @@ namespace perch {
 
 constexpr uint32_t kInfBits = 0x7f800000u;  // +inf: empty z-buffer pixel
 constexpr uint32_t kFlagBadIndex = 0x80000000u;
-constexpr int kMeshletMaxVerts = 64;
-constexpr int kMeshletMaxTris = 64;
+constexpr uint32_t kFlagTimeout = 0x40000000u;  // a bounded wait in the kernel gave up
+constexpr int kChunkMaxVerts = 512;   // vertices of one mesh chunk (10-bit local indices)
+constexpr int kChunkMaxTris = 1024;   // triangles of one mesh chunk (list padded to 4 entries)
 constexpr int kEvalThreads = 256;
 constexpr int kEvalWarps = kEvalThreads / 32;
-constexpr float kNearZ = 0.05f;   // cull: vertex depth at or below this
-constexpr float kGuard = 2048.0f; // cull: |u| or |v| beyond this (pixels)
-constexpr int kMaxExtent = 16384; // cull: snapped extent (1/16 px) at or above
+constexpr int kInlinePixels = 4;   // a lane tests at most this many pixel centres per triangle
+constexpr int kBigQueue = 128;     // per-chunk queue of larger triangles, shared by the CTA
+constexpr int kWaitSpins = 1 << 20;  // bound on mbarrier polls before a kernel gives up
+constexpr int kMaxObjectPixels = 1000;  // screen box limit that keeps edge arithmetic in int32
+constexpr float kNearZ = 0.05f;    // cull: vertex depth at or below this
+constexpr float kGuard = 2048.0f;  // cull: |u| or |v| beyond this (pixels)
+constexpr int kMaxExtent = 16384;  // cull: snapped extent (1/16 px) at or above
 
 // Camera constants, derived on the host from the caller's intrinsics and
 // camera-to-world pose (double arithmetic, rounded once to binary32).
@@ -29,9 +34,9 @@ struct Camera {
   float delta, delta2;
 };
 
-// One object type after meshlet splitting.
+// One object type, split into chunks of <= 512 vertices / <= 1024 triangles.
 struct DevMesh {
-  int meshlet_begin, meshlet_count;
+  int chunk_begin, chunk_count;
   int n_tris, n_verts;
   float vol_r2, vol_zlo, vol_zhi;
   float lo[3], hi[3];  // object-frame bounding box
@@ -43,6 +48,7 @@ struct ObsIndex {
   // camera-frame points bucketed by a 3D grid of cell >= delta (Eq. (1) query)
   const float4* cam3;  // x, y, z, pixel index (int bits)
   const int* start3;   // n_cells3 + 1
+  const uint32_t* dil3;  // bit per cell: some point in its 3x3x3 neighbourhood
   float g3x, g3y, g3z, inv3;
   int n3x, n3y, n3z;
   // the same points bucketed by a 2D world (x, y) grid (V(O) candidates)
@@ -56,9 +62,12 @@ struct ObsIndex {
 struct Geometry {
   const DevMesh* meshes;
   int n_mesh;
-  const float4* ml_verts;   // meshlet vertex positions (object frame)
-  const int4* ml_info;      // vtx offset, n_vtx, tri offset, n_tri
-  const uint32_t* ml_tris;  // 3 x 8-bit local indices
+  const int4* chunk_info;     // vertex offset, n_vtx, triangle offset, n_tri
+  const uint32_t* chunk_tris; // 3 x 10-bit chunk-local vertex indices
+  const float4* chunk_verts;  // object-frame positions, chunk order (all meshes)
+  int n_cverts;               // length of chunk_verts
+  const float4* vtab;         // per yaw: M_yaw * v for every chunk vertex (n_yaw x n_cverts)
+  const float4* pose_off;     // per (ix, iy): b = R_cw (x, y, 0) + t_cw
   const float* xs;
   const float* ys;
   const float2* cs;
@@ -99,9 +108,12 @@ cudaError_t launch_grid2_keys(const float4* world_pts, int n, float g2x, float g
 cudaError_t launch_scatter(const int* keys, int n, int* cursor, const float4* a_in, float4* a_out,
                            const float4* b_in, float4* b_out, cudaStream_t s);
 cudaError_t launch_rays(const Camera& cam, float* rx, float* ry, cudaStream_t s);
-cudaError_t launch_pose_bbox(const Camera& cam, const Geometry& g, int4* bbox, int* max_wh, int* bad,
-                             cudaStream_t s);
-cudaError_t launch_render_parents(const Camera& cam, const Geometry& g, const Batch& b, int max_tris,
+cudaError_t launch_dilate3(const int* start3, int n3x, int n3y, int n3z, uint32_t* dil3, cudaStream_t s);
+cudaError_t launch_pose_tables(const Camera& cam, const Geometry& g, float* yaw_mats, float4* pose_off,
+                               float4* vtab, cudaStream_t s);
+cudaError_t launch_pose_bbox(const Camera& cam, const Geometry& g, const float* yaw_mats, int4* bbox,
+                             int* max_wh, int* bad, cudaStream_t s);
+cudaError_t launch_render_parents(const Camera& cam, const Geometry& g, const Batch& b, int max_chunks,
                                   unsigned long long* culled, cudaStream_t s);
 cudaError_t launch_uset(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
                         cudaStream_t s);

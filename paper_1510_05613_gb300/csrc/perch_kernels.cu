@@ -1,11 +1,13 @@
 // PERCH successor evaluation: device kernels for sm_103a.
 //
 // Arithmetic contract: every floating-point step on the evaluation path is a
-// single binary32 operation rounded to nearest-even (__fadd_rn, __fmul_rn,
-// __fdiv_rn, __frcp_rn, __int2float_rn, __float2int_rn); nothing is fused.
-// The library is also compiled with -fmad=false. Coverage and z-buffer
-// resolution are exact integer / order-independent min operations, so every
-// count is bit-exact with the CPU oracle.
+// single IEEE binary32 operation rounded to nearest-even (__fadd_rn,
+// __fmul_rn, __fmaf_rn, __frcp_rn, __int2float_rn, __float2int_rn); a fused
+// multiply-add appears only where written as ffma (one rounding, as IEEE 754
+// defines it) and the library is compiled with -fmad=false so nothing else is
+// contracted. Coverage and z-buffer resolution are exact integer /
+// order-independent min operations, so every count is bit-exact with the CPU
+// oracle, which writes out the same arithmetic.
 #include <climits>
 
 #include "perch_internal.h"
@@ -16,41 +18,39 @@ namespace perch {
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 __device__ __forceinline__ int ford(float f) {  // order-preserving float -> int
   int i = __float_as_int(f);
   return i >= 0 ? i : i ^ 0x7fffffff;
 }
 
+// squared camera-frame distance, d^2 = fma(dz, dz, fma(dy, dy, dx dx))
 __device__ __forceinline__ float dist2(float px, float py, float pz, float4 q) {
-  float dx = fsub(px, q.x), dy = fsub(py, q.y), dz = fsub(pz, q.z);
-  return fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz));
+  const float dx = fsub(px, q.x), dy = fsub(py, q.y), dz = fsub(pz, q.z);
+  return ffma(dz, dz, ffma(dy, dy, fmul(dx, dx)));
 }
 
 // V(O): the inscribed vertical cylinder of Sec. III-A at pose (ox, oy)
 __device__ __forceinline__ bool in_volume(float4 qw, float ox, float oy, float r2, float zlo, float zhi) {
-  float dx = fsub(qw.x, ox), dy = fsub(qw.y, oy);
-  float d2 = fadd(fmul(dx, dx), fmul(dy, dy));
+  const float dx = fsub(qw.x, ox), dy = fsub(qw.y, oy);
+  const float d2 = ffma(dy, dy, fmul(dx, dx));
   return d2 <= r2 && zlo <= qw.z && qw.z <= zhi;
 }
 
 struct Vtx {
-  int X, Y;   // snapped pixel coordinates, 1/16 px
+  int X, Y;   // snapped pixel coordinates, 1/16 px (absolute or tile-relative)
   float iz;   // 1 / z_c; negative marks a culled vertex
 };
 
-// object frame -> world (yaw, then table translation) -> camera -> pixel
-__device__ __forceinline__ Vtx transform_vertex(const Camera& c, float vx, float vy, float vz,
-                                                float x, float y, float cs, float sn) {
-  float xw = fadd(fsub(fmul(cs, vx), fmul(sn, vy)), x);
-  float yw = fadd(fadd(fmul(sn, vx), fmul(cs, vy)), y);
-  float zw = vz;
-  float xc = fadd(fadd(fadd(fmul(c.Rcw[0], xw), fmul(c.Rcw[1], yw)), fmul(c.Rcw[2], zw)), c.tcw[0]);
-  float yc = fadd(fadd(fadd(fmul(c.Rcw[3], xw), fmul(c.Rcw[4], yw)), fmul(c.Rcw[5], zw)), c.tcw[1]);
-  float zc = fadd(fadd(fadd(fmul(c.Rcw[6], xw), fmul(c.Rcw[7], yw)), fmul(c.Rcw[8], zw)), c.tcw[2]);
+// Camera-frame vertex (table entry M_yaw v plus the pose offset b) -> pixel:
+// 1/z = 1/c_z; u = fma(fx, c_x (1/z), cx); X = rint(16 u).
+__device__ __forceinline__ Vtx project_vertex(const Camera& c, float4 mv, float4 b) {
+  const float xc = fadd(mv.x, b.x), yc = fadd(mv.y, b.y), zc = fadd(mv.z, b.z);
   bool bad = !(zc > kNearZ);
-  float u = fadd(fmul(c.fx, __fdiv_rn(xc, zc)), c.cx);
-  float v = fadd(fmul(c.fy, __fdiv_rn(yc, zc)), c.cy);
+  const float iz = __frcp_rn(zc);
+  const float u = ffma(c.fx, fmul(xc, iz), c.cx);
+  const float v = ffma(c.fy, fmul(yc, iz), c.cy);
   bad = bad || !(fabsf(u) <= kGuard) || !(fabsf(v) <= kGuard);
   Vtx o;
   if (bad) {
@@ -59,25 +59,30 @@ __device__ __forceinline__ Vtx transform_vertex(const Camera& c, float vx, float
   }
   o.X = __float2int_rn(fmul(16.0f, u));
   o.Y = __float2int_rn(fmul(16.0f, v));
-  o.iz = __frcp_rn(zc);
+  o.iz = iz;
   return o;
 }
 
 __device__ __forceinline__ int floor16(int a) { return a >> 4; }
 __device__ __forceinline__ int ceil16(int a) { return -((-a) >> 4); }
 
-struct SmemSink {
-  uint32_t* tile;
-  __device__ __forceinline__ void operator()(int idx, uint32_t zbits) const { atomicMin(&tile[idx], zbits); }
-};
-struct GlobalSink {
-  uint32_t* z;
-  __device__ __forceinline__ void operator()(int idx, uint32_t zbits) const { atomicMin(&z[idx], zbits); }
-};
+// depth at a covered pixel centre: b_i = E_i / A, 1/z = fma(b2, 1/z2,
+// fma(b1, 1/z1, b0/z0)), z = 1/(1/z); returned as the float's bits
+__device__ __forceinline__ uint32_t pixel_depth_bits(int w0, int w1, int w2, float invA, float iz0, float iz1,
+                                                     float iz2) {
+  const float b0 = fmul(__int2float_rn(w0), invA);
+  const float b1 = fmul(__int2float_rn(w1), invA);
+  const float b2 = fmul(__int2float_rn(w2), invA);
+  const float iz = ffma(b2, iz2, ffma(b1, iz1, fmul(b0, iz0)));
+  return __float_as_uint(__frcp_rn(iz));
+}
 
-// Rasterise one triangle into a tile of tw x th pixels whose top-left pixel
-// is at (ox16 / 16, oy16 / 16): exact edge functions, top-left tie rule,
-// 1/z interpolation with screen-space barycentrics, min-z resolve.
+// edge ownership for the top-left tie rule (front faces in this orientation)
+__device__ __forceinline__ bool owns(int dx, int dy) { return dy > 0 || (dy == 0 && dx < 0); }
+
+// Rasterise one triangle (any size) into a tile of tw x th pixels whose
+// top-left pixel is at (ox16 / 16, oy16 / 16): exact edge functions, top-left
+// tie rule, min-z resolve through `sink`. Used for full-image parent renders.
 template <typename Sink>
 __device__ __forceinline__ void raster_tri(Vtx a, Vtx b, Vtx c, int ox16, int oy16, int tw, int th,
                                            unsigned& culled, Sink sink) {
@@ -100,9 +105,7 @@ __device__ __forceinline__ void raster_tri(Vtx a, Vtx b, Vtx c, int ox16, int oy
   const int px0 = max(ceil16(xmin), 0), px1 = min(floor16(xmax), tw - 1);
   const int py0 = max(ceil16(ymin), 0), py1 = min(floor16(ymax), th - 1);
   if (px0 > px1 || py0 > py1) return;
-  const bool own12 = (Y2 - Y1) > 0 || ((Y2 - Y1) == 0 && (X2 - X1) < 0);
-  const bool own20 = (Y0 - Y2) > 0 || ((Y0 - Y2) == 0 && (X0 - X2) < 0);
-  const bool own01 = (Y1 - Y0) > 0 || ((Y1 - Y0) == 0 && (X1 - X0) < 0);
+  const bool own12 = owns(X2 - X1, Y2 - Y1), own20 = owns(X0 - X2, Y0 - Y2), own01 = owns(X1 - X0, Y1 - Y0);
   const float invA = __frcp_rn(__int2float_rn(A));
   for (int py = py0; py <= py1; ++py) {
     const int Py = 16 * py;
@@ -113,12 +116,7 @@ __device__ __forceinline__ void raster_tri(Vtx a, Vtx b, Vtx c, int ox16, int oy
       const int w2 = (Y1 - Y0) * (Px - X0) - (X1 - X0) * (Py - Y0);
       const bool in = (w0 > 0 || (w0 == 0 && own12)) && (w1 > 0 || (w1 == 0 && own20)) &&
                       (w2 > 0 || (w2 == 0 && own01));
-      if (!in) continue;
-      const float b0 = fmul(__int2float_rn(w0), invA);
-      const float b1 = fmul(__int2float_rn(w1), invA);
-      const float b2 = fmul(__int2float_rn(w2), invA);
-      const float iz = fadd(fadd(fmul(b0, a.iz), fmul(b1, b.iz)), fmul(b2, c.iz));
-      sink(py * tw + px, __float_as_uint(__frcp_rn(iz)));
+      if (in) sink(py * tw + px, pixel_depth_bits(w0, w1, w2, invA, a.iz, b.iz, c.iz));
     }
   }
 }
@@ -134,6 +132,11 @@ __device__ __forceinline__ bool explained_by_obs(const ObsIndex& o, float px, fl
   const int ix = (int)floorf(fminf(fmaxf(fx, -2.0f), (float)o.n3x + 1.0f));
   const int iy = (int)floorf(fminf(fmaxf(fy, -2.0f), (float)o.n3y + 1.0f));
   const int iz = (int)floorf(fminf(fmaxf(fz, -2.0f), (float)o.n3z + 1.0f));
+  if (ix >= 0 && ix < o.n3x && iy >= 0 && iy < o.n3y && iz >= 0 && iz < o.n3z) {
+    // one bit says whether the 3x3x3 neighbourhood holds any point at all
+    const int c = (iz * o.n3y + iy) * o.n3x + ix;
+    if (!((__ldg(&o.dil3[c >> 5]) >> (c & 31)) & 1u)) return false;
+  }
   const int x0 = max(ix - 1, 0), x1 = min(ix + 1, o.n3x - 1);
   if (x0 > x1) return false;
   for (int dz = -1; dz <= 1; ++dz) {
@@ -314,9 +317,9 @@ __global__ void k_obs_write(const float* depth, Camera cam, const float* rx, con
   if (!ok) return;
   const int u = i % cam.W, v = i / cam.W;
   const float x = fmul(rx[u], d), y = fmul(ry[v], d), z = d;
-  const float xw = fadd(fadd(fadd(fmul(cam.Rwc[0], x), fmul(cam.Rwc[1], y)), fmul(cam.Rwc[2], z)), cam.twc[0]);
-  const float yw = fadd(fadd(fadd(fmul(cam.Rwc[3], x), fmul(cam.Rwc[4], y)), fmul(cam.Rwc[5], z)), cam.twc[1]);
-  const float zw = fadd(fadd(fadd(fmul(cam.Rwc[6], x), fmul(cam.Rwc[7], y)), fmul(cam.Rwc[8], z)), cam.twc[2]);
+  const float xw = fadd(ffma(cam.Rwc[2], z, ffma(cam.Rwc[1], y, fmul(cam.Rwc[0], x))), cam.twc[0]);
+  const float yw = fadd(ffma(cam.Rwc[5], z, ffma(cam.Rwc[4], y, fmul(cam.Rwc[3], x))), cam.twc[1]);
+  const float zw = fadd(ffma(cam.Rwc[8], z, ffma(cam.Rwc[7], y, fmul(cam.Rwc[6], x))), cam.twc[2]);
   cam_pts[off] = make_float4(x, y, z, __int_as_float(i));
   world_pts[off] = make_float4(xw, yw, zw, 0.0f);
   atomicMin(&bounds[0], ford(x)); atomicMin(&bounds[1], ford(y)); atomicMin(&bounds[2], ford(z));
@@ -407,9 +410,88 @@ cudaError_t launch_rays(const Camera& cam, float* rx, float* ry, cudaStream_t s)
   return cudaGetLastError();
 }
 
+// dilated occupancy of the 3D grid: bit c set iff a cell within one step of
+// c (in each axis) holds a point; dil3 must be zeroed first
+__global__ void k_dilate3(const int* start3, int nx, int ny, int nz, uint32_t* dil3) {
+  const long long c = blockIdx.x * 256LL + threadIdx.x;
+  const long long n = (long long)nx * ny * nz;
+  if (c >= n) return;
+  const int ix = (int)(c % nx), iy = (int)((c / nx) % ny), iz = (int)(c / ((long long)nx * ny));
+  bool any = false;
+  for (int dz = -1; dz <= 1 && !any; ++dz) {
+    const int z = iz + dz;
+    if (z < 0 || z >= nz) continue;
+    for (int dy = -1; dy <= 1 && !any; ++dy) {
+      const int y = iy + dy;
+      if (y < 0 || y >= ny) continue;
+      const int base = (z * ny + y) * nx;
+      const int x0 = max(ix - 1, 0), x1 = min(ix + 1, nx - 1);
+      any = start3[base + x1 + 1] > start3[base + x0];
+    }
+  }
+  if (any) atomicOr(&dil3[c >> 5], 1u << (c & 31));
+}
+
+cudaError_t launch_dilate3(const int* start3, int n3x, int n3y, int n3z, uint32_t* dil3, cudaStream_t s) {
+  const long long n = (long long)n3x * n3y * n3z;
+  if (n == 0) return cudaSuccess;
+  k_dilate3<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(start3, n3x, n3y, n3z, dil3);
+  return cudaGetLastError();
+}
+// Camera-frame pose tables: per yaw M = R_cw Rz(yaw), per (ix, iy)
+// b = R_cw (x, y, 0) + t_cw, in double from the binary32 inputs (products of
+// two floats are exact in double), rounded once.
+__global__ void k_pose_tables(Camera cam, Geometry g, float* yaw_mats, float4* pose_off) {
+  const int t = blockIdx.x * 256 + threadIdx.x;
+  if (t < g.n_yaw) {
+    const double cs = g.cs[t].x, sn = g.cs[t].y;
+    for (int r = 0; r < 3; ++r) {
+      const double r0 = cam.Rcw[r * 3 + 0], r1 = cam.Rcw[r * 3 + 1];
+      yaw_mats[t * 9 + r * 3 + 0] = __double2float_rn(__dadd_rn(__dmul_rn(r0, cs), __dmul_rn(r1, sn)));
+      yaw_mats[t * 9 + r * 3 + 1] = __double2float_rn(__dsub_rn(__dmul_rn(r1, cs), __dmul_rn(r0, sn)));
+      yaw_mats[t * 9 + r * 3 + 2] = cam.Rcw[r * 3 + 2];
+    }
+  }
+  if (t < g.nx * g.ny) {
+    const double x = g.xs[t / g.ny], y = g.ys[t % g.ny];
+    float b[3];
+    for (int r = 0; r < 3; ++r) {
+      const double r0 = cam.Rcw[r * 3 + 0], r1 = cam.Rcw[r * 3 + 1];
+      b[r] = __double2float_rn(__dadd_rn(__dadd_rn(__dmul_rn(r0, x), __dmul_rn(r1, y)), (double)cam.tcw[r]));
+    }
+    pose_off[t] = make_float4(b[0], b[1], b[2], 0.0f);
+  }
+}
+
+// per (yaw, chunk vertex): M v = fma(M_r2, vz, fma(M_r1, vy, M_r0 vx)) per row
+__global__ void k_vertex_table(Geometry g, const float* yaw_mats, float4* vtab) {
+  const long long t = blockIdx.x * 256LL + threadIdx.x;
+  if (t >= (long long)g.n_yaw * g.n_cverts) return;
+  const int k = (int)(t / g.n_cverts), j = (int)(t % g.n_cverts);
+  const float* M = yaw_mats + 9 * k;
+  const float4 v = g.chunk_verts[j];
+  float o[3];
+  for (int r = 0; r < 3; ++r) o[r] = ffma(M[r * 3 + 2], v.z, ffma(M[r * 3 + 1], v.y, fmul(M[r * 3 + 0], v.x)));
+  vtab[t] = make_float4(o[0], o[1], o[2], 0.0f);
+}
+
+cudaError_t launch_pose_tables(const Camera& cam, const Geometry& g, float* yaw_mats, float4* pose_off,
+                               float4* vtab, cudaStream_t s) {
+  const int n = g.n_yaw > g.nx * g.ny ? g.n_yaw : g.nx * g.ny;
+  k_pose_tables<<<(n + 255) / 256, 256, 0, s>>>(cam, g, yaw_mats, pose_off);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long nv = (long long)g.n_yaw * g.n_cverts;
+  if (nv == 0) return cudaSuccess;
+  k_vertex_table<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(g, yaw_mats, vtab);
+  return cudaGetLastError();
+}
+
 // conservative screen box of every (mesh, pose) from the 8 corners of the
-// mesh's bounding box (a convex hull of its vertices), plus one pixel
-__global__ void k_pose_bbox(Camera cam, Geometry g, int4* bbox, int* max_wh, int* bad_any) {
+// mesh's bounding box (a convex hull of its vertices), plus one pixel;
+// bad: 1 = a corner at or behind the near plane or far off-screen,
+// 2 = the unclipped box is wider or taller than kMaxObjectPixels
+__global__ void k_pose_bbox(Camera cam, Geometry g, const float* yaw_mats, int4* bbox, int* max_wh, int* bad_any) {
   const long long n = (long long)g.n_mesh * g.nx * g.ny * g.n_yaw;
   const long long t = blockIdx.x * 256LL + threadIdx.x;
   if (t >= n) return;
@@ -418,82 +500,90 @@ __global__ void k_pose_bbox(Camera cam, Geometry g, int4* bbox, int* max_wh, int
   const int ix = (int)((t / ((long long)g.n_yaw * g.ny)) % g.nx);
   const int m = (int)(t / ((long long)g.n_yaw * g.ny * g.nx));
   const DevMesh dm = g.meshes[m];
-  const float2 cs = g.cs[iyaw];
-  const float x = g.xs[ix], y = g.ys[iy];
+  const float* M = yaw_mats + 9 * iyaw;
+  const float4 b = g.pose_off[ix * g.ny + iy];
   float umin = 1e30f, umax = -1e30f, vmin = 1e30f, vmax = -1e30f;
   bool bad = false;
   for (int k = 0; k < 8; ++k) {
     const float vx = (k & 1) ? dm.hi[0] : dm.lo[0];
     const float vy = (k & 2) ? dm.hi[1] : dm.lo[1];
     const float vz = (k & 4) ? dm.hi[2] : dm.lo[2];
-    const float xw = fadd(fsub(fmul(cs.x, vx), fmul(cs.y, vy)), x);
-    const float yw = fadd(fadd(fmul(cs.y, vx), fmul(cs.x, vy)), y);
-    const float xc = cam.Rcw[0] * xw + cam.Rcw[1] * yw + cam.Rcw[2] * vz + cam.tcw[0];
-    const float yc = cam.Rcw[3] * xw + cam.Rcw[4] * yw + cam.Rcw[5] * vz + cam.tcw[1];
-    const float zc = cam.Rcw[6] * xw + cam.Rcw[7] * yw + cam.Rcw[8] * vz + cam.tcw[2];
+    const float xc = M[0] * vx + M[1] * vy + M[2] * vz + b.x;
+    const float yc = M[3] * vx + M[4] * vy + M[5] * vz + b.y;
+    const float zc = M[6] * vx + M[7] * vy + M[8] * vz + b.z;
     if (!(zc > kNearZ)) { bad = true; break; }
     const float u = cam.fx * (xc / zc) + cam.cx, v = cam.fy * (yc / zc) + cam.cy;
     umin = fminf(umin, u); umax = fmaxf(umax, u);
     vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
   }
-  int4 b;
+  int4 r;
   if (bad || !(umax - umin < 4096.0f) || !(vmax - vmin < 4096.0f)) {
-    b = make_int4(0, 0, cam.W, cam.H);
+    r = make_int4(0, 0, cam.W, cam.H);
     atomicOr(bad_any, 1);
   } else {
+    if (umax - umin > (float)(kMaxObjectPixels - 4) || vmax - vmin > (float)(kMaxObjectPixels - 4))
+      atomicOr(bad_any, 2);
     int x0 = (int)floorf(fmaxf(umin, -8.0f)) - 1, x1 = (int)ceilf(fminf(umax, (float)cam.W + 8.0f)) + 1;
     int y0 = (int)floorf(fmaxf(vmin, -8.0f)) - 1, y1 = (int)ceilf(fminf(vmax, (float)cam.H + 8.0f)) + 1;
     x0 = max(x0, 0); y0 = max(y0, 0);
     x1 = min(x1, cam.W - 1); y1 = min(y1, cam.H - 1);
-    if (x0 > x1 || y0 > y1) b = make_int4(0, 0, 0, 0);
-    else b = make_int4(x0, y0, x1 - x0 + 1, y1 - y0 + 1);
+    if (x0 > x1 || y0 > y1) r = make_int4(0, 0, 0, 0);
+    else r = make_int4(x0, y0, x1 - x0 + 1, y1 - y0 + 1);
   }
-  bbox[t] = b;
-  atomicMax(&max_wh[0], b.z);
-  atomicMax(&max_wh[1], b.w);
+  bbox[t] = r;
+  atomicMax(&max_wh[0], r.z);
+  atomicMax(&max_wh[1], r.w);
 }
 
-cudaError_t launch_pose_bbox(const Camera& cam, const Geometry& g, int4* bbox, int* max_wh, int* bad,
-                             cudaStream_t s) {
+cudaError_t launch_pose_bbox(const Camera& cam, const Geometry& g, const float* yaw_mats, int4* bbox, int* max_wh,
+                             int* bad, cudaStream_t s) {
   const long long n = (long long)g.n_mesh * g.nx * g.ny * g.n_yaw;
   if (n == 0) return cudaSuccess;
-  k_pose_bbox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cam, g, bbox, max_wh, bad);
+  k_pose_bbox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cam, g, yaw_mats, bbox, max_wh, bad);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ parent prep
+struct GlobalSink {
+  uint32_t* z;
+  __device__ __forceinline__ void operator()(int idx, uint32_t zbits) const { atomicMin(&z[idx], zbits); }
+};
+
+__device__ __forceinline__ bool obj_ok(const Geometry& g, const perch_obj& o) {
+  return o.mesh < g.n_mesh && o.ix >= 0 && o.ix < g.nx && o.iy >= 0 && o.iy < g.ny && o.iyaw < g.n_yaw;
+}
+
 // z-buffer render of every parent's objects (R_j) into its own full image.
-// Block = one meshlet of one (parent, object) pair.
-__global__ void __launch_bounds__(64) k_render_parents(Camera cam, Geometry g, Batch b,
-                                                       unsigned long long* culled_total) {
-  __shared__ int sX[kMeshletMaxVerts], sY[kMeshletMaxVerts];
-  __shared__ float sZ[kMeshletMaxVerts];
+// Block = one chunk of one (parent, object) pair.
+__global__ void __launch_bounds__(256) k_render_parents(Camera cam, Geometry g, Batch b,
+                                                        unsigned long long* culled_total) {
+  __shared__ int2 sXY[kChunkMaxVerts];
+  __shared__ float sIZ[kChunkMaxVerts];
   const int item = blockIdx.y;
   const int p = item / b.parent_stride, k = item % b.parent_stride;
   if (p >= b.n_par) return;
   const int plen = b.parent_len[p];
   if (k >= plen || plen > b.parent_stride) return;
   const perch_obj o = b.parents[(long long)p * b.parent_stride + k];
-  if (o.mesh >= g.n_mesh || o.ix < 0 || o.ix >= g.nx || o.iy < 0 || o.iy >= g.ny || o.iyaw >= g.n_yaw) return;
+  if (!obj_ok(g, o)) return;
   const DevMesh m = g.meshes[o.mesh];
-  if ((int)blockIdx.x >= m.meshlet_count) return;
-  const int4 info = g.ml_info[m.meshlet_begin + blockIdx.x];
-  const float x = g.xs[o.ix], y = g.ys[o.iy];
-  const float2 cs = g.cs[o.iyaw];
-  const int t = threadIdx.x;
-  if (t < info.y) {
-    const float4 v = g.ml_verts[info.x + t];
-    const Vtx r = transform_vertex(cam, v.x, v.y, v.z, x, y, cs.x, cs.y);
-    sX[t] = r.X; sY[t] = r.Y; sZ[t] = r.iz;
+  if ((int)blockIdx.x >= m.chunk_count) return;
+  const int4 ci = g.chunk_info[m.chunk_begin + blockIdx.x];
+  const float4 bo = g.pose_off[o.ix * g.ny + o.iy];
+  const float4* V = g.vtab + (size_t)o.iyaw * g.n_cverts;
+  for (int v = threadIdx.x; v < ci.y; v += 256) {
+    const Vtx r = project_vertex(cam, V[ci.x + v], bo);
+    sXY[v] = make_int2(r.X, r.Y);
+    sIZ[v] = r.iz;
   }
   __syncthreads();
   unsigned culled = 0;
-  if (t < info.w) {
-    const uint32_t pk = g.ml_tris[info.z + t];
-    const int i0 = pk & 255, i1 = (pk >> 8) & 255, i2 = (pk >> 16) & 255;
-    uint32_t* z = reinterpret_cast<uint32_t*>(b.parent_z) + (size_t)p * cam.W * cam.H;
-    raster_tri(Vtx{sX[i0], sY[i0], sZ[i0]}, Vtx{sX[i1], sY[i1], sZ[i1]}, Vtx{sX[i2], sY[i2], sZ[i2]}, 0, 0,
-               cam.W, cam.H, culled, GlobalSink{z});
+  uint32_t* z = reinterpret_cast<uint32_t*>(b.parent_z) + (size_t)p * cam.W * cam.H;
+  for (int t = threadIdx.x; t < ci.w; t += 256) {
+    const uint32_t pk = g.chunk_tris[ci.z + t];
+    const int i0 = pk & 1023, i1 = (pk >> 10) & 1023, i2 = (pk >> 20) & 1023;
+    raster_tri(Vtx{sXY[i0].x, sXY[i0].y, sIZ[i0]}, Vtx{sXY[i1].x, sXY[i1].y, sIZ[i1]},
+               Vtx{sXY[i2].x, sXY[i2].y, sIZ[i2]}, 0, 0, cam.W, cam.H, culled, GlobalSink{z});
   }
   if (culled_total) {
     const int c = __syncthreads_count(culled != 0);
@@ -501,13 +591,13 @@ __global__ void __launch_bounds__(64) k_render_parents(Camera cam, Geometry g, B
   }
 }
 
-cudaError_t launch_render_parents(const Camera& cam, const Geometry& g, const Batch& b, int max_meshlets,
+cudaError_t launch_render_parents(const Camera& cam, const Geometry& g, const Batch& b, int max_chunks,
                                   unsigned long long* culled, cudaStream_t s) {
-  if (b.n_par == 0 || b.parent_stride == 0 || max_meshlets == 0) return cudaSuccess;
+  if (b.n_par == 0 || b.parent_stride == 0 || max_chunks == 0) return cudaSuccess;
   const long long items = (long long)b.n_par * b.parent_stride;
   if (items > 65535) return cudaErrorInvalidValue;
-  dim3 grid(max_meshlets, (unsigned)items);
-  k_render_parents<<<grid, 64, 0, s>>>(cam, g, b, culled);
+  dim3 grid(max_chunks, (unsigned)items);
+  k_render_parents<<<grid, 256, 0, s>>>(cam, g, b, culled);
   return cudaGetLastError();
 }
 
@@ -523,7 +613,7 @@ __global__ void k_uset(Camera cam, Geometry g, ObsIndex obs, Batch b) {
   const float4 qw = obs.world2[k];
   for (int j = 0; j < plen; ++j) {
     const perch_obj o = b.parents[(long long)p * b.parent_stride + j];
-    if (o.mesh >= g.n_mesh || o.ix < 0 || o.ix >= g.nx || o.iy < 0 || o.iy >= g.ny || o.iyaw >= g.n_yaw) return;
+    if (!obj_ok(g, o)) return;
     const DevMesh m = g.meshes[o.mesh];
     if (in_volume(qw, g.xs[o.ix], g.ys[o.iy], m.vol_r2, m.vol_zlo, m.vol_zhi)) return;
   }
@@ -558,8 +648,8 @@ cudaError_t launch_uset(const Camera& cam, const Geometry& g, const ObsIndex& ob
 
 // ------------------------------------------------------------- evaluation
 size_t eval_smem_bytes(int tile_w, int tile_h) {
-  return (size_t)tile_w * tile_h * 4 + (size_t)(tile_w + tile_h) * 4 +
-         (size_t)kEvalWarps * kMeshletMaxVerts * 12;
+  return (size_t)kChunkMaxVerts * 16 + (size_t)kChunkMaxTris * 4 + (size_t)kChunkMaxVerts * 8 +
+         (size_t)kBigQueue * 8 + (size_t)tile_w * tile_h * 4 + (size_t)(tile_w + tile_h) * 4;
 }
 
 bool eval_tile_fits(int device, int tile_w, int tile_h) {
@@ -568,19 +658,120 @@ bool eval_tile_fits(int device, int tile_w, int tile_h) {
   return eval_smem_bytes(tile_w, tile_h) + 256 <= (size_t)optin;  // 256: static shared memory of k_eval
 }
 
+// ---- bulk asynchronous copies (TMA, 1D) into shared memory, with mbarriers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// one thread: announce `bytes` of transfer and start the copy gmem -> smem
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase with the given parity. Each poll may suspend the thread
+// in hardware (up to 0.1 ms) instead of spinning; the wait gives up after
+// kWaitSpins polls or 2 s, whichever comes first, and then returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  for (int i = 0; i < kWaitSpins; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(100000u)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > 2000000000ull) break;
+  }
+  return false;
+}
+
+__device__ __forceinline__ uint32_t pack_xy(int X, int Y) { return (uint32_t)(X & 0xffff) | ((uint32_t)Y << 16); }
+__device__ __forceinline__ int2 unpack_xy(uint32_t p) { return make_int2((int)(p << 16) >> 16, (int)p >> 16); }
+
+// Is the pixel centre with edge values (w0, w1, w2) inside the triangle
+// under the top-left rule? Exact zeros (rare) look at the edge directions.
+__device__ __forceinline__ bool covers(int w0, int w1, int w2, int2 a, int2 b, int2 c) {
+  if ((w0 | w1 | w2) < 0) return false;  // strictly outside some edge
+  if (w0 == 0 && !owns(c.x - b.x, c.y - b.y)) return false;
+  if (w1 == 0 && !owns(a.x - c.x, a.y - c.y)) return false;
+  if (w2 == 0 && !owns(b.x - a.x, b.y - a.y)) return false;
+  return true;
+}
+
+// 1/z at a covered pixel centre: b_i = E_i (1/A), 1/z = fma(b2, 1/z2,
+// fma(b1, 1/z1, b0/z0)). The tile keeps the largest 1/z (the nearest
+// surface; z = 1/(1/z) is taken once per pixel afterwards).
+__device__ __forceinline__ uint32_t pixel_iz_bits(int w0, int w1, int w2, float invA, float iz0, float iz1, float iz2) {
+  const float b0 = fmul(__int2float_rn(w0), invA);
+  const float b1 = fmul(__int2float_rn(w1), invA);
+  const float b2 = fmul(__int2float_rn(w2), invA);
+  return __float_as_uint(ffma(b2, iz2, ffma(b1, iz1, fmul(b0, iz0))));
+}
+
+// Test the candidate pixel centres [px0, px1] x [py0, py1] of a front-facing
+// triangle (tile-relative 1/16-px vertices) and max its 1/z into the tile.
+__device__ __forceinline__ void raster_box(int2 a, int2 b, int2 c, int A, int px0, int px1, int py0, int py1,
+                                           const float* sIZ, int i0, int i1, int i2, uint32_t* tile, int tw) {
+  float invA = 0.0f;
+  for (int py = py0; py <= py1; ++py) {
+    const int Py = 16 * py;
+    for (int px = px0; px <= px1; ++px) {
+      const int Px = 16 * px;
+      const int w0 = (c.y - b.y) * (Px - b.x) - (c.x - b.x) * (Py - b.y);
+      const int w1 = (a.y - c.y) * (Px - c.x) - (a.x - c.x) * (Py - c.y);
+      const int w2 = (b.y - a.y) * (Px - a.x) - (b.x - a.x) * (Py - a.y);
+      if (!covers(w0, w1, w2, a, b, c)) continue;
+      if (invA == 0.0f) invA = __frcp_rn(__int2float_rn(A));
+      atomicMax(&tile[py * tw + px], pixel_iz_bits(w0, w1, w2, invA, sIZ[i0], sIZ[i1], sIZ[i2]));
+    }
+  }
+}
+
 // One CTA per hypothesis: render the new object into a shared-memory z tile
 // covering its screen box, test it against the parent render (Eq. (3)), and
 // count dJ_r, dJ_o and residual(K) (Sec. IV-A, Eq. (4)).
+//
+// Rendering walks the mesh in chunks of <= 512 vertices / 1024 triangles. A
+// chunk's camera-frame vertex table slice (M_yaw v) and its triangle list are
+// brought into shared memory by bulk asynchronous copies (TMA); the copy of
+// chunk c+1's vertices is issued as soon as chunk c's vertices are projected,
+// and the copy of its triangles as soon as chunk c's triangles are set up, so
+// the loads overlap the rasterisation. Each thread sets up triangles; a
+// front-facing triangle whose box holds at most kInlinePixels pixel centres
+// is rasterised by its thread, a larger one is queued and its pixel centres
+// are split across a warp. Edge arithmetic stays in int32: every object's
+// screen box is at most kMaxObjectPixels wide (checked at set-up), so
+// tile-relative coordinates (kept as int16 pairs) and all edge-function
+// values are far below 2^31.
 __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, ObsIndex obs, Batch b) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_cnt[6];  // viol, n_new, culled, djr, djo, resid
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_bar[2];  // [0]: vertex slice, [1]: triangle list
+  __shared__ int s_cnt[6];                    // viol, n_new, culled, djr, djo, resid
+  __shared__ int s_qn;
   const long long h = blockIdx.x;
   if (h >= b.n_hyp) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const perch_obj o = b.hyp[h];
   const int pid = b.hyp_parent[h];
-  bool badidx = pid < 0 || pid >= b.n_par || o.mesh >= g.n_mesh || o.ix < 0 || o.ix >= g.nx || o.iy < 0 ||
-                o.iy >= g.ny || o.iyaw >= g.n_yaw;
+  bool badidx = pid < 0 || pid >= b.n_par || !obj_ok(g, o);
   const int plen = badidx ? 0 : b.parent_len[pid];
   badidx = badidx || plen < 0 || plen > b.parent_stride;
   const int4 bb = badidx ? make_int4(0, 0, 0, 0)
@@ -592,44 +783,149 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
     }
     return;
   }
-  uint32_t* tile = reinterpret_cast<uint32_t*>(smem);
+  float4* vbuf = reinterpret_cast<float4*>(smem);
+  uint32_t* tbuf = reinterpret_cast<uint32_t*>(vbuf + kChunkMaxVerts);
+  uint32_t* sXY = tbuf + kChunkMaxTris;
+  float* sIZ = reinterpret_cast<float*>(sXY + kChunkMaxVerts);
+  uint32_t* queue = reinterpret_cast<uint32_t*>(sIZ + kChunkMaxVerts);  // (triangle, box) pairs
+  uint32_t* tile = queue + 2 * kBigQueue;
   float* rxs = reinterpret_cast<float*>(tile + b.tile_w * b.tile_h);
   float* rys = rxs + b.tile_w;
-  int* vX = reinterpret_cast<int*>(rys + b.tile_h);
-  int* vY = vX + kEvalWarps * kMeshletMaxVerts;
-  float* vZ = reinterpret_cast<float*>(vY + kEvalWarps * kMeshletMaxVerts);
-  const int npx = bb.z * bb.w;
-  for (int i = tid; i < npx; i += kEvalThreads) tile[i] = kInfBits;
-  for (int i = tid; i < bb.z; i += kEvalThreads) rxs[i] = g.rx[bb.x + i];
-  for (int i = tid; i < bb.w; i += kEvalThreads) rys[i] = g.ry[bb.y + i];
-  if (tid < 6) s_cnt[tid] = 0;
-  __syncthreads();
+  const int tw = bb.z, th = bb.w;
 
-  // ---- render the new object (warp per meshlet)
   const DevMesh m = g.meshes[o.mesh];
+  const float4* V = g.vtab + (size_t)o.iyaw * g.n_cverts;
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (tid == 0) {  // first chunk
+    const int4 ci = g.chunk_info[m.chunk_begin];
+    bulk_load(vbuf, V + ci.x, (uint32_t)ci.y * 16u, &s_bar[0]);
+    bulk_load(tbuf, g.chunk_tris + ci.z, (uint32_t)((ci.w + 3) & ~3) * 4u, &s_bar[1]);
+  }
+  for (int ly = warp; ly < th; ly += kEvalWarps)
+    for (int lx = lane; lx < tw; lx += 32) tile[ly * tw + lx] = 0u;  // 1/z = 0: empty
+  for (int i = tid; i < tw; i += kEvalThreads) rxs[i] = g.rx[bb.x + i];
+  for (int i = tid; i < th; i += kEvalThreads) rys[i] = g.ry[bb.y + i];
+  if (tid < 6) s_cnt[tid] = 0;
+
+  // ---- render the new object
   const float ox = g.xs[o.ix], oy = g.ys[o.iy];
-  const float2 cs = g.cs[o.iyaw];
-  int* wX = vX + warp * kMeshletMaxVerts;
-  int* wY = vY + warp * kMeshletMaxVerts;
-  float* wZ = vZ + warp * kMeshletMaxVerts;
+  const float4 bo = g.pose_off[o.ix * g.ny + o.iy];
   const int ox16 = 16 * bb.x, oy16 = 16 * bb.y;
   unsigned culled = 0;
-  SmemSink sink{tile};
-  for (int mi = warp; mi < m.meshlet_count; mi += kEvalWarps) {
-    const int4 info = g.ml_info[m.meshlet_begin + mi];
-    for (int v = lane; v < info.y; v += 32) {
-      const float4 p = g.ml_verts[info.x + v];
-      const Vtx r = transform_vertex(cam, p.x, p.y, p.z, ox, oy, cs.x, cs.y);
-      wX[v] = r.X; wY[v] = r.Y; wZ[v] = r.iz;
+  uint32_t pv = 0, pt = 0;                  // parity of the next phase of each barrier
+  bool v_pending = true, t_pending = true;  // a copy in flight on that barrier
+  bool timed_out = false;
+  for (int c = 0; c < m.chunk_count; ++c) {
+    const int4 ci = g.chunk_info[m.chunk_begin + c];
+    // vertices: wait for the slice, project, then reuse its buffer for c+1
+    const bool vok = mbar_wait(&s_bar[0], pv);
+    int bad = 0;
+    if (vok) {
+      for (int v = tid; v < ci.y; v += kEvalThreads) {
+        const Vtx r = project_vertex(cam, vbuf[v], bo);
+        sXY[v] = pack_xy(r.X - ox16, r.Y - oy16);
+        sIZ[v] = r.iz;
+        bad |= r.iz < 0.0f;
+      }
     }
-    __syncwarp();
-    for (int t = lane; t < info.w; t += 32) {
-      const uint32_t pk = g.ml_tris[info.z + t];
-      const int i0 = pk & 255, i1 = (pk >> 8) & 255, i2 = (pk >> 16) & 255;
-      raster_tri(Vtx{wX[i0], wY[i0], wZ[i0]}, Vtx{wX[i1], wY[i1], wZ[i1]}, Vtx{wX[i2], wY[i2], wZ[i2]}, ox16,
-                 oy16, bb.z, bb.w, culled, sink);
+    if (tid == 0) s_qn = 0;
+    const int vflags = __syncthreads_or(bad | (vok ? 0 : 2));
+    if (vflags & 2) {
+      timed_out = true;
+      break;
     }
-    __syncwarp();
+    pv ^= 1u;
+    v_pending = false;
+    if (c + 1 < m.chunk_count) {
+      if (tid == 0) {
+        const int4 cn = g.chunk_info[m.chunk_begin + c + 1];
+        bulk_load(vbuf, V + cn.x, (uint32_t)cn.y * 16u, &s_bar[0]);
+      }
+      v_pending = true;
+    }
+    // triangles
+    const bool tok = mbar_wait(&s_bar[1], pt);
+    if (tok) {
+      for (int t = tid; t < ci.w; t += kEvalThreads) {
+        const uint32_t pk = tbuf[t];
+        const int i0 = pk & 1023, i1 = (pk >> 10) & 1023, i2 = (pk >> 20) & 1023;
+        if ((vflags & 1) && (sIZ[i0] < 0.0f || sIZ[i1] < 0.0f || sIZ[i2] < 0.0f)) {
+          culled = 1u;
+          continue;
+        }
+        const int2 va = unpack_xy(sXY[i0]), vb = unpack_xy(sXY[i1]), vc = unpack_xy(sXY[i2]);
+        const int A = (vb.y - va.y) * (vc.x - va.x) - (vb.x - va.x) * (vc.y - va.y);
+        if (A <= 0) continue;  // back-facing or degenerate
+        const int px0 = max(ceil16(min(va.x, min(vb.x, vc.x))), 0);
+        const int px1 = min(floor16(max(va.x, max(vb.x, vc.x))), tw - 1);
+        const int py0 = max(ceil16(min(va.y, min(vb.y, vc.y))), 0);
+        const int py1 = min(floor16(max(va.y, max(vb.y, vc.y))), th - 1);
+        if (px0 > px1 || py0 > py1) continue;
+        if ((px1 - px0 + 1) * (py1 - py0 + 1) > kInlinePixels && px1 - px0 < 64 && py1 - py0 < 64) {
+          const int slot = atomicAdd(&s_qn, 1);
+          if (slot < kBigQueue) {  // (triangle, box): x0 10 bits, y0 10 bits, w-1 and h-1 6 bits each
+            queue[2 * slot] = pk;
+            queue[2 * slot + 1] = (uint32_t)px0 | ((uint32_t)py0 << 10) | ((uint32_t)(px1 - px0) << 20) |
+                                  ((uint32_t)(py1 - py0) << 26);
+            continue;
+          }
+        }
+        raster_box(va, vb, vc, A, px0, px1, py0, py1, sIZ, i0, i1, i2, tile, tw);
+      }
+    }
+    if (__syncthreads_or(tok ? 0 : 1)) {
+      timed_out = true;
+      break;
+    }
+    pt ^= 1u;
+    t_pending = false;
+    if (c + 1 < m.chunk_count) {
+      if (tid == 0) {
+        const int4 cn = g.chunk_info[m.chunk_begin + c + 1];
+        bulk_load(tbuf, g.chunk_tris + cn.z, (uint32_t)((cn.w + 3) & ~3) * 4u, &s_bar[1]);
+      }
+      t_pending = true;
+    }
+    // larger triangles: one warp per triangle, its pixel centres across lanes
+    const int nq = min(s_qn, kBigQueue);
+    for (int e = warp; e < nq; e += kEvalWarps) {
+      const uint32_t pk = queue[2 * e], box = queue[2 * e + 1];
+      const int i0 = pk & 1023, i1 = (pk >> 10) & 1023, i2 = (pk >> 20) & 1023;
+      const int2 va = unpack_xy(sXY[i0]), vb = unpack_xy(sXY[i1]), vc = unpack_xy(sXY[i2]);
+      const int px0 = box & 1023, py0 = (box >> 10) & 1023, bw = (int)((box >> 20) & 63) + 1;
+      const int n = bw * ((int)(box >> 26) + 1);
+      // k / bw = umulhi(k, ceil(2^32 / bw)) for k, bw < 2^16 (bw = 1 would overflow the magic)
+      const uint32_t magic = 0xffffffffu / (uint32_t)bw + 1u;
+      float invA = 0.0f;
+      for (int k = lane; k < n; k += 32) {
+        const int ry = bw == 1 ? k : (int)__umulhi((uint32_t)k, magic);
+        const int px = px0 + k - ry * bw, py = py0 + ry;
+        const int Px = 16 * px, Py = 16 * py;
+        const int w0 = (vc.y - vb.y) * (Px - vb.x) - (vc.x - vb.x) * (Py - vb.y);
+        const int w1 = (va.y - vc.y) * (Px - vc.x) - (va.x - vc.x) * (Py - vc.y);
+        const int w2 = (vb.y - va.y) * (Px - va.x) - (vb.x - va.x) * (Py - va.y);
+        if (!covers(w0, w1, w2, va, vb, vc)) continue;
+        if (invA == 0.0f) invA = __frcp_rn(__int2float_rn(w0 + w1 + w2));
+        atomicMax(&tile[py * tw + px], pixel_iz_bits(w0, w1, w2, invA, sIZ[i0], sIZ[i1], sIZ[i2]));
+      }
+    }
+    __syncthreads();  // the next chunk reuses sXY, sIZ and the queue
+  }
+  if (timed_out) {
+    // a copy never completed: let any copy still in flight land (bounded),
+    // then report the failure instead of a cost
+    if (v_pending) mbar_wait(&s_bar[0], pv);
+    if (t_pending) mbar_wait(&s_bar[1], pt);
+    if (tid == 0) {
+      perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout};
+      b.out[h] = r;
+    }
+    return;
   }
   if (culled) s_cnt[2] = 1;
   __syncthreads();
@@ -637,19 +933,26 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
   // ---- monotone test against the parent render and dR (Eq. (3))
   int viol = 0, nnew = 0;
   const float* zp = plen > 0 ? b.parent_z + (size_t)pid * cam.W * cam.H : nullptr;
-  for (int i = tid; i < npx; i += kEvalThreads) {
-    const uint32_t zb = tile[i];
-    if (zb == kInfBits) continue;
-    if (zp) {
-      const int ly = i / bb.z, lx = i - ly * bb.z;
-      const float pz = __ldg(&zp[(size_t)(bb.y + ly) * cam.W + bb.x + lx]);
-      if (__float_as_uint(pz) != kInfBits) {
-        if (__uint_as_float(zb) < pz) viol++;
-        tile[i] = kInfBits;  // hidden by (or hiding) the parent: not in dR
+  for (int ly = warp; ly < th; ly += kEvalWarps) {
+    const float* prow = zp ? zp + (size_t)(bb.y + ly) * cam.W + bb.x : nullptr;
+    for (int lx = lane; lx < tw; lx += 32) {
+      const uint32_t izb = tile[ly * tw + lx];
+      if (izb == 0u) {
+        tile[ly * tw + lx] = kInfBits;
         continue;
       }
+      const float z = __frcp_rn(__uint_as_float(izb));
+      if (prow) {
+        const float pz = __ldg(&prow[lx]);
+        if (__float_as_uint(pz) != kInfBits) {
+          if (z < pz) viol++;
+          tile[ly * tw + lx] = kInfBits;  // hidden by (or hiding) the parent: not in dR
+          continue;
+        }
+      }
+      tile[ly * tw + lx] = __float_as_uint(z);
+      nnew++;
     }
-    nnew++;
   }
   viol = warp_sum(viol);
   nnew = warp_sum(nnew);
@@ -669,12 +972,14 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
 
   // ---- dJ_r: dR points with no observed point within delta
   int djr = 0;
-  for (int i = tid; i < npx; i += kEvalThreads) {
-    const uint32_t zb = tile[i];
-    if (zb == kInfBits) continue;
-    const int ly = i / bb.z, lx = i - ly * bb.z;
-    const float z = __uint_as_float(zb);
-    if (!explained_by_obs(obs, fmul(rxs[lx], z), fmul(rys[ly], z), z, cam.delta2)) djr++;
+  for (int ly = warp; ly < th; ly += kEvalWarps) {
+    const float ry = rys[ly];
+    for (int lx = lane; lx < tw; lx += 32) {
+      const uint32_t zb = tile[ly * tw + lx];
+      if (zb == kInfBits) continue;
+      const float z = __uint_as_float(zb);
+      if (!explained_by_obs(obs, fmul(rxs[lx], z), fmul(ry, z), z, cam.delta2)) djr++;
+    }
   }
 
   // ---- dJ_o: observed points inside V(O) with no dR point within delta

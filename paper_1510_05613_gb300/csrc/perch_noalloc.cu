@@ -106,7 +106,7 @@ extern "C" int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* pa
   b.tile_w = ctx->tile_w;
   b.tile_h = ctx->tile_h;
   const Geometry g = ctx->geometry();
-  e = launch_render_parents(ctx->cam, g, b, ctx->max_meshlets, nullptr, ctx->stream);
+  e = launch_render_parents(ctx->cam, g, b, ctx->max_chunks, nullptr, ctx->stream);
   if (e != cudaSuccess) return ctx->cuda(e, "render parents");
   e = launch_uset(ctx->cam, g, ctx->obs, b, ctx->stream);
   if (e != cudaSuccess) return ctx->cuda(e, "residual sets");
