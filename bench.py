@@ -39,6 +39,14 @@ UNIT = "hypotheses/s"
 L2_FLUSH_BYTES = 256 << 20
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
+WORKLOADS = {
+    "c2": "640x480 fx=525, 3 procedural meshes (box/cylinder/superquadric, ~10k triangles), 50x50x16 pose grid, "
+          "sigma 3 mm, 5% dropout, delta 1 cm; one expansion batch = root + 1-object + 2-object parents, "
+          "240000 hypotheses",
+    "c3": "640x480 fx=525, heavy occlusion: 5 of 8 procedural meshes of 2k-50k triangles, one object >70% occluded, "
+          "50x50x16 pose grid, sigma 3 mm, 5% dropout, delta 1 cm; one expansion batch = the children of a "
+          "2-object parent, 120000 hypotheses",
+}
 
 
 def c2_batch(wl):
@@ -55,6 +63,16 @@ def c2_batch(wl):
     hp = np.concatenate([g[0] for g in groups])
     hyps = np.concatenate([g[1] for g in groups])
     return parents, hp, hyps
+
+
+def c3_batch(wl):
+    """(parents, hyp_parent, hyps) of one expansion of the heavy-occlusion
+    workload: the children of the first two ground-truth objects, i.e. every
+    pose of the three remaining (uneven) meshes, 120k hypotheses."""
+    parents = [wl.gt[:2]]
+    rem = sorted(set(_remaining(wl.mesh_multiset, parents[0])))
+    h = synth.all_hypotheses(wl.grid, rem)
+    return parents, np.zeros(len(h), np.int32), h
 
 
 def _remaining(multiset, parent):
@@ -224,8 +242,8 @@ def run_ours(args):
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
 
-    wl = synth.workload_c2()
-    parents, hp, hyps = c2_batch(wl)
+    wl = synth.workload_c3() if args.workload == "c3" else synth.workload_c2()
+    parents, hp, hyps = c3_batch(wl) if args.workload == "c3" else c2_batch(wl)
     if args.max_hyps and args.max_hyps < len(hyps):  # reduced batch (profiling case)
         keep = np.linspace(0, len(hyps) - 1, args.max_hyps).astype(np.int64)
         hp, hyps = hp[keep], hyps[keep]
@@ -241,8 +259,14 @@ def run_ours(args):
     tout = torch.zeros(n_hyp * 6, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
-    def step():
-        p.perch_eval_successors_dev(tP, stride, tplen, thp, th, wl.K, tout)
+    if args.threads:
+        p.perch_set_threads(args.threads)
+        widths = [args.threads] * len(wl.meshes)
+    else:
+        widths = p.perch_autotune(args.tune_sample) if not args.no_autotune else None
+
+    def step():  # the whole evaluation sequence as one CUDA-graph launch
+        p.perch_eval_graph(tP, stride, tplen, thp, th, wl.K, tout)
 
     for _ in range(max(args.warmup, 3)):
         flush.fill_(1)
@@ -260,10 +284,16 @@ def run_ours(args):
             evs[k][0].record(stream)
             step()
             evs[k][1].record(stream)
-            a, b = p.perch_last_timing()
-            prep_ms.append(a)
-            eval_ms.append(b)
         torch.cuda.synchronize()
+    # the same sequence without the graph, to time its phases with the
+    # library's events (parent prep; the per-mesh evaluation launches)
+    for k in range(max(3, args.steps // 2)):
+        flush.fill_(k)
+        p.perch_eval_successors_dev(tP, stride, tplen, thp, th, wl.K, tout)
+        a, b = p.perch_last_timing()
+        prep_ms.append(a)
+        eval_ms.append(b)
+    torch.cuda.synchronize()
     step_ms = [s.elapsed_time(e) for s, e in evs]
     total_s = sum(step_ms) / 1e3
     if ws > 1:
@@ -327,9 +357,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "640x480 fx=525, 3 procedural meshes (box/cylinder/superquadric, ~10k triangles), "
-                                   "50x50x16 pose grid, sigma 3 mm, 5% dropout, delta 1 cm; one expansion batch = "
-                                   "root + 1-object + 2-object parents, 240000 hypotheses",
+            "config": {"workload": WORKLOADS[args.workload],
                        "hypotheses_per_step": n_hyp, "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "alu", "kernel": "k_eval", "achieved": achieved, "peak": peak_tops,
@@ -339,7 +367,8 @@ def run_ours(args):
                          "peak_from": f"{n_sm} SMs x {FP32_LANES_PER_SM} lanes x {sm_max:.0f} MHz "
                                       "(sm_max_mhz of MEASURED_PEAKS.json)"},
             "e2e": e2e, "e2e_matches_device_records": consistent,
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": (8 + len(wl.meshes)) * args.steps,
+            "launch": {"graph": True, "persistent_per_mesh": True, "autotuned_threads": widths},
             "clocks": cl,
             "time_to_optimum": search,
             "cpu_baseline": base,
@@ -363,7 +392,12 @@ def main():
     ap.add_argument("--no-search", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--threads", type=int, default=0, help="fix the CTA width (128/256/512) instead of autotuning")
+    ap.add_argument("--tune-sample", type=int, default=8192, help="hypotheses per mesh the autotuner times")
     ap.add_argument("--max-hyps", type=int, default=0, help="evenly subsample the batch (profiling case)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+                    help="c2: 640x480 three ~10k-triangle meshes (the headline); c3: heavy occlusion, 2k-50k triangles")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

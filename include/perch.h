@@ -149,8 +149,9 @@ int perch_eval_successors_dev(perch_ctx* ctx, const perch_obj* parents, int32_t 
  * loop that must not stall on cudaMalloc/cudaFree, or a process whose GPU
  * memory is fixed by its own pool after start-up). They set the context up
  * first; the set-up calls do allocate.
- * Limit: n_par * (4*W*H + 4*max(|I|,1) + 4) bytes (each part rounded up to
- * 256) must not exceed 8 MiB, else PERCH_E_RANGE and nothing is enqueued.
+ * Limit: 4*n_par*W*H + 4*n_par*max(|I|,1) + 4*n_par + 8 bytes (each of the
+ * three parts rounded up to 256) must not exceed 8 MiB, else PERCH_E_RANGE
+ * and nothing is enqueued.
  * The first call on a device looks up the array's device address (once per
  * device); make that first call before any stream capture. Every call shares
  * the array and re-initialises it, so calls whose work overlaps on the GPU
@@ -193,6 +194,33 @@ typedef struct {
 } perch_result;
 
 int perch_search(perch_ctx* ctx, const perch_search_params* params, perch_result* result);
+
+/* Launch tuning (not in the paper). The evaluation runs one persistent
+ * launch per mesh with a shared-memory tile sized for that mesh; this call
+ * times each CTA width the kernel is built for (128, 256, 512 threads) on
+ * max(n_sample, 32 x SM count) hypotheses of each mesh (a fixed spread of its poses, children of
+ * the empty scene), keeps the fastest per mesh for all later evaluations on
+ * this context, and writes them to threads_out[n_mesh] (may be NULL). Results
+ * are cached in the process per (device, triangle count, vertex count, tile
+ * size). Without this call every mesh uses 256 threads. Requires an
+ * observation (PERCH_E_STATE). */
+int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads_out);
+
+/* Set the CTA width (128, 256 or 512) used for one mesh (mesh = -1: all
+ * meshes), overriding the default 256 or an autotuned choice. */
+int perch_set_threads(perch_ctx* ctx, int32_t mesh, int32_t threads);
+
+/* Same work and arguments as perch_eval_successors_dev (device pointers), run
+ * as a CUDA graph: the first call for a given argument set (and after any
+ * change of meshes, pose grid or observation) runs the evaluation once and
+ * captures it; later calls only launch the graph on the context's stream.
+ * out_host (may be NULL) must be page-locked host memory; when given, the
+ * graph also copies the n_hyp records there. The caller may rewrite the
+ * contents of the device buffers between calls. perch_last_timing does not
+ * cover graph launches. */
+int perch_eval_graph(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride, const int32_t* parent_len,
+                     int32_t n_par, const int32_t* hyp_parent, const perch_obj* hyp, int64_t n_hyp,
+                     int32_t K_total, perch_cost* out, perch_cost* out_host);
 
 /* Device time of the most recent evaluation (perch_eval_successors or
  * perch_eval_successors_dev), measured with CUDA events recorded on the

@@ -107,22 +107,34 @@ int perch_ctx::ensure_tables() {
   CK(vtab.ensure(sizeof(float4) * (size_t)n_yaw * n_cverts), "alloc vertex tables");
   CK(pose_bbox.ensure(sizeof(int4) * n), "alloc pose boxes");
   CK(scratch_small.ensure(64), "alloc");
-  int* d = scratch_small.as<int>();
-  CK(cudaMemsetAsync(d, 0, 3 * sizeof(int), stream), "memset");
+  DevBuf& wh = g_cursor;  // per-mesh tile sizes (scratch until the first batch)
+  CK(wh.ensure(sizeof(int) * (2 * (size_t)n_mesh + 1)), "alloc");
+  int* d = wh.as<int>();
+  CK(cudaMemsetAsync(d, 0, sizeof(int) * (2 * (size_t)n_mesh + 1), stream), "memset");
   const Geometry g = geometry();
   CK(launch_pose_tables(cam, g, yaw_mats.as<float>(), pose_off.as<float4>(), vtab.as<float4>(), stream),
      "pose tables kernel");
-  CK(launch_pose_bbox(cam, g, yaw_mats.as<float>(), pose_bbox.as<int4>(), d, d + 2, stream), "pose_bbox kernel");
-  int h[3];
-  CK(cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, stream), "copy pose boxes");
+  CK(launch_pose_bbox(cam, g, yaw_mats.as<float>(), pose_bbox.as<int4>(), d, d + 2 * n_mesh, stream),
+     "pose_bbox kernel");
+  std::vector<int> h(2 * (size_t)n_mesh + 1);
+  CK(cudaMemcpyAsync(h.data(), d, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, stream), "copy pose boxes");
   CK(cudaStreamSynchronize(stream), "pose tables sync");
-  if (h[2] & 1) return fail(PERCH_E_RANGE, "a (mesh, pose) projects behind the near plane or far off-screen");
-  if (h[2] & 2)
+  const int bad = h[2 * n_mesh];
+  if (bad & 1) return fail(PERCH_E_RANGE, "a (mesh, pose) projects behind the near plane or far off-screen");
+  if (bad & 2)
     return fail(PERCH_E_RANGE, "an object's screen box exceeds %d pixels (too close to the camera)", kMaxObjectPixels);
-  if (!eval_tile_fits(device, std::max(h[0], 1), std::max(h[1], 1)))
-    return fail(PERCH_E_RANGE, "object screen box %dx%d does not fit in shared memory", h[0], h[1]);
-  tile_w = std::max(h[0], 1);
-  tile_h = std::max(h[1], 1);
+  mesh_tile_w.assign(n_mesh, 1);
+  mesh_tile_h.assign(n_mesh, 1);
+  tile_w = tile_h = 1;
+  for (int m = 0; m < n_mesh; ++m) {
+    mesh_tile_w[m] = std::max(h[2 * m], 1);
+    mesh_tile_h[m] = std::max(h[2 * m + 1], 1);
+    tile_w = std::max(tile_w, mesh_tile_w[m]);
+    tile_h = std::max(tile_h, mesh_tile_h[m]);
+  }
+  if (!eval_tile_fits(device, tile_w, tile_h))
+    return fail(PERCH_E_RANGE, "object screen box %dx%d does not fit in shared memory", tile_w, tile_h);
+  if ((int)mesh_threads.size() != n_mesh) mesh_threads.assign(n_mesh, 256);
   tables_valid = true;
   return PERCH_OK;
 }
@@ -142,6 +154,10 @@ int perch_create(perch_ctx** out, int device, void* cuda_stream) {
   perch_ctx* ctx = new (std::nothrow) perch_ctx();
   if (!ctx) return PERCH_E_OOM;
   ctx->device = device;
+  if (cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete ctx;
+    return PERCH_E_CUDA;
+  }
   if (cuda_stream) {
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->own_stream = false;
@@ -163,6 +179,7 @@ int perch_destroy(perch_ctx* ctx) {
   for (DevBuf* b : ctx->all_buffers()) b->release();
   for (int k = 0; k < 3; ++k)
     if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return PERCH_OK;
@@ -268,6 +285,7 @@ int perch_load_meshes(perch_ctx* ctx, const perch_mesh* meshes, int32_t n) {
   ctx->max_tris = max_tris;
   ctx->n_cverts = (int)verts.size();
   ctx->tables_valid = false;
+  ctx->tables_version++;
   return ctx->ensure_tables();
 }
 
@@ -289,6 +307,7 @@ int perch_set_pose_grid(perch_ctx* ctx, const float* xs, int32_t nx, const float
   ctx->ny = ny;
   ctx->n_yaw = n_yaw;
   ctx->tables_valid = false;
+  ctx->tables_version++;
   return ctx->ensure_tables();
 }
 
@@ -325,6 +344,7 @@ int perch_set_observation(perch_ctx* ctx, const float* depth, int32_t W, int32_t
   c.delta2 = (float)((double)delta * (double)delta);
   ctx->has_cam = true;
   ctx->tables_valid = false;
+  ctx->tables_version++;
 
   const int npx = W * H;
   const int nblk = (npx + 255) / 256;
@@ -481,15 +501,35 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
   const Geometry g = geometry();
   if (!ev[0])
     for (int k = 0; k < 3; ++k) CK(cudaEventCreate(&ev[k]), "cudaEventCreate");
-  CK(cudaEventRecord(ev[0], stream), "event");
+  if (!capturing) CK(cudaEventRecord(ev[0], stream), "event");
   CK(launch_fill_u32(parent_z.as<uint32_t>(), kInfBits, (long long)npx * n_par, stream), "clear parents");
   CK(cudaMemsetAsync(uset_count.p, 0, 4 * (size_t)std::max(n_par, 1), stream), "memset");
   CK(launch_render_parents(cam, g, b, max_chunks, nullptr, stream), "render parents");
   CK(launch_uset(cam, g, obs, b, stream), "U sets");
-  CK(cudaEventRecord(ev[1], stream), "event");
-  CK(launch_eval(cam, g, obs, b, stream), "eval kernel");
-  CK(cudaEventRecord(ev[2], stream), "event");
-  timed = true;
+  if (!capturing) CK(cudaEventRecord(ev[1], stream), "event");
+  // group by mesh; one persistent launch per mesh with its own tile and CTA width
+  CK(g_hist.ensure(sizeof(int) * (size_t)n_mesh), "alloc");
+  CK(g_off.ensure(sizeof(int) * ((size_t)n_mesh + 1)), "alloc");
+  CK(g_cursor.ensure(sizeof(int) * (2 * (size_t)n_mesh + 1)), "alloc");
+  CK(g_next.ensure(sizeof(int) * (size_t)n_mesh), "alloc");
+  CK(g_order.ensure(sizeof(int) * (size_t)std::max(n_hyp, 1LL)), "alloc");
+  CK(scan_tmp.ensure(sizeof(int) * ((size_t)n_mesh / 1024 + 2)), "alloc");
+  CK(launch_group_by_mesh(d_hyp, n_hyp, n_mesh, g_hist.as<int>(), g_off.as<int>(), g_cursor.as<int>(),
+                          g_order.as<int>(), scan_tmp.as<int>(), stream),
+     "group by mesh");
+  CK(cudaMemsetAsync(g_next.p, 0, sizeof(int) * (size_t)n_mesh, stream), "memset");
+  for (int m = 0; m < n_mesh; ++m) {
+    Batch bm = b;
+    bm.tile_w = mesh_tile_w[m];
+    bm.tile_h = mesh_tile_h[m];
+    CK(launch_eval_group(cam, g, obs, bm, g_order.as<int>(), g_off.as<int>() + m, g_hist.as<int>() + m,
+                         g_next.as<int>() + m, n_hyp, mesh_threads[m], sm_count, stream),
+       "eval kernel");
+  }
+  if (!capturing) {
+    CK(cudaEventRecord(ev[2], stream), "event");
+    timed = true;
+  }
   return PERCH_OK;
 }
 

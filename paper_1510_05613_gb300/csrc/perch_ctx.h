@@ -17,6 +17,22 @@ struct DevBuf {
   }
 };
 
+// Arguments a captured evaluation graph was made for (all 8-byte fields: no
+// padding, so keys compare with memcmp).
+struct GraphKey {
+  const void* parents;
+  long long stride;
+  const void* plen;
+  long long n_par;
+  const void* hp;
+  const void* hyp;
+  long long n_hyp;
+  long long K;
+  const void* out;
+  const void* out_host;
+  long long version;
+};
+
 struct perch_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -42,11 +58,22 @@ struct perch_ctx {
   // camera-frame pose tables and the screen box of every (mesh, pose)
   DevBuf yaw_mats, pose_off, vtab, pose_bbox;
   bool tables_valid = false;
-  int tile_w = 0, tile_h = 0;
+  int tile_w = 0, tile_h = 0;             // largest over all meshes
+  std::vector<int> mesh_tile_w, mesh_tile_h;  // per mesh
+  std::vector<int> mesh_threads;          // CTA width per mesh (autotuned; 256 by default)
+  int sm_count = 0;
 
   // per-batch buffers
   DevBuf parent_z, uset, uset_count;
+  DevBuf g_hist, g_off, g_cursor, g_order, g_next;  // hypotheses grouped by mesh
   DevBuf b_parents, b_plen, b_hp, b_hyp, b_out;
+
+  // captured evaluation graph (perch_eval_graph); `version` changes whenever
+  // the meshes, the pose grid or the observation change
+  cudaGraphExec_t graph_exec = nullptr;
+  GraphKey graph_key{};
+  bool capturing = false;
+  long long tables_version = 0;
 
   // events around the phases of the last evaluation
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -56,7 +83,7 @@ struct perch_ctx {
     return {&meshes, &chunk_verts, &chunk_info, &chunk_tris, &yaw_mats, &pose_off, &vtab, &xs, &ys, &cs, &depth, &rx, &ry, &blockcnt, &blockoff,
             &scan_tmp, &cam_pts, &world_pts, &keys, &counts, &cursor, &start3, &start2, &obs3, &world2, &cam2, &dil3,
             &scratch_small, &pose_bbox, &parent_z, &uset, &uset_count, &b_parents, &b_plen, &b_hp, &b_hyp,
-            &b_out};
+            &b_out, &g_hist, &g_off, &g_cursor, &g_order, &g_next};
   }
 
   int fail(int code, const char* fmt, ...);

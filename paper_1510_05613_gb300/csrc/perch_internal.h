@@ -117,8 +117,11 @@ cudaError_t launch_render_parents(const Camera& cam, const Geometry& g, const Ba
                                   unsigned long long* culled, cudaStream_t s);
 cudaError_t launch_uset(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
                         cudaStream_t s);
-cudaError_t launch_eval(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
-                        cudaStream_t s);
+cudaError_t launch_group_by_mesh(const perch_obj* hyp, long long n, int n_mesh, int* hist, int* offsets,
+                                 int* cursor, int* order, int* scan_tmp, cudaStream_t s);
+cudaError_t launch_eval_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                              const int* order, const int* offset, const int* count, int* next, long long max_items,
+                              int threads, int sm_count, cudaStream_t s);
 size_t eval_smem_bytes(int tile_w, int tile_h);
 bool eval_tile_fits(int device, int tile_w, int tile_h);
 

@@ -531,8 +531,8 @@ __global__ void k_pose_bbox(Camera cam, Geometry g, const float* yaw_mats, int4*
     else r = make_int4(x0, y0, x1 - x0 + 1, y1 - y0 + 1);
   }
   bbox[t] = r;
-  atomicMax(&max_wh[0], r.z);
-  atomicMax(&max_wh[1], r.w);
+  atomicMax(&max_wh[2 * m], r.z);  // per-mesh tile
+  atomicMax(&max_wh[2 * m + 1], r.w);
 }
 
 cudaError_t launch_pose_bbox(const Camera& cam, const Geometry& g, const float* yaw_mats, int4* bbox, int* max_wh,
@@ -761,14 +761,27 @@ __device__ __forceinline__ void raster_box(int2 a, int2 b, int2 c, int A, int px
 // screen box is at most kMaxObjectPixels wide (checked at set-up), so
 // tile-relative coordinates (kept as int16 pairs) and all edge-function
 // values are far below 2^31.
-__global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, ObsIndex obs, Batch b) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t s_bar[2];  // [0]: vertex slice, [1]: triangle list
-  __shared__ int s_cnt[6];                    // viol, n_new, culled, djr, djo, resid
-  __shared__ int s_qn;
-  const long long h = blockIdx.x;
-  if (h >= b.n_hyp) return;
+struct EvalShared {
+  uint64_t* bar;   // [0]: vertex slice, [1]: triangle list
+  int* cnt;        // viol, n_new, culled, djr, djo, resid
+  int* qn;         // queued larger triangles
+  unsigned char* dyn;
+  uint32_t pv, pt;  // parity of the next phase of each barrier
+};
+
+// Evaluate hypothesis h with a CTA of NT threads. The CTA's two mbarriers
+// persist across hypotheses (their phase parities are in sh). Returns false
+// if a bounded wait gave up (the record then carries kFlagTimeout and the
+// barriers must not be used again).
+template <int NT>
+__device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                         EvalShared& sh) {
+  constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint64_t* s_bar = sh.bar;
+  int* s_cnt = sh.cnt;
+  int& s_qn = *sh.qn;
+  unsigned char* smem = sh.dyn;
   const perch_obj o = b.hyp[h];
   const int pid = b.hyp_parent[h];
   bool badidx = pid < 0 || pid >= b.n_par || !obj_ok(g, o);
@@ -781,7 +794,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
       perch_cost r = {0, 0, 0, 0, 0, kFlagBadIndex};
       b.out[h] = r;
     }
-    return;
+    return true;
   }
   float4* vbuf = reinterpret_cast<float4*>(smem);
   uint32_t* tbuf = reinterpret_cast<uint32_t*>(vbuf + kChunkMaxVerts);
@@ -795,21 +808,15 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
 
   const DevMesh m = g.meshes[o.mesh];
   const float4* V = g.vtab + (size_t)o.iyaw * g.n_cverts;
-  if (tid == 0) {
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
-    fence_barrier_init();
-  }
-  __syncthreads();
   if (tid == 0) {  // first chunk
     const int4 ci = g.chunk_info[m.chunk_begin];
     bulk_load(vbuf, V + ci.x, (uint32_t)ci.y * 16u, &s_bar[0]);
     bulk_load(tbuf, g.chunk_tris + ci.z, (uint32_t)((ci.w + 3) & ~3) * 4u, &s_bar[1]);
   }
-  for (int ly = warp; ly < th; ly += kEvalWarps)
+  for (int ly = warp; ly < th; ly += NW)
     for (int lx = lane; lx < tw; lx += 32) tile[ly * tw + lx] = 0u;  // 1/z = 0: empty
-  for (int i = tid; i < tw; i += kEvalThreads) rxs[i] = g.rx[bb.x + i];
-  for (int i = tid; i < th; i += kEvalThreads) rys[i] = g.ry[bb.y + i];
+  for (int i = tid; i < tw; i += NT) rxs[i] = g.rx[bb.x + i];
+  for (int i = tid; i < th; i += NT) rys[i] = g.ry[bb.y + i];
   if (tid < 6) s_cnt[tid] = 0;
 
   // ---- render the new object
@@ -817,7 +824,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
   const float4 bo = g.pose_off[o.ix * g.ny + o.iy];
   const int ox16 = 16 * bb.x, oy16 = 16 * bb.y;
   unsigned culled = 0;
-  uint32_t pv = 0, pt = 0;                  // parity of the next phase of each barrier
+  uint32_t& pv = sh.pv;
+  uint32_t& pt = sh.pt;
   bool v_pending = true, t_pending = true;  // a copy in flight on that barrier
   bool timed_out = false;
   for (int c = 0; c < m.chunk_count; ++c) {
@@ -826,7 +834,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
     const bool vok = mbar_wait(&s_bar[0], pv);
     int bad = 0;
     if (vok) {
-      for (int v = tid; v < ci.y; v += kEvalThreads) {
+      for (int v = tid; v < ci.y; v += NT) {
         const Vtx r = project_vertex(cam, vbuf[v], bo);
         sXY[v] = pack_xy(r.X - ox16, r.Y - oy16);
         sIZ[v] = r.iz;
@@ -851,7 +859,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
     // triangles
     const bool tok = mbar_wait(&s_bar[1], pt);
     if (tok) {
-      for (int t = tid; t < ci.w; t += kEvalThreads) {
+      for (int t = tid; t < ci.w; t += NT) {
         const uint32_t pk = tbuf[t];
         const int i0 = pk & 1023, i1 = (pk >> 10) & 1023, i2 = (pk >> 20) & 1023;
         if ((vflags & 1) && (sIZ[i0] < 0.0f || sIZ[i1] < 0.0f || sIZ[i2] < 0.0f)) {
@@ -893,7 +901,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
     }
     // larger triangles: one warp per triangle, its pixel centres across lanes
     const int nq = min(s_qn, kBigQueue);
-    for (int e = warp; e < nq; e += kEvalWarps) {
+    for (int e = warp; e < nq; e += NW) {
       const uint32_t pk = queue[2 * e], box = queue[2 * e + 1];
       const int i0 = pk & 1023, i1 = (pk >> 10) & 1023, i2 = (pk >> 20) & 1023;
       const int2 va = unpack_xy(sXY[i0]), vb = unpack_xy(sXY[i1]), vc = unpack_xy(sXY[i2]);
@@ -925,7 +933,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
       perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout};
       b.out[h] = r;
     }
-    return;
+    return false;
   }
   if (culled) s_cnt[2] = 1;
   __syncthreads();
@@ -933,7 +941,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
   // ---- monotone test against the parent render and dR (Eq. (3))
   int viol = 0, nnew = 0;
   const float* zp = plen > 0 ? b.parent_z + (size_t)pid * cam.W * cam.H : nullptr;
-  for (int ly = warp; ly < th; ly += kEvalWarps) {
+  for (int ly = warp; ly < th; ly += NW) {
     const float* prow = zp ? zp + (size_t)(bb.y + ly) * cam.W + bb.x : nullptr;
     for (int lx = lane; lx < tw; lx += 32) {
       const uint32_t izb = tile[ly * tw + lx];
@@ -967,12 +975,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
       perch_cost r = {0, 0, 0, s_cnt[0], s_cnt[1], flags | PERCH_FLAG_INVALID};
       b.out[h] = r;
     }
-    return;
+    __syncthreads();  // s_cnt is reset by the next hypothesis
+    return true;
   }
 
   // ---- dJ_r: dR points with no observed point within delta
   int djr = 0;
-  for (int ly = warp; ly < th; ly += kEvalWarps) {
+  for (int ly = warp; ly < th; ly += NW) {
     const float ry = rys[ly];
     for (int lx = lane; lx < tw; lx += 32) {
       const uint32_t zb = tile[ly * tw + lx];
@@ -993,7 +1002,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
     if (cx0 <= cx1) {
       for (int cy = cy0; cy <= cy1; ++cy) {
         const int s = obs.start2[cy * obs.n2x + cx0], e = obs.start2[cy * obs.n2x + cx1 + 1];
-        for (int k = s + tid; k < e; k += kEvalThreads) {
+        for (int k = s + tid; k < e; k += NT) {
           const float4 qw = obs.world2[k];
           if (!in_volume(qw, ox, oy, m.vol_r2, m.vol_zlo, m.vol_zhi)) continue;
           if (!explained_by_tile(cam, obs.cam2[k], tile, rxs, rys, bb)) djo++;
@@ -1007,7 +1016,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
   if (plen + 1 == b.K_total) {
     const int nu = b.uset_count[pid];
     const int* U = b.uset + (size_t)pid * b.uset_stride;
-    for (int k = tid; k < nu; k += kEvalThreads) {
+    for (int k = tid; k < nu; k += NT) {
       const int qi = U[k];
       if (in_volume(obs.world2[qi], ox, oy, m.vol_r2, m.vol_zlo, m.vol_zhi)) continue;
       if (explained_by_tile(cam, obs.cam2[qi], tile, rxs, rys, bb)) continue;
@@ -1027,17 +1036,104 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(Camera cam, Geometry g, O
     perch_cost r = {s_cnt[3], s_cnt[4], s_cnt[5], 0, s_cnt[1], flags};
     b.out[h] = r;
   }
+  __syncthreads();  // s_cnt and the tile are reused by the next hypothesis
+  return true;
 }
 
-cudaError_t launch_eval(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
-                        cudaStream_t s) {
-  if (b.n_hyp == 0) return cudaSuccess;
-  if (b.n_hyp > 0x7fffffffLL) return cudaErrorInvalidValue;
-  const size_t smem = eval_smem_bytes(b.tile_w, b.tile_h);
-  cudaError_t e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_eval<<<(unsigned)b.n_hyp, kEvalThreads, smem, s>>>(cam, g, obs, b);
+// A group of hypotheses evaluated by one persistent launch: items
+// order[offset .. offset + count) (order == nullptr: hypotheses 0 .. count-1),
+// claimed one at a time from the device counter `next`.
+struct EvalGroup {
+  const int* order;
+  const int* offset;  // device scalar
+  const int* count;   // device scalar
+  int* next;          // device counter, zero before the launch
+};
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_eval(Camera cam, Geometry g, ObsIndex obs, Batch b, EvalGroup grp) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int s_cnt[6];
+  __shared__ int s_qn;
+  __shared__ int s_item;
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  EvalShared sh{s_bar, s_cnt, &s_qn, smem, 0u, 0u};
+  const int count = *grp.count, offset = grp.order ? *grp.offset : 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(grp.next, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= count) break;
+    const long long h = grp.order ? grp.order[offset + item] : item;
+    if (!eval_one<NT>(h, cam, g, obs, b, sh)) break;
+  }
+}
+
+// group hypotheses by mesh: hist -> offsets (exclusive scan) -> order
+__global__ void k_group_hist(const perch_obj* hyp, long long n, int n_mesh, int* hist) {
+  const long long h = blockIdx.x * 256LL + threadIdx.x;
+  if (h >= n) return;
+  const int m = min((int)hyp[h].mesh, n_mesh - 1);
+  atomicAdd(&hist[m], 1);
+}
+
+__global__ void k_group_scatter(const perch_obj* hyp, long long n, int n_mesh, int* cursor, int* order) {
+  const long long h = blockIdx.x * 256LL + threadIdx.x;
+  if (h >= n) return;
+  const int m = min((int)hyp[h].mesh, n_mesh - 1);
+  order[atomicAdd(&cursor[m], 1)] = (int)h;
+}
+
+cudaError_t launch_group_by_mesh(const perch_obj* hyp, long long n, int n_mesh, int* hist, int* offsets,
+                                 int* cursor, int* order, int* scan_tmp, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * n_mesh, s);
+  if (e != cudaSuccess || n == 0) return e;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  k_group_hist<<<blocks, 256, 0, s>>>(hyp, n, n_mesh, hist);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_exclusive_scan(hist, offsets, n_mesh, scan_tmp, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(cursor, offsets, sizeof(int) * n_mesh, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return e;
+  k_group_scatter<<<blocks, 256, 0, s>>>(hyp, n, n_mesh, cursor, order);
   return cudaGetLastError();
+}
+
+template <int NT>
+static cudaError_t launch_group_t(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                                  const EvalGroup& grp, long long max_items, int sm_count, cudaStream_t s) {
+  const size_t smem = eval_smem_bytes(b.tile_w, b.tile_h);
+  cudaError_t e = cudaFuncSetAttribute(k_eval<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval<NT>, NT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long grid = (long long)per_sm * sm_count;
+  if (grid > max_items) grid = max_items;
+  if (grid < 1) grid = 1;
+  k_eval<NT><<<(unsigned)grid, NT, smem, s>>>(cam, g, obs, b, grp);
+  return cudaGetLastError();
+}
+
+// One persistent launch for one group of hypotheses with CTAs of `threads`
+// (128, 256 or 512) and the group's tile (b.tile_w x b.tile_h).
+cudaError_t launch_eval_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                              const int* order, const int* offset, const int* count, int* next, long long max_items,
+                              int threads, int sm_count, cudaStream_t s) {
+  if (max_items <= 0) return cudaSuccess;
+  EvalGroup grp{order, offset, count, next};
+  switch (threads) {
+    case 128: return launch_group_t<128>(cam, g, obs, b, grp, max_items, sm_count, s);
+    case 512: return launch_group_t<512>(cam, g, obs, b, grp, max_items, sm_count, s);
+    default: return launch_group_t<256>(cam, g, obs, b, grp, max_items, sm_count, s);
+  }
 }
 
 }  // namespace perch

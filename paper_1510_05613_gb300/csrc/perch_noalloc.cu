@@ -69,7 +69,7 @@ extern "C" int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* pa
   const size_t n_obs = (size_t)(ctx->obs.n > 0 ? ctx->obs.n : 1);
   const size_t z_bytes = round256(4 * npx * (size_t)n_par);
   const size_t u_bytes = round256(4 * n_obs * (size_t)n_par);
-  const size_t c_bytes = round256(4 * (size_t)n_par);
+  const size_t c_bytes = round256(4 * (size_t)n_par + 8);  // residual-set counters, item count and cursor
   if (z_bytes + u_bytes + c_bytes > kNoallocBytes)
     return ctx->fail(PERCH_E_RANGE,
                      "noalloc scratch: %d parents at %dx%d with %d observed points need %zu bytes, limit %zu",
@@ -83,6 +83,8 @@ extern "C" int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* pa
   float* parent_z = reinterpret_cast<float*>(p);
   int* uset = reinterpret_cast<int*>(p + z_bytes);
   int* uset_count = reinterpret_cast<int*>(p + z_bytes + u_bytes);
+  int* item_count = uset_count + n_par;  // the evaluation's work counter pair
+  int* item_next = item_count + 1;
 
   e = launch_fill_u32(reinterpret_cast<uint32_t*>(parent_z), kInfBits, (long long)npx * n_par, ctx->stream);
   if (e != cudaSuccess) return ctx->cuda(e, "clear parents");
@@ -110,7 +112,12 @@ extern "C" int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* pa
   if (e != cudaSuccess) return ctx->cuda(e, "render parents");
   e = launch_uset(ctx->cam, g, ctx->obs, b, ctx->stream);
   if (e != cudaSuccess) return ctx->cuda(e, "residual sets");
-  e = launch_eval(ctx->cam, g, ctx->obs, b, ctx->stream);
+  e = launch_fill_u32(reinterpret_cast<uint32_t*>(item_count), (uint32_t)n_hyp, 1, ctx->stream);
+  if (e != cudaSuccess) return ctx->cuda(e, "item count");
+  e = launch_fill_u32(reinterpret_cast<uint32_t*>(item_next), 0u, 1, ctx->stream);
+  if (e != cudaSuccess) return ctx->cuda(e, "item cursor");
+  e = launch_eval_group(ctx->cam, g, ctx->obs, b, nullptr, nullptr, item_count, item_next, n_hyp, 256,
+                        ctx->sm_count, ctx->stream);
   if (e != cudaSuccess) return ctx->cuda(e, "eval kernel");
   return PERCH_OK;
 }

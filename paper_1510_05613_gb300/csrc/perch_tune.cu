@@ -1,0 +1,183 @@
+// Launch-configuration autotuner and CUDA-graph capture of the evaluation.
+//
+// The evaluation runs one persistent launch per mesh (its own shared-memory
+// tile, sized by the mesh's largest screen box over the pose grid). The
+// autotuner times the CTA widths the kernel is compiled for on a sample of
+// each mesh's hypotheses and keeps the fastest per mesh; results are cached
+// in the process by (triangle count, vertex count, tile), so contexts with the
+// same meshes and camera reuse them. The graph entry point captures the whole
+// evaluation sequence (parent z-buffers, residual sets, grouping, the
+// per-mesh launches and optionally the record download) once per argument set
+// and replays it.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "perch_ctx.h"
+#include "perch_internal.h"
+
+using namespace perch;
+
+namespace {
+
+using TuneKey = std::tuple<int, int, int, int, int>;  // device, tris, verts, tile_w, tile_h
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune_cache;
+
+constexpr int kWidths[3] = {128, 256, 512};
+
+}  // namespace
+
+#define CK(expr, what)                 \
+  do {                                 \
+    int rc_ = ctx->cuda((expr), what); \
+    if (rc_ != PERCH_OK) return rc_;   \
+  } while (0)
+
+extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads_out) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (!ctx->has_obs) return ctx->fail(PERCH_E_STATE, "set an observation first");
+  if (n_sample < 1 || n_sample > (1 << 22)) return ctx->fail(PERCH_E_ARG, "n_sample out of range");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  // time throughput, not latency: the sample must keep every SM busy for
+  // many items, or wide CTAs win by finishing a near-empty launch sooner
+  n_sample = std::max(n_sample, 32 * ctx->sm_count);
+  const int n_mesh = ctx->n_mesh;
+  const long long n_poses = (long long)ctx->nx * ctx->ny * ctx->n_yaw;
+  std::vector<perch_obj> hyps(n_sample);
+  std::vector<int32_t> hp(n_sample, 0);
+  const int32_t plen = 0;
+  CK(ctx->b_parents.ensure(sizeof(perch_obj)), "alloc");
+  CK(ctx->b_plen.ensure(4), "alloc");
+  CK(ctx->b_hp.ensure(4 * (size_t)n_sample), "alloc");
+  CK(ctx->b_hyp.ensure(sizeof(perch_obj) * (size_t)n_sample), "alloc");
+  CK(ctx->b_out.ensure(sizeof(perch_cost) * (size_t)n_sample), "alloc");
+  CK(cudaMemcpyAsync(ctx->b_plen.p, &plen, 4, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  CK(cudaMemcpyAsync(ctx->b_hp.p, hp.data(), 4 * (size_t)n_sample, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  const std::vector<int> saved = ctx->mesh_threads;
+  for (int m = 0; m < n_mesh; ++m) {
+    const TuneKey key{ctx->device, ctx->h_meshes[m].n_tris, ctx->h_meshes[m].n_verts, ctx->mesh_tile_w[m],
+                      ctx->mesh_tile_h[m]};
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        ctx->mesh_threads[m] = it->second;
+        continue;
+      }
+    }
+    // a spread of poses of mesh m (a fixed stride through the pose grid)
+    const long long stride = std::max(1LL, n_poses / n_sample) | 1LL;
+    for (int i = 0; i < n_sample; ++i) {
+      const long long q = (i * stride) % n_poses;
+      perch_obj o;
+      o.mesh = (uint16_t)m;
+      o.iyaw = (uint16_t)(q % ctx->n_yaw);
+      o.iy = (int16_t)((q / ctx->n_yaw) % ctx->ny);
+      o.ix = (int16_t)(q / ((long long)ctx->n_yaw * ctx->ny));
+      hyps[i] = o;
+    }
+    CK(cudaMemcpyAsync(ctx->b_hyp.p, hyps.data(), sizeof(perch_obj) * (size_t)n_sample, cudaMemcpyHostToDevice,
+                       ctx->stream),
+       "copy");
+    int best = 256;
+    float best_ms = 1e30f;
+    for (int w : kWidths) {
+      ctx->mesh_threads[m] = w;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {
+        int rc = ctx->enqueue_eval(ctx->b_parents.as<perch_obj>(), 1, ctx->b_plen.as<int32_t>(), 1,
+                                   ctx->b_hp.as<int32_t>(), ctx->b_hyp.as<perch_obj>(), n_sample, 1,
+                                   ctx->b_out.as<perch_cost>());
+        if (rc != PERCH_OK) {
+          ctx->mesh_threads = saved;
+          return rc;
+        }
+        float a = 0.0f, b = 0.0f;
+        CK(cudaEventSynchronize(ctx->ev[2]), "event sync");
+        CK(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]), "event time");
+        CK(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]), "event time");
+        if (rep > 0) ms = std::min(ms, b);  // the first launch of a width also loads its code
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = w;
+      }
+    }
+    ctx->mesh_threads[m] = best;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  if (threads_out)
+    for (int m = 0; m < n_mesh; ++m) threads_out[m] = ctx->mesh_threads[m];
+  return PERCH_OK;
+}
+
+extern "C" int perch_eval_graph(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride,
+                                const int32_t* parent_len, int32_t n_par, const int32_t* hyp_parent,
+                                const perch_obj* hyp, int64_t n_hyp, int32_t K_total, perch_cost* out,
+                                perch_cost* out_host) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (!ctx->has_obs) return ctx->fail(PERCH_E_STATE, "set an observation first");
+  if (n_hyp < 1 || n_hyp > 0x7fffffffLL) return ctx->fail(PERCH_E_ARG, "n_hyp out of range");
+  if (!parent_len || !hyp_parent || !hyp || !out || n_par < 1 || parent_stride < 0 || K_total < 1 ||
+      (parent_stride > 0 && !parents))
+    return ctx->fail(PERCH_E_ARG, "null pointer or bad sizes");
+  if (n_par > 65535 || (long long)n_par * std::max(parent_stride, 1) > 65535)
+    return ctx->fail(PERCH_E_ARG, "too many parents in one batch (n_par x stride <= 65535)");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const GraphKey key{parents, parent_stride, parent_len, n_par, hyp_parent, hyp, n_hyp, K_total, out, out_host,
+                     ctx->tables_version};
+  if (!ctx->graph_exec || std::memcmp(&key, &ctx->graph_key, sizeof key) != 0) {
+    if (ctx->graph_exec) {
+      cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+    }
+    // one plain run sizes every buffer and sets kernel attributes, so the
+    // capture below records only stream work (no allocation)
+    int rc = ctx->enqueue_eval(parents, parent_stride, parent_len, n_par, hyp_parent, hyp, n_hyp, K_total, out);
+    if (rc != PERCH_OK) return rc;
+    CK(cudaStreamSynchronize(ctx->stream), "graph warm-up");
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    ctx->capturing = true;
+    rc = ctx->enqueue_eval(parents, parent_stride, parent_len, n_par, hyp_parent, hyp, n_hyp, K_total, out);
+    if (rc == PERCH_OK && out_host)
+      rc = ctx->cuda(cudaMemcpyAsync(out_host, out, sizeof(perch_cost) * (size_t)n_hyp, cudaMemcpyDeviceToHost,
+                                     ctx->stream),
+                     "record download");
+    ctx->capturing = false;
+    const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
+    if (rc != PERCH_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    CK(ec, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ei, "graph instantiate");
+    ctx->graph_exec = exec;
+    ctx->graph_key = key;
+  }
+  CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream), "graph launch");
+  return PERCH_OK;
+}
+
+extern "C" int perch_set_threads(perch_ctx* ctx, int32_t mesh, int32_t threads) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (threads != 128 && threads != 256 && threads != 512)
+    return ctx->fail(PERCH_E_ARG, "threads must be 128, 256 or 512");
+  if (mesh < -1 || mesh >= ctx->n_mesh) return ctx->fail(PERCH_E_ARG, "mesh %d out of range", mesh);
+  if ((int)ctx->mesh_threads.size() != ctx->n_mesh) ctx->mesh_threads.assign(ctx->n_mesh, 256);
+  for (int m = 0; m < ctx->n_mesh; ++m)
+    if (mesh < 0 || m == mesh) ctx->mesh_threads[m] = threads;
+  ctx->tables_version++;  // a captured graph holds the old widths
+  return PERCH_OK;
+}

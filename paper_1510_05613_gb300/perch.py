@@ -24,7 +24,8 @@ COST = np.dtype([("djr", np.int32), ("djo", np.int32), ("resid", np.int32), ("vi
 # names exported by the library (include/perch.h)
 EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_meshes", "perch_set_pose_grid",
            "perch_set_observation", "perch_eval_successors", "perch_eval_successors_dev", "perch_render",
-           "perch_search", "perch_last_timing", "perch_eval_successors_noalloc")
+           "perch_search", "perch_last_timing", "perch_eval_successors_noalloc", "perch_autotune",
+           "perch_eval_graph", "perch_set_threads")
 
 
 class perch_mesh(ctypes.Structure):
@@ -80,6 +81,9 @@ def load(path: str = LIB_PATH):
         "perch_search": ([P, P, P], ctypes.c_int),
         "perch_last_timing": ([P, P, P], ctypes.c_int),
         "perch_eval_successors_noalloc": ([P, P, I32, P, I32, P, P, I64, I32, P], ctypes.c_int),
+        "perch_autotune": ([P, I32, P], ctypes.c_int),
+        "perch_set_threads": ([P, I32, I32], ctypes.c_int),
+        "perch_eval_graph": ([P, P, I32, P, I32, P, P, I64, I32, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -149,6 +153,7 @@ class Perch:
 
     def setup(self, workload):
         """Meshes, pose grid and observation of a synth.Workload."""
+        self.n_mesh = len(workload.meshes)
         self.perch_load_meshes(workload.meshes)
         self.perch_set_pose_grid(workload.grid)
         self.perch_set_observation(workload.depth, workload.cam.fxfycxcy, workload.cam.T_wc, workload.delta)
@@ -190,6 +195,24 @@ class Perch:
         return self._check(self.lib.perch_eval_successors_noalloc(
             self.h, parents_t.data_ptr(), stride, plen_t.data_ptr(), plen_t.numel(), hyp_parent_t.data_ptr(),
             hyps_t.data_ptr(), hyp_parent_t.numel(), K_total, out_t.data_ptr()))
+
+    def perch_autotune(self, n_sample: int = 2048):
+        """Pick the CTA width per mesh by timing; returns the choices."""
+        out = (ctypes.c_int32 * 65536)()
+        self._check(self.lib.perch_autotune(self.h, n_sample, out))
+        return [int(out[i]) for i in range(self.n_mesh)]
+
+    def perch_set_threads(self, threads: int, mesh: int = -1):
+        return self._check(self.lib.perch_set_threads(self.h, mesh, threads))
+
+    def perch_eval_graph(self, parents_t, stride: int, plen_t, hyp_parent_t, hyps_t, K_total: int, out_t,
+                         out_host=None):
+        """As perch_eval_successors_dev, captured once into a CUDA graph and
+        replayed; out_host: optional pinned host array (torch, uint8/int32)."""
+        return self._check(self.lib.perch_eval_graph(
+            self.h, parents_t.data_ptr(), stride, plen_t.data_ptr(), plen_t.numel(), hyp_parent_t.data_ptr(),
+            hyps_t.data_ptr(), hyp_parent_t.numel(), K_total, out_t.data_ptr(),
+            None if out_host is None else out_host.data_ptr()))
 
     def perch_render(self, objs):
         o = _c(objs, OBJ)

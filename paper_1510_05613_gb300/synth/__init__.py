@@ -445,3 +445,178 @@ def workload_c2(scene: int = 0, grid: PoseGrid | None = None) -> Workload:
     gt = sample_scene(meshes, grid, [0, 1, 2], seed)
     depth = observe(cam, meshes, grid, gt, 0.003, 0.05, seed)
     return Workload("c2", cam, meshes, grid, 0.01, gt, depth, 0.003, 0.05, seed)
+
+
+# ---------------------------------------------------------------------------
+# heavy-occlusion workload: eight meshes of uneven size (2k to 50k triangles)
+# ---------------------------------------------------------------------------
+def prism_mesh(profile, corners, sub: int, n_rings: int, name: str) -> Mesh:
+    """Closed solid of revolution-like prism: the boundary polygon `corners`
+    (unit circumradius, counter-clockwise), each side split into `sub`
+    segments, scaled by profile(z) = (radius, z) at n_rings + 1 heights;
+    fan caps. Triangles face outwards."""
+    corners = np.asarray(corners, np.float64)
+    ring = []
+    for k in range(len(corners)):
+        a, b = corners[k], corners[(k + 1) % len(corners)]
+        for j in range(sub):
+            ring.append(a + (b - a) * j / sub)
+    ring = np.array(ring)
+    n = len(ring)
+    pts = []
+    for l in range(n_rings + 1):
+        r, z = profile(l / n_rings)
+        for p in ring:
+            pts.append((r * p[0], r * p[1], z))
+    top_r, top_z = profile(1.0)
+    bot_r, bot_z = profile(0.0)
+    top_c = len(pts); pts.append((0.0, 0.0, top_z))
+    bot_c = len(pts); pts.append((0.0, 0.0, bot_z))
+    tris = []
+    for l in range(n_rings):
+        for k in range(n):
+            a, b = l * n + k, l * n + (k + 1) % n
+            c, d = (l + 1) * n + (k + 1) % n, (l + 1) * n + k
+            tris.append((a, b, c)); tris.append((a, c, d))
+    for k in range(n):
+        tris.append((top_c, n_rings * n + k, n_rings * n + (k + 1) % n))
+        tris.append((bot_c, (k + 1) % n, k))
+    P, T = np.array(pts), np.array(tris, np.int64)
+    T = _orient_outward(P, T, (0.0, 0.0, 0.5 * (top_z + bot_z)))
+    return P, T
+
+
+def _ngon(k: int):
+    return [(math.cos(2 * math.pi * j / k), math.sin(2 * math.pi * j / k)) for j in range(k)]
+
+
+def frustum_mesh(r_bot: float, r_top: float, h: float, n_seg: int, n_rings: int, name: str = "frustum") -> Mesh:
+    P, T = prism_mesh(lambda t: (r_bot + (r_top - r_bot) * t, h * t), _ngon(n_seg), 1, n_rings, name)
+    r = 0.9 * min(r_bot, r_top) * math.cos(math.pi / n_seg)
+    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h)
+
+
+def hex_prism_mesh(R: float, h: float, sub: int, n_rings: int, name: str = "hexprism") -> Mesh:
+    P, T = prism_mesh(lambda t: (R, h * t), _ngon(6), sub, n_rings, name)
+    r = 0.9 * R * math.cos(math.pi / 6)
+    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h)
+
+
+def superquadric_general(a1, a2, a3, e1, e2, n_eta, n_omega, name):
+    """Superquadric with e2 <= 1 (cross-sections contain the circle of radius
+    min(a1, a2) rho(z)); inscribed cylinder shrunk by 15% for tessellation."""
+    m = superquadric_mesh(a1, a2, a3, e1, e2, n_eta, n_omega, name)
+    z = m.verts[:, 2].astype(np.float64)
+    zr = np.abs(z - a3)
+    beyond = zr[zr >= 0.8 * a3]
+    zb = beyond.min() if beyond.size else a3
+    s = min(1.0, zb / a3)
+    rho = max(0.0, 1.0 - s ** (2.0 / e1)) ** (e1 / 2.0)
+    m.vol_r = 0.85 * min(a1, a2) * rho * math.cos(math.pi / n_omega)
+    return m
+
+
+def meshes_c3():
+    """Eight procedural objects of uneven size (2k to 50k triangles) and
+    height (6 to 22 cm), so that tall objects can hide short ones."""
+    return [
+        box_mesh(0.08, 0.06, 0.06, 13, "box2k"),
+        cylinder_mesh(0.035, 0.22, 96, 25, "cylinder5k"),
+        superquadric_general(0.04, 0.04, 0.045, 0.5, 1.0, 41, 100, "superquadric8k"),
+        superquadric_general(0.05, 0.035, 0.03, 1.0, 0.5, 61, 100, "pillow12k"),
+        superquadric_general(0.045, 0.04, 0.04, 1.0, 1.0, 91, 100, "ellipsoid18k"),
+        frustum_mesh(0.045, 0.03, 0.18, 250, 49, "frustum25k"),
+        hex_prism_mesh(0.045, 0.10, 48, 60, "hexprism35k"),
+        superquadric_general(0.04, 0.04, 0.035, 0.4, 0.4, 126, 200, "cube50k"),
+    ]
+
+
+def raycast_ids(cam: Camera, meshes, grid: PoseGrid, scene):
+    """Noise-free depth (float64) and the index into `scene` of the object
+    seen at every pixel (-1 = none)."""
+    soups = [place(meshes[int(o["mesh"])], grid, int(o["ix"]), int(o["iy"]), int(o["iyaw"])) for o in scene]
+    ids = np.concatenate([np.full(len(s), i, np.int32) for i, s in enumerate(soups)]) if soups else np.zeros(0, np.int32)
+    tris = np.ascontiguousarray(np.concatenate(soups, 0) if soups else np.zeros((0, 3, 3)), np.float64)
+    T = np.ascontiguousarray(cam.T_wc.astype(np.float64))
+    depth = np.zeros((cam.H, cam.W), np.float64)
+    obj = np.zeros((cam.H, cam.W), np.int32)
+    lib = _load_sensor()
+    fn = lib.synth_raycast_ids
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [ctypes.c_void_p] * 2 + [
+        ctypes.c_long, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    ids = np.ascontiguousarray(ids)
+    if fn(cam.W, cam.H, cam.fx, cam.fy, cam.cx, cam.cy, T.ctypes.data, tris.ctypes.data, tris.shape[0],
+          ids.ctypes.data, depth.ctypes.data, obj.ctypes.data) != 0:
+        raise RuntimeError("synth_raycast_ids failed")
+    return depth, obj
+
+
+def occlusion_fractions(cam: Camera, meshes, grid: PoseGrid, scene) -> np.ndarray:
+    """Per object: 1 - (pixels where it is the visible surface of the whole
+    scene) / (pixels it covers when alone)."""
+    _, obj = raycast_ids(cam, meshes, grid, scene)
+    out = np.zeros(len(scene))
+    for i in range(len(scene)):
+        alone = (raycast_ids(cam, meshes, grid, scene[i:i + 1])[1] >= 0).sum()
+        out[i] = 1.0 - (obj == i).sum() / max(1, alone)
+    return out
+
+
+def workload_c3(scene: int = 0, grid: PoseGrid | None = None, min_occlusion: float = 0.7) -> Workload:
+    """640x480, fx=fy=525; five of the eight uneven meshes, footprints
+    disjoint, one of them placed just behind a taller one (as seen from the
+    camera) so that at least one object is more than 70% (and less than 100%)
+    occluded; poses on the 50x50 x 16-yaw grid; sigma 3 mm, 5% dropout,
+    delta 1 cm."""
+    seed = 1000 * 3 + scene
+    cam, meshes = camera_c2(), meshes_c3()
+    grid = grid or pose_grid(-0.49, 0.02, 50, 16)
+    step = float(grid.xs[1] - grid.xs[0])
+    height = [float(m.verts[:, 2].max()) for m in meshes]
+    u = uniform(substream(seed, 4), 200000)
+    pos = 0
+
+    def take():
+        nonlocal pos
+        pos += 1
+        return u[pos - 1]
+
+    def disjoint(rows):
+        for i in range(len(rows)):
+            for j in range(i + 1, len(rows)):
+                dx = float(grid.xs[rows[i][1]]) - float(grid.xs[rows[j][1]])
+                dy = float(grid.ys[rows[i][2]]) - float(grid.ys[rows[j][2]])
+                rr = meshes[rows[i][0]].footprint_radius + meshes[rows[j][0]].footprint_radius + 0.005
+                if dx * dx + dy * dy < rr * rr:
+                    return False
+        return True
+
+    for attempt in range(400):
+        ids = np.argsort(u[pos:pos + 8]).tolist()
+        pos += 8
+        ids = ids[:5]
+        front = max(ids, key=lambda m: height[m])  # tallest chosen object in front
+        back = [m for m in ids if m != front][int(take() * 4)]
+        fx_, fy_ = 15 + int(take() * 20), 12 + int(take() * 12)
+        gap = meshes[front].footprint_radius + meshes[back].footprint_radius + 0.006
+        by = fy_ + int(math.ceil(gap / step)) + int(take() * 2)
+        bx = fx_ + int(take() * 3) - 1
+        rows = [(front, fx_, fy_, int(take() * grid.n_yaw)), (back, bx, by, int(take() * grid.n_yaw))]
+        for m in ids:
+            if m in (front, back):
+                continue
+            for _ in range(50):
+                cand = (m, 10 + int(take() * 30), 8 + int(take() * 34), int(take() * grid.n_yaw))
+                if disjoint(rows + [cand]):
+                    rows.append(cand)
+                    break
+        if len(rows) < 5 or not disjoint(rows) or max(by, bx) >= grid.ny:
+            continue
+        gt = objs(sorted(rows))
+        occ = occlusion_fractions(cam, meshes, grid, gt)
+        if occ.max() > min_occlusion and occ.max() < 1.0:
+            depth = observe(cam, meshes, grid, gt, 0.003, 0.05, seed)
+            return Workload("c3", cam, meshes, grid, 0.01, gt, depth, 0.003, 0.05, seed,
+                            extra={"occlusion": occ.tolist()})
+    raise RuntimeError("no heavily occluded scene found")

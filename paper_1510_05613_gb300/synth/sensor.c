@@ -30,10 +30,12 @@ static int project(const double Rcw[9], const double tcw[3], double fx, double f
 }
 
 /* T_wc: row-major 3x4 camera->world. tris: n_tri_total*9 doubles (world
- * frame, three vertices per triangle). Returns 0 on success. */
-int synth_raycast(int W, int H, double fx, double fy, double cx, double cy,
-                  const double* T_wc, const double* tris, long n_tri,
-                  double* depth_out) {
+ * frame, three vertices per triangle); tri_obj (may be NULL): the object id
+ * of each triangle, written per pixel to obj_out (-1 = no hit) when both are
+ * given. Returns 0 on success. */
+int synth_raycast_ids(int W, int H, double fx, double fy, double cx, double cy,
+                      const double* T_wc, const double* tris, long n_tri, const int* tri_obj,
+                      double* depth_out, int* obj_out) {
   double Rwc[9] = {T_wc[0], T_wc[1], T_wc[2], T_wc[4], T_wc[5],
                    T_wc[6], T_wc[8], T_wc[9], T_wc[10]};
   double twc[3] = {T_wc[3], T_wc[7], T_wc[11]};
@@ -90,6 +92,7 @@ int synth_raycast(int W, int H, double fx, double fy, double cx, double cy,
       double d[3];
       for (int r = 0; r < 3; ++r) d[r] = Rwc[r * 3 + 0] * dc[0] + Rwc[r * 3 + 1] * dc[1] + Rwc[r * 3 + 2] * dc[2];
       double best = INFINITY;
+      int best_obj = -1;
       int tile = (v / TILE) * TX + (u / TILE);
       for (int li = counts[tile]; li < counts[tile + 1]; ++li) {
         const double* tr = tris + (long)list[li] * 9;
@@ -109,12 +112,21 @@ int synth_raycast(int W, int H, double fx, double fy, double cx, double cy,
         double bv = f * (d[0] * q[0] + d[1] * q[1] + d[2] * q[2]);
         if (bv < 0.0 || bu + bv > 1.0) continue;
         double t = f * (e2[0] * q[0] + e2[1] * q[1] + e2[2] * q[2]);
-        if (t > 1e-6 && t < best) best = t;
+        if (t > 1e-6 && t < best) {
+          best = t;
+          best_obj = tri_obj ? tri_obj[list[li]] : 0;
+        }
       }
       /* the ray direction has camera-frame z = 1, so t is camera-frame Z */
       depth_out[(long)v * W + u] = isinf(best) ? 0.0 : best;
+      if (obj_out) obj_out[(long)v * W + u] = best_obj;
     }
   }
   free(counts); free(bbox); free(list); free(cursor);
   return 0;
+}
+
+int synth_raycast(int W, int H, double fx, double fy, double cx, double cy,
+                  const double* T_wc, const double* tris, long n_tri, double* depth_out) {
+  return synth_raycast_ids(W, H, fx, fy, cx, cy, T_wc, tris, n_tri, NULL, depth_out, NULL);
 }

@@ -224,3 +224,70 @@ def test_search_matches_oracle_ucs_full_c1(c1):
     cost, key, _ = search.uniform_cost_search(w, wl.depth, wl.grid, wl.mesh_multiset)
     r = p.perch_search(wl.mesh_multiset, batch_states=16)
     assert r["proven_optimal"] and (r["cost"], r["key"]) == (cost, key)
+
+
+def test_c3_uneven_meshes_sampled():
+    """Heavy-occlusion workload: five of eight meshes of 2k-50k triangles;
+    sampled records at the root, a middle level and the last level."""
+    wl = synth.workload_c3()
+    p = perch.Perch(0)
+    p.setup(wl)
+    w = oracle.World.of(wl)
+    rng = np.random.default_rng(3)
+    parents = [wl.gt[:0], wl.gt[:2], wl.gt[:4]]
+    hyps, hp = [], []
+    for i, par in enumerate(parents):
+        rem = sorted(set(int(m) for m in wl.gt["mesh"]) - set(int(m) for m in par["mesh"]))
+        allh = synth.all_hypotheses(wl.grid, rem)
+        pick = allh[rng.choice(len(allh), 40, replace=False)]
+        near = [o for o in wl.gt if int(o["mesh"]) in rem]
+        hyps += [pick, np.array(near, synth.OBJ_DTYPE)]
+        hp += [np.full(len(pick) + len(near), i, np.int32)]
+    hyps, hp = np.concatenate(hyps), np.concatenate(hp)
+    got = _compare(wl, p, w, parents, hp, hyps, wl.K)
+    assert (got[:, 2] > 0).any()
+    p.close()
+
+
+def _dev_batch(torch, parents, hp, hyps):
+    dev = torch.device("cuda:0")
+    P, plen, stride = perch.Perch.pack_parents(parents)
+    tP = torch.from_numpy(P.view(np.int16).reshape(-1).copy()).to(dev)
+    th = torch.from_numpy(np.ascontiguousarray(hyps).view(np.int16).reshape(-1).copy()).to(dev)
+    return tP, stride, torch.from_numpy(plen).to(dev), torch.from_numpy(np.ascontiguousarray(hp)).to(dev), th
+
+
+def test_graph_and_autotune_match_oracle(c2):
+    """The CUDA-graph entry point and autotuned launch widths give the same
+    records as the oracle; replaying the graph after rewriting the
+    hypotheses in place evaluates the new ones."""
+    import torch
+    wl, _, w = c2
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    p = perch.Perch(0, stream=stream.cuda_stream)
+    p.setup(wl)
+    widths = p.perch_autotune(256)
+    assert len(widths) == 3 and set(widths) <= {128, 256, 512}
+    rng = np.random.default_rng(9)
+    allh = synth.all_hypotheses(wl.grid, [0, 1, 2])
+    parents = [wl.gt[:0], wl.gt[:2]]
+    hp = rng.integers(0, 2, 90).astype(np.int32)
+    outs = []
+    for rep in range(2):
+        hyps = allh[rng.choice(len(allh), 90, replace=False)]
+        hyps["mesh"] = np.where(hp == 1, 2, hyps["mesh"])  # the 2-object parent needs the third type
+        tP, stride, tplen, thp, th = _dev_batch(torch, parents, hp, hyps)
+        if rep == 0:
+            keep = (tP, tplen, thp, th)
+            tout = torch.zeros(len(hyps) * 6, dtype=torch.int32, device="cuda:0")
+        else:
+            keep[3].copy_(th)  # same device buffers, new contents
+        p.perch_eval_graph(keep[0], stride, keep[1], keep[2], keep[3], wl.K, tout)
+        torch.cuda.synchronize()
+        got = tout.cpu().numpy().reshape(-1, 6).astype(np.int64)
+        exp = oracle.eval_batch(w, wl.depth, parents, hp, hyps, wl.K)
+        assert np.array_equal(got, exp)
+        outs.append(got)
+    assert not np.array_equal(outs[0], outs[1])
+    p.close()

@@ -8,7 +8,7 @@ import pytest
 from paper_1510_05613_gb300 import synth
 
 
-ALL = synth.meshes_c1() + synth.meshes_c2()
+ALL = synth.meshes_c1() + synth.meshes_c2() + synth.meshes_c3()
 
 
 @pytest.mark.parametrize("m", ALL, ids=[f"{m.name}{m.n_tris}" for m in ALL])
@@ -69,3 +69,12 @@ def test_workloads_are_seeded_and_shaped():
     c2 = synth.workload_c2()
     assert c2.depth.shape == (480, 640) and c2.grid.n_poses == 40000
     assert all(9000 <= m.n_tris <= 11000 for m in c2.meshes)
+
+
+def test_c3_workload_is_heavily_occluded():
+    wl = synth.workload_c3()
+    assert wl.K == 5 and len(set(int(m) for m in wl.gt["mesh"])) == 5
+    occ = np.array(wl.extra["occlusion"])
+    assert 0.7 < occ.max() < 1.0
+    sizes = sorted(m.n_tris for m in wl.meshes)
+    assert sizes[0] <= 2100 and sizes[-1] >= 49000
