@@ -65,7 +65,7 @@ typedef struct {
   int16_t ix, iy;
 } perch_obj;
 
-/* Result for one successor (24 bytes). For a valid child (viol == 0) the edge
+/* Result for one successor (28 bytes). For a valid child (viol == 0) the edge
  * cost of Eq. (4) is djr + djo + resid:
  *   djr   = #{p in dR unexplained by I}             (Sec. IV-A, dJ_r)
  *   djo   = #{q in I n V(O) unexplained by dR}       (Sec. IV-A, dJ_o)
@@ -75,10 +75,15 @@ typedef struct {
  *           is not a successor: its cost fields are then 0
  *   n_new = |dR|, the child's pixels where the parent render is empty
  *   flags = bit 0: a triangle of the child was culled (near plane / guard
- *           band); bit 1: invalid (viol > 0). */
+ *           band); bit 1: invalid (viol > 0)
+ *   n_vol = #{q in I n V(O) outside every parent object's volume}: how much
+ *           the overlap heuristic h_overlap of Sec. IV-C (observed points
+ *           outside the assigned volumes) drops from parent to child; 0 when
+ *           viol > 0. */
 typedef struct {
   int32_t djr, djo, resid, viol, n_new;
   uint32_t flags;
+  int32_t n_vol;
 } perch_cost;
 
 #define PERCH_FLAG_CULLED 1u
@@ -162,16 +167,38 @@ int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* parents, int3
                                   const int32_t* parent_len, int32_t n_par, const int32_t* hyp_parent,
                                   const perch_obj* hyp, int64_t n_hyp, int32_t K_total, perch_cost* out);
 
+/* Several scenes in one context (many independent searches at once). Every
+ * scene shares the meshes, the pose grid, the camera and delta of
+ * perch_set_observation, which is scene 0; this call sets (or replaces) the
+ * observed depth of scene `scene` (0..65535; unset scenes in between are
+ * empty). depth[H * W] as in perch_set_observation. */
+int perch_set_scene(perch_ctx* ctx, int32_t scene, const float* depth);
+
+/* perch_eval_successors for a batch that mixes scenes: parent i belongs to
+ * scene parent_scene[i] and to a problem of parent_K[i] objects (the residual
+ * is added on its children when parent_len[i] + 1 == parent_K[i]). Host
+ * pointers; returns when out is written. */
+int perch_eval_successors_multi(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride,
+                                const int32_t* parent_len, const int32_t* parent_scene, const int32_t* parent_K,
+                                int32_t n_par, const int32_t* hyp_parent, const perch_obj* hyp, int64_t n_hyp,
+                                perch_cost* out);
+
 /* z-buffer render (min depth, +inf where empty) of n objects into
  * depth_out[H * W] (host pointer), the R_j of Sec. III-A. Returns the number
  * of culled triangles in *n_culled (may be NULL). */
 int perch_render(perch_ctx* ctx, const perch_obj* objs, int32_t n, float* depth_out,
                  int64_t* n_culled);
 
-/* Tree search (Sec. IV-B, Alg. 1 with the admissible h0 = 0; w = 1 gives
- * uniform-cost search). mesh_multiset[K]: the types of the K objects in the
- * scene (Sec. III: known number and types). batch_states: states expanded
- * per device launch (>= 1). Stops at optimality or at time_limit_s /
+/* Tree search (Sec. IV-B, Alg. 1). With w = 1 and no heuristics:
+ * uniform-cost search (A* with the admissible h0 = 0), which returns an
+ * optimal scene. Otherwise Focal-MHA*: the anchor queue is keyed by g + h0,
+ * states with g <= w * (smallest anchor key) are also expanded greedily by
+ * each inadmissible heuristic in `heuristics` (bit 0: h_depth = K - |s|;
+ * bit 1: h_overlap = observed points outside the assigned volumes,
+ * Sec. IV-C), and the search returns a scene of cost <= w * OPT
+ * (Theorem 2). mesh_multiset[K]: the types of the K objects (Sec. III: known
+ * number and types). batch_states: states taken from each queue per device
+ * launch (>= 1). Stops at the optimum / the bound, or at time_limit_s /
  * max_expansions (0 = none) and then returns PERCH_E_TIMEOUT with the best
  * goal found so far (or cost -1 if none). */
 typedef struct {
@@ -181,6 +208,7 @@ typedef struct {
   int32_t batch_states;
   double time_limit_s;
   int64_t max_expansions;
+  int32_t heuristics;
 } perch_search_params;
 
 typedef struct {
@@ -194,6 +222,15 @@ typedef struct {
 } perch_result;
 
 int perch_search(perch_ctx* ctx, const perch_search_params* params, perch_result* result);
+
+/* One search per scene (scenes[i] with params[i]), run together: the
+ * expansions of every unfinished search are packed into shared evaluation
+ * launches of at most max_hyps_per_launch hypotheses (at least one state's
+ * children). results[i].seconds is the time from the start until search i
+ * finished (its time to the optimum). Limits as perch_search, taken as the
+ * largest over params. */
+int perch_search_multi(perch_ctx* ctx, int32_t n_scenes, const int32_t* scenes, const perch_search_params* params,
+                       int64_t max_hyps_per_launch, perch_result* results);
 
 /* Launch tuning (not in the paper). The evaluation runs one persistent
  * launch per mesh with a shared-memory tile sized for that mesh; this call

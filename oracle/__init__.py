@@ -29,7 +29,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "perch_oracle.c")
 _LIB = os.path.join(_HERE, "libperch_oracle.so")
 
-REC_FIELDS = ("djr", "djo", "resid", "viol", "n_new", "flags")
+REC_FIELDS = ("djr", "djo", "resid", "viol", "n_new", "flags", "n_vol")
 FLAG_CULLED, FLAG_INVALID = 1, 2
 
 
@@ -167,7 +167,8 @@ def cost_J(world: World, depth, objs):
 
 
 def eval_batch(world: World, depth, parents, hyp_parent, hyps, K_total: int, threads: int = 0):
-    """Edge-cost records (n_hyp, 6) int32: dJr, dJo, resid, viol, n_new, flags.
+    """Edge-cost records (n_hyp, 7) int32: dJr, dJo, resid, viol, n_new, flags,
+    n_vol (observed points newly inside the assigned volumes).
 
     ``parents`` is a list of object arrays (each a partial assignment)."""
     from paper_1510_05613_gb300.synth import OBJ_DTYPE
@@ -180,7 +181,7 @@ def eval_batch(world: World, depth, parents, hyp_parent, hyps, K_total: int, thr
     hp = _c(hyp_parent, np.int32)
     h = _objs(hyps)
     d = _c(depth, np.float32)
-    recs = np.zeros((len(h), 6), np.int32)
+    recs = np.zeros((len(h), 7), np.int32)
     rc = _load().or_eval_batch(world.ptr(), d.ctypes.data, P.ctypes.data, plen.ctypes.data, len(parents), k_max,
                                hp.ctypes.data, h.ctypes.data, len(h), K_total, recs.ctypes.data, threads)
     if rc:

@@ -70,8 +70,11 @@ typedef struct {
   float delta;
 } or_world;
 
-/* record: dJr, dJo, resid, viol, n_new, flags */
-enum { OR_DJR = 0, OR_DJO, OR_RESID, OR_VIOL, OR_NNEW, OR_FLAGS, OR_REC };
+/* record: dJr, dJo, resid, viol, n_new, flags, n_vol
+ * n_vol = #{q in I n V(O) : q outside every parent object's volume}, the
+ * decrease of the overlap heuristic h_overlap of Sec. IV-C from parent to
+ * child (h_overlap(s) = |I| - #{q in I n V_j}). */
+enum { OR_DJR = 0, OR_DJO, OR_RESID, OR_VIOL, OR_NNEW, OR_FLAGS, OR_NVOL, OR_REC };
 #define OR_FLAG_CULLED 1u
 #define OR_FLAG_INVALID 2u
 
@@ -336,11 +339,17 @@ static void edge_cost(const or_world* w, const or_cam* c, const or_cloud* I,
   int64_t djr = 0;
   for (int64_t k = 0; k < nd; ++k)
     if (!explained(pts[k], I->cam, I->n, c->delta2)) djr++;
-  int64_t djo = 0;
-  for (int64_t k = 0; k < I->n; ++k)
-    if (in_volume(w, o, I->world[k]) && !explained(I->cam[k], pts, nd, c->delta2)) djo++;
+  int64_t djo = 0, nvol = 0;
+  for (int64_t k = 0; k < I->n; ++k) {
+    if (!in_volume(w, o, I->world[k])) continue;
+    if (!explained(I->cam[k], pts, nd, c->delta2)) djo++;
+    int in_parent = 0;
+    for (int j = 0; j < n_parent && !in_parent; ++j) in_parent = in_volume(w, parent[j], I->world[k]);
+    if (!in_parent) nvol++;
+  }
   rec[OR_DJR] = (int32_t)djr;
   rec[OR_DJO] = (int32_t)djo;
+  rec[OR_NVOL] = (int32_t)nvol;
 
   if (n_parent + 1 == K_total) {
     /* residual(K): observed points outside V_K unexplained by R_K */
@@ -424,7 +433,7 @@ int32_t or_cost_J(const or_world* w, const float* depth, const or_obj* objs, int
 
 /* Edge costs for a batch of successors. parents: n_par x k_max objects,
  * parent_len[i] of them used; hypothesis h adds hyps[h] to parent
- * hyp_parent[h]; K_total = objects in a complete scene. recs: n_hyp x 6. */
+ * hyp_parent[h]; K_total = objects in a complete scene. recs: n_hyp x 7. */
 int32_t or_eval_batch(const or_world* w, const float* depth,
                       const or_obj* parents, const int32_t* parent_len, int32_t n_par, int32_t k_max,
                       const int32_t* hyp_parent, const or_obj* hyps, int64_t n_hyp,

@@ -120,3 +120,60 @@ def exhaustive(world, depth, grid, multiset, threads: int = 0):
         return None, None
     best = min((g, key_of(s)) for s, g in frontier)
     return best[0], best[1]
+
+
+def focal_mha(world, depth, grid, multiset, w: float, heuristics=("depth", "overlap"), n_obs: int = 0,
+              threads: int = 0, max_expansions: int = 10 ** 6):
+    """Focal-MHA* as Sec. IV-B describes it, one expansion per iteration:
+    the anchor orders the open states by g + h0 (h0 = 0); the focal set holds
+    the open states with g <= w * (smallest anchor key); the queues take turns
+    (anchor, then each inadmissible heuristic picking its minimum over the
+    focal set). h_depth(s) = K - |s|; h_overlap(s) = |I| - |I n V_j|, kept per
+    state from the records' n_vol. Stops when the best goal has
+    g <= w * (smallest anchor key). Returns (cost, goal_key, expansions)."""
+    from paper_1510_05613_gb300.synth import OBJ_DTYPE
+    K = len(multiset)
+    states = {(): (np.zeros(0, OBJ_DTYPE), 0, n_obs)}  # key -> (objects, g, h_overlap)
+    open_set = {()}
+    closed = set()
+    best = None
+    expansions = 0
+    queues = ["anchor"] + list(heuristics)
+    turn = 0
+    while open_set:
+        f0 = min(states[k][1] for k in open_set)
+        if best is not None and best[0] <= w * f0:
+            break
+        q = queues[turn % len(queues)]
+        turn += 1
+        if q == "anchor":
+            key = min(open_set, key=lambda k: (states[k][1], k))
+        else:
+            focal = [k for k in open_set if states[k][1] <= w * f0]
+            h = (lambda k: K - len(k)) if q == "depth" else (lambda k: states[k][2])
+            key = min(focal, key=lambda k: (h(k), states[k][1], k))
+        open_set.discard(key)
+        closed.add(key)
+        s, g, hov = states[key]
+        expansions += 1
+        if expansions > max_expansions:
+            raise RuntimeError("expansion limit")
+        hyps = _children(grid, _remaining(multiset, s))
+        recs = eval_batch(world, depth, [s], np.zeros(len(hyps), np.int32), hyps, K, threads)
+        for hh, r in zip(hyps, recs):
+            if r[3] > 0:
+                continue
+            child = np.concatenate([s, np.array([hh], OBJ_DTYPE)])
+            ck = key_of(child)
+            ng = g + int(r[0]) + int(r[1]) + int(r[2])
+            if len(child) == K:
+                if best is None or (ng, ck) < best:
+                    best = (ng, ck)
+                continue
+            if ck not in states or ng < states[ck][1]:
+                states[ck] = (child, ng, hov - int(r[6]))
+                closed.discard(ck)
+                open_set.add(ck)
+    if best is None:
+        return None, None, expansions
+    return best[0], best[1], expansions

@@ -139,6 +139,142 @@ int perch_ctx::ensure_tables() {
   return PERCH_OK;
 }
 
+// Observed cloud of one scene and its two indices (A0). Every scene shares
+// the camera and delta of the last perch_set_observation.
+int perch_ctx::build_scene(int s, const float* depth_host) {
+  perch_ctx* ctx = this;
+  const Camera& c = cam;
+  const int W = c.W, H = c.H;
+  const float delta = c.delta;
+  if ((int)scenes.size() <= s) scenes.resize(s + 1);
+  SceneBufs& sc = scenes[s];
+  const int npx = W * H;
+  const int nblk = (npx + 255) / 256;
+  CK(ctx->depth.ensure(4 * (size_t)npx), "alloc depth");
+  CK(ctx->blockcnt.ensure(4 * ((size_t)nblk + 1)), "alloc");
+  CK(ctx->scan_tmp.ensure(4 * ((size_t)npx / 1024 + 2 + 4096)), "alloc");
+  CK(ctx->cam_pts.ensure(16 * (size_t)npx), "alloc");
+  CK(ctx->world_pts.ensure(16 * (size_t)npx), "alloc");
+  CK(ctx->scratch_small.ensure(64), "alloc");
+  CK(cudaMemcpyAsync(ctx->depth.p, depth_host, 4 * (size_t)npx, cudaMemcpyHostToDevice, ctx->stream), "copy depth");
+  int binit[10] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN, INT_MAX, INT_MAX, INT_MIN, INT_MIN};
+  int* bounds = ctx->scratch_small.as<int>();
+  CK(cudaMemcpyAsync(bounds, binit, sizeof binit, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  int* offs = ctx->blockcnt.as<int>();
+  CK(ctx->blockoff.ensure(4 * ((size_t)nblk + 1)), "alloc");
+  CK(launch_obs_count(ctx->depth.as<float>(), W, H, offs, ctx->stream), "obs count kernel");
+  CK(launch_exclusive_scan(offs, ctx->blockoff.as<int>(), nblk, ctx->scan_tmp.as<int>(), ctx->stream), "scan");
+  CK(launch_obs_write(ctx->depth.as<float>(), c, ctx->rx.as<float>(), ctx->ry.as<float>(), ctx->blockoff.as<int>(),
+                      ctx->cam_pts.as<float4>(), ctx->world_pts.as<float4>(), bounds, ctx->stream),
+     "obs write kernel");
+  int hb[11];
+  CK(cudaMemcpyAsync(hb, bounds, 10 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "copy");
+  CK(cudaMemcpyAsync(hb + 10, ctx->blockoff.as<int>() + nblk, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+     "copy");
+  CK(cudaStreamSynchronize(ctx->stream), "observation sync");
+  const int n = hb[10];
+  ObsIndex& o = sc.idx;
+  std::memset(&o, 0, sizeof o);
+  o.n = n;
+  if (n > 0) {
+    float lo[3], hi[3], wlo[2], whi[2];
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = ordered_to_float(hb[k]);
+      hi[k] = ordered_to_float(hb[3 + k]);
+    }
+    for (int k = 0; k < 2; ++k) {
+      wlo[k] = ordered_to_float(hb[6 + k]);
+      whi[k] = ordered_to_float(hb[8 + k]);
+    }
+    // 3D camera-frame grid, cells >= 1.02 delta (Eq. (1) neighbourhood = 3x3x3)
+    double h = 1.02 * (double)delta;
+    long long cells;
+    int dims[3];
+    for (;;) {
+      cells = 1;
+      for (int k = 0; k < 3; ++k) {
+        dims[k] = (int)std::floor(((double)hi[k] - lo[k]) / h) + 3;
+        cells *= dims[k];
+      }
+      if (cells <= (16LL << 20)) break;
+      h *= 1.25;
+    }
+    o.g3x = (float)(lo[0] - h);
+    o.g3y = (float)(lo[1] - h);
+    o.g3z = (float)(lo[2] - h);
+    o.inv3 = (float)(1.0 / h);
+    o.n3x = dims[0];
+    o.n3y = dims[1];
+    o.n3z = dims[2];
+    // 2D world grid for V(O) candidates
+    double g2 = 0.01;
+    int d2[2];
+    for (;;) {
+      for (int k = 0; k < 2; ++k) d2[k] = (int)std::floor(((double)whi[k] - wlo[k]) / g2) + 3;
+      if ((long long)d2[0] * d2[1] <= (4LL << 20)) break;
+      g2 *= 1.5;
+    }
+    o.g2x = (float)(wlo[0] - g2);
+    o.g2y = (float)(wlo[1] - g2);
+    o.inv2 = (float)(1.0 / g2);
+    o.n2x = d2[0];
+    o.n2y = d2[1];
+    const long long c2 = (long long)d2[0] * d2[1];
+    const long long cmax = std::max(cells, c2);
+    CK(ctx->keys.ensure(4 * (size_t)n), "alloc");
+    CK(ctx->counts.ensure(4 * ((size_t)cmax + 1)), "alloc");
+    CK(ctx->cursor.ensure(4 * ((size_t)cmax + 1)), "alloc");
+    CK(sc.start3.ensure(4 * ((size_t)cells + 1)), "alloc");
+    CK(sc.start2.ensure(4 * ((size_t)c2 + 1)), "alloc");
+    CK(sc.obs3.ensure(16 * (size_t)n), "alloc");
+    CK(sc.dil3.ensure(4 * ((size_t)cells / 32 + 1)), "alloc");
+    CK(sc.world2.ensure(16 * (size_t)n), "alloc");
+    CK(sc.cam2.ensure(16 * (size_t)n), "alloc");
+    CK(ctx->scan_tmp.ensure(4 * ((size_t)cmax / 1024 + 2)), "alloc");
+    // bucket the camera-frame cloud
+    CK(cudaMemsetAsync(ctx->counts.p, 0, 4 * (size_t)cells, ctx->stream), "memset");
+    CK(launch_grid3_keys(ctx->cam_pts.as<float4>(), n, o.g3x, o.g3y, o.g3z, o.inv3, o.n3x, o.n3y, o.n3z,
+                         ctx->keys.as<int>(), ctx->counts.as<int>(), ctx->stream), "grid3 keys");
+    CK(launch_exclusive_scan(ctx->counts.as<int>(), sc.start3.as<int>(), (int)cells, ctx->scan_tmp.as<int>(),
+                             ctx->stream), "scan3");
+    CK(cudaMemcpyAsync(ctx->cursor.p, sc.start3.p, 4 * (size_t)cells, cudaMemcpyDeviceToDevice, ctx->stream),
+       "copy");
+    CK(launch_scatter(ctx->keys.as<int>(), n, ctx->cursor.as<int>(), ctx->cam_pts.as<float4>(),
+                      sc.obs3.as<float4>(), nullptr, nullptr, ctx->stream), "scatter3");
+    CK(cudaMemsetAsync(sc.dil3.p, 0, 4 * ((size_t)cells / 32 + 1), ctx->stream), "memset");
+    CK(launch_dilate3(sc.start3.as<int>(), o.n3x, o.n3y, o.n3z, sc.dil3.as<uint32_t>(), ctx->stream),
+       "dilate3");
+    // bucket the world-frame cloud (with its camera-frame copy)
+    CK(cudaMemsetAsync(ctx->counts.p, 0, 4 * (size_t)c2, ctx->stream), "memset");
+    CK(launch_grid2_keys(ctx->world_pts.as<float4>(), n, o.g2x, o.g2y, o.inv2, o.n2x, o.n2y, ctx->keys.as<int>(),
+                         ctx->counts.as<int>(), ctx->stream), "grid2 keys");
+    CK(launch_exclusive_scan(ctx->counts.as<int>(), sc.start2.as<int>(), (int)c2, ctx->scan_tmp.as<int>(),
+                             ctx->stream), "scan2");
+    CK(cudaMemcpyAsync(ctx->cursor.p, sc.start2.p, 4 * (size_t)c2, cudaMemcpyDeviceToDevice, ctx->stream),
+       "copy");
+    CK(launch_scatter(ctx->keys.as<int>(), n, ctx->cursor.as<int>(), ctx->world_pts.as<float4>(),
+                      sc.world2.as<float4>(), ctx->cam_pts.as<float4>(), sc.cam2.as<float4>(), ctx->stream),
+       "scatter2");
+    o.cam3 = sc.obs3.as<float4>();
+    o.start3 = sc.start3.as<int>();
+    o.dil3 = sc.dil3.as<uint32_t>();
+    o.world2 = sc.world2.as<float4>();
+    o.cam2 = sc.cam2.as<float4>();
+    o.start2 = sc.start2.as<int>();
+  }
+  if (s == 0) obs = sc.idx;
+  // device copy of every scene's index, for batches that mix scenes
+  CK(d_scenes.ensure(sizeof(ObsIndex) * scenes.size()), "alloc scene table");
+  std::vector<ObsIndex> all(scenes.size());
+  for (size_t k = 0; k < scenes.size(); ++k) all[k] = scenes[k].idx;
+  CK(cudaMemcpyAsync(d_scenes.p, all.data(), sizeof(ObsIndex) * all.size(), cudaMemcpyHostToDevice, stream),
+     "copy scene table");
+  CK(cudaStreamSynchronize(stream), "scene index");
+  max_obs = 0;
+  for (auto& x : scenes) max_obs = std::max(max_obs, x.idx.n);
+  return PERCH_OK;
+}
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 
@@ -177,6 +313,7 @@ int perch_destroy(perch_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (DevBuf* b : ctx->all_buffers()) b->release();
+  for (SceneBufs& sc : ctx->scenes) sc.release();
   for (int k = 0; k < 3; ++k)
     if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
@@ -346,123 +483,11 @@ int perch_set_observation(perch_ctx* ctx, const float* depth, int32_t W, int32_t
   ctx->tables_valid = false;
   ctx->tables_version++;
 
-  const int npx = W * H;
-  const int nblk = (npx + 255) / 256;
-  CK(ctx->depth.ensure(4 * (size_t)npx), "alloc depth");
   CK(ctx->rx.ensure(4 * (size_t)W), "alloc");
   CK(ctx->ry.ensure(4 * (size_t)H), "alloc");
-  CK(ctx->blockcnt.ensure(4 * ((size_t)nblk + 1)), "alloc");
-  CK(ctx->scan_tmp.ensure(4 * ((size_t)npx / 1024 + 2 + 4096)), "alloc");
-  CK(ctx->cam_pts.ensure(16 * (size_t)npx), "alloc");
-  CK(ctx->world_pts.ensure(16 * (size_t)npx), "alloc");
-  CK(ctx->scratch_small.ensure(64), "alloc");
-  CK(cudaMemcpyAsync(ctx->depth.p, depth, 4 * (size_t)npx, cudaMemcpyHostToDevice, ctx->stream), "copy depth");
   CK(launch_rays(c, ctx->rx.as<float>(), ctx->ry.as<float>(), ctx->stream), "rays kernel");
-  int binit[10] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN, INT_MAX, INT_MAX, INT_MIN, INT_MIN};
-  int* bounds = ctx->scratch_small.as<int>();
-  CK(cudaMemcpyAsync(bounds, binit, sizeof binit, cudaMemcpyHostToDevice, ctx->stream), "copy");
-  int* offs = ctx->blockcnt.as<int>();
-  CK(ctx->blockoff.ensure(4 * ((size_t)nblk + 1)), "alloc");
-  CK(launch_obs_count(ctx->depth.as<float>(), W, H, offs, ctx->stream), "obs count kernel");
-  CK(launch_exclusive_scan(offs, ctx->blockoff.as<int>(), nblk, ctx->scan_tmp.as<int>(), ctx->stream), "scan");
-  CK(launch_obs_write(ctx->depth.as<float>(), c, ctx->rx.as<float>(), ctx->ry.as<float>(), ctx->blockoff.as<int>(),
-                      ctx->cam_pts.as<float4>(), ctx->world_pts.as<float4>(), bounds, ctx->stream),
-     "obs write kernel");
-  int hb[11];
-  CK(cudaMemcpyAsync(hb, bounds, 10 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "copy");
-  CK(cudaMemcpyAsync(hb + 10, ctx->blockoff.as<int>() + nblk, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
-     "copy");
-  CK(cudaStreamSynchronize(ctx->stream), "observation sync");
-  const int n = hb[10];
-  ObsIndex& o = ctx->obs;
-  std::memset(&o, 0, sizeof o);
-  o.n = n;
-  if (n > 0) {
-    float lo[3], hi[3], wlo[2], whi[2];
-    for (int k = 0; k < 3; ++k) {
-      lo[k] = ordered_to_float(hb[k]);
-      hi[k] = ordered_to_float(hb[3 + k]);
-    }
-    for (int k = 0; k < 2; ++k) {
-      wlo[k] = ordered_to_float(hb[6 + k]);
-      whi[k] = ordered_to_float(hb[8 + k]);
-    }
-    // 3D camera-frame grid, cells >= 1.02 delta (Eq. (1) neighbourhood = 3x3x3)
-    double h = 1.02 * (double)delta;
-    long long cells;
-    int dims[3];
-    for (;;) {
-      cells = 1;
-      for (int k = 0; k < 3; ++k) {
-        dims[k] = (int)std::floor(((double)hi[k] - lo[k]) / h) + 3;
-        cells *= dims[k];
-      }
-      if (cells <= (16LL << 20)) break;
-      h *= 1.25;
-    }
-    o.g3x = (float)(lo[0] - h);
-    o.g3y = (float)(lo[1] - h);
-    o.g3z = (float)(lo[2] - h);
-    o.inv3 = (float)(1.0 / h);
-    o.n3x = dims[0];
-    o.n3y = dims[1];
-    o.n3z = dims[2];
-    // 2D world grid for V(O) candidates
-    double g2 = 0.01;
-    int d2[2];
-    for (;;) {
-      for (int k = 0; k < 2; ++k) d2[k] = (int)std::floor(((double)whi[k] - wlo[k]) / g2) + 3;
-      if ((long long)d2[0] * d2[1] <= (4LL << 20)) break;
-      g2 *= 1.5;
-    }
-    o.g2x = (float)(wlo[0] - g2);
-    o.g2y = (float)(wlo[1] - g2);
-    o.inv2 = (float)(1.0 / g2);
-    o.n2x = d2[0];
-    o.n2y = d2[1];
-    const long long c2 = (long long)d2[0] * d2[1];
-    const long long cmax = std::max(cells, c2);
-    CK(ctx->keys.ensure(4 * (size_t)n), "alloc");
-    CK(ctx->counts.ensure(4 * ((size_t)cmax + 1)), "alloc");
-    CK(ctx->cursor.ensure(4 * ((size_t)cmax + 1)), "alloc");
-    CK(ctx->start3.ensure(4 * ((size_t)cells + 1)), "alloc");
-    CK(ctx->start2.ensure(4 * ((size_t)c2 + 1)), "alloc");
-    CK(ctx->obs3.ensure(16 * (size_t)n), "alloc");
-    CK(ctx->dil3.ensure(4 * ((size_t)cells / 32 + 1)), "alloc");
-    CK(ctx->world2.ensure(16 * (size_t)n), "alloc");
-    CK(ctx->cam2.ensure(16 * (size_t)n), "alloc");
-    CK(ctx->scan_tmp.ensure(4 * ((size_t)cmax / 1024 + 2)), "alloc");
-    // bucket the camera-frame cloud
-    CK(cudaMemsetAsync(ctx->counts.p, 0, 4 * (size_t)cells, ctx->stream), "memset");
-    CK(launch_grid3_keys(ctx->cam_pts.as<float4>(), n, o.g3x, o.g3y, o.g3z, o.inv3, o.n3x, o.n3y, o.n3z,
-                         ctx->keys.as<int>(), ctx->counts.as<int>(), ctx->stream), "grid3 keys");
-    CK(launch_exclusive_scan(ctx->counts.as<int>(), ctx->start3.as<int>(), (int)cells, ctx->scan_tmp.as<int>(),
-                             ctx->stream), "scan3");
-    CK(cudaMemcpyAsync(ctx->cursor.p, ctx->start3.p, 4 * (size_t)cells, cudaMemcpyDeviceToDevice, ctx->stream),
-       "copy");
-    CK(launch_scatter(ctx->keys.as<int>(), n, ctx->cursor.as<int>(), ctx->cam_pts.as<float4>(),
-                      ctx->obs3.as<float4>(), nullptr, nullptr, ctx->stream), "scatter3");
-    CK(cudaMemsetAsync(ctx->dil3.p, 0, 4 * ((size_t)cells / 32 + 1), ctx->stream), "memset");
-    CK(launch_dilate3(ctx->start3.as<int>(), o.n3x, o.n3y, o.n3z, ctx->dil3.as<uint32_t>(), ctx->stream),
-       "dilate3");
-    // bucket the world-frame cloud (with its camera-frame copy)
-    CK(cudaMemsetAsync(ctx->counts.p, 0, 4 * (size_t)c2, ctx->stream), "memset");
-    CK(launch_grid2_keys(ctx->world_pts.as<float4>(), n, o.g2x, o.g2y, o.inv2, o.n2x, o.n2y, ctx->keys.as<int>(),
-                         ctx->counts.as<int>(), ctx->stream), "grid2 keys");
-    CK(launch_exclusive_scan(ctx->counts.as<int>(), ctx->start2.as<int>(), (int)c2, ctx->scan_tmp.as<int>(),
-                             ctx->stream), "scan2");
-    CK(cudaMemcpyAsync(ctx->cursor.p, ctx->start2.p, 4 * (size_t)c2, cudaMemcpyDeviceToDevice, ctx->stream),
-       "copy");
-    CK(launch_scatter(ctx->keys.as<int>(), n, ctx->cursor.as<int>(), ctx->world_pts.as<float4>(),
-                      ctx->world2.as<float4>(), ctx->cam_pts.as<float4>(), ctx->cam2.as<float4>(), ctx->stream),
-       "scatter2");
-    o.cam3 = ctx->obs3.as<float4>();
-    o.start3 = ctx->start3.as<int>();
-    o.dil3 = ctx->dil3.as<uint32_t>();
-    o.world2 = ctx->world2.as<float4>();
-    o.cam2 = ctx->cam2.as<float4>();
-    o.start2 = ctx->start2.as<int>();
-  }
+  int brc = ctx->build_scene(0, depth);
+  if (brc != PERCH_OK) return brc;
   int rc = ctx->ensure_tables();
   if (rc != PERCH_OK) return rc;
   CK(cudaStreamSynchronize(ctx->stream), "observation index");
@@ -476,11 +501,12 @@ int perch_set_observation(perch_ctx* ctx, const float* depth, int32_t W, int32_t
 // batch arrays (no host synchronisation).
 int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const int32_t* d_plen, int n_par,
                             const int32_t* d_hp, const perch_obj* d_hyp, long long n_hyp, int K_total,
-                            perch_cost* d_out) {
+                            perch_cost* d_out, const int32_t* d_parent_scene, const int32_t* d_parent_K) {
   perch_ctx* ctx = this;
   const size_t npx = (size_t)cam.W * cam.H;
   CK(parent_z.ensure(4 * npx * std::max(n_par, 1)), "alloc parent z-buffers");
-  CK(uset.ensure(4 * (size_t)std::max(obs.n, 1) * std::max(n_par, 1)), "alloc U sets");
+  const int ustride = std::max(d_parent_scene ? max_obs : obs.n, 1);
+  CK(uset.ensure(4 * (size_t)ustride * std::max(n_par, 1)), "alloc U sets");
   CK(uset_count.ensure(4 * (size_t)std::max(n_par, 1)), "alloc");
   Batch b;
   b.parents = d_parents;
@@ -490,7 +516,11 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
   b.parent_z = parent_z.as<float>();
   b.uset = uset.as<int>();
   b.uset_count = uset_count.as<int>();
-  b.uset_stride = std::max(obs.n, 1);
+  b.uset_stride = ustride;
+  b.scenes = d_scenes.as<ObsIndex>();
+  b.n_scenes = (int)scenes.size();
+  b.parent_scene = d_parent_scene;
+  b.parent_K = d_parent_K;
   b.hyp_parent = d_hp;
   b.hyp = d_hyp;
   b.n_hyp = n_hyp;
@@ -657,6 +687,85 @@ int perch_render(perch_ctx* ctx, const perch_obj* objs, int32_t n, float* depth_
   CK(cudaMemcpyAsync(&hc, culled, 8, cudaMemcpyDeviceToHost, ctx->stream), "copy");
   CK(cudaStreamSynchronize(ctx->stream), "render");
   if (n_culled) *n_culled = (int64_t)hc;
+  return PERCH_OK;
+}
+
+
+int perch_set_scene(perch_ctx* ctx, int32_t scene, const float* depth) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (!ctx->has_obs) return ctx->fail(PERCH_E_STATE, "call perch_set_observation first (camera and delta)");
+  if (!depth || scene < 0 || scene > 65535) return ctx->fail(PERCH_E_ARG, "bad scene index or null depth");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (scene == 0) {
+    int rc = ctx->build_scene(0, depth);
+    ctx->tables_version++;
+    return rc;
+  }
+  for (int s = (int)ctx->scenes.size(); s < scene; ++s) {  // gaps: empty scenes
+    std::vector<float> empty((size_t)ctx->cam.W * ctx->cam.H, 0.0f);
+    int rc = ctx->build_scene(s, empty.data());
+    if (rc != PERCH_OK) return rc;
+  }
+  int rc = ctx->build_scene(scene, depth);
+  ctx->tables_version++;
+  return rc;
+}
+
+int perch_eval_successors_multi(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride,
+                                const int32_t* parent_len, const int32_t* parent_scene, const int32_t* parent_K,
+                                int32_t n_par, const int32_t* hyp_parent, const perch_obj* hyp, int64_t n_hyp,
+                                perch_cost* out) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (!ctx->has_obs) return ctx->fail(PERCH_E_STATE, "set an observation first");
+  if (n_hyp < 0 || n_hyp > 0x7fffffffLL) return ctx->fail(PERCH_E_ARG, "n_hyp out of range");
+  if (n_hyp == 0) return PERCH_OK;
+  if (!parent_len || !parent_scene || !parent_K || !hyp_parent || !hyp || !out || n_par < 1 || parent_stride < 0 ||
+      (parent_stride > 0 && !parents))
+    return ctx->fail(PERCH_E_ARG, "null pointer or bad sizes");
+  if (n_par > 65535 || (long long)n_par * std::max(parent_stride, 1) > 65535)
+    return ctx->fail(PERCH_E_ARG, "too many parents in one batch (n_par x stride <= 65535)");
+  for (int i = 0; i < n_par; ++i) {
+    if (parent_scene[i] < 0 || parent_scene[i] >= (int)ctx->scenes.size())
+      return ctx->fail(PERCH_E_ARG, "parent %d: scene %d not set", i, parent_scene[i]);
+    if (parent_K[i] < 1 || parent_len[i] < 0 || parent_len[i] > parent_stride || parent_len[i] >= parent_K[i])
+      return ctx->fail(PERCH_E_ARG, "parent %d: length %d / K %d inconsistent", i, parent_len[i], parent_K[i]);
+    for (int k = 0; k < parent_len[i]; ++k) {
+      int rc = check_obj(ctx, parents[(long long)i * parent_stride + k], "parent object", i);
+      if (rc) return rc;
+    }
+  }
+  for (long long h = 0; h < n_hyp; ++h) {
+    if (hyp_parent[h] < 0 || hyp_parent[h] >= n_par)
+      return ctx->fail(PERCH_E_ARG, "hypothesis %lld: parent %d out of range", h, hyp_parent[h]);
+    int rc = check_obj(ctx, hyp[h], "hypothesis", h);
+    if (rc) return rc;
+  }
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const size_t pbytes = sizeof(perch_obj) * std::max<size_t>((size_t)n_par * parent_stride, 1);
+  CK(ctx->b_parents.ensure(pbytes), "alloc");
+  CK(ctx->b_plen.ensure(12 * (size_t)n_par), "alloc");  // lengths, scenes, K
+  CK(ctx->b_hp.ensure(4 * (size_t)n_hyp), "alloc");
+  CK(ctx->b_hyp.ensure(sizeof(perch_obj) * (size_t)n_hyp), "alloc");
+  CK(ctx->b_out.ensure(sizeof(perch_cost) * (size_t)n_hyp), "alloc");
+  int32_t* d_plen = ctx->b_plen.as<int32_t>();
+  if (parent_stride > 0)
+    CK(cudaMemcpyAsync(ctx->b_parents.p, parents, sizeof(perch_obj) * (size_t)n_par * parent_stride,
+                       cudaMemcpyHostToDevice, ctx->stream), "copy parents");
+  CK(cudaMemcpyAsync(d_plen, parent_len, 4 * (size_t)n_par, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  CK(cudaMemcpyAsync(d_plen + n_par, parent_scene, 4 * (size_t)n_par, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  CK(cudaMemcpyAsync(d_plen + 2 * n_par, parent_K, 4 * (size_t)n_par, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  CK(cudaMemcpyAsync(ctx->b_hp.p, hyp_parent, 4 * (size_t)n_hyp, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  CK(cudaMemcpyAsync(ctx->b_hyp.p, hyp, sizeof(perch_obj) * (size_t)n_hyp, cudaMemcpyHostToDevice, ctx->stream),
+     "copy");
+  int rc = ctx->enqueue_eval(ctx->b_parents.as<perch_obj>(), parent_stride, d_plen, n_par, ctx->b_hp.as<int32_t>(),
+                             ctx->b_hyp.as<perch_obj>(), n_hyp, 1, ctx->b_out.as<perch_cost>(), d_plen + n_par,
+                             d_plen + 2 * n_par);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(out, ctx->b_out.p, sizeof(perch_cost) * (size_t)n_hyp, cudaMemcpyDeviceToHost, ctx->stream),
+     "copy results");
+  CK(cudaStreamSynchronize(ctx->stream), "eval");
   return PERCH_OK;
 }
 

@@ -33,6 +33,15 @@ struct GraphKey {
   long long version;
 };
 
+// One scene's observed cloud and its indices (device buffers).
+struct SceneBufs {
+  DevBuf start3, start2, obs3, world2, cam2, dil3;
+  perch::ObsIndex idx{};
+  void release() {
+    for (DevBuf* b : {&start3, &start2, &obs3, &world2, &cam2, &dil3}) b->release();
+  }
+};
+
 struct perch_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -53,7 +62,10 @@ struct perch_ctx {
   perch::Camera cam{};
   perch::ObsIndex obs{};
   DevBuf depth, rx, ry, blockcnt, blockoff, scan_tmp, cam_pts, world_pts, keys, counts, cursor;
-  DevBuf start3, start2, obs3, world2, cam2, dil3, scratch_small;
+  DevBuf scratch_small;
+  std::vector<SceneBufs> scenes;  // scene 0: perch_set_observation; others: perch_set_scene
+  DevBuf d_scenes;                // ObsIndex per scene
+  int max_obs = 0;                // largest cloud over the scenes
 
   // camera-frame pose tables and the screen box of every (mesh, pose)
   DevBuf yaw_mats, pose_off, vtab, pose_bbox;
@@ -81,7 +93,7 @@ struct perch_ctx {
 
   std::vector<DevBuf*> all_buffers() {
     return {&meshes, &chunk_verts, &chunk_info, &chunk_tris, &yaw_mats, &pose_off, &vtab, &xs, &ys, &cs, &depth, &rx, &ry, &blockcnt, &blockoff,
-            &scan_tmp, &cam_pts, &world_pts, &keys, &counts, &cursor, &start3, &start2, &obs3, &world2, &cam2, &dil3,
+            &scan_tmp, &cam_pts, &world_pts, &keys, &counts, &cursor, &d_scenes,
             &scratch_small, &pose_bbox, &parent_z, &uset, &uset_count, &b_parents, &b_plen, &b_hp, &b_hyp,
             &b_out, &g_hist, &g_off, &g_cursor, &g_order, &g_next};
   }
@@ -90,6 +102,8 @@ struct perch_ctx {
   int cuda(cudaError_t e, const char* what);
   perch::Geometry geometry() const;
   int ensure_tables();
+  int build_scene(int s, const float* depth_host);
   int enqueue_eval(const perch_obj* d_parents, int parent_stride, const int32_t* d_plen, int n_par,
-                   const int32_t* d_hp, const perch_obj* d_hyp, long long n_hyp, int K_total, perch_cost* d_out);
+                   const int32_t* d_hp, const perch_obj* d_hyp, long long n_hyp, int K_total, perch_cost* d_out,
+                   const int32_t* d_parent_scene = nullptr, const int32_t* d_parent_K = nullptr);
 };

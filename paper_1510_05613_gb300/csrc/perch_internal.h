@@ -92,6 +92,11 @@ struct Batch {
   int K_total;
   perch_cost* out;
   int tile_w, tile_h;
+  // several scenes in one batch (nullable: every parent in scene 0 with K_total)
+  const ObsIndex* scenes;       // device array, one observation index per scene
+  int n_scenes;
+  const int32_t* parent_scene;  // scene of each parent
+  const int32_t* parent_K;      // objects in a complete scene, per parent
 };
 
 // kernels.cu launchers (all asynchronous on `s`)

@@ -604,10 +604,14 @@ cudaError_t launch_render_parents(const Camera& cam, const Geometry& g, const Ba
 // U set of a parent one object short of a complete scene:
 // U = {q in I - V_{K-1} : q unexplained by R_{K-1}}; then for the last object
 // O_K, residual(K) = #{q in U : q not in V(O_K), q unexplained by dR_K}.
-__global__ void k_uset(Camera cam, Geometry g, ObsIndex obs, Batch b) {
+__global__ void k_uset(Camera cam, Geometry g, ObsIndex obs0, Batch b) {
   const int p = blockIdx.y;
   const int plen = b.parent_len[p];
-  if (plen + 1 != b.K_total || plen > b.parent_stride) return;
+  const int K_total = b.parent_K ? b.parent_K[p] : b.K_total;
+  if (plen + 1 != K_total || plen > b.parent_stride) return;
+  const int scene = b.parent_scene ? b.parent_scene[p] : 0;
+  if (b.parent_scene && (scene < 0 || scene >= b.n_scenes)) return;
+  const ObsIndex& obs = b.parent_scene ? b.scenes[scene] : obs0;
   const int k = blockIdx.x * 256 + threadIdx.x;
   if (k >= obs.n) return;
   const float4 qw = obs.world2[k];
@@ -639,9 +643,10 @@ __global__ void k_uset(Camera cam, Geometry g, ObsIndex obs, Batch b) {
 
 cudaError_t launch_uset(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
                         cudaStream_t s) {
-  if (b.n_par == 0 || obs.n == 0) return cudaSuccess;
+  const int n_max = b.parent_scene ? b.uset_stride : obs.n;  // the largest cloud of the batch's scenes
+  if (b.n_par == 0 || n_max == 0) return cudaSuccess;
   if (b.n_par > 65535) return cudaErrorInvalidValue;
-  dim3 grid((obs.n + 255) / 256, b.n_par);
+  dim3 grid((n_max + 255) / 256, b.n_par);
   k_uset<<<grid, 256, 0, s>>>(cam, g, obs, b);
   return cudaGetLastError();
 }
@@ -763,7 +768,7 @@ __device__ __forceinline__ void raster_box(int2 a, int2 b, int2 c, int A, int px
 // values are far below 2^31.
 struct EvalShared {
   uint64_t* bar;   // [0]: vertex slice, [1]: triangle list
-  int* cnt;        // viol, n_new, culled, djr, djo, resid
+  int* cnt;        // viol, n_new, culled, djr, djo, resid, n_vol
   int* qn;         // queued larger triangles
   unsigned char* dyn;
   uint32_t pv, pt;  // parity of the next phase of each barrier
@@ -773,9 +778,9 @@ struct EvalShared {
 // persist across hypotheses (their phase parities are in sh). Returns false
 // if a bounded wait gave up (the record then carries kFlagTimeout and the
 // barriers must not be used again).
-template <int NT>
-__device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
-                         EvalShared& sh) {
+template <int NT, bool MULTI>
+__device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, const ObsIndex& obs0, const Batch& b,
+                         EvalShared& sh, ObsIndex* s_obs) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint64_t* s_bar = sh.bar;
@@ -787,15 +792,21 @@ __device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, cons
   bool badidx = pid < 0 || pid >= b.n_par || !obj_ok(g, o);
   const int plen = badidx ? 0 : b.parent_len[pid];
   badidx = badidx || plen < 0 || plen > b.parent_stride;
+  const int scene = (badidx || !b.parent_scene) ? 0 : b.parent_scene[pid];
+  const int K_total = (badidx || !b.parent_K) ? b.K_total : b.parent_K[pid];
+  badidx = badidx || (b.parent_scene && (scene < 0 || scene >= b.n_scenes));
   const int4 bb = badidx ? make_int4(0, 0, 0, 0)
                          : g.pose_bbox[(((long long)o.mesh * g.nx + o.ix) * g.ny + o.iy) * g.n_yaw + o.iyaw];
   if (badidx || bb.z > b.tile_w || bb.w > b.tile_h) {
     if (tid == 0) {
-      perch_cost r = {0, 0, 0, 0, 0, kFlagBadIndex};
+      perch_cost r = {0, 0, 0, 0, 0, kFlagBadIndex, 0};
       b.out[h] = r;
     }
     return true;
   }
+  if (MULTI && tid < (int)(sizeof(ObsIndex) / 4))  // this scene's index, read from shared memory below
+    reinterpret_cast<int*>(s_obs)[tid] = reinterpret_cast<const int*>(&b.scenes[scene])[tid];
+  const ObsIndex& obs = MULTI ? *s_obs : obs0;
   float4* vbuf = reinterpret_cast<float4*>(smem);
   uint32_t* tbuf = reinterpret_cast<uint32_t*>(vbuf + kChunkMaxVerts);
   uint32_t* sXY = tbuf + kChunkMaxTris;
@@ -817,7 +828,7 @@ __device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, cons
     for (int lx = lane; lx < tw; lx += 32) tile[ly * tw + lx] = 0u;  // 1/z = 0: empty
   for (int i = tid; i < tw; i += NT) rxs[i] = g.rx[bb.x + i];
   for (int i = tid; i < th; i += NT) rys[i] = g.ry[bb.y + i];
-  if (tid < 6) s_cnt[tid] = 0;
+  if (tid < 7) s_cnt[tid] = 0;
 
   // ---- render the new object
   const float ox = g.xs[o.ix], oy = g.ys[o.iy];
@@ -930,7 +941,7 @@ __device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, cons
     if (v_pending) mbar_wait(&s_bar[0], pv);
     if (t_pending) mbar_wait(&s_bar[1], pt);
     if (tid == 0) {
-      perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout};
+      perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout, 0};
       b.out[h] = r;
     }
     return false;
@@ -972,7 +983,7 @@ __device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, cons
   const uint32_t flags = s_cnt[2] ? PERCH_FLAG_CULLED : 0u;
   if (s_cnt[0] > 0) {
     if (tid == 0) {
-      perch_cost r = {0, 0, 0, s_cnt[0], s_cnt[1], flags | PERCH_FLAG_INVALID};
+      perch_cost r = {0, 0, 0, s_cnt[0], s_cnt[1], flags | PERCH_FLAG_INVALID, 0};
       b.out[h] = r;
     }
     __syncthreads();  // s_cnt is reset by the next hypothesis
@@ -992,7 +1003,7 @@ __device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, cons
   }
 
   // ---- dJ_o: observed points inside V(O) with no dR point within delta
-  int djo = 0;
+  int djo = 0, nvol = 0;
   if (obs.n > 0) {
     const float r = sqrtf(m.vol_r2) * 1.001f + 1e-6f;
     const int cx0 = max(cell_of(ox - r, obs.g2x, obs.inv2, obs.n2x) - 1, 0);
@@ -1006,6 +1017,13 @@ __device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, cons
           const float4 qw = obs.world2[k];
           if (!in_volume(qw, ox, oy, m.vol_r2, m.vol_zlo, m.vol_zhi)) continue;
           if (!explained_by_tile(cam, obs.cam2[k], tile, rxs, rys, bb)) djo++;
+          bool in_parent = false;  // already inside an assigned volume?
+          for (int j = 0; j < plen && !in_parent; ++j) {
+            const perch_obj po = b.parents[(long long)pid * b.parent_stride + j];
+            const DevMesh pm = g.meshes[po.mesh];
+            in_parent = in_volume(qw, g.xs[po.ix], g.ys[po.iy], pm.vol_r2, pm.vol_zlo, pm.vol_zhi);
+          }
+          if (!in_parent) nvol++;
         }
       }
     }
@@ -1013,7 +1031,7 @@ __device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, cons
 
   // ---- residual(K) on edges into the last level
   int resid = 0;
-  if (plen + 1 == b.K_total) {
+  if (plen + 1 == K_total) {
     const int nu = b.uset_count[pid];
     const int* U = b.uset + (size_t)pid * b.uset_stride;
     for (int k = tid; k < nu; k += NT) {
@@ -1026,14 +1044,16 @@ __device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, cons
   djr = warp_sum(djr);
   djo = warp_sum(djo);
   resid = warp_sum(resid);
+  nvol = warp_sum(nvol);
   if (lane == 0) {
     if (djr) atomicAdd(&s_cnt[3], djr);
     if (djo) atomicAdd(&s_cnt[4], djo);
     if (resid) atomicAdd(&s_cnt[5], resid);
+    if (nvol) atomicAdd(&s_cnt[6], nvol);
   }
   __syncthreads();
   if (tid == 0) {
-    perch_cost r = {s_cnt[3], s_cnt[4], s_cnt[5], 0, s_cnt[1], flags};
+    perch_cost r = {s_cnt[3], s_cnt[4], s_cnt[5], 0, s_cnt[1], flags, s_cnt[6]};
     b.out[h] = r;
   }
   __syncthreads();  // s_cnt and the tile are reused by the next hypothesis
@@ -1050,11 +1070,12 @@ struct EvalGroup {
   int* next;          // device counter, zero before the launch
 };
 
-template <int NT>
+template <int NT, bool MULTI>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_eval(Camera cam, Geometry g, ObsIndex obs, Batch b, EvalGroup grp) {
   extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(16) ObsIndex s_obs;
   __shared__ __align__(8) uint64_t s_bar[2];
-  __shared__ int s_cnt[6];
+  __shared__ int s_cnt[7];
   __shared__ int s_qn;
   __shared__ int s_item;
   if (threadIdx.x == 0) {
@@ -1072,7 +1093,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_eval(Camera cam, Geometry g, 
     __syncthreads();
     if (item >= count) break;
     const long long h = grp.order ? grp.order[offset + item] : item;
-    if (!eval_one<NT>(h, cam, g, obs, b, sh)) break;
+    if (!eval_one<NT, MULTI>(h, cam, g, obs, b, sh, &s_obs)) break;
   }
 }
 
@@ -1105,20 +1126,21 @@ cudaError_t launch_group_by_mesh(const perch_obj* hyp, long long n, int n_mesh, 
   return cudaGetLastError();
 }
 
-template <int NT>
+template <int NT, bool MULTI>
 static cudaError_t launch_group_t(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
                                   const EvalGroup& grp, long long max_items, int sm_count, cudaStream_t s) {
   const size_t smem = eval_smem_bytes(b.tile_w, b.tile_h);
-  cudaError_t e = cudaFuncSetAttribute(k_eval<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = k_eval<NT, MULTI>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval<NT>, NT, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)per_sm * sm_count;
   if (grid > max_items) grid = max_items;
   if (grid < 1) grid = 1;
-  k_eval<NT><<<(unsigned)grid, NT, smem, s>>>(cam, g, obs, b, grp);
+  kern<<<(unsigned)grid, NT, smem, s>>>(cam, g, obs, b, grp);
   return cudaGetLastError();
 }
 
@@ -1129,10 +1151,14 @@ cudaError_t launch_eval_group(const Camera& cam, const Geometry& g, const ObsInd
                               int threads, int sm_count, cudaStream_t s) {
   if (max_items <= 0) return cudaSuccess;
   EvalGroup grp{order, offset, count, next};
+  const bool multi = b.parent_scene != nullptr;
   switch (threads) {
-    case 128: return launch_group_t<128>(cam, g, obs, b, grp, max_items, sm_count, s);
-    case 512: return launch_group_t<512>(cam, g, obs, b, grp, max_items, sm_count, s);
-    default: return launch_group_t<256>(cam, g, obs, b, grp, max_items, sm_count, s);
+    case 128: return multi ? launch_group_t<128, true>(cam, g, obs, b, grp, max_items, sm_count, s)
+                           : launch_group_t<128, false>(cam, g, obs, b, grp, max_items, sm_count, s);
+    case 512: return multi ? launch_group_t<512, true>(cam, g, obs, b, grp, max_items, sm_count, s)
+                           : launch_group_t<512, false>(cam, g, obs, b, grp, max_items, sm_count, s);
+    default: return multi ? launch_group_t<256, true>(cam, g, obs, b, grp, max_items, sm_count, s)
+                          : launch_group_t<256, false>(cam, g, obs, b, grp, max_items, sm_count, s);
   }
 }
 

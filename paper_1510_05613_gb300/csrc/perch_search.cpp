@@ -10,12 +10,13 @@
 // found so far, and the search ends only when the smallest open g exceeds it,
 // so batching never changes the answer (edge costs are non-negative). Among
 // goals of minimum cost the lexicographically smallest sorted key is returned.
+//
+// perch_search_multi runs one such search per scene and packs the expansions
+// of all unfinished scenes into shared evaluation launches.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
-#include <functional>
 #include <limits>
-#include <queue>
 #include <unordered_map>
 #include <vector>
 
@@ -24,6 +25,8 @@
 namespace {
 
 using Key = std::vector<uint64_t>;
+using Clock = std::chrono::steady_clock;
+constexpr int64_t kInf = std::numeric_limits<int64_t>::max();
 
 uint64_t pack(const perch_obj& o) {
   return ((uint64_t)o.mesh << 48) | ((uint64_t)(uint16_t)o.ix << 32) | ((uint64_t)(uint16_t)o.iy << 16) |
@@ -54,6 +57,12 @@ struct State {
   Key key;
   int64_t g;
   bool closed;
+  int64_t h_overlap;  // observed points outside the volumes of the state's objects
+};
+
+struct HEntry {  // entry of an inadmissible queue
+  int64_t h, g;
+  int idx;
 };
 
 struct OpenEntry {
@@ -61,143 +70,342 @@ struct OpenEntry {
   int idx;
 };
 
+// One scene's search: uniform-cost search for w = 1 without heuristics,
+// Focal-MHA* otherwise (Sec. IV-B, Alg. 1): the anchor queue is keyed by
+// g + h0 with h0 = 0; states whose g is within w times the smallest anchor
+// key (the focal set) are also ordered by each inadmissible heuristic
+// (h_depth = K - |s|, h_overlap = |I| - |I n V_j|, Sec. IV-C), and every round
+// expands states from the anchor and from each heuristic queue. The search
+// stops once its best goal has g <= w * (smallest anchor key), which is at
+// most w * OPT (Theorem 2).
+struct SceneSearch {
+  int scene = 0, K = 0;
+  std::vector<int> multiset;
+  std::vector<State> states;
+  std::unordered_map<Key, int, KeyHash> index;
+  std::vector<OpenEntry> heap;  // anchor
+  int64_t best_g = kInf;
+  Key best_key;
+  int64_t expansions = 0, successors = 0;
+  bool done = false;
+  double seconds = 0.0;
+  double w = 1.0;
+  int heur = 0;                        // bit 0: h_depth, bit 1: h_overlap
+  std::vector<OpenEntry> pending;      // generated, not yet in the focal set (min g)
+  std::vector<HEntry> hq[2];           // focal states ordered by each heuristic
+  bool focal() const { return w > 1.0 || heur != 0; }
+  int64_t hval(int which, int idx) const {
+    return which == 0 ? (int64_t)(K - (int)states[idx].key.size()) : states[idx].h_overlap;
+  }
+  static bool hworse(const HEntry& a, const HEntry& b) {
+    if (a.h != b.h) return a.h > b.h;
+    if (a.g != b.g) return a.g > b.g;
+    return a.idx > b.idx;
+  }
+  static bool gworse(const OpenEntry& a, const OpenEntry& b) {
+    if (a.g != b.g) return a.g > b.g;
+    return a.idx > b.idx;
+  }
+  void add_open(int64_t g, int idx) {
+    push(g, idx);
+    if (focal()) {
+      pending.push_back(OpenEntry{g, idx});
+      std::push_heap(pending.begin(), pending.end(), gworse);
+    }
+  }
+  bool stale(const OpenEntry& e) const { return states[e.idx].closed || e.g > states[e.idx].g; }
+
+  bool worse(const OpenEntry& a, const OpenEntry& b) const {
+    if (a.g != b.g) return a.g > b.g;
+    return states[a.idx].key > states[b.idx].key;
+  }
+  void push(int64_t g, int idx) {
+    heap.push_back(OpenEntry{g, idx});
+    std::push_heap(heap.begin(), heap.end(), [this](const OpenEntry& a, const OpenEntry& b) { return worse(a, b); });
+  }
+  void init(int sc, int k, const uint16_t* ms, double w_, int heur_, int64_t n_obs) {
+    scene = sc;
+    K = k;
+    w = w_;
+    heur = heur_;
+    multiset.assign(ms, ms + k);
+    states.push_back(State{Key{}, 0, false, n_obs});
+    index[Key{}] = 0;
+    add_open(0, 0);
+  }
+  // Focal-MHA* round: up to B states from the anchor and from each queue
+  void pop_focal(int B, std::vector<int>& out) {
+    auto cmp = [this](const OpenEntry& a, const OpenEntry& b) { return worse(a, b); };
+    while (!heap.empty() && stale(heap.front())) {
+      std::pop_heap(heap.begin(), heap.end(), cmp);
+      heap.pop_back();
+    }
+    if (heap.empty()) {
+      done = true;
+      return;
+    }
+    const int64_t f0 = heap.front().g;
+    const double bound = w * (double)f0;
+    if (best_g != kInf && (double)best_g <= bound) {  // within w * OPT
+      done = true;
+      return;
+    }
+    while (!pending.empty() && (double)pending.front().g <= bound) {  // admit into the focal set
+      const OpenEntry e = pending.front();
+      std::pop_heap(pending.begin(), pending.end(), gworse);
+      pending.pop_back();
+      if (stale(e)) continue;
+      for (int q = 0; q < 2; ++q)
+        if (heur & (1 << q)) {
+          hq[q].push_back(HEntry{hval(q, e.idx), e.g, e.idx});
+          std::push_heap(hq[q].begin(), hq[q].end(), hworse);
+        }
+    }
+    for (int n = 0; n < B && !heap.empty();) {  // anchor
+      const OpenEntry top = heap.front();
+      std::pop_heap(heap.begin(), heap.end(), cmp);
+      heap.pop_back();
+      if (stale(top) || top.g > best_g) continue;
+      states[top.idx].closed = true;
+      out.push_back(top.idx);
+      ++n;
+    }
+    for (int q = 0; q < 2; ++q) {
+      if (!(heur & (1 << q))) continue;
+      for (int n = 0; n < B && !hq[q].empty();) {
+        const HEntry top = hq[q].front();
+        std::pop_heap(hq[q].begin(), hq[q].end(), hworse);
+        hq[q].pop_back();
+        State& st = states[top.idx];
+        if (st.closed || top.g > st.g || top.g > best_g) continue;
+        st.closed = true;
+        out.push_back(top.idx);
+        ++n;
+      }
+    }
+    if (out.empty() && heap.empty()) done = true;
+  }
+  // pop up to B expandable states; marks the search done when none is left
+  void pop(int B, std::vector<int>& out) {
+    out.clear();
+    if (focal()) {
+      pop_focal(B, out);
+      return;
+    }
+    auto cmp = [this](const OpenEntry& a, const OpenEntry& b) { return worse(a, b); };
+    while (!heap.empty() && (int)out.size() < B) {
+      const OpenEntry top = heap.front();
+      if (top.g > best_g) break;
+      std::pop_heap(heap.begin(), heap.end(), cmp);
+      heap.pop_back();
+      State& s = states[top.idx];
+      if (s.closed || top.g > s.g) continue;  // stale entry
+      s.closed = true;
+      out.push_back(top.idx);
+    }
+    if (out.empty() && (heap.empty() || heap.front().g > best_g)) done = true;
+  }
+  // distinct unplaced types of a state (the branching of Sec. IV-B)
+  std::vector<int> remaining(const Key& key) const {
+    std::vector<int> rem = multiset;
+    for (uint64_t k : key) {
+      auto it = std::find(rem.begin(), rem.end(), (int)(k >> 48));
+      if (it != rem.end()) rem.erase(it);
+    }
+    std::sort(rem.begin(), rem.end());
+    rem.erase(std::unique(rem.begin(), rem.end()), rem.end());
+    return rem;
+  }
+  void absorb(int pidx, const perch_obj& h, const perch_cost& r) {
+    if (r.viol > 0) return;  // occludes the parent: not a successor (Eq. (3))
+    const int64_t ng = states[pidx].g + (int64_t)r.djr + r.djo + r.resid;
+    if (ng > best_g) return;
+    Key ck = states[pidx].key;
+    ck.insert(std::upper_bound(ck.begin(), ck.end(), pack(h)), pack(h));
+    if ((int)ck.size() == K) {
+      if (ng < best_g || (ng == best_g && ck < best_key)) {
+        best_g = ng;
+        best_key = ck;
+      }
+      return;
+    }
+    auto it = index.find(ck);
+    if (it == index.end()) {
+      const int idx = (int)states.size();
+      states.push_back(State{std::move(ck), ng, false, states[pidx].h_overlap - (int64_t)r.n_vol});
+      index.emplace(states[idx].key, idx);
+      add_open(ng, idx);
+    } else {
+      State& s = states[it->second];
+      if (ng < s.g) {
+        s.g = ng;
+        s.closed = false;  // a cheaper way in: reopen
+        add_open(ng, it->second);
+      }
+    }
+  }
+};
+
+struct Work {
+  int scene_slot;
+  int state;
+};
+
+// Run the searches until every one is done or a limit is reached.
+int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states, double time_limit_s,
+                 int64_t max_expansions, int64_t max_hyps_per_launch, bool multi) {
+  const auto t0 = Clock::now();
+  auto elapsed = [&]() { return std::chrono::duration<double>(Clock::now() - t0).count(); };
+  int stride = 1;
+  for (auto& s : ss) stride = std::max(stride, s.K - 1);
+  const int B = std::max(1, std::min(batch_states, 65535 / stride));
+  const int64_t per_state_max = (int64_t)ctx->nx * ctx->ny * ctx->n_yaw * ctx->n_mesh;
+  std::vector<perch_obj> parents, hyps;
+  std::vector<int32_t> plen, pscene, pK, hparent;
+  std::vector<perch_cost> out;
+  std::vector<Work> work;
+  std::vector<int> popped;
+  int64_t expansions = 0;
+  size_t rr = 0;  // round-robin start over scenes
+  while (true) {
+    bool any = false;
+    for (auto& s : ss) any |= !s.done;
+    if (!any) return PERCH_OK;
+    if ((time_limit_s > 0 && elapsed() > time_limit_s) || (max_expansions > 0 && expansions >= max_expansions))
+      return PERCH_E_TIMEOUT;
+    // gather expansions across scenes, within the launch budgets
+    work.clear();
+    int64_t budget = max_hyps_per_launch > 0 ? std::max<int64_t>(max_hyps_per_launch, per_state_max)
+                                             : (int64_t)B * per_state_max * (int64_t)ss.size();
+    for (size_t k = 0; k < ss.size() && budget > 0 && (int)work.size() < 65535 / stride; ++k) {
+      const size_t si = (rr + k) % ss.size();
+      SceneSearch& s = ss[si];
+      if (s.done) continue;
+      const int want = (int)std::max<int64_t>(1, std::min<int64_t>(B, budget / std::max<int64_t>(per_state_max, 1)));
+      s.pop(want, popped);
+      if (s.done) s.seconds = elapsed();
+      for (int idx : popped) {
+        work.push_back(Work{(int)si, idx});
+        budget -= per_state_max;
+      }
+    }
+    rr = (rr + 1) % ss.size();
+    if (work.empty()) continue;
+    parents.assign(work.size() * stride, perch_obj{0, 0, 0, 0});
+    plen.assign(work.size(), 0);
+    pscene.assign(work.size(), 0);
+    pK.assign(work.size(), 1);
+    hyps.clear();
+    hparent.clear();
+    for (size_t w = 0; w < work.size(); ++w) {
+      const SceneSearch& s = ss[work[w].scene_slot];
+      const Key& key = s.states[work[w].state].key;
+      plen[w] = (int32_t)key.size();
+      pscene[w] = s.scene;
+      pK[w] = s.K;
+      for (size_t j = 0; j < key.size(); ++j) parents[w * stride + j] = unpack(key[j]);
+      for (int m : s.remaining(key))
+        for (int ix = 0; ix < ctx->nx; ++ix)
+          for (int iy = 0; iy < ctx->ny; ++iy)
+            for (int k = 0; k < ctx->n_yaw; ++k) {
+              hyps.push_back(perch_obj{(uint16_t)m, (uint16_t)k, (int16_t)ix, (int16_t)iy});
+              hparent.push_back((int32_t)w);
+            }
+    }
+    out.resize(hyps.size());
+    const int rc = multi ? perch_eval_successors_multi(ctx, parents.data(), stride, plen.data(), pscene.data(),
+                                                       pK.data(), (int32_t)work.size(), hparent.data(),
+                                                       hyps.data(), (int64_t)hyps.size(), out.data())
+                         : perch_eval_successors(ctx, parents.data(), stride, plen.data(), (int32_t)work.size(),
+                                                 hparent.data(), hyps.data(), (int64_t)hyps.size(), ss[0].K,
+                                                 out.data());
+    if (rc != PERCH_OK) return rc;
+    expansions += (int64_t)work.size();
+    for (size_t w = 0; w < work.size(); ++w) {
+      ss[work[w].scene_slot].expansions++;
+    }
+    for (size_t h = 0; h < hyps.size(); ++h) {
+      const Work& w = work[hparent[h]];
+      SceneSearch& s = ss[w.scene_slot];
+      s.successors++;
+      s.absorb(w.state, hyps[h], out[h]);
+    }
+  }
+}
+
+void fill_result(const SceneSearch& s, int status, perch_result* res) {
+  std::memset(res, 0, sizeof *res);
+  res->cost = -1;
+  res->expansions = s.expansions;
+  res->successors = s.successors;
+  res->seconds = s.seconds;
+  if (s.best_g != kInf) {
+    res->cost = s.best_g;
+    res->n_objs = (int32_t)s.best_key.size();
+    for (size_t j = 0; j < s.best_key.size(); ++j) res->objs[j] = unpack(s.best_key[j]);
+  }
+  // w = 1: optimal; w > 1: within w times the optimum (Theorem 2)
+  res->proven_optimal = (status == PERCH_OK && s.done && s.best_g != kInf && s.w <= 1.0) ? 1 : 0;
+}
+
+int check_params(perch_ctx* ctx, const perch_search_params* prm) {
+  if (!prm || prm->K < 1 || prm->K > 16 || !prm->mesh_multiset || prm->batch_states < 1)
+    return ctx->fail(PERCH_E_ARG, "search: bad parameters");
+  if (!(prm->w >= 1.0f)) return ctx->fail(PERCH_E_ARG, "search: w must be >= 1");
+  if (prm->heuristics & ~3) return ctx->fail(PERCH_E_ARG, "search: unknown heuristic bits %d", prm->heuristics);
+  for (int i = 0; i < prm->K; ++i)
+    if (prm->mesh_multiset[i] >= ctx->n_mesh) return ctx->fail(PERCH_E_ARG, "search: mesh %d out of range", i);
+  return PERCH_OK;
+}
+
 }  // namespace
 
 extern "C" int perch_search(perch_ctx* ctx, const perch_search_params* prm, perch_result* res) {
   if (!ctx) return PERCH_E_ARG;
   ctx->err.clear();
-  if (!prm || !res || prm->K < 1 || prm->K > 16 || !prm->mesh_multiset || prm->batch_states < 1)
-    return ctx->fail(PERCH_E_ARG, "search: bad parameters");
-  if (!(prm->w >= 1.0f)) return ctx->fail(PERCH_E_ARG, "search: w must be >= 1");
+  if (!res) return ctx->fail(PERCH_E_ARG, "search: null result");
+  int rc = check_params(ctx, prm);
+  if (rc) return rc;
   if (!ctx->has_obs) return ctx->fail(PERCH_E_STATE, "set an observation first");
-  const int K = prm->K;
-  for (int i = 0; i < K; ++i)
-    if (prm->mesh_multiset[i] >= ctx->n_mesh) return ctx->fail(PERCH_E_ARG, "search: mesh %d out of range", i);
-  std::memset(res, 0, sizeof *res);
-  res->cost = -1;
-  const auto t0 = std::chrono::steady_clock::now();
-  auto elapsed = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
-
-  std::vector<State> states;
-  std::unordered_map<Key, int, KeyHash> index;
-  std::vector<OpenEntry> heap;
-  // min-heap on (g, key)
-  auto worse = [&](const OpenEntry& a, const OpenEntry& b) {
-    if (a.g != b.g) return a.g > b.g;
-    return states[a.idx].key > states[b.idx].key;
-  };
-  states.push_back(State{Key{}, 0, false});
-  index[Key{}] = 0;
-  heap.push_back(OpenEntry{0, 0});
-
-  const int64_t INF = std::numeric_limits<int64_t>::max();
-  int64_t best_g = INF;
-  Key best_key;
-  int64_t expansions = 0, successors = 0;
-  const int n_poses_per_type = ctx->nx * ctx->ny * ctx->n_yaw;
-  const int B = std::min(prm->batch_states, std::max(1, 65535 / std::max(K - 1, 1)));
-  int status = PERCH_OK;
-
-  std::vector<perch_obj> parents, hyps;
-  std::vector<int32_t> plen, hparent;
-  std::vector<perch_cost> out;
-  std::vector<int> batch;
-  while (!heap.empty()) {
-    if ((prm->time_limit_s > 0 && elapsed() > prm->time_limit_s) ||
-        (prm->max_expansions > 0 && expansions >= prm->max_expansions)) {
-      status = PERCH_E_TIMEOUT;
-      break;
-    }
-    batch.clear();
-    while (!heap.empty() && (int)batch.size() < B) {
-      const OpenEntry top = heap.front();
-      if (top.g > best_g) break;
-      std::pop_heap(heap.begin(), heap.end(), worse);
-      heap.pop_back();
-      State& s = states[top.idx];
-      if (s.closed || top.g > s.g) continue;  // stale entry
-      s.closed = true;
-      batch.push_back(top.idx);
-    }
-    if (batch.empty()) {
-      if (heap.empty() || heap.front().g > best_g) break;
-      continue;
-    }
-    // successors of the batch: distinct unplaced types x every pose (Eq. (3))
-    const int stride = std::max(K - 1, 1);
-    parents.assign((size_t)batch.size() * stride, perch_obj{0, 0, 0, 0});
-    plen.assign(batch.size(), 0);
-    hyps.clear();
-    hparent.clear();
-    for (size_t bi = 0; bi < batch.size(); ++bi) {
-      const Key& key = states[batch[bi]].key;
-      plen[bi] = (int32_t)key.size();
-      std::vector<int> remaining(prm->mesh_multiset, prm->mesh_multiset + K);
-      for (size_t j = 0; j < key.size(); ++j) {
-        parents[bi * stride + j] = unpack(key[j]);
-        auto it = std::find(remaining.begin(), remaining.end(), (int)(key[j] >> 48));
-        if (it != remaining.end()) remaining.erase(it);
-      }
-      std::sort(remaining.begin(), remaining.end());
-      remaining.erase(std::unique(remaining.begin(), remaining.end()), remaining.end());
-      for (int m : remaining)
-        for (int ix = 0; ix < ctx->nx; ++ix)
-          for (int iy = 0; iy < ctx->ny; ++iy)
-            for (int k = 0; k < ctx->n_yaw; ++k) {
-              hyps.push_back(perch_obj{(uint16_t)m, (uint16_t)k, (int16_t)ix, (int16_t)iy});
-              hparent.push_back((int32_t)bi);
-            }
-    }
-    (void)n_poses_per_type;
-    out.resize(hyps.size());
-    int rc = perch_eval_successors(ctx, parents.data(), stride, plen.data(), (int32_t)batch.size(), hparent.data(),
-                                   hyps.data(), (int64_t)hyps.size(), K, out.data());
-    if (rc != PERCH_OK) return rc;
-    expansions += (int64_t)batch.size();
-    successors += (int64_t)hyps.size();
-    for (size_t h = 0; h < hyps.size(); ++h) {
-      const perch_cost& r = out[h];
-      if (r.viol > 0) continue;  // occludes the parent: not a successor
-      const int pidx = batch[hparent[h]];
-      const int64_t ng = states[pidx].g + (int64_t)r.djr + r.djo + r.resid;
-      if (ng > best_g) continue;
-      Key ck = states[pidx].key;
-      ck.insert(std::upper_bound(ck.begin(), ck.end(), pack(hyps[h])), pack(hyps[h]));
-      if ((int)ck.size() == K) {
-        if (ng < best_g || (ng == best_g && ck < best_key)) {
-          best_g = ng;
-          best_key = ck;
-        }
-        continue;
-      }
-      auto it = index.find(ck);
-      if (it == index.end()) {
-        const int idx = (int)states.size();
-        states.push_back(State{std::move(ck), ng, false});
-        index.emplace(states[idx].key, idx);
-        heap.push_back(OpenEntry{ng, idx});
-        std::push_heap(heap.begin(), heap.end(), worse);
-      } else {
-        State& s = states[it->second];
-        if (ng < s.g) {
-          s.g = ng;
-          s.closed = false;  // a cheaper way in: reopen
-          heap.push_back(OpenEntry{ng, it->second});
-          std::push_heap(heap.begin(), heap.end(), worse);
-        }
-      }
-    }
-  }
-  res->expansions = expansions;
-  res->successors = successors;
-  res->seconds = elapsed();
-  if (best_g != INF) {
-    res->cost = best_g;
-    res->n_objs = (int32_t)best_key.size();
-    for (size_t j = 0; j < best_key.size(); ++j) res->objs[j] = unpack(best_key[j]);
-  }
-  res->proven_optimal = (status == PERCH_OK && best_g != INF) ? 1 : 0;
+  std::vector<SceneSearch> ss(1);
+  ss[0].init(0, prm->K, prm->mesh_multiset, prm->w, prm->heuristics, ctx->scenes.empty() ? 0 : ctx->scenes[0].idx.n);
+  const auto t0 = Clock::now();
+  const int status = run_searches(ctx, ss, prm->batch_states, prm->time_limit_s, prm->max_expansions, 0, false);
+  if (status != PERCH_OK && status != PERCH_E_TIMEOUT) return status;
+  ss[0].seconds = std::chrono::duration<double>(Clock::now() - t0).count();
+  fill_result(ss[0], status, res);
   if (status == PERCH_E_TIMEOUT) return ctx->fail(PERCH_E_TIMEOUT, "search limit reached; best so far returned");
-  if (best_g == INF) return ctx->fail(PERCH_E_RANGE, "no valid complete scene exists in the tree");
+  if (ss[0].best_g == kInf) return ctx->fail(PERCH_E_RANGE, "no valid complete scene exists in the tree");
+  return PERCH_OK;
+}
+
+extern "C" int perch_search_multi(perch_ctx* ctx, int32_t n_scenes, const int32_t* scenes,
+                                  const perch_search_params* params, int64_t max_hyps_per_launch,
+                                  perch_result* results) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (n_scenes < 1 || !scenes || !params || !results) return ctx->fail(PERCH_E_ARG, "search: bad arguments");
+  if (!ctx->has_obs) return ctx->fail(PERCH_E_STATE, "set an observation first");
+  std::vector<SceneSearch> ss(n_scenes);
+  for (int i = 0; i < n_scenes; ++i) {
+    int rc = check_params(ctx, &params[i]);
+    if (rc) return rc;
+    if (scenes[i] < 0 || scenes[i] >= (int)ctx->scenes.size())
+      return ctx->fail(PERCH_E_ARG, "search %d: scene %d not set", i, scenes[i]);
+    ss[i].init(scenes[i], params[i].K, params[i].mesh_multiset, params[i].w, params[i].heuristics,
+               ctx->scenes[scenes[i]].idx.n);
+  }
+  double tl = 0.0;
+  int64_t me = 0;
+  int B = 1;
+  for (int i = 0; i < n_scenes; ++i) {
+    tl = std::max(tl, params[i].time_limit_s);
+    me = std::max(me, params[i].max_expansions);
+    B = std::max(B, params[i].batch_states);
+  }
+  const int status = run_searches(ctx, ss, B, tl, me, std::max<int64_t>(max_hyps_per_launch, 1), true);
+  if (status != PERCH_OK && status != PERCH_E_TIMEOUT) return status;
+  for (int i = 0; i < n_scenes; ++i) fill_result(ss[i], status, &results[i]);
+  if (status == PERCH_E_TIMEOUT) return ctx->fail(PERCH_E_TIMEOUT, "search limit reached; best so far returned");
   return PERCH_OK;
 }

@@ -19,13 +19,14 @@ FLAG_CULLED, FLAG_INVALID, FLAG_BAD_INDEX = 1, 2, 1 << 31
 
 OBJ = np.dtype([("mesh", np.uint16), ("iyaw", np.uint16), ("ix", np.int16), ("iy", np.int16)])
 COST = np.dtype([("djr", np.int32), ("djo", np.int32), ("resid", np.int32), ("viol", np.int32),
-                 ("n_new", np.int32), ("flags", np.uint32)])
+                 ("n_new", np.int32), ("flags", np.uint32), ("n_vol", np.int32)])
 
 # names exported by the library (include/perch.h)
 EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_meshes", "perch_set_pose_grid",
            "perch_set_observation", "perch_eval_successors", "perch_eval_successors_dev", "perch_render",
            "perch_search", "perch_last_timing", "perch_eval_successors_noalloc", "perch_autotune",
-           "perch_eval_graph", "perch_set_threads")
+           "perch_eval_graph", "perch_set_threads", "perch_set_scene", "perch_eval_successors_multi",
+           "perch_search_multi")
 
 
 class perch_mesh(ctypes.Structure):
@@ -41,7 +42,7 @@ class perch_obj(ctypes.Structure):
 class perch_search_params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("mesh_multiset", ctypes.c_void_p), ("w", ctypes.c_float),
                 ("batch_states", ctypes.c_int32), ("time_limit_s", ctypes.c_double),
-                ("max_expansions", ctypes.c_int64)]
+                ("max_expansions", ctypes.c_int64), ("heuristics", ctypes.c_int32)]
 
 
 class perch_result(ctypes.Structure):
@@ -83,6 +84,9 @@ def load(path: str = LIB_PATH):
         "perch_eval_successors_noalloc": ([P, P, I32, P, I32, P, P, I64, I32, P], ctypes.c_int),
         "perch_autotune": ([P, I32, P], ctypes.c_int),
         "perch_set_threads": ([P, I32, I32], ctypes.c_int),
+        "perch_set_scene": ([P, I32, P], ctypes.c_int),
+        "perch_eval_successors_multi": ([P, P, I32, P, P, P, I32, P, P, I64, P], ctypes.c_int),
+        "perch_search_multi": ([P, I32, P, P, I64, P], ctypes.c_int),
         "perch_eval_graph": ([P, P, I32, P, I32, P, P, I64, I32, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -214,6 +218,41 @@ class Perch:
             hyps_t.data_ptr(), hyp_parent_t.numel(), K_total, out_t.data_ptr(),
             None if out_host is None else out_host.data_ptr()))
 
+    def perch_set_scene(self, scene: int, depth):
+        d = _c(depth, np.float32)
+        return self._check(self.lib.perch_set_scene(self.h, scene, d.ctypes.data))
+
+    def perch_eval_successors_multi(self, parents, parent_scene, parent_K, hyp_parent, hyps):
+        P, plen, stride = self.pack_parents(parents)
+        ps, pk = _c(parent_scene, np.int32), _c(parent_K, np.int32)
+        hp, h = _c(hyp_parent, np.int32), _c(hyps, OBJ)
+        out = np.zeros(len(h), COST)
+        self._check(self.lib.perch_eval_successors_multi(self.h, P.ctypes.data, stride, plen.ctypes.data,
+                                                         ps.ctypes.data, pk.ctypes.data, len(plen), _ptr(hp),
+                                                         _ptr(h), len(h), _ptr(out)))
+        return out
+
+    def perch_search_multi(self, scenes, multisets, batch_states: int = 1, max_hyps_per_launch: int = 1 << 22,
+                           time_limit_s: float = 0.0, w: float = 1.0, heuristics: int = 0):
+        n = len(scenes)
+        keep = [_c(ms, np.uint16) for ms in multisets]
+        params = (perch_search_params * n)()
+        for i, ms in enumerate(keep):
+            params[i] = perch_search_params(len(ms), ms.ctypes.data, w, batch_states, time_limit_s, 0, heuristics)
+        sc = _c(scenes, np.int32)
+        res = (perch_result * n)()
+        rc = self.lib.perch_search_multi(self.h, n, sc.ctypes.data, params, max_hyps_per_launch, res)
+        self._check(rc, ok=(PERCH_OK, PERCH_E_TIMEOUT))
+        return [self._result(res[i], PERCH_OK) for i in range(n)]
+
+    @staticmethod
+    def _result(r, rc):
+        objs = np.array([(r.objs[i].mesh, r.objs[i].iyaw, r.objs[i].ix, r.objs[i].iy) for i in range(r.n_objs)], OBJ)
+        key = tuple(sorted((int(o["mesh"]), int(o["ix"]), int(o["iy"]), int(o["iyaw"])) for o in objs))
+        return {"cost": int(r.cost), "key": key, "objs": objs, "expansions": int(r.expansions),
+                "successors": int(r.successors), "seconds": float(r.seconds),
+                "proven_optimal": bool(r.proven_optimal), "status": rc}
+
     def perch_render(self, objs):
         o = _c(objs, OBJ)
         out = np.empty((self.H, self.W), np.float32)
@@ -228,9 +267,9 @@ class Perch:
         return float(a.value), float(b.value)
 
     def perch_search(self, mesh_multiset, w: float = 1.0, batch_states: int = 8, time_limit_s: float = 0.0,
-                     max_expansions: int = 0):
+                     max_expansions: int = 0, heuristics: int = 0):
         ms = _c(mesh_multiset, np.uint16)
-        p = perch_search_params(len(ms), ms.ctypes.data, w, batch_states, time_limit_s, max_expansions)
+        p = perch_search_params(len(ms), ms.ctypes.data, w, batch_states, time_limit_s, max_expansions, heuristics)
         r = perch_result()
         rc = self.lib.perch_search(self.h, ctypes.byref(p), ctypes.byref(r))
         self._check(rc, ok=(PERCH_OK, PERCH_E_TIMEOUT))
@@ -242,5 +281,5 @@ class Perch:
 
 
 def records(out) -> np.ndarray:
-    """COST structured array -> (n, 6) int64 (djr, djo, resid, viol, n_new, flags)."""
+    """COST structured array -> (n, 7) int64 (djr, djo, resid, viol, n_new, flags, n_vol)."""
     return np.stack([out[f].astype(np.int64) for f in COST.names], 1)

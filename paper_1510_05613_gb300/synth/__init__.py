@@ -620,3 +620,24 @@ def workload_c3(scene: int = 0, grid: PoseGrid | None = None, min_occlusion: flo
             return Workload("c3", cam, meshes, grid, 0.01, gt, depth, 0.003, 0.05, seed,
                             extra={"occlusion": occ.tolist()})
     raise RuntimeError("no heavily occluded scene found")
+
+
+def workloads_c5(n_scenes: int = 256, grid: PoseGrid | None = None, cam: Camera | None = None, meshes=None,
+                 k_range=(2, 6)):
+    """Many independent scenes for concurrent search: scene s draws K uniform
+    in k_range and K distinct meshes of the eight uneven ones, poses anywhere
+    on the grid with disjoint footprints; 640x480 by default, sigma 3 mm,
+    5% dropout, delta 1 cm. Scene s is seeded with 5000 + s."""
+    cam = cam or camera_c2()
+    meshes = meshes or meshes_c3()
+    grid = grid or pose_grid(-0.49, 0.02, 50, 16)
+    out = []
+    for s in range(n_scenes):
+        seed = 5000 + s
+        u = uniform(substream(seed, 5), 16)
+        K = k_range[0] + min(int(u[0] * (k_range[1] - k_range[0] + 1)), k_range[1] - k_range[0])
+        ids = sorted(np.argsort(u[1:1 + len(meshes)])[:K].tolist())
+        gt = sample_scene(meshes, grid, ids, seed)
+        depth = observe(cam, meshes, grid, gt, 0.003, 0.05, seed)
+        out.append(Workload(f"c5/{s}", cam, meshes, grid, 0.01, gt, depth, 0.003, 0.05, seed))
+    return out

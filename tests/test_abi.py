@@ -39,8 +39,9 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_struct_layouts():
     assert ctypes.sizeof(perch.perch_obj) == 8 == perch.OBJ.itemsize
-    assert perch.COST.itemsize == 24
+    assert perch.COST.itemsize == 28
     assert ctypes.sizeof(perch.perch_mesh) == 40
+    assert ctypes.sizeof(perch.perch_search_params) == 48
     assert ctypes.sizeof(perch.perch_result) == 16 * 8 + 4 + 4 + 8 * 4 + 4 + 4
 
 

@@ -121,7 +121,7 @@ def test_c2_bench_launch_sampled(c2):
     from bench import c2_batch
     parents, hp, hyps = c2_batch(wl)
     got = _recs(p.perch_eval_successors(parents, hp, hyps, wl.K))
-    assert got.shape == (len(hyps), 6)
+    assert got.shape == (len(hyps), 7)
     # invariants on every record
     inval = got[:, 3] > 0
     assert np.all((got[:, 5] & 2 > 0) == inval)
@@ -182,11 +182,11 @@ def test_device_pointer_entry_point(c1):
     tplen = torch.from_numpy(plen).to(dev)
     thp = torch.zeros(len(hyps), dtype=torch.int32, device=dev)
     th = torch.from_numpy(np.ascontiguousarray(hyps).view(np.int16).reshape(-1).copy()).to(dev)
-    tout = torch.zeros(len(hyps) * 6, dtype=torch.int32, device=dev)
+    tout = torch.zeros(len(hyps) * 7, dtype=torch.int32, device=dev)
     torch.cuda.synchronize()
     p.perch_eval_successors_dev(tP, stride, tplen, thp, th, 2, tout)
     torch.cuda.synchronize()
-    got = tout.cpu().numpy().reshape(-1, 6).astype(np.int64)
+    got = tout.cpu().numpy().reshape(-1, 7).astype(np.int64)
     exp = oracle.eval_batch(w, wl.depth, [wl.gt[:1]], np.zeros(len(hyps), np.int32), hyps, 2)
     assert np.array_equal(got, exp)
 
@@ -280,14 +280,89 @@ def test_graph_and_autotune_match_oracle(c2):
         tP, stride, tplen, thp, th = _dev_batch(torch, parents, hp, hyps)
         if rep == 0:
             keep = (tP, tplen, thp, th)
-            tout = torch.zeros(len(hyps) * 6, dtype=torch.int32, device="cuda:0")
+            tout = torch.zeros(len(hyps) * 7, dtype=torch.int32, device="cuda:0")
         else:
             keep[3].copy_(th)  # same device buffers, new contents
         p.perch_eval_graph(keep[0], stride, keep[1], keep[2], keep[3], wl.K, tout)
         torch.cuda.synchronize()
-        got = tout.cpu().numpy().reshape(-1, 6).astype(np.int64)
+        got = tout.cpu().numpy().reshape(-1, 7).astype(np.int64)
         exp = oracle.eval_batch(w, wl.depth, parents, hp, hyps, wl.K)
         assert np.array_equal(got, exp)
         outs.append(got)
     assert not np.array_equal(outs[0], outs[1])
     p.close()
+
+
+def _multi_c1(n):
+    """n small independent scenes sharing the C1 camera and meshes."""
+    cam, meshes = synth.camera_c1(), synth.meshes_c1()
+    grid = synth.pose_grid(-0.15, 0.1, 4, 4)
+    return synth.workloads_c5(n, grid=grid, cam=cam, meshes=meshes, k_range=(1, 2))
+
+
+def test_multi_scene_eval_matches_oracle():
+    wls = _multi_c1(5)
+    p = perch.Perch(0)
+    p.setup(wls[0])
+    for s, wl in enumerate(wls[1:], 1):
+        p.perch_set_scene(s, wl.depth)
+    rng = np.random.default_rng(4)
+    allh = synth.all_hypotheses(wls[0].grid, [0, 1])
+    parents, pscene, pK = [], [], []
+    for s, wl in enumerate(wls):
+        parents += [wl.gt[:0], wl.gt[:1]]
+        pscene += [s, s]
+        pK += [max(wl.K, 2), max(wl.K, 2)]
+    hp = rng.integers(0, len(parents), 400).astype(np.int32)
+    hyps = allh[rng.choice(len(allh), 400)]
+    got = _recs(p.perch_eval_successors_multi(parents, pscene, pK, hp, hyps))
+    for s, wl in enumerate(wls):
+        w = oracle.World.of(wl)
+        for j in (2 * s, 2 * s + 1):
+            sel = hp == j
+            exp = oracle.eval_batch(w, wl.depth, [parents[j]], np.zeros(sel.sum(), np.int32), hyps[sel], pK[j])
+            assert np.array_equal(got[sel], exp), (s, j)
+    p.close()
+
+
+def test_multi_scene_search_matches_oracle():
+    wls = _multi_c1(6)
+    p = perch.Perch(0)
+    p.setup(wls[0])
+    for s, wl in enumerate(wls[1:], 1):
+        p.perch_set_scene(s, wl.depth)
+    res = p.perch_search_multi(list(range(len(wls))), [wl.mesh_multiset for wl in wls], batch_states=2,
+                               max_hyps_per_launch=300)
+    for wl, r in zip(wls, res):
+        w = oracle.World.of(wl)
+        cost, key = search.exhaustive(w, wl.depth, wl.grid, wl.mesh_multiset)
+        assert r["proven_optimal"] and (r["cost"], r["key"]) == (cost, key)
+    p.close()
+
+
+@pytest.mark.parametrize("w,heur", [(1.0, 3), (1.5, 3), (3.0, 3), (3.0, 1), (3.0, 2)])
+def test_focal_mha_search_bound(w, heur):
+    """Library Focal-MHA* on the reduced 2-object grid: cost within w times
+    the exhaustive optimum (Theorem 2); with w = 1 exactly optimal."""
+    grid = synth.pose_grid(-0.15, 0.1, 4, 4)
+    wl = synth.workload_c1(scene=3, grid=grid)
+    p = perch.Perch(0)
+    p.setup(wl)
+    wo = oracle.World.of(wl)
+    opt, opt_key = search.exhaustive(wo, wl.depth, wl.grid, wl.mesh_multiset)
+    r = p.perch_search(wl.mesh_multiset, w=w, heuristics=heur, batch_states=2)
+    assert r["status"] == perch.PERCH_OK and opt <= r["cost"] <= w * opt
+    if w == 1.0:
+        assert (r["cost"], r["key"]) == (opt, opt_key) and r["proven_optimal"]
+    p.close()
+
+
+def test_focal_mha_full_c1_fewer_expansions(c1):
+    """On the full 800-pose C1 tree, w = 3 with both heuristics stays within
+    the bound and expands no more states than the exact search."""
+    wl, p, w = c1
+    cost, key, _ = search.uniform_cost_search(w, wl.depth, wl.grid, wl.mesh_multiset)
+    exact = p.perch_search(wl.mesh_multiset, batch_states=4)
+    fast = p.perch_search(wl.mesh_multiset, w=3.0, heuristics=3, batch_states=4)
+    assert exact["cost"] == cost and cost <= fast["cost"] <= 3 * cost
+    assert fast["expansions"] <= exact["expansions"]

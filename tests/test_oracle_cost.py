@@ -166,3 +166,34 @@ def test_residual_only_at_last_level(c1):
     assert np.all(r_mid[:, 2] == 0)
     r_last = oracle.eval_batch(w, c1.depth, [c1.gt[:1]], np.zeros(len(hyps), np.int32), hyps, 2)
     assert (r_last[r_last[:, 3] == 0, 2] > 0).any()
+
+
+def test_overlap_count_matches_direct_cylinder_test(c1):
+    """n_vol (the drop of h_overlap, Sec. IV-C) at the root is |I n V(O)|,
+    checked with a float64 cylinder test away from its boundary; along a
+    valid path the drops add up to |I n V_K|."""
+    w = oracle.World.of(c1)
+    cam_pts, world_pts = oracle.observed(w, c1.depth)
+    hyps = np.concatenate([c1.gt, synth.all_hypotheses(c1.grid, [0, 1])[::17]])
+    recs = oracle.eval_batch(w, c1.depth, [c1.gt[:0]], np.zeros(len(hyps), np.int32), hyps, 2)
+    q = world_pts.astype(np.float64)
+
+    def inside(o):
+        m = c1.meshes[int(o["mesh"])]
+        d2 = (q[:, 0] - float(c1.grid.xs[o["ix"]])) ** 2 + (q[:, 1] - float(c1.grid.ys[o["iy"]])) ** 2
+        return (d2 <= m.vol_r ** 2) & (q[:, 2] >= m.vol_zlo) & (q[:, 2] <= m.vol_zhi), d2, m
+
+    nonzero = 0
+    for o, r in zip(hyps, recs):
+        ins, d2, m = inside(o)
+        clear = np.abs(d2 - m.vol_r ** 2) > 1e-9
+        assert r[6] == ins.sum() or not clear.all()
+        nonzero += r[6] > 0
+    assert nonzero >= 2
+    # telescoping along the ground-truth path (both orders tried)
+    for order in (c1.gt, c1.gt[::-1]):
+        r0 = oracle.eval_batch(w, c1.depth, [order[:0]], np.zeros(1, np.int32), order[:1], 2)[0]
+        r1 = oracle.eval_batch(w, c1.depth, [order[:1]], np.zeros(1, np.int32), order[1:], 2)[0]
+        if r0[3] == 0 and r1[3] == 0:
+            union = inside(order[0])[0] | inside(order[1])[0]
+            assert r0[6] + r1[6] == union.sum()

@@ -66,3 +66,18 @@ def test_set_key_cost_is_order_independent(small_c1):
             n_multi += 1
             assert costs[0] == costs[1]
     assert n_multi > 5
+
+
+@pytest.mark.parametrize("w", [1.0, 1.5, 3.0])
+def test_focal_mha_respects_the_suboptimality_bound(small_c1, w):
+    """Theorem 2: the returned cost is at most w times the optimum
+    (exhaustive enumeration); Theorem 1: a solution is found; w = 1 is
+    optimal."""
+    wl = small_c1
+    wo = oracle.World.of(wl)
+    opt, opt_key = search.exhaustive(wo, wl.depth, wl.grid, wl.mesh_multiset)
+    n_obs = oracle.observed(wo, wl.depth)[0].shape[0]
+    cost, key, exp = search.focal_mha(wo, wl.depth, wl.grid, wl.mesh_multiset, w, n_obs=n_obs)
+    assert cost is not None and opt <= cost <= w * opt + 1e-9
+    if w == 1.0:
+        assert cost == opt

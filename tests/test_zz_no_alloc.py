@@ -42,12 +42,12 @@ def test_noalloc_matches_existing_entry_point_twice():
         P, plen, stride = perch.Perch.pack_parents(parents)
         tP, tplen = _dev(torch, P, dev), torch.from_numpy(plen).to(dev)
         thp, th = torch.from_numpy(hp).to(dev), _dev(torch, hyps, dev)
-        ref = torch.full((len(hyps) * 6,), -7, dtype=torch.int32, device=dev)
-        got = torch.full((len(hyps) * 6,), -7, dtype=torch.int32, device=dev)
+        ref = torch.full((len(hyps) * 7,), -7, dtype=torch.int32, device=dev)
+        got = torch.full((len(hyps) * 7,), -7, dtype=torch.int32, device=dev)
         p.perch_eval_successors_dev(tP, stride, tplen, thp, th, wl.K, ref)
         p.perch_eval_successors_noalloc(tP, stride, tplen, thp, th, wl.K, got)
         torch.cuda.synchronize()
-        r, g = ref.cpu().numpy().reshape(-1, 6), got.cpu().numpy().reshape(-1, 6)
+        r, g = ref.cpu().numpy().reshape(-1, 7), got.cpu().numpy().reshape(-1, 7)
         assert (r[:, 3] >= 0).all() and (r != -7).all()
         assert np.array_equal(g, r)
         assert (r[:, 2] > 0).any()  # the residual path (shared-array U sets) was exercised
