@@ -641,3 +641,22 @@ def workloads_c5(n_scenes: int = 256, grid: PoseGrid | None = None, cam: Camera 
         depth = observe(cam, meshes, grid, gt, 0.003, 0.05, seed)
         out.append(Workload(f"c5/{s}", cam, meshes, grid, 0.01, gt, depth, 0.003, 0.05, seed))
     return out
+
+
+# ---------------------------------------------------------------------------
+# seeded initial weights of the learned heuristic's network
+# ---------------------------------------------------------------------------
+def he_normal(shapes, seed: int):
+    """One float32 array per shape: arrays of rank > 1 are weights, drawn
+    normal with variance 2 / fan_in (fan_in = product of all but the first
+    dimension); rank-1 arrays (biases) are zero. Array i uses sub-stream i."""
+    out = []
+    for i, shp in enumerate(shapes):
+        n = int(np.prod(shp))
+        if len(shp) > 1:
+            fan_in = int(np.prod(shp[1:]))
+            a = normal(substream(seed, 100 + i), n) * math.sqrt(2.0 / fan_in)
+        else:
+            a = np.zeros(n)
+        out.append(a.reshape(shp).astype(np.float32))
+    return out
