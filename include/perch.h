@@ -267,6 +267,72 @@ int perch_eval_graph(perch_ctx* ctx, const perch_obj* parents, int32_t parent_st
  * has been issued yet. */
 int perch_last_timing(perch_ctx* ctx, float* prep_ms, float* eval_ms);
 
+
+/* ------------------------------------------------------------------------
+ * Learned heuristic (the inadmissible heuristics of Sec. IV-C admit any
+ * estimate of cost-to-go; Sec. VI proposes learning them; no network is
+ * given in the paper). A small convolutional network predicts
+ * y = log(1 + dJr + dJo + residual) of one successor from two 64 x 64 crops
+ * centred on the projected hypothesis and a one-hot of (mesh, yaw):
+ *   conv 3x3 2->32 stride 1, 32->64 s2, 64->128 s2, 128->128 s2 (pad 1,
+ *   ReLU) -> flatten (row, column, channel) ++ one-hot -> FC 96 (ReLU) -> FC 1.
+ * Activations and weights are bfloat16 with FP32 accumulation on the tensor
+ * cores; Adam (beta 0.9 / 0.999, eps 1e-8) keeps FP32 master weights.
+ * ------------------------------------------------------------------------ */
+typedef struct perch_cnn perch_cnn;
+
+/* Create a network with all parameters zero on `device` (stream as in
+ * perch_create). n_onehot >= 1 one-hot inputs (index mesh * n_yaw + iyaw);
+ * max_batch in [32, 1024], a multiple of 32: the largest batch of one
+ * training step (forward passes of more crops run in chunks of it). */
+int perch_cnn_create(perch_cnn** out, int device, void* cuda_stream, int32_t n_onehot, int32_t max_batch);
+int perch_cnn_destroy(perch_cnn* net);
+const char* perch_cnn_last_error(const perch_cnn* net);
+
+/* Parameters as one FP32 array in this order: for each convolution its
+ * weights [Cout][3][3][Cin] then bias [Cout]; FC1 weights [96][8192 +
+ * n_onehot] then bias [96]; FC2 weights [96]; FC2 bias [1]. */
+int perch_cnn_param_count(const perch_cnn* net, int64_t* n);
+/* Host array of param_count floats; resets Adam's moments and step. */
+int perch_cnn_set_params(perch_cnn* net, const float* params, int64_t n);
+int perch_cnn_get_params(perch_cnn* net, float* params, int64_t n);
+
+/* Network inputs for n_hyp hypotheses (host arrays in, DEVICE arrays out):
+ * parents / hyp_parent / hyp as perch_eval_successors; parent_scene (may be
+ * NULL: scene 0) selects the observed depth image. crops: n_hyp x 64 x 64 x 2
+ * bfloat16 (row, column, channel; channel 0 observed depth, channel 1 the
+ * parent's z-buffer), centred on the projection of (x, y, middle of V(O)'s
+ * height range) computed in double: pixel (floor(u + 0.5), floor(v + 0.5));
+ * value clamp((z_ref - d) * 10 / m, -3, 3) rounded to float then bfloat16
+ * where the depth d is finite and > 0, else -4. onehot: n_hyp indices
+ * mesh * n_yaw + iyaw. Synchronous. */
+int perch_cnn_crops(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride, const int32_t* parent_len,
+                    const int32_t* parent_scene, int32_t n_par, const int32_t* hyp_parent, const perch_obj* hyp,
+                    int64_t n_hyp, uint16_t* crops, int32_t* onehot);
+
+/* Predictions for n crops (device arrays), asynchronous on the network's
+ * stream. */
+int perch_cnn_forward(perch_cnn* net, const uint16_t* crops, const int32_t* onehot, int64_t n, float* pred);
+
+/* One Adam step on the batch (device arrays; n a multiple of 32 up to
+ * max_batch; loss 0.5 mean (pred - target)^2 before the step written to the
+ * device float `loss`, may be NULL). Asynchronous. */
+int perch_cnn_train_step(perch_cnn* net, const uint16_t* crops, const int32_t* onehot, const float* target,
+                         int32_t n, float lr, float* loss);
+
+/* Forward and backward pass without an update: gradients of the loss in the
+ * parameter order above (host array of param_count floats, may be NULL), the
+ * loss and the n predictions (host, may be NULL). Device inputs as
+ * perch_cnn_train_step. Synchronous. */
+int perch_cnn_gradients(perch_cnn* net, const uint16_t* crops, const int32_t* onehot, const float* target, int32_t n,
+                        float* grads, float* loss, float* pred);
+
+/* Use `net` (not owned; NULL detaches) for the learned heuristic of the
+ * search (heuristics bit 2). n_candidates: placements per remaining object
+ * type scored for a state (see perch_search). PERCH_E_ARG if the network's
+ * one-hot is narrower than meshes x yaws. */
+int perch_set_heuristic_net(perch_ctx* ctx, perch_cnn* net, int32_t n_candidates);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libperch.so")
-SOURCES = ["perch_kernels.cu", "perch_api.cu", "perch_search.cpp", "perch_noalloc.cu", "perch_tune.cu"]
+SOURCES = ["perch_kernels.cu", "perch_api.cu", "perch_search.cpp", "perch_noalloc.cu", "perch_tune.cu",
+           "perch_cnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

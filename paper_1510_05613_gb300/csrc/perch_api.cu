@@ -157,6 +157,8 @@ int perch_ctx::build_scene(int s, const float* depth_host) {
   CK(ctx->world_pts.ensure(16 * (size_t)npx), "alloc");
   CK(ctx->scratch_small.ensure(64), "alloc");
   CK(cudaMemcpyAsync(ctx->depth.p, depth_host, 4 * (size_t)npx, cudaMemcpyHostToDevice, ctx->stream), "copy depth");
+  CK(sc.img.ensure(4 * (size_t)npx), "alloc scene image");
+  CK(cudaMemcpyAsync(sc.img.p, ctx->depth.p, 4 * (size_t)npx, cudaMemcpyDeviceToDevice, ctx->stream), "copy depth");
   int binit[10] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN, INT_MAX, INT_MAX, INT_MIN, INT_MIN};
   int* bounds = ctx->scratch_small.as<int>();
   CK(cudaMemcpyAsync(bounds, binit, sizeof binit, cudaMemcpyHostToDevice, ctx->stream), "copy");
@@ -269,6 +271,11 @@ int perch_ctx::build_scene(int s, const float* depth_host) {
   for (size_t k = 0; k < scenes.size(); ++k) all[k] = scenes[k].idx;
   CK(cudaMemcpyAsync(d_scenes.p, all.data(), sizeof(ObsIndex) * all.size(), cudaMemcpyHostToDevice, stream),
      "copy scene table");
+  CK(d_scene_img.ensure(sizeof(float*) * scenes.size()), "alloc scene image table");
+  std::vector<const float*> imgs(scenes.size());
+  for (size_t k = 0; k < scenes.size(); ++k) imgs[k] = scenes[k].img.as<float>();
+  CK(cudaMemcpyAsync(d_scene_img.p, imgs.data(), sizeof(float*) * imgs.size(), cudaMemcpyHostToDevice, stream),
+     "copy scene image table");
   CK(cudaStreamSynchronize(stream), "scene index");
   max_obs = 0;
   for (auto& x : scenes) max_obs = std::max(max_obs, x.idx.n);

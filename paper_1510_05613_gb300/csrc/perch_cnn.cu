@@ -1,0 +1,1081 @@
+// Learned heuristic network: crop extraction, BF16 forward and backward
+// passes on the tensor cores, and Adam (training and inference kernels).
+//
+// The paper's multi-heuristic search (Sec. IV-B/C) admits any inadmissible
+// heuristic and names learned ones as the next step (Sec. IV-C, Sec. VI); it
+// fixes no network. This one predicts y = log(1 + edge cost) of one MSGT
+// successor from a 2 x 64 x 64 crop (observed depth, parent z-buffer) centred
+// on the projected hypothesis, and a one-hot of (mesh, yaw):
+//   conv 3x3 2->32 s1, 32->64 s2, 64->128 s2, 128->128 s2 (pad 1, ReLU)
+//   -> flatten (h, w, c) ++ one-hot -> FC 96 (ReLU) -> FC 1; loss 0.5 (pred - y)^2
+//
+// Data layout: activations NHWC bfloat16; every convolution is an explicit
+// im2col ([rows = N x Ho x Wo][K = 9 Cin padded to 32]) followed by one GEMM
+// C = A B^T with both operands K-contiguous. The GEMM is mma.sync m16n8k16
+// (BF16 in, FP32 accumulate) fed by a 3-stage cp.async pipeline and ldmatrix.
+// Weight gradients are GEMMs over the transposed activations, split along the
+// reduction and summed in a fixed order (deterministic). Gradients between
+// layers are rounded to bfloat16, like the activations; weights keep an FP32
+// master copy updated by Adam and re-rounded to bfloat16 after each step.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "perch_ctx.h"
+
+using namespace perch;
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int kCrop = 64;
+constexpr int kHidden = 96;
+constexpr int kConvs = 4;
+constexpr int kCin[kConvs] = {2, 32, 64, 128};
+constexpr int kCout[kConvs] = {32, 64, 128, 128};
+constexpr int kStride[kConvs] = {1, 2, 2, 2};
+constexpr int kHin[kConvs] = {64, 64, 32, 16};  // input side of each layer
+constexpr int kFeat = 128 * 8 * 8;               // flattened last conv output
+constexpr float kMissing = -4.0f, kClamp = 3.0f;
+constexpr double kScale = 10.0;  // per metre
+
+int round32(int v) { return (v + 31) / 32 * 32; }
+int kp_of(int l) { return round32(9 * kCin[l]); }
+
+// ---------------------------------------------------------------- GEMM
+constexpr int BM = 128, BK = 32, LDS = BK + 8, STAGES = 3;
+enum { EPI_BIAS_RELU = 0, EPI_F32 = 1 };
+
+struct GemmArgs {
+  const bf16* A;  // [M][lda], K-contiguous
+  long long lda;
+  const bf16* B;  // [N][ldb], K-contiguous
+  long long ldb;
+  int M, N, K, Ksplit;  // split z covers columns [z Ksplit, min(K, (z + 1) Ksplit))
+  float* Cf;            // EPI_F32 output (partial z at Cf + z split_stride)
+  bf16* Cb;             // EPI_BIAS_RELU output
+  long long ldc;
+  int grp;              // output row m lives at (m / grp) ldg + (m % grp) ldc
+  long long ldg;
+  long long split_stride;
+  const float* bias;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool pred) {
+  const int sz = pred ? 16 : 0;  // src-size 0: the 16 bytes are zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(sz));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// C[M x N] = A[M x K] B[N x K]^T. 256 threads; CTA tile 128 x BN; warp tile
+// (128 / (8 / (BN / 32))) x 32. K (and Ksplit) multiples of 32.
+template <int BN, int EPI>
+__global__ void __launch_bounds__(256) k_gemm(GemmArgs p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  bf16* As = reinterpret_cast<bf16*>(smem_raw);  // [STAGES][BM][LDS]
+  bf16* Bs = As + STAGES * BM * LDS;              // [STAGES][BN][LDS]
+  constexpr int WN = BN / 32, WM = 8 / WN, TM = BM / WM, MI = TM / 16;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp / WN, wn = warp % WN;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int kbeg = blockIdx.z * p.Ksplit;
+  const int kend = min(p.K, kbeg + p.Ksplit);
+  const int KT = kend > kbeg ? (kend - kbeg) / BK : 0;
+  float acc[MI][4][4];
+#pragma unroll
+  for (int i = 0; i < MI; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
+
+  auto load = [&](int stage, int kt) {
+    const int k0 = kbeg + kt * BK;
+    for (int c = tid; c < BM * 4; c += 256) {
+      const int r = c >> 2, q = c & 3, gm = m0 + r;
+      const bool ok = gm < p.M;
+      const bf16* src = ok ? p.A + (long long)gm * p.lda + k0 + q * 8 : p.A;
+      cp_async16(smem_addr(As + (stage * BM + r) * LDS + q * 8), src, ok);
+    }
+    for (int c = tid; c < BN * 4; c += 256) {
+      const int r = c >> 2, q = c & 3, gn = n0 + r;
+      const bool ok = gn < p.N;
+      const bf16* src = ok ? p.B + (long long)gn * p.ldb + k0 + q * 8 : p.B;
+      cp_async16(smem_addr(Bs + (stage * BN + r) * LDS + q * 8), src, ok);
+    }
+  };
+#pragma unroll
+  for (int s = 0; s < STAGES - 1; ++s) {
+    if (s < KT) load(s, s);
+    cp_commit();
+  }
+  for (int kt = 0; kt < KT; ++kt) {
+    cp_wait<STAGES - 2>();
+    __syncthreads();  // stage kt landed for every thread; stage kt - 1 is free
+    {
+      const int nk = kt + STAGES - 1;
+      if (nk < KT) load(nk % STAGES, nk);
+      cp_commit();
+    }
+    const bf16* as = As + (kt % STAGES) * BM * LDS;
+    const bf16* bs = Bs + (kt % STAGES) * BN * LDS;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      uint32_t af[MI][4], bfr[4][2];
+#pragma unroll
+      for (int i = 0; i < MI; ++i) {
+        const int row = wm * TM + i * 16 + (lane & 15), col = kk * 16 + (lane >> 4) * 8;
+        ldsm_x4(smem_addr(as + row * LDS + col), af[i][0], af[i][1], af[i][2], af[i][3]);
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int row = wn * 32 + j * 16 + (lane & 7) + ((lane >> 4) << 3);
+        const int col = kk * 16 + ((lane >> 3) & 1) * 8;
+        ldsm_x4(smem_addr(bs + row * LDS + col), bfr[2 * j][0], bfr[2 * j][1], bfr[2 * j + 1][0],
+                bfr[2 * j + 1][1]);
+      }
+#pragma unroll
+      for (int i = 0; i < MI; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j][0], bfr[j][1]);
+    }
+  }
+  cp_wait<0>();
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int i = 0; i < MI; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int row = m0 + wm * TM + i * 16 + g + h * 8;
+        const int col = n0 + wn * 32 + j * 8 + 2 * t;
+        if (row >= p.M || col >= p.N) continue;
+        float v0 = acc[i][j][2 * h], v1 = acc[i][j][2 * h + 1];
+        const long long off = (long long)(row / p.grp) * p.ldg + (long long)(row % p.grp) * p.ldc + col;
+        if (EPI == EPI_BIAS_RELU) {
+          v0 = fmaxf(v0 + p.bias[col], 0.0f);
+          v1 = fmaxf(v1 + p.bias[col + 1], 0.0f);
+          *reinterpret_cast<__nv_bfloat162*>(p.Cb + off) = __floats2bfloat162_rn(v0, v1);
+        } else {
+          *reinterpret_cast<float2*>(p.Cf + (long long)blockIdx.z * p.split_stride + off) = make_float2(v0, v1);
+        }
+      }
+}
+
+template <int BN, int EPI>
+cudaError_t gemm_bn(const GemmArgs& p, int splits, cudaStream_t s) {
+  const int smem = STAGES * (BM + BN) * LDS * (int)sizeof(bf16);
+  cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((p.N + BN - 1) / BN, (p.M + BM - 1) / BM, splits);
+  k_gemm<BN, EPI><<<grid, 256, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int EPI>
+cudaError_t gemm(GemmArgs p, int splits, cudaStream_t s) {
+  if (p.grp <= 0) {
+    p.grp = 1 << 30;
+    p.ldg = 0;
+  }
+  if (p.N <= 32) return gemm_bn<32, EPI>(p, splits, s);
+  if (p.N <= 64) return gemm_bn<64, EPI>(p, splits, s);
+  return gemm_bn<128, EPI>(p, splits, s);
+}
+
+// ---------------------------------------------------------------- layout kernels
+// col[m][k] of a 3x3 pad-1 stride-s convolution, k = (kh 3 + kw) Cin + c;
+// zero for k >= 9 Cin and outside the image. One thread per 8 columns.
+__global__ void k_im2col(const bf16* __restrict__ x, int N, int H, int W, int Cin, int s, int Kp,
+                         bf16* __restrict__ col) {
+  const int Ho = H / s, Wo = W / s;
+  const int chunks = Kp / 8;
+  const long long total = (long long)N * Ho * Wo * chunks;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(e % chunks);
+    const long long m = e / chunks;
+    const int j = (int)(m % Wo), i = (int)((m / Wo) % Ho);
+    const long long n = m / ((long long)Wo * Ho);
+    const int k0 = q * 8;
+    uint4 out;
+    if ((Cin & 7) == 0) {
+      const int tap = k0 / Cin, c = k0 % Cin;
+      const int r = s * i - 1 + tap / 3, cc = s * j - 1 + tap % 3;
+      if (tap < 9 && r >= 0 && r < H && cc >= 0 && cc < W)
+        out = *reinterpret_cast<const uint4*>(x + ((n * H + r) * W + cc) * Cin + c);
+      else
+        out = make_uint4(0, 0, 0, 0);
+    } else {
+      unsigned short v[8];
+      for (int t = 0; t < 8; ++t) {
+        const int k = k0 + t;
+        v[t] = 0;
+        if (k < 9 * Cin) {
+          const int tap = k / Cin, c = k % Cin;
+          const int r = s * i - 1 + tap / 3, cc = s * j - 1 + tap % 3;
+          if (r >= 0 && r < H && cc >= 0 && cc < W)
+            v[t] = reinterpret_cast<const unsigned short*>(x)[((n * H + r) * W + cc) * Cin + c];
+        }
+      }
+      out = make_uint4(v[0] | (uint32_t)v[1] << 16, v[2] | (uint32_t)v[3] << 16, v[4] | (uint32_t)v[5] << 16,
+                       v[6] | (uint32_t)v[7] << 16);
+    }
+    *reinterpret_cast<uint4*>(col + m * Kp + k0) = out;
+  }
+}
+
+// dx[n][h][w][c] = sum over the taps that read (h, w) of dcol, in (kh, kw)
+// order, times [x > 0] (the ReLU of the layer that produced x); bfloat16 out.
+// Four channels per thread (Cin multiple of 4).
+__global__ void k_col2im_relu(const float* __restrict__ dcol, const bf16* __restrict__ x, int N, int H, int W,
+                              int Cin, int s, int Kp, bf16* __restrict__ dx) {
+  const int Ho = H / s, Wo = W / s;
+  const int quads = Cin / 4;
+  const long long total = (long long)N * H * W * quads;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e % quads) * 4;
+    const long long pix = e / quads;
+    const int w = (int)(pix % W), h = (int)((pix / W) % H);
+    const long long n = pix / ((long long)W * H);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (int kh = 0; kh < 3; ++kh) {
+      const int ti = h + 1 - kh;
+      if (ti < 0 || ti % s) continue;
+      const int i = ti / s;
+      if (i >= Ho) continue;
+      for (int kw = 0; kw < 3; ++kw) {
+        const int tj = w + 1 - kw;
+        if (tj < 0 || tj % s) continue;
+        const int j = tj / s;
+        if (j >= Wo) continue;
+        const float4 v =
+            *reinterpret_cast<const float4*>(dcol + ((n * Ho + i) * Wo + j) * Kp + (kh * 3 + kw) * Cin + c);
+        a0 += v.x;
+        a1 += v.y;
+        a2 += v.z;
+        a3 += v.w;
+      }
+    }
+    const long long o = pix * Cin + c;
+    const __nv_bfloat162 x01 = *reinterpret_cast<const __nv_bfloat162*>(x + o);
+    const __nv_bfloat162 x23 = *reinterpret_cast<const __nv_bfloat162*>(x + o + 2);
+    if (!(__low2float(x01) > 0.f)) a0 = 0.f;
+    if (!(__high2float(x01) > 0.f)) a1 = 0.f;
+    if (!(__low2float(x23) > 0.f)) a2 = 0.f;
+    if (!(__high2float(x23) > 0.f)) a3 = 0.f;
+    *reinterpret_cast<__nv_bfloat162*>(dx + o) = __floats2bfloat162_rn(a0, a1);
+    *reinterpret_cast<__nv_bfloat162*>(dx + o + 2) = __floats2bfloat162_rn(a2, a3);
+  }
+}
+
+// out[c][r] = in[r][c] for a bfloat16 matrix with R, C multiples of 32.
+__global__ void k_transpose(const unsigned short* __restrict__ in, long long R, int C,
+                            unsigned short* __restrict__ out) {
+  __shared__ unsigned short tile[32][33];
+  const long long r0 = (long long)blockIdx.x * 32;  // rows on x: up to 2^31 - 1 blocks
+  const int c0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) tile[k][threadIdx.x] = in[(r0 + k) * C + c0 + threadIdx.x];
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) out[(long long)(c0 + k) * R + r0 + threadIdx.x] = tile[threadIdx.x][k];
+}
+
+// out[r] = sum of row r of a bfloat16 [R][C] matrix (fixed order).
+__global__ void k_row_sum(const bf16* __restrict__ in, long long C, float* __restrict__ out) {
+  const bf16* row = in + (long long)blockIdx.x * C;
+  float a = 0.0f;
+  for (long long k = threadIdx.x; k < C; k += blockDim.x) a += __bfloat162float(row[k]);
+  __shared__ float red[32];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    a = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (threadIdx.x == 0) out[blockIdx.x] = a;
+  }
+}
+
+// out[e] = sum over z of part[z][e] (split-K partials, fixed order).
+__global__ void k_split_sum(const float* __restrict__ part, int splits, long long n, float* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    float a = 0.0f;
+    for (int z = 0; z < splits; ++z) a += part[(long long)z * n + e];
+    out[e] = a;
+  }
+}
+
+// one-hot columns of the FC input: feat[n][kFeat + j] = [j == idx[n]] (ragged rows zero)
+__global__ void k_onehot(const int32_t* __restrict__ idx, int n, int n_rows, int n_onehot_pad, long long ldf,
+                         bf16* __restrict__ feat) {
+  const long long total = (long long)n_rows * n_onehot_pad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e % n_onehot_pad);
+    const int r = (int)(e / n_onehot_pad);
+    const bool on = r < n && idx[r] == j;
+    feat[(long long)r * ldf + kFeat + j] = __float2bfloat16_rn(on ? 1.0f : 0.0f);
+  }
+}
+
+// pred[n] = h1[n] . bf16(w2) + b2; with a target: err[n] = pred - y
+__global__ void k_fc2(const bf16* __restrict__ h1, const float* __restrict__ w2, const float* __restrict__ b2, int n,
+                      float* __restrict__ pred, const float* __restrict__ target, float* __restrict__ err) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  float a = 0.0f;
+  for (int j = lane; j < kHidden; j += 32)
+    a += __bfloat162float(h1[(long long)warp * kHidden + j]) * __bfloat162float(__float2bfloat16_rn(w2[j]));
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (lane == 0) {
+    const float pr = a + b2[0];
+    if (pred) pred[warp] = pr;
+    if (target) err[warp] = pr - target[warp];
+  }
+}
+
+// loss = mean 0.5 err^2; grads of w2, b2; dz1 = (err / n) bf16(w2) [h1 > 0]
+// (rows n..n_rows-1 of dz1 zero). One block of 256 threads.
+__global__ void k_fc2_backward(const bf16* __restrict__ h1, const float* __restrict__ w2, const float* __restrict__ err,
+                               int n, int n_rows, float* __restrict__ g_w2, float* __restrict__ g_b2,
+                               float* __restrict__ loss, bf16* __restrict__ dz1) {
+  __shared__ float red[32];
+  const float inv = 1.0f / (float)n;
+  float a = 0.0f;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) a += 0.5f * err[r] * err[r];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float l = 0.0f, gb = 0.0f;
+    for (int k = 0; k < (int)blockDim.x / 32; ++k) l += red[k];
+    for (int r = 0; r < n; ++r) gb += err[r] * inv;
+    if (loss) *loss = l * inv;
+    g_b2[0] = gb;
+  }
+  for (int j = threadIdx.x; j < kHidden; j += blockDim.x) {
+    float g = 0.0f;
+    for (int r = 0; r < n; ++r) g += err[r] * inv * __bfloat162float(h1[(long long)r * kHidden + j]);
+    g_w2[j] = g;
+  }
+  for (long long e = threadIdx.x; e < (long long)n_rows * kHidden; e += blockDim.x) {
+    const int r = (int)(e / kHidden), j = (int)(e % kHidden);
+    float v = 0.0f;
+    if (r < n && __bfloat162float(h1[e]) > 0.0f) v = err[r] * inv * __bfloat162float(__float2bfloat16_rn(w2[j]));
+    dz1[e] = __float2bfloat16_rn(v);
+  }
+}
+
+// dz of the last convolution: dfeat (fp32, [n][kFeat]) times [x4 > 0], where
+// x4 is read back from the FC input rows
+__global__ void k_feat_relu_grad(const float* __restrict__ dfeat, const bf16* __restrict__ feat, long long ldf,
+                                 int n, bf16* __restrict__ dz) {
+  const long long total = (long long)n * kFeat;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / kFeat, k = e % kFeat;
+    const float x = __bfloat162float(feat[r * ldf + k]);
+    dz[e] = __float2bfloat16_rn(x > 0.0f ? dfeat[e] : 0.0f);
+  }
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float c1, float c2,
+                       float eps) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[e];
+    const float mi = b1 * m[e] + (1.0f - b1) * gi;
+    const float vi = b2 * v[e] + (1.0f - b2) * gi * gi;
+    m[e] = mi;
+    v[e] = vi;
+    p[e] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ in, long long n, bf16* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = __float2bfloat16_rn(in[e]);
+}
+
+// ---------------------------------------------------------------- crops
+// One block per hypothesis. The centre is the projection of (x, y, middle of
+// V(O)'s height range), in double with every operation rounded separately:
+// camera point = R_wc^T (p - t_wc) summed in the order 0, 1, 2; pixel
+// floor(f (x_c / z_c) + c + 0.5). A pixel's value is
+// clamp((z_ref - d) 10 / m, -3, 3) (float, then bfloat16) where the depth d is
+// finite and > 0, else -4 (also outside the image and for a centre behind
+// the camera or beyond 1e6 pixels).
+__global__ void k_crops(Camera cam, const float* __restrict__ xs, const float* __restrict__ ys,
+                        const DevMesh* __restrict__ meshes, int n_yaw, const float* const* __restrict__ scene_img,
+                        const int32_t* __restrict__ parent_scene, const float* __restrict__ parent_z,
+                        const int32_t* __restrict__ hyp_parent, const perch_obj* __restrict__ hyp, long long n_hyp,
+                        bf16* __restrict__ crops, int32_t* __restrict__ onehot) {
+  __shared__ int s_cu, s_cv, s_ok;
+  __shared__ double s_zr;
+  const long long h = blockIdx.x;
+  if (h >= n_hyp) return;
+  const perch_obj o = hyp[h];
+  const int par = hyp_parent[h];
+  if (threadIdx.x == 0) {
+    const DevMesh& m = meshes[o.mesh];
+    const double px = (double)xs[o.ix], py = (double)ys[o.iy];
+    const double pz = __dmul_rn(__dadd_rn((double)m.vol_zlo, (double)m.vol_zhi), 0.5);
+    const double d0 = __dsub_rn(px, (double)cam.twc[0]);
+    const double d1 = __dsub_rn(py, (double)cam.twc[1]);
+    const double d2 = __dsub_rn(pz, (double)cam.twc[2]);
+    double c[3];
+    for (int k = 0; k < 3; ++k)
+      c[k] = __dadd_rn(__dadd_rn(__dmul_rn((double)cam.Rwc[0 * 3 + k], d0), __dmul_rn((double)cam.Rwc[1 * 3 + k], d1)),
+                       __dmul_rn((double)cam.Rwc[2 * 3 + k], d2));
+    int ok = c[2] > 0.0;
+    double u = 0.0, v = 0.0;
+    if (ok) {
+      u = __dadd_rn(__dmul_rn((double)cam.fx, __ddiv_rn(c[0], c[2])), (double)cam.cx);
+      v = __dadd_rn(__dmul_rn((double)cam.fy, __ddiv_rn(c[1], c[2])), (double)cam.cy);
+      ok = fabs(u) < 1e6 && fabs(v) < 1e6;
+    }
+    s_ok = ok;
+    s_cu = ok ? (int)floor(__dadd_rn(u, 0.5)) : 0;
+    s_cv = ok ? (int)floor(__dadd_rn(v, 0.5)) : 0;
+    s_zr = c[2];
+    onehot[h] = (int32_t)o.mesh * n_yaw + o.iyaw;
+  }
+  __syncthreads();
+  const int W = cam.W, H = cam.H;
+  const int sc = parent_scene ? parent_scene[par] : 0;
+  const float* img = scene_img[sc];
+  const float* pz = parent_z + (long long)par * W * H;
+  const double zr = s_zr;
+  for (int px = threadIdx.x; px < kCrop * kCrop; px += blockDim.x) {
+    const int r = s_cv - kCrop / 2 + px / kCrop, c = s_cu - kCrop / 2 + px % kCrop;
+    float val[2] = {kMissing, kMissing};
+    if (s_ok && r >= 0 && r < H && c >= 0 && c < W) {
+      const float d[2] = {img[(long long)r * W + c], pz[(long long)r * W + c]};
+      for (int ch = 0; ch < 2; ++ch)
+        if (isfinite(d[ch]) && d[ch] > 0.0f) {
+          const float t = __double2float_rn(__dmul_rn(__dsub_rn(zr, (double)d[ch]), kScale));
+          val[ch] = fminf(fmaxf(t, -kClamp), kClamp);
+        }
+    }
+    *reinterpret_cast<__nv_bfloat162*>(crops + (h * kCrop * kCrop + px) * 2) = __floats2bfloat162_rn(val[0], val[1]);
+  }
+}
+
+int grid_for(long long n, int threads = 256) {
+  return (int)std::max<long long>(1, std::min<long long>((n + threads - 1) / threads, 152LL * 16));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- network object
+struct perch_cnn {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  int n_onehot = 0, onehot_pad = 0, Kf = 0, max_batch = 0;
+  long long step = 0;
+  // FP32 master layout: conv weights [Cout][Kp], FC1 [96][Kf] (the bfloat16
+  // region, contiguous), then conv biases, FC1 bias, FC2 weights, FC2 bias
+  long long off_w[kConvs], off_f1, n_w16, off_b[kConvs], off_fb1, off_f2, off_fb2, n_total;
+  DevBuf master, grad, adam_m, adam_v, w16, wt16;
+  long long off_wt[kConvs], off_f1t;
+  // batch buffers
+  DevBuf col[kConvs], act[kConvs], feat, h1, err_buf, pred_buf, loss_buf;
+  DevBuf dz1, dz1t, featt, dfeat, dz, dzt, colt, dcol, part;
+  bool params_set = false;
+
+  int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    err = buf;
+    return code;
+  }
+  int cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return PERCH_OK;
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation) return fail(PERCH_E_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(PERCH_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  }
+  std::vector<DevBuf*> buffers() {
+    std::vector<DevBuf*> v = {&master, &grad, &adam_m, &adam_v, &w16, &wt16, &feat, &h1, &err_buf, &pred_buf,
+                              &loss_buf, &dz1, &dz1t, &featt, &dfeat, &dz, &dzt, &colt, &dcol, &part};
+    for (int l = 0; l < kConvs; ++l) {
+      v.push_back(&col[l]);
+      v.push_back(&act[l]);
+    }
+    return v;
+  }
+  void layout() {
+    long long o = 0;
+    for (int l = 0; l < kConvs; ++l) {
+      off_w[l] = o;
+      o += (long long)kCout[l] * kp_of(l);
+    }
+    off_f1 = o;
+    o += (long long)kHidden * Kf;
+    n_w16 = o;
+    for (int l = 0; l < kConvs; ++l) {
+      off_b[l] = o;
+      o += kCout[l];
+    }
+    off_fb1 = o;
+    o += kHidden;
+    off_f2 = o;
+    o += kHidden;
+    off_fb2 = o;
+    o += 4;
+    n_total = o;
+    long long t = 0;
+    for (int l = 0; l < kConvs; ++l) {
+      off_wt[l] = t;
+      t += (long long)kCout[l] * kp_of(l);
+    }
+    off_f1t = t;
+  }
+  long long n_params() const {  // unpadded count, the packed order of the ABI
+    long long n = 0;
+    for (int l = 0; l < kConvs; ++l) n += (long long)kCout[l] * 9 * kCin[l] + kCout[l];
+    return n + (long long)kHidden * (kFeat + n_onehot) + kHidden + kHidden + 1;
+  }
+  // packed (ABI) index <-> padded master index, in the packed order
+  template <typename F>
+  void for_each_param(F f) const {
+    long long q = 0;
+    for (int l = 0; l < kConvs; ++l) {
+      const int K = 9 * kCin[l], Kp = kp_of(l);
+      for (int o = 0; o < kCout[l]; ++o)
+        for (int k = 0; k < K; ++k) f(q++, off_w[l] + (long long)o * Kp + k);
+      for (int o = 0; o < kCout[l]; ++o) f(q++, off_b[l] + o);
+    }
+    for (int o = 0; o < kHidden; ++o)
+      for (int k = 0; k < kFeat + n_onehot; ++k) f(q++, off_f1 + (long long)o * Kf + k);
+    for (int o = 0; o < kHidden; ++o) f(q++, off_fb1 + o);
+    for (int o = 0; o < kHidden; ++o) f(q++, off_f2 + o);
+    f(q++, off_fb2);
+  }
+  int ensure_batch(int n);
+  int refresh_weights();
+  int forward(const bf16* crops, const int32_t* onehot, int n, float* pred, const float* target);
+  int backward(const bf16* crops, int n);
+};
+
+#define CK_CTX(expr, what)                    \
+  do {                                        \
+    int rc_ = ctx->cuda((expr), what);        \
+    if (rc_ != PERCH_OK) return rc_;          \
+  } while (0)
+
+#define CKN(expr, what)                       \
+  do {                                        \
+    int rc_ = net->cuda((expr), what);        \
+    if (rc_ != PERCH_OK) return rc_;          \
+  } while (0)
+
+int perch_cnn::ensure_batch(int n) {
+  perch_cnn* net = this;
+  const long long N = std::max(n, 32);
+  for (int l = 0; l < kConvs; ++l) {
+    const long long Ho = kHin[l] / kStride[l];
+    CKN(col[l].ensure(2 * N * Ho * Ho * kp_of(l)), "alloc im2col");
+    if (l < kConvs - 1) CKN(act[l].ensure(2 * N * Ho * Ho * kCout[l]), "alloc activations");
+  }
+  CKN(feat.ensure(2 * N * Kf), "alloc");
+  CKN(h1.ensure(2 * N * kHidden), "alloc");
+  CKN(err_buf.ensure(4 * N), "alloc");
+  CKN(pred_buf.ensure(4 * N), "alloc");
+  CKN(loss_buf.ensure(16), "alloc");
+  return PERCH_OK;
+}
+
+int perch_cnn::refresh_weights() {
+  perch_cnn* net = this;
+  CKN(w16.ensure(2 * n_w16), "alloc");
+  CKN(wt16.ensure(2 * n_w16), "alloc");
+  k_to_bf16<<<grid_for(n_w16), 256, 0, stream>>>(master.as<float>(), n_w16, w16.as<bf16>());
+  CKN(cudaGetLastError(), "cast kernel");
+  for (int l = 1; l < kConvs; ++l) {  // [Cout][Kp] -> [Kp][Cout]
+    dim3 grid(kCout[l] / 32, kp_of(l) / 32);
+    k_transpose<<<grid, dim3(32, 8), 0, stream>>>(w16.as<unsigned short>() + off_w[l], kCout[l], kp_of(l),
+                                                   wt16.as<unsigned short>() + off_wt[l]);
+  }
+  dim3 grid(kHidden / 32, Kf / 32);
+  k_transpose<<<grid, dim3(32, 8), 0, stream>>>(w16.as<unsigned short>() + off_f1, kHidden, Kf,
+                                                 wt16.as<unsigned short>() + off_f1t);
+  CKN(cudaGetLastError(), "transpose kernel");
+  return PERCH_OK;
+}
+
+// Forward pass of n <= max_batch crops; with a target also the per-sample
+// errors (for the backward pass).
+int perch_cnn::forward(const bf16* crops, const int32_t* onehot, int n, float* pred, const float* target) {
+  perch_cnn* net = this;
+  int rc = ensure_batch(n);
+  if (rc) return rc;
+  const bf16* x = crops;
+  for (int l = 0; l < kConvs; ++l) {
+    const int H = kHin[l], s = kStride[l], Ho = H / s, Kp = kp_of(l);
+    const long long M = (long long)n * Ho * Ho;
+    k_im2col<<<grid_for(M * (Kp / 8)), 256, 0, stream>>>(x, n, H, H, kCin[l], s, Kp, col[l].as<bf16>());
+    CKN(cudaGetLastError(), "im2col kernel");
+    GemmArgs p{};
+    p.A = col[l].as<bf16>();
+    p.lda = Kp;
+    p.B = w16.as<bf16>() + off_w[l];
+    p.ldb = Kp;
+    p.M = (int)M;
+    p.N = kCout[l];
+    p.K = Kp;
+    p.Ksplit = Kp;
+    p.bias = master.as<float>() + off_b[l];
+    if (l < kConvs - 1) {
+      p.Cb = act[l].as<bf16>();
+      p.ldc = kCout[l];
+    } else {  // straight into the FC input rows: crop m / 64, position m % 64
+      p.Cb = feat.as<bf16>();
+      p.ldc = kCout[l];
+      p.grp = Ho * Ho;
+      p.ldg = Kf;
+    }
+    CKN(gemm<EPI_BIAS_RELU>(p, 1, stream), "conv gemm");
+    x = l < kConvs - 1 ? act[l].as<bf16>() : nullptr;
+  }
+  k_onehot<<<grid_for((long long)n * onehot_pad), 256, 0, stream>>>(onehot, n, n, onehot_pad, Kf, feat.as<bf16>());
+  CKN(cudaGetLastError(), "one-hot kernel");
+  GemmArgs p{};
+  p.A = feat.as<bf16>();
+  p.lda = Kf;
+  p.B = w16.as<bf16>() + off_f1;
+  p.ldb = Kf;
+  p.M = n;
+  p.N = kHidden;
+  p.K = Kf;
+  p.Ksplit = Kf;
+  p.bias = master.as<float>() + off_fb1;
+  p.Cb = h1.as<bf16>();
+  p.ldc = kHidden;
+  CKN(gemm<EPI_BIAS_RELU>(p, 1, stream), "fc1 gemm");
+  k_fc2<<<(n * 32 + 255) / 256, 256, 0, stream>>>(h1.as<bf16>(), master.as<float>() + off_f2,
+                                                   master.as<float>() + off_fb2, n, pred, target, err_buf.as<float>());
+  CKN(cudaGetLastError(), "fc2 kernel");
+  return PERCH_OK;
+}
+
+// Backward pass after forward(..., target); n a multiple of 32. Fills `grad`.
+int perch_cnn::backward(const bf16* crops, int n) {
+  perch_cnn* net = this;
+  const long long N = n;
+  float* G = grad.as<float>();
+  CKN(dz1.ensure(2 * N * kHidden), "alloc");
+  CKN(dz1t.ensure(2 * N * kHidden), "alloc");
+  CKN(featt.ensure(2 * N * Kf), "alloc");
+  CKN(dfeat.ensure(4 * N * kFeat), "alloc");
+  long long max_mk = 0, max_part = (long long)kHidden * Kf;
+  for (int l = 0; l < kConvs; ++l) {
+    const long long Ho = kHin[l] / kStride[l];
+    max_mk = std::max(max_mk, N * Ho * Ho * std::max(kp_of(l), kCout[l]));
+  }
+  CKN(dz.ensure(2 * max_mk), "alloc");
+  CKN(dzt.ensure(2 * max_mk), "alloc");
+  CKN(colt.ensure(2 * max_mk), "alloc");
+  CKN(dcol.ensure(4 * max_mk), "alloc");
+  for (int l = 0; l < kConvs; ++l) {
+    const long long M = N * (kHin[l] / kStride[l]) * (kHin[l] / kStride[l]);
+    const long long S = std::max<long long>(1, M / 4096);
+    max_part = std::max(max_part, S * kCout[l] * kp_of(l));
+  }
+  CKN(part.ensure(4 * max_part), "alloc");
+  // FC2 and the loss
+  k_fc2_backward<<<1, 256, 0, stream>>>(h1.as<bf16>(), master.as<float>() + off_f2, err_buf.as<float>(), n, n,
+                                         G + off_f2, G + off_fb2, loss_buf.as<float>(), dz1.as<bf16>());
+  CKN(cudaGetLastError(), "fc2 backward kernel");
+  // FC1: dW = dz1^T feat (reduction over the batch), db = column sums of dz1, dfeat = dz1 W
+  k_transpose<<<dim3(n / 32, kHidden / 32), dim3(32, 8), 0, stream>>>(dz1.as<unsigned short>(), N, kHidden,
+                                                                       dz1t.as<unsigned short>());
+  k_transpose<<<dim3(n / 32, Kf / 32), dim3(32, 8), 0, stream>>>(feat.as<unsigned short>(), N, Kf,
+                                                                  featt.as<unsigned short>());
+  CKN(cudaGetLastError(), "transpose kernel");
+  {
+    GemmArgs p{};
+    p.A = dz1t.as<bf16>();
+    p.lda = N;
+    p.B = featt.as<bf16>();
+    p.ldb = N;
+    p.M = kHidden;
+    p.N = Kf;
+    p.K = n;
+    p.Ksplit = n;
+    p.Cf = G + off_f1;
+    p.ldc = Kf;
+    CKN(gemm<EPI_F32>(p, 1, stream), "fc1 weight-gradient gemm");
+  }
+  k_row_sum<<<kHidden, 256, 0, stream>>>(dz1t.as<bf16>(), N, G + off_fb1);
+  {
+    GemmArgs p{};
+    p.A = dz1.as<bf16>();
+    p.lda = kHidden;
+    p.B = wt16.as<bf16>() + off_f1t;  // rows 0 .. kFeat-1 of W^T: the conv features only
+    p.ldb = kHidden;
+    p.M = n;
+    p.N = kFeat;
+    p.K = kHidden;
+    p.Ksplit = kHidden;
+    p.Cf = dfeat.as<float>();
+    p.ldc = kFeat;
+    CKN(gemm<EPI_F32>(p, 1, stream), "fc1 data-gradient gemm");
+  }
+  k_feat_relu_grad<<<grid_for(N * kFeat), 256, 0, stream>>>(dfeat.as<float>(), feat.as<bf16>(), Kf, n,
+                                                             dz.as<bf16>());
+  CKN(cudaGetLastError(), "relu gradient kernel");
+  for (int l = kConvs - 1; l >= 0; --l) {
+    const int H = kHin[l], s = kStride[l], Ho = H / s, Kp = kp_of(l), Co = kCout[l];
+    const long long M = N * Ho * Ho;
+    // dz (bf16 [M][Co]) -> dz^T; bias gradient = its row sums
+    k_transpose<<<dim3((unsigned)(M / 32), Co / 32), dim3(32, 8), 0, stream>>>(dz.as<unsigned short>(), M, Co,
+                                                                                 dzt.as<unsigned short>());
+    k_transpose<<<dim3((unsigned)(M / 32), Kp / 32), dim3(32, 8), 0, stream>>>(col[l].as<unsigned short>(), M, Kp,
+                                                                                colt.as<unsigned short>());
+    CKN(cudaGetLastError(), "transpose kernel");
+    k_row_sum<<<Co, 256, 0, stream>>>(dzt.as<bf16>(), M, G + off_b[l]);
+    // dW = dz^T col, split along the M reduction, partials summed in order
+    const int S = (int)std::max<long long>(1, M / 4096);
+    const int Ks = (int)((M / S + 31) / 32 * 32);
+    {
+      GemmArgs p{};
+      p.A = dzt.as<bf16>();
+      p.lda = M;
+      p.B = colt.as<bf16>();
+      p.ldb = M;
+      p.M = Co;
+      p.N = Kp;
+      p.K = (int)M;
+      p.Ksplit = Ks;
+      p.Cf = part.as<float>();
+      p.ldc = Kp;
+      p.split_stride = (long long)Co * Kp;
+      CKN(gemm<EPI_F32>(p, S, stream), "conv weight-gradient gemm");
+    }
+    k_split_sum<<<grid_for((long long)Co * Kp), 256, 0, stream>>>(part.as<float>(), S, (long long)Co * Kp,
+                                                                   G + off_w[l]);
+    CKN(cudaGetLastError(), "split sum kernel");
+    if (l == 0) break;
+    // dcol = dz W (fp32), then col2im with the ReLU mask of this layer's input
+    {
+      GemmArgs p{};
+      p.A = dz.as<bf16>();
+      p.lda = Co;
+      p.B = wt16.as<bf16>() + off_wt[l];
+      p.ldb = Co;
+      p.M = (int)M;
+      p.N = Kp;
+      p.K = Co;
+      p.Ksplit = Co;
+      p.Cf = dcol.as<float>();
+      p.ldc = Kp;
+      CKN(gemm<EPI_F32>(p, 1, stream), "conv data-gradient gemm");
+    }
+    k_col2im_relu<<<grid_for(N * H * H * (kCin[l] / 4)), 256, 0, stream>>>(
+        dcol.as<float>(), act[l - 1].as<bf16>(), n, H, H, kCin[l], s, Kp, dz.as<bf16>());
+    CKN(cudaGetLastError(), "col2im kernel");
+  }
+  (void)crops;
+  return PERCH_OK;
+}
+
+int net_predict(perch_ctx* ctx, perch_cnn* net, const perch_obj* parents, int parent_stride, const int32_t* plen,
+                const int32_t* pscene, int n_par, const int32_t* hyp_parent, const perch_obj* hyp, long long n_hyp,
+                float* pred_host) {
+  if (n_hyp == 0) return PERCH_OK;
+  CK_CTX(ctx->net_crops.ensure(2 * (size_t)kCrop * kCrop * 2 * n_hyp), "alloc crops");
+  CK_CTX(ctx->net_onehot.ensure(4 * (size_t)n_hyp), "alloc");
+  CK_CTX(ctx->net_pred.ensure(4 * (size_t)n_hyp), "alloc");
+  int rc = perch_cnn_crops(ctx, parents, parent_stride, plen, pscene, n_par, hyp_parent, hyp, n_hyp,
+                           ctx->net_crops.as<uint16_t>(), ctx->net_onehot.as<int32_t>());
+  if (rc) return rc;
+  rc = perch_cnn_forward(net, ctx->net_crops.as<uint16_t>(), ctx->net_onehot.as<int32_t>(), n_hyp,
+                         ctx->net_pred.as<float>());
+  if (rc) return ctx->fail(rc, "learned heuristic: %s", net->err.c_str());
+  CK_CTX(cudaMemcpyAsync(pred_host, ctx->net_pred.p, 4 * (size_t)n_hyp, cudaMemcpyDeviceToHost, net->stream),
+         "copy predictions");
+  CK_CTX(cudaStreamSynchronize(net->stream), "learned heuristic");
+  return PERCH_OK;
+}
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+int perch_cnn_create(perch_cnn** out, int device, void* cuda_stream, int32_t n_onehot, int32_t max_batch) {
+  if (!out) return PERCH_E_ARG;
+  *out = nullptr;
+  if (n_onehot < 1 || n_onehot > 65536 || max_batch < 32 || max_batch > 1024 || max_batch % 32) return PERCH_E_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return PERCH_E_CUDA;
+  }
+  perch_cnn* net = new perch_cnn;
+  net->device = device;
+  net->n_onehot = n_onehot;
+  net->onehot_pad = round32(n_onehot);
+  net->Kf = kFeat + net->onehot_pad;
+  net->max_batch = max_batch;
+  net->layout();
+  if (cuda_stream) {
+    net->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&net->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete net;
+      return PERCH_E_CUDA;
+    }
+    net->own_stream = true;
+  }
+  const size_t bytes = 4 * (size_t)net->n_total;
+  bool ok = net->master.ensure(bytes) == cudaSuccess && net->grad.ensure(bytes) == cudaSuccess &&
+            net->adam_m.ensure(bytes) == cudaSuccess && net->adam_v.ensure(bytes) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(net->master.p, 0, bytes, net->stream) == cudaSuccess &&
+       cudaMemsetAsync(net->grad.p, 0, bytes, net->stream) == cudaSuccess &&
+       cudaMemsetAsync(net->adam_m.p, 0, bytes, net->stream) == cudaSuccess &&
+       cudaMemsetAsync(net->adam_v.p, 0, bytes, net->stream) == cudaSuccess;
+  ok = ok && net->refresh_weights() == PERCH_OK && cudaStreamSynchronize(net->stream) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    for (DevBuf* b : net->buffers()) b->release();
+    if (net->own_stream) cudaStreamDestroy(net->stream);
+    delete net;
+    return PERCH_E_CUDA;
+  }
+  *out = net;
+  return PERCH_OK;
+}
+
+int perch_cnn_destroy(perch_cnn* net) {
+  if (!net) return PERCH_OK;
+  cudaSetDevice(net->device);
+  cudaStreamSynchronize(net->stream);
+  for (DevBuf* b : net->buffers()) b->release();
+  if (net->own_stream) cudaStreamDestroy(net->stream);
+  delete net;
+  return PERCH_OK;
+}
+
+const char* perch_cnn_last_error(const perch_cnn* net) { return net ? net->err.c_str() : "null network"; }
+
+int perch_cnn_param_count(const perch_cnn* net, int64_t* n) {
+  if (!net || !n) return PERCH_E_ARG;
+  *n = net->n_params();
+  return PERCH_OK;
+}
+
+int perch_cnn_set_params(perch_cnn* net, const float* params, int64_t n) {
+  if (!net) return PERCH_E_ARG;
+  net->err.clear();
+  if (!params || n != net->n_params()) return net->fail(PERCH_E_ARG, "expected %lld parameters", net->n_params());
+  CKN(cudaSetDevice(net->device), "cudaSetDevice");
+  std::vector<float> h((size_t)net->n_total, 0.0f);
+  net->for_each_param([&](long long q, long long i) { h[i] = params[q]; });
+  const size_t bytes = 4 * (size_t)net->n_total;
+  CKN(cudaMemcpyAsync(net->master.p, h.data(), bytes, cudaMemcpyHostToDevice, net->stream), "copy parameters");
+  CKN(cudaMemsetAsync(net->adam_m.p, 0, bytes, net->stream), "memset");
+  CKN(cudaMemsetAsync(net->adam_v.p, 0, bytes, net->stream), "memset");
+  net->step = 0;
+  int rc = net->refresh_weights();
+  if (rc) return rc;
+  CKN(cudaStreamSynchronize(net->stream), "set parameters");
+  net->params_set = true;
+  return PERCH_OK;
+}
+
+int perch_cnn_get_params(perch_cnn* net, float* params, int64_t n) {
+  if (!net) return PERCH_E_ARG;
+  net->err.clear();
+  if (!params || n != net->n_params()) return net->fail(PERCH_E_ARG, "expected %lld parameters", net->n_params());
+  CKN(cudaSetDevice(net->device), "cudaSetDevice");
+  std::vector<float> h((size_t)net->n_total);
+  CKN(cudaMemcpyAsync(h.data(), net->master.p, 4 * h.size(), cudaMemcpyDeviceToHost, net->stream), "copy");
+  CKN(cudaStreamSynchronize(net->stream), "get parameters");
+  net->for_each_param([&](long long q, long long i) { params[q] = h[i]; });
+  return PERCH_OK;
+}
+
+int perch_cnn_forward(perch_cnn* net, const uint16_t* crops, const int32_t* onehot, int64_t n, float* pred) {
+  if (!net) return PERCH_E_ARG;
+  net->err.clear();
+  if (n < 0 || (n > 0 && (!crops || !onehot || !pred))) return net->fail(PERCH_E_ARG, "bad arguments");
+  CKN(cudaSetDevice(net->device), "cudaSetDevice");
+  for (int64_t b = 0; b < n; b += net->max_batch) {
+    const int nb = (int)std::min<int64_t>(net->max_batch, n - b);
+    int rc = net->forward(reinterpret_cast<const bf16*>(crops) + b * 2 * kCrop * kCrop, onehot + b, nb, pred + b,
+                          nullptr);
+    if (rc) return rc;
+  }
+  return PERCH_OK;
+}
+
+int perch_cnn_gradients(perch_cnn* net, const uint16_t* crops, const int32_t* onehot, const float* target, int32_t n,
+                        float* grads, float* loss, float* pred) {
+  if (!net) return PERCH_E_ARG;
+  net->err.clear();
+  if (!crops || !onehot || !target || n < 32 || n > net->max_batch || n % 32)
+    return net->fail(PERCH_E_ARG, "need device crops / one-hot / targets and 32 <= n <= %d, n %% 32 == 0",
+                     net->max_batch);
+  CKN(cudaSetDevice(net->device), "cudaSetDevice");
+  int rc = net->ensure_batch(n);
+  if (rc) return rc;
+  rc = net->forward(reinterpret_cast<const bf16*>(crops), onehot, n, net->pred_buf.as<float>(), target);
+  if (rc) return rc;
+  rc = net->backward(reinterpret_cast<const bf16*>(crops), n);
+  if (rc) return rc;
+  if (grads) {
+    std::vector<float> h((size_t)net->n_total);
+    CKN(cudaMemcpyAsync(h.data(), net->grad.p, 4 * h.size(), cudaMemcpyDeviceToHost, net->stream), "copy");
+    CKN(cudaStreamSynchronize(net->stream), "gradients");
+    net->for_each_param([&](long long q, long long i) { grads[q] = h[i]; });
+  }
+  if (loss) CKN(cudaMemcpyAsync(loss, net->loss_buf.p, 4, cudaMemcpyDeviceToHost, net->stream), "copy");
+  if (pred) CKN(cudaMemcpyAsync(pred, net->pred_buf.p, 4 * (size_t)n, cudaMemcpyDeviceToHost, net->stream), "copy");
+  CKN(cudaStreamSynchronize(net->stream), "gradients");
+  return PERCH_OK;
+}
+
+int perch_cnn_train_step(perch_cnn* net, const uint16_t* crops, const int32_t* onehot, const float* target,
+                         int32_t n, float lr, float* loss) {
+  if (!net) return PERCH_E_ARG;
+  net->err.clear();
+  if (!crops || !onehot || !target || n < 32 || n > net->max_batch || n % 32 || !(lr > 0.0f))
+    return net->fail(PERCH_E_ARG, "need device crops / one-hot / targets, 32 <= n <= %d, n %% 32 == 0, lr > 0",
+                     net->max_batch);
+  CKN(cudaSetDevice(net->device), "cudaSetDevice");
+  int rc = net->forward(reinterpret_cast<const bf16*>(crops), onehot, n, net->pred_buf.as<float>(), target);
+  if (rc) return rc;
+  rc = net->backward(reinterpret_cast<const bf16*>(crops), n);
+  if (rc) return rc;
+  net->step++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = (float)(1.0 - std::pow((double)b1, (double)net->step));
+  const float c2 = (float)(1.0 - std::pow((double)b2, (double)net->step));
+  k_adam<<<grid_for(net->n_total), 256, 0, net->stream>>>(net->master.as<float>(), net->grad.as<float>(),
+                                                           net->adam_m.as<float>(), net->adam_v.as<float>(),
+                                                           net->n_total, lr, b1, b2, c1, c2, 1e-8f);
+  CKN(cudaGetLastError(), "adam kernel");
+  rc = net->refresh_weights();
+  if (rc) return rc;
+  if (loss) CKN(cudaMemcpyAsync(loss, net->loss_buf.p, 4, cudaMemcpyDeviceToDevice, net->stream), "copy loss");
+  return PERCH_OK;
+}
+
+int perch_cnn_crops(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride, const int32_t* parent_len,
+                    const int32_t* parent_scene, int32_t n_par, const int32_t* hyp_parent, const perch_obj* hyp,
+                    int64_t n_hyp, uint16_t* crops, int32_t* onehot) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (!ctx->has_obs) return ctx->fail(PERCH_E_STATE, "set an observation first");
+  if (n_hyp < 0 || n_hyp > 0x7fffffffLL) return ctx->fail(PERCH_E_ARG, "n_hyp out of range");
+  if (n_hyp == 0) return PERCH_OK;
+  if (!parent_len || !hyp_parent || !hyp || !crops || !onehot || n_par < 1 || parent_stride < 0 ||
+      (parent_stride > 0 && !parents))
+    return ctx->fail(PERCH_E_ARG, "null pointer or bad sizes");
+  if (n_par > 65535 || (long long)n_par * std::max(parent_stride, 1) > 65535)
+    return ctx->fail(PERCH_E_ARG, "too many parents in one batch (n_par x stride <= 65535)");
+  auto bad = [&](const perch_obj& o) {
+    return o.mesh >= ctx->n_mesh || o.ix < 0 || o.ix >= ctx->nx || o.iy < 0 || o.iy >= ctx->ny ||
+           o.iyaw >= ctx->n_yaw;
+  };
+  for (int i = 0; i < n_par; ++i) {
+    if (parent_len[i] < 0 || parent_len[i] > parent_stride)
+      return ctx->fail(PERCH_E_ARG, "parent %d: length %d outside [0, stride]", i, parent_len[i]);
+    if (parent_scene && (parent_scene[i] < 0 || parent_scene[i] >= (int)ctx->scenes.size()))
+      return ctx->fail(PERCH_E_ARG, "parent %d: scene %d not set", i, parent_scene[i]);
+    for (int k = 0; k < parent_len[i]; ++k)
+      if (bad(parents[(long long)i * parent_stride + k])) return ctx->fail(PERCH_E_ARG, "parent %d: bad object", i);
+  }
+  for (long long h = 0; h < n_hyp; ++h)
+    if (hyp_parent[h] < 0 || hyp_parent[h] >= n_par || bad(hyp[h]))
+      return ctx->fail(PERCH_E_ARG, "hypothesis %lld: bad parent or object", h);
+  perch_ctx* c = ctx;
+  auto ck = [c](cudaError_t e, const char* what) { return c->cuda(e, what); };
+  int rc;
+  if ((rc = ck(cudaSetDevice(ctx->device), "cudaSetDevice"))) return rc;
+  const size_t npx = (size_t)ctx->cam.W * ctx->cam.H;
+  const size_t pbytes = sizeof(perch_obj) * std::max<size_t>((size_t)n_par * parent_stride, 1);
+  if ((rc = ck(ctx->parent_z.ensure(4 * npx * n_par), "alloc parent z-buffers"))) return rc;
+  if ((rc = ck(ctx->b_parents.ensure(pbytes), "alloc"))) return rc;
+  if ((rc = ck(ctx->b_plen.ensure(8 * (size_t)n_par), "alloc"))) return rc;
+  if ((rc = ck(ctx->b_hp.ensure(4 * (size_t)n_hyp), "alloc"))) return rc;
+  if ((rc = ck(ctx->b_hyp.ensure(sizeof(perch_obj) * (size_t)n_hyp), "alloc"))) return rc;
+  int32_t* d_plen = ctx->b_plen.as<int32_t>();
+  cudaStream_t s = ctx->stream;
+  if (parent_stride > 0 &&
+      (rc = ck(cudaMemcpyAsync(ctx->b_parents.p, parents, sizeof(perch_obj) * (size_t)n_par * parent_stride,
+                               cudaMemcpyHostToDevice, s), "copy")))
+    return rc;
+  if ((rc = ck(cudaMemcpyAsync(d_plen, parent_len, 4 * (size_t)n_par, cudaMemcpyHostToDevice, s), "copy"))) return rc;
+  if (parent_scene &&
+      (rc = ck(cudaMemcpyAsync(d_plen + n_par, parent_scene, 4 * (size_t)n_par, cudaMemcpyHostToDevice, s), "copy")))
+    return rc;
+  if ((rc = ck(cudaMemcpyAsync(ctx->b_hp.p, hyp_parent, 4 * (size_t)n_hyp, cudaMemcpyHostToDevice, s), "copy")))
+    return rc;
+  if ((rc = ck(cudaMemcpyAsync(ctx->b_hyp.p, hyp, sizeof(perch_obj) * (size_t)n_hyp, cudaMemcpyHostToDevice, s),
+               "copy")))
+    return rc;
+  if ((rc = ck(launch_fill_u32(ctx->parent_z.as<uint32_t>(), kInfBits, (long long)npx * n_par, s), "clear")))
+    return rc;
+  Batch b;
+  std::memset(&b, 0, sizeof b);
+  b.parents = ctx->b_parents.as<perch_obj>();
+  b.parent_stride = std::max(parent_stride, 1);  // stride 0: every parent is empty
+  b.parent_len = d_plen;
+  b.n_par = n_par;
+  b.parent_z = ctx->parent_z.as<float>();
+  if ((rc = ck(launch_render_parents(ctx->cam, ctx->geometry(), b, ctx->max_chunks, nullptr, s), "render parents")))
+    return rc;
+  k_crops<<<(unsigned)n_hyp, 256, 0, s>>>(ctx->cam, ctx->xs.as<float>(), ctx->ys.as<float>(),
+                                          ctx->meshes.as<DevMesh>(), ctx->n_yaw, ctx->d_scene_img.as<const float*>(),
+                                          parent_scene ? d_plen + n_par : nullptr, ctx->parent_z.as<float>(),
+                                          ctx->b_hp.as<int32_t>(), ctx->b_hyp.as<perch_obj>(), n_hyp,
+                                          reinterpret_cast<bf16*>(crops), onehot);
+  if ((rc = ck(cudaGetLastError(), "crop kernel"))) return rc;
+  return ck(cudaStreamSynchronize(s), "crops");
+}
+
+int perch_set_heuristic_net(perch_ctx* ctx, perch_cnn* net, int32_t n_candidates) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (net && net->n_onehot < ctx->n_mesh * ctx->n_yaw)
+    return ctx->fail(PERCH_E_ARG, "network one-hot width %d < meshes x yaws %d", net->n_onehot,
+                     ctx->n_mesh * ctx->n_yaw);
+  if (n_candidates < 1 || n_candidates > 4096) return ctx->fail(PERCH_E_ARG, "n_candidates outside [1, 4096]");
+  ctx->net = net;
+  ctx->net_candidates = n_candidates;
+  return PERCH_OK;
+}
+
+}  // extern "C"

@@ -36,11 +36,14 @@ struct GraphKey {
 // One scene's observed cloud and its indices (device buffers).
 struct SceneBufs {
   DevBuf start3, start2, obs3, world2, cam2, dil3;
+  DevBuf img;  // the scene's depth image (H x W, metres, 0 = no return)
   perch::ObsIndex idx{};
   void release() {
-    for (DevBuf* b : {&start3, &start2, &obs3, &world2, &cam2, &dil3}) b->release();
+    for (DevBuf* b : {&start3, &start2, &obs3, &world2, &cam2, &dil3, &img}) b->release();
   }
 };
+
+struct perch_cnn;
 
 struct perch_ctx {
   int device = 0;
@@ -65,6 +68,7 @@ struct perch_ctx {
   DevBuf scratch_small;
   std::vector<SceneBufs> scenes;  // scene 0: perch_set_observation; others: perch_set_scene
   DevBuf d_scenes;                // ObsIndex per scene
+  DevBuf d_scene_img;             // const float* per scene: its depth image
   int max_obs = 0;                // largest cloud over the scenes
 
   // camera-frame pose tables and the screen box of every (mesh, pose)
@@ -87,15 +91,20 @@ struct perch_ctx {
   bool capturing = false;
   long long tables_version = 0;
 
+  // learned heuristic used by the search (heuristics bit 2); not owned
+  perch_cnn* net = nullptr;
+  int net_candidates = 16;
+  DevBuf net_crops, net_onehot, net_pred;
+
   // events around the phases of the last evaluation
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   bool timed = false;
 
   std::vector<DevBuf*> all_buffers() {
     return {&meshes, &chunk_verts, &chunk_info, &chunk_tris, &yaw_mats, &pose_off, &vtab, &xs, &ys, &cs, &depth, &rx, &ry, &blockcnt, &blockoff,
-            &scan_tmp, &cam_pts, &world_pts, &keys, &counts, &cursor, &d_scenes,
+            &scan_tmp, &cam_pts, &world_pts, &keys, &counts, &cursor, &d_scenes, &d_scene_img,
             &scratch_small, &pose_bbox, &parent_z, &uset, &uset_count, &b_parents, &b_plen, &b_hp, &b_hyp,
-            &b_out, &g_hist, &g_off, &g_cursor, &g_order, &g_next};
+            &b_out, &g_hist, &g_off, &g_cursor, &g_order, &g_next, &net_crops, &net_onehot, &net_pred};
   }
 
   int fail(int code, const char* fmt, ...);
@@ -107,3 +116,9 @@ struct perch_ctx {
                    const int32_t* d_hp, const perch_obj* d_hyp, long long n_hyp, int K_total, perch_cost* d_out,
                    const int32_t* d_parent_scene = nullptr, const int32_t* d_parent_K = nullptr);
 };
+
+// Learned heuristic: network predictions (host) for hypotheses over parents
+// (host arrays as perch_cnn_crops); crops and forward pass on the device.
+int net_predict(perch_ctx* ctx, perch_cnn* net, const perch_obj* parents, int parent_stride, const int32_t* plen,
+                const int32_t* pscene, int n_par, const int32_t* hyp_parent, const perch_obj* hyp, long long n_hyp,
+                float* pred_host);

@@ -13,8 +13,20 @@
 //
 // perch_search_multi runs one such search per scene and packs the expansions
 // of all unfinished scenes into shared evaluation launches.
+//
+// Learned queue (heuristics bit 2, not in the paper's experiments): every
+// expansion keeps, per remaining object type, its `n_candidates` cheapest valid
+// placements and their exact edge costs. A child s' gets the free estimate
+// h_free(s') = sum over its remaining objects of the cheapest exact cost of
+// that type at the parent; the queue's pool holds focal states ordered by
+// g + h_free. Each round the front of the pool is re-ranked by g + h_cnn, where
+// h_cnn(s') = sum over the remaining objects of min over the parent's
+// candidates of that type of (exp(prediction) - 1), the network's edge-cost
+// estimate with s' itself as the parent (its z-buffer in the crop). States are
+// scored once, lazily, in one batch across scenes.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <limits>
 #include <unordered_map>
@@ -58,6 +70,18 @@ struct State {
   int64_t g;
   bool closed;
   int64_t h_overlap;  // observed points outside the volumes of the state's objects
+  int parent = -1;    // state whose expansion generated the cheapest known way in
+  int exp = -1;       // this state's own expansion record (learned queue)
+  int64_t h_free = 0; // learned queue pool key part (see header)
+  double h_cnn = -1;  // < 0: not scored yet
+};
+
+// What the learned queue keeps of one expansion: per distinct remaining type,
+// up to T cheapest valid placements (mesh = 0xffff pads) and the cheapest cost.
+struct ExpansionRecord {
+  std::vector<int> types;
+  std::vector<perch_obj> top;  // types.size() x T
+  std::vector<int64_t> best;   // per type; kInf if no valid placement
 };
 
 struct HEntry {  // entry of an inadmissible queue
@@ -90,11 +114,15 @@ struct SceneSearch {
   bool done = false;
   double seconds = 0.0;
   double w = 1.0;
-  int heur = 0;                        // bit 0: h_depth, bit 1: h_overlap
+  int heur = 0;                        // bit 0: h_depth, bit 1: h_overlap, bit 2: learned
   std::vector<OpenEntry> pending;      // generated, not yet in the focal set (min g)
-  std::vector<HEntry> hq[2];           // focal states ordered by each heuristic
+  std::vector<HEntry> hq[3];           // focal states ordered by each heuristic
+  std::vector<ExpansionRecord> exps;   // learned queue: one per expanded state
+  std::vector<int> pool;               // learned queue: this round's candidates
+  int T = 16;                          // learned queue: placements kept per type
   bool focal() const { return w > 1.0 || heur != 0; }
   int64_t hval(int which, int idx) const {
+    if (which == 2) return states[idx].g + states[idx].h_free;
     return which == 0 ? (int64_t)(K - (int)states[idx].key.size()) : states[idx].h_overlap;
   }
   static bool hworse(const HEntry& a, const HEntry& b) {
@@ -155,7 +183,7 @@ struct SceneSearch {
       std::pop_heap(pending.begin(), pending.end(), gworse);
       pending.pop_back();
       if (stale(e)) continue;
-      for (int q = 0; q < 2; ++q)
+      for (int q = 0; q < 3; ++q)
         if (heur & (1 << q)) {
           hq[q].push_back(HEntry{hval(q, e.idx), e.g, e.idx});
           std::push_heap(hq[q].begin(), hq[q].end(), hworse);
@@ -183,7 +211,84 @@ struct SceneSearch {
         ++n;
       }
     }
-    if (out.empty() && heap.empty()) done = true;
+    if (heur & 4) {  // learned queue: gather the pool; the caller scores it and calls choose()
+      const int L = std::max(32, 4 * B);
+      pool.clear();
+      while ((int)pool.size() < L && !hq[2].empty()) {
+        const HEntry top = hq[2].front();
+        std::pop_heap(hq[2].begin(), hq[2].end(), hworse);
+        hq[2].pop_back();
+        State& st = states[top.idx];
+        if (st.closed || top.g > st.g || top.g > best_g) continue;
+        if (std::find(pool.begin(), pool.end(), top.idx) != pool.end()) continue;
+        pool.push_back(top.idx);
+      }
+    }
+    if (out.empty() && heap.empty() && pool.empty()) done = true;
+  }
+  // learned queue: expand the B pool states of smallest g + h_cnn; the rest go back
+  void choose(int B, std::vector<int>& out) {
+    std::vector<int> live;
+    for (int idx : pool)
+      if (!states[idx].closed) live.push_back(idx);
+    std::sort(live.begin(), live.end(), [this](int a, int b) {
+      const double fa = (double)states[a].g + states[a].h_cnn, fb = (double)states[b].g + states[b].h_cnn;
+      if (fa != fb) return fa < fb;
+      return a < b;
+    });
+    for (size_t k = 0; k < live.size(); ++k) {
+      if ((int)k < B) {
+        states[live[k]].closed = true;
+        out.push_back(live[k]);
+      } else {
+        hq[2].push_back(HEntry{hval(2, live[k]), states[live[k]].g, live[k]});
+        std::push_heap(hq[2].begin(), hq[2].end(), hworse);
+      }
+    }
+    pool.clear();
+  }
+  // learned queue: the expansion record of state `pidx` from its children's records
+  void record_expansion(int pidx, const perch_obj* hyps, const perch_cost* recs, long long n) {
+    ExpansionRecord er;
+    er.types = remaining(states[pidx].key);
+    const size_t nt = er.types.size();
+    er.top.assign(nt * T, perch_obj{0xffff, 0, 0, 0});
+    er.best.assign(nt, kInf);
+    std::vector<std::vector<std::pair<int64_t, long long>>> by(nt);
+    for (long long h = 0; h < n; ++h) {
+      if (recs[h].viol > 0) continue;
+      const size_t t = std::lower_bound(er.types.begin(), er.types.end(), (int)hyps[h].mesh) - er.types.begin();
+      if (t >= nt) continue;
+      by[t].push_back({(int64_t)recs[h].djr + recs[h].djo + recs[h].resid, h});
+    }
+    for (size_t t = 0; t < nt; ++t) {
+      const size_t k = std::min<size_t>(T, by[t].size());
+      std::partial_sort(by[t].begin(), by[t].begin() + k, by[t].end());
+      for (size_t j = 0; j < k; ++j) er.top[t * T + j] = hyps[by[t][j].second];
+      if (k) er.best[t] = by[t][0].first;
+    }
+    states[pidx].exp = (int)exps.size();
+    exps.push_back(std::move(er));
+  }
+  // free estimate of a child of `pidx` that keeps `rem` (sorted multiset) unplaced
+  int64_t free_estimate(int pidx, const std::vector<int>& rem_multiset) const {
+    const ExpansionRecord& er = exps[states[pidx].exp];
+    int64_t h = 0;
+    for (int m : rem_multiset) {
+      const size_t t = std::lower_bound(er.types.begin(), er.types.end(), m) - er.types.begin();
+      const int64_t b = t < er.types.size() ? er.best[t] : kInf;
+      h += b == kInf ? (int64_t)1 << 40 : b;
+    }
+    return h;
+  }
+  std::vector<int> remaining_multiset(const Key& key) const {
+    std::vector<int> rem = multiset;
+    for (uint64_t k : key) {
+      auto it = std::find(rem.begin(), rem.end(), (int)(k >> 48));
+      if (it != rem.end()) rem.erase(it);
+    }
+    std::sort(rem.begin(), rem.end());
+    return rem;
   }
   // pop up to B expandable states; marks the search done when none is left
   void pop(int B, std::vector<int>& out) {
@@ -216,6 +321,12 @@ struct SceneSearch {
     rem.erase(std::unique(rem.begin(), rem.end()), rem.end());
     return rem;
   }
+  void set_parent(int idx, int pidx) {
+    State& s = states[idx];
+    s.parent = pidx;
+    s.h_free = free_estimate(pidx, remaining_multiset(s.key));
+    s.h_cnn = -1.0;  // candidates changed: score again
+  }
   void absorb(int pidx, const perch_obj& h, const perch_cost& r) {
     if (r.viol > 0) return;  // occludes the parent: not a successor (Eq. (3))
     const int64_t ng = states[pidx].g + (int64_t)r.djr + r.djo + r.resid;
@@ -234,12 +345,14 @@ struct SceneSearch {
       const int idx = (int)states.size();
       states.push_back(State{std::move(ck), ng, false, states[pidx].h_overlap - (int64_t)r.n_vol});
       index.emplace(states[idx].key, idx);
+      if (heur & 4) set_parent(idx, pidx);
       add_open(ng, idx);
     } else {
       State& s = states[it->second];
       if (ng < s.g) {
         s.g = ng;
         s.closed = false;  // a cheaper way in: reopen
+        if ((heur & 4) && s.parent != pidx) set_parent(it->second, pidx);
         add_open(ng, it->second);
       }
     }
@@ -250,6 +363,86 @@ struct Work {
   int scene_slot;
   int state;
 };
+
+// Learned queue: h_cnn of every unscored state in the scenes' pools, one
+// batch of crops and one forward pass for all of them.
+int score_pools(perch_ctx* ctx, std::vector<SceneSearch>& ss) {
+  std::vector<Work> todo;
+  int stride = 1;
+  for (size_t k = 0; k < ss.size(); ++k)
+    for (int idx : ss[k].pool) {
+      State& st = ss[k].states[idx];
+      if (st.h_cnn >= 0.0) continue;
+      if (st.parent < 0) {
+        st.h_cnn = 0.0;  // the root: nothing placed, nothing to compare
+        continue;
+      }
+      todo.push_back(Work{(int)k, idx});
+      stride = std::max(stride, (int)st.key.size());
+    }
+  const int max_par = std::max(1, 65535 / stride);
+  std::vector<perch_obj> parents, hyps;
+  std::vector<int32_t> plen, pscene, hparent;
+  std::vector<int> hyp_type;  // remaining-type slot of each hypothesis
+  std::vector<float> pred;
+  for (size_t b0 = 0; b0 < todo.size(); b0 += max_par) {
+    const size_t b1 = std::min(todo.size(), b0 + (size_t)max_par);
+    parents.assign((b1 - b0) * stride, perch_obj{0, 0, 0, 0});
+    plen.assign(b1 - b0, 0);
+    pscene.assign(b1 - b0, 0);
+    hyps.clear();
+    hparent.clear();
+    hyp_type.clear();
+    std::vector<std::vector<int>> types(b1 - b0);
+    for (size_t i = b0; i < b1; ++i) {
+      SceneSearch& s = ss[todo[i].scene_slot];
+      const State& st = s.states[todo[i].state];
+      const size_t w = i - b0;
+      plen[w] = (int32_t)st.key.size();
+      pscene[w] = s.scene;
+      for (size_t j = 0; j < st.key.size(); ++j) parents[w * stride + j] = unpack(st.key[j]);
+      const ExpansionRecord& er = s.exps[s.states[st.parent].exp];
+      types[w] = s.remaining(st.key);
+      for (size_t t = 0; t < types[w].size(); ++t) {
+        const size_t et = std::lower_bound(er.types.begin(), er.types.end(), types[w][t]) - er.types.begin();
+        if (et >= er.types.size()) continue;
+        for (int j = 0; j < s.T; ++j) {
+          const perch_obj& o = er.top[et * s.T + j];
+          if (o.mesh == 0xffff) break;
+          hyps.push_back(o);
+          hparent.push_back((int32_t)w);
+          hyp_type.push_back((int)t);
+        }
+      }
+    }
+    pred.assign(hyps.size(), 0.0f);
+    if (!hyps.empty()) {
+      const int rc = net_predict(ctx, ctx->net, parents.data(), stride, plen.data(), pscene.data(),
+                                 (int32_t)(b1 - b0), hparent.data(), hyps.data(), (long long)hyps.size(), pred.data());
+      if (rc != PERCH_OK) return rc;
+    }
+    // per state and remaining type: the smallest predicted edge cost
+    std::vector<std::vector<double>> best(b1 - b0);
+    for (size_t w = 0; w < b1 - b0; ++w) best[w].assign(types[w].size(), 1e7);
+    for (size_t h = 0; h < hyps.size(); ++h) {
+      const double c = std::max(0.0, std::expm1((double)pred[h]));
+      double& b = best[hparent[h]][hyp_type[h]];
+      b = std::min(b, c);
+    }
+    for (size_t i = b0; i < b1; ++i) {
+      SceneSearch& s = ss[todo[i].scene_slot];
+      State& st = s.states[todo[i].state];
+      const size_t w = i - b0;
+      double h = 0.0;
+      for (int m : s.remaining_multiset(st.key)) {
+        const size_t t = std::lower_bound(types[w].begin(), types[w].end(), m) - types[w].begin();
+        h += t < types[w].size() ? best[w][t] : 1e7;
+      }
+      st.h_cnn = h;
+    }
+  }
+  return PERCH_OK;
+}
 
 // Run the searches until every one is done or a limit is reached.
 int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states, double time_limit_s,
@@ -277,6 +470,8 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
     work.clear();
     int64_t budget = max_hyps_per_launch > 0 ? std::max<int64_t>(max_hyps_per_launch, per_state_max)
                                              : (int64_t)B * per_state_max * (int64_t)ss.size();
+    std::vector<int> wants(ss.size(), 0);
+    bool any_pool = false;
     for (size_t k = 0; k < ss.size() && budget > 0 && (int)work.size() < 65535 / stride; ++k) {
       const size_t si = (rr + k) % ss.size();
       SceneSearch& s = ss[si];
@@ -288,6 +483,26 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
         work.push_back(Work{(int)si, idx});
         budget -= per_state_max;
       }
+      wants[si] = want;
+      any_pool |= !s.pool.empty();
+    }
+    if (any_pool) {  // learned queue: score the pools, then take each scene's best
+      if (!ctx->net) return ctx->fail(PERCH_E_STATE, "search: heuristic bit 2 needs perch_set_heuristic_net");
+      const int rc = score_pools(ctx, ss);
+      if (rc != PERCH_OK) return rc;
+      for (size_t si = 0; si < ss.size(); ++si) {
+        if (ss[si].pool.empty()) continue;
+        popped.clear();
+        ss[si].choose(std::max(1, wants[si]), popped);
+        for (int idx : popped) {
+          if ((int)work.size() >= 65535 / stride) {  // no room this launch: back into the open set
+            ss[si].states[idx].closed = false;
+            ss[si].add_open(ss[si].states[idx].g, idx);
+            continue;
+          }
+          work.push_back(Work{(int)si, idx});
+        }
+      }
     }
     rr = (rr + 1) % ss.size();
     if (work.empty()) continue;
@@ -297,7 +512,9 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
     pK.assign(work.size(), 1);
     hyps.clear();
     hparent.clear();
+    std::vector<size_t> hbeg(work.size() + 1, 0);
     for (size_t w = 0; w < work.size(); ++w) {
+      hbeg[w] = hyps.size();
       const SceneSearch& s = ss[work[w].scene_slot];
       const Key& key = s.states[work[w].state].key;
       plen[w] = (int32_t)key.size();
@@ -312,6 +529,7 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
               hparent.push_back((int32_t)w);
             }
     }
+    hbeg[work.size()] = hyps.size();
     out.resize(hyps.size());
     const int rc = multi ? perch_eval_successors_multi(ctx, parents.data(), stride, plen.data(), pscene.data(),
                                                        pK.data(), (int32_t)work.size(), hparent.data(),
@@ -322,7 +540,11 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
     if (rc != PERCH_OK) return rc;
     expansions += (int64_t)work.size();
     for (size_t w = 0; w < work.size(); ++w) {
-      ss[work[w].scene_slot].expansions++;
+      SceneSearch& s = ss[work[w].scene_slot];
+      s.expansions++;
+      if (s.heur & 4)
+        s.record_expansion(work[w].state, hyps.data() + hbeg[w], out.data() + hbeg[w],
+                           (long long)(hbeg[w + 1] - hbeg[w]));
     }
     for (size_t h = 0; h < hyps.size(); ++h) {
       const Work& w = work[hparent[h]];
@@ -352,7 +574,9 @@ int check_params(perch_ctx* ctx, const perch_search_params* prm) {
   if (!prm || prm->K < 1 || prm->K > 16 || !prm->mesh_multiset || prm->batch_states < 1)
     return ctx->fail(PERCH_E_ARG, "search: bad parameters");
   if (!(prm->w >= 1.0f)) return ctx->fail(PERCH_E_ARG, "search: w must be >= 1");
-  if (prm->heuristics & ~3) return ctx->fail(PERCH_E_ARG, "search: unknown heuristic bits %d", prm->heuristics);
+  if (prm->heuristics & ~7) return ctx->fail(PERCH_E_ARG, "search: unknown heuristic bits %d", prm->heuristics);
+  if ((prm->heuristics & 4) && !ctx->net)
+    return ctx->fail(PERCH_E_STATE, "search: heuristic bit 2 needs perch_set_heuristic_net");
   for (int i = 0; i < prm->K; ++i)
     if (prm->mesh_multiset[i] >= ctx->n_mesh) return ctx->fail(PERCH_E_ARG, "search: mesh %d out of range", i);
   return PERCH_OK;
@@ -369,6 +593,7 @@ extern "C" int perch_search(perch_ctx* ctx, const perch_search_params* prm, perc
   if (!ctx->has_obs) return ctx->fail(PERCH_E_STATE, "set an observation first");
   std::vector<SceneSearch> ss(1);
   ss[0].init(0, prm->K, prm->mesh_multiset, prm->w, prm->heuristics, ctx->scenes.empty() ? 0 : ctx->scenes[0].idx.n);
+  ss[0].T = ctx->net_candidates;
   const auto t0 = Clock::now();
   const int status = run_searches(ctx, ss, prm->batch_states, prm->time_limit_s, prm->max_expansions, 0, false);
   if (status != PERCH_OK && status != PERCH_E_TIMEOUT) return status;
@@ -394,6 +619,7 @@ extern "C" int perch_search_multi(perch_ctx* ctx, int32_t n_scenes, const int32_
       return ctx->fail(PERCH_E_ARG, "search %d: scene %d not set", i, scenes[i]);
     ss[i].init(scenes[i], params[i].K, params[i].mesh_multiset, params[i].w, params[i].heuristics,
                ctx->scenes[scenes[i]].idx.n);
+    ss[i].T = ctx->net_candidates;
   }
   double tl = 0.0;
   int64_t me = 0;

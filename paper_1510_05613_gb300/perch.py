@@ -26,7 +26,9 @@ EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_mesh
            "perch_set_observation", "perch_eval_successors", "perch_eval_successors_dev", "perch_render",
            "perch_search", "perch_last_timing", "perch_eval_successors_noalloc", "perch_autotune",
            "perch_eval_graph", "perch_set_threads", "perch_set_scene", "perch_eval_successors_multi",
-           "perch_search_multi")
+           "perch_search_multi", "perch_cnn_create", "perch_cnn_destroy", "perch_cnn_last_error",
+           "perch_cnn_param_count", "perch_cnn_set_params", "perch_cnn_get_params", "perch_cnn_crops",
+           "perch_cnn_forward", "perch_cnn_train_step", "perch_cnn_gradients", "perch_set_heuristic_net")
 
 
 class perch_mesh(ctypes.Structure):
@@ -88,6 +90,17 @@ def load(path: str = LIB_PATH):
         "perch_eval_successors_multi": ([P, P, I32, P, P, P, I32, P, P, I64, P], ctypes.c_int),
         "perch_search_multi": ([P, I32, P, P, I64, P], ctypes.c_int),
         "perch_eval_graph": ([P, P, I32, P, I32, P, P, I64, I32, P, P], ctypes.c_int),
+        "perch_cnn_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, P, I32, I32], ctypes.c_int),
+        "perch_cnn_destroy": ([P], ctypes.c_int),
+        "perch_cnn_last_error": ([P], ctypes.c_char_p),
+        "perch_cnn_param_count": ([P, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "perch_cnn_set_params": ([P, P, I64], ctypes.c_int),
+        "perch_cnn_get_params": ([P, P, I64], ctypes.c_int),
+        "perch_cnn_crops": ([P, P, I32, P, P, I32, P, P, I64, P, P], ctypes.c_int),
+        "perch_cnn_forward": ([P, P, P, I64, P], ctypes.c_int),
+        "perch_cnn_train_step": ([P, P, P, P, I32, F, P], ctypes.c_int),
+        "perch_cnn_gradients": ([P, P, P, P, I32, P, P, P], ctypes.c_int),
+        "perch_set_heuristic_net": ([P, P, I32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -253,6 +266,26 @@ class Perch:
                 "successors": int(r.successors), "seconds": float(r.seconds),
                 "proven_optimal": bool(r.proven_optimal), "status": rc}
 
+    def perch_cnn_crops(self, parents, hyp_parent, hyps, parent_scene=None):
+        """Network inputs of the hypotheses: (crops, onehot) as torch device
+        tensors, (n, 64, 64, 2) bfloat16 and (n,) int32."""
+        import torch
+        P, plen, stride = self.pack_parents(parents)
+        hp, h = _c(hyp_parent, np.int32), _c(hyps, OBJ)
+        ps = None if parent_scene is None else _c(parent_scene, np.int32)
+        crops = torch.empty((len(h), 64, 64, 2), dtype=torch.bfloat16, device="cuda")
+        onehot = torch.empty(len(h), dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        self._check(self.lib.perch_cnn_crops(self.h, P.ctypes.data, stride, plen.ctypes.data, _ptr(ps), len(plen),
+                                             _ptr(hp), _ptr(h), len(h), crops.data_ptr() if len(h) else None,
+                                             onehot.data_ptr() if len(h) else None))
+        return crops, onehot
+
+    def perch_set_heuristic_net(self, net, n_candidates: int = 16):
+        """Attach a PerchCNN (None detaches) for search heuristic bit 2."""
+        self._net = net  # keep it alive while attached
+        return self._check(self.lib.perch_set_heuristic_net(self.h, None if net is None else net.h, n_candidates))
+
     def perch_render(self, objs):
         o = _c(objs, OBJ)
         out = np.empty((self.H, self.W), np.float32)
@@ -278,6 +311,82 @@ class Perch:
         return {"cost": int(r.cost), "key": key, "objs": objs, "expansions": int(r.expansions),
                 "successors": int(r.successors), "seconds": float(r.seconds),
                 "proven_optimal": bool(r.proven_optimal), "status": rc}
+
+
+class PerchCNN:
+    """The learned heuristic's network on one GPU (perch_cnn_* entry points).
+    Device arrays are torch tensors; calls are ordered with torch's work by
+    synchronising the device around them."""
+
+    def __init__(self, n_onehot: int, max_batch: int = 256, device: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        rc = self.lib.perch_cnn_create(ctypes.byref(h), device, None, n_onehot, max_batch)
+        if rc != PERCH_OK:
+            raise PerchError(rc, "perch_cnn_create failed")
+        self.h = h
+        self.n_onehot = n_onehot
+        self.max_batch = max_batch
+        n = ctypes.c_int64(0)
+        self._check(self.lib.perch_cnn_param_count(self.h, ctypes.byref(n)))
+        self.n_params = int(n.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.perch_cnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != PERCH_OK:
+            raise PerchError(rc, self.lib.perch_cnn_last_error(self.h).decode())
+        return rc
+
+    def perch_cnn_set_params(self, params):
+        p = _c(np.concatenate([np.asarray(a, np.float32).reshape(-1) for a in params]), np.float32)
+        return self._check(self.lib.perch_cnn_set_params(self.h, p.ctypes.data, p.size))
+
+    def perch_cnn_get_params(self) -> np.ndarray:
+        p = np.empty(self.n_params, np.float32)
+        self._check(self.lib.perch_cnn_get_params(self.h, p.ctypes.data, p.size))
+        return p
+
+    def perch_cnn_forward(self, crops, onehot):
+        import torch
+        pred = torch.empty(crops.shape[0], dtype=torch.float32, device=crops.device)
+        torch.cuda.synchronize()
+        self._check(self.lib.perch_cnn_forward(self.h, crops.data_ptr(), onehot.data_ptr(), crops.shape[0],
+                                               pred.data_ptr()))
+        torch.cuda.synchronize()
+        return pred
+
+    def perch_cnn_train_step(self, crops, onehot, target, lr: float, loss=None):
+        """Enqueue one Adam step; ``loss`` (a device float32 tensor of one
+        element, optional) receives the batch loss."""
+        return self._check(self.lib.perch_cnn_train_step(self.h, crops.data_ptr(), onehot.data_ptr(),
+                                                         target.data_ptr(), crops.shape[0], lr,
+                                                         None if loss is None else loss.data_ptr()))
+
+    def perch_cnn_gradients(self, crops, onehot, target):
+        """(packed gradients, loss, predictions) on the host."""
+        import torch
+        n = crops.shape[0]
+        g = np.empty(self.n_params, np.float32)
+        loss = ctypes.c_float(0)
+        pred = np.empty(n, np.float32)
+        torch.cuda.synchronize()
+        self._check(self.lib.perch_cnn_gradients(self.h, crops.data_ptr(), onehot.data_ptr(), target.data_ptr(), n,
+                                                 g.ctypes.data, ctypes.byref(loss), pred.ctypes.data))
+        return g, float(loss.value), pred
+
+    def synchronize(self):
+        import torch
+        torch.cuda.synchronize()
 
 
 def records(out) -> np.ndarray:
