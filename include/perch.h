@@ -20,8 +20,19 @@
  *   - world frame: z up, table plane z = 0; camera frame: x right, y down,
  *     z forward (pinhole, pixel centres at integer (u, v), depth = camera Z);
  *   - all floating-point arithmetic on the evaluation path is IEEE binary32
- *     with round-to-nearest-even and no fused multiply-add, in the operation
- *     order the oracle in oracle/ states, so results are bit-exact with it.
+ *     with round-to-nearest-even, in the operation order the oracle in
+ *     oracle/ states; a fused multiply-add (one rounding) appears exactly
+ *     where that order writes one and nowhere else, so results are bit-exact
+ *     with it:
+ *       vertex   c_r = fma(M_r2, v_z, fma(M_r1, v_y, M_r0 v_x)) + b_r with
+ *                M = R_cw Rz(yaw) and b = R_cw (x, y, 0) + t_cw (double,
+ *                rounded once); 1/z = 1 / c_z; u = fma(f_x, c_x (1/z), c_x0);
+ *                snapped X = rint(16 u);
+ *       depth    1/z = fma(b2, 1/z2, fma(b1, 1/z1, b0 (1/z0))), z = 1 / (1/z),
+ *                b_i = (float)E_i * (1 / (float)A) from exact integer edge
+ *                functions E_i and twice the area A;
+ *       Eq. (1)  d^2 = fma(dz, dz, fma(dy, dy, dx dx)) <= (float)(delta^2);
+ *       V(O)     fma(dy, dy, dx dx) <= (float)(r^2), z_lo <= z <= z_hi.
  */
 #ifndef PERCH_H_
 #define PERCH_H_
@@ -102,8 +113,8 @@ int perch_destroy(perch_ctx* ctx);
 const char* perch_last_error(const perch_ctx* ctx);
 
 /* Upload n object meshes (Sec. III: the known 3D models). Replaces any
- * previous meshes. Meshes are split into meshlets on the host (at most 64
- * vertices and 64 triangles each). Errors: PERCH_E_ARG for empty meshes,
+ * previous meshes. Meshes are split into chunks on the host (at most 512
+ * vertices and 1024 triangles each). Errors: PERCH_E_ARG for empty meshes,
  * out-of-range indices or n < 1. */
 int perch_load_meshes(perch_ctx* ctx, const perch_mesh* meshes, int32_t n);
 
@@ -195,7 +206,14 @@ int perch_render(perch_ctx* ctx, const perch_obj* objs, int32_t n, float* depth_
  * states with g <= w * (smallest anchor key) are also expanded greedily by
  * each inadmissible heuristic in `heuristics` (bit 0: h_depth = K - |s|;
  * bit 1: h_overlap = observed points outside the assigned volumes,
- * Sec. IV-C), and the search returns a scene of cost <= w * OPT
+ * Sec. IV-C; bit 2: the learned heuristic of perch_set_heuristic_net: each
+ * expansion keeps the n_candidates cheapest valid placements of every
+ * remaining type; a child's queue pool is ordered by g + the sum of its
+ * remaining objects' cheapest exact costs at the parent, and each round the
+ * front of the pool is re-ranked by g + h_cnn, h_cnn = sum over the remaining
+ * objects of the smallest predicted edge cost exp(y) - 1 among the parent's
+ * candidates of that type, predicted with the child as parent; PERCH_E_STATE
+ * without a network), and the search returns a scene of cost <= w * OPT
  * (Theorem 2). mesh_multiset[K]: the types of the K objects (Sec. III: known
  * number and types). batch_states: states taken from each queue per device
  * launch (>= 1). Stops at the optimum / the bound, or at time_limit_s /

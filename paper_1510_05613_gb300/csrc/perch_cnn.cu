@@ -9,12 +9,15 @@
 //   conv 3x3 2->32 s1, 32->64 s2, 64->128 s2, 128->128 s2 (pad 1, ReLU)
 //   -> flatten (h, w, c) ++ one-hot -> FC 96 (ReLU) -> FC 1; loss 0.5 (pred - y)^2
 //
-// Data layout: activations NHWC bfloat16; every convolution is an explicit
-// im2col ([rows = N x Ho x Wo][K = 9 Cin padded to 32]) followed by one GEMM
-// C = A B^T with both operands K-contiguous. The GEMM is mma.sync m16n8k16
-// (BF16 in, FP32 accumulate) fed by a 3-stage cp.async pipeline and ldmatrix.
-// Weight gradients are GEMMs over the transposed activations, split along the
-// reduction and summed in a fixed order (deterministic). Gradients between
+// Data layout: activations NHWC bfloat16. Every convolution is one GEMM over
+// rows = output pixels (N x Ho x Wo) and columns = (tap, channel) (K = 9 Cin,
+// padded to 32): the 2-channel input layer through an explicit im2col, the
+// others by gathering 16-byte chunks of the NHWC input straight into shared
+// memory (implicit im2col, zero padding through the copy's source size). The
+// GEMM is mma.sync m16n8k16 (BF16 in, FP32 accumulate) fed by a 3-stage
+// cp.async pipeline and ldmatrix (.trans for MN-contiguous operands). Weight
+// gradients reduce over pixels with both operands read in place, split along
+// the reduction and summed in a fixed order (deterministic). Gradients between
 // layers are rounded to bfloat16, like the activations; weights keep an FP32
 // master copy updated by Adam and re-rounded to bfloat16 after each step.
 #include <cuda_bf16.h>
@@ -65,6 +68,10 @@ struct GemmArgs {
   long long ldg;
   long long split_stride;
   const float* bias;
+  // implicit im2col (CONV = 1: A, CONV = 2: B): the operand is the NHWC
+  // input of a 3x3 pad-1 convolution with power-of-two channels and output
+  // side; pixel index (n, i, j) and column index (tap, c), tap = 3 kh + kw
+  int cH, cs, lg_c, lg_wo;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -83,6 +90,11 @@ __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r
                : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
                : "r"(addr));
 }
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
 __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
@@ -91,13 +103,32 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// C[M x N] = A[M x K] B[N x K]^T. 256 threads; CTA tile 128 x BN; warp tile
-// (128 / (8 / (BN / 32))) x 32. K (and Ksplit) multiples of 32.
-template <int BN, int EPI>
+// C[M x N] = A B^T over K. A is K-contiguous (AK: element (m, k) at
+// m lda + k) or M-contiguous (element (m, k) at k lda + m); B likewise
+// (BKC: (n, k) at n ldb + k, else k ldb + n). MN-contiguous operands are
+// staged as [k][m] tiles and fed to the tensor cores with ldmatrix .trans, so
+// weight and data gradients need no transposed copies. 256 threads; CTA tile
+// 128 x BN; warp tile (128 / (8 / (BN / 32))) x 32. K and Ksplit multiples of
+// 32; an MN-contiguous operand needs its M (or N) to be a multiple of 8.
+// Source of one 16-byte chunk of an implicit im2col operand: output pixel
+// `m`, columns k .. k + 7 (one tap, 8 channels); nullptr where the tap falls
+// in the zero padding.
+__device__ __forceinline__ const bf16* conv_src(const GemmArgs& p, const bf16* x, int m, int k) {
+  const int tap = k >> p.lg_c, c = k & ((1 << p.lg_c) - 1);
+  const int wo = 1 << p.lg_wo;
+  const int j = m & (wo - 1), i = (m >> p.lg_wo) & (wo - 1), n = m >> (2 * p.lg_wo);
+  const int r = p.cs * i - 1 + tap / 3, cc = p.cs * j - 1 + tap % 3;
+  if (tap >= 9 || r < 0 || r >= p.cH || cc < 0 || cc >= p.cH) return nullptr;
+  return x + ((((long long)n * p.cH + r) * p.cH + cc) << p.lg_c) + c;
+}
+
+template <int BN, int EPI, bool AK, bool BKC, int CONV>
 __global__ void __launch_bounds__(256) k_gemm(GemmArgs p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  bf16* As = reinterpret_cast<bf16*>(smem_raw);  // [STAGES][BM][LDS]
-  bf16* Bs = As + STAGES * BM * LDS;              // [STAGES][BN][LDS]
+  constexpr int A_LD = AK ? LDS : BM + 8, A_STAGE = AK ? BM * LDS : BK * (BM + 8);
+  constexpr int B_LD = BKC ? LDS : BN + 8, B_STAGE = BKC ? BN * LDS : BK * (BN + 8);
+  bf16* As = reinterpret_cast<bf16*>(smem_raw);  // [STAGES][A_STAGE]
+  bf16* Bs = As + STAGES * A_STAGE;               // [STAGES][B_STAGE]
   constexpr int WN = BN / 32, WM = 8 / WN, TM = BM / WM, MI = TM / 16;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int wm = warp / WN, wn = warp % WN;
@@ -115,17 +146,51 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs p) {
 
   auto load = [&](int stage, int kt) {
     const int k0 = kbeg + kt * BK;
-    for (int c = tid; c < BM * 4; c += 256) {
-      const int r = c >> 2, q = c & 3, gm = m0 + r;
-      const bool ok = gm < p.M;
-      const bf16* src = ok ? p.A + (long long)gm * p.lda + k0 + q * 8 : p.A;
-      cp_async16(smem_addr(As + (stage * BM + r) * LDS + q * 8), src, ok);
+    bf16* as = As + stage * A_STAGE;
+    bf16* bs = Bs + stage * B_STAGE;
+    if (AK) {
+      for (int c = tid; c < BM * 4; c += 256) {
+        const int r = c >> 2, q = c & 3, gm = m0 + r;
+        bool ok = gm < p.M;
+        const bf16* src = p.A;
+        if (CONV == 1) {
+          const bf16* g = ok ? conv_src(p, p.A, gm, k0 + q * 8) : nullptr;
+          ok = g != nullptr;
+          if (ok) src = g;
+        } else if (ok) {
+          src = p.A + (long long)gm * p.lda + k0 + q * 8;
+        }
+        cp_async16(smem_addr(as + r * A_LD + q * 8), src, ok);
+      }
+    } else {
+      for (int c = tid; c < BK * (BM / 8); c += 256) {
+        const int r = c / (BM / 8), q = c % (BM / 8), gm = m0 + q * 8;
+        const bool ok = gm < p.M;
+        const bf16* src = ok ? p.A + (long long)(k0 + r) * p.lda + gm : p.A;
+        cp_async16(smem_addr(as + r * A_LD + q * 8), src, ok);
+      }
     }
-    for (int c = tid; c < BN * 4; c += 256) {
-      const int r = c >> 2, q = c & 3, gn = n0 + r;
-      const bool ok = gn < p.N;
-      const bf16* src = ok ? p.B + (long long)gn * p.ldb + k0 + q * 8 : p.B;
-      cp_async16(smem_addr(Bs + (stage * BN + r) * LDS + q * 8), src, ok);
+    if (BKC) {
+      for (int c = tid; c < BN * 4; c += 256) {
+        const int r = c >> 2, q = c & 3, gn = n0 + r;
+        const bool ok = gn < p.N;
+        const bf16* src = ok ? p.B + (long long)gn * p.ldb + k0 + q * 8 : p.B;
+        cp_async16(smem_addr(bs + r * B_LD + q * 8), src, ok);
+      }
+    } else {
+      for (int c = tid; c < BK * (BN / 8); c += 256) {
+        const int r = c / (BN / 8), q = c % (BN / 8), gn = n0 + q * 8;
+        bool ok = gn < p.N;
+        const bf16* src = p.B;
+        if (CONV == 2) {
+          const bf16* g = ok ? conv_src(p, p.B, k0 + r, gn) : nullptr;
+          ok = g != nullptr;
+          if (ok) src = g;
+        } else if (ok) {
+          src = p.B + (long long)(k0 + r) * p.ldb + gn;
+        }
+        cp_async16(smem_addr(bs + r * B_LD + q * 8), src, ok);
+      }
     }
   };
 #pragma unroll
@@ -141,22 +206,37 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs p) {
       if (nk < KT) load(nk % STAGES, nk);
       cp_commit();
     }
-    const bf16* as = As + (kt % STAGES) * BM * LDS;
-    const bf16* bs = Bs + (kt % STAGES) * BN * LDS;
+    const bf16* as = As + (kt % STAGES) * A_STAGE;
+    const bf16* bs = Bs + (kt % STAGES) * B_STAGE;
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
       uint32_t af[MI][4], bfr[4][2];
 #pragma unroll
       for (int i = 0; i < MI; ++i) {
-        const int row = wm * TM + i * 16 + (lane & 15), col = kk * 16 + (lane >> 4) * 8;
-        ldsm_x4(smem_addr(as + row * LDS + col), af[i][0], af[i][1], af[i][2], af[i][3]);
+        const int mb = wm * TM + i * 16;
+        if (AK) {
+          const int row = mb + (lane & 15), col = kk * 16 + (lane >> 4) * 8;
+          ldsm_x4(smem_addr(as + row * A_LD + col), af[i][0], af[i][1], af[i][2], af[i][3]);
+        } else {  // matrices (m, k) blocks: (0, 0), (8, 0), (0, 8), (8, 8)
+          const int q = lane >> 3;
+          const int mm = mb + 8 * (q & 1), kr = kk * 16 + 8 * (q >> 1) + (lane & 7);
+          ldsm_x4_t(smem_addr(as + kr * A_LD + mm), af[i][0], af[i][1], af[i][2], af[i][3]);
+        }
       }
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const int row = wn * 32 + j * 16 + (lane & 7) + ((lane >> 4) << 3);
-        const int col = kk * 16 + ((lane >> 3) & 1) * 8;
-        ldsm_x4(smem_addr(bs + row * LDS + col), bfr[2 * j][0], bfr[2 * j][1], bfr[2 * j + 1][0],
-                bfr[2 * j + 1][1]);
+        const int nb = wn * 32 + j * 16;
+        if (BKC) {
+          const int row = nb + (lane & 7) + ((lane >> 4) << 3);
+          const int col = kk * 16 + ((lane >> 3) & 1) * 8;
+          ldsm_x4(smem_addr(bs + row * B_LD + col), bfr[2 * j][0], bfr[2 * j][1], bfr[2 * j + 1][0],
+                  bfr[2 * j + 1][1]);
+        } else {  // matrices (n, k) blocks: (0, 0), (0, 8), (8, 0), (8, 8)
+          const int q = lane >> 3;
+          const int nn = nb + 8 * (q >> 1), kr = kk * 16 + 8 * (q & 1) + (lane & 7);
+          ldsm_x4_t(smem_addr(bs + kr * B_LD + nn), bfr[2 * j][0], bfr[2 * j][1], bfr[2 * j + 1][0],
+                    bfr[2 * j + 1][1]);
+        }
       }
 #pragma unroll
       for (int i = 0; i < MI; ++i)
@@ -187,66 +267,77 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs p) {
       }
 }
 
-template <int BN, int EPI>
+template <int BN, int EPI, bool AK, bool BKC, int CONV>
 cudaError_t gemm_bn(const GemmArgs& p, int splits, cudaStream_t s) {
-  const int smem = STAGES * (BM + BN) * LDS * (int)sizeof(bf16);
-  cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  constexpr int A_STAGE = AK ? BM * LDS : BK * (BM + 8), B_STAGE = BKC ? BN * LDS : BK * (BN + 8);
+  const int smem = STAGES * (A_STAGE + B_STAGE) * (int)sizeof(bf16);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_gemm<BN, EPI, AK, BKC, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((p.N + BN - 1) / BN, (p.M + BM - 1) / BM, splits);
-  k_gemm<BN, EPI><<<grid, 256, smem, s>>>(p);
+  k_gemm<BN, EPI, AK, BKC, CONV><<<grid, 256, smem, s>>>(p);
   return cudaGetLastError();
 }
 
-template <int EPI>
+// C = A B^T (layouts as k_gemm); `splits` CTAs along K, each writing its
+// partial at Cf + z split_stride (EPI_F32) or, with one split, the epilogue.
+template <int EPI, bool AK = true, bool BKC = true, int CONV = 0>
 cudaError_t gemm(GemmArgs p, int splits, cudaStream_t s) {
   if (p.grp <= 0) {
     p.grp = 1 << 30;
     p.ldg = 0;
   }
-  if (p.N <= 32) return gemm_bn<32, EPI>(p, splits, s);
-  if (p.N <= 64) return gemm_bn<64, EPI>(p, splits, s);
-  return gemm_bn<128, EPI>(p, splits, s);
+  if ((!AK && p.M % 8) || (!BKC && p.N % 8) || p.K % 32 || p.Ksplit % 32) return cudaErrorInvalidValue;
+  if (CONV && p.lg_c < 3) return cudaErrorInvalidValue;  // chunks of 8 channels within one tap
+  if (p.N <= 32) return gemm_bn<32, EPI, AK, BKC, CONV>(p, splits, s);
+  if (p.N <= 64) return gemm_bn<64, EPI, AK, BKC, CONV>(p, splits, s);
+  return gemm_bn<128, EPI, AK, BKC, CONV>(p, splits, s);
+}
+
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+void set_conv(GemmArgs& p, int l) {
+  p.cH = kHin[l];
+  p.cs = kStride[l];
+  p.lg_c = ilog2(kCin[l]);
+  p.lg_wo = ilog2(kHin[l] / kStride[l]);
+}
+
+// splits along K so that the grid has about two CTAs per SM (each split a
+// multiple of 32 long, at least 256)
+int choose_splits(int M, int N, int K, int* ksplit) {
+  const int bn = N <= 32 ? 32 : N <= 64 ? 64 : 128;
+  const int tiles = ((M + BM - 1) / BM) * ((N + bn - 1) / bn);
+  int S = std::max(1, std::min((2 * 152 + tiles - 1) / tiles, K / 256));
+  int ks = (K / S + 31) / 32 * 32;
+  S = (K + ks - 1) / ks;
+  *ksplit = ks;
+  return S;
 }
 
 // ---------------------------------------------------------------- layout kernels
-// col[m][k] of a 3x3 pad-1 stride-s convolution, k = (kh 3 + kw) Cin + c;
-// zero for k >= 9 Cin and outside the image. One thread per 8 columns.
-__global__ void k_im2col(const bf16* __restrict__ x, int N, int H, int W, int Cin, int s, int Kp,
-                         bf16* __restrict__ col) {
-  const int Ho = H / s, Wo = W / s;
-  const int chunks = Kp / 8;
-  const long long total = (long long)N * Ho * Wo * chunks;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(e % chunks);
-    const long long m = e / chunks;
-    const int j = (int)(m % Wo), i = (int)((m / Wo) % Ho);
-    const long long n = m / ((long long)Wo * Ho);
-    const int k0 = q * 8;
-    uint4 out;
-    if ((Cin & 7) == 0) {
-      const int tap = k0 / Cin, c = k0 % Cin;
-      const int r = s * i - 1 + tap / 3, cc = s * j - 1 + tap % 3;
-      if (tap < 9 && r >= 0 && r < H && cc >= 0 && cc < W)
-        out = *reinterpret_cast<const uint4*>(x + ((n * H + r) * W + cc) * Cin + c);
-      else
-        out = make_uint4(0, 0, 0, 0);
-    } else {
-      unsigned short v[8];
-      for (int t = 0; t < 8; ++t) {
-        const int k = k0 + t;
-        v[t] = 0;
-        if (k < 9 * Cin) {
-          const int tap = k / Cin, c = k % Cin;
-          const int r = s * i - 1 + tap / 3, cc = s * j - 1 + tap % 3;
-          if (r >= 0 && r < H && cc >= 0 && cc < W)
-            v[t] = reinterpret_cast<const unsigned short*>(x)[((n * H + r) * W + cc) * Cin + c];
-        }
-      }
-      out = make_uint4(v[0] | (uint32_t)v[1] << 16, v[2] | (uint32_t)v[3] << 16, v[4] | (uint32_t)v[5] << 16,
-                       v[6] | (uint32_t)v[7] << 16);
+// im2col of the 2-channel input layer (stride 1, Kp = 32): one thread per
+// output pixel gathers its 9 taps (4 bytes each) and writes one 64-byte row
+__global__ void k_im2col_c2(const uint32_t* __restrict__ x, int N, int H, int W, uint4* __restrict__ col) {
+  const long long total = (long long)N * H * W;
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < total;
+       m += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(m % W), i = (int)((m / W) % H);
+    const long long n = m / ((long long)W * H);
+    uint32_t v[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = 0u;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int r = i - 1 + tap / 3, c = j - 1 + tap % 3;
+      if (r >= 0 && r < H && c >= 0 && c < W) v[tap] = x[(n * H + r) * W + c];
     }
-    *reinterpret_cast<uint4*>(col + m * Kp + k0) = out;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) col[m * 4 + q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
   }
 }
 
@@ -295,30 +386,34 @@ __global__ void k_col2im_relu(const float* __restrict__ dcol, const bf16* __rest
   }
 }
 
-// out[c][r] = in[r][c] for a bfloat16 matrix with R, C multiples of 32.
-__global__ void k_transpose(const unsigned short* __restrict__ in, long long R, int C,
-                            unsigned short* __restrict__ out) {
-  __shared__ unsigned short tile[32][33];
-  const long long r0 = (long long)blockIdx.x * 32;  // rows on x: up to 2^31 - 1 blocks
-  const int c0 = blockIdx.y * 32;
-  for (int k = threadIdx.y; k < 32; k += 8) tile[k][threadIdx.x] = in[(r0 + k) * C + c0 + threadIdx.x];
+// part[b][c] = sum of column c over rows [b R, (b + 1) R) of a bfloat16
+// [M][C] matrix (bias gradients); 256 threads, 256 / C row groups.
+__global__ void k_col_sum(const bf16* __restrict__ in, long long M, int C, int R, float* __restrict__ part) {
+  __shared__ float red[256];
+  const int G = 256 / C;
+  const int c = threadIdx.x % C, grp = threadIdx.x / C;
+  const long long r0 = (long long)blockIdx.x * R;
+  const long long r1 = min(M, r0 + R);
+  float a = 0.0f;
+  if (grp < G)
+    for (long long r = r0 + grp; r < r1; r += G) a += __bfloat162float(in[r * C + c]);
+  red[threadIdx.x] = a;
   __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += 8) out[(long long)(c0 + k) * R + r0 + threadIdx.x] = tile[threadIdx.x][k];
+  if (threadIdx.x < C) {
+    float v = 0.0f;
+    for (int k = 0; k < G; ++k) v += red[k * C + threadIdx.x];
+    part[(long long)blockIdx.x * C + threadIdx.x] = v;
+  }
 }
 
-// out[r] = sum of row r of a bfloat16 [R][C] matrix (fixed order).
-__global__ void k_row_sum(const bf16* __restrict__ in, long long C, float* __restrict__ out) {
-  const bf16* row = in + (long long)blockIdx.x * C;
-  float a = 0.0f;
-  for (long long k = threadIdx.x; k < C; k += blockDim.x) a += __bfloat162float(row[k]);
-  __shared__ float red[32];
-  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    a = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.0f;
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (threadIdx.x == 0) out[blockIdx.x] = a;
+// out[r][c] = bf16(relu(sum over z of part[z][r][c] + bias[c])) (split-K FC1)
+__global__ void k_splits_bias_relu(const float* __restrict__ part, int splits, long long rows, int C,
+                                   const float* __restrict__ bias, bf16* __restrict__ out) {
+  const long long n = rows * C;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    float a = 0.0f;
+    for (int z = 0; z < splits; ++z) a += part[(long long)z * n + e];
+    out[e] = __float2bfloat16_rn(fmaxf(a + bias[e % C], 0.0f));
   }
 }
 
@@ -360,34 +455,61 @@ __global__ void k_fc2(const bf16* __restrict__ h1, const float* __restrict__ w2,
   }
 }
 
-// loss = mean 0.5 err^2; grads of w2, b2; dz1 = (err / n) bf16(w2) [h1 > 0]
-// (rows n..n_rows-1 of dz1 zero). One block of 256 threads.
-__global__ void k_fc2_backward(const bf16* __restrict__ h1, const float* __restrict__ w2, const float* __restrict__ err,
-                               int n, int n_rows, float* __restrict__ g_w2, float* __restrict__ g_b2,
-                               float* __restrict__ loss, bf16* __restrict__ dz1) {
+// loss = mean 0.5 err^2 and the gradient of b2 (one block)
+__global__ void k_fc2_loss(const float* __restrict__ err, int n, float* __restrict__ g_b2, float* __restrict__ loss) {
+  __shared__ float red[2][32];
+  const float inv = 1.0f / (float)n;
+  float l = 0.0f, gb = 0.0f;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    l += 0.5f * err[r] * err[r];
+    gb += err[r] * inv;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    l += __shfl_xor_sync(0xffffffffu, l, o);
+    gb += __shfl_xor_sync(0xffffffffu, gb, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = l;
+    red[1][threadIdx.x >> 5] = gb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = 0.0f, b = 0.0f;
+    for (int k = 0; k < (int)blockDim.x / 32; ++k) {
+      a += red[0][k];
+      b += red[1][k];
+    }
+    if (loss) *loss = a * inv;
+    g_b2[0] = b;
+  }
+}
+
+// gradient of w2: one block per hidden unit j, sum over the batch
+__global__ void k_fc2_wgrad(const bf16* __restrict__ h1, const float* __restrict__ err, int n, float* __restrict__ g_w2) {
   __shared__ float red[32];
+  const int j = blockIdx.x;
   const float inv = 1.0f / (float)n;
   float a = 0.0f;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) a += 0.5f * err[r] * err[r];
+  for (int r = threadIdx.x; r < n; r += blockDim.x) a += err[r] * inv * __bfloat162float(h1[(long long)r * kHidden + j]);
   for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
   __syncthreads();
   if (threadIdx.x == 0) {
-    float l = 0.0f, gb = 0.0f;
-    for (int k = 0; k < (int)blockDim.x / 32; ++k) l += red[k];
-    for (int r = 0; r < n; ++r) gb += err[r] * inv;
-    if (loss) *loss = l * inv;
-    g_b2[0] = gb;
+    float v = 0.0f;
+    for (int k = 0; k < (int)blockDim.x / 32; ++k) v += red[k];
+    g_w2[j] = v;
   }
-  for (int j = threadIdx.x; j < kHidden; j += blockDim.x) {
-    float g = 0.0f;
-    for (int r = 0; r < n; ++r) g += err[r] * inv * __bfloat162float(h1[(long long)r * kHidden + j]);
-    g_w2[j] = g;
-  }
-  for (long long e = threadIdx.x; e < (long long)n_rows * kHidden; e += blockDim.x) {
+}
+
+// dz1 = (err / n) bf16(w2) [h1 > 0]
+__global__ void k_fc2_dz1(const bf16* __restrict__ h1, const float* __restrict__ w2, const float* __restrict__ err,
+                          int n, bf16* __restrict__ dz1) {
+  const float inv = 1.0f / (float)n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * kHidden;
+       e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e / kHidden), j = (int)(e % kHidden);
     float v = 0.0f;
-    if (r < n && __bfloat162float(h1[e]) > 0.0f) v = err[r] * inv * __bfloat162float(__float2bfloat16_rn(w2[j]));
+    if (__bfloat162float(h1[e]) > 0.0f) v = err[r] * inv * __bfloat162float(__float2bfloat16_rn(w2[j]));
     dz1[e] = __float2bfloat16_rn(v);
   }
 }
@@ -504,11 +626,10 @@ struct perch_cnn {
   // FP32 master layout: conv weights [Cout][Kp], FC1 [96][Kf] (the bfloat16
   // region, contiguous), then conv biases, FC1 bias, FC2 weights, FC2 bias
   long long off_w[kConvs], off_f1, n_w16, off_b[kConvs], off_fb1, off_f2, off_fb2, n_total;
-  DevBuf master, grad, adam_m, adam_v, w16, wt16;
-  long long off_wt[kConvs], off_f1t;
+  DevBuf master, grad, adam_m, adam_v, w16;
   // batch buffers
   DevBuf col[kConvs], act[kConvs], feat, h1, err_buf, pred_buf, loss_buf;
-  DevBuf dz1, dz1t, featt, dfeat, dz, dzt, colt, dcol, part;
+  DevBuf dz1, dfeat, dz, dcol, part, bpart;
   bool params_set = false;
 
   int fail(int code, const char* fmt, ...) {
@@ -527,8 +648,8 @@ struct perch_cnn {
     return fail(PERCH_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
   }
   std::vector<DevBuf*> buffers() {
-    std::vector<DevBuf*> v = {&master, &grad, &adam_m, &adam_v, &w16, &wt16, &feat, &h1, &err_buf, &pred_buf,
-                              &loss_buf, &dz1, &dz1t, &featt, &dfeat, &dz, &dzt, &colt, &dcol, &part};
+    std::vector<DevBuf*> v = {&master, &grad, &adam_m, &adam_v, &w16, &feat, &h1, &err_buf, &pred_buf,
+                              &loss_buf, &dz1, &dfeat, &dz, &dcol, &part, &bpart};
     for (int l = 0; l < kConvs; ++l) {
       v.push_back(&col[l]);
       v.push_back(&act[l]);
@@ -555,12 +676,6 @@ struct perch_cnn {
     off_fb2 = o;
     o += 4;
     n_total = o;
-    long long t = 0;
-    for (int l = 0; l < kConvs; ++l) {
-      off_wt[l] = t;
-      t += (long long)kCout[l] * kp_of(l);
-    }
-    off_f1t = t;
   }
   long long n_params() const {  // unpadded count, the packed order of the ABI
     long long n = 0;
@@ -606,7 +721,7 @@ int perch_cnn::ensure_batch(int n) {
   const long long N = std::max(n, 32);
   for (int l = 0; l < kConvs; ++l) {
     const long long Ho = kHin[l] / kStride[l];
-    CKN(col[l].ensure(2 * N * Ho * Ho * kp_of(l)), "alloc im2col");
+    if (l == 0) CKN(col[0].ensure(2 * N * Ho * Ho * kp_of(0)), "alloc im2col");
     if (l < kConvs - 1) CKN(act[l].ensure(2 * N * Ho * Ho * kCout[l]), "alloc activations");
   }
   CKN(feat.ensure(2 * N * Kf), "alloc");
@@ -620,18 +735,8 @@ int perch_cnn::ensure_batch(int n) {
 int perch_cnn::refresh_weights() {
   perch_cnn* net = this;
   CKN(w16.ensure(2 * n_w16), "alloc");
-  CKN(wt16.ensure(2 * n_w16), "alloc");
   k_to_bf16<<<grid_for(n_w16), 256, 0, stream>>>(master.as<float>(), n_w16, w16.as<bf16>());
   CKN(cudaGetLastError(), "cast kernel");
-  for (int l = 1; l < kConvs; ++l) {  // [Cout][Kp] -> [Kp][Cout]
-    dim3 grid(kCout[l] / 32, kp_of(l) / 32);
-    k_transpose<<<grid, dim3(32, 8), 0, stream>>>(w16.as<unsigned short>() + off_w[l], kCout[l], kp_of(l),
-                                                   wt16.as<unsigned short>() + off_wt[l]);
-  }
-  dim3 grid(kHidden / 32, Kf / 32);
-  k_transpose<<<grid, dim3(32, 8), 0, stream>>>(w16.as<unsigned short>() + off_f1, kHidden, Kf,
-                                                 wt16.as<unsigned short>() + off_f1t);
-  CKN(cudaGetLastError(), "transpose kernel");
   return PERCH_OK;
 }
 
@@ -645,11 +750,17 @@ int perch_cnn::forward(const bf16* crops, const int32_t* onehot, int n, float* p
   for (int l = 0; l < kConvs; ++l) {
     const int H = kHin[l], s = kStride[l], Ho = H / s, Kp = kp_of(l);
     const long long M = (long long)n * Ho * Ho;
-    k_im2col<<<grid_for(M * (Kp / 8)), 256, 0, stream>>>(x, n, H, H, kCin[l], s, Kp, col[l].as<bf16>());
-    CKN(cudaGetLastError(), "im2col kernel");
     GemmArgs p{};
-    p.A = col[l].as<bf16>();
-    p.lda = Kp;
+    if (l == 0) {  // two input channels: explicit rows of 32 columns
+      k_im2col_c2<<<grid_for(M), 256, 0, stream>>>(reinterpret_cast<const uint32_t*>(x), n, H, H,
+                                                   col[0].as<uint4>());
+      CKN(cudaGetLastError(), "im2col kernel");
+      p.A = col[0].as<bf16>();
+      p.lda = Kp;
+    } else {  // implicit im2col from the NHWC activations
+      p.A = x;
+      set_conv(p, l);
+    }
     p.B = w16.as<bf16>() + off_w[l];
     p.ldb = Kp;
     p.M = (int)M;
@@ -666,11 +777,15 @@ int perch_cnn::forward(const bf16* crops, const int32_t* onehot, int n, float* p
       p.grp = Ho * Ho;
       p.ldg = Kf;
     }
-    CKN(gemm<EPI_BIAS_RELU>(p, 1, stream), "conv gemm");
+    if (l == 0)
+      CKN(gemm<EPI_BIAS_RELU>(p, 1, stream), "conv gemm");
+    else
+      CKN((gemm<EPI_BIAS_RELU, true, true, 1>(p, 1, stream)), "conv gemm");
     x = l < kConvs - 1 ? act[l].as<bf16>() : nullptr;
   }
   k_onehot<<<grid_for((long long)n * onehot_pad), 256, 0, stream>>>(onehot, n, n, onehot_pad, Kf, feat.as<bf16>());
   CKN(cudaGetLastError(), "one-hot kernel");
+  // FC1: few output tiles over a long K, so split K and finish bias + ReLU in a second pass
   GemmArgs p{};
   p.A = feat.as<bf16>();
   p.lda = Kf;
@@ -679,11 +794,15 @@ int perch_cnn::forward(const bf16* crops, const int32_t* onehot, int n, float* p
   p.M = n;
   p.N = kHidden;
   p.K = Kf;
-  p.Ksplit = Kf;
-  p.bias = master.as<float>() + off_fb1;
-  p.Cb = h1.as<bf16>();
+  const int S = choose_splits(n, kHidden, Kf, &p.Ksplit);
+  CKN(part.ensure(4 * (size_t)S * n * kHidden), "alloc");
+  p.Cf = part.as<float>();
   p.ldc = kHidden;
-  CKN(gemm<EPI_BIAS_RELU>(p, 1, stream), "fc1 gemm");
+  p.split_stride = (long long)n * kHidden;
+  CKN(gemm<EPI_F32>(p, S, stream), "fc1 gemm");
+  k_splits_bias_relu<<<grid_for((long long)n * kHidden), 256, 0, stream>>>(
+      part.as<float>(), S, n, kHidden, master.as<float>() + off_fb1, h1.as<bf16>());
+  CKN(cudaGetLastError(), "fc1 epilogue kernel");
   k_fc2<<<(n * 32 + 255) / 256, 256, 0, stream>>>(h1.as<bf16>(), master.as<float>() + off_f2,
                                                    master.as<float>() + off_fb2, n, pred, target, err_buf.as<float>());
   CKN(cudaGetLastError(), "fc2 kernel");
@@ -696,62 +815,64 @@ int perch_cnn::backward(const bf16* crops, int n) {
   const long long N = n;
   float* G = grad.as<float>();
   CKN(dz1.ensure(2 * N * kHidden), "alloc");
-  CKN(dz1t.ensure(2 * N * kHidden), "alloc");
-  CKN(featt.ensure(2 * N * Kf), "alloc");
   CKN(dfeat.ensure(4 * N * kFeat), "alloc");
-  long long max_mk = 0, max_part = (long long)kHidden * Kf;
+  long long max_mk = 0, max_part = 0, max_bpart = 0;
+  constexpr int kRows = 1024;  // rows per block of the bias-gradient column sums
   for (int l = 0; l < kConvs; ++l) {
-    const long long Ho = kHin[l] / kStride[l];
-    max_mk = std::max(max_mk, N * Ho * Ho * std::max(kp_of(l), kCout[l]));
+    const long long Ho = kHin[l] / kStride[l], M = N * Ho * Ho;
+    max_mk = std::max(max_mk, M * std::max(kp_of(l), kCout[l]));
+    int ks;
+    const int S = choose_splits(kCout[l], kp_of(l), (int)M, &ks);
+    max_part = std::max(max_part, (long long)S * kCout[l] * kp_of(l));
+    max_bpart = std::max(max_bpart, (M + kRows - 1) / kRows * kCout[l]);
   }
+  max_bpart = std::max(max_bpart, (N + kRows - 1) / kRows * kHidden);
   CKN(dz.ensure(2 * max_mk), "alloc");
-  CKN(dzt.ensure(2 * max_mk), "alloc");
-  CKN(colt.ensure(2 * max_mk), "alloc");
   CKN(dcol.ensure(4 * max_mk), "alloc");
-  for (int l = 0; l < kConvs; ++l) {
-    const long long M = N * (kHin[l] / kStride[l]) * (kHin[l] / kStride[l]);
-    const long long S = std::max<long long>(1, M / 4096);
-    max_part = std::max(max_part, S * kCout[l] * kp_of(l));
-  }
   CKN(part.ensure(4 * max_part), "alloc");
+  CKN(bpart.ensure(4 * max_bpart), "alloc");
+  auto bias_grad = [&](const bf16* d, long long M, int C, float* out) -> int {
+    const int nb = (int)((M + kRows - 1) / kRows);
+    k_col_sum<<<nb, 256, 0, stream>>>(d, M, C, kRows, bpart.as<float>());
+    k_split_sum<<<grid_for(C), 256, 0, stream>>>(bpart.as<float>(), nb, C, out);
+    return net->cuda(cudaGetLastError(), "bias gradient kernels");
+  };
   // FC2 and the loss
-  k_fc2_backward<<<1, 256, 0, stream>>>(h1.as<bf16>(), master.as<float>() + off_f2, err_buf.as<float>(), n, n,
-                                         G + off_f2, G + off_fb2, loss_buf.as<float>(), dz1.as<bf16>());
-  CKN(cudaGetLastError(), "fc2 backward kernel");
-  // FC1: dW = dz1^T feat (reduction over the batch), db = column sums of dz1, dfeat = dz1 W
-  k_transpose<<<dim3(n / 32, kHidden / 32), dim3(32, 8), 0, stream>>>(dz1.as<unsigned short>(), N, kHidden,
-                                                                       dz1t.as<unsigned short>());
-  k_transpose<<<dim3(n / 32, Kf / 32), dim3(32, 8), 0, stream>>>(feat.as<unsigned short>(), N, Kf,
-                                                                  featt.as<unsigned short>());
-  CKN(cudaGetLastError(), "transpose kernel");
+  k_fc2_loss<<<1, 256, 0, stream>>>(err_buf.as<float>(), n, G + off_fb2, loss_buf.as<float>());
+  k_fc2_wgrad<<<kHidden, 256, 0, stream>>>(h1.as<bf16>(), err_buf.as<float>(), n, G + off_f2);
+  k_fc2_dz1<<<grid_for(N * kHidden), 256, 0, stream>>>(h1.as<bf16>(), master.as<float>() + off_f2,
+                                                       err_buf.as<float>(), n, dz1.as<bf16>());
+  CKN(cudaGetLastError(), "fc2 backward kernels");
+  // FC1: dW = dz1^T feat (reduction over the batch, both operands batch-major),
+  // db = column sums of dz1, dfeat = dz1 W (W read as [K][N])
   {
     GemmArgs p{};
-    p.A = dz1t.as<bf16>();
-    p.lda = N;
-    p.B = featt.as<bf16>();
-    p.ldb = N;
+    p.A = dz1.as<bf16>();
+    p.lda = kHidden;
+    p.B = feat.as<bf16>();
+    p.ldb = Kf;
     p.M = kHidden;
     p.N = Kf;
     p.K = n;
     p.Ksplit = n;
     p.Cf = G + off_f1;
     p.ldc = Kf;
-    CKN(gemm<EPI_F32>(p, 1, stream), "fc1 weight-gradient gemm");
+    CKN((gemm<EPI_F32, false, false>(p, 1, stream)), "fc1 weight-gradient gemm");
   }
-  k_row_sum<<<kHidden, 256, 0, stream>>>(dz1t.as<bf16>(), N, G + off_fb1);
+  if (int rc = bias_grad(dz1.as<bf16>(), N, kHidden, G + off_fb1)) return rc;
   {
     GemmArgs p{};
     p.A = dz1.as<bf16>();
     p.lda = kHidden;
-    p.B = wt16.as<bf16>() + off_f1t;  // rows 0 .. kFeat-1 of W^T: the conv features only
-    p.ldb = kHidden;
+    p.B = w16.as<bf16>() + off_f1;  // columns 0 .. kFeat-1 of W: the conv features only
+    p.ldb = Kf;
     p.M = n;
     p.N = kFeat;
     p.K = kHidden;
     p.Ksplit = kHidden;
     p.Cf = dfeat.as<float>();
     p.ldc = kFeat;
-    CKN(gemm<EPI_F32>(p, 1, stream), "fc1 data-gradient gemm");
+    CKN((gemm<EPI_F32, true, false>(p, 1, stream)), "fc1 data-gradient gemm");
   }
   k_feat_relu_grad<<<grid_for(N * kFeat), 256, 0, stream>>>(dfeat.as<float>(), feat.as<bf16>(), Kf, n,
                                                              dz.as<bf16>());
@@ -759,49 +880,49 @@ int perch_cnn::backward(const bf16* crops, int n) {
   for (int l = kConvs - 1; l >= 0; --l) {
     const int H = kHin[l], s = kStride[l], Ho = H / s, Kp = kp_of(l), Co = kCout[l];
     const long long M = N * Ho * Ho;
-    // dz (bf16 [M][Co]) -> dz^T; bias gradient = its row sums
-    k_transpose<<<dim3((unsigned)(M / 32), Co / 32), dim3(32, 8), 0, stream>>>(dz.as<unsigned short>(), M, Co,
-                                                                                 dzt.as<unsigned short>());
-    k_transpose<<<dim3((unsigned)(M / 32), Kp / 32), dim3(32, 8), 0, stream>>>(col[l].as<unsigned short>(), M, Kp,
-                                                                                colt.as<unsigned short>());
-    CKN(cudaGetLastError(), "transpose kernel");
-    k_row_sum<<<Co, 256, 0, stream>>>(dzt.as<bf16>(), M, G + off_b[l]);
-    // dW = dz^T col, split along the M reduction, partials summed in order
-    const int S = (int)std::max<long long>(1, M / 4096);
-    const int Ks = (int)((M / S + 31) / 32 * 32);
-    {
-      GemmArgs p{};
-      p.A = dzt.as<bf16>();
-      p.lda = M;
-      p.B = colt.as<bf16>();
-      p.ldb = M;
-      p.M = Co;
-      p.N = Kp;
-      p.K = (int)M;
-      p.Ksplit = Ks;
-      p.Cf = part.as<float>();
-      p.ldc = Kp;
-      p.split_stride = (long long)Co * Kp;
-      CKN(gemm<EPI_F32>(p, S, stream), "conv weight-gradient gemm");
-    }
-    k_split_sum<<<grid_for((long long)Co * Kp), 256, 0, stream>>>(part.as<float>(), S, (long long)Co * Kp,
-                                                                   G + off_w[l]);
-    CKN(cudaGetLastError(), "split sum kernel");
-    if (l == 0) break;
-    // dcol = dz W (fp32), then col2im with the ReLU mask of this layer's input
+    if (int rc = bias_grad(dz.as<bf16>(), M, Co, G + off_b[l])) return rc;
+    // dW = dz^T col: both operands pixel-major, split along the pixel reduction,
+    // partials summed in order
     {
       GemmArgs p{};
       p.A = dz.as<bf16>();
       p.lda = Co;
-      p.B = wt16.as<bf16>() + off_wt[l];
-      p.ldb = Co;
+      p.M = Co;
+      p.N = Kp;
+      p.K = (int)M;
+      const int S = choose_splits(Co, Kp, (int)M, &p.Ksplit);
+      p.Cf = part.as<float>();
+      p.ldc = Kp;
+      p.split_stride = (long long)Co * Kp;
+      if (l == 0) {
+        p.B = col[0].as<bf16>();
+        p.ldb = Kp;
+        CKN((gemm<EPI_F32, false, false>(p, S, stream)), "conv weight-gradient gemm");
+      } else {  // implicit im2col of this layer's input
+        p.B = act[l - 1].as<bf16>();
+        set_conv(p, l);
+        CKN((gemm<EPI_F32, false, false, 2>(p, S, stream)), "conv weight-gradient gemm");
+      }
+      k_split_sum<<<grid_for((long long)Co * Kp), 256, 0, stream>>>(part.as<float>(), S, (long long)Co * Kp,
+                                                                     G + off_w[l]);
+      CKN(cudaGetLastError(), "split sum kernel");
+    }
+    if (l == 0) break;
+    // dcol = dz W (fp32; W read as [K = Co][N = Kp]), then col2im with the ReLU
+    // mask of this layer's input
+    {
+      GemmArgs p{};
+      p.A = dz.as<bf16>();
+      p.lda = Co;
+      p.B = w16.as<bf16>() + off_w[l];
+      p.ldb = Kp;
       p.M = (int)M;
       p.N = Kp;
       p.K = Co;
       p.Ksplit = Co;
       p.Cf = dcol.as<float>();
       p.ldc = Kp;
-      CKN(gemm<EPI_F32>(p, 1, stream), "conv data-gradient gemm");
+      CKN((gemm<EPI_F32, true, false>(p, 1, stream)), "conv data-gradient gemm");
     }
     k_col2im_relu<<<grid_for(N * H * H * (kCin[l] / 4)), 256, 0, stream>>>(
         dcol.as<float>(), act[l - 1].as<bf16>(), n, H, H, kCin[l], s, Kp, dz.as<bf16>());

@@ -318,10 +318,13 @@ class PerchCNN:
     Device arrays are torch tensors; calls are ordered with torch's work by
     synchronising the device around them."""
 
-    def __init__(self, n_onehot: int, max_batch: int = 256, device: int = 0):
+    def __init__(self, n_onehot: int, max_batch: int = 256, device: int = 0, stream=None):
+        """``stream``: a torch.cuda.Stream (or raw handle) to run on; None: the
+        network's own stream."""
         self.lib = load()
         h = ctypes.c_void_p()
-        rc = self.lib.perch_cnn_create(ctypes.byref(h), device, None, n_onehot, max_batch)
+        handle = getattr(stream, "cuda_stream", stream)
+        rc = self.lib.perch_cnn_create(ctypes.byref(h), device, handle or None, n_onehot, max_batch)
         if rc != PERCH_OK:
             raise PerchError(rc, "perch_cnn_create failed")
         self.h = h

@@ -325,9 +325,32 @@ def place(mesh: Mesh, grid: PoseGrid, ix: int, iy: int, iyaw: int) -> np.ndarray
     return w[mesh.tris]
 
 
-def raycast_depth(cam: Camera, meshes, grid: PoseGrid, scene) -> np.ndarray:
-    """Noise-free sensor depth (float64, H x W, 0 = no return)."""
-    soups = [place(meshes[int(o["mesh"])], grid, int(o["ix"]), int(o["iy"]), int(o["iyaw"])) for o in scene]
+def place_at(mesh: Mesh, x: float, y: float, yaw: float) -> np.ndarray:
+    """World-frame triangle soup of a mesh at a continuous pose, in double."""
+    v = mesh.verts.astype(np.float64)
+    c, s = math.cos(yaw), math.sin(yaw)
+    w = np.empty_like(v)
+    w[:, 0] = c * v[:, 0] - s * v[:, 1] + x
+    w[:, 1] = s * v[:, 0] + c * v[:, 1] + y
+    w[:, 2] = v[:, 2]
+    return w[mesh.tris]
+
+
+def _soups(meshes, grid: PoseGrid, scene, jitter=None):
+    if jitter is None:
+        return [place(meshes[int(o["mesh"])], grid, int(o["ix"]), int(o["iy"]), int(o["iyaw"])) for o in scene]
+    out = []
+    for o, (dx, dy, dyaw) in zip(scene, np.asarray(jitter, np.float64)):
+        yaw = math.atan2(float(grid.cos_sin[o["iyaw"], 1]), float(grid.cos_sin[o["iyaw"], 0])) + dyaw
+        out.append(place_at(meshes[int(o["mesh"])], float(grid.xs[o["ix"]]) + dx, float(grid.ys[o["iy"]]) + dy, yaw))
+    return out
+
+
+def raycast_depth(cam: Camera, meshes, grid: PoseGrid, scene, jitter=None) -> np.ndarray:
+    """Noise-free sensor depth (float64, H x W, 0 = no return). ``jitter``:
+    optional per-object (dx, dy, dyaw) added to the grid poses (objects off
+    the grid)."""
+    soups = _soups(meshes, grid, scene, jitter)
     tris = np.ascontiguousarray(np.concatenate(soups, 0) if soups else np.zeros((0, 3, 3)), np.float64)
     T = np.ascontiguousarray(cam.T_wc.astype(np.float64))
     out = np.zeros((cam.H, cam.W), np.float64)
@@ -338,10 +361,11 @@ def raycast_depth(cam: Camera, meshes, grid: PoseGrid, scene) -> np.ndarray:
     return out
 
 
-def observe(cam: Camera, meshes, grid: PoseGrid, scene, sigma: float, dropout: float, seed: int) -> np.ndarray:
+def observe(cam: Camera, meshes, grid: PoseGrid, scene, sigma: float, dropout: float, seed: int,
+            jitter=None) -> np.ndarray:
     """Simulated observation: ray-cast depth + N(0, sigma^2) on z, then each
     pixel dropped (set to 0 = missing) with probability ``dropout``."""
-    d = raycast_depth(cam, meshes, grid, scene)
+    d = raycast_depth(cam, meshes, grid, scene, jitter)
     n = d.size
     noise = normal(substream(seed, 1), n).reshape(d.shape)
     drop = uniform(substream(seed, 2), n).reshape(d.shape) < dropout
@@ -623,23 +647,37 @@ def workload_c3(scene: int = 0, grid: PoseGrid | None = None, min_occlusion: flo
 
 
 def workloads_c5(n_scenes: int = 256, grid: PoseGrid | None = None, cam: Camera | None = None, meshes=None,
-                 k_range=(2, 6)):
+                 k_range=(2, 6), seed_base: int = 5000, first: int = 0, off_grid: float = 0.0):
     """Many independent scenes for concurrent search: scene s draws K uniform
     in k_range and K distinct meshes of the eight uneven ones, poses anywhere
     on the grid with disjoint footprints; 640x480 by default, sigma 3 mm,
-    5% dropout, delta 1 cm. Scene s is seeded with 5000 + s."""
+    5% dropout, delta 1 cm. Scene s is seeded with seed_base + s (s from
+    ``first``); disjoint seed ranges give disjoint scene sets (training scenes
+    of the learned heuristic: 7000 + s; its held-out 5-object scenes: 9000 + s).
+    off_grid = a in (0, 1]: the observed objects sit at their grid pose plus
+    a uniform offset of up to a/2 grid steps in x and y and a/2 yaw steps (the
+    recorded ground truth stays the grid pose, extra["jitter"] the offsets);
+    footprints are then kept 1.5 grid steps further apart."""
     cam = cam or camera_c2()
     meshes = meshes or meshes_c3()
     grid = grid or pose_grid(-0.49, 0.02, 50, 16)
     out = []
-    for s in range(n_scenes):
-        seed = 5000 + s
+    for s in range(first, first + n_scenes):
+        seed = seed_base + s
         u = uniform(substream(seed, 5), 16)
         K = k_range[0] + min(int(u[0] * (k_range[1] - k_range[0] + 1)), k_range[1] - k_range[0])
         ids = sorted(np.argsort(u[1:1 + len(meshes)])[:K].tolist())
-        gt = sample_scene(meshes, grid, ids, seed)
-        depth = observe(cam, meshes, grid, gt, 0.003, 0.05, seed)
-        out.append(Workload(f"c5/{s}", cam, meshes, grid, 0.01, gt, depth, 0.003, 0.05, seed))
+        step = float(grid.xs[1] - grid.xs[0]) if grid.nx > 1 else 0.0
+        jitter = None
+        if off_grid:
+            gt = sample_scene(meshes, grid, ids, seed, margin=0.005 + 1.5 * step)
+            j = (uniform(substream(seed, 6), 3 * K).reshape(K, 3) - 0.5) * float(off_grid)
+            jitter = j * np.array([step, step, 2.0 * math.pi / grid.n_yaw])
+        else:
+            gt = sample_scene(meshes, grid, ids, seed)
+        depth = observe(cam, meshes, grid, gt, 0.003, 0.05, seed, jitter)
+        extra = {} if jitter is None else {"jitter": jitter.tolist()}
+        out.append(Workload(f"c5/{s}", cam, meshes, grid, 0.01, gt, depth, 0.003, 0.05, seed, extra=extra))
     return out
 
 
