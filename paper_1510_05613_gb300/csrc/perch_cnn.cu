@@ -53,7 +53,7 @@ int kp_of(int l) { return round32(9 * kCin[l]); }
 
 // ---------------------------------------------------------------- GEMM
 constexpr int BM = 128, BK = 32, LDS = BK + 8, STAGES = 3;
-enum { EPI_BIAS_RELU = 0, EPI_F32 = 1 };
+enum { EPI_BIAS_RELU = 0, EPI_F32 = 1, EPI_BF16 = 2 };
 
 struct GemmArgs {
   const bf16* A;  // [M][lda], K-contiguous
@@ -261,6 +261,8 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs p) {
           v0 = fmaxf(v0 + p.bias[col], 0.0f);
           v1 = fmaxf(v1 + p.bias[col + 1], 0.0f);
           *reinterpret_cast<__nv_bfloat162*>(p.Cb + off) = __floats2bfloat162_rn(v0, v1);
+        } else if (EPI == EPI_BF16) {
+          *reinterpret_cast<__nv_bfloat162*>(p.Cb + off) = __floats2bfloat162_rn(v0, v1);
         } else {
           *reinterpret_cast<float2*>(p.Cf + (long long)blockIdx.z * p.split_stride + off) = make_float2(v0, v1);
         }
@@ -341,21 +343,23 @@ __global__ void k_im2col_c2(const uint32_t* __restrict__ x, int N, int H, int W,
   }
 }
 
-// dx[n][h][w][c] = sum over the taps that read (h, w) of dcol, in (kh, kw)
-// order, times [x > 0] (the ReLU of the layer that produced x); bfloat16 out.
-// Four channels per thread (Cin multiple of 4).
-__global__ void k_col2im_relu(const float* __restrict__ dcol, const bf16* __restrict__ x, int N, int H, int W,
+// dx[n][h][w][c] = sum over the taps that read (h, w) of dcol (bfloat16), in
+// (kh, kw) order, times [x > 0] (the ReLU of the layer that produced x);
+// bfloat16 out. Eight channels per thread (Cin multiple of 8).
+__global__ void k_col2im_relu(const bf16* __restrict__ dcol, const bf16* __restrict__ x, int N, int H, int W,
                               int Cin, int s, int Kp, bf16* __restrict__ dx) {
   const int Ho = H / s, Wo = W / s;
-  const int quads = Cin / 4;
-  const long long total = (long long)N * H * W * quads;
+  const int octs = Cin / 8;
+  const long long total = (long long)N * H * W * octs;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(e % quads) * 4;
-    const long long pix = e / quads;
+    const int c = (int)(e % octs) * 8;
+    const long long pix = e / octs;
     const int w = (int)(pix % W), h = (int)((pix / W) % H);
     const long long n = pix / ((long long)W * H);
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    float a[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) a[t] = 0.0f;
     for (int kh = 0; kh < 3; ++kh) {
       const int ti = h + 1 - kh;
       if (ti < 0 || ti % s) continue;
@@ -366,23 +370,27 @@ __global__ void k_col2im_relu(const float* __restrict__ dcol, const bf16* __rest
         if (tj < 0 || tj % s) continue;
         const int j = tj / s;
         if (j >= Wo) continue;
-        const float4 v =
-            *reinterpret_cast<const float4*>(dcol + ((n * Ho + i) * Wo + j) * Kp + (kh * 3 + kw) * Cin + c);
-        a0 += v.x;
-        a1 += v.y;
-        a2 += v.z;
-        a3 += v.w;
+        const uint4 v = *reinterpret_cast<const uint4*>(dcol + ((n * Ho + i) * Wo + j) * Kp + (kh * 3 + kw) * Cin + c);
+        const __nv_bfloat162* b = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          a[2 * t] += __low2float(b[t]);
+          a[2 * t + 1] += __high2float(b[t]);
+        }
       }
     }
     const long long o = pix * Cin + c;
-    const __nv_bfloat162 x01 = *reinterpret_cast<const __nv_bfloat162*>(x + o);
-    const __nv_bfloat162 x23 = *reinterpret_cast<const __nv_bfloat162*>(x + o + 2);
-    if (!(__low2float(x01) > 0.f)) a0 = 0.f;
-    if (!(__high2float(x01) > 0.f)) a1 = 0.f;
-    if (!(__low2float(x23) > 0.f)) a2 = 0.f;
-    if (!(__high2float(x23) > 0.f)) a3 = 0.f;
-    *reinterpret_cast<__nv_bfloat162*>(dx + o) = __floats2bfloat162_rn(a0, a1);
-    *reinterpret_cast<__nv_bfloat162*>(dx + o + 2) = __floats2bfloat162_rn(a2, a3);
+    const uint4 xv = *reinterpret_cast<const uint4*>(x + o);
+    const __nv_bfloat162* xb = reinterpret_cast<const __nv_bfloat162*>(&xv);
+    uint4 out;
+    __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&out);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float v0 = __low2float(xb[t]) > 0.0f ? a[2 * t] : 0.0f;
+      const float v1 = __high2float(xb[t]) > 0.0f ? a[2 * t + 1] : 0.0f;
+      ob[t] = __floats2bfloat162_rn(v0, v1);
+    }
+    *reinterpret_cast<uint4*>(dx + o) = out;
   }
 }
 
@@ -417,14 +425,26 @@ __global__ void k_splits_bias_relu(const float* __restrict__ part, int splits, l
   }
 }
 
-// out[e] = sum over z of part[z][e] (split-K partials, fixed order).
-__global__ void k_split_sum(const float* __restrict__ part, int splits, long long n, float* __restrict__ out) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    float a = 0.0f;
-    for (int z = 0; z < splits; ++z) a += part[(long long)z * n + e];
-    out[e] = a;
+// out[e] = sum over z of part[z][e] for many partials and few outputs: 32
+// outputs per block, blockDim / 32 partial groups per output (at most 32),
+// then a fixed-order sum of the groups (deterministic).
+__global__ void k_split_sum_wide(const float* __restrict__ part, int splits, long long n, float* __restrict__ out) {
+  __shared__ float red[32][33];
+  const int G = blockDim.x >> 5;
+  const long long e = (long long)blockIdx.x * 32 + (threadIdx.x & 31);
+  const int g = threadIdx.x >> 5;
+  float a = 0.0f;
+  if (e < n)
+    for (int z = g; z < splits; z += G) a += part[(long long)z * n + e];
+  red[g][threadIdx.x & 31] = a;
+  __syncthreads();
+  if (threadIdx.x < 32 && e < n) {
+    float v = 0.0f;
+    for (int k = 0; k < G; ++k) v += red[k][threadIdx.x];
+    out[e] = v;
   }
 }
+
 
 // one-hot columns of the FC input: feat[n][kFeat + j] = [j == idx[n]] (ragged rows zero)
 __global__ void k_onehot(const int32_t* __restrict__ idx, int n, int n_rows, int n_onehot_pad, long long ldf,
@@ -817,24 +837,24 @@ int perch_cnn::backward(const bf16* crops, int n) {
   CKN(dz1.ensure(2 * N * kHidden), "alloc");
   CKN(dfeat.ensure(4 * N * kFeat), "alloc");
   long long max_mk = 0, max_part = 0, max_bpart = 0;
-  constexpr int kRows = 1024;  // rows per block of the bias-gradient column sums
   for (int l = 0; l < kConvs; ++l) {
     const long long Ho = kHin[l] / kStride[l], M = N * Ho * Ho;
     max_mk = std::max(max_mk, M * std::max(kp_of(l), kCout[l]));
     int ks;
     const int S = choose_splits(kCout[l], kp_of(l), (int)M, &ks);
     max_part = std::max(max_part, (long long)S * kCout[l] * kp_of(l));
-    max_bpart = std::max(max_bpart, (M + kRows - 1) / kRows * kCout[l]);
+    max_bpart = std::max(max_bpart, 2048LL * kCout[l]);
   }
-  max_bpart = std::max(max_bpart, (N + kRows - 1) / kRows * kHidden);
+  max_bpart = std::max(max_bpart, 2048LL * kHidden);
   CKN(dz.ensure(2 * max_mk), "alloc");
-  CKN(dcol.ensure(4 * max_mk), "alloc");
+  CKN(dcol.ensure(2 * max_mk), "alloc");
   CKN(part.ensure(4 * max_part), "alloc");
   CKN(bpart.ensure(4 * max_bpart), "alloc");
   auto bias_grad = [&](const bf16* d, long long M, int C, float* out) -> int {
-    const int nb = (int)((M + kRows - 1) / kRows);
-    k_col_sum<<<nb, 256, 0, stream>>>(d, M, C, kRows, bpart.as<float>());
-    k_split_sum<<<grid_for(C), 256, 0, stream>>>(bpart.as<float>(), nb, C, out);
+    const int R = (int)std::max<long long>(16, (M + 2047) / 2048);  // at most 2048 blocks
+    const int nb = (int)((M + R - 1) / R);
+    k_col_sum<<<nb, 256, 0, stream>>>(d, M, C, R, bpart.as<float>());
+    k_split_sum_wide<<<(C + 31) / 32, 1024, 0, stream>>>(bpart.as<float>(), nb, C, out);
     return net->cuda(cudaGetLastError(), "bias gradient kernels");
   };
   // FC2 and the loss
@@ -903,8 +923,8 @@ int perch_cnn::backward(const bf16* crops, int n) {
         set_conv(p, l);
         CKN((gemm<EPI_F32, false, false, 2>(p, S, stream)), "conv weight-gradient gemm");
       }
-      k_split_sum<<<grid_for((long long)Co * Kp), 256, 0, stream>>>(part.as<float>(), S, (long long)Co * Kp,
-                                                                     G + off_w[l]);
+      k_split_sum_wide<<<(unsigned)((Co * Kp + 31) / 32), 256, 0, stream>>>(part.as<float>(), S,
+                                                                             (long long)Co * Kp, G + off_w[l]);
       CKN(cudaGetLastError(), "split sum kernel");
     }
     if (l == 0) break;
@@ -920,12 +940,12 @@ int perch_cnn::backward(const bf16* crops, int n) {
       p.N = Kp;
       p.K = Co;
       p.Ksplit = Co;
-      p.Cf = dcol.as<float>();
+      p.Cb = dcol.as<bf16>();
       p.ldc = Kp;
-      CKN((gemm<EPI_F32, true, false>(p, 1, stream)), "conv data-gradient gemm");
+      CKN((gemm<EPI_BF16, true, false>(p, 1, stream)), "conv data-gradient gemm");
     }
-    k_col2im_relu<<<grid_for(N * H * H * (kCin[l] / 4)), 256, 0, stream>>>(
-        dcol.as<float>(), act[l - 1].as<bf16>(), n, H, H, kCin[l], s, Kp, dz.as<bf16>());
+    k_col2im_relu<<<grid_for(N * H * H * (kCin[l] / 8)), 256, 0, stream>>>(
+        dcol.as<bf16>(), act[l - 1].as<bf16>(), n, H, H, kCin[l], s, Kp, dz.as<bf16>());
     CKN(cudaGetLastError(), "col2im kernel");
   }
   (void)crops;
