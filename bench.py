@@ -265,8 +265,14 @@ def run_ours(args):
     else:
         widths = p.perch_autotune(args.tune_sample) if not args.no_autotune else None
 
-    def step():  # the whole evaluation sequence as one CUDA-graph launch
-        p.perch_eval_graph(tP, stride, tplen, thp, th, wl.K, tout)
+    # the headline renders every hypothesis; the exact shortcut is measured after
+    p.perch_set_shortcut(False)
+
+    def step():  # the whole evaluation sequence as one CUDA-graph launch (or direct launches)
+        if args.no_graph:
+            p.perch_eval_successors_dev(tP, stride, tplen, thp, th, wl.K, tout)
+        else:
+            p.perch_eval_graph(tP, stride, tplen, thp, th, wl.K, tout)
 
     for _ in range(max(args.warmup, 3)):
         flush.fill_(1)
@@ -338,7 +344,31 @@ def run_ours(args):
                        "(batch upload, evaluation, record download)"}
     consistent = bool(np.array_equal(perch.records(out), rec.astype(np.int64)))
 
-    # time to the optimal scene (uniform-cost search, exact)
+    # the same batch with the exact shortcut (records identical, checked)
+    p.perch_set_shortcut(True)
+    for _ in range(3):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    sc_ms = []
+    for k in range(args.steps):
+        flush.fill_(k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        sc_ms.append(e0.elapsed_time(e1))
+    p.perch_eval_successors_dev(tP, stride, tplen, thp, th, wl.K, tout)
+    n_short, _ = p.perch_shortcut_stats()
+    sc_same = bool(np.array_equal(tout.view(-1, 7).cpu().numpy(), rec))
+    shortcut = {"value": ws * n_hyp / (statistics.mean(sc_ms) / 1e3), "unit": UNIT,
+                "ms_per_step": statistics.mean(sc_ms), "fraction_shortcut": n_short / n_hyp,
+                "records_identical": sc_same,
+                "meaning": "exact shortcut on: hypotheses far from the observation and from the parent's render get "
+                           "their record from a per-pose solo render table instead of being rasterised again"}
+
+    # time to the optimal scene (uniform-cost search, exact; shortcut on)
     search = None
     if not args.no_search:
         r = p.perch_search(wl.mesh_multiset, batch_states=args.batch_states, time_limit_s=args.search_limit)
@@ -361,16 +391,19 @@ def run_ours(args):
                        "hypotheses_per_step": n_hyp, "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "alu", "kernel": "k_eval", "achieved": achieved, "peak": peak_tops,
-                         "unit": "Tops/s", "frac": achieved / peak_tops, "traffic": None,
+                         "unit": "Tops/s", "frac": achieved / peak_tops,
+                         "traffic": measured_traffic("perch_kernels.cu", f"k_eval_{args.workload}_launches.md")
+                         if not args.max_hyps else None,
                          "ops_per_launch": ops, "eval_ms": statistics.mean(eval_ms),
                          "prep_ms": statistics.mean(prep_ms),
                          "peak_from": f"{n_sm} SMs x {FP32_LANES_PER_SM} lanes x {sm_max:.0f} MHz "
                                       "(sm_max_mhz of MEASURED_PEAKS.json)"},
             "e2e": e2e, "e2e_matches_device_records": consistent,
             "gpu_launches": (8 + len(wl.meshes)) * args.steps,
-            "launch": {"graph": True, "persistent_per_mesh": True, "autotuned_threads": widths},
+            "launch": {"graph": not args.no_graph, "persistent_per_mesh": True, "autotuned_threads": widths},
             "clocks": cl,
             "time_to_optimum": search,
+            "shortcut": shortcut,
             "cpu_baseline": base,
         }
         print(json.dumps(line), flush=True)
@@ -429,6 +462,98 @@ def run_c5(args):
 
 CNN_TRAIN_FLOP_PER_CROP = 297.1e6  # forward 100.7 MFLOP + weight and data gradients (no data gradient of layer 1)
 CNN_FWD_FLOP_PER_CROP = 100.7e6
+
+
+def measured_traffic(kernel_file: str, summary: str):
+    """DRAM bytes per step from a committed ncu summary, if it was taken on
+    the current source of the kernel (its sha256 recorded there), else None."""
+    import hashlib
+    try:
+        src = open(os.path.join(ROOT, "paper_1510_05613_gb300", "csrc", kernel_file), "rb").read()
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+    except OSError:
+        return None
+    h = hashlib.sha256(src).hexdigest()
+    vals = dict(l.split(":", 1) for l in text.splitlines() if l.startswith(("source_sha256:", "dram_bytes_per_step:")))
+    if vals.get("source_sha256", "").strip() != h:
+        return None
+    try:
+        return float(vals["dram_bytes_per_step"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_cnn(args):
+    """The heuristic network alone: W warm-up and K timed training steps
+    (forward, backward, Adam) of 256 seeded synthetic crops, then forward
+    passes of 2048 crops; CUDA events on the network's stream, L2 flushed
+    before every timed step. FLOPs per crop: forward 100.7 M, training 297.1 M
+    (the network's GEMMs, algorithmic, without padding)."""
+    import torch
+    from paper_1510_05613_gb300 import heuristic as H
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    n_onehot = 8 * 16
+    B = 256
+    net = H.new_network(n_onehot, B, seed=3, stream=stream)
+    u = synth.uniform(11, B * 64 * 64 * 2)
+    crops = torch.from_numpy((u * 7.0 - 4.0).astype(np.float32)).reshape(B, 64, 64, 2).to(torch.bfloat16).cuda()
+    onehot = torch.from_numpy((synth.uniform(12, B) * n_onehot).astype(np.int32)).cuda()
+    target = torch.from_numpy((synth.uniform(13, B) * 5.0).astype(np.float32)).cuda()
+    loss = torch.zeros(1, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            flush.fill_(1)
+            net.perch_cnn_train_step(crops, onehot, target, 1e-4, loss)
+    torch.cuda.synchronize()
+    ms = []
+    with ClockSampler(0) as clocks, torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            net.perch_cnn_train_step(crops, onehot, target, 1e-4, loss)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    step_ms = statistics.mean(ms)
+    F = 2048
+    big, oh = crops.repeat(F // B, 1, 1, 1).contiguous(), onehot.repeat(F // B).contiguous()
+    pred = torch.empty(F, device="cuda")
+    torch.cuda.synchronize()
+    fwd = []
+    with torch.cuda.stream(stream):
+        for k in range(3 + args.steps):
+            flush.fill_(k)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            net.lib.perch_cnn_forward(net.h, big.data_ptr(), oh.data_ptr(), F, pred.data_ptr())
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 3:
+                fwd.append(e0.elapsed_time(e1))
+    fwd_ms = statistics.mean(fwd)
+    peaks = _measured_peaks()
+    peak = peaks.get("bf16_tflops") or 1900.0
+    achieved = B * CNN_TRAIN_FLOP_PER_CROP / step_ms / 1e9
+    line = {"metric": "heuristic network training crops/sec (BF16, 1 GB300)", "value": B / step_ms * 1e3,
+            "unit": "crops/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "heuristic network, batch of 256 seeded synthetic 2x64x64 crops + one-hot of "
+                                   "8 meshes x 16 yaws; one step = forward, backward, Adam",
+                       "l2": "flushed (256 MiB write) before every timed step"},
+            "roofline": {"bound": "tensor", "kernel": "training step (k_gemm and its helpers)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": measured_traffic("perch_cnn.cu", "cnn_train_step_launches.md"),
+                         "flop_per_crop": CNN_TRAIN_FLOP_PER_CROP,
+                         "peak_from": "bf16_tflops (burst cuBLAS) of MEASURED_PEAKS.json"},
+            "forward": {"batch": F, "ms": fwd_ms, "crops_per_s": F / fwd_ms * 1e3,
+                        "tflops": F * CNN_FWD_FLOP_PER_CROP / fwd_ms / 1e9},
+            "gpu_launches": None, "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_c4(args):
@@ -548,6 +673,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0, help="fix the CTA width (128/256/512) instead of autotuning")
     ap.add_argument("--tune-sample", type=int, default=8192, help="hypotheses per mesh the autotuner times")
     ap.add_argument("--max-hyps", type=int, default=0, help="evenly subsample the batch (profiling case)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the evaluation directly instead of replaying its CUDA graph (same kernels)")
     ap.add_argument("--scenes", type=int, default=64, help="c5: number of scenes")
     ap.add_argument("--w", type=float, default=3.0, help="c5: suboptimality bound of Focal-MHA*")
     ap.add_argument("--heuristics", type=int, default=3, help="c5: bit 0 h_depth, bit 1 h_overlap")
@@ -558,7 +685,7 @@ def main():
     ap.add_argument("--candidates", type=int, default=16, help="c4: placements per type the learned queue scores")
     ap.add_argument("--c4-grid", type=int, default=50, choices=[25, 50], help="c4: 50 = 2 cm x 16 yaws, 25 = 4 cm x 8")
     ap.add_argument("--off-grid", type=float, default=1.0, help="c4: off-grid offsets, in grid steps (0..1)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "cnn"],
                     help="c2: 640x480 three ~10k-triangle meshes (the headline); c3: heavy occlusion, 2k-50k triangles")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -567,6 +694,8 @@ def main():
         return run_c5(args)
     if args.workload == "c4":
         return run_c4(args)
+    if args.workload == "cnn":
+        return run_cnn(args)
     return run_ours(args)
 
 

@@ -277,6 +277,23 @@ int perch_eval_graph(perch_ctx* ctx, const perch_obj* parents, int32_t parent_st
                      int32_t n_par, const int32_t* hyp_parent, const perch_obj* hyp, int64_t n_hyp,
                      int32_t K_total, perch_cost* out, perch_cost* out_host);
 
+/* Exact shortcut (on by default; not in the paper). A hypothesis whose
+ * parent render is empty over its screen box and which has no observed point
+ * within (its largest horizontal vertex radius + delta + 2 cm) of its (x, y)
+ * gets its record without being rasterised again: all its pixels are new
+ * (dR = its solo render, viol = 0), none is explained (djr = n_new = the
+ * solo pixel count), no observed point lies in V(O) (djo = n_vol = 0) and on a
+ * last-level edge every point of U stays unexplained (resid = |U|). The solo
+ * pixel counts and cull flags come from the same rasteriser, run once per
+ * (mesh, pose) against an empty parent and observation; the table is rebuilt
+ * when the meshes, the pose grid or the camera change. Records are identical
+ * with the shortcut on or off. on = 0 renders every hypothesis. */
+int perch_set_shortcut(perch_ctx* ctx, int32_t on);
+
+/* Of the hypotheses of the most recent evaluation, how many took the
+ * shortcut (0 if it was off) and how many there were. Waits for the stream. */
+int perch_shortcut_stats(perch_ctx* ctx, int64_t* n_short, int64_t* n_total);
+
 /* Device time of the most recent evaluation (perch_eval_successors or
  * perch_eval_successors_dev), measured with CUDA events recorded on the
  * context's stream around its two phases: prep_ms = parent z-buffers and

@@ -257,6 +257,11 @@ int perch_ctx::build_scene(int s, const float* depth_host) {
     CK(launch_scatter(ctx->keys.as<int>(), n, ctx->cursor.as<int>(), ctx->world_pts.as<float4>(),
                       sc.world2.as<float4>(), ctx->cam_pts.as<float4>(), sc.cam2.as<float4>(), ctx->stream),
        "scatter2");
+    // summed-area table of points per 2D cell (the exact shortcut's emptiness test)
+    CK(sc.sat2.ensure(4 * ((size_t)d2[0] + 1) * ((size_t)d2[1] + 1)), "alloc");
+    CK(launch_grid2_sat(sc.start2.as<int>(), d2[0], d2[1], ctx->counts.as<int>(), sc.sat2.as<int>(), ctx->stream),
+       "grid2 table");
+    o.sat2 = sc.sat2.as<int>();
     o.cam3 = sc.obs3.as<float4>();
     o.start3 = sc.start3.as<int>();
     o.dil3 = sc.dil3.as<uint32_t>();
@@ -357,6 +362,10 @@ int perch_load_meshes(perch_ctx* ctx, const perch_mesh* meshes, int32_t n) {
       d.lo[k] = INFINITY;
       d.hi[k] = -INFINITY;
     }
+    double fp2 = (double)m.vol_r * (double)m.vol_r;
+    for (int v = 0; v < m.n_verts; ++v)
+      fp2 = std::max(fp2, (double)m.verts[3 * v] * m.verts[3 * v] + (double)m.verts[3 * v + 1] * m.verts[3 * v + 1]);
+    d.fp_r = (float)(std::sqrt(fp2) * (1.0 + 1e-6)) + 1e-6f;
     for (int v = 0; v < m.n_verts; ++v)
       for (int k = 0; k < 3; ++k) {
         float x = m.verts[3 * v + k];
@@ -430,6 +439,7 @@ int perch_load_meshes(perch_ctx* ctx, const perch_mesh* meshes, int32_t n) {
   ctx->n_cverts = (int)verts.size();
   ctx->tables_valid = false;
   ctx->tables_version++;
+  ctx->geom_version++;
   return ctx->ensure_tables();
 }
 
@@ -452,6 +462,7 @@ int perch_set_pose_grid(perch_ctx* ctx, const float* xs, int32_t nx, const float
   ctx->n_yaw = n_yaw;
   ctx->tables_valid = false;
   ctx->tables_version++;
+  ctx->geom_version++;
   return ctx->ensure_tables();
 }
 
@@ -504,18 +515,67 @@ int perch_set_observation(perch_ctx* ctx, const float* depth, int32_t W, int32_t
 
 }  // extern "C"
 
+// The exact shortcut's solo table: every (mesh, pose) evaluated once against
+// an empty parent and an empty observation (its record's |dR| is then the
+// number of covered pixels, its flags the cull bit). Rebuilt when the
+// meshes, the pose grid or the camera (not delta or the depth) change.
+int perch_ctx::ensure_solo() {
+  perch_ctx* ctx = this;
+  auto same_camera = [&]() {
+    return solo_cam.W == cam.W && solo_cam.H == cam.H && solo_cam.fx == cam.fx && solo_cam.fy == cam.fy &&
+           solo_cam.cx == cam.cx && solo_cam.cy == cam.cy && !std::memcmp(solo_cam.Rwc, cam.Rwc, sizeof cam.Rwc) &&
+           !std::memcmp(solo_cam.twc, cam.twc, sizeof cam.twc);
+  };
+  if (solo_version == geom_version && same_camera()) return PERCH_OK;
+  const long long n = (long long)n_mesh * nx * ny * n_yaw;
+  std::vector<perch_obj> all((size_t)n);
+  long long h = 0;
+  for (int m = 0; m < n_mesh; ++m)
+    for (int ix = 0; ix < nx; ++ix)
+      for (int iy = 0; iy < ny; ++iy)
+        for (int k = 0; k < n_yaw; ++k) all[h++] = perch_obj{(uint16_t)m, (uint16_t)k, (int16_t)ix, (int16_t)iy};
+  CK(solo.ensure(sizeof(int2) * (size_t)n), "alloc solo table");
+  CK(solo_rec.ensure(sizeof(perch_cost) * (size_t)n), "alloc");
+  CK(solo_hyp.ensure(sizeof(perch_obj) * (size_t)n), "alloc");
+  CK(solo_hp.ensure(4 * (size_t)n), "alloc");
+  CK(solo_parent.ensure(16), "alloc");
+  CK(cudaMemcpyAsync(solo_hyp.p, all.data(), sizeof(perch_obj) * (size_t)n, cudaMemcpyHostToDevice, stream), "copy");
+  CK(cudaMemsetAsync(solo_hp.p, 0, 4 * (size_t)n, stream), "memset");
+  CK(cudaMemsetAsync(solo_parent.p, 0, 16, stream), "memset");
+  const ObsIndex saved = obs;
+  std::memset(&obs, 0, sizeof obs);  // the empty observation
+  building_solo = true;
+  const int rc = enqueue_eval(solo_parent.as<perch_obj>(), 1, solo_parent.as<int32_t>() + 2, 1, solo_hp.as<int32_t>(),
+                              solo_hyp.as<perch_obj>(), n, 2, solo_rec.as<perch_cost>());
+  building_solo = false;
+  obs = saved;
+  if (rc != PERCH_OK) return rc;
+  CK(launch_solo_pack(solo_rec.as<perch_cost>(), n, solo.as<int2>(), stream), "solo table");
+  CK(cudaStreamSynchronize(stream), "solo table");
+  solo_version = geom_version;
+  solo_cam = cam;
+  return PERCH_OK;
+}
+
 // Enqueue parent preparation and successor evaluation for device-resident
 // batch arrays (no host synchronisation).
 int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const int32_t* d_plen, int n_par,
                             const int32_t* d_hp, const perch_obj* d_hyp, long long n_hyp, int K_total,
                             perch_cost* d_out, const int32_t* d_parent_scene, const int32_t* d_parent_K) {
   perch_ctx* ctx = this;
+  bool use_short = shortcut && !building_solo && n_hyp > 0;
+  if (use_short && !capturing) {
+    const int rc = ensure_solo();
+    if (rc != PERCH_OK) return rc;
+  }
+  use_short = use_short && solo_version == geom_version;  // while capturing: only with a ready table
   const size_t npx = (size_t)cam.W * cam.H;
   CK(parent_z.ensure(4 * npx * std::max(n_par, 1)), "alloc parent z-buffers");
   const int ustride = std::max(d_parent_scene ? max_obs : obs.n, 1);
   CK(uset.ensure(4 * (size_t)ustride * std::max(n_par, 1)), "alloc U sets");
   CK(uset_count.ensure(4 * (size_t)std::max(n_par, 1)), "alloc");
   Batch b;
+  std::memset(&b, 0, sizeof b);
   b.parents = d_parents;
   b.parent_stride = parent_stride;
   b.parent_len = d_plen;
@@ -543,6 +603,24 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
   CK(cudaMemsetAsync(uset_count.p, 0, 4 * (size_t)std::max(n_par, 1), stream), "memset");
   CK(launch_render_parents(cam, g, b, max_chunks, nullptr, stream), "render parents");
   CK(launch_uset(cam, g, obs, b, stream), "U sets");
+  if (use_short) {  // records fixed by the solo render, written now and left out of the evaluation
+    b.tiles_w = (cam.W + 7) / 8;
+    b.tiles_h = (cam.H + 7) / 8;
+    const size_t per = (size_t)b.tiles_w * b.tiles_h, per_sat = (size_t)(b.tiles_w + 1) * (b.tiles_h + 1);
+    CK(ptile_counts.ensure(4 * per * std::max(n_par, 1)), "alloc");
+    CK(ptile_sat.ensure(4 * per_sat * std::max(n_par, 1)), "alloc");
+    CK(skip.ensure((size_t)n_hyp), "alloc");
+    CK(n_short.ensure(8), "alloc");
+    CK(cudaMemsetAsync(n_short.p, 0, 8, stream), "memset");
+    b.solo = solo.as<int2>();
+    b.parent_sat = ptile_sat.as<int>();
+    b.skip = skip.as<uint8_t>();
+    b.n_short = n_short.as<unsigned long long>();
+    CK(launch_parent_tiles(cam, b, ptile_counts.as<int>(), ptile_sat.as<int>(), stream), "parent tiles");
+    CK(launch_shortcut(cam, g, obs, b, stream), "shortcut");
+  }
+  short_counted = use_short;
+  last_total = n_hyp;
   if (!capturing) CK(cudaEventRecord(ev[1], stream), "event");
   // group by mesh; one persistent launch per mesh with its own tile and CTA width
   CK(g_hist.ensure(sizeof(int) * (size_t)n_mesh), "alloc");
@@ -552,7 +630,7 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
   CK(g_order.ensure(sizeof(int) * (size_t)std::max(n_hyp, 1LL)), "alloc");
   CK(scan_tmp.ensure(sizeof(int) * ((size_t)n_mesh / 1024 + 2)), "alloc");
   CK(launch_group_by_mesh(d_hyp, n_hyp, n_mesh, g_hist.as<int>(), g_off.as<int>(), g_cursor.as<int>(),
-                          g_order.as<int>(), scan_tmp.as<int>(), stream),
+                          g_order.as<int>(), scan_tmp.as<int>(), stream, use_short ? skip.as<uint8_t>() : nullptr),
      "group by mesh");
   CK(cudaMemsetAsync(g_next.p, 0, sizeof(int) * (size_t)n_mesh, stream), "memset");
   for (int m = 0; m < n_mesh; ++m) {
@@ -697,6 +775,29 @@ int perch_render(perch_ctx* ctx, const perch_obj* objs, int32_t n, float* depth_
   return PERCH_OK;
 }
 
+
+int perch_set_shortcut(perch_ctx* ctx, int32_t on) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  ctx->shortcut = on != 0;
+  ctx->tables_version++;  // a captured graph holds the old choice
+  return PERCH_OK;
+}
+
+int perch_shortcut_stats(perch_ctx* ctx, int64_t* n_short, int64_t* n_total) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  int64_t a = 0;
+  if (ctx->short_counted) {
+    unsigned long long v = 0;
+    CK(cudaMemcpyAsync(&v, ctx->n_short.p, 8, cudaMemcpyDeviceToHost, ctx->stream), "copy");
+    CK(cudaStreamSynchronize(ctx->stream), "shortcut stats");
+    a = (int64_t)v;
+  }
+  if (n_short) *n_short = a;
+  if (n_total) *n_total = ctx->last_total;
+  return PERCH_OK;
+}
 
 int perch_set_scene(perch_ctx* ctx, int32_t scene, const float* depth) {
   if (!ctx) return PERCH_E_ARG;

@@ -37,9 +37,10 @@ struct GraphKey {
 struct SceneBufs {
   DevBuf start3, start2, obs3, world2, cam2, dil3;
   DevBuf img;  // the scene's depth image (H x W, metres, 0 = no return)
+  DevBuf sat2;  // summed-area table of observed points per 2D world cell
   perch::ObsIndex idx{};
   void release() {
-    for (DevBuf* b : {&start3, &start2, &obs3, &world2, &cam2, &dil3, &img}) b->release();
+    for (DevBuf* b : {&start3, &start2, &obs3, &world2, &cam2, &dil3, &img, &sat2}) b->release();
   }
 };
 
@@ -91,6 +92,16 @@ struct perch_ctx {
   bool capturing = false;
   long long tables_version = 0;
 
+  // exact shortcut: per (mesh, pose) solo render (pixels, cull flag), valid
+  // for the geometry version and camera it was built for
+  bool shortcut = true;
+  bool building_solo = false;
+  DevBuf solo, solo_rec, solo_hyp, solo_hp, solo_parent, ptile_counts, ptile_sat, skip, n_short;
+  long long geom_version = 0, solo_version = -1;
+  perch::Camera solo_cam{};
+  long long last_short = 0, last_total = 0;
+  bool short_counted = false;
+
   // learned heuristic used by the search (heuristics bit 2); not owned
   perch_cnn* net = nullptr;
   int net_candidates = 16;
@@ -104,7 +115,8 @@ struct perch_ctx {
     return {&meshes, &chunk_verts, &chunk_info, &chunk_tris, &yaw_mats, &pose_off, &vtab, &xs, &ys, &cs, &depth, &rx, &ry, &blockcnt, &blockoff,
             &scan_tmp, &cam_pts, &world_pts, &keys, &counts, &cursor, &d_scenes, &d_scene_img,
             &scratch_small, &pose_bbox, &parent_z, &uset, &uset_count, &b_parents, &b_plen, &b_hp, &b_hyp,
-            &b_out, &g_hist, &g_off, &g_cursor, &g_order, &g_next, &net_crops, &net_onehot, &net_pred};
+            &b_out, &g_hist, &g_off, &g_cursor, &g_order, &g_next, &net_crops, &net_onehot, &net_pred,
+            &solo, &solo_rec, &solo_hyp, &solo_hp, &solo_parent, &ptile_counts, &ptile_sat, &skip, &n_short};
   }
 
   int fail(int code, const char* fmt, ...);
@@ -112,6 +124,7 @@ struct perch_ctx {
   perch::Geometry geometry() const;
   int ensure_tables();
   int build_scene(int s, const float* depth_host);
+  int ensure_solo();
   int enqueue_eval(const perch_obj* d_parents, int parent_stride, const int32_t* d_plen, int n_par,
                    const int32_t* d_hp, const perch_obj* d_hyp, long long n_hyp, int K_total, perch_cost* d_out,
                    const int32_t* d_parent_scene = nullptr, const int32_t* d_parent_K = nullptr);

@@ -40,6 +40,7 @@ struct DevMesh {
   int n_tris, n_verts;
   float vol_r2, vol_zlo, vol_zhi;
   float lo[3], hi[3];  // object-frame bounding box
+  float fp_r;          // max(largest horizontal vertex radius, V(O) radius), rounded up
 };
 
 // Observed cloud with its two spatial indices.
@@ -57,6 +58,7 @@ struct ObsIndex {
   const int* start2;     // n_cells2 + 1
   float g2x, g2y, inv2;
   int n2x, n2y;
+  const int* sat2;       // summed-area table of points per 2D cell, (n2y + 1) x (n2x + 1)
 };
 
 struct Geometry {
@@ -97,6 +99,14 @@ struct Batch {
   int n_scenes;
   const int32_t* parent_scene;  // scene of each parent
   const int32_t* parent_K;      // objects in a complete scene, per parent
+  // exact shortcut (nullable): per (mesh, pose) solo pixel count and flags,
+  // per parent a summed-area table of occupied 8x8-pixel tiles, per
+  // hypothesis the shortcut decision, and a counter of shortcut records
+  const int2* solo;
+  const int* parent_sat;
+  int tiles_w, tiles_h;
+  uint8_t* skip;
+  unsigned long long* n_short;
 };
 
 // kernels.cu launchers (all asynchronous on `s`)
@@ -123,7 +133,14 @@ cudaError_t launch_render_parents(const Camera& cam, const Geometry& g, const Ba
 cudaError_t launch_uset(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
                         cudaStream_t s);
 cudaError_t launch_group_by_mesh(const perch_obj* hyp, long long n, int n_mesh, int* hist, int* offsets,
-                                 int* cursor, int* order, int* scan_tmp, cudaStream_t s);
+                                 int* cursor, int* order, int* scan_tmp, cudaStream_t s,
+                                 const uint8_t* skip = nullptr);
+// exact shortcut (see k_shortcut)
+cudaError_t launch_grid2_sat(const int* start2, int n2x, int n2y, int* counts, int* sat, cudaStream_t s);
+cudaError_t launch_parent_tiles(const Camera& cam, const Batch& b, int* counts, int* sat, cudaStream_t s);
+cudaError_t launch_shortcut(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                            cudaStream_t s);
+cudaError_t launch_solo_pack(const perch_cost* rec, long long n, int2* solo, cudaStream_t s);
 cudaError_t launch_eval_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
                               const int* order, const int* offset, const int* count, int* next, long long max_items,
                               int threads, int sm_count, cudaStream_t s);

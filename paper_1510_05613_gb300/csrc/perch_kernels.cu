@@ -1097,32 +1097,177 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_eval(Camera cam, Geometry g, 
   }
 }
 
-// group hypotheses by mesh: hist -> offsets (exclusive scan) -> order
-__global__ void k_group_hist(const perch_obj* hyp, long long n, int n_mesh, int* hist) {
+// group hypotheses by mesh: hist -> offsets (exclusive scan) -> order;
+// hypotheses whose record the shortcut already wrote (skip[h] = 1) are left out
+__global__ void k_group_hist(const perch_obj* hyp, long long n, int n_mesh, int* hist, const uint8_t* skip) {
   const long long h = blockIdx.x * 256LL + threadIdx.x;
-  if (h >= n) return;
+  if (h >= n || (skip && skip[h])) return;
   const int m = min((int)hyp[h].mesh, n_mesh - 1);
   atomicAdd(&hist[m], 1);
 }
 
-__global__ void k_group_scatter(const perch_obj* hyp, long long n, int n_mesh, int* cursor, int* order) {
+__global__ void k_group_scatter(const perch_obj* hyp, long long n, int n_mesh, int* cursor, int* order,
+                                const uint8_t* skip) {
   const long long h = blockIdx.x * 256LL + threadIdx.x;
-  if (h >= n) return;
+  if (h >= n || (skip && skip[h])) return;
   const int m = min((int)hyp[h].mesh, n_mesh - 1);
   order[atomicAdd(&cursor[m], 1)] = (int)h;
 }
 
 cudaError_t launch_group_by_mesh(const perch_obj* hyp, long long n, int n_mesh, int* hist, int* offsets,
-                                 int* cursor, int* order, int* scan_tmp, cudaStream_t s) {
+                                 int* cursor, int* order, int* scan_tmp, cudaStream_t s, const uint8_t* skip) {
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * n_mesh, s);
   if (e != cudaSuccess || n == 0) return e;
   const unsigned blocks = (unsigned)((n + 255) / 256);
-  k_group_hist<<<blocks, 256, 0, s>>>(hyp, n, n_mesh, hist);
+  k_group_hist<<<blocks, 256, 0, s>>>(hyp, n, n_mesh, hist, skip);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_exclusive_scan(hist, offsets, n_mesh, scan_tmp, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(cursor, offsets, sizeof(int) * n_mesh, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
     return e;
-  k_group_scatter<<<blocks, 256, 0, s>>>(hyp, n, n_mesh, cursor, order);
+  k_group_scatter<<<blocks, 256, 0, s>>>(hyp, n, n_mesh, cursor, order, skip);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ exact shortcut
+// A hypothesis whose parent render is empty over its screen box and which has
+// no observed point within (footprint radius + delta + 2 cm) of its (x, y)
+// in the world plane has a record fixed by its solo render alone: every
+// rendered pixel is new (dR = R(O)) and in no conflict with the parent
+// (viol = 0); no observed point is within delta of a rendered point (all of
+// dR unexplained: dJ_r = |dR|); none lies in V(O) (dJ_o = 0, n_vol = 0); and on
+// a last-level edge every q of U is outside V(O) and unexplained (residual =
+// |U|). |dR| and the cull flag come from the same rasteriser run once per
+// (mesh, pose) against an empty parent and an empty observation.
+
+// summed-area table S[(r + 1) (cols + 1) + c + 1] = sum of counts[0..r][0..c]
+// of `mats` matrices (one block each); S's first row and column are zero
+__global__ void k_sat(const int* counts, int rows, int cols, int* sat) {
+  const int* cnt = counts + (size_t)blockIdx.x * rows * cols;
+  int* S = sat + (size_t)blockIdx.x * (rows + 1) * (cols + 1);
+  for (int c = threadIdx.x; c <= cols; c += blockDim.x) S[c] = 0;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    int* row = S + (size_t)(r + 1) * (cols + 1);
+    row[0] = 0;
+    int a = 0;
+    for (int c = 0; c < cols; ++c) {
+      a += cnt[(size_t)r * cols + c];
+      row[c + 1] = a;
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < cols; c += blockDim.x)
+    for (int r = 1; r < rows; ++r) S[(size_t)(r + 1) * (cols + 1) + c + 1] += S[(size_t)r * (cols + 1) + c + 1];
+}
+
+__device__ __forceinline__ int sat_sum(const int* S, int cols, int r0, int r1, int c0, int c1) {  // inclusive
+  const int w = cols + 1;
+  return S[(r1 + 1) * w + c1 + 1] - S[r0 * w + c1 + 1] - S[(r1 + 1) * w + c0] + S[r0 * w + c0];
+}
+
+__global__ void k_cell_counts(const int* start2, int n, int* counts) {
+  const int c = blockIdx.x * 256 + threadIdx.x;
+  if (c < n) counts[c] = start2[c + 1] - start2[c];
+}
+
+cudaError_t launch_grid2_sat(const int* start2, int n2x, int n2y, int* counts, int* sat, cudaStream_t s) {
+  const int n = n2x * n2y;
+  k_cell_counts<<<(n + 255) / 256, 256, 0, s>>>(start2, n, counts);
+  k_sat<<<1, 1024, 0, s>>>(counts, n2y, n2x, sat);
+  return cudaGetLastError();
+}
+
+// occupied pixels of each parent render per 8x8 tile
+__global__ void k_parent_tile_counts(Camera cam, Batch b, int* counts) {
+  const int p = blockIdx.y;
+  const int t = blockIdx.x * 256 + threadIdx.x;
+  if (t >= b.tiles_w * b.tiles_h) return;
+  const int tx = t % b.tiles_w, ty = t / b.tiles_w;
+  const float* z = b.parent_z + (size_t)p * cam.W * cam.H;
+  int c = 0;
+  for (int v = ty * 8; v < min(ty * 8 + 8, cam.H); ++v)
+    for (int u = tx * 8; u < min(tx * 8 + 8, cam.W); ++u) c += __float_as_uint(z[(size_t)v * cam.W + u]) != kInfBits;
+  counts[(size_t)p * b.tiles_w * b.tiles_h + t] = c;
+}
+
+cudaError_t launch_parent_tiles(const Camera& cam, const Batch& b, int* counts, int* sat, cudaStream_t s) {
+  if (b.n_par > 65535) return cudaErrorInvalidValue;
+  dim3 grid((b.tiles_w * b.tiles_h + 255) / 256, b.n_par);
+  k_parent_tile_counts<<<grid, 256, 0, s>>>(cam, b, counts);
+  k_sat<<<b.n_par, 128, 0, s>>>(counts, b.tiles_h, b.tiles_w, sat);
+  return cudaGetLastError();
+}
+
+__global__ void k_shortcut(Camera cam, Geometry g, ObsIndex obs0, Batch b) {
+  const long long h = blockIdx.x * 256LL + threadIdx.x;
+  int fast = 0;
+  if (h < b.n_hyp) {
+    const perch_obj o = b.hyp[h];
+    const int pid = b.hyp_parent[h];
+    bool ok = pid >= 0 && pid < b.n_par && obj_ok(g, o);
+    const int plen = ok ? b.parent_len[pid] : 0;
+    ok = ok && plen >= 0 && plen <= b.parent_stride;
+    const int scene = (ok && b.parent_scene) ? b.parent_scene[pid] : 0;
+    ok = ok && (!b.parent_scene || (scene >= 0 && scene < b.n_scenes));
+    const long long pose = (((long long)o.mesh * g.nx + o.ix) * g.ny + o.iy) * g.n_yaw + o.iyaw;
+    const int4 bb = ok ? g.pose_bbox[pose] : make_int4(0, 0, 0, 0);
+    ok = ok && bb.z <= b.tile_w && bb.w <= b.tile_h;
+    if (ok && plen > 0 && bb.z > 0 && bb.w > 0) {  // parent render empty over the screen box?
+      const int tx0 = max(bb.x, 0) >> 3, tx1 = min(bb.x + bb.z - 1, cam.W - 1) >> 3;
+      const int ty0 = max(bb.y, 0) >> 3, ty1 = min(bb.y + bb.w - 1, cam.H - 1) >> 3;
+      if (tx0 <= tx1 && ty0 <= ty1) {
+        const int* S = b.parent_sat + (size_t)pid * (b.tiles_h + 1) * (b.tiles_w + 1);
+        ok = sat_sum(S, b.tiles_w, ty0, ty1, tx0, tx1) == 0;
+      }
+    }
+    if (ok) {  // no observed point near (x, y)?
+      const ObsIndex& obs = b.parent_scene ? b.scenes[scene] : obs0;
+      if (obs.n > 0) {
+        const float R = g.meshes[o.mesh].fp_r + cam.delta + 0.02f;
+        const float ox = g.xs[o.ix], oy = g.ys[o.iy];
+        const int cx0 = max(cell_of(ox - R, obs.g2x, obs.inv2, obs.n2x) - 1, 0);
+        const int cx1 = min(cell_of(ox + R, obs.g2x, obs.inv2, obs.n2x) + 1, obs.n2x - 1);
+        const int cy0 = max(cell_of(oy - R, obs.g2y, obs.inv2, obs.n2y) - 1, 0);
+        const int cy1 = min(cell_of(oy + R, obs.g2y, obs.inv2, obs.n2y) + 1, obs.n2y - 1);
+        if (cx0 <= cx1 && cy0 <= cy1) ok = sat_sum(obs.sat2, obs.n2x, cy0, cy1, cx0, cx1) == 0;
+      }
+    }
+    if (ok) {
+      const int K_total = b.parent_K ? b.parent_K[pid] : b.K_total;
+      const int2 so = b.solo[pose];
+      perch_cost r;
+      r.djr = so.x;
+      r.djo = 0;
+      r.resid = plen + 1 == K_total ? b.uset_count[pid] : 0;
+      r.viol = 0;
+      r.n_new = so.x;
+      r.flags = (uint32_t)so.y;
+      r.n_vol = 0;
+      b.out[h] = r;
+      fast = 1;
+    }
+    b.skip[h] = (uint8_t)fast;
+  }
+  const int n_fast = __syncthreads_count(fast);
+  if (threadIdx.x == 0 && n_fast && b.n_short) atomicAdd(b.n_short, (unsigned long long)n_fast);
+}
+
+cudaError_t launch_shortcut(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                            cudaStream_t s) {
+  if (b.n_hyp == 0) return cudaSuccess;
+  k_shortcut<<<(unsigned)((b.n_hyp + 255) / 256), 256, 0, s>>>(cam, g, obs, b);
+  return cudaGetLastError();
+}
+
+// solo table entry from a record evaluated against an empty parent and an
+// empty observation: (|dR| = pixels covered, cull flag)
+__global__ void k_solo_pack(const perch_cost* rec, long long n, int2* solo) {
+  const long long h = blockIdx.x * 256LL + threadIdx.x;
+  if (h < n) solo[h] = make_int2(rec[h].n_new, (int)(rec[h].flags & 1u));
+}
+
+cudaError_t launch_solo_pack(const perch_cost* rec, long long n, int2* solo, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_solo_pack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rec, n, solo);
   return cudaGetLastError();
 }
 

@@ -59,6 +59,13 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
   CK(cudaMemcpyAsync(ctx->b_plen.p, &plen, 4, cudaMemcpyHostToDevice, ctx->stream), "copy");
   CK(cudaMemcpyAsync(ctx->b_hp.p, hp.data(), 4 * (size_t)n_sample, cudaMemcpyHostToDevice, ctx->stream), "copy");
   const std::vector<int> saved = ctx->mesh_threads;
+  // time the rasteriser itself: the exact shortcut would skip most root children
+  struct ShortcutOff {
+    perch_ctx* c;
+    bool was;
+    ~ShortcutOff() { c->shortcut = was; }
+  } shortcut_off{ctx, ctx->shortcut};
+  ctx->shortcut = false;
   for (int m = 0; m < n_mesh; ++m) {
     const TuneKey key{ctx->device, ctx->h_meshes[m].n_tris, ctx->h_meshes[m].n_verts, ctx->mesh_tile_w[m],
                       ctx->mesh_tile_h[m]};

@@ -28,7 +28,8 @@ EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_mesh
            "perch_eval_graph", "perch_set_threads", "perch_set_scene", "perch_eval_successors_multi",
            "perch_search_multi", "perch_cnn_create", "perch_cnn_destroy", "perch_cnn_last_error",
            "perch_cnn_param_count", "perch_cnn_set_params", "perch_cnn_get_params", "perch_cnn_crops",
-           "perch_cnn_forward", "perch_cnn_train_step", "perch_cnn_gradients", "perch_set_heuristic_net")
+           "perch_cnn_forward", "perch_cnn_train_step", "perch_cnn_gradients", "perch_set_heuristic_net",
+           "perch_set_shortcut", "perch_shortcut_stats")
 
 
 class perch_mesh(ctypes.Structure):
@@ -101,6 +102,8 @@ def load(path: str = LIB_PATH):
         "perch_cnn_train_step": ([P, P, P, P, I32, F, P], ctypes.c_int),
         "perch_cnn_gradients": ([P, P, P, P, I32, P, P, P], ctypes.c_int),
         "perch_set_heuristic_net": ([P, P, I32], ctypes.c_int),
+        "perch_set_shortcut": ([P, I32], ctypes.c_int),
+        "perch_shortcut_stats": ([P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -285,6 +288,16 @@ class Perch:
         """Attach a PerchCNN (None detaches) for search heuristic bit 2."""
         self._net = net  # keep it alive while attached
         return self._check(self.lib.perch_set_heuristic_net(self.h, None if net is None else net.h, n_candidates))
+
+    def perch_set_shortcut(self, on: bool):
+        """Exact shortcut for hypotheses far from the observation and the parent (on by default)."""
+        return self._check(self.lib.perch_set_shortcut(self.h, 1 if on else 0))
+
+    def perch_shortcut_stats(self):
+        """(hypotheses that took the shortcut, hypotheses) of the last evaluation."""
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._check(self.lib.perch_shortcut_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
 
     def perch_render(self, objs):
         o = _c(objs, OBJ)

@@ -135,6 +135,60 @@ def test_c2_bench_launch_sampled(c2):
     assert np.array_equal(got[idx], exp)
 
 
+def test_shortcut_records_identical_and_taken(c2):
+    """The exact shortcut (hypotheses far from the observation and from the
+    parent's render) gives the same records as rendering every hypothesis,
+    on the full benchmark batch, and takes most of it."""
+    wl, p, w = c2
+    from bench import c2_batch
+    parents, hp, hyps = c2_batch(wl)
+    p.perch_set_shortcut(False)
+    full = _recs(p.perch_eval_successors(parents, hp, hyps, wl.K))
+    assert p.perch_shortcut_stats() == (0, len(hyps))
+    p.perch_set_shortcut(True)
+    fast = _recs(p.perch_eval_successors(parents, hp, hyps, wl.K))
+    n_short, n = p.perch_shortcut_stats()
+    assert n == len(hyps) and n_short > len(hyps) // 2
+    bad = np.nonzero((full != fast).any(1))[0]
+    assert bad.size == 0, (bad[:5], full[bad[:3]], fast[bad[:3]])
+
+
+def test_shortcut_multi_scene_identical():
+    meshes = synth.meshes_c3()[:4]
+    grid = synth.pose_grid(-0.49, 0.04, 25, 8)
+    wls = synth.workloads_c5(3, grid=grid, meshes=meshes, k_range=(2, 3))
+    p = perch.Perch(0)
+    p.setup(wls[0])
+    for s, wl in enumerate(wls[1:], 1):
+        p.perch_set_scene(s, wl.depth)
+    parents, ps, pk, hp, hyps = [], [], [], [], []
+    rng = np.random.default_rng(7)
+    for s, wl in enumerate(wls):
+        for j in range(wl.K):
+            h = synth.all_hypotheses(grid, sorted(set(int(m) for m in wl.gt["mesh"][j:])))
+            h = h[rng.choice(len(h), min(len(h), 3000), replace=False)]
+            hp.append(np.full(len(h), len(parents), np.int32))
+            hyps.append(h)
+            parents.append(wl.gt[:j])
+            ps.append(s)
+            pk.append(wl.K)
+    hp, hyps = np.concatenate(hp), np.concatenate(hyps)
+    p.perch_set_shortcut(False)
+    full = _recs(p.perch_eval_successors_multi(parents, ps, pk, hp, hyps))
+    p.perch_set_shortcut(True)
+    fast = _recs(p.perch_eval_successors_multi(parents, ps, pk, hp, hyps))
+    assert p.perch_shortcut_stats()[0] > len(hyps) // 3
+    assert np.array_equal(full, fast)
+    # sampled records of every parent against the oracle (shortcut on)
+    for s, wl in enumerate(wls):
+        wo = oracle.World.of(wl)
+        for j in range(wl.K):
+            pi = [i for i in range(len(parents)) if ps[i] == s and len(parents[i]) == j][0]
+            idx = np.nonzero(hp == pi)[0][::97]
+            exp = oracle.eval_batch(wo, wl.depth, [parents[pi]], np.zeros(len(idx), np.int32), hyps[idx], wl.K)
+            assert np.array_equal(fast[idx], exp)
+
+
 def test_empty_observation_and_huge_delta():
     wl = synth.workload_c1()
     allh = synth.all_hypotheses(wl.grid, [0, 1])[::7]
