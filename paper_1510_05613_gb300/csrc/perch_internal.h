@@ -16,7 +16,7 @@ constexpr int kChunkMaxVerts = 512;   // vertices of one mesh chunk (10-bit loca
 constexpr int kChunkMaxTris = 1024;   // triangles of one mesh chunk (list padded to 4 entries)
 constexpr int kEvalThreads = 256;
 constexpr int kEvalWarps = kEvalThreads / 32;
-constexpr int kInlinePixels = 4;   // a lane tests at most this many pixel centres per triangle
+constexpr int kInlinePixels = 16;  // a lane tests at most this many pixel centres per triangle
 constexpr int kBigQueue = 128;     // per-chunk queue of larger triangles, shared by the CTA
 constexpr int kWaitSpins = 1 << 20;  // bound on mbarrier polls before a kernel gives up
 constexpr int kMaxObjectPixels = 1000;  // screen box limit that keeps edge arithmetic in int32

@@ -735,18 +735,28 @@ __device__ __forceinline__ uint32_t pixel_iz_bits(int w0, int w1, int w2, float 
 // triangle (tile-relative 1/16-px vertices) and max its 1/z into the tile.
 __device__ __forceinline__ void raster_box(int2 a, int2 b, int2 c, int A, int px0, int px1, int py0, int py1,
                                            const float* sIZ, int i0, int i1, int i2, uint32_t* tile, int tw) {
-  float invA = 0.0f;
+  // edge functions at the first candidate, then stepped by their exact
+  // integer increments per pixel (16 sub-pixel units)
+  const float invA = __frcp_rn(__int2float_rn(A));
+  const int d0x = 16 * (c.y - b.y), d0y = -16 * (c.x - b.x);
+  const int d1x = 16 * (a.y - c.y), d1y = -16 * (a.x - c.x);
+  const int d2x = 16 * (b.y - a.y), d2y = -16 * (b.x - a.x);
+  int r0 = (c.y - b.y) * (16 * px0 - b.x) - (c.x - b.x) * (16 * py0 - b.y);
+  int r1 = (a.y - c.y) * (16 * px0 - c.x) - (a.x - c.x) * (16 * py0 - c.y);
+  int r2 = (b.y - a.y) * (16 * px0 - a.x) - (b.x - a.x) * (16 * py0 - a.y);
+  const float z0 = sIZ[i0], z1 = sIZ[i1], z2 = sIZ[i2];
   for (int py = py0; py <= py1; ++py) {
-    const int Py = 16 * py;
+    int w0 = r0, w1 = r1, w2 = r2;
     for (int px = px0; px <= px1; ++px) {
-      const int Px = 16 * px;
-      const int w0 = (c.y - b.y) * (Px - b.x) - (c.x - b.x) * (Py - b.y);
-      const int w1 = (a.y - c.y) * (Px - c.x) - (a.x - c.x) * (Py - c.y);
-      const int w2 = (b.y - a.y) * (Px - a.x) - (b.x - a.x) * (Py - a.y);
-      if (!covers(w0, w1, w2, a, b, c)) continue;
-      if (invA == 0.0f) invA = __frcp_rn(__int2float_rn(A));
-      atomicMax(&tile[py * tw + px], pixel_iz_bits(w0, w1, w2, invA, sIZ[i0], sIZ[i1], sIZ[i2]));
+      if (covers(w0, w1, w2, a, b, c))
+        atomicMax(&tile[py * tw + px], pixel_iz_bits(w0, w1, w2, invA, z0, z1, z2));
+      w0 += d0x;
+      w1 += d1x;
+      w2 += d2x;
     }
+    r0 += d0y;
+    r1 += d1y;
+    r2 += d2y;
   }
 }
 
