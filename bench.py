@@ -601,7 +601,8 @@ def run_c4(args):
     fwd_ms = e0.elapsed_time(e1) / 10
     p.perch_set_heuristic_net(net, args.candidates)
     peaks = _measured_peaks()
-    arms = [("plain", 1.0, 0), ("mha", args.w, 3), ("mha+learned", args.w, 7)]
+    arms = [("plain", 1.0, 0), ("mha_depth", args.w, 1), ("mha", args.w, 3), ("mha_depth+learned", args.w, 5),
+            ("mha+learned", args.w, 7)]
     out = {}
     with ClockSampler(0) as clocks:
         for name, w, hb in arms:
@@ -627,7 +628,7 @@ def run_c4(args):
                 "cost_gap_rel_max": float(max((a["cost"] - b["cost"]) / max(b["cost"], 1) for a, b in both))
                 if both else None}
 
-    learned = summary("mha+learned")
+    learned = summary("mha_depth+learned")
     train_tflops = steps * 256 * CNN_TRAIN_FLOP_PER_CROP / train_s / 1e12
     peak = peaks.get("bf16_tflops_sustained") or 1700.0
     line = {"metric": METRIC, "value": learned["time_to_scene_p50_s"], "unit": "s (time to scene, p50, learned search)",
@@ -682,7 +683,7 @@ def main():
     ap.add_argument("--train-scenes", type=int, default=256, help="c4: training scenes")
     ap.add_argument("--per-parent", type=int, default=1536, help="c4: labelled hypotheses per training parent")
     ap.add_argument("--epochs", type=int, default=2, help="c4: training epochs")
-    ap.add_argument("--candidates", type=int, default=16, help="c4: placements per type the learned queue scores")
+    ap.add_argument("--candidates", type=int, default=8, help="c4: placements per type the learned queue scores")
     ap.add_argument("--c4-grid", type=int, default=50, choices=[25, 50], help="c4: 50 = 2 cm x 16 yaws, 25 = 4 cm x 8")
     ap.add_argument("--off-grid", type=float, default=1.0, help="c4: off-grid offsets, in grid steps (0..1)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "cnn"],

@@ -210,7 +210,7 @@ int perch_render(perch_ctx* ctx, const perch_obj* objs, int32_t n, float* depth_
  * expansion keeps the n_candidates cheapest valid placements of every
  * remaining type; a child's queue pool is ordered by g + the sum of its
  * remaining objects' cheapest exact costs at the parent, and each round the
- * front of the pool is re-ranked by g + h_cnn, h_cnn = sum over the remaining
+ * front of the pool (max(16, 2 batch_states) states) is re-ranked by g + h_cnn, h_cnn = sum over the remaining
  * objects of the smallest predicted edge cost exp(y) - 1 among the parent's
  * candidates of that type, predicted with the child as parent; PERCH_E_STATE
  * without a network), and the search returns a scene of cost <= w * OPT

@@ -118,7 +118,7 @@ struct SceneSearch {
   std::vector<OpenEntry> pending;      // generated, not yet in the focal set (min g)
   std::vector<HEntry> hq[3];           // focal states ordered by each heuristic
   std::vector<ExpansionRecord> exps;   // learned queue: one per expanded state
-  std::vector<int> pool;               // learned queue: this round's candidates
+  std::vector<int> pool;               // learned queue: candidates of the current step
   int T = 16;                          // learned queue: placements kept per type
   bool focal() const { return w > 1.0 || heur != 0; }
   int64_t hval(int which, int idx) const {
@@ -212,7 +212,7 @@ struct SceneSearch {
       }
     }
     if (heur & 4) {  // learned queue: gather the pool; the caller scores it and calls choose()
-      const int L = std::max(32, 4 * B);
+      const int L = std::max(16, 2 * B);
       pool.clear();
       while ((int)pool.size() < L && !hq[2].empty()) {
         const HEntry top = hq[2].front();
