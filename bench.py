@@ -151,6 +151,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def whole_job(local_seconds: float, local_units: float):
+    """(max over ranks of the timed seconds, whole-job rate = units of all
+    ranks / that time). Every rank processes the same number of units (weak
+    scaling); with one rank there is no collective."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return local_seconds, local_units / local_seconds
+    ws = dist.get_world_size()
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total = float(t.item())
+    dist.barrier()
+    return total, ws * local_units / total
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -301,13 +318,7 @@ def run_ours(args):
         eval_ms.append(b)
     torch.cuda.synchronize()
     step_ms = [s.elapsed_time(e) for s, e in evs]
-    total_s = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-        dist.barrier()
-    value = ws * n_hyp * args.steps / total_s
+    total_s, value = whole_job(sum(step_ms) / 1e3, n_hyp * args.steps)
 
     rec = tout.view(-1, 7).cpu().numpy()
     ops = algorithmic_ops(wl, hyps, rec[:, 4])
