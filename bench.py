@@ -592,7 +592,7 @@ def run_c4(args):
     n_onehot = len(train_sc[0].meshes) * grid.n_yaw
     data, dstats = H.make_dataset(p, train_sc, tr, per_parent=args.per_parent, seed=1)
     val, _ = H.make_dataset(p, test_sc[:min(32, len(test_sc))], te[:min(32, len(te))], per_parent=256, seed=2)
-    net = H.new_network(n_onehot, 256, seed=3, stream=stream)
+    net = H.new_network(n_onehot, 1024, seed=3, stream=stream)  # trains on 256, forwards the search's crops 1024 at a time
     with ClockSampler(0) as train_clocks:
         losses, train_s = H.train(net, data, epochs=args.epochs, batch=256, lr=1e-3, stream=stream)
     steps = len(losses)
