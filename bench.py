@@ -614,7 +614,7 @@ def run_c4(args):
     peaks = _measured_peaks()
     arms = [("plain", 1.0, 0), ("mha_depth", args.w, 1), ("mha", args.w, 3), ("mha_depth+learned", args.w, 5),
             ("mha+learned", args.w, 7)]
-    out = {}
+    out, learned_cost = {}, {}
     with ClockSampler(0) as clocks:
         for name, w, hb in arms:
             t1 = time.perf_counter()
@@ -622,6 +622,7 @@ def run_c4(args):
                                      max_hyps_per_launch=args.launch_hyps, time_limit_s=args.search_limit, w=w,
                                      heuristics=hb)
             out[name] = (r, time.perf_counter() - t1)
+            learned_cost[name] = p.perch_search_stats()
     plain = out["plain"][0]
 
     def summary(name):
@@ -637,7 +638,9 @@ def run_c4(args):
                 "compared_with_plain": len(both),
                 "cost_gap_mean": float(np.mean([a["cost"] - b["cost"] for a, b in both])) if both else None,
                 "cost_gap_rel_max": float(max((a["cost"] - b["cost"]) / max(b["cost"], 1) for a, b in both))
-                if both else None}
+                if both else None,
+                "learned_queue_seconds": learned_cost[name][0], "learned_states_scored": learned_cost[name][1],
+                "learned_crops": learned_cost[name][2]}
 
     learned = summary("mha_depth+learned")
     train_tflops = steps * 256 * CNN_TRAIN_FLOP_PER_CROP / train_s / 1e12

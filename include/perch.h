@@ -250,6 +250,12 @@ int perch_search(perch_ctx* ctx, const perch_search_params* params, perch_result
 int perch_search_multi(perch_ctx* ctx, int32_t n_scenes, const int32_t* scenes, const perch_search_params* params,
                        int64_t max_hyps_per_launch, perch_result* results);
 
+/* Cost of the learned queue in the most recent perch_search or
+ * perch_search_multi: wall seconds spent scoring states (parent renders,
+ * crops, forward pass, host work), states scored and crops evaluated. Any
+ * pointer may be NULL. */
+int perch_search_stats(perch_ctx* ctx, double* learned_seconds, int64_t* learned_states, int64_t* learned_crops);
+
 /* Launch tuning (not in the paper). The evaluation runs one persistent
  * launch per mesh with a shared-memory tile sized for that mesh; this call
  * times each CTA width the kernel is built for (128, 256, 512 threads) on

@@ -106,6 +106,8 @@ struct perch_ctx {
   perch_cnn* net = nullptr;
   int net_candidates = 16;
   DevBuf net_crops, net_onehot, net_pred;
+  double net_seconds = 0.0;            // last search: host time spent scoring the learned queue
+  long long net_states = 0, net_crops_scored = 0;
 
   // events around the phases of the last evaluation
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};

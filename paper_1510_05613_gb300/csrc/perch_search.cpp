@@ -416,6 +416,8 @@ int score_pools(perch_ctx* ctx, std::vector<SceneSearch>& ss) {
       }
     }
     pred.assign(hyps.size(), 0.0f);
+    ctx->net_states += (long long)(b1 - b0);
+    ctx->net_crops_scored += (long long)hyps.size();
     if (!hyps.empty()) {
       const int rc = net_predict(ctx, ctx->net, parents.data(), stride, plen.data(), pscene.data(),
                                  (int32_t)(b1 - b0), hparent.data(), hyps.data(), (long long)hyps.size(), pred.data());
@@ -449,6 +451,8 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
                  int64_t max_expansions, int64_t max_hyps_per_launch, bool multi) {
   const auto t0 = Clock::now();
   auto elapsed = [&]() { return std::chrono::duration<double>(Clock::now() - t0).count(); };
+  ctx->net_seconds = 0.0;
+  ctx->net_states = ctx->net_crops_scored = 0;
   int stride = 1;
   for (auto& s : ss) stride = std::max(stride, s.K - 1);
   const int B = std::max(1, std::min(batch_states, 65535 / stride));
@@ -488,7 +492,9 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
     }
     if (any_pool) {  // learned queue: score the pools, then take each scene's best
       if (!ctx->net) return ctx->fail(PERCH_E_STATE, "search: heuristic bit 2 needs perch_set_heuristic_net");
+      const auto ts = Clock::now();
       const int rc = score_pools(ctx, ss);
+      ctx->net_seconds += std::chrono::duration<double>(Clock::now() - ts).count();
       if (rc != PERCH_OK) return rc;
       for (size_t si = 0; si < ss.size(); ++si) {
         if (ss[si].pool.empty()) continue;
@@ -583,6 +589,16 @@ int check_params(perch_ctx* ctx, const perch_search_params* prm) {
 }
 
 }  // namespace
+
+extern "C" int perch_search_stats(perch_ctx* ctx, double* learned_seconds, int64_t* learned_states,
+                                  int64_t* learned_crops) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (learned_seconds) *learned_seconds = ctx->net_seconds;
+  if (learned_states) *learned_states = ctx->net_states;
+  if (learned_crops) *learned_crops = ctx->net_crops_scored;
+  return PERCH_OK;
+}
 
 extern "C" int perch_search(perch_ctx* ctx, const perch_search_params* prm, perch_result* res) {
   if (!ctx) return PERCH_E_ARG;
