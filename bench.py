@@ -622,7 +622,7 @@ def run_c4(args):
                                      max_hyps_per_launch=args.launch_hyps, time_limit_s=args.search_limit, w=w,
                                      heuristics=hb)
             out[name] = (r, time.perf_counter() - t1)
-            learned_cost[name] = p.perch_search_stats()
+            learned_cost[name] = p.perch_search_stats() + p.perch_search_times()
     plain = out["plain"][0]
 
     def summary(name):
@@ -634,13 +634,16 @@ def run_c4(args):
                 "time_to_scene_p50_s": float(np.percentile([x["seconds"] for x in fin], 50)) if fin else None,
                 "time_to_scene_mean_s": float(np.mean([x["seconds"] for x in fin])) if fin else None,
                 "expansions_mean": float(np.mean([x["expansions"] for x in r])),
+                "successors_mean": float(np.mean([x["successors"] for x in r])),
                 "same_scene_as_plain": sum(a["key"] == b["key"] for a, b in both),
                 "compared_with_plain": len(both),
                 "cost_gap_mean": float(np.mean([a["cost"] - b["cost"] for a, b in both])) if both else None,
                 "cost_gap_rel_max": float(max((a["cost"] - b["cost"]) / max(b["cost"], 1) for a, b in both))
                 if both else None,
                 "learned_queue_seconds": learned_cost[name][0], "learned_states_scored": learned_cost[name][1],
-                "learned_crops": learned_cost[name][2]}
+                "learned_crops": learned_cost[name][2],
+                "search_eval_s": learned_cost[name][3], "search_absorb_s": learned_cost[name][4],
+                "search_select_s": learned_cost[name][5]}
 
     learned = summary("mha_depth+learned")
     train_tflops = steps * 256 * CNN_TRAIN_FLOP_PER_CROP / train_s / 1e12

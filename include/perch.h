@@ -208,9 +208,10 @@ int perch_render(perch_ctx* ctx, const perch_obj* objs, int32_t n, float* depth_
  * bit 1: h_overlap = observed points outside the assigned volumes,
  * Sec. IV-C; bit 2: the learned heuristic of perch_set_heuristic_net: each
  * expansion keeps the n_candidates cheapest valid placements of every
- * remaining type; a child's queue pool is ordered by g + the sum of its
- * remaining objects' cheapest exact costs at the parent, and each round the
- * front of the pool (max(16, 2 batch_states) states) is re-ranked by g + h_cnn, h_cnn = sum over the remaining
+ * remaining type; a child's queue pool is ordered deepest first, then by g +
+ * the sum of its remaining objects' cheapest exact costs at the parent, and
+ * each round the front of the pool (max(16, 2 batch_states) states) is
+ * re-ranked, within each depth, by g + h_cnn, h_cnn = sum over the remaining
  * objects of the smallest predicted edge cost exp(y) - 1 among the parent's
  * candidates of that type, predicted with the child as parent; PERCH_E_STATE
  * without a network), and the search returns a scene of cost <= w * OPT
@@ -255,6 +256,13 @@ int perch_search_multi(perch_ctx* ctx, int32_t n_scenes, const int32_t* scenes, 
  * crops, forward pass, host work), states scored and crops evaluated. Any
  * pointer may be NULL. */
 int perch_search_stats(perch_ctx* ctx, double* learned_seconds, int64_t* learned_states, int64_t* learned_crops);
+
+/* Where the wall time of the most recent search went: device evaluation
+ * calls (uploads, kernels, record downloads), absorbing the records into the
+ * search (duplicate detection, queues), and selecting the next states and
+ * building their batch (including the learned queue's scoring). Any pointer
+ * may be NULL. */
+int perch_search_times(perch_ctx* ctx, double* eval_seconds, double* absorb_seconds, double* select_seconds);
 
 /* Launch tuning (not in the paper). The evaluation runs one persistent
  * launch per mesh with a shared-memory tile sized for that mesh; this call

@@ -108,6 +108,9 @@ struct perch_ctx {
   DevBuf net_crops, net_onehot, net_pred;
   double net_seconds = 0.0;            // last search: host time spent scoring the learned queue
   long long net_states = 0, net_crops_scored = 0;
+  // last search: wall seconds in device evaluation calls, in absorbing their
+  // records, and in selecting states and building batches (learned scoring included)
+  double search_eval_seconds = 0.0, search_absorb_seconds = 0.0, search_host_seconds = 0.0;
 
   // events around the phases of the last evaluation
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};

@@ -19,7 +19,9 @@
 // placements and their exact edge costs. A child s' gets the free estimate
 // h_free(s') = sum over its remaining objects of the cheapest exact cost of
 // that type at the parent; the queue's pool holds focal states ordered by
-// g + h_free. Each round the front of the pool is re-ranked by g + h_cnn, where
+// depth (deepest first, so its expansions have few remaining types and stay
+// cheap), then g + h_free. Each round the front of the pool is re-ranked,
+// within each depth, by g + h_cnn, where
 // h_cnn(s') = sum over the remaining objects of min over the parent's
 // candidates of that type of (exp(prediction) - 1), the network's edge-cost
 // estimate with s' itself as the parent (its z-buffer in the crop). States are
@@ -29,7 +31,6 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
-#include <unordered_map>
 #include <vector>
 
 #include "perch_ctx.h"
@@ -54,26 +55,71 @@ perch_obj unpack(uint64_t k) {
   return o;
 }
 
-struct KeyHash {
-  size_t operator()(const Key& k) const {
-    uint64_t h = 1469598103934665603ULL;
-    for (uint64_t x : k) {
-      h ^= x + 0x9E3779B97F4A7C15ULL + (h << 6) + (h >> 2);
-      h *= 1099511628211ULL;
-    }
-    return (size_t)h;
-  }
-};
+// Order-independent hash of an object multiset: the sum (mod 2^64) of a
+// SplitMix64 finaliser of each packed object, in two independent variants.
+// A state's hash is its parent's plus the added object's, so it costs O(1);
+// equal hashes are confirmed by comparing the objects themselves, so the
+// hash only speeds up duplicate detection and never decides it.
+uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+uint64_t zobj0(uint64_t o) { return mix64(o); }
+uint64_t zobj1(uint64_t o) { return mix64(o ^ 0xD1B54A32D192ED03ULL); }
 
+// A state is its predecessor `link` plus one object (the root has none), so
+// its key (sorted objects) is rebuilt by walking at most K links.
 struct State {
-  Key key;
   int64_t g;
-  bool closed;
   int64_t h_overlap;  // observed points outside the volumes of the state's objects
-  int parent = -1;    // state whose expansion generated the cheapest known way in
-  int exp = -1;       // this state's own expansion record (learned queue)
   int64_t h_free = 0; // learned queue pool key part (see header)
   double h_cnn = -1;  // < 0: not scored yet
+  uint64_t hk0 = 0, hk1 = 0;  // multiset hash
+  uint64_t obj = 0;   // packed object added to `link`
+  int link = -1;      // the state this one extends (fixed at creation)
+  int parent = -1;    // state whose expansion generated the cheapest known way in
+  int exp = -1;       // this state's own expansion record (learned queue)
+  uint8_t depth = 0;  // number of objects
+  bool closed = false;
+};
+
+// Open-addressing table from a state's first hash to its index (entries with
+// equal hashes sit in the same probe run; every match is confirmed).
+struct StateIndex {
+  std::vector<uint64_t> h;
+  std::vector<int32_t> idx;  // -1: empty
+  size_t n = 0;
+  void init(size_t cap) {
+    h.assign(cap, 0);
+    idx.assign(cap, -1);
+    n = 0;
+  }
+  template <typename Eq>
+  int find(uint64_t key, Eq eq) const {
+    const size_t mask = h.size() - 1;
+    for (size_t i = key & mask;; i = (i + 1) & mask) {
+      if (idx[i] < 0) return -1;
+      if (h[i] == key && eq(idx[i])) return idx[i];
+    }
+  }
+  void insert(uint64_t key, int v) {
+    if (2 * (n + 1) > h.size()) grow();
+    const size_t mask = h.size() - 1;
+    size_t i = key & mask;
+    while (idx[i] >= 0) i = (i + 1) & mask;
+    h[i] = key;
+    idx[i] = v;
+    ++n;
+  }
+  void grow() {
+    std::vector<uint64_t> oh = std::move(h);
+    std::vector<int32_t> oi = std::move(idx);
+    init(oh.size() * 2);
+    for (size_t i = 0; i < oh.size(); ++i)
+      if (oi[i] >= 0) insert(oh[i], oi[i]);
+  }
 };
 
 // What the learned queue keeps of one expansion: per distinct remaining type,
@@ -82,6 +128,7 @@ struct ExpansionRecord {
   std::vector<int> types;
   std::vector<perch_obj> top;  // types.size() x T
   std::vector<int64_t> best;   // per type; kInf if no valid placement
+  int64_t total = 0;           // sum over the remaining objects (with multiplicity) of best (or a penalty)
 };
 
 struct HEntry {  // entry of an inadmissible queue
@@ -92,6 +139,7 @@ struct HEntry {  // entry of an inadmissible queue
 struct OpenEntry {
   int64_t g;
   int idx;
+  int depth;  // ties in g: deeper states first (complete scenes, hence pruning bounds, come early)
 };
 
 // One scene's search: uniform-cost search for w = 1 without heuristics,
@@ -106,7 +154,7 @@ struct SceneSearch {
   int scene = 0, K = 0;
   std::vector<int> multiset;
   std::vector<State> states;
-  std::unordered_map<Key, int, KeyHash> index;
+  StateIndex index;
   std::vector<OpenEntry> heap;  // anchor
   int64_t best_g = kInf;
   Key best_key;
@@ -122,8 +170,11 @@ struct SceneSearch {
   int T = 16;                          // learned queue: placements kept per type
   bool focal() const { return w > 1.0 || heur != 0; }
   int64_t hval(int which, int idx) const {
-    if (which == 2) return states[idx].g + states[idx].h_free;
-    return which == 0 ? (int64_t)(K - (int)states[idx].key.size()) : states[idx].h_overlap;
+    if (which == 2) {  // deepest first, then g + the free estimate
+      const int64_t f = std::min<int64_t>(states[idx].g + states[idx].h_free, ((int64_t)1 << 40) - 1);
+      return ((int64_t)(K - (int)states[idx].depth) << 40) | f;
+    }
+    return which == 0 ? (int64_t)(K - (int)states[idx].depth) : states[idx].h_overlap;
   }
   static bool hworse(const HEntry& a, const HEntry& b) {
     if (a.h != b.h) return a.h > b.h;
@@ -132,23 +183,40 @@ struct SceneSearch {
   }
   static bool gworse(const OpenEntry& a, const OpenEntry& b) {
     if (a.g != b.g) return a.g > b.g;
+    if (a.depth != b.depth) return a.depth < b.depth;
     return a.idx > b.idx;
   }
   void add_open(int64_t g, int idx) {
     push(g, idx);
     if (focal()) {
-      pending.push_back(OpenEntry{g, idx});
+      pending.push_back(OpenEntry{g, idx, states[idx].depth});
       std::push_heap(pending.begin(), pending.end(), gworse);
     }
   }
   bool stale(const OpenEntry& e) const { return states[e.idx].closed || e.g > states[e.idx].g; }
 
-  bool worse(const OpenEntry& a, const OpenEntry& b) const {
-    if (a.g != b.g) return a.g > b.g;
-    return states[a.idx].key > states[b.idx].key;
+  bool worse(const OpenEntry& a, const OpenEntry& b) const { return gworse(a, b); }
+  // the sorted objects of state idx
+  Key key_of(int idx) const {
+    Key k;
+    for (int i = idx; i > 0; i = states[i].link) k.push_back(states[i].obj);
+    std::sort(k.begin(), k.end());
+    return k;
+  }
+  // is state idx the multiset key(pidx) + {o}?
+  bool same_set(int idx, int pidx, uint64_t o) const {
+    if (states[idx].depth != states[pidx].depth + 1) return false;
+    uint64_t a[17], b[17];
+    int na = 0, nb = 0;
+    for (int i = idx; i > 0; i = states[i].link) a[na++] = states[i].obj;
+    for (int i = pidx; i > 0; i = states[i].link) b[nb++] = states[i].obj;
+    b[nb++] = o;
+    std::sort(a, a + na);
+    std::sort(b, b + nb);
+    return std::equal(a, a + na, b);
   }
   void push(int64_t g, int idx) {
-    heap.push_back(OpenEntry{g, idx});
+    heap.push_back(OpenEntry{g, idx, states[idx].depth});
     std::push_heap(heap.begin(), heap.end(), [this](const OpenEntry& a, const OpenEntry& b) { return worse(a, b); });
   }
   void init(int sc, int k, const uint16_t* ms, double w_, int heur_, int64_t n_obs) {
@@ -157,8 +225,11 @@ struct SceneSearch {
     w = w_;
     heur = heur_;
     multiset.assign(ms, ms + k);
-    states.push_back(State{Key{}, 0, false, n_obs});
-    index[Key{}] = 0;
+    State root;
+    root.g = 0;
+    root.h_overlap = n_obs;
+    states.push_back(root);
+    index.init(1 << 16);  // the root is never looked up (no child has depth 0)
     add_open(0, 0);
   }
   // Focal-MHA* round: up to B states from the anchor and from each queue
@@ -232,6 +303,8 @@ struct SceneSearch {
     for (int idx : pool)
       if (!states[idx].closed) live.push_back(idx);
     std::sort(live.begin(), live.end(), [this](int a, int b) {
+      const size_t da = states[a].depth, db = states[b].depth;
+      if (da != db) return da > db;  // deepest first, as the pool
       const double fa = (double)states[a].g + states[a].h_cnn, fb = (double)states[b].g + states[b].h_cnn;
       if (fa != fb) return fa < fb;
       return a < b;
@@ -250,7 +323,7 @@ struct SceneSearch {
   // learned queue: the expansion record of state `pidx` from its children's records
   void record_expansion(int pidx, const perch_obj* hyps, const perch_cost* recs, long long n) {
     ExpansionRecord er;
-    er.types = remaining(states[pidx].key);
+    er.types = remaining(key_of(pidx));
     const size_t nt = er.types.size();
     er.top.assign(nt * T, perch_obj{0xffff, 0, 0, 0});
     er.best.assign(nt, kInf);
@@ -267,19 +340,12 @@ struct SceneSearch {
       for (size_t j = 0; j < k; ++j) er.top[t * T + j] = hyps[by[t][j].second];
       if (k) er.best[t] = by[t][0].first;
     }
+    for (int m : remaining_multiset(key_of(pidx))) {
+      const size_t t = std::lower_bound(er.types.begin(), er.types.end(), m) - er.types.begin();
+      er.total += (t < nt && er.best[t] != kInf) ? er.best[t] : (int64_t)1 << 40;
+    }
     states[pidx].exp = (int)exps.size();
     exps.push_back(std::move(er));
-  }
-  // free estimate of a child of `pidx` that keeps `rem` (sorted multiset) unplaced
-  int64_t free_estimate(int pidx, const std::vector<int>& rem_multiset) const {
-    const ExpansionRecord& er = exps[states[pidx].exp];
-    int64_t h = 0;
-    for (int m : rem_multiset) {
-      const size_t t = std::lower_bound(er.types.begin(), er.types.end(), m) - er.types.begin();
-      const int64_t b = t < er.types.size() ? er.best[t] : kInf;
-      h += b == kInf ? (int64_t)1 << 40 : b;
-    }
-    return h;
   }
   std::vector<int> remaining_multiset(const Key& key) const {
     std::vector<int> rem = multiset;
@@ -321,39 +387,58 @@ struct SceneSearch {
     rem.erase(std::unique(rem.begin(), rem.end()), rem.end());
     return rem;
   }
-  void set_parent(int idx, int pidx) {
+  // the child idx = pidx + {o}: its free estimate is the parent's total less
+  // the cheapest cost of o's type (o itself is valid, so that type has one)
+  void set_parent(int idx, int pidx, const perch_obj& o) {
     State& s = states[idx];
     s.parent = pidx;
-    s.h_free = free_estimate(pidx, remaining_multiset(s.key));
+    const ExpansionRecord& er = exps[states[pidx].exp];
+    const size_t t = std::lower_bound(er.types.begin(), er.types.end(), (int)o.mesh) - er.types.begin();
+    s.h_free = er.total - ((t < er.types.size() && er.best[t] != kInf) ? er.best[t] : (int64_t)1 << 40);
     s.h_cnn = -1.0;  // candidates changed: score again
   }
   void absorb(int pidx, const perch_obj& h, const perch_cost& r) {
     if (r.viol > 0) return;  // occludes the parent: not a successor (Eq. (3))
     const int64_t ng = states[pidx].g + (int64_t)r.djr + r.djo + r.resid;
     if (ng > best_g) return;
-    Key ck = states[pidx].key;
-    ck.insert(std::upper_bound(ck.begin(), ck.end(), pack(h)), pack(h));
-    if ((int)ck.size() == K) {
-      if (ng < best_g || (ng == best_g && ck < best_key)) {
+    const uint64_t o = pack(h);
+    const State& ps = states[pidx];
+    if (ps.depth + 1 == K) {  // a goal: only its cost and key matter
+      if (ng < best_g) {
         best_g = ng;
-        best_key = ck;
+        best_key = key_of(pidx);
+        best_key.insert(std::upper_bound(best_key.begin(), best_key.end(), o), o);
+      } else if (ng == best_g) {
+        Key ck = key_of(pidx);
+        ck.insert(std::upper_bound(ck.begin(), ck.end(), o), o);
+        if (ck < best_key) best_key = std::move(ck);
       }
       return;
     }
-    auto it = index.find(ck);
-    if (it == index.end()) {
+    const uint64_t h0 = ps.hk0 + zobj0(o), h1 = ps.hk1 + zobj1(o);
+    const int found =
+        index.find(h0, [&](int i) { return states[i].hk1 == h1 && same_set(i, pidx, o); });
+    if (found < 0) {
       const int idx = (int)states.size();
-      states.push_back(State{std::move(ck), ng, false, states[pidx].h_overlap - (int64_t)r.n_vol});
-      index.emplace(states[idx].key, idx);
-      if (heur & 4) set_parent(idx, pidx);
+      State c;
+      c.g = ng;
+      c.h_overlap = ps.h_overlap - (int64_t)r.n_vol;
+      c.hk0 = h0;
+      c.hk1 = h1;
+      c.obj = o;
+      c.link = pidx;
+      c.depth = (uint8_t)(ps.depth + 1);
+      states.push_back(c);
+      index.insert(h0, idx);
+      if (heur & 4) set_parent(idx, pidx, h);
       add_open(ng, idx);
     } else {
-      State& s = states[it->second];
+      State& s = states[found];
       if (ng < s.g) {
         s.g = ng;
         s.closed = false;  // a cheaper way in: reopen
-        if ((heur & 4) && s.parent != pidx) set_parent(it->second, pidx);
-        add_open(ng, it->second);
+        if ((heur & 4) && s.parent != pidx) set_parent(found, pidx, h);
+        add_open(ng, found);
       }
     }
   }
@@ -378,7 +463,7 @@ int score_pools(perch_ctx* ctx, std::vector<SceneSearch>& ss) {
         continue;
       }
       todo.push_back(Work{(int)k, idx});
-      stride = std::max(stride, (int)st.key.size());
+      stride = std::max(stride, (int)st.depth);
     }
   const int max_par = std::max(1, 65535 / stride);
   std::vector<perch_obj> parents, hyps;
@@ -398,11 +483,12 @@ int score_pools(perch_ctx* ctx, std::vector<SceneSearch>& ss) {
       SceneSearch& s = ss[todo[i].scene_slot];
       const State& st = s.states[todo[i].state];
       const size_t w = i - b0;
-      plen[w] = (int32_t)st.key.size();
+      const Key key = s.key_of(todo[i].state);
+      plen[w] = (int32_t)key.size();
       pscene[w] = s.scene;
-      for (size_t j = 0; j < st.key.size(); ++j) parents[w * stride + j] = unpack(st.key[j]);
+      for (size_t j = 0; j < key.size(); ++j) parents[w * stride + j] = unpack(key[j]);
       const ExpansionRecord& er = s.exps[s.states[st.parent].exp];
-      types[w] = s.remaining(st.key);
+      types[w] = s.remaining(key);
       for (size_t t = 0; t < types[w].size(); ++t) {
         const size_t et = std::lower_bound(er.types.begin(), er.types.end(), types[w][t]) - er.types.begin();
         if (et >= er.types.size()) continue;
@@ -436,7 +522,7 @@ int score_pools(perch_ctx* ctx, std::vector<SceneSearch>& ss) {
       State& st = s.states[todo[i].state];
       const size_t w = i - b0;
       double h = 0.0;
-      for (int m : s.remaining_multiset(st.key)) {
+      for (int m : s.remaining_multiset(s.key_of(todo[i].state))) {
         const size_t t = std::lower_bound(types[w].begin(), types[w].end(), m) - types[w].begin();
         h += t < types[w].size() ? best[w][t] : 1e7;
       }
@@ -451,7 +537,7 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
                  int64_t max_expansions, int64_t max_hyps_per_launch, bool multi) {
   const auto t0 = Clock::now();
   auto elapsed = [&]() { return std::chrono::duration<double>(Clock::now() - t0).count(); };
-  ctx->net_seconds = 0.0;
+  ctx->net_seconds = ctx->search_eval_seconds = ctx->search_absorb_seconds = ctx->search_host_seconds = 0.0;
   ctx->net_states = ctx->net_crops_scored = 0;
   int stride = 1;
   for (auto& s : ss) stride = std::max(stride, s.K - 1);
@@ -465,6 +551,7 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
   int64_t expansions = 0;
   size_t rr = 0;  // round-robin start over scenes
   while (true) {
+    const auto tr = Clock::now();
     bool any = false;
     for (auto& s : ss) any |= !s.done;
     if (!any) return PERCH_OK;
@@ -522,7 +609,7 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
     for (size_t w = 0; w < work.size(); ++w) {
       hbeg[w] = hyps.size();
       const SceneSearch& s = ss[work[w].scene_slot];
-      const Key& key = s.states[work[w].state].key;
+      const Key key = s.key_of(work[w].state);
       plen[w] = (int32_t)key.size();
       pscene[w] = s.scene;
       pK[w] = s.K;
@@ -537,6 +624,8 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
     }
     hbeg[work.size()] = hyps.size();
     out.resize(hyps.size());
+    const auto te = Clock::now();
+    ctx->search_host_seconds += std::chrono::duration<double>(te - tr).count();
     const int rc = multi ? perch_eval_successors_multi(ctx, parents.data(), stride, plen.data(), pscene.data(),
                                                        pK.data(), (int32_t)work.size(), hparent.data(),
                                                        hyps.data(), (int64_t)hyps.size(), out.data())
@@ -544,6 +633,8 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
                                                  hparent.data(), hyps.data(), (int64_t)hyps.size(), ss[0].K,
                                                  out.data());
     if (rc != PERCH_OK) return rc;
+    const auto ta = Clock::now();
+    ctx->search_eval_seconds += std::chrono::duration<double>(ta - te).count();
     expansions += (int64_t)work.size();
     for (size_t w = 0; w < work.size(); ++w) {
       SceneSearch& s = ss[work[w].scene_slot];
@@ -558,6 +649,7 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
       s.successors++;
       s.absorb(w.state, hyps[h], out[h]);
     }
+    ctx->search_absorb_seconds += std::chrono::duration<double>(Clock::now() - ta).count();
   }
 }
 
@@ -589,6 +681,16 @@ int check_params(perch_ctx* ctx, const perch_search_params* prm) {
 }
 
 }  // namespace
+
+extern "C" int perch_search_times(perch_ctx* ctx, double* eval_seconds, double* absorb_seconds,
+                                  double* select_seconds) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (eval_seconds) *eval_seconds = ctx->search_eval_seconds;
+  if (absorb_seconds) *absorb_seconds = ctx->search_absorb_seconds;
+  if (select_seconds) *select_seconds = ctx->search_host_seconds;
+  return PERCH_OK;
+}
 
 extern "C" int perch_search_stats(perch_ctx* ctx, double* learned_seconds, int64_t* learned_states,
                                   int64_t* learned_crops) {

@@ -29,7 +29,7 @@ EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_mesh
            "perch_search_multi", "perch_cnn_create", "perch_cnn_destroy", "perch_cnn_last_error",
            "perch_cnn_param_count", "perch_cnn_set_params", "perch_cnn_get_params", "perch_cnn_crops",
            "perch_cnn_forward", "perch_cnn_train_step", "perch_cnn_gradients", "perch_set_heuristic_net",
-           "perch_set_shortcut", "perch_shortcut_stats", "perch_search_stats")
+           "perch_set_shortcut", "perch_shortcut_stats", "perch_search_stats", "perch_search_times")
 
 
 class perch_mesh(ctypes.Structure):
@@ -105,6 +105,8 @@ def load(path: str = LIB_PATH):
         "perch_set_shortcut": ([P, I32], ctypes.c_int),
         "perch_search_stats": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "perch_search_times": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "perch_shortcut_stats": ([P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -306,6 +308,12 @@ class Perch:
         a, b, c = ctypes.c_double(0), ctypes.c_int64(0), ctypes.c_int64(0)
         self._check(self.lib.perch_search_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return float(a.value), int(b.value), int(c.value)
+
+    def perch_search_times(self):
+        """Wall seconds of the last search: (device evaluation, absorbing records, selecting states)."""
+        a, b, c = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        self._check(self.lib.perch_search_times(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return float(a.value), float(b.value), float(c.value)
 
     def perch_render(self, objs):
         o = _c(objs, OBJ)
