@@ -424,6 +424,47 @@ def run_ours(args):
     return 0
 
 
+class MemoryGuard:
+    """Polls this process's resident memory; past `frac` of the host's RAM it
+    prints an error line and exits, so a search that keeps too many states
+    stops cleanly instead of exhausting the host. Records the peak."""
+
+    def __init__(self, frac: float = 0.6):
+        self.peak = 0
+        self.limit = None
+        try:
+            with open("/proc/meminfo") as f:
+                total_kb = int(next(l for l in f if l.startswith("MemTotal")).split()[1])
+            self.limit = int(total_kb * 1024 * frac)
+        except (OSError, StopIteration, ValueError):
+            pass
+        self.stop = threading.Event()
+
+    def _rss(self):
+        try:
+            with open("/proc/self/statm") as f:
+                return int(f.read().split()[1]) * os.sysconf("SC_PAGE_SIZE")
+        except (OSError, ValueError):
+            return 0
+
+    def _run(self):
+        while not self.stop.wait(0.5):
+            r = self._rss()
+            self.peak = max(self.peak, r)
+            if self.limit and r > self.limit:
+                print(json.dumps({"error": f"host memory {r / 2**30:.1f} GiB above the guard "
+                                           f"{self.limit / 2**30:.1f} GiB; run stopped"}), flush=True)
+                os._exit(3)
+
+    def __enter__(self):
+        threading.Thread(target=self._run, daemon=True).start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop.set()
+        self.peak = max(self.peak, self._rss())
+
+
 def run_c5(args):
     """Many scenes at once: one exact search per scene, all expansions packed
     into shared evaluation launches (perch_search_multi). Reports aggregate
@@ -441,7 +482,7 @@ def run_c5(args):
     for s, wl in enumerate(wls[1:], 1):
         p.perch_set_scene(s, wl.depth)
     p.perch_autotune(args.tune_sample)
-    with ClockSampler(0) as clocks:
+    with ClockSampler(0) as clocks, MemoryGuard() as mem:
         t0 = time.perf_counter()
         res = p.perch_search_multi(list(range(len(wls))), [wl.mesh_multiset for wl in wls],
                                    batch_states=args.batch_states, max_hyps_per_launch=args.launch_hyps,
@@ -465,7 +506,7 @@ def run_c5(args):
                 for r, wl in zip(res, wls)),
             "time_to_optimum_p50_s": float(np.percentile(done, 50)) if done else None,
             "time_to_optimum_p99_s": float(np.percentile(done, 99)) if done else None,
-            "successors": succ, "wall_s": wall, "clocks": clocks.summary()}
+            "successors": succ, "wall_s": wall, "host_peak_rss_gib": mem.peak / 2**30, "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)
     p.close()
     return 0
@@ -615,7 +656,7 @@ def run_c4(args):
     arms = [("plain", 1.0, 0), ("mha_depth", args.w, 1), ("mha", args.w, 3), ("mha_depth+learned", args.w, 5),
             ("mha+learned", args.w, 7)]
     out, learned_cost = {}, {}
-    with ClockSampler(0) as clocks:
+    with ClockSampler(0) as clocks, MemoryGuard() as mem:
         for name, w, hb in arms:
             t1 = time.perf_counter()
             r = p.perch_search_multi(te, [wl.mesh_multiset for wl in test_sc], batch_states=args.batch_states,
@@ -669,7 +710,7 @@ def run_c4(args):
                          "note": "whole training step (algorithmic FLOPs / step time) against the sustained "
                                  "cuBLAS bf16 peak of MEASURED_PEAKS.json"},
             "arms": {n: summary(n) for n, _, _ in arms},
-            "clocks": clocks.summary(), "train_clocks": train_clocks.summary()}
+            "host_peak_rss_gib": mem.peak / 2**30, "clocks": clocks.summary(), "train_clocks": train_clocks.summary()}
     print(json.dumps(line), flush=True)
     p.close()
     return 0

@@ -53,7 +53,7 @@ int kp_of(int l) { return round32(9 * kCin[l]); }
 
 // ---------------------------------------------------------------- GEMM
 constexpr int BM = 128, BK = 32, LDS = BK + 8, STAGES = 3;
-enum { EPI_BIAS_RELU = 0, EPI_F32 = 1, EPI_BF16 = 2 };
+enum { EPI_BIAS_RELU = 0, EPI_F32 = 1, EPI_BF16 = 2, EPI_DGRAD = 3 };
 
 struct GemmArgs {
   const bf16* A;  // [M][lda], K-contiguous
@@ -72,6 +72,14 @@ struct GemmArgs {
   // input of a 3x3 pad-1 convolution with power-of-two channels and output
   // side; pixel index (n, i, j) and column index (tap, c), tap = 3 kh + kw
   int cH, cs, lg_c, lg_wo;
+  // fused data gradient of a stride-2 convolution (CONV = 3, EPI_DGRAD), one
+  // parity class (par_h, par_w) of the input pixels: rows = the class's
+  // pixels (n, a, b) at (2a + par_h, 2b + par_w); columns = input channels;
+  // K = (tap of the class, output channel). A gathers dz, B reads W in place,
+  // the epilogue applies the ReLU mask of the layer input and scatters rows
+  // back to NHWC.
+  int par_h, par_w, ntw, dg_lg_ho, dg_lg_co, dg_H, dg_cin, dg_kp;
+  const bf16* mask;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -122,6 +130,37 @@ __device__ __forceinline__ const bf16* conv_src(const GemmArgs& p, const bf16* x
   return x + ((((long long)n * p.cH + r) * p.cH + cc) << p.lg_c) + c;
 }
 
+// Taps of one parity of a stride-2, pad-1, 3x3 convolution's input: an even
+// coordinate 2a is read by kernel offset 1 of output a; an odd one 2a + 1 by
+// offset 0 of output a + 1 and offset 2 of output a.
+__device__ __forceinline__ void dg_tap(int par, int t, int& kofs, int& d) {
+  kofs = par == 0 ? 1 : (t == 0 ? 0 : 2);
+  d = (par == 1 && t == 0) ? 1 : 0;
+}
+
+// A chunk of the fused data gradient: class pixel m, columns k .. k + 7 (one
+// tap, 8 output channels) of dz; nullptr where that output pixel is outside.
+__device__ __forceinline__ const bf16* dgrad_a_src(const GemmArgs& p, int m, int k) {
+  const int t = k >> p.dg_lg_co, o = k & ((1 << p.dg_lg_co) - 1);
+  int kh, dh, kw, dw;
+  dg_tap(p.par_h, t / p.ntw, kh, dh);
+  dg_tap(p.par_w, t % p.ntw, kw, dw);
+  const int ho = 1 << p.dg_lg_ho;
+  const int b = m & (ho - 1), a = (m >> p.dg_lg_ho) & (ho - 1), n = m >> (2 * p.dg_lg_ho);
+  const int i = a + dh, j = b + dw;
+  if (i >= ho || j >= ho) return nullptr;
+  return p.A + ((((long long)n * ho + i) * ho + j) << p.dg_lg_co) + o;
+}
+
+// B chunk: K row (tap, o), input channels n .. n + 7 of W[o][kh][kw][.]
+__device__ __forceinline__ const bf16* dgrad_b_src(const GemmArgs& p, int k, int n) {
+  const int t = k >> p.dg_lg_co, o = k & ((1 << p.dg_lg_co) - 1);
+  int kh, dh, kw, dw;
+  dg_tap(p.par_h, t / p.ntw, kh, dh);
+  dg_tap(p.par_w, t % p.ntw, kw, dw);
+  return p.B + (long long)o * p.dg_kp + (kh * 3 + kw) * p.dg_cin + n;
+}
+
 template <int BN, int EPI, bool AK, bool BKC, int CONV>
 __global__ void __launch_bounds__(256) k_gemm(GemmArgs p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -153,8 +192,9 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs p) {
         const int r = c >> 2, q = c & 3, gm = m0 + r;
         bool ok = gm < p.M;
         const bf16* src = p.A;
-        if (CONV == 1) {
-          const bf16* g = ok ? conv_src(p, p.A, gm, k0 + q * 8) : nullptr;
+        if (CONV == 1 || CONV == 3) {
+          const bf16* g = ok ? (CONV == 1 ? conv_src(p, p.A, gm, k0 + q * 8) : dgrad_a_src(p, gm, k0 + q * 8))
+                             : nullptr;
           ok = g != nullptr;
           if (ok) src = g;
         } else if (ok) {
@@ -186,6 +226,8 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs p) {
           const bf16* g = ok ? conv_src(p, p.B, k0 + r, gn) : nullptr;
           ok = g != nullptr;
           if (ok) src = g;
+        } else if (CONV == 3) {
+          if (ok) src = dgrad_b_src(p, k0 + r, gn);
         } else if (ok) {
           src = p.B + (long long)(k0 + r) * p.ldb + gn;
         }
@@ -256,6 +298,17 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs p) {
         const int col = n0 + wn * 32 + j * 8 + 2 * t;
         if (row >= p.M || col >= p.N) continue;
         float v0 = acc[i][j][2 * h], v1 = acc[i][j][2 * h + 1];
+        if (EPI == EPI_DGRAD) {  // class pixel -> NHWC input pixel, times the ReLU mask
+          const int ho = 1 << p.dg_lg_ho;
+          const int b = row & (ho - 1), a = (row >> p.dg_lg_ho) & (ho - 1), n = row >> (2 * p.dg_lg_ho);
+          const long long o =
+              (((long long)n * p.dg_H + 2 * a + p.par_h) * p.dg_H + 2 * b + p.par_w) * p.dg_cin + col;
+          const __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162*>(p.mask + o);
+          if (!(__low2float(x) > 0.0f)) v0 = 0.0f;
+          if (!(__high2float(x) > 0.0f)) v1 = 0.0f;
+          *reinterpret_cast<__nv_bfloat162*>(p.Cb + o) = __floats2bfloat162_rn(v0, v1);
+          continue;
+        }
         const long long off = (long long)(row / p.grp) * p.ldg + (long long)(row % p.grp) * p.ldc + col;
         if (EPI == EPI_BIAS_RELU) {
           v0 = fmaxf(v0 + p.bias[col], 0.0f);
@@ -340,57 +393,6 @@ __global__ void k_im2col_c2(const uint32_t* __restrict__ x, int N, int H, int W,
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) col[m * 4 + q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-  }
-}
-
-// dx[n][h][w][c] = sum over the taps that read (h, w) of dcol (bfloat16), in
-// (kh, kw) order, times [x > 0] (the ReLU of the layer that produced x);
-// bfloat16 out. Eight channels per thread (Cin multiple of 8).
-__global__ void k_col2im_relu(const bf16* __restrict__ dcol, const bf16* __restrict__ x, int N, int H, int W,
-                              int Cin, int s, int Kp, bf16* __restrict__ dx) {
-  const int Ho = H / s, Wo = W / s;
-  const int octs = Cin / 8;
-  const long long total = (long long)N * H * W * octs;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(e % octs) * 8;
-    const long long pix = e / octs;
-    const int w = (int)(pix % W), h = (int)((pix / W) % H);
-    const long long n = pix / ((long long)W * H);
-    float a[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) a[t] = 0.0f;
-    for (int kh = 0; kh < 3; ++kh) {
-      const int ti = h + 1 - kh;
-      if (ti < 0 || ti % s) continue;
-      const int i = ti / s;
-      if (i >= Ho) continue;
-      for (int kw = 0; kw < 3; ++kw) {
-        const int tj = w + 1 - kw;
-        if (tj < 0 || tj % s) continue;
-        const int j = tj / s;
-        if (j >= Wo) continue;
-        const uint4 v = *reinterpret_cast<const uint4*>(dcol + ((n * Ho + i) * Wo + j) * Kp + (kh * 3 + kw) * Cin + c);
-        const __nv_bfloat162* b = reinterpret_cast<const __nv_bfloat162*>(&v);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          a[2 * t] += __low2float(b[t]);
-          a[2 * t + 1] += __high2float(b[t]);
-        }
-      }
-    }
-    const long long o = pix * Cin + c;
-    const uint4 xv = *reinterpret_cast<const uint4*>(x + o);
-    const __nv_bfloat162* xb = reinterpret_cast<const __nv_bfloat162*>(&xv);
-    uint4 out;
-    __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&out);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const float v0 = __low2float(xb[t]) > 0.0f ? a[2 * t] : 0.0f;
-      const float v1 = __high2float(xb[t]) > 0.0f ? a[2 * t + 1] : 0.0f;
-      ob[t] = __floats2bfloat162_rn(v0, v1);
-    }
-    *reinterpret_cast<uint4*>(dx + o) = out;
   }
 }
 
@@ -894,18 +896,20 @@ int perch_cnn::backward(const bf16* crops, int n) {
     p.ldc = kFeat;
     CKN((gemm<EPI_F32, true, false>(p, 1, stream)), "fc1 data-gradient gemm");
   }
+  bf16* cur = dz.as<bf16>();   // gradient of the current layer's output
+  bf16* nxt = dcol.as<bf16>();  // receives the gradient of its input
   k_feat_relu_grad<<<grid_for(N * kFeat), 256, 0, stream>>>(dfeat.as<float>(), feat.as<bf16>(), Kf, n,
-                                                             dz.as<bf16>());
+                                                             cur);
   CKN(cudaGetLastError(), "relu gradient kernel");
   for (int l = kConvs - 1; l >= 0; --l) {
     const int H = kHin[l], s = kStride[l], Ho = H / s, Kp = kp_of(l), Co = kCout[l];
     const long long M = N * Ho * Ho;
-    if (int rc = bias_grad(dz.as<bf16>(), M, Co, G + off_b[l])) return rc;
+    if (int rc = bias_grad(cur, M, Co, G + off_b[l])) return rc;
     // dW = dz^T col: both operands pixel-major, split along the pixel reduction,
     // partials summed in order
     {
       GemmArgs p{};
-      p.A = dz.as<bf16>();
+      p.A = cur;
       p.lda = Co;
       p.M = Co;
       p.N = Kp;
@@ -928,25 +932,32 @@ int perch_cnn::backward(const bf16* crops, int n) {
       CKN(cudaGetLastError(), "split sum kernel");
     }
     if (l == 0) break;
-    // dcol = dz W (fp32; W read as [K = Co][N = Kp]), then col2im with the ReLU
-    // mask of this layer's input
-    {
-      GemmArgs p{};
-      p.A = dz.as<bf16>();
-      p.lda = Co;
-      p.B = w16.as<bf16>() + off_w[l];
-      p.ldb = Kp;
-      p.M = (int)M;
-      p.N = Kp;
-      p.K = Co;
-      p.Ksplit = Co;
-      p.Cb = dcol.as<bf16>();
-      p.ldc = Kp;
-      CKN((gemm<EPI_BF16, true, false>(p, 1, stream)), "conv data-gradient gemm");
-    }
-    k_col2im_relu<<<grid_for(N * H * H * (kCin[l] / 8)), 256, 0, stream>>>(
-        dcol.as<bf16>(), act[l - 1].as<bf16>(), n, H, H, kCin[l], s, Kp, dz.as<bf16>());
-    CKN(cudaGetLastError(), "col2im kernel");
+    // data gradient of this layer's input, ReLU mask applied: one implicit
+    // GEMM per parity class of the input pixels (1, 2, 2 or 4 taps), written
+    // straight into the other gradient buffer
+    for (int ph = 0; ph < 2; ++ph)
+      for (int pw = 0; pw < 2; ++pw) {
+        GemmArgs p{};
+        p.A = cur;
+        p.B = w16.as<bf16>() + off_w[l];
+        p.M = (int)M;  // the class has as many pixels as the layer output
+        p.N = kCin[l];
+        p.ntw = pw ? 2 : 1;
+        p.K = (ph ? 2 : 1) * p.ntw * Co;
+        p.Ksplit = p.K;
+        p.par_h = ph;
+        p.par_w = pw;
+        p.dg_lg_ho = ilog2(Ho);
+        p.dg_lg_co = ilog2(Co);
+        p.lg_c = p.dg_lg_co;
+        p.dg_H = H;
+        p.dg_cin = kCin[l];
+        p.dg_kp = Kp;
+        p.mask = act[l - 1].as<bf16>();
+        p.Cb = nxt;
+        CKN((gemm<EPI_DGRAD, true, false, 3>(p, 1, stream)), "conv data-gradient gemm");
+      }
+    std::swap(cur, nxt);
   }
   (void)crops;
   return PERCH_OK;
