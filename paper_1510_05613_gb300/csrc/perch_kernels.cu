@@ -139,11 +139,11 @@ __device__ __forceinline__ bool explained_by_obs(const ObsIndex& o, float px, fl
   }
   const int x0 = max(ix - 1, 0), x1 = min(ix + 1, o.n3x - 1);
   if (x0 > x1) return false;
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int cz = iz + dz;
+  for (int a = 0; a < 3; ++a) {  // the centre row first: the likeliest to hold a match
+    const int cz = iz + (a == 0 ? 0 : (a == 1 ? -1 : 1));
     if (cz < 0 || cz >= o.n3z) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int cy = iy + dy;
+    for (int bq = 0; bq < 3; ++bq) {
+      const int cy = iy + (bq == 0 ? 0 : (bq == 1 ? -1 : 1));
       if (cy < 0 || cy >= o.n3y) continue;
       const int base = (cz * o.n3y + cy) * o.n3x;
       const int s = __ldg(&o.start3[base + x0]), e = __ldg(&o.start3[base + x1 + 1]);
