@@ -655,6 +655,8 @@ def run_c4(args):
     peaks = _measured_peaks()
     arms = [("plain", 1.0, 0), ("mha_depth", args.w, 1), ("mha", args.w, 3), ("mha_depth+learned", args.w, 5),
             ("mha+learned", args.w, 7)]
+    if args.arms:
+        arms = [a for a in arms if a[0] in args.arms.split(",")]
     out, learned_cost = {}, {}
     with ClockSampler(0) as clocks, MemoryGuard() as mem:
         for name, w, hb in arms:
@@ -744,6 +746,8 @@ def main():
     ap.add_argument("--candidates", type=int, default=8, help="c4: placements per type the learned queue scores")
     ap.add_argument("--c4-grid", type=int, default=50, choices=[25, 50], help="c4: 50 = 2 cm x 16 yaws, 25 = 4 cm x 8")
     ap.add_argument("--off-grid", type=float, default=1.0, help="c4: off-grid offsets, in grid steps (0..1)")
+    ap.add_argument("--arms", default="", help="c4: comma-separated subset of plain, mha_depth, mha, "
+                                               "mha_depth+learned, mha+learned (default: all)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "cnn"],
                     help="c2: 640x480 three ~10k-triangle meshes (the headline); c3: heavy occlusion, 2k-50k triangles")
     args = ap.parse_args()
