@@ -129,8 +129,10 @@ def focal_mha(world, depth, grid, multiset, w: float, heuristics=("depth", "over
     the open states with g <= w * (smallest anchor key); the queues take turns
     (anchor, then each inadmissible heuristic picking its minimum over the
     focal set). h_depth(s) = K - |s|; h_overlap(s) = |I| - |I n V_j|, kept per
-    state from the records' n_vol. Stops when the best goal has
-    g <= w * (smallest anchor key). Returns (cost, goal_key, expansions)."""
+    state from the records' n_vol; any other entry of `heuristics` is a
+    callable h(sorted key) (Theorem 2 holds for every inadmissible heuristic).
+    Stops when the best goal has g <= w * (smallest anchor key). Returns
+    (cost, goal_key, expansions)."""
     from paper_1510_05613_gb300.synth import OBJ_DTYPE
     K = len(multiset)
     states = {(): (np.zeros(0, OBJ_DTYPE), 0, n_obs)}  # key -> (objects, g, h_overlap)
@@ -150,7 +152,10 @@ def focal_mha(world, depth, grid, multiset, w: float, heuristics=("depth", "over
             key = min(open_set, key=lambda k: (states[k][1], k))
         else:
             focal = [k for k in open_set if states[k][1] <= w * f0]
-            h = (lambda k: K - len(k)) if q == "depth" else (lambda k: states[k][2])
+            if callable(q):
+                h = q
+            else:
+                h = (lambda k: K - len(k)) if q == "depth" else (lambda k: states[k][2])
             key = min(focal, key=lambda k: (h(k), states[k][1], k))
         open_set.discard(key)
         closed.add(key)

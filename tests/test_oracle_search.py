@@ -81,3 +81,20 @@ def test_focal_mha_respects_the_suboptimality_bound(small_c1, w):
     assert cost is not None and opt <= cost <= w * opt + 1e-9
     if w == 1.0:
         assert cost == opt
+
+
+def test_focal_mha_bound_holds_for_any_inadmissible_heuristic(small_c1):
+    """Theorem 2 does not depend on what the inadmissible queues compute:
+    with adversarial heuristics (preferring the emptiest states, or an
+    arbitrary hash of the key) the answer still costs at most w * OPT."""
+    wl = small_c1
+    wo = oracle.World.of(wl)
+    opt, _ = search.exhaustive(wo, wl.depth, wl.grid, wl.mesh_multiset)
+    adversarial = lambda k: len(k)  # shallowest first
+    scrambled = lambda k: hash(k) % 97
+    for w in (1.0, 2.0):
+        cost, key, exp = search.focal_mha(wo, wl.depth, wl.grid, wl.mesh_multiset, w,
+                                          heuristics=(adversarial, scrambled))
+        assert cost is not None and opt <= cost <= w * opt
+        if w == 1.0:
+            assert cost == opt
