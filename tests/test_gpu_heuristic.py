@@ -84,3 +84,16 @@ def test_learned_queue_needs_a_network(setup):
         p.perch_search_multi(te[:1], [test_sc[0].mesh_multiset], w=2.0, heuristics=4)
     assert e.value.code == perch.PERCH_E_STATE
     p.perch_set_heuristic_net(net, 8)
+
+
+def test_search_statistics_account_for_the_learned_queue(setup):
+    p, net, test_sc, te, *_ = setup
+    ms = [wl.mesh_multiset for wl in test_sc]
+    p.perch_set_heuristic_net(net, 8)
+    p.perch_search_multi(te, ms, batch_states=2, w=2.0, heuristics=5)
+    seconds, states, crops = p.perch_search_stats()
+    ev, ab, sel = p.perch_search_times()
+    assert states > 0 and crops > 0 and seconds > 0.0
+    assert ev > 0.0 and ab > 0.0 and sel > 0.0
+    p.perch_search_multi(te, ms, batch_states=2, w=1.0, heuristics=0)
+    assert p.perch_search_stats()[1:] == (0, 0)
