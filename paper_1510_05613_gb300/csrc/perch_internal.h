@@ -18,6 +18,8 @@ constexpr int kEvalThreads = 256;
 constexpr int kEvalWarps = kEvalThreads / 32;
 constexpr int kInlinePixels = 16;  // a lane tests at most this many pixel centres per triangle
 constexpr int kBigQueue = 128;     // per-chunk queue of larger triangles, shared by the CTA
+// dR pixel list of one hypothesis (uint16 tile indices) over the chunk buffers
+constexpr int kDrListMax = (kChunkMaxVerts * 16 + kChunkMaxTris * 4 + kChunkMaxVerts * 8) / 2;
 constexpr int kWaitSpins = 1 << 20;  // bound on mbarrier polls before a kernel gives up
 constexpr int kMaxObjectPixels = 1000;  // screen box limit that keeps edge arithmetic in int32
 constexpr float kNearZ = 0.05f;    // cull: vertex depth at or below this

@@ -187,14 +187,21 @@ __device__ __forceinline__ bool explained_by_tile(const Camera& cam, float4 q, c
   delta_window(cam, q, u0, u1, v0, v1);
   u0 = max(u0, bb.x); u1 = min(u1, bb.x + bb.z - 1);
   v0 = max(v0, bb.y); v1 = min(v1, bb.y + bb.w - 1);
+  if (u0 > u1) return false;
+  const int la = u0 - bb.x, lb = u1 - bb.x;
   for (int v = v0; v <= v1; ++v) {
     const int ly = v - bb.y;
     const float ry = rys[ly];
-    for (int u = u0; u <= u1; ++u) {
-      const int lx = u - bb.x;
-      if (!in_dr(dmask, mw, lx, ly)) continue;
-      const float z = __uint_as_float(tile[ly * bb.z + lx]);
-      if (dist2(fmul(rxs[lx], z), fmul(ry, z), z, q) <= cam.delta2) return true;
+    const uint32_t* row = dmask + ly * mw;
+    for (int wi = la >> 5; wi <= lb >> 5; ++wi) {  // only the dR pixels of the window's row
+      const int lo = max(la - 32 * wi, 0), hi = min(lb - 32 * wi, 31);
+      uint32_t bits = row[wi] & (0xffffffffu << lo) & (0xffffffffu >> (31 - hi));
+      while (bits) {
+        const int lx = 32 * wi + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const float z = __uint_as_float(tile[ly * bb.z + lx]);
+        if (dist2(fmul(rxs[lx], z), fmul(ry, z), z, q) <= cam.delta2) return true;
+      }
     }
   }
   return false;
@@ -961,15 +968,13 @@ __device__ bool eval_group(const int* members, int n, long long h1, const Camera
   }
   if (culled) s_cnt[2] = 1;
   __syncthreads();
-  // the tile now holds z = 1/(1/z), taken once per pixel, and +inf where empty
-  for (int ly = warp; ly < th; ly += NW)
-    for (int lx = lane; lx < tw; lx += 32) {
-      const uint32_t izb = tile[ly * tw + lx];
-      tile[ly * tw + lx] = izb == 0u ? kInfBits : __float_as_uint(__frcp_rn(__uint_as_float(izb)));
-    }
   const uint32_t flags = s_cnt[2] ? PERCH_FLAG_CULLED : 0u;
-  __syncthreads();
+  // dR pixel list (tile indices; a tile fits shared memory, so it has fewer
+  // than 2^16 pixels) over the chunk buffers, which are idle until the next
+  // work item's first copies
+  uint16_t* drlist = reinterpret_cast<uint16_t*>(smem);
 
+  bool as_z = false;  // the tile holds 1/z until the first member's pass turns it into z
   for (int j = 0; j < n; ++j) {
     const long long h = member(j);
     const int pid = b.hyp_parent[h];
@@ -996,7 +1001,7 @@ __device__ bool eval_group(const int* members, int n, long long h1, const Camera
     // rendered pixel is in dR where the parent render is empty; where it is
     // not, the pixel is hidden by (or hides) the parent and a nearer new
     // surface is a violation
-    int viol = 0, nnew = 0;
+    int viol = 0;
     const float* zp = plen > 0 ? b.parent_z + (size_t)pid * cam.W * cam.H : nullptr;
     for (int ly = warp; ly < th; ly += NW) {
       const float* prow = zp ? zp + (size_t)(bb.y + ly) * cam.W + bb.x : nullptr;
@@ -1004,7 +1009,11 @@ __device__ bool eval_group(const int* members, int n, long long h1, const Camera
         const int lx = lx0 + lane;
         bool in = false;
         if (lx < tw) {
-          const uint32_t zb = tile[ly * tw + lx];
+          uint32_t zb = tile[ly * tw + lx];
+          if (!as_z) {  // z = 1/(1/z), once per pixel; +inf where empty
+            zb = zb == 0u ? kInfBits : __float_as_uint(__frcp_rn(__uint_as_float(zb)));
+            tile[ly * tw + lx] = zb;
+          }
           if (zb != kInfBits) {
             in = true;
             if (prow) {
@@ -1016,17 +1025,19 @@ __device__ bool eval_group(const int* members, int n, long long h1, const Camera
             }
           }
         }
-        nnew += in;
         const uint32_t word = __ballot_sync(0xffffffffu, in);
-        if (lane == 0) dmask[ly * mw + (lx0 >> 5)] = word;
+        int base = 0;  // |dR| so far (s_cnt[1]) is also the word's place in the dR list
+        if (lane == 0) {
+          dmask[ly * mw + (lx0 >> 5)] = word;
+          if (word) base = atomicAdd(&s_cnt[1], __popc(word));
+        }
+        base = __shfl_sync(0xffffffffu, base, 0) + __popc(word & ((1u << lane) - 1u));
+        if (in && base < kDrListMax) drlist[base] = (uint16_t)(ly * tw + lx);
       }
     }
+    as_z = true;
     viol = warp_sum(viol);
-    nnew = warp_sum(nnew);
-    if (lane == 0) {
-      if (viol) atomicAdd(&s_cnt[0], viol);
-      if (nnew) atomicAdd(&s_cnt[1], nnew);
-    }
+    if (lane == 0 && viol) atomicAdd(&s_cnt[0], viol);
     __syncthreads();
     if (s_cnt[0] > 0) {
       if (tid == 0) {
@@ -1037,14 +1048,26 @@ __device__ bool eval_group(const int* members, int n, long long h1, const Camera
       continue;
     }
 
-    // ---- dJ_r: dR points with no observed point within delta
+    // ---- dJ_r: dR points with no observed point within delta (from the
+    // compact list when it holds all of dR, else from the mask)
     int djr = 0;
-    for (int ly = warp; ly < th; ly += NW) {
-      const float ry = rys[ly];
-      for (int lx = lane; lx < tw; lx += 32) {
-        if (!in_dr(dmask, mw, lx, ly)) continue;
-        const float z = __uint_as_float(tile[ly * tw + lx]);
-        if (!explained_by_obs(obs, fmul(rxs[lx], z), fmul(ry, z), z, cam.delta2)) djr++;
+    const int ndr = s_cnt[1];
+    if (ndr <= kDrListMax) {
+      const uint32_t magic = 0xffffffffu / (uint32_t)tw + 1u;  // k / tw for k, tw < 2^16 (tw > 1)
+      for (int k = tid; k < ndr; k += NT) {
+        const int idx = drlist[k];
+        const int ly = tw == 1 ? idx : (int)__umulhi((uint32_t)idx, magic), lx = idx - ly * tw;
+        const float z = __uint_as_float(tile[idx]);
+        if (!explained_by_obs(obs, fmul(rxs[lx], z), fmul(rys[ly], z), z, cam.delta2)) djr++;
+      }
+    } else {
+      for (int ly = warp; ly < th; ly += NW) {
+        const float ry = rys[ly];
+        for (int lx = lane; lx < tw; lx += 32) {
+          if (!in_dr(dmask, mw, lx, ly)) continue;
+          const float z = __uint_as_float(tile[ly * tw + lx]);
+          if (!explained_by_obs(obs, fmul(rxs[lx], z), fmul(ry, z), z, cam.delta2)) djr++;
+        }
       }
     }
 
@@ -1102,8 +1125,11 @@ __device__ bool eval_group(const int* members, int n, long long h1, const Camera
       perch_cost r = {s_cnt[3], s_cnt[4], s_cnt[5], 0, s_cnt[1], flags, s_cnt[6]};
       b.out[h] = r;
     }
-    __syncthreads();  // s_cnt, s_obs and the mask are reused by the next member
+    __syncthreads();  // s_cnt, s_obs, the mask and the dR list are reused by the next member
   }
+  // the dR list's (generic) writes come before the next item's bulk copies
+  // into the same shared memory (async proxy)
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();  // the tile is reused by the next work item
   return true;
 }
