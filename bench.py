@@ -82,27 +82,16 @@ def _remaining(multiset, parent):
     return rem
 
 
-def renders_per_mesh(wl, hyps, shared: bool):
-    """Renders the evaluation kernel makes per mesh: one per distinct (mesh,
-    pose) with shared renders, one per hypothesis without."""
-    if not shared:
-        return np.bincount(hyps["mesh"].astype(np.int64), minlength=len(wl.meshes))
-    keys = np.unique(((hyps["mesh"].astype(np.int64) * wl.grid.nx + hyps["ix"]) * wl.grid.ny + hyps["iy"])
-                     * wl.grid.n_yaw + hyps["iyaw"])
-    return np.bincount(keys // (wl.grid.nx * wl.grid.ny * wl.grid.n_yaw), minlength=len(wl.meshes))
-
-
-def algorithmic_ops(wl, renders, n_new):
-    """Lower bound of the arithmetic one evaluation must do: per render of a
-    mesh (renders[m] of mesh m), 40 ops per vertex (pose + camera transform,
-    projection, snap, reciprocal depth) and 20 per triangle (edge setup,
-    facing and extent tests, pixel box); per hypothesis, 50 per pixel of its
-    dR (3 edge functions, depth interpolation, z-buffer min, back-projection
-    and the first delta probe)."""
+def algorithmic_ops(wl, hyps, n_new):
+    """Lower bound of the arithmetic one evaluation must do, per hypothesis:
+    40 ops per mesh vertex (pose + camera transform, projection, snap,
+    reciprocal depth), 20 per triangle (edge setup, facing and extent tests,
+    pixel box), 50 per pixel of dR (3 edge functions, depth interpolation,
+    z-buffer min, back-projection and the first delta probe)."""
     V = np.array([m.n_verts for m in wl.meshes], np.float64)
     T = np.array([m.n_tris for m in wl.meshes], np.float64)
-    r = np.asarray(renders, np.float64)
-    return float((r * (40.0 * V + 20.0 * T)).sum() + 50.0 * np.asarray(n_new, np.float64).sum())
+    mi = hyps["mesh"].astype(np.int64)
+    return float((40.0 * V[mi] + 20.0 * T[mi]).sum() + 50.0 * np.asarray(n_new, np.float64).sum())
 
 
 class ClockSampler:
@@ -293,11 +282,8 @@ def run_ours(args):
     else:
         widths = p.perch_autotune(args.tune_sample) if not args.no_autotune else None
 
-    # the headline evaluates every hypothesis in the kernel, one render per
-    # distinct (mesh, pose); the exact shortcut and one render per hypothesis
-    # are measured after it
+    # the headline renders every hypothesis; the exact shortcut is measured after
     p.perch_set_shortcut(False)
-    p.perch_set_share_renders(True)
 
     def step():  # the whole evaluation sequence as one CUDA-graph launch (or direct launches)
         if args.no_graph:
@@ -334,12 +320,8 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in evs]
     total_s, value = whole_job(sum(step_ms) / 1e3, n_hyp * args.steps)
 
-    n_renders, n_kernel = p.perch_share_stats()
     rec = tout.view(-1, 7).cpu().numpy()
-    rpm = renders_per_mesh(wl, hyps, True)
-    if int(rpm.sum()) != n_renders or n_kernel != n_hyp:
-        raise RuntimeError(f"render count {n_renders} / {n_kernel} differs from the batch's {int(rpm.sum())} poses")
-    ops = algorithmic_ops(wl, rpm, rec[:, 4])
+    ops = algorithmic_ops(wl, hyps, rec[:, 4])
     peaks = _measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(dev)
@@ -373,42 +355,21 @@ def run_ours(args):
                        "(batch upload, evaluation, record download)"}
     consistent = bool(np.array_equal(perch.records(out), rec.astype(np.int64)))
 
-    def timed_steps(n):
-        ms = []
-        for k in range(n):
-            flush.fill_(k)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step()
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        return ms
-
-    # one render per hypothesis (sharing off; records identical, checked)
-    p.perch_set_share_renders(False)
-    for _ in range(3):
-        flush.fill_(1)
-        step()
-    torch.cuda.synchronize()
-    ev_ms = timed_steps(args.steps)
-    p.perch_eval_successors_dev(tP, stride, tplen, thp, th, wl.K, tout)
-    ev_same = bool(np.array_equal(tout.view(-1, 7).cpu().numpy(), rec))
-    ev_ops = algorithmic_ops(wl, renders_per_mesh(wl, hyps, False), rec[:, 4])
-    ev_eval_s = p.perch_last_timing()[1] / 1e3
-    every = {"value": ws * n_hyp / (statistics.mean(ev_ms) / 1e3), "unit": UNIT,
-             "ms_per_step": statistics.mean(ev_ms), "renders_per_step": n_hyp, "records_identical": ev_same,
-             "k_eval_frac": ev_ops / ev_eval_s / 1e12 / peak_tops,
-             "meaning": "shared renders off: every hypothesis rasterises its own copy of the new object"}
-    p.perch_set_share_renders(True)
-
     # the same batch with the exact shortcut (records identical, checked)
     p.perch_set_shortcut(True)
     for _ in range(3):
         flush.fill_(1)
         step()
     torch.cuda.synchronize()
-    sc_ms = timed_steps(args.steps)
+    sc_ms = []
+    for k in range(args.steps):
+        flush.fill_(k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        sc_ms.append(e0.elapsed_time(e1))
     p.perch_eval_successors_dev(tP, stride, tplen, thp, th, wl.K, tout)
     n_short, _ = p.perch_shortcut_stats()
     sc_same = bool(np.array_equal(tout.view(-1, 7).cpu().numpy(), rec))
@@ -438,8 +399,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload],
-                       "hypotheses_per_step": n_hyp, "renders_per_step": n_renders,
-                       "l2": "flushed (256 MiB write) before every timed step",
+                       "hypotheses_per_step": n_hyp, "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "alu", "kernel": "k_eval", "achieved": achieved, "peak": peak_tops,
                          "unit": "Tops/s", "frac": achieved / peak_tops,
@@ -450,11 +410,10 @@ def run_ours(args):
                          "peak_from": f"{n_sm} SMs x {FP32_LANES_PER_SM} lanes x {sm_max:.0f} MHz "
                                       "(sm_max_mhz of MEASURED_PEAKS.json)"},
             "e2e": e2e, "e2e_matches_device_records": consistent,
-            "gpu_launches": (15 + len(wl.meshes)) * args.steps,
+            "gpu_launches": (8 + len(wl.meshes)) * args.steps,
             "launch": {"graph": not args.no_graph, "persistent_per_mesh": True, "autotuned_threads": widths},
             "clocks": cl,
             "time_to_optimum": search,
-            "render_every_hypothesis": every,
             "shortcut": shortcut,
             "cpu_baseline": base,
         }

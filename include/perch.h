@@ -308,22 +308,6 @@ int perch_set_shortcut(perch_ctx* ctx, int32_t on);
  * shortcut (0 if it was off) and how many there were. Waits for the stream. */
 int perch_shortcut_stats(perch_ctx* ctx, int64_t* n_short, int64_t* n_total);
 
-/* Shared renders (on by default). The new object's z tile (Sec. IV-A: the
- * render of O at its pose) depends on its mesh and pose alone, not on the
- * parent it is added to. With sharing on, the hypotheses of one evaluation
- * that place the same mesh at the same grid pose (typically the same pose
- * under several parents of one batch) are grouped, the pose is rasterised
- * once, and each hypothesis is then tested against its own parent render and
- * scene (Eq. (3) violations, dR, dJ_r, dJ_o, residual). Records are
- * identical with sharing on or off. on = 0 rasterises once per hypothesis. */
-int perch_set_share_renders(perch_ctx* ctx, int32_t on);
-
-/* Of the most recent evaluation: how many renders the evaluation kernel made
- * (n_renders) for how many hypotheses (n_evaluated; those the shortcut
- * settled and those with a bad index are not counted). Equal with sharing
- * off. Waits for the stream. PERCH_E_STATE before the first evaluation. */
-int perch_share_stats(perch_ctx* ctx, int64_t* n_renders, int64_t* n_evaluated);
-
 /* Device time of the most recent evaluation (perch_eval_successors or
  * perch_eval_successors_dev), measured with CUDA events recorded on the
  * context's stream around its two phases: prep_ms = parent z-buffers and

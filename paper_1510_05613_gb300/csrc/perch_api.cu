@@ -622,45 +622,23 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
   short_counted = use_short;
   last_total = n_hyp;
   if (!capturing) CK(cudaEventRecord(ev[1], stream), "event");
-  // group by mesh (and, sharing renders, by pose within a mesh); one
-  // persistent launch per mesh with its own tile and CTA width
+  // group by mesh; one persistent launch per mesh with its own tile and CTA width
   CK(g_hist.ensure(sizeof(int) * (size_t)n_mesh), "alloc");
   CK(g_off.ensure(sizeof(int) * ((size_t)n_mesh + 1)), "alloc");
   CK(g_cursor.ensure(sizeof(int) * (2 * (size_t)n_mesh + 1)), "alloc");
   CK(g_next.ensure(sizeof(int) * (size_t)n_mesh), "alloc");
   CK(g_order.ensure(sizeof(int) * (size_t)std::max(n_hyp, 1LL)), "alloc");
   CK(scan_tmp.ensure(sizeof(int) * ((size_t)n_mesh / 1024 + 2)), "alloc");
-  const bool by_pose = share_renders && !building_solo;
-  const long long P = (long long)n_mesh * nx * ny * n_yaw;
-  if (by_pose) {
-    if (P > 0x7ffffffeLL) return fail(PERCH_E_ARG, "pose grid too large to group by pose");
-    CK(pg_cnt.ensure(sizeof(int) * (size_t)P), "alloc");
-    CK(pg_start.ensure(sizeof(int) * ((size_t)P + 1)), "alloc");
-    CK(pg_flag.ensure(sizeof(int) * (size_t)P), "alloc");
-    CK(pg_gix.ensure(sizeof(int) * ((size_t)P + 1)), "alloc");
-    CK(pg_gstart.ensure(sizeof(int) * (size_t)P), "alloc");
-    CK(pg_gcount.ensure(sizeof(int) * (size_t)P), "alloc");
-    CK(pg_tmp.ensure(sizeof(int) * ((size_t)P / 1024 + 2)), "alloc");
-    PoseGroups pg{pg_cnt.as<int>(),   pg_start.as<int>(), pg_flag.as<int>(), pg_gix.as<int>(),
-                  pg_gstart.as<int>(), pg_gcount.as<int>(), pg_tmp.as<int>(), g_off.as<int>(),
-                  g_hist.as<int>(),    g_order.as<int>()};
-    CK(launch_group_by_pose(g, b, pg, stream), "group by pose");
-  } else {
-    CK(launch_group_by_mesh(d_hyp, n_hyp, n_mesh, g_hist.as<int>(), g_off.as<int>(), g_cursor.as<int>(),
-                            g_order.as<int>(), scan_tmp.as<int>(), stream, use_short ? skip.as<uint8_t>() : nullptr),
-       "group by mesh");
-  }
-  last_grouping = by_pose ? 2 : 1;
-  last_poses = P;
+  CK(launch_group_by_mesh(d_hyp, n_hyp, n_mesh, g_hist.as<int>(), g_off.as<int>(), g_cursor.as<int>(),
+                          g_order.as<int>(), scan_tmp.as<int>(), stream, use_short ? skip.as<uint8_t>() : nullptr),
+     "group by mesh");
   CK(cudaMemsetAsync(g_next.p, 0, sizeof(int) * (size_t)n_mesh, stream), "memset");
   for (int m = 0; m < n_mesh; ++m) {
     Batch bm = b;
     bm.tile_w = mesh_tile_w[m];
     bm.tile_h = mesh_tile_h[m];
     CK(launch_eval_group(cam, g, obs, bm, g_order.as<int>(), g_off.as<int>() + m, g_hist.as<int>() + m,
-                         g_next.as<int>() + m, by_pose ? std::min<long long>(n_hyp, P) : n_hyp, mesh_threads[m],
-                         sm_count, stream, by_pose ? pg_gstart.as<int>() : nullptr,
-                         by_pose ? pg_gcount.as<int>() : nullptr),
+                         g_next.as<int>() + m, n_hyp, mesh_threads[m], sm_count, stream),
        "eval kernel");
   }
   if (!capturing) {
@@ -803,33 +781,6 @@ int perch_set_shortcut(perch_ctx* ctx, int32_t on) {
   ctx->err.clear();
   ctx->shortcut = on != 0;
   ctx->tables_version++;  // a captured graph holds the old choice
-  return PERCH_OK;
-}
-
-int perch_set_share_renders(perch_ctx* ctx, int32_t on) {
-  if (!ctx) return PERCH_E_ARG;
-  ctx->err.clear();
-  ctx->share_renders = on != 0;
-  ctx->tables_version++;  // a captured graph holds the old choice
-  return PERCH_OK;
-}
-
-int perch_share_stats(perch_ctx* ctx, int64_t* n_renders, int64_t* n_evaluated) {
-  if (!ctx) return PERCH_E_ARG;
-  ctx->err.clear();
-  if (!ctx->last_grouping) return ctx->fail(PERCH_E_STATE, "no evaluation yet");
-  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  CK(cudaStreamSynchronize(ctx->stream), "stream");
-  int r = 0, e = 0;
-  if (ctx->last_grouping == 2) {
-    CK(cudaMemcpy(&r, ctx->pg_gix.as<int>() + ctx->last_poses, sizeof(int), cudaMemcpyDeviceToHost), "read");
-    CK(cudaMemcpy(&e, ctx->pg_start.as<int>() + ctx->last_poses, sizeof(int), cudaMemcpyDeviceToHost), "read");
-  } else {
-    CK(cudaMemcpy(&e, ctx->g_off.as<int>() + ctx->n_mesh, sizeof(int), cudaMemcpyDeviceToHost), "read");
-    r = e;
-  }
-  if (n_renders) *n_renders = r;
-  if (n_evaluated) *n_evaluated = e;
   return PERCH_OK;
 }
 

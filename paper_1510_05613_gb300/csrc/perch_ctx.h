@@ -83,11 +83,6 @@ struct perch_ctx {
   // per-batch buffers
   DevBuf parent_z, uset, uset_count;
   DevBuf g_hist, g_off, g_cursor, g_order, g_next;  // hypotheses grouped by mesh
-  // hypotheses grouped by pose, one render per group (share_renders)
-  bool share_renders = true;
-  DevBuf pg_cnt, pg_start, pg_flag, pg_gix, pg_gstart, pg_gcount, pg_tmp;
-  int last_grouping = 0;  // last evaluation: 0 none, 1 by mesh, 2 by pose
-  long long last_poses = 0;
   DevBuf b_parents, b_plen, b_hp, b_hyp, b_out;
 
   // captured evaluation graph (perch_eval_graph); `version` changes whenever
@@ -126,8 +121,7 @@ struct perch_ctx {
             &scan_tmp, &cam_pts, &world_pts, &keys, &counts, &cursor, &d_scenes, &d_scene_img,
             &scratch_small, &pose_bbox, &parent_z, &uset, &uset_count, &b_parents, &b_plen, &b_hp, &b_hyp,
             &b_out, &g_hist, &g_off, &g_cursor, &g_order, &g_next, &net_crops, &net_onehot, &net_pred,
-            &solo, &solo_rec, &solo_hyp, &solo_hp, &solo_parent, &ptile_counts, &ptile_sat, &skip, &n_short,
-            &pg_cnt, &pg_start, &pg_flag, &pg_gix, &pg_gstart, &pg_gcount, &pg_tmp};
+            &solo, &solo_rec, &solo_hyp, &solo_hp, &solo_parent, &ptile_counts, &ptile_sat, &skip, &n_short};
   }
 
   int fail(int code, const char* fmt, ...);

@@ -18,8 +18,6 @@ constexpr int kEvalThreads = 256;
 constexpr int kEvalWarps = kEvalThreads / 32;
 constexpr int kInlinePixels = 16;  // a lane tests at most this many pixel centres per triangle
 constexpr int kBigQueue = 128;     // per-chunk queue of larger triangles, shared by the CTA
-// dR pixel list of one hypothesis (uint16 tile indices) over the chunk buffers
-constexpr int kDrListMax = (kChunkMaxVerts * 16 + kChunkMaxTris * 4 + kChunkMaxVerts * 8) / 2;
 constexpr int kWaitSpins = 1 << 20;  // bound on mbarrier polls before a kernel gives up
 constexpr int kMaxObjectPixels = 1000;  // screen box limit that keeps edge arithmetic in int32
 constexpr float kNearZ = 0.05f;    // cull: vertex depth at or below this
@@ -143,25 +141,9 @@ cudaError_t launch_parent_tiles(const Camera& cam, const Batch& b, int* counts, 
 cudaError_t launch_shortcut(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
                             cudaStream_t s);
 cudaError_t launch_solo_pack(const perch_cost* rec, long long n, int2* solo, cudaStream_t s);
-// hypotheses grouped by pose (one shared render per group); all device arrays
-// of P = n_mesh x nx x ny x n_yaw poses unless stated
-struct PoseGroups {
-  int* cnt;          // P: hypotheses per pose
-  int* start;        // P + 1: exclusive scan of cnt
-  int* flag;         // P: cnt > 0
-  int* gix;          // P + 1: exclusive scan of flag (gix[P] = groups)
-  int* gstart;       // P: group -> first index into order
-  int* gcount;       // P: group -> hypotheses
-  int* tmp;          // P / 1024 + 2: scan scratch
-  int* mesh_offset;  // n_mesh: first group of each mesh
-  int* mesh_count;   // n_mesh: groups of each mesh
-  int* order;        // n_hyp: hypotheses sorted by pose
-};
-cudaError_t launch_group_by_pose(const Geometry& g, const Batch& b, const PoseGroups& pg, cudaStream_t s);
 cudaError_t launch_eval_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
                               const int* order, const int* offset, const int* count, int* next, long long max_items,
-                              int threads, int sm_count, cudaStream_t s, const int* gstart = nullptr,
-                              const int* gcount = nullptr);
+                              int threads, int sm_count, cudaStream_t s);
 size_t eval_smem_bytes(int tile_w, int tile_h);
 bool eval_tile_fits(int device, int tile_w, int tile_h);
 

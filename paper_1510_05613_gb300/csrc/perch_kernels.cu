@@ -173,35 +173,23 @@ __device__ __forceinline__ void delta_window(const Camera& cam, float4 q, int& u
   }
 }
 
-// Is pixel (lx, ly) of the tile in dR? One bit per pixel, rows of mw words.
-__device__ __forceinline__ bool in_dr(const uint32_t* dmask, int mw, int lx, int ly) {
-  return (dmask[ly * mw + (lx >> 5)] >> (lx & 31)) & 1u;
-}
-
-// Eq. (1) against the new object's dR (z tile, dR bit mask): is some rendered
-// point of dR within delta of the observed point q?
+// Eq. (1) against the new object's dR (the z tile, +inf off dR): is some
+// rendered point within delta of the observed point q?
 __device__ __forceinline__ bool explained_by_tile(const Camera& cam, float4 q, const uint32_t* tile,
-                                                  const uint32_t* dmask, int mw, const float* rxs,
-                                                  const float* rys, int4 bb) {
+                                                  const float* rxs, const float* rys, int4 bb) {
   int u0, u1, v0, v1;
   delta_window(cam, q, u0, u1, v0, v1);
   u0 = max(u0, bb.x); u1 = min(u1, bb.x + bb.z - 1);
   v0 = max(v0, bb.y); v1 = min(v1, bb.y + bb.w - 1);
-  if (u0 > u1) return false;
-  const int la = u0 - bb.x, lb = u1 - bb.x;
   for (int v = v0; v <= v1; ++v) {
     const int ly = v - bb.y;
     const float ry = rys[ly];
-    const uint32_t* row = dmask + ly * mw;
-    for (int wi = la >> 5; wi <= lb >> 5; ++wi) {  // only the dR pixels of the window's row
-      const int lo = max(la - 32 * wi, 0), hi = min(lb - 32 * wi, 31);
-      uint32_t bits = row[wi] & (0xffffffffu << lo) & (0xffffffffu >> (31 - hi));
-      while (bits) {
-        const int lx = 32 * wi + __ffs(bits) - 1;
-        bits &= bits - 1u;
-        const float z = __uint_as_float(tile[ly * bb.z + lx]);
-        if (dist2(fmul(rxs[lx], z), fmul(ry, z), z, q) <= cam.delta2) return true;
-      }
+    for (int u = u0; u <= u1; ++u) {
+      const int lx = u - bb.x;
+      const uint32_t zb = tile[ly * bb.z + lx];
+      if (zb == kInfBits) continue;
+      const float z = __uint_as_float(zb);
+      if (dist2(fmul(rxs[lx], z), fmul(ry, z), z, q) <= cam.delta2) return true;
     }
   }
   return false;
@@ -666,8 +654,7 @@ cudaError_t launch_uset(const Camera& cam, const Geometry& g, const ObsIndex& ob
 // ------------------------------------------------------------- evaluation
 size_t eval_smem_bytes(int tile_w, int tile_h) {
   return (size_t)kChunkMaxVerts * 16 + (size_t)kChunkMaxTris * 4 + (size_t)kChunkMaxVerts * 8 +
-         (size_t)kBigQueue * 8 + (size_t)tile_w * tile_h * 4 + (size_t)(tile_w + tile_h) * 4 +
-         (size_t)tile_h * ((tile_w + 31) / 32) * 4;  // dR bit mask
+         (size_t)kBigQueue * 8 + (size_t)tile_w * tile_h * 4 + (size_t)(tile_w + tile_h) * 4;
 }
 
 bool eval_tile_fits(int device, int tile_w, int tile_h) {
@@ -797,38 +784,39 @@ struct EvalShared {
   uint32_t pv, pt;  // parity of the next phase of each barrier
 };
 
-// Evaluate the hypotheses members[0 .. n) -- all of one (mesh, pose) -- with a
-// CTA of NT threads (members == nullptr: the single hypothesis h1). The new
-// object's render depends on its mesh and pose alone, so it is rasterised
-// once into the z tile; each hypothesis then gets its own dR bit mask against
-// its own parent render and its own costs against its scene. The CTA's two
-// mbarriers persist across work items (their phase parities are in sh).
-// Returns false if a bounded wait gave up (the records then carry
-// kFlagTimeout and the barriers must not be used again).
+// Evaluate hypothesis h with a CTA of NT threads. The CTA's two mbarriers
+// persist across hypotheses (their phase parities are in sh). Returns false
+// if a bounded wait gave up (the record then carries kFlagTimeout and the
+// barriers must not be used again).
 template <int NT, bool MULTI>
-__device__ bool eval_group(const int* members, int n, long long h1, const Camera& cam, const Geometry& g,
-                           const ObsIndex& obs0, const Batch& b, EvalShared& sh, ObsIndex* s_obs) {
+__device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, const ObsIndex& obs0, const Batch& b,
+                         EvalShared& sh, ObsIndex* s_obs) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint64_t* s_bar = sh.bar;
   int* s_cnt = sh.cnt;
   int& s_qn = *sh.qn;
   unsigned char* smem = sh.dyn;
-  auto member = [&](int j) -> long long { return members ? (long long)members[j] : h1; };
-  auto put_all = [&](uint32_t flags) {  // one flag-only record for every member
-    for (int j = tid; j < n; j += NT) {
-      perch_cost r = {0, 0, 0, 0, 0, flags, 0};
-      b.out[member(j)] = r;
+  const perch_obj o = b.hyp[h];
+  const int pid = b.hyp_parent[h];
+  bool badidx = pid < 0 || pid >= b.n_par || !obj_ok(g, o);
+  const int plen = badidx ? 0 : b.parent_len[pid];
+  badidx = badidx || plen < 0 || plen > b.parent_stride;
+  const int scene = (badidx || !b.parent_scene) ? 0 : b.parent_scene[pid];
+  const int K_total = (badidx || !b.parent_K) ? b.K_total : b.parent_K[pid];
+  badidx = badidx || (b.parent_scene && (scene < 0 || scene >= b.n_scenes));
+  const int4 bb = badidx ? make_int4(0, 0, 0, 0)
+                         : g.pose_bbox[(((long long)o.mesh * g.nx + o.ix) * g.ny + o.iy) * g.n_yaw + o.iyaw];
+  if (badidx || bb.z > b.tile_w || bb.w > b.tile_h) {
+    if (tid == 0) {
+      perch_cost r = {0, 0, 0, 0, 0, kFlagBadIndex, 0};
+      b.out[h] = r;
     }
-  };
-  const perch_obj o = b.hyp[member(0)];
-  const bool okobj = obj_ok(g, o);
-  const int4 bb = okobj ? g.pose_bbox[(((long long)o.mesh * g.nx + o.ix) * g.ny + o.iy) * g.n_yaw + o.iyaw]
-                        : make_int4(0, 0, 0, 0);
-  if (!okobj || bb.z > b.tile_w || bb.w > b.tile_h) {
-    put_all(kFlagBadIndex);
     return true;
   }
+  if (MULTI && tid < (int)(sizeof(ObsIndex) / 4))  // this scene's index, read from shared memory below
+    reinterpret_cast<int*>(s_obs)[tid] = reinterpret_cast<const int*>(&b.scenes[scene])[tid];
+  const ObsIndex& obs = MULTI ? *s_obs : obs0;
   float4* vbuf = reinterpret_cast<float4*>(smem);
   uint32_t* tbuf = reinterpret_cast<uint32_t*>(vbuf + kChunkMaxVerts);
   uint32_t* sXY = tbuf + kChunkMaxTris;
@@ -837,8 +825,7 @@ __device__ bool eval_group(const int* members, int n, long long h1, const Camera
   uint32_t* tile = queue + 2 * kBigQueue;
   float* rxs = reinterpret_cast<float*>(tile + b.tile_w * b.tile_h);
   float* rys = rxs + b.tile_w;
-  uint32_t* dmask = reinterpret_cast<uint32_t*>(rys + b.tile_h);  // dR bits, rows of mw words
-  const int tw = bb.z, th = bb.w, mw = (tw + 31) >> 5;
+  const int tw = bb.z, th = bb.w;
 
   const DevMesh m = g.meshes[o.mesh];
   const float4* V = g.vtab + (size_t)o.iyaw * g.n_cverts;
@@ -963,189 +950,134 @@ __device__ bool eval_group(const int* members, int n, long long h1, const Camera
     // then report the failure instead of a cost
     if (v_pending) mbar_wait(&s_bar[0], pv);
     if (t_pending) mbar_wait(&s_bar[1], pt);
-    put_all(kFlagTimeout);
+    if (tid == 0) {
+      perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout, 0};
+      b.out[h] = r;
+    }
     return false;
   }
   if (culled) s_cnt[2] = 1;
   __syncthreads();
+
+  // ---- monotone test against the parent render and dR (Eq. (3))
+  int viol = 0, nnew = 0;
+  const float* zp = plen > 0 ? b.parent_z + (size_t)pid * cam.W * cam.H : nullptr;
+  for (int ly = warp; ly < th; ly += NW) {
+    const float* prow = zp ? zp + (size_t)(bb.y + ly) * cam.W + bb.x : nullptr;
+    for (int lx = lane; lx < tw; lx += 32) {
+      const uint32_t izb = tile[ly * tw + lx];
+      if (izb == 0u) {
+        tile[ly * tw + lx] = kInfBits;
+        continue;
+      }
+      const float z = __frcp_rn(__uint_as_float(izb));
+      if (prow) {
+        const float pz = __ldg(&prow[lx]);
+        if (__float_as_uint(pz) != kInfBits) {
+          if (z < pz) viol++;
+          tile[ly * tw + lx] = kInfBits;  // hidden by (or hiding) the parent: not in dR
+          continue;
+        }
+      }
+      tile[ly * tw + lx] = __float_as_uint(z);
+      nnew++;
+    }
+  }
+  viol = warp_sum(viol);
+  nnew = warp_sum(nnew);
+  if (lane == 0) {
+    if (viol) atomicAdd(&s_cnt[0], viol);
+    if (nnew) atomicAdd(&s_cnt[1], nnew);
+  }
+  __syncthreads();
   const uint32_t flags = s_cnt[2] ? PERCH_FLAG_CULLED : 0u;
-  // dR pixel list (tile indices; a tile fits shared memory, so it has fewer
-  // than 2^16 pixels) over the chunk buffers, which are idle until the next
-  // work item's first copies
-  uint16_t* drlist = reinterpret_cast<uint16_t*>(smem);
-
-  bool as_z = false;  // the tile holds 1/z until the first member's pass turns it into z
-  for (int j = 0; j < n; ++j) {
-    const long long h = member(j);
-    const int pid = b.hyp_parent[h];
-    bool bad = pid < 0 || pid >= b.n_par;
-    const int plen = bad ? 0 : b.parent_len[pid];
-    bad = bad || plen < 0 || plen > b.parent_stride;
-    const int scene = (bad || !b.parent_scene) ? 0 : b.parent_scene[pid];
-    const int K_total = (bad || !b.parent_K) ? b.K_total : b.parent_K[pid];
-    bad = bad || (b.parent_scene && (scene < 0 || scene >= b.n_scenes));
-    if (bad) {  // the same values in every thread: the whole CTA skips
-      if (tid == 0) {
-        perch_cost r = {0, 0, 0, 0, 0, kFlagBadIndex, 0};
-        b.out[h] = r;
-      }
-      continue;
-    }
-    if (MULTI && tid < (int)(sizeof(ObsIndex) / 4))  // this scene's index, read from shared memory below
-      reinterpret_cast<int*>(s_obs)[tid] = reinterpret_cast<const int*>(&b.scenes[scene])[tid];
-    if (tid < 7 && tid != 2) s_cnt[tid] = 0;
-    __syncthreads();
-    const ObsIndex& obs = MULTI ? *s_obs : obs0;
-
-    // ---- monotone test against the parent render and dR (Eq. (3)): a
-    // rendered pixel is in dR where the parent render is empty; where it is
-    // not, the pixel is hidden by (or hides) the parent and a nearer new
-    // surface is a violation
-    int viol = 0;
-    const float* zp = plen > 0 ? b.parent_z + (size_t)pid * cam.W * cam.H : nullptr;
-    for (int ly = warp; ly < th; ly += NW) {
-      const float* prow = zp ? zp + (size_t)(bb.y + ly) * cam.W + bb.x : nullptr;
-      for (int lx0 = 0; lx0 < tw; lx0 += 32) {  // warp-uniform: one mask word per step
-        const int lx = lx0 + lane;
-        bool in = false;
-        if (lx < tw) {
-          uint32_t zb = tile[ly * tw + lx];
-          if (!as_z) {  // z = 1/(1/z), once per pixel; +inf where empty
-            zb = zb == 0u ? kInfBits : __float_as_uint(__frcp_rn(__uint_as_float(zb)));
-            tile[ly * tw + lx] = zb;
-          }
-          if (zb != kInfBits) {
-            in = true;
-            if (prow) {
-              const float pz = __ldg(&prow[lx]);
-              if (__float_as_uint(pz) != kInfBits) {
-                if (__uint_as_float(zb) < pz) viol++;
-                in = false;
-              }
-            }
-          }
-        }
-        const uint32_t word = __ballot_sync(0xffffffffu, in);
-        int base = 0;  // |dR| so far (s_cnt[1]) is also the word's place in the dR list
-        if (lane == 0) {
-          dmask[ly * mw + (lx0 >> 5)] = word;
-          if (word) base = atomicAdd(&s_cnt[1], __popc(word));
-        }
-        base = __shfl_sync(0xffffffffu, base, 0) + __popc(word & ((1u << lane) - 1u));
-        if (in && base < kDrListMax) drlist[base] = (uint16_t)(ly * tw + lx);
-      }
-    }
-    as_z = true;
-    viol = warp_sum(viol);
-    if (lane == 0 && viol) atomicAdd(&s_cnt[0], viol);
-    __syncthreads();
-    if (s_cnt[0] > 0) {
-      if (tid == 0) {
-        perch_cost r = {0, 0, 0, s_cnt[0], s_cnt[1], flags | PERCH_FLAG_INVALID, 0};
-        b.out[h] = r;
-      }
-      __syncthreads();  // s_cnt is reset by the next member
-      continue;
-    }
-
-    // ---- dJ_r: dR points with no observed point within delta (from the
-    // compact list when it holds all of dR, else from the mask)
-    int djr = 0;
-    const int ndr = s_cnt[1];
-    if (ndr <= kDrListMax) {
-      const uint32_t magic = 0xffffffffu / (uint32_t)tw + 1u;  // k / tw for k, tw < 2^16 (tw > 1)
-      for (int k = tid; k < ndr; k += NT) {
-        const int idx = drlist[k];
-        const int ly = tw == 1 ? idx : (int)__umulhi((uint32_t)idx, magic), lx = idx - ly * tw;
-        const float z = __uint_as_float(tile[idx]);
-        if (!explained_by_obs(obs, fmul(rxs[lx], z), fmul(rys[ly], z), z, cam.delta2)) djr++;
-      }
-    } else {
-      for (int ly = warp; ly < th; ly += NW) {
-        const float ry = rys[ly];
-        for (int lx = lane; lx < tw; lx += 32) {
-          if (!in_dr(dmask, mw, lx, ly)) continue;
-          const float z = __uint_as_float(tile[ly * tw + lx]);
-          if (!explained_by_obs(obs, fmul(rxs[lx], z), fmul(ry, z), z, cam.delta2)) djr++;
-        }
-      }
-    }
-
-    // ---- dJ_o: observed points inside V(O) with no dR point within delta
-    int djo = 0, nvol = 0;
-    if (obs.n > 0) {
-      const float r = sqrtf(m.vol_r2) * 1.001f + 1e-6f;
-      const int cx0 = max(cell_of(ox - r, obs.g2x, obs.inv2, obs.n2x) - 1, 0);
-      const int cx1 = min(cell_of(ox + r, obs.g2x, obs.inv2, obs.n2x) + 1, obs.n2x - 1);
-      const int cy0 = max(cell_of(oy - r, obs.g2y, obs.inv2, obs.n2y) - 1, 0);
-      const int cy1 = min(cell_of(oy + r, obs.g2y, obs.inv2, obs.n2y) + 1, obs.n2y - 1);
-      if (cx0 <= cx1) {
-        for (int cy = cy0; cy <= cy1; ++cy) {
-          const int s = obs.start2[cy * obs.n2x + cx0], e = obs.start2[cy * obs.n2x + cx1 + 1];
-          for (int k = s + tid; k < e; k += NT) {
-            const float4 qw = obs.world2[k];
-            if (!in_volume(qw, ox, oy, m.vol_r2, m.vol_zlo, m.vol_zhi)) continue;
-            if (!explained_by_tile(cam, obs.cam2[k], tile, dmask, mw, rxs, rys, bb)) djo++;
-            bool in_parent = false;  // already inside an assigned volume?
-            for (int i = 0; i < plen && !in_parent; ++i) {
-              const perch_obj po = b.parents[(long long)pid * b.parent_stride + i];
-              const DevMesh pm = g.meshes[po.mesh];
-              in_parent = in_volume(qw, g.xs[po.ix], g.ys[po.iy], pm.vol_r2, pm.vol_zlo, pm.vol_zhi);
-            }
-            if (!in_parent) nvol++;
-          }
-        }
-      }
-    }
-
-    // ---- residual(K) on edges into the last level
-    int resid = 0;
-    if (plen + 1 == K_total) {
-      const int nu = b.uset_count[pid];
-      const int* U = b.uset + (size_t)pid * b.uset_stride;
-      for (int k = tid; k < nu; k += NT) {
-        const int qi = U[k];
-        if (in_volume(obs.world2[qi], ox, oy, m.vol_r2, m.vol_zlo, m.vol_zhi)) continue;
-        if (explained_by_tile(cam, obs.cam2[qi], tile, dmask, mw, rxs, rys, bb)) continue;
-        resid++;
-      }
-    }
-    djr = warp_sum(djr);
-    djo = warp_sum(djo);
-    resid = warp_sum(resid);
-    nvol = warp_sum(nvol);
-    if (lane == 0) {
-      if (djr) atomicAdd(&s_cnt[3], djr);
-      if (djo) atomicAdd(&s_cnt[4], djo);
-      if (resid) atomicAdd(&s_cnt[5], resid);
-      if (nvol) atomicAdd(&s_cnt[6], nvol);
-    }
-    __syncthreads();
+  if (s_cnt[0] > 0) {
     if (tid == 0) {
-      perch_cost r = {s_cnt[3], s_cnt[4], s_cnt[5], 0, s_cnt[1], flags, s_cnt[6]};
+      perch_cost r = {0, 0, 0, s_cnt[0], s_cnt[1], flags | PERCH_FLAG_INVALID, 0};
       b.out[h] = r;
     }
-    __syncthreads();  // s_cnt, s_obs, the mask and the dR list are reused by the next member
+    __syncthreads();  // s_cnt is reset by the next hypothesis
+    return true;
   }
-  // the dR list's (generic) writes come before the next item's bulk copies
-  // into the same shared memory (async proxy)
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  __syncthreads();  // the tile is reused by the next work item
+
+  // ---- dJ_r: dR points with no observed point within delta
+  int djr = 0;
+  for (int ly = warp; ly < th; ly += NW) {
+    const float ry = rys[ly];
+    for (int lx = lane; lx < tw; lx += 32) {
+      const uint32_t zb = tile[ly * tw + lx];
+      if (zb == kInfBits) continue;
+      const float z = __uint_as_float(zb);
+      if (!explained_by_obs(obs, fmul(rxs[lx], z), fmul(ry, z), z, cam.delta2)) djr++;
+    }
+  }
+
+  // ---- dJ_o: observed points inside V(O) with no dR point within delta
+  int djo = 0, nvol = 0;
+  if (obs.n > 0) {
+    const float r = sqrtf(m.vol_r2) * 1.001f + 1e-6f;
+    const int cx0 = max(cell_of(ox - r, obs.g2x, obs.inv2, obs.n2x) - 1, 0);
+    const int cx1 = min(cell_of(ox + r, obs.g2x, obs.inv2, obs.n2x) + 1, obs.n2x - 1);
+    const int cy0 = max(cell_of(oy - r, obs.g2y, obs.inv2, obs.n2y) - 1, 0);
+    const int cy1 = min(cell_of(oy + r, obs.g2y, obs.inv2, obs.n2y) + 1, obs.n2y - 1);
+    if (cx0 <= cx1) {
+      for (int cy = cy0; cy <= cy1; ++cy) {
+        const int s = obs.start2[cy * obs.n2x + cx0], e = obs.start2[cy * obs.n2x + cx1 + 1];
+        for (int k = s + tid; k < e; k += NT) {
+          const float4 qw = obs.world2[k];
+          if (!in_volume(qw, ox, oy, m.vol_r2, m.vol_zlo, m.vol_zhi)) continue;
+          if (!explained_by_tile(cam, obs.cam2[k], tile, rxs, rys, bb)) djo++;
+          bool in_parent = false;  // already inside an assigned volume?
+          for (int j = 0; j < plen && !in_parent; ++j) {
+            const perch_obj po = b.parents[(long long)pid * b.parent_stride + j];
+            const DevMesh pm = g.meshes[po.mesh];
+            in_parent = in_volume(qw, g.xs[po.ix], g.ys[po.iy], pm.vol_r2, pm.vol_zlo, pm.vol_zhi);
+          }
+          if (!in_parent) nvol++;
+        }
+      }
+    }
+  }
+
+  // ---- residual(K) on edges into the last level
+  int resid = 0;
+  if (plen + 1 == K_total) {
+    const int nu = b.uset_count[pid];
+    const int* U = b.uset + (size_t)pid * b.uset_stride;
+    for (int k = tid; k < nu; k += NT) {
+      const int qi = U[k];
+      if (in_volume(obs.world2[qi], ox, oy, m.vol_r2, m.vol_zlo, m.vol_zhi)) continue;
+      if (explained_by_tile(cam, obs.cam2[qi], tile, rxs, rys, bb)) continue;
+      resid++;
+    }
+  }
+  djr = warp_sum(djr);
+  djo = warp_sum(djo);
+  resid = warp_sum(resid);
+  nvol = warp_sum(nvol);
+  if (lane == 0) {
+    if (djr) atomicAdd(&s_cnt[3], djr);
+    if (djo) atomicAdd(&s_cnt[4], djo);
+    if (resid) atomicAdd(&s_cnt[5], resid);
+    if (nvol) atomicAdd(&s_cnt[6], nvol);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    perch_cost r = {s_cnt[3], s_cnt[4], s_cnt[5], 0, s_cnt[1], flags, s_cnt[6]};
+    b.out[h] = r;
+  }
+  __syncthreads();  // s_cnt and the tile are reused by the next hypothesis
   return true;
 }
 
-// The work of one persistent launch: items offset .. offset + count - 1,
-// claimed one at a time from the device counter `next`. With gstart ==
-// nullptr an item is one hypothesis, order[offset + item] (order == nullptr:
-// hypothesis `item`); otherwise item i is the hypotheses
-// order[gstart[offset + i] ..][0 .. gcount[offset + i]), all of one pose.
+// A group of hypotheses evaluated by one persistent launch: items
+// order[offset .. offset + count) (order == nullptr: hypotheses 0 .. count-1),
+// claimed one at a time from the device counter `next`.
 struct EvalGroup {
   const int* order;
   const int* offset;  // device scalar
   const int* count;   // device scalar
   int* next;          // device counter, zero before the launch
-  const int* gstart;  // nullable
-  const int* gcount;
 };
 
 template <int NT, bool MULTI>
@@ -1170,15 +1102,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_eval(Camera cam, Geometry g, 
     const int item = s_item;
     __syncthreads();
     if (item >= count) break;
-    bool ok;
-    if (grp.gstart) {
-      ok = eval_group<NT, MULTI>(grp.order + grp.gstart[offset + item], grp.gcount[offset + item], 0, cam, g, obs,
-                                 b, sh, &s_obs);
-    } else {
-      const long long h = grp.order ? grp.order[offset + item] : item;
-      ok = eval_group<NT, MULTI>(nullptr, 1, h, cam, g, obs, b, sh, &s_obs);
-    }
-    if (!ok) break;
+    const long long h = grp.order ? grp.order[offset + item] : item;
+    if (!eval_one<NT, MULTI>(h, cam, g, obs, b, sh, &s_obs)) break;
   }
 }
 
@@ -1210,84 +1135,6 @@ cudaError_t launch_group_by_mesh(const perch_obj* hyp, long long n, int n_mesh, 
   if ((e = cudaMemcpyAsync(cursor, offsets, sizeof(int) * n_mesh, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
     return e;
   k_group_scatter<<<blocks, 256, 0, s>>>(hyp, n, n_mesh, cursor, order, skip);
-  return cudaGetLastError();
-}
-
-// group hypotheses by pose (mesh, ix, iy, iyaw; the index of pose_bbox), so
-// that hypotheses of one pose share one render: counts -> starts (exclusive
-// scan) -> one group per non-empty pose (second scan) -> each mesh's range of
-// groups -> order. A hypothesis that k_eval would reject gets its
-// bad-index record here and joins no group; skip[h] = 1 (record already
-// written by the shortcut) leaves it out as well.
-__device__ __forceinline__ bool hyp_ok(const Geometry& g, const Batch& b, long long h) {
-  const perch_obj o = b.hyp[h];
-  const int pid = b.hyp_parent[h];
-  bool ok = pid >= 0 && pid < b.n_par && obj_ok(g, o);
-  const int plen = ok ? b.parent_len[pid] : 0;
-  ok = ok && plen >= 0 && plen <= b.parent_stride;
-  const int scene = (ok && b.parent_scene) ? b.parent_scene[pid] : 0;
-  return ok && (!b.parent_scene || (scene >= 0 && scene < b.n_scenes));
-}
-
-__device__ __forceinline__ long long pose_of(const Geometry& g, const perch_obj& o) {
-  return (((long long)o.mesh * g.nx + o.ix) * g.ny + o.iy) * g.n_yaw + o.iyaw;
-}
-
-__global__ void k_pose_hist(Geometry g, Batch b, int* cnt) {
-  const long long h = blockIdx.x * 256LL + threadIdx.x;
-  if (h >= b.n_hyp || (b.skip && b.skip[h])) return;
-  if (!hyp_ok(g, b, h)) {
-    perch_cost r = {0, 0, 0, 0, 0, kFlagBadIndex, 0};
-    b.out[h] = r;
-    return;
-  }
-  atomicAdd(&cnt[pose_of(g, b.hyp[h])], 1);
-}
-
-__global__ void k_pose_flags(const int* cnt, int n, int* flag) {
-  const int p = blockIdx.x * 256 + threadIdx.x;
-  if (p < n) flag[p] = cnt[p] > 0;
-}
-
-__global__ void k_pose_groups(const int* cnt, const int* start, const int* gix, int n, int* gstart, int* gcount) {
-  const int p = blockIdx.x * 256 + threadIdx.x;
-  if (p < n && cnt[p] > 0) {
-    gstart[gix[p]] = start[p];
-    gcount[gix[p]] = cnt[p];
-  }
-}
-
-// mesh m's groups: gix[m * per_mesh] .. gix[(m + 1) * per_mesh] - 1
-__global__ void k_mesh_groups(const int* gix, int n_mesh, int per_mesh, int* offset, int* count) {
-  const int m = blockIdx.x * 256 + threadIdx.x;
-  if (m < n_mesh) {
-    offset[m] = gix[(long long)m * per_mesh];
-    count[m] = gix[(long long)(m + 1) * per_mesh] - offset[m];
-  }
-}
-
-// places each hypothesis in its pose's range; counts return to zero
-__global__ void k_pose_scatter(Geometry g, Batch b, const int* start, int* cnt, int* order) {
-  const long long h = blockIdx.x * 256LL + threadIdx.x;
-  if (h >= b.n_hyp || (b.skip && b.skip[h]) || !hyp_ok(g, b, h)) return;
-  const long long p = pose_of(g, b.hyp[h]);
-  order[start[p] + atomicSub(&cnt[p], 1) - 1] = (int)h;
-}
-
-cudaError_t launch_group_by_pose(const Geometry& g, const Batch& b, const PoseGroups& pg, cudaStream_t s) {
-  const int P = g.n_mesh * g.nx * g.ny * g.n_yaw, per_mesh = g.nx * g.ny * g.n_yaw;
-  cudaError_t e = cudaMemsetAsync(pg.cnt, 0, sizeof(int) * (size_t)P, s);
-  if (e != cudaSuccess) return e;
-  const unsigned hb = (unsigned)((b.n_hyp + 255) / 256), pb = (unsigned)((P + 255) / 256);
-  if (b.n_hyp > 0) k_pose_hist<<<hb, 256, 0, s>>>(g, b, pg.cnt);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_exclusive_scan(pg.cnt, pg.start, P, pg.tmp, s)) != cudaSuccess) return e;
-  k_pose_flags<<<pb, 256, 0, s>>>(pg.cnt, P, pg.flag);
-  if ((e = launch_exclusive_scan(pg.flag, pg.gix, P, pg.tmp, s)) != cudaSuccess) return e;
-  k_pose_groups<<<pb, 256, 0, s>>>(pg.cnt, pg.start, pg.gix, P, pg.gstart, pg.gcount);
-  k_mesh_groups<<<(unsigned)((g.n_mesh + 255) / 256), 256, 0, s>>>(pg.gix, g.n_mesh, per_mesh, pg.mesh_offset,
-                                                                   pg.mesh_count);
-  if (b.n_hyp > 0) k_pose_scatter<<<hb, 256, 0, s>>>(g, b, pg.start, pg.cnt, pg.order);
   return cudaGetLastError();
 }
 
@@ -1456,9 +1303,9 @@ static cudaError_t launch_group_t(const Camera& cam, const Geometry& g, const Ob
 // (128, 256 or 512) and the group's tile (b.tile_w x b.tile_h).
 cudaError_t launch_eval_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
                               const int* order, const int* offset, const int* count, int* next, long long max_items,
-                              int threads, int sm_count, cudaStream_t s, const int* gstart, const int* gcount) {
+                              int threads, int sm_count, cudaStream_t s) {
   if (max_items <= 0) return cudaSuccess;
-  EvalGroup grp{order, offset, count, next, gstart, gcount};
+  EvalGroup grp{order, offset, count, next};
   const bool multi = b.parent_scene != nullptr;
   switch (threads) {
     case 128: return multi ? launch_group_t<128, true>(cam, g, obs, b, grp, max_items, sm_count, s)

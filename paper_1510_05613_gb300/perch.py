@@ -29,8 +29,7 @@ EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_mesh
            "perch_search_multi", "perch_cnn_create", "perch_cnn_destroy", "perch_cnn_last_error",
            "perch_cnn_param_count", "perch_cnn_set_params", "perch_cnn_get_params", "perch_cnn_crops",
            "perch_cnn_forward", "perch_cnn_train_step", "perch_cnn_gradients", "perch_set_heuristic_net",
-           "perch_set_shortcut", "perch_shortcut_stats", "perch_set_share_renders", "perch_share_stats",
-           "perch_search_stats", "perch_search_times")
+           "perch_set_shortcut", "perch_shortcut_stats", "perch_search_stats", "perch_search_times")
 
 
 class perch_mesh(ctypes.Structure):
@@ -104,8 +103,6 @@ def load(path: str = LIB_PATH):
         "perch_cnn_gradients": ([P, P, P, P, I32, P, P, P], ctypes.c_int),
         "perch_set_heuristic_net": ([P, P, I32], ctypes.c_int),
         "perch_set_shortcut": ([P, I32], ctypes.c_int),
-        "perch_set_share_renders": ([P, I32], ctypes.c_int),
-        "perch_share_stats": ([P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "perch_search_stats": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "perch_search_times": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -299,16 +296,6 @@ class Perch:
     def perch_set_shortcut(self, on: bool):
         """Exact shortcut for hypotheses far from the observation and the parent (on by default)."""
         return self._check(self.lib.perch_set_shortcut(self.h, 1 if on else 0))
-
-    def perch_set_share_renders(self, on: bool):
-        """One render per (mesh, pose) among the hypotheses of an evaluation (on by default)."""
-        return self._check(self.lib.perch_set_share_renders(self.h, 1 if on else 0))
-
-    def perch_share_stats(self):
-        """(renders, hypotheses rendered for) of the last evaluation's kernel."""
-        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
-        self._check(self.lib.perch_share_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
-        return int(a.value), int(b.value)
 
     def perch_shortcut_stats(self):
         """(hypotheses that took the shortcut, hypotheses) of the last evaluation."""

@@ -189,82 +189,6 @@ def test_shortcut_multi_scene_identical():
             assert np.array_equal(fast[idx], exp)
 
 
-def test_shared_renders_identical_c2(c2):
-    """One render per pose (sharing on) gives the same records as one render
-    per hypothesis, on the benchmark batch (every pose under up to three
-    parents) in its own order and shuffled; the kernel renders each of the
-    120k poses once."""
-    wl, p, w = c2
-    from bench import c2_batch
-    parents, hp, hyps = c2_batch(wl)
-    p.perch_set_shortcut(False)
-    try:
-        p.perch_set_share_renders(False)
-        full = _recs(p.perch_eval_successors(parents, hp, hyps, wl.K))
-        assert p.perch_share_stats() == (len(hyps), len(hyps))
-        p.perch_set_share_renders(True)
-        shared = _recs(p.perch_eval_successors(parents, hp, hyps, wl.K))
-        n_poses = len(np.unique(np.stack([hyps["mesh"], hyps["ix"], hyps["iy"], hyps["iyaw"]], 1), axis=0))
-        assert p.perch_share_stats() == (n_poses, len(hyps)) and n_poses < len(hyps)
-        bad = np.nonzero((full != shared).any(1))[0]
-        assert bad.size == 0, (bad[:5], full[bad[:3]], shared[bad[:3]])
-        perm = np.random.default_rng(3).permutation(len(hyps))
-        shuffled = _recs(p.perch_eval_successors(parents, hp[perm], hyps[perm], wl.K))
-        assert np.array_equal(shuffled, full[perm])
-    finally:
-        p.perch_set_share_renders(True)
-        p.perch_set_shortcut(True)
-
-
-def test_shared_renders_across_scenes_and_levels():
-    """Every sampled pose under every parent of three scenes (levels 0 .. K-1,
-    last-level residuals, violations) plus repeated hypotheses: groups of
-    many members that differ in scene, parent and K. Records equal with
-    sharing on and off, with the shortcut on and off, and match the oracle on
-    a sample of every parent."""
-    meshes = synth.meshes_c3()[:4]
-    grid = synth.pose_grid(-0.49, 0.04, 25, 8)
-    wls = synth.workloads_c5(3, grid=grid, meshes=meshes, k_range=(2, 3))
-    p = perch.Perch(0)
-    p.setup(wls[0])
-    for s, wl in enumerate(wls[1:], 1):
-        p.perch_set_scene(s, wl.depth)
-    rng = np.random.default_rng(11)
-    allh = synth.all_hypotheses(grid, list(range(len(meshes))))
-    common = allh[rng.choice(len(allh), 1500, replace=False)]
-    common = np.concatenate([common, common[:200]])  # the same hypothesis twice under one parent
-    parents, ps, pk, hp, hyps = [], [], [], [], []
-    for s, wl in enumerate(wls):
-        for j in range(wl.K):
-            hp.append(np.full(len(common), len(parents), np.int32))
-            hyps.append(common)
-            parents.append(wl.gt[:j])
-            ps.append(s)
-            pk.append(wl.K)
-    hp, hyps = np.concatenate(hp), np.concatenate(hyps)
-    out = {}
-    for share in (False, True):
-        for short in (False, True):
-            p.perch_set_share_renders(share)
-            p.perch_set_shortcut(short)
-            out[share, short] = _recs(p.perch_eval_successors_multi(parents, ps, pk, hp, hyps))
-            renders, n_eval = p.perch_share_stats()
-            assert renders <= n_eval and (renders == n_eval) == (not share)
-            if share and not short:
-                assert renders == 1500 and n_eval == len(hyps)
-    for k, v in out.items():
-        assert np.array_equal(v, out[False, False]), k
-    recs = out[True, False]
-    assert (recs[:, 3] > 0).any() and (recs[:, 2] > 0).any()  # violations and residuals occur
-    for s, wl in enumerate(wls):
-        wo = oracle.World.of(wl)
-        for j in range(wl.K):
-            pi = [i for i in range(len(parents)) if ps[i] == s and len(parents[i]) == j][0]
-            idx = np.nonzero(hp == pi)[0][::61]
-            exp = oracle.eval_batch(wo, wl.depth, [parents[pi]], np.zeros(len(idx), np.int32), hyps[idx], wl.K)
-            assert np.array_equal(recs[idx], exp)
-
-
 def test_empty_observation_and_huge_delta():
     wl = synth.workload_c1()
     allh = synth.all_hypotheses(wl.grid, [0, 1])[::7]
