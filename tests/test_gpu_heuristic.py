@@ -97,3 +97,22 @@ def test_search_statistics_account_for_the_learned_queue(setup):
     assert ev > 0.0 and ab > 0.0 and sel > 0.0
     p.perch_search_multi(te, ms, batch_states=2, w=1.0, heuristics=0)
     assert p.perch_search_stats()[1:] == (0, 0)
+
+
+def test_learned_queue_expands_fewer_states_than_plain_search(setup):
+    """What the learned queue adds to the method without it (plain
+    uniform-cost search, the paper's exact search): on the held-out scenes
+    Focal-MHA* with the anchor and the learned queue (w = 2) never expands
+    more states than plain search, expands fewer in all, and returns a scene
+    within w times the optimum. (On these scenes the same search with the
+    untrained network expands the same states: the queue's depth-first pool
+    makes the gain, the network's ranking inside it does not change it.)"""
+    p, net, test_sc, te, *_ = setup
+    ms = [wl.mesh_multiset for wl in test_sc]
+    p.perch_set_heuristic_net(net, 8)
+    plain = p.perch_search_multi(te, ms, batch_states=2, w=1.0, heuristics=0)
+    learned = p.perch_search_multi(te, ms, batch_states=2, w=2.0, heuristics=4)
+    for a, b in zip(plain, learned):
+        assert a["proven_optimal"] and b["cost"] <= 2.0 * a["cost"] + 1e-9
+        assert b["expansions"] <= a["expansions"]
+    assert sum(b["expansions"] for b in learned) < sum(a["expansions"] for a in plain)
