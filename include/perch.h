@@ -359,6 +359,19 @@ int perch_cnn_crops(perch_ctx* ctx, const perch_obj* parents, int32_t parent_str
                     const int32_t* parent_scene, int32_t n_par, const int32_t* hyp_parent, const perch_obj* hyp,
                     int64_t n_hyp, uint16_t* crops, int32_t* onehot);
 
+/* Tensor-core path of the forward 3x3 convolutions of layers 2-4 (the
+ * implicit-im2col GEMMs): 0 = warp-level mma.sync (the default), 1 = tcgen05
+ * MMAs into a tensor-memory accumulator (one 128-row x C_out tile per CTA,
+ * operands staged in shared memory by cp.async). Both accumulate BF16
+ * products in FP32 and apply bias + ReLU before rounding to BF16; sums are
+ * taken in a different order, so outputs may differ in the last BF16 bit.
+ * The backward pass always uses mma.sync. PERCH_E_ARG for another value. */
+int perch_cnn_set_tensor_path(perch_cnn* net, int32_t path);
+
+/* The current tensor path and whether a bounded wait of the tcgen05 kernel
+ * ever gave up (its tile then keeps stale outputs). Waits for the stream. */
+int perch_cnn_tensor_status(perch_cnn* net, int32_t* path, int32_t* waits_gave_up);
+
 /* Predictions for n crops (device arrays), asynchronous on the network's
  * stream. */
 int perch_cnn_forward(perch_cnn* net, const uint16_t* crops, const int32_t* onehot, int64_t n, float* pred);

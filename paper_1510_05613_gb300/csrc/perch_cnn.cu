@@ -349,6 +349,203 @@ cudaError_t gemm(GemmArgs p, int splits, cudaStream_t s) {
   return gemm_bn<128, EPI, AK, BKC, CONV>(p, splits, s);
 }
 
+// ------------------------------------------------- tcgen05 convolution
+// Forward 3x3 convolution with implicit im2col (layers 2-4) on the
+// fifth-generation tensor cores: C[M x N] = A B^T, A the im2col rows of the
+// NHWC input (conv_src), B the weights [N][K]. One CTA of 256 threads owns a
+// 128-row tile and all N (64 or 128) columns; its FP32 accumulator lives in
+// tensor memory (N columns, lanes = rows). K advances BK columns per step
+// through a ring of S shared-memory stages filled by cp.async in the
+// canonical no-swizzle K-major layout: core matrices of 8 rows x 16 bytes,
+// the K-adjacent ones 128 bytes apart, the row-adjacent ones BK / 8 x 128
+// bytes apart. One thread issues the step's BK / 16 m128 nN k16 MMAs and
+// commits them to the stage's mbarrier, which frees the stage for the copy
+// of step + S. The epilogue reads the accumulator back with tcgen05.ld (warp
+// w: rows 32 (w mod 4) .. + 31, columns of half w / 4), adds the bias,
+// applies ReLU and stores bfloat16 rows (GemmArgs addressing). Every wait is
+// bounded; a wait that gives up sets *err and skips the stores, and the
+// tensor memory is freed all the same.
+constexpr int kTcRows = 128, kTcThreads = 256;
+
+template <int BK>
+__device__ __forceinline__ uint32_t tc_canon(int r, int kc) {  // (row r, 16-byte chunk kc) in a stage
+  return (uint32_t)((r >> 3) * (BK / 8) * 128 + kc * 128 + (r & 7) * 16);
+}
+// shared-memory matrix descriptor: start address, leading (K) byte offset
+// 128, stride (row-group) byte offset, descriptor version 1, no swizzle
+template <int BK>
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)((BK / 8) * 128 >> 4) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M = 128, N
+template <int N>
+__device__ __forceinline__ uint32_t tc_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ uint64_t tc_now() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// wait for the phase of the given parity: bounded by polls and by 2 s
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = tc_now();
+  for (int i = 0; i < (1 << 22); ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((i & 255) == 255 && tc_now() - t0 > 2000000000ull) break;
+  }
+  return false;
+}
+
+template <int N, int BK, int S>
+__global__ void __launch_bounds__(kTcThreads) k_conv_tc(GemmArgs p, int* err) {
+  static_assert(N == 64 || N == 128, "N must be 64 or 128");
+  static_assert(BK % 16 == 0, "BK must be a multiple of 16");
+  constexpr int CH = BK / 8, A_BYTES = kTcRows * BK * 2, STAGE = A_BYTES + N * BK * 2;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar[S];
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kTcRows, nk = p.K / BK;
+  const uint32_t sbase = smem_addr(smem);
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) tc_mbar_init(&bar[s]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {  // N columns of tensor memory for the accumulator
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                 "r"(N)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  auto load = [&](int ks) {  // this thread's share of step ks's A and B chunks
+    const uint32_t a = sbase + (uint32_t)((ks % S) * STAGE), b = a + A_BYTES;
+    const int k0 = ks * BK;
+    for (int i = tid; i < kTcRows * CH; i += kTcThreads) {
+      const int r = i / CH, kc = i % CH, m = m0 + r;
+      const bf16* src = m < p.M ? conv_src(p, p.A, m, k0 + 8 * kc) : nullptr;
+      cp_async16(a + tc_canon<BK>(r, kc), src ? src : p.A, src != nullptr);
+    }
+    for (int i = tid; i < N * CH; i += kTcThreads) {
+      const int n = i / CH, kc = i % CH;
+      cp_async16(b + tc_canon<BK>(n, kc), p.B + (long long)n * p.ldb + k0 + 8 * kc, true);
+    }
+  };
+
+  for (int ks = 0; ks < S - 1; ++ks) {
+    if (ks < nk) load(ks);
+    cp_commit();
+  }
+  bool ok = true;
+  int last = -1;  // last step whose MMAs were issued (the same in every thread)
+  for (int ks = 0; ks < nk; ++ks) {
+    const int kl = ks + S - 1;  // the step loaded now, into the stage step ks - 1 used
+    if (kl < nk) {
+      if (kl >= S) ok = ok && tc_wait(&bar[kl % S], (uint32_t)(((kl - S) / S) & 1));
+      if (ok) load(kl);
+    }
+    cp_commit();
+    cp_wait<S - 1>();  // this thread's copies of step ks have landed
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+    ok = __syncthreads_and(ok);
+    if (ok) last = ks;
+    if (ok && tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a = sbase + (uint32_t)((ks % S) * STAGE), b = a + A_BYTES;
+      for (int j = 0; j < BK / 16; ++j) {
+        const uint64_t ad = tc_desc<BK>(a + 256 * j), bd = tc_desc<BK>(b + 256 * j);
+        const uint32_t acc = (ks | j) != 0;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(tc_idesc<N>()), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_addr(&bar[ks % S]))
+                   : "memory");
+    }
+  }
+  cp_wait<0>();
+  // the last commit covers every MMA before it; wait for it (bounded) even
+  // after a failure, so that no MMA still writes the tensor memory freed below
+  if (last >= 0 && !tc_wait(&bar[last % S], (uint32_t)((last / S) & 1))) ok = false;
+  ok = __syncthreads_and(ok && last == nk - 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int q = warp & 3, half = warp >> 2;  // TMEM lanes 32q .. 32q + 31, columns of this half
+  const int row = m0 + 32 * q + lane;
+  const long long off = (long long)(row / p.grp) * p.ldg + (long long)(row % p.grp) * p.ldc;
+  if (ok) {
+    for (int c0 = half * (N / 2); c0 < (half + 1) * (N / 2); c0 += 16) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < p.M) {
+        uint32_t o[8];
+        for (int e = 0; e < 8; ++e) {
+          const float x0 = fmaxf(__uint_as_float(v[2 * e]) + p.bias[c0 + 2 * e], 0.0f);
+          const float x1 = fmaxf(__uint_as_float(v[2 * e + 1]) + p.bias[c0 + 2 * e + 1], 0.0f);
+          const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+          o[e] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(p.Cb + off + c0);
+        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(N) : "memory");
+}
+
+template <int N, int BK, int S>
+cudaError_t conv_tc_t(const GemmArgs& p, int* err, cudaStream_t s) {
+  constexpr int smem = S * (kTcRows + N) * BK * 2;
+  cudaError_t e = cudaFuncSetAttribute(k_conv_tc<N, BK, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_conv_tc<N, BK, S><<<(unsigned)((p.M + kTcRows - 1) / kTcRows), kTcThreads, smem, s>>>(p, err);
+  return cudaGetLastError();
+}
+
+// C = relu(A B^T + bias) for one implicit-im2col convolution layer on the
+// tcgen05 path (N = 64 or 128, K a multiple of 32, 8-channel chunks). Steps
+// of 64 columns where K allows, else 32.
+cudaError_t conv_tc(GemmArgs p, int* err, cudaStream_t s) {
+  if (p.grp <= 0) {
+    p.grp = 1 << 30;
+    p.ldg = 0;
+  }
+  if ((p.N != 64 && p.N != 128) || p.K % 32 || p.lg_c < 3 || p.ldc % 8 || p.ldg % 8) return cudaErrorInvalidValue;
+  const bool k64 = p.K % 64 == 0;
+  if (p.N == 64) return k64 ? conv_tc_t<64, 64, 4>(p, err, s) : conv_tc_t<64, 32, 4>(p, err, s);
+  return k64 ? conv_tc_t<128, 64, 3>(p, err, s) : conv_tc_t<128, 32, 4>(p, err, s);
+}
+
 int ilog2(int v) {
   int l = 0;
   while ((1 << l) < v) ++l;
@@ -653,6 +850,10 @@ struct perch_cnn {
   DevBuf col[kConvs], act[kConvs], feat, h1, err_buf, pred_buf, loss_buf;
   DevBuf dz1, dfeat, dz, dcol, part, bpart;
   bool params_set = false;
+  // forward 3x3 convolutions 2-4 on tcgen05 (else mma.sync); tc_err: the
+  // tcgen05 kernel's wait-gave-up flag (device int)
+  bool tensor_tc = false;
+  DevBuf tc_err;
 
   int fail(int code, const char* fmt, ...) {
     char buf[512];
@@ -671,7 +872,7 @@ struct perch_cnn {
   }
   std::vector<DevBuf*> buffers() {
     std::vector<DevBuf*> v = {&master, &grad, &adam_m, &adam_v, &w16, &feat, &h1, &err_buf, &pred_buf,
-                              &loss_buf, &dz1, &dfeat, &dz, &dcol, &part, &bpart};
+                              &loss_buf, &dz1, &dfeat, &dz, &dcol, &part, &bpart, &tc_err};
     for (int l = 0; l < kConvs; ++l) {
       v.push_back(&col[l]);
       v.push_back(&act[l]);
@@ -801,6 +1002,8 @@ int perch_cnn::forward(const bf16* crops, const int32_t* onehot, int n, float* p
     }
     if (l == 0)
       CKN(gemm<EPI_BIAS_RELU>(p, 1, stream), "conv gemm");
+    else if (tensor_tc)
+      CKN(conv_tc(p, tc_err.as<int>(), stream), "conv tcgen05");
     else
       CKN((gemm<EPI_BIAS_RELU, true, true, 1>(p, 1, stream)), "conv gemm");
     x = l < kConvs - 1 ? act[l].as<bf16>() : nullptr;
@@ -1012,7 +1215,8 @@ int perch_cnn_create(perch_cnn** out, int device, void* cuda_stream, int32_t n_o
   }
   const size_t bytes = 4 * (size_t)net->n_total;
   bool ok = net->master.ensure(bytes) == cudaSuccess && net->grad.ensure(bytes) == cudaSuccess &&
-            net->adam_m.ensure(bytes) == cudaSuccess && net->adam_v.ensure(bytes) == cudaSuccess;
+            net->adam_m.ensure(bytes) == cudaSuccess && net->adam_v.ensure(bytes) == cudaSuccess &&
+            net->tc_err.ensure(16) == cudaSuccess && cudaMemsetAsync(net->tc_err.p, 0, 16, net->stream) == cudaSuccess;
   ok = ok && cudaMemsetAsync(net->master.p, 0, bytes, net->stream) == cudaSuccess &&
        cudaMemsetAsync(net->grad.p, 0, bytes, net->stream) == cudaSuccess &&
        cudaMemsetAsync(net->adam_m.p, 0, bytes, net->stream) == cudaSuccess &&
@@ -1040,6 +1244,26 @@ int perch_cnn_destroy(perch_cnn* net) {
 }
 
 const char* perch_cnn_last_error(const perch_cnn* net) { return net ? net->err.c_str() : "null network"; }
+
+int perch_cnn_set_tensor_path(perch_cnn* net, int32_t path) {
+  if (!net) return PERCH_E_ARG;
+  if (path != 0 && path != 1) return net->fail(PERCH_E_ARG, "tensor path must be 0 (mma.sync) or 1 (tcgen05)");
+  net->tensor_tc = path == 1;
+  return PERCH_OK;
+}
+
+int perch_cnn_tensor_status(perch_cnn* net, int32_t* path, int32_t* waits_gave_up) {
+  if (!net) return PERCH_E_ARG;
+  if (cudaSetDevice(net->device) != cudaSuccess) return net->cuda(cudaGetLastError(), "cudaSetDevice");
+  int e = 0;
+  int rc = net->cuda(cudaStreamSynchronize(net->stream), "stream");
+  if (rc) return rc;
+  rc = net->cuda(cudaMemcpy(&e, net->tc_err.p, sizeof e, cudaMemcpyDeviceToHost), "read flag");
+  if (rc) return rc;
+  if (path) *path = net->tensor_tc ? 1 : 0;
+  if (waits_gave_up) *waits_gave_up = e;
+  return PERCH_OK;
+}
 
 int perch_cnn_param_count(const perch_cnn* net, int64_t* n) {
   if (!net || !n) return PERCH_E_ARG;

@@ -29,6 +29,7 @@ EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_mesh
            "perch_search_multi", "perch_cnn_create", "perch_cnn_destroy", "perch_cnn_last_error",
            "perch_cnn_param_count", "perch_cnn_set_params", "perch_cnn_get_params", "perch_cnn_crops",
            "perch_cnn_forward", "perch_cnn_train_step", "perch_cnn_gradients", "perch_set_heuristic_net",
+           "perch_cnn_set_tensor_path", "perch_cnn_tensor_status",
            "perch_set_shortcut", "perch_shortcut_stats", "perch_search_stats", "perch_search_times")
 
 
@@ -99,6 +100,8 @@ def load(path: str = LIB_PATH):
         "perch_cnn_get_params": ([P, P, I64], ctypes.c_int),
         "perch_cnn_crops": ([P, P, I32, P, P, I32, P, P, I64, P, P], ctypes.c_int),
         "perch_cnn_forward": ([P, P, P, I64, P], ctypes.c_int),
+        "perch_cnn_set_tensor_path": ([P, I32], ctypes.c_int),
+        "perch_cnn_tensor_status": ([P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "perch_cnn_train_step": ([P, P, P, P, I32, F, P], ctypes.c_int),
         "perch_cnn_gradients": ([P, P, P, P, I32, P, P, P], ctypes.c_int),
         "perch_set_heuristic_net": ([P, P, I32], ctypes.c_int),
@@ -387,6 +390,16 @@ class PerchCNN:
         p = np.empty(self.n_params, np.float32)
         self._check(self.lib.perch_cnn_get_params(self.h, p.ctypes.data, p.size))
         return p
+
+    def perch_cnn_set_tensor_path(self, path: int):
+        """0: mma.sync convolutions (default); 1: tcgen05 for the forward 3x3 convolutions 2-4."""
+        self._check(self.lib.perch_cnn_set_tensor_path(self.h, int(path)))
+
+    def perch_cnn_tensor_status(self):
+        """(tensor path, 1 if a bounded wait of the tcgen05 kernel gave up)."""
+        a, b = ctypes.c_int32(0), ctypes.c_int32(0)
+        self._check(self.lib.perch_cnn_tensor_status(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
 
     def perch_cnn_forward(self, crops, onehot):
         import torch

@@ -154,3 +154,30 @@ def test_training_reduces_the_loss(c1):
         hist.append(float(loss.item()))
     assert all(np.isfinite(hist))
     assert hist[-1] < 0.3 * hist[0], hist[::10]
+
+
+@pytest.mark.parametrize("n,max_batch", [(77, 64), (256, 256)])
+def test_tcgen05_forward_matches_mma_sync_and_oracle(c1, n, max_batch):
+    """The forward 3x3 convolutions 2-4 on tcgen05 (FP32 accumulator in tensor
+    memory) against the mma.sync path and the oracle, on a ragged batch (row
+    tiles of 128 that end inside the batch) and a full one. Both tensor paths
+    round the same FP32 sums to bfloat16 after bias and ReLU, in different
+    summation orders: predictions agree within the bfloat16 tolerance of the
+    oracle comparison, and no bounded wait of the tcgen05 kernel gives up."""
+    wl, p, w = c1
+    n_onehot = len(wl.meshes) * wl.grid.n_yaw
+    hyps = _hyps_c1(wl, n, 12 + n)
+    crops, onehot, x, idx = _crops_both(wl, p, w, wl.gt[:1], hyps)
+    params = _params(n_onehot, 13)
+    net = _net_with(params, n_onehot, max_batch=max_batch)
+    ref = net.perch_cnn_forward(crops, onehot).cpu().numpy()
+    net.perch_cnn_set_tensor_path(1)
+    got = net.perch_cnn_forward(crops, onehot).cpu().numpy()
+    assert net.perch_cnn_tensor_status() == (1, 0)
+    ep, _ = cnn.forward(params, x, cnn.onehot(idx, n_onehot), bf16=True)
+    scale = max(1.0, float(np.max(np.abs(ep))))
+    assert np.all(np.isfinite(got))
+    assert np.max(np.abs(got - ep)) < 2e-2 * scale
+    assert np.max(np.abs(got - ref)) < 2e-2 * scale
+    with pytest.raises(perch.PerchError):
+        net.perch_cnn_set_tensor_path(2)
