@@ -607,18 +607,27 @@ def run_cnn(args):
     big, oh = crops.repeat(F // B, 1, 1, 1).contiguous(), onehot.repeat(F // B).contiguous()
     pred = torch.empty(F, device="cuda")
     torch.cuda.synchronize()
-    fwd = []
-    with torch.cuda.stream(stream):
-        for k in range(3 + args.steps):
-            flush.fill_(k)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            net.lib.perch_cnn_forward(net.h, big.data_ptr(), oh.data_ptr(), F, pred.data_ptr())
-            e1.record(stream)
-            e1.synchronize()
-            if k >= 3:
-                fwd.append(e0.elapsed_time(e1))
-    fwd_ms = statistics.mean(fwd)
+    def time_forward():
+        fwd = []
+        with torch.cuda.stream(stream):
+            for k in range(3 + args.steps):
+                flush.fill_(k)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                net.lib.perch_cnn_forward(net.h, big.data_ptr(), oh.data_ptr(), F, pred.data_ptr())
+                e1.record(stream)
+                e1.synchronize()
+                if k >= 3:
+                    fwd.append(e0.elapsed_time(e1))
+        return statistics.mean(fwd)
+
+    fwd_ms = time_forward()
+    ref_pred = pred.clone()
+    net.perch_cnn_set_tensor_path(1)  # convolutions 2-4 on tcgen05
+    tc_ms = time_forward()
+    tc_status = net.perch_cnn_tensor_status()
+    tc_dev = float((pred - ref_pred).abs().max())
+    net.perch_cnn_set_tensor_path(0)
     peaks = _measured_peaks()
     peak = peaks.get("bf16_tflops") or 1900.0
     achieved = B * CNN_TRAIN_FLOP_PER_CROP / step_ms / 1e9
@@ -635,6 +644,10 @@ def run_cnn(args):
                          "peak_from": "bf16_tflops (burst cuBLAS) of MEASURED_PEAKS.json"},
             "forward": {"batch": F, "ms": fwd_ms, "crops_per_s": F / fwd_ms * 1e3,
                         "tflops": F * CNN_FWD_FLOP_PER_CROP / fwd_ms / 1e9},
+            "forward_tcgen05": {"batch": F, "ms": tc_ms, "crops_per_s": F / tc_ms * 1e3,
+                                "tflops": F * CNN_FWD_FLOP_PER_CROP / tc_ms / 1e9,
+                                "max_abs_diff_vs_mma_sync": tc_dev, "waits_gave_up": tc_status[1],
+                                "meaning": "forward with convolutions 2-4 on tcgen05 (tensor-memory accumulator)"},
             "gpu_launches": None, "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)
     return 0
