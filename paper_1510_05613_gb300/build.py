@@ -32,7 +32,7 @@ def _nvcc() -> str:
 
 def _flags():
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "--expt-relaxed-constexpr",
-                   "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math",
+                   "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math,-fopenmp",
                    "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 
@@ -56,7 +56,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
+    r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lgomp"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

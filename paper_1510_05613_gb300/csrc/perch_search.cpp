@@ -27,6 +27,7 @@
 // estimate with s' itself as the parent (its z-buffer in the crop). States are
 // scored once, lazily, in one batch across scenes.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -40,6 +41,9 @@ namespace {
 using Key = std::vector<uint64_t>;
 using Clock = std::chrono::steady_clock;
 constexpr int64_t kInf = std::numeric_limits<int64_t>::max();
+// batches of at least this many hypotheses are built and absorbed by host
+// threads (OpenMP), one expanded state or one scene per task
+constexpr size_t kParallelMin = 65536;
 
 uint64_t pack(const perch_obj& o) {
   return ((uint64_t)o.mesh << 48) | ((uint64_t)(uint16_t)o.ix << 32) | ((uint64_t)(uint16_t)o.iy << 16) |
@@ -548,6 +552,8 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
   std::vector<perch_cost> out;
   std::vector<Work> work;
   std::vector<int> popped;
+  std::vector<std::vector<int>> rem, by_scene;  // per work item: remaining types; per scene slot: work items
+  std::vector<int> slots;
   int64_t expansions = 0;
   size_t rr = 0;  // round-robin start over scenes
   while (true) {
@@ -603,26 +609,35 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
     plen.assign(work.size(), 0);
     pscene.assign(work.size(), 0);
     pK.assign(work.size(), 1);
-    hyps.clear();
-    hparent.clear();
+    // every pose of every remaining type, per expanded state: offsets first,
+    // then the (independent) per-state fills in parallel
     std::vector<size_t> hbeg(work.size() + 1, 0);
+    rem.resize(work.size());
+    const size_t poses = (size_t)ctx->nx * ctx->ny * ctx->n_yaw;
     for (size_t w = 0; w < work.size(); ++w) {
-      hbeg[w] = hyps.size();
       const SceneSearch& s = ss[work[w].scene_slot];
       const Key key = s.key_of(work[w].state);
       plen[w] = (int32_t)key.size();
       pscene[w] = s.scene;
       pK[w] = s.K;
       for (size_t j = 0; j < key.size(); ++j) parents[w * stride + j] = unpack(key[j]);
-      for (int m : s.remaining(key))
-        for (int ix = 0; ix < ctx->nx; ++ix)
-          for (int iy = 0; iy < ctx->ny; ++iy)
-            for (int k = 0; k < ctx->n_yaw; ++k) {
-              hyps.push_back(perch_obj{(uint16_t)m, (uint16_t)k, (int16_t)ix, (int16_t)iy});
-              hparent.push_back((int32_t)w);
+      rem[w] = s.remaining(key);
+      hbeg[w + 1] = hbeg[w] + rem[w].size() * poses;
+    }
+    hyps.resize(hbeg[work.size()]);
+    hparent.resize(hbeg[work.size()]);
+    const int nx = ctx->nx, ny = ctx->ny, nyaw = ctx->n_yaw;
+#pragma omp parallel for schedule(dynamic, 1) if (hbeg[work.size()] >= kParallelMin)
+    for (long long w = 0; w < (long long)work.size(); ++w) {
+      size_t h = hbeg[w];
+      for (int m : rem[w])
+        for (int ix = 0; ix < nx; ++ix)
+          for (int iy = 0; iy < ny; ++iy)
+            for (int k = 0; k < nyaw; ++k, ++h) {
+              hyps[h] = perch_obj{(uint16_t)m, (uint16_t)k, (int16_t)ix, (int16_t)iy};
+              hparent[h] = (int32_t)w;
             }
     }
-    hbeg[work.size()] = hyps.size();
     out.resize(hyps.size());
     const auto te = Clock::now();
     ctx->search_host_seconds += std::chrono::duration<double>(te - tr).count();
@@ -636,19 +651,39 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
     const auto ta = Clock::now();
     ctx->search_eval_seconds += std::chrono::duration<double>(ta - te).count();
     expansions += (int64_t)work.size();
+    // Scenes share nothing, so each scene's expansions and records are taken
+    // by one thread, in batch order: per scene the same sequence as a single
+    // thread taking the whole batch (results do not depend on the threads).
+    for (auto& v : by_scene) v.clear();
+    by_scene.resize(ss.size());
+    slots.clear();
     for (size_t w = 0; w < work.size(); ++w) {
-      SceneSearch& s = ss[work[w].scene_slot];
-      s.expansions++;
-      if (s.heur & 4)
-        s.record_expansion(work[w].state, hyps.data() + hbeg[w], out.data() + hbeg[w],
-                           (long long)(hbeg[w + 1] - hbeg[w]));
+      std::vector<int>& v = by_scene[work[w].scene_slot];
+      if (v.empty()) slots.push_back(work[w].scene_slot);
+      v.push_back((int)w);
     }
-    for (size_t h = 0; h < hyps.size(); ++h) {
-      const Work& w = work[hparent[h]];
-      SceneSearch& s = ss[w.scene_slot];
-      s.successors++;
-      s.absorb(w.state, hyps[h], out[h]);
-    }
+    std::atomic<bool> failed{false};
+    auto absorb_scene = [&](int si) {
+      try {
+        SceneSearch& s = ss[si];
+        for (int w : by_scene[si]) {
+          s.expansions++;
+          if (s.heur & 4)
+            s.record_expansion(work[w].state, hyps.data() + hbeg[w], out.data() + hbeg[w],
+                               (long long)(hbeg[w + 1] - hbeg[w]));
+        }
+        for (int w : by_scene[si])
+          for (size_t h = hbeg[w]; h < hbeg[w + 1]; ++h) {
+            s.successors++;
+            s.absorb(work[w].state, hyps[h], out[h]);
+          }
+      } catch (...) {
+        failed = true;
+      }
+    };
+#pragma omp parallel for schedule(dynamic, 1) if (slots.size() > 1 && hyps.size() >= kParallelMin)
+    for (long long i = 0; i < (long long)slots.size(); ++i) absorb_scene(slots[i]);
+    if (failed) return ctx->fail(PERCH_E_OOM, "search: out of host memory while absorbing records");
     ctx->search_absorb_seconds += std::chrono::duration<double>(Clock::now() - ta).count();
   }
 }

@@ -420,3 +420,25 @@ def test_focal_mha_full_c1_fewer_expansions(c1):
     fast = p.perch_search(wl.mesh_multiset, w=3.0, heuristics=3, batch_states=4)
     assert exact["cost"] == cost and cost <= fast["cost"] <= 3 * cost
     assert fast["expansions"] <= exact["expansions"]
+
+
+@pytest.mark.parametrize("heur,w", [(0, 1.0), (3, 3.0)])
+def test_multi_scene_search_threads_do_not_change_results(heur, w):
+    """Scenes searched together (batches of >= 64k hypotheses, built and
+    absorbed by host threads, one scene per thread) give exactly the results
+    of each scene searched alone (small batches, one thread): the same cost,
+    scene, expansions and successors. Without a launch cap every scene
+    expands the same states per round either way."""
+    grid = synth.pose_grid(-0.48, 0.04, 25, 8)
+    wls = synth.workloads_c5(6, grid=grid, k_range=(3, 3))
+    p = perch.Perch(0)
+    p.setup(wls[0])
+    for s, wl in enumerate(wls[1:], 1):
+        p.perch_set_scene(s, wl.depth)
+    ids, ms = list(range(len(wls))), [wl.mesh_multiset for wl in wls]
+    joint = p.perch_search_multi(ids, ms, batch_states=2, w=w, heuristics=heur)
+    assert len(wls) * 3 * grid.n_poses >= 65536  # the root batch alone engages the threads
+    for sid, m, r in zip(ids, ms, joint):
+        solo = p.perch_search_multi([sid], [m], batch_states=2, w=w, heuristics=heur)[0]
+        for k in ("cost", "key", "expansions", "successors", "proven_optimal"):
+            assert solo[k] == r[k], (sid, k, solo[k], r[k])
