@@ -219,7 +219,8 @@ def run_reference(args):
     import oracle
     w = oracle.World.of(wl)
     threads = oracle.max_threads()
-    per = max(threads * 2, 32)  # bounded sample per step
+    # bounded sample per step, large enough to keep every thread busy
+    per = args.ref_sample if args.ref_sample > 0 else 128 * threads
     rng = np.random.default_rng(1)
     times = []
     for s in range(args.warmup + args.steps):
@@ -781,6 +782,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0, help="fix the CTA width (128/256/512) instead of autotuning")
     ap.add_argument("--tune-sample", type=int, default=8192, help="hypotheses per mesh the autotuner times")
     ap.add_argument("--max-hyps", type=int, default=0, help="evenly subsample the batch (profiling case)")
+    ap.add_argument("--ref-sample", type=int, default=0,
+                    help="--impl reference: hypotheses per step (default 128 per host thread)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the evaluation directly instead of replaying its CUDA graph (same kernels)")
     ap.add_argument("--scenes", type=int, default=64, help="c5: number of scenes")
