@@ -183,12 +183,13 @@ def _measured_peaks():
         return {}
 
 
-def cpu_baseline(wl, parents, hp, hyps, target_s: float = 12.0, seed: int = 0):
-    """The oracle as it stands on the host cores, on a bounded random sample
-    of the same batch (sample grown until it takes about target_s)."""
+def cpu_baseline(wl, parents, hp, hyps, target_s: float = 12.0, seed: int = 0, threads: int = 0):
+    """The oracle as it stands on the host cores (threads = 0: all of them),
+    on a bounded random sample of the same batch (sample grown until it
+    takes about target_s)."""
     import oracle
     w = oracle.World.of(wl)
-    threads = oracle.max_threads()
+    threads = threads if threads > 0 else oracle.max_threads()
     rng = np.random.default_rng(seed)
     order = rng.permutation(len(hyps))
     n = max(threads, 16)
@@ -243,6 +244,33 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def c1_time_to_optimum(threads: int):
+    """Time to the optimal scene on the 160x120 two-object workload, GPU
+    search (warm, second run) beside the oracle's exact uniform-cost search
+    on the host cores; both must return the same cost and scene."""
+    try:
+        import oracle
+        from oracle import search
+        from paper_1510_05613_gb300 import perch
+        wl = synth.workload_c1()
+        p = perch.Perch(0)
+        p.setup(wl)
+        p.perch_search(wl.mesh_multiset, batch_states=16)
+        r = p.perch_search(wl.mesh_multiset, batch_states=16)
+        p.close()
+        w = oracle.World.of(wl)
+        t0 = time.perf_counter()
+        cost, key, expansions = search.uniform_cost_search(w, wl.depth, wl.grid, wl.mesh_multiset, threads=threads)
+        oracle_s = time.perf_counter() - t0
+        return {"gpu_s": r["seconds"], "oracle_s": oracle_s, "oracle_cores": threads,
+                "cost": r["cost"], "proven_optimal": r["proven_optimal"],
+                "same_cost_and_scene": (r["cost"], r["key"]) == (cost, key),
+                "expansions": {"gpu": r["expansions"], "oracle": expansions},
+                "workload": "160x120 fx=140, box + cylinder (1k/2k triangles), 10x10x8 poses, K=2, delta 1 cm"}
+    except Exception as e:  # reported, never fatal to the headline line
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def run_ours(args):
@@ -392,6 +420,9 @@ def run_ours(args):
     base = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(wl, parents, hp, hyps, target_s=args.cpu_seconds)
+        one = cpu_baseline(wl, parents, hp, hyps, target_s=args.cpu_seconds / 4, seed=1, threads=1)
+        base["single_core"] = {"value": one["value"], "unit": one["unit"], "sample": one["sample"]}
+        base["time_to_optimum_c1"] = c1_time_to_optimum(base["cores"])
 
     if rank == 0:
         cl = clocks.summary()
