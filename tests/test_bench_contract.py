@@ -27,3 +27,26 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
     assert "24-hypothesis sample" in d["config"]["workload"]
+
+
+def test_cpu_baseline_leg_on_the_small_workload():
+    """The bench's cpu_baseline leg: the oracle timed on a bounded sample on
+    all host threads and on one, with the fields the JSON line carries; the
+    C1 time-to-optimum leg reports an error entry, never an exception, where
+    no GPU is present."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1510_05613_gb300 import synth
+    wl = synth.workload_c1()
+    hyps = synth.all_hypotheses(wl.grid, [0, 1])[::50]
+    parents = [wl.gt[:0]]
+    hp = __import__("numpy").zeros(len(hyps), "int32")
+    for threads in (0, 1):
+        b = bench.cpu_baseline(wl, parents, hp, hyps, target_s=0.2, threads=threads)
+        assert b["kind"] == "oracle" and b["value"] > 0 and b["unit"] == bench.UNIT
+        assert b["cores"] >= 1 and (threads == 0 or b["cores"] == 1)
+        assert f"{len(hyps)} hypotheses of the batch" in b["sample"]
+    import torch
+    if not torch.cuda.is_available():
+        r = bench.c1_time_to_optimum(1)
+        assert set(r) == {"error"}
