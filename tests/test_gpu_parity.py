@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle.
 
 Integer records (dJr, dJo, residual, violations, |dR|, flags) must be
-bit-exact; rendered depths are compared bit for bit as well (the north-star
+bit-exact; rendered depths are compared bit for bit as well (the required
 tolerance for depths is 1e-4 m, and the arithmetic contract makes them equal).
 """
 import numpy as np
