@@ -10,8 +10,10 @@ decomposition into per-edge costs, Eq. (3)/(4) monotone successors and edge
 cost); ``search.py`` holds the plain tree searches (uniform-cost search over
 the MSGT of Sec. IV-A/B, and exhaustive enumeration for tiny inputs).
 
-Pins (tests/test_oracle_*.py): closed-form depths of single triangles and
-box faces, the watertightness invariant of the coverage rule, brute-force
+Pins (tests/test_oracle_*.py): the observed cloud's camera and world points
+against float64 pinhole back-projection and sensor pose (a camera with
+fx != fy, cx != cy, a non-square image; the table plane and ray-cast box faces),
+closed-form depths of single triangles and box faces, the watertightness invariant of the coverage rule, brute-force
 point-in-triangle coverage with exact rationals, exact-delta ties of Eq. (1),
 the K = 1 identity between the decomposed and undecomposed cost, the
 zero-cost ground-truth path on a noise-free observation, empty-observation and
