@@ -50,7 +50,10 @@ typedef enum {
   PERCH_E_OOM = -3,     /* device or host allocation failed */
   PERCH_E_STATE = -4,   /* call order: meshes / pose grid / observation missing */
   PERCH_E_TIMEOUT = -5, /* search limit reached; best solution so far returned */
-  PERCH_E_RANGE = -6    /* a hypothesis does not fit the renderer's tile limit */
+  PERCH_E_RANGE = -6,   /* a hypothesis does not fit the renderer's tile limit */
+  PERCH_E_DEVICE = -7   /* a bounded wait in a kernel gave up (flags bit 30) or a
+                           device-side index check failed (bit 31): the affected
+                           records hold no cost; the context stays usable */
 } perch_status;
 
 typedef struct perch_ctx perch_ctx;
@@ -86,7 +89,12 @@ typedef struct {
  *           is not a successor: its cost fields are then 0
  *   n_new = |dR|, the child's pixels where the parent render is empty
  *   flags = bit 0: a triangle of the child was culled (near plane / guard
- *           band); bit 1: invalid (viol > 0)
+ *           band); bit 1: invalid (viol > 0); bit 30: a bounded wait of the
+ *           evaluation kernel for one of its bulk copies gave up, so no cost
+ *           was computed (every other field is 0); bit 31: a parent or pose
+ *           index was out of range (device-pointer calls only; other fields 0).
+ *           The host-pointer calls and the search return PERCH_E_DEVICE when
+ *           any record carries bit 30 or 31
  *   n_vol = #{q in I n V(O) outside every parent object's volume}: how much
  *           the overlap heuristic h_overlap of Sec. IV-C (observed points
  *           outside the assigned volumes) drops from parent to child; 0 when
@@ -151,8 +159,8 @@ int perch_eval_successors(perch_ctx* ctx, const perch_obj* parents, int32_t pare
  * out are DEVICE pointers (e.g. torch tensors on the context's device) and
  * the work is only enqueued on the context's stream; out is valid once that
  * stream reaches this point. Indices are not validated on the host (an
- * out-of-range parent or pose index sets PERCH_FLAG bit 31 in that record's
- * flags and zeroes the rest). */
+ * out-of-range parent or pose index sets bit 31 in that record's flags and
+ * zeroes the rest); a record whose bounded wait gave up carries bit 30. */
 int perch_eval_successors_dev(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride,
                               const int32_t* parent_len, int32_t n_par, const int32_t* hyp_parent,
                               const perch_obj* hyp, int64_t n_hyp, int32_t K_total, perch_cost* out);
@@ -168,12 +176,13 @@ int perch_eval_successors_dev(perch_ctx* ctx, const perch_obj* parents, int32_t 
  * Limit: 4*n_par*W*H + 4*n_par*max(|I|,1) + 4*n_par + 8 bytes (each of the
  * three parts rounded up to 256) must not exceed 8 MiB, else PERCH_E_RANGE
  * and nothing is enqueued.
- * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture. Every call shares
- * the array and re-initialises it, so calls whose work overlaps on the GPU
- * (other streams, or other contexts on the same device) race; serialise them.
- * The array is held by every GPU that loads the library until the process
- * exits. */
+ * perch_set_observation does this entry point's own set-up, once per device:
+ * it looks up the array's device address and loads the kernels the call
+ * launches (either could otherwise allocate on first use); the call itself
+ * then only enqueues work. Every call shares the array and re-initialises
+ * it, so calls whose work overlaps on the GPU (other streams, or other
+ * contexts on the same device) race; serialise them. The array is held by
+ * every GPU that loads the library until the process exits. */
 int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride,
                                   const int32_t* parent_len, int32_t n_par, const int32_t* hyp_parent,
                                   const perch_obj* hyp, int64_t n_hyp, int32_t K_total, perch_cost* out);
@@ -303,6 +312,15 @@ int perch_eval_graph(perch_ctx* ctx, const perch_obj* parents, int32_t parent_st
  * when the meshes, the pose grid or the camera change. Records are identical
  * with the shortcut on or off. on = 0 renders every hypothesis. */
 int perch_set_shortcut(perch_ctx* ctx, int32_t on);
+
+/* Bound on the polls of the evaluation kernel's first wait for each of its
+ * bulk copies into shared memory (default, and for polls < 0: 2^20 polls or
+ * 2 s, whichever comes first). A wait that gives up marks its record with
+ * flags bit 30 and no cost; the kernel then waits for every copy still in
+ * flight with the default bound before it takes further work, so a small
+ * limit (0 = give up at once) exercises the failure path without leaving a
+ * copy outstanding. Not in the paper; for failure-path tests. */
+int perch_set_wait_limit(perch_ctx* ctx, int32_t polls);
 
 /* Of the hypotheses of the most recent evaluation, how many took the
  * shortcut (0 if it was off) and how many there were. Waits for the stream. */

@@ -58,6 +58,20 @@ int perch_ctx::cuda(cudaError_t e, const char* what) {
   return fail(PERCH_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+int perch_ctx::check_records(const perch_cost* out, long long n) {
+  long long bad = 0, first = -1;
+  for (long long h = 0; h < n; ++h)
+    if (out[h].flags & (kFlagTimeout | kFlagBadIndex)) {
+      if (first < 0) first = h;
+      ++bad;
+    }
+  if (!bad) return PERCH_OK;
+  return fail(PERCH_E_DEVICE,
+              "%lld records (the first: hypothesis %lld, flags 0x%08x) carry no cost: a bounded wait in the "
+              "evaluation kernel gave up or an index was out of range",
+              bad, first, out[first].flags);
+}
+
 Geometry perch_ctx::geometry() const {
   Geometry g;
   g.meshes = meshes.as<DevMesh>();
@@ -508,6 +522,8 @@ int perch_set_observation(perch_ctx* ctx, const float* depth, int32_t W, int32_t
   if (brc != PERCH_OK) return brc;
   int rc = ctx->ensure_tables();
   if (rc != PERCH_OK) return rc;
+  rc = noalloc_prepare(ctx);
+  if (rc != PERCH_OK) return rc;
   CK(cudaStreamSynchronize(ctx->stream), "observation index");
   ctx->has_obs = true;
   return PERCH_OK;
@@ -595,6 +611,7 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
   b.out = d_out;
   b.tile_w = tile_w;
   b.tile_h = tile_h;
+  b.wait_polls = building_solo ? kWaitSpins : wait_polls;
   const Geometry g = geometry();
   if (!ev[0])
     for (int k = 0; k < 3; ++k) CK(cudaEventCreate(&ev[k]), "cudaEventCreate");
@@ -705,7 +722,7 @@ int perch_eval_successors(perch_ctx* ctx, const perch_obj* parents, int32_t pare
   CK(cudaMemcpyAsync(out, ctx->b_out.p, sizeof(perch_cost) * (size_t)n_hyp, cudaMemcpyDeviceToHost, ctx->stream),
      "copy results");
   CK(cudaStreamSynchronize(ctx->stream), "eval");
-  return PERCH_OK;
+  return ctx->check_records(out, n_hyp);
 }
 
 int perch_eval_successors_dev(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride,
@@ -775,6 +792,14 @@ int perch_render(perch_ctx* ctx, const perch_obj* objs, int32_t n, float* depth_
   return PERCH_OK;
 }
 
+
+int perch_set_wait_limit(perch_ctx* ctx, int32_t polls) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  ctx->wait_polls = polls < 0 ? kWaitSpins : polls;
+  ctx->tables_version++;  // a captured graph holds the old limit
+  return PERCH_OK;
+}
 
 int perch_set_shortcut(perch_ctx* ctx, int32_t on) {
   if (!ctx) return PERCH_E_ARG;
@@ -874,7 +899,7 @@ int perch_eval_successors_multi(perch_ctx* ctx, const perch_obj* parents, int32_
   CK(cudaMemcpyAsync(out, ctx->b_out.p, sizeof(perch_cost) * (size_t)n_hyp, cudaMemcpyDeviceToHost, ctx->stream),
      "copy results");
   CK(cudaStreamSynchronize(ctx->stream), "eval");
-  return PERCH_OK;
+  return ctx->check_records(out, n_hyp);
 }
 
 }  // extern "C"

@@ -112,6 +112,10 @@ struct perch_ctx {
   // records, and in selecting states and building batches (learned scoring included)
   double search_eval_seconds = 0.0, search_absorb_seconds = 0.0, search_host_seconds = 0.0;
 
+  // poll bound of the evaluation kernel's first wait for each bulk copy
+  // (perch_set_wait_limit); the solo table always uses the default
+  int wait_polls = perch::kWaitSpins;
+
   // events around the phases of the last evaluation
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   bool timed = false;
@@ -125,6 +129,9 @@ struct perch_ctx {
   }
 
   int fail(int code, const char* fmt, ...);
+  // PERCH_E_DEVICE if some record of a finished host-side evaluation carries
+  // kFlagTimeout or kFlagBadIndex (no cost was computed for it)
+  int check_records(const perch_cost* out, long long n);
   int cuda(cudaError_t e, const char* what);
   perch::Geometry geometry() const;
   int ensure_tables();
@@ -134,6 +141,10 @@ struct perch_ctx {
                    const int32_t* d_hp, const perch_obj* d_hyp, long long n_hyp, int K_total, perch_cost* d_out,
                    const int32_t* d_parent_scene = nullptr, const int32_t* d_parent_K = nullptr);
 };
+
+// Set-up of perch_eval_successors_noalloc on the context's device (scratch
+// address, kernels, events); called by perch_set_observation.
+int noalloc_prepare(perch_ctx* ctx);
 
 // Learned heuristic: network predictions (host) for hypotheses over parents
 // (host arrays as perch_cnn_crops); crops and forward pass on the device.

@@ -107,6 +107,10 @@ struct Batch {
   int tiles_w, tiles_h;
   uint8_t* skip;
   unsigned long long* n_short;
+  // bound on the polls of the first wait for each bulk copy (kWaitSpins by
+  // default); the wait that drains a copy after one gave up always uses
+  // kWaitSpins
+  int wait_polls;
 };
 
 // kernels.cu launchers (all asynchronous on `s`)
@@ -145,6 +149,10 @@ cudaError_t launch_eval_group(const Camera& cam, const Geometry& g, const ObsInd
                               const int* order, const int* offset, const int* count, int* next, long long max_items,
                               int threads, int sm_count, cudaStream_t s);
 size_t eval_smem_bytes(int tile_w, int tile_h);
+// loads the kernels the allocation-free evaluation launches (a lazily loaded
+// module or function would otherwise be loaded, and may allocate, at its
+// first launch)
+cudaError_t preload_eval_kernels();
 bool eval_tile_fits(int device, int tile_w, int tile_h);
 
 }  // namespace perch

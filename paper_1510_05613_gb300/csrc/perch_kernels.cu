@@ -692,10 +692,10 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 // Wait for the phase with the given parity. Each poll may suspend the thread
 // in hardware (up to 0.1 ms) instead of spinning; the wait gives up after
-// kWaitSpins polls or 2 s, whichever comes first, and then returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// `polls` polls or 2 s, whichever comes first, and then returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int polls = kWaitSpins) {
   const uint64_t t0 = global_ns();
-  for (int i = 0; i < kWaitSpins; ++i) {
+  for (int i = 0; i < polls; ++i) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -784,12 +784,15 @@ struct EvalShared {
   uint32_t pv, pt;  // parity of the next phase of each barrier
 };
 
+// Outcome of one evaluation: done; a bounded wait gave up but every copy it
+// was waiting for has landed since (the record carries kFlagTimeout and the
+// CTA may go on); or a copy may still be in flight (the CTA must stop).
+enum EvalStatus { kEvalDone = 0, kEvalTimedOut = 1, kEvalStop = 2 };
+
 // Evaluate hypothesis h with a CTA of NT threads. The CTA's two mbarriers
-// persist across hypotheses (their phase parities are in sh). Returns false
-// if a bounded wait gave up (the record then carries kFlagTimeout and the
-// barriers must not be used again).
+// persist across hypotheses (their phase parities are in sh).
 template <int NT, bool MULTI>
-__device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, const ObsIndex& obs0, const Batch& b,
+__device__ int eval_one(long long h, const Camera& cam, const Geometry& g, const ObsIndex& obs0, const Batch& b,
                          EvalShared& sh, ObsIndex* s_obs) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -812,7 +815,7 @@ __device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, cons
       perch_cost r = {0, 0, 0, 0, 0, kFlagBadIndex, 0};
       b.out[h] = r;
     }
-    return true;
+    return kEvalDone;
   }
   if (MULTI && tid < (int)(sizeof(ObsIndex) / 4))  // this scene's index, read from shared memory below
     reinterpret_cast<int*>(s_obs)[tid] = reinterpret_cast<const int*>(&b.scenes[scene])[tid];
@@ -852,7 +855,7 @@ __device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, cons
   for (int c = 0; c < m.chunk_count; ++c) {
     const int4 ci = g.chunk_info[m.chunk_begin + c];
     // vertices: wait for the slice, project, then reuse its buffer for c+1
-    const bool vok = mbar_wait(&s_bar[0], pv);
+    const bool vok = mbar_wait(&s_bar[0], pv, b.wait_polls);
     int bad = 0;
     if (vok) {
       for (int v = tid; v < ci.y; v += NT) {
@@ -878,7 +881,7 @@ __device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, cons
       v_pending = true;
     }
     // triangles
-    const bool tok = mbar_wait(&s_bar[1], pt);
+    const bool tok = mbar_wait(&s_bar[1], pt, b.wait_polls);
     if (tok) {
       for (int t = tid; t < ci.w; t += NT) {
         const uint32_t pk = tbuf[t];
@@ -946,15 +949,25 @@ __device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, cons
     __syncthreads();  // the next chunk reuses sXY, sIZ and the queue
   }
   if (timed_out) {
-    // a copy never completed: let any copy still in flight land (bounded),
-    // then report the failure instead of a cost
-    if (v_pending) mbar_wait(&s_bar[0], pv);
-    if (t_pending) mbar_wait(&s_bar[1], pt);
+    // A wait gave up: report the failure instead of a cost, after draining
+    // every copy still in flight with the full bound (kWaitSpins polls or
+    // 2 s). Once both have landed the barriers' phases are known again and
+    // the CTA may take further work; if a drain also gives up, a copy may
+    // still be writing into this CTA's shared memory and it must stop.
+    bool ok = true;
+    if (v_pending) ok = mbar_wait(&s_bar[0], pv) && ok;
+    if (t_pending) ok = mbar_wait(&s_bar[1], pt) && ok;
+    ok = __syncthreads_and(ok);
+    if (ok) {
+      if (v_pending) pv ^= 1u;
+      if (t_pending) pt ^= 1u;
+    }
     if (tid == 0) {
       perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout, 0};
       b.out[h] = r;
     }
-    return false;
+    __syncthreads();  // s_cnt and the tile are reused by the next hypothesis
+    return ok ? kEvalTimedOut : kEvalStop;
   }
   if (culled) s_cnt[2] = 1;
   __syncthreads();
@@ -997,7 +1010,7 @@ __device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, cons
       b.out[h] = r;
     }
     __syncthreads();  // s_cnt is reset by the next hypothesis
-    return true;
+    return kEvalDone;
   }
 
   // ---- dJ_r: dR points with no observed point within delta
@@ -1067,7 +1080,7 @@ __device__ bool eval_one(long long h, const Camera& cam, const Geometry& g, cons
     b.out[h] = r;
   }
   __syncthreads();  // s_cnt and the tile are reused by the next hypothesis
-  return true;
+  return kEvalDone;
 }
 
 // A group of hypotheses evaluated by one persistent launch: items
@@ -1103,8 +1116,17 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_eval(Camera cam, Geometry g, 
     __syncthreads();
     if (item >= count) break;
     const long long h = grp.order ? grp.order[offset + item] : item;
-    if (!eval_one<NT, MULTI>(h, cam, g, obs, b, sh, &s_obs)) break;
+    if (eval_one<NT, MULTI>(h, cam, g, obs, b, sh, &s_obs) == kEvalStop) break;
   }
+}
+
+cudaError_t preload_eval_kernels() {
+  cudaFuncAttributes a;
+  cudaError_t e;
+  if ((e = cudaFuncGetAttributes(&a, k_fill_u32)) != cudaSuccess) return e;
+  if ((e = cudaFuncGetAttributes(&a, k_render_parents)) != cudaSuccess) return e;
+  if ((e = cudaFuncGetAttributes(&a, k_uset)) != cudaSuccess) return e;
+  return cudaFuncGetAttributes(&a, k_eval<256, false>);
 }
 
 // group hypotheses by mesh: hist -> offsets (exclusive scan) -> order;

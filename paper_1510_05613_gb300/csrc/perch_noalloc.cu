@@ -51,6 +51,25 @@ cudaError_t scratch_address(int device, void** out) {
 
 }  // namespace
 
+// Set-up of the allocation-free entry point on the context's device (called
+// by perch_set_observation, which allocates anyway): resolves the array's
+// address, which loads this file's module and with it the array, loads the
+// kernels the entry point launches, and creates the timing events. After it
+// the entry point only enqueues work.
+int noalloc_prepare(perch_ctx* ctx) {
+  void* base = nullptr;
+  cudaError_t e = scratch_address(ctx->device, &base);
+  if (e != cudaSuccess) return ctx->cuda(e, "cudaGetSymbolAddress(noalloc scratch)");
+  e = preload_eval_kernels();
+  if (e != cudaSuccess) return ctx->cuda(e, "load evaluation kernels");
+  if (!ctx->ev[0])
+    for (int k = 0; k < 3; ++k) {
+      e = cudaEventCreate(&ctx->ev[k]);
+      if (e != cudaSuccess) return ctx->cuda(e, "cudaEventCreate");
+    }
+  return PERCH_OK;
+}
+
 extern "C" int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride,
                                              const int32_t* parent_len, int32_t n_par, const int32_t* hyp_parent,
                                              const perch_obj* hyp, int64_t n_hyp, int32_t K_total,
@@ -77,8 +96,9 @@ extern "C" int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* pa
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return ctx->cuda(e, "cudaSetDevice");
   void* base = nullptr;
-  e = scratch_address(ctx->device, &base);
+  e = scratch_address(ctx->device, &base);  // resolved by perch_set_observation: a table lookup here
   if (e != cudaSuccess) return ctx->cuda(e, "cudaGetSymbolAddress(noalloc scratch)");
+  if (!ctx->ev[0]) return ctx->fail(PERCH_E_STATE, "noalloc: set an observation first");
   unsigned char* p = static_cast<unsigned char*>(base);
   float* parent_z = reinterpret_cast<float*>(p);
   int* uset = reinterpret_cast<int*>(p + z_bytes);
@@ -86,6 +106,8 @@ extern "C" int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* pa
   int* item_count = uset_count + n_par;  // the evaluation's work counter pair
   int* item_next = item_count + 1;
 
+  e = cudaEventRecord(ctx->ev[0], ctx->stream);
+  if (e != cudaSuccess) return ctx->cuda(e, "event");
   e = launch_fill_u32(reinterpret_cast<uint32_t*>(parent_z), kInfBits, (long long)npx * n_par, ctx->stream);
   if (e != cudaSuccess) return ctx->cuda(e, "clear parents");
   e = cudaMemsetAsync(uset_count, 0, 4 * (size_t)n_par, ctx->stream);
@@ -107,11 +129,14 @@ extern "C" int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* pa
   b.out = out;
   b.tile_w = ctx->tile_w;
   b.tile_h = ctx->tile_h;
+  b.wait_polls = ctx->wait_polls;
   const Geometry g = ctx->geometry();
   e = launch_render_parents(ctx->cam, g, b, ctx->max_chunks, nullptr, ctx->stream);
   if (e != cudaSuccess) return ctx->cuda(e, "render parents");
   e = launch_uset(ctx->cam, g, ctx->obs, b, ctx->stream);
   if (e != cudaSuccess) return ctx->cuda(e, "residual sets");
+  e = cudaEventRecord(ctx->ev[1], ctx->stream);
+  if (e != cudaSuccess) return ctx->cuda(e, "event");
   e = launch_fill_u32(reinterpret_cast<uint32_t*>(item_count), (uint32_t)n_hyp, 1, ctx->stream);
   if (e != cudaSuccess) return ctx->cuda(e, "item count");
   e = launch_fill_u32(reinterpret_cast<uint32_t*>(item_next), 0u, 1, ctx->stream);
@@ -119,5 +144,8 @@ extern "C" int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* pa
   e = launch_eval_group(ctx->cam, g, ctx->obs, b, nullptr, nullptr, item_count, item_next, n_hyp, 256,
                         ctx->sm_count, ctx->stream);
   if (e != cudaSuccess) return ctx->cuda(e, "eval kernel");
+  e = cudaEventRecord(ctx->ev[2], ctx->stream);
+  if (e != cudaSuccess) return ctx->cuda(e, "event");
+  ctx->timed = true;  // perch_last_timing: prep = clears, parent renders, U sets; eval = the kernel
   return PERCH_OK;
 }

@@ -44,6 +44,9 @@ constexpr int64_t kInf = std::numeric_limits<int64_t>::max();
 // batches of at least this many hypotheses are built and absorbed by host
 // threads (OpenMP), one expanded state or one scene per task
 constexpr size_t kParallelMin = 65536;
+// record flags that mean "no cost computed": a bounded wait gave up, or an
+// index check failed on the device
+constexpr uint32_t kNoCost = perch::kFlagTimeout | perch::kFlagBadIndex;
 
 uint64_t pack(const perch_obj& o) {
   return ((uint64_t)o.mesh << 48) | ((uint64_t)(uint16_t)o.ix << 32) | ((uint64_t)(uint16_t)o.iy << 16) |
@@ -172,6 +175,7 @@ struct SceneSearch {
   std::vector<ExpansionRecord> exps;   // learned queue: one per expanded state
   std::vector<int> pool;               // learned queue: candidates of the current step
   int T = 16;                          // learned queue: placements kept per type
+  bool bad_record = false;             // a record carried no cost (flags bit 30 or 31)
   bool focal() const { return w > 1.0 || heur != 0; }
   int64_t hval(int which, int idx) const {
     if (which == 2) {  // deepest first, then g + the free estimate
@@ -333,6 +337,10 @@ struct SceneSearch {
     er.best.assign(nt, kInf);
     std::vector<std::vector<std::pair<int64_t, long long>>> by(nt);
     for (long long h = 0; h < n; ++h) {
+      if (recs[h].flags & kNoCost) {
+        bad_record = true;
+        continue;
+      }
       if (recs[h].viol > 0) continue;
       const size_t t = std::lower_bound(er.types.begin(), er.types.end(), (int)hyps[h].mesh) - er.types.begin();
       if (t >= nt) continue;
@@ -402,6 +410,10 @@ struct SceneSearch {
     s.h_cnn = -1.0;  // candidates changed: score again
   }
   void absorb(int pidx, const perch_obj& h, const perch_cost& r) {
+    if (r.flags & kNoCost) {  // no cost was computed: the search cannot go on
+      bad_record = true;
+      return;
+    }
     if (r.viol > 0) return;  // occludes the parent: not a successor (Eq. (3))
     const int64_t ng = states[pidx].g + (int64_t)r.djr + r.djo + r.resid;
     if (ng > best_g) return;
@@ -684,6 +696,9 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
 #pragma omp parallel for schedule(dynamic, 1) if (slots.size() > 1 && hyps.size() >= kParallelMin)
     for (long long i = 0; i < (long long)slots.size(); ++i) absorb_scene(slots[i]);
     if (failed) return ctx->fail(PERCH_E_OOM, "search: out of host memory while absorbing records");
+    for (int si : slots)
+      if (ss[si].bad_record)
+        return ctx->fail(PERCH_E_DEVICE, "search: an evaluation record carries no cost (flags bit 30 or 31)");
     ctx->search_absorb_seconds += std::chrono::duration<double>(Clock::now() - ta).count();
   }
 }

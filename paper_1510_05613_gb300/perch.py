@@ -15,7 +15,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libperch.so")
 
 PERCH_OK, PERCH_E_ARG, PERCH_E_CUDA, PERCH_E_OOM, PERCH_E_STATE, PERCH_E_TIMEOUT, PERCH_E_RANGE = 0, -1, -2, -3, -4, -5, -6
-FLAG_CULLED, FLAG_INVALID, FLAG_BAD_INDEX = 1, 2, 1 << 31
+PERCH_E_DEVICE = -7
+FLAG_CULLED, FLAG_INVALID, FLAG_TIMEOUT, FLAG_BAD_INDEX = 1, 2, 1 << 30, 1 << 31
 
 OBJ = np.dtype([("mesh", np.uint16), ("iyaw", np.uint16), ("ix", np.int16), ("iy", np.int16)])
 COST = np.dtype([("djr", np.int32), ("djo", np.int32), ("resid", np.int32), ("viol", np.int32),
@@ -30,7 +31,8 @@ EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_mesh
            "perch_cnn_param_count", "perch_cnn_set_params", "perch_cnn_get_params", "perch_cnn_crops",
            "perch_cnn_forward", "perch_cnn_train_step", "perch_cnn_gradients", "perch_set_heuristic_net",
            "perch_cnn_set_tensor_path", "perch_cnn_tensor_status",
-           "perch_set_shortcut", "perch_shortcut_stats", "perch_search_stats", "perch_search_times")
+           "perch_set_shortcut", "perch_shortcut_stats", "perch_search_stats", "perch_search_times",
+           "perch_set_wait_limit")
 
 
 class perch_mesh(ctypes.Structure):
@@ -106,6 +108,7 @@ def load(path: str = LIB_PATH):
         "perch_cnn_gradients": ([P, P, P, P, I32, P, P, P], ctypes.c_int),
         "perch_set_heuristic_net": ([P, P, I32], ctypes.c_int),
         "perch_set_shortcut": ([P, I32], ctypes.c_int),
+        "perch_set_wait_limit": ([P, I32], ctypes.c_int),
         "perch_search_stats": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "perch_search_times": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -295,6 +298,11 @@ class Perch:
         """Attach a PerchCNN (None detaches) for search heuristic bit 2."""
         self._net = net  # keep it alive while attached
         return self._check(self.lib.perch_set_heuristic_net(self.h, None if net is None else net.h, n_candidates))
+
+    def perch_set_wait_limit(self, polls: int):
+        """Poll bound of the evaluation kernel's first wait per bulk copy
+        (< 0: the default); 0 makes every such wait give up at once."""
+        return self._check(self.lib.perch_set_wait_limit(self.h, int(polls)))
 
     def perch_set_shortcut(self, on: bool):
         """Exact shortcut for hypotheses far from the observation and the parent (on by default)."""

@@ -260,6 +260,49 @@ def test_argument_errors(c1):
     assert len(p.perch_eval_successors([wl.gt[:0]], np.zeros(0, np.int32), hyps[:0], 2)) == 0
 
 
+def test_wait_limit_failure_path_reports_and_recovers(c1):
+    """A bounded wait of the evaluation kernel that gives up (limit 0 polls:
+    every first wait for a bulk copy gives up at once) leaves records with
+    flags bit 30 and no cost; the host call and the search return
+    PERCH_E_DEVICE instead of a result. The kernel drains every copy in
+    flight before it goes on, so the context stays usable: with the default
+    limit the records equal the oracle's again."""
+    import torch
+    wl, p, w = c1
+    hyps = synth.all_hypotheses(wl.grid, [0, 1])[::5]
+    hp = np.zeros(len(hyps), np.int32)
+    dev = torch.device("cuda:0")
+    P, plen, stride = perch.Perch.pack_parents([wl.gt[:1]])
+    tP = torch.from_numpy(P.view(np.int16).reshape(-1).copy()).to(dev)
+    tplen = torch.from_numpy(plen).to(dev)
+    thp = torch.zeros(len(hyps), dtype=torch.int32, device=dev)
+    th = torch.from_numpy(np.ascontiguousarray(hyps).view(np.int16).reshape(-1).copy()).to(dev)
+    tout = torch.full((len(hyps) * 7,), -7, dtype=torch.int32, device=dev)
+    p.perch_set_shortcut(False)
+    try:
+        p.perch_set_wait_limit(0)
+        with pytest.raises(perch.PerchError) as e:
+            p.perch_eval_successors([wl.gt[:0]], hp, hyps, wl.K)
+        assert e.value.code == perch.PERCH_E_DEVICE
+        torch.cuda.synchronize()
+        p.perch_eval_successors_dev(tP, stride, tplen, thp, th, wl.K, tout)
+        torch.cuda.synchronize()
+        got = tout.cpu().numpy().reshape(-1, 7)
+        assert (got[:, 5].astype(np.uint32) == perch.FLAG_TIMEOUT).all()  # every record: bit 30 and nothing else
+        assert (got[:, [0, 1, 2, 3, 4, 6]] == 0).all()
+        with pytest.raises(perch.PerchError) as e:
+            p.perch_search(wl.mesh_multiset, batch_states=4)
+        assert e.value.code == perch.PERCH_E_DEVICE
+    finally:
+        p.perch_set_wait_limit(-1)
+        p.perch_set_shortcut(True)
+    _compare(wl, p, w, [wl.gt[:0]], hp, hyps, wl.K)
+    p.perch_eval_successors_dev(tP, stride, tplen, thp, th, wl.K, tout)
+    torch.cuda.synchronize()
+    exp = oracle.eval_batch(w, wl.depth, [wl.gt[:1]], hp, hyps, wl.K)
+    assert np.array_equal(tout.cpu().numpy().reshape(-1, 7).astype(np.int64), exp)
+
+
 def test_search_matches_oracle_exhaustive_small_c1():
     grid = synth.pose_grid(-0.15, 0.1, 4, 4)
     wl = synth.workload_c1(scene=3, grid=grid)

@@ -3,7 +3,8 @@
 perch_eval_successors_noalloc is for callers that cannot allocate device
 memory when they evaluate successors (a real-time loop that must not stall on
 cudaMalloc, or a process whose GPU memory is fixed after start-up); its
-scratch is a fixed array inside the library. Its records must equal those of
+scratch is a fixed array inside the library. The call must leave the
+device's free memory unchanged, and its records must equal those of
 perch_eval_successors_dev on the same inputs, bit for bit (the tolerance of
 every record test here), on two calls in a row: the second call must not see
 the first call's z-buffers or residual sets, which stay in the shared array.
@@ -45,8 +46,13 @@ def test_noalloc_matches_existing_entry_point_twice():
         ref = torch.full((len(hyps) * 7,), -7, dtype=torch.int32, device=dev)
         got = torch.full((len(hyps) * 7,), -7, dtype=torch.int32, device=dev)
         p.perch_eval_successors_dev(tP, stride, tplen, thp, th, wl.K, ref)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info(dev)[0]
         p.perch_eval_successors_noalloc(tP, stride, tplen, thp, th, wl.K, got)
         torch.cuda.synchronize()
+        # the call allocated nothing on the device (its set-up was done by
+        # perch_set_observation inside p.setup)
+        assert torch.cuda.mem_get_info(dev)[0] == free_before
         r, g = ref.cpu().numpy().reshape(-1, 7), got.cpu().numpy().reshape(-1, 7)
         assert (r[:, 3] >= 0).all() and (r != -7).all()
         assert np.array_equal(g, r)
