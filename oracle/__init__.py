@@ -47,7 +47,9 @@ def build() -> str:
 class _Mesh(ctypes.Structure):
     _fields_ = [("n_verts", ctypes.c_int32), ("n_tris", ctypes.c_int32),
                 ("verts", ctypes.c_void_p), ("tris", ctypes.c_void_p),
-                ("vol_r", ctypes.c_float), ("vol_zlo", ctypes.c_float), ("vol_zhi", ctypes.c_float)]
+                ("vol_r", ctypes.c_float), ("vol_zlo", ctypes.c_float), ("vol_zhi", ctypes.c_float),
+                ("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("p", ctypes.c_float * 4),
+                ("zlo", ctypes.c_float), ("zhi", ctypes.c_float), ("normals", ctypes.c_void_p)]
 
 
 class _World(ctypes.Structure):
@@ -59,6 +61,10 @@ class _World(ctypes.Structure):
                 ("cos_sin", ctypes.c_void_p), ("n_yaw", ctypes.c_int32),
                 ("meshes", ctypes.c_void_p), ("n_mesh", ctypes.c_int32),
                 ("delta", ctypes.c_float)]
+
+
+class _ObjArg(ctypes.Structure):
+    _fields_ = [("mesh", ctypes.c_uint16), ("iyaw", ctypes.c_uint16), ("ix", ctypes.c_int16), ("iy", ctypes.c_int16)]
 
 
 _lib = None
@@ -82,6 +88,8 @@ def _load():
         lib.or_eval_batch.restype = I32
         lib.or_eval_batch.argtypes = [P, P, P, P, I32, I32, P, P, I64, I32, P, I32]
         lib.or_max_threads.restype = I32
+        lib.or_in_volume.restype = I32
+        lib.or_in_volume.argtypes = [P, _ObjArg, P, I64, P]
         _lib = lib
     return _lib
 
@@ -93,13 +101,24 @@ def _c(a, dtype):
 class World:
     """Camera, meshes, pose tables and delta, as the oracle sees them."""
 
-    def __init__(self, cam, meshes, grid, delta: float):
+    def __init__(self, cam, meshes, grid, delta: float, exact_volumes: bool = False):
+        """``exact_volumes``: V(O) is each mesh's closed-form solid where it
+        has one (mesh.volume), else the inscribed cylinder."""
         self._keep = []
         ms = (_Mesh * max(1, len(meshes)))()
         for i, m in enumerate(meshes):
             v, t = _c(m.verts, np.float32), _c(m.tris, np.int32)
             self._keep += [v, t]
             ms[i] = _Mesh(m.n_verts, m.n_tris, v.ctypes.data, t.ctypes.data, m.vol_r, m.vol_zlo, m.vol_zhi)
+            vol = getattr(m, "volume", None)
+            if exact_volumes and vol is not None:
+                nr = _c(vol.normals, np.float32)
+                self._keep.append(nr)
+                ms[i].kind, ms[i].n = int(vol.kind), int(vol.n)
+                for k in range(4):
+                    ms[i].p[k] = float(np.float32(vol.p[k]))
+                ms[i].zlo, ms[i].zhi = float(vol.zlo), float(vol.zhi)
+                ms[i].normals = nr.ctypes.data if nr.size else None
         self._keep.append(ms)
         xs, ys, cs = _c(grid.xs, np.float32), _c(grid.ys, np.float32), _c(grid.cos_sin, np.float32)
         self._keep += [xs, ys, cs]
@@ -119,8 +138,8 @@ class World:
         self.n_mesh = len(meshes)
 
     @classmethod
-    def of(cls, wl, delta=None):
-        return cls(wl.cam, wl.meshes, wl.grid, wl.delta if delta is None else delta)
+    def of(cls, wl, delta=None, exact_volumes: bool = False):
+        return cls(wl.cam, wl.meshes, wl.grid, wl.delta if delta is None else delta, exact_volumes)
 
     def ptr(self):
         return ctypes.addressof(self.c)
@@ -189,6 +208,16 @@ def eval_batch(world: World, depth, parents, hyp_parent, hyps, K_total: int, thr
     if rc:
         raise MemoryError("oracle eval_batch")
     return recs
+
+
+def in_volume(world: World, obj, pts):
+    """V(O) membership (0/1 per row) of world points (n, 3) for one object."""
+    o = _objs([obj])[0]
+    q = _c(pts, np.float32).reshape(-1, 3)
+    out = np.empty(q.shape[0], np.int32)
+    _load().or_in_volume(world.ptr(), _ObjArg(int(o["mesh"]), int(o["iyaw"]), int(o["ix"]), int(o["iy"])),
+                         q.ctypes.data, q.shape[0], out.ctypes.data)
+    return out
 
 
 def max_threads() -> int:

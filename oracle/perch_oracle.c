@@ -40,7 +40,9 @@
  *   - distances are measured in the camera frame; "explained" is d^2 <= delta^2
  *     (Eq. (1) calls a point unexplained only when the distance exceeds delta);
  *   - V(O) is an inscribed vertical cylinder about the object origin, the
- *     conservative volume the paper names in Sec. III-A.
+ *     conservative volume the paper names in Sec. III-A, or, where the
+ *     mesh describes a box, a regular prism or a superquadric with
+ *     polynomial exponents, that solid in closed form (in_volume).
  */
 #include <math.h>
 #include <stdint.h>
@@ -54,7 +56,18 @@ typedef struct {
   int32_t n_verts, n_tris;
   const float* verts;   /* n_verts x 3, object frame, z up */
   const int32_t* tris;  /* n_tris x 3 */
-  float vol_r, vol_zlo, vol_zhi; /* V(O): inscribed cylinder */
+  float vol_r, vol_zlo, vol_zhi; /* V(O): inscribed cylinder (kind 0) */
+  /* V(O) in closed form (kind 1 box, 2 regular prism, 3 superquadric; 0 =
+   * the inscribed cylinder above), in the object frame:
+   *   box:          |x| <= p0, |y| <= p1, zlo <= z <= zhi
+   *   prism:        zlo <= z <= zhi and normals[k] . (x, y) <= p1 for all k < n
+   *   superquadric: X = x / p0, Y = y / p1, Z = (z - p3) / p2 (each as a
+   *                 product with the binary32 reciprocal of the semi-axis);
+   *                 n = 1: X^2 + Y^2 + Z^2 <= 1; n = 2: (X^2 + Y^2)^2 + Z^4 <= 1 */
+  int32_t kind, n;
+  float p[4];
+  float zlo, zhi;
+  const float* normals; /* prism: n x 2 */
 } or_mesh;
 
 typedef struct { uint16_t mesh, iyaw; int16_t ix, iy; } or_obj;
@@ -268,13 +281,38 @@ static int explained(or_pt p, const or_pt* C, int64_t n, float delta2) {
   return 0;
 }
 
-/* V(O): inscribed vertical cylinder of the object's mesh at its pose */
+/* V(O) (Sec. III-A: the volume the object occupies) at the object's pose:
+ * the inscribed vertical cylinder about its origin (kind 0), or the closed
+ * form of its solid (kinds 1-3), tested in the object frame: the world
+ * point's offset from (x, y) turned by -yaw with the pose table's binary32
+ * (cos, sin): x' = fma(s, dy, c dx), y' = fma(c, dy, -(s dx)); z is the
+ * world height (objects stand on the table plane z = 0). */
 static int in_volume(const or_world* w, or_obj o, or_pt qw) {
   const or_mesh* m = &w->meshes[o.mesh];
-  float r2 = (float)((double)m->vol_r * (double)m->vol_r);
   float dx = qw.x - w->xs[o.ix], dy = qw.y - w->ys[o.iy];
-  float d2 = fmaf(dy, dy, dx * dx);
-  return d2 <= r2 && m->vol_zlo <= qw.z && qw.z <= m->vol_zhi;
+  if (m->kind == 0) {
+    float r2 = (float)((double)m->vol_r * (double)m->vol_r);
+    float d2 = fmaf(dy, dy, dx * dx);
+    return d2 <= r2 && m->vol_zlo <= qw.z && qw.z <= m->vol_zhi;
+  }
+  float c = w->cos_sin[2 * o.iyaw], sn = w->cos_sin[2 * o.iyaw + 1];
+  float xo = fmaf(sn, dy, c * dx);
+  float yo = fmaf(c, dy, -(sn * dx));
+  if (m->kind == 1) return fabsf(xo) <= m->p[0] && fabsf(yo) <= m->p[1] && m->zlo <= qw.z && qw.z <= m->zhi;
+  if (m->kind == 2) {
+    if (!(m->zlo <= qw.z && qw.z <= m->zhi)) return 0;
+    for (int k = 0; k < m->n; ++k)
+      if (fmaf(m->normals[2 * k + 1], yo, m->normals[2 * k] * xo) > m->p[1]) return 0;
+    return 1;
+  }
+  /* superquadric */
+  float X = xo * (float)(1.0 / (double)m->p[0]);
+  float Y = yo * (float)(1.0 / (double)m->p[1]);
+  float Z = (qw.z - m->p[3]) * (float)(1.0 / (double)m->p[2]);
+  float t = fmaf(Y, Y, X * X);
+  float z2 = Z * Z;
+  float F = m->n == 2 ? fmaf(t, t, z2 * z2) : t + z2;
+  return F <= 1.0f;
 }
 
 typedef struct { or_pt* cam; or_pt* world; int64_t n; } or_cloud;
@@ -393,6 +431,15 @@ int64_t or_observed(const or_world* w, const float* depth, float* cam_xyz, float
   int64_t n = I.n;
   free(I.cam); free(I.world); cam_free(&c);
   return n;
+}
+
+/* V(O) membership of n world points for one object (the test above) */
+int32_t or_in_volume(const or_world* w, or_obj o, const float* pts, int64_t n, int32_t* out) {
+  for (int64_t k = 0; k < n; ++k) {
+    or_pt q = {pts[3 * k], pts[3 * k + 1], pts[3 * k + 2]};
+    out[k] = in_volume(w, o, q);
+  }
+  return 0;
 }
 
 /* Eq. (1) over explicit clouds: out[k] = 1 iff P[k] is unexplained by Q */

@@ -75,6 +75,8 @@ class Mesh:
     vol_r: float  # V(O): inscribed vertical cylinder about the object origin
     vol_zlo: float
     vol_zhi: float
+    # the closed-form solid the mesh describes, when it has one (see Volume)
+    volume: "Volume | None" = None
 
     @property
     def n_verts(self) -> int:
@@ -88,6 +90,53 @@ class Mesh:
     def footprint_radius(self) -> float:
         v = self.verts.astype(np.float64)
         return float(np.sqrt((v[:, 0] ** 2 + v[:, 1] ** 2).max()))
+
+
+# closed-form object volumes V(O) (Sec. III-A: the volume the object
+# occupies, in closed form where there is one)
+VOL_CYLINDER, VOL_BOX, VOL_PRISM, VOL_SUPERQUADRIC = 0, 1, 2, 3
+
+
+@dataclass
+class Volume:
+    """Closed-form solid of one mesh, in its object frame (z up, base on
+    z = 0). kind VOL_BOX: |x| <= p[0], |y| <= p[1], zlo <= z <= zhi.
+    VOL_PRISM: the regular n-gon whose vertex k is at angle 2 pi k / n and
+    radius p[0] (apothem p[1]): every face k has n_k . (x, y) <= p[1] with the
+    outward unit normals n_k = normals[k] (angle (2k + 1) pi / n), and
+    zlo <= z <= zhi. VOL_SUPERQUADRIC with exponent pair n: semi-axes p[0..2],
+    centre height p[3]; X = x / p[0], Y = y / p[1], Z = (z - p[3]) / p[2];
+    n = 1 (eps1 = eps2 = 1, ellipsoid): X^2 + Y^2 + Z^2 <= 1; n = 2
+    (eps1 = 0.5, eps2 = 1): (X^2 + Y^2)^2 + Z^4 <= 1. The parameters are
+    binary32 as given to the oracle and the library, computed here in
+    double; the normals are the input data both sides use."""
+    kind: int
+    n: int
+    p: np.ndarray  # float32 (4,)
+    zlo: float
+    zhi: float
+    normals: np.ndarray  # float32 (n, 2) for VOL_PRISM, else (0, 2)
+
+
+def box_volume(a: float, b: float, h: float) -> Volume:
+    return Volume(VOL_BOX, 0, np.array([a / 2, b / 2, 0, 0], np.float32), 0.0, float(np.float32(h)),
+                  np.zeros((0, 2), np.float32))
+
+
+def prism_volume(R: float, n: int, h: float) -> Volume:
+    ang = [(2 * k + 1) * math.pi / n for k in range(n)]
+    normals = np.array([[math.cos(t), math.sin(t)] for t in ang], np.float64).astype(np.float32)
+    p = np.array([R, R * math.cos(math.pi / n), 0, 0], np.float64).astype(np.float32)
+    return Volume(VOL_PRISM, n, p, 0.0, float(np.float32(h)), normals)
+
+
+def superquadric_volume(a1: float, a2: float, a3: float, e1: float, e2: float) -> "Volume | None":
+    n = {(1.0, 1.0): 1, (0.5, 1.0): 2}.get((float(e1), float(e2)))
+    if n is None:
+        return None  # exponents without a polynomial closed form here: the inscribed cylinder stays
+    p = np.array([a1, a2, a3, a3], np.float32)
+    return Volume(VOL_SUPERQUADRIC, n, p, float(np.float32(0.0)), float(np.float32(2 * a3)),
+                  np.zeros((0, 2), np.float32))
 
 
 def _orient_outward(verts: np.ndarray, tris: np.ndarray, centre) -> np.ndarray:
@@ -138,7 +187,7 @@ def box_mesh(a: float, b: float, h: float, n: int, name: str = "box") -> Mesh:
     P, T = _weld(np.array(pts), np.array(tris, np.int64))
     T = _orient_outward(P, T, (0.0, 0.0, h / 2))
     r = 0.9 * min(a, b) / 2
-    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h)
+    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h, box_volume(a, b, h))
 
 
 def cylinder_mesh(R: float, h: float, n_seg: int, n_rings: int, name: str = "cylinder") -> Mesh:
@@ -165,7 +214,7 @@ def cylinder_mesh(R: float, h: float, n_seg: int, n_rings: int, name: str = "cyl
     P, T = np.array(pts), np.array(tris, np.int64)
     T = _orient_outward(P, T, (0.0, 0.0, h / 2))
     r = 0.9 * R * math.cos(math.pi / n_seg)
-    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h)
+    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h, prism_volume(R, n_seg, h))
 
 
 def _spow(x, e):
@@ -208,7 +257,8 @@ def superquadric_mesh(a1: float, a2: float, a3: float, e1: float, e2: float,
     s = min(1.0, zb / a3)
     rho = max(0.0, 1.0 - s ** (2.0 / e1)) ** (e1 / 2.0)
     r = 0.9 * min(a1, a2) * rho * math.cos(math.pi / n_omega)
-    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.2 * a3, 1.8 * a3)
+    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.2 * a3, 1.8 * a3,
+                superquadric_volume(a1, a2, a3, e1, e2))
 
 
 # ---------------------------------------------------------------------------
@@ -523,7 +573,7 @@ def frustum_mesh(r_bot: float, r_top: float, h: float, n_seg: int, n_rings: int,
 def hex_prism_mesh(R: float, h: float, sub: int, n_rings: int, name: str = "hexprism") -> Mesh:
     P, T = prism_mesh(lambda t: (R, h * t), _ngon(6), sub, n_rings, name)
     r = 0.9 * R * math.cos(math.pi / 6)
-    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h)
+    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h, prism_volume(R, 6, h))
 
 
 def superquadric_general(a1, a2, a3, e1, e2, n_eta, n_omega, name):
