@@ -82,16 +82,24 @@ def _remaining(multiset, parent):
     return rem
 
 
-def algorithmic_ops(wl, hyps, n_new):
-    """Lower bound of the arithmetic one evaluation must do, per hypothesis:
-    40 ops per mesh vertex (pose + camera transform, projection, snap,
-    reciprocal depth), 20 per triangle (edge setup, facing and extent tests,
-    pixel box), 50 per pixel of dR (3 edge functions, depth interpolation,
-    z-buffer min, back-projection and the first delta probe)."""
+def distinct_poses(hyps):
+    """The distinct (mesh, ix, iy, iyaw) of a batch, as object records."""
+    return np.unique(np.ascontiguousarray(hyps))
+
+
+def algorithmic_ops(wl, poses, covered, n_new):
+    """Lower bound of the arithmetic one evaluation step must do, split by
+    kernel. Render (k_render, once per distinct pose): 40 ops per mesh vertex
+    (pose + camera transform, projection, snap, reciprocal depth), 20 per
+    triangle (edge setup, facing and extent tests, pixel box), 30 per covered
+    pixel (3 edge functions, depth interpolation, z-buffer max). Cost (k_cost,
+    per hypothesis): 20 per pixel of dR (back-projection and the first delta
+    probe). Returns (render ops, cost ops)."""
     V = np.array([m.n_verts for m in wl.meshes], np.float64)
     T = np.array([m.n_tris for m in wl.meshes], np.float64)
-    mi = hyps["mesh"].astype(np.int64)
-    return float((40.0 * V[mi] + 20.0 * T[mi]).sum() + 50.0 * np.asarray(n_new, np.float64).sum())
+    mi = poses["mesh"].astype(np.int64)
+    render = float((40.0 * V[mi] + 20.0 * T[mi]).sum() + 30.0 * np.asarray(covered, np.float64).sum())
+    return render, 20.0 * float(np.asarray(n_new, np.float64).sum())
 
 
 class ClockSampler:
@@ -338,26 +346,36 @@ def run_ours(args):
             evs[k][1].record(stream)
         torch.cuda.synchronize()
     # the same sequence without the graph, to time its phases with the
-    # library's events (parent prep; the per-mesh evaluation launches)
+    # library's events on its stream (parent prep; grouping; the per-mesh
+    # render launches; the per-mesh cost launches)
+    phases, shared = [], False
     for k in range(max(3, args.steps // 2)):
         flush.fill_(k)
         p.perch_eval_successors_dev(tP, stride, tplen, thp, th, wl.K, tout)
         a, b = p.perch_last_timing()
         prep_ms.append(a)
         eval_ms.append(b)
+        ph, shared = p.perch_last_phase_times()
+        phases.append(ph)
     torch.cuda.synchronize()
     step_ms = [s.elapsed_time(e) for s, e in evs]
     total_s, value = whole_job(sum(step_ms) / 1e3, n_hyp * args.steps)
+    phase_ms = np.mean(np.array(phases), 0)
 
     rec = tout.view(-1, 7).cpu().numpy()
-    ops = algorithmic_ops(wl, hyps, rec[:, 4])
+    # pixels each distinct pose covers: its record against the empty parent
+    poses = distinct_poses(hyps)
+    covered = perch.records(p.perch_eval_successors([wl.gt[:0]], np.zeros(len(poses), np.int32), poses, wl.K))[:, 4]
+    render_ops, cost_ops = algorithmic_ops(wl, poses, covered, rec[:, 4])
     peaks = _measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     peak_tops = n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
     eval_s = statistics.mean(eval_ms) / 1e3
-    achieved = ops / eval_s / 1e12
+    render_s = phase_ms[2] / 1e3
+    achieved = render_ops / render_s / 1e12
+    achieved_cost = cost_ops / max(phase_ms[3] / 1e3, 1e-9) / 1e12
 
     # end to end through the C ABI with host buffers (pinned)
     def pin(a):
@@ -435,18 +453,24 @@ def run_ours(args):
             "config": {"workload": WORKLOADS[args.workload],
                        "hypotheses_per_step": n_hyp, "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": f"replicas x{ws}"},
-            "roofline": {"bound": "alu", "kernel": "k_eval", "achieved": achieved, "peak": peak_tops,
-                         "unit": "Tops/s", "frac": achieved / peak_tops,
+            "roofline": {"bound": "alu", "kernel": "k_render" if shared else "k_eval", "achieved": achieved,
+                         "peak": peak_tops, "unit": "Tops/s", "frac": achieved / peak_tops,
                          "traffic": traffic,
-                         "ops_per_launch": ops, "eval_ms": statistics.mean(eval_ms),
-                         "prep_ms": statistics.mean(prep_ms),
+                         "ops_per_step": render_ops, "render_ms": float(phase_ms[2]),
+                         "distinct_poses": int(len(poses)),
                          "peak_from": f"{n_sm} SMs x {FP32_LANES_PER_SM} lanes x {sm_max:.0f} MHz "
-                                      "(sm_max_mhz of MEASURED_PEAKS.json)"},
+                                      "(sm_max_mhz of MEASURED_PEAKS.json)",
+                         "phases_ms": {"parent_prep": float(phase_ms[0]), "grouping": float(phase_ms[1]),
+                                       "render": float(phase_ms[2]), "cost": float(phase_ms[3])},
+                         "cost_kernel": {"kernel": "k_cost", "ops_per_step": cost_ops, "achieved": achieved_cost,
+                                         "frac": achieved_cost / peak_tops},
+                         "eval_ms": statistics.mean(eval_ms), "prep_ms": statistics.mean(prep_ms)},
             "hbm": hbm_fields(n_hyp / eval_s, traffic / n_hyp if traffic else None),
             "paper_context": PAPER_CONTEXT,
             "e2e": e2e, "e2e_matches_device_records": consistent,
-            "gpu_launches": (8 + len(wl.meshes)) * args.steps,
-            "launch": {"graph": not args.no_graph, "persistent_per_mesh": True, "autotuned_threads": widths},
+            "gpu_launches": ((14 + 2 * len(wl.meshes)) if shared else (8 + len(wl.meshes))) * args.steps,
+            "launch": {"graph": not args.no_graph, "persistent_per_mesh": True, "autotuned_threads": widths,
+                       "shared_renders": shared},
             "clocks": cl,
             "time_to_optimum": search,
             "shortcut": shortcut,
@@ -728,15 +752,23 @@ def run_c4(args):
     e1.record(stream)
     torch.cuda.synchronize()
     fwd_ms = e0.elapsed_time(e1) / 10
-    p.perch_set_heuristic_net(net, args.candidates)
+    # the same network before training (same seeded initial weights): the
+    # "_untrained" arms measure what training adds to the queue itself
+    untrained = H.new_network(n_onehot, 1024, seed=3, stream=stream)
     peaks = _measured_peaks()
-    arms = [("plain", 1.0, 0), ("mha_depth", args.w, 1), ("mha_learned", args.w, 4), ("mha", args.w, 3),
-            ("mha_depth+learned", args.w, 5), ("mha+learned", args.w, 7)]
+    # (name, w, heuristic bits): bit 0 h_depth, bit 1 h_overlap, bit 2 the
+    # learned queue ordered by g + h_cnn across depths, bit 3 the learned
+    # depth-first queue
+    arms = [("plain", 1.0, 0), ("mha_depth", args.w, 1), ("mha_learned", args.w, 4),
+            ("mha_learned_untrained", args.w, 4), ("mha_learned_dive", args.w, 8),
+            ("mha_learned_dive_untrained", args.w, 8), ("mha", args.w, 3), ("mha_depth+learned", args.w, 5),
+            ("mha_depth+learned_untrained", args.w, 5), ("mha+learned", args.w, 7)]
     if args.arms:
         arms = [a for a in arms if a[0] in args.arms.split(",")]
     out, learned_cost = {}, {}
     with ClockSampler(0) as clocks, MemoryGuard() as mem:
         for name, w, hb in arms:
+            p.perch_set_heuristic_net(untrained if name.endswith("_untrained") else net, args.candidates)
             t1 = time.perf_counter()
             r = p.perch_search_multi(te, [wl.mesh_multiset for wl in test_sc], batch_states=args.batch_states,
                                      max_hyps_per_launch=args.launch_hyps, time_limit_s=args.search_limit, w=w,
@@ -763,7 +795,9 @@ def run_c4(args):
                 "learned_queue_seconds": learned_cost[name][0], "learned_states_scored": learned_cost[name][1],
                 "learned_crops": learned_cost[name][2],
                 "search_eval_s": learned_cost[name][3], "search_absorb_s": learned_cost[name][4],
-                "search_select_s": learned_cost[name][5]}
+                "search_select_s": learned_cost[name][5],
+                "per_scene": [{"cost": x["cost"], "expansions": x["expansions"], "seconds": round(x["seconds"], 3),
+                               "proven": x["proven_optimal"]} for x in r]}
 
     head = next((n for n in ("mha_depth+learned", "mha_learned", "mha+learned", "mha_depth", "plain") if n in out),
                 arms[0][0])
@@ -827,8 +861,10 @@ def main():
     ap.add_argument("--candidates", type=int, default=8, help="c4: placements per type the learned queue scores")
     ap.add_argument("--c4-grid", type=int, default=50, choices=[25, 50], help="c4: 50 = 2 cm x 16 yaws, 25 = 4 cm x 8")
     ap.add_argument("--off-grid", type=float, default=1.0, help="c4: off-grid offsets, in grid steps (0..1)")
-    ap.add_argument("--arms", default="", help="c4: comma-separated subset of plain, mha_depth, mha_learned, mha, "
-                                               "mha_depth+learned, mha+learned (default: all)")
+    ap.add_argument("--arms", default="", help="c4: comma-separated subset of plain, mha_depth, mha_learned, "
+                                               "mha_learned_untrained, mha_learned_dive, mha_learned_dive_untrained, "
+                                               "mha, mha_depth+learned, mha_depth+learned_untrained, mha+learned "
+                                               "(default: all)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "cnn"],
                     help="c2: 640x480 three ~10k-triangle meshes (the headline); c3: heavy occlusion, 2k-50k triangles")
     args = ap.parse_args()

@@ -215,15 +215,19 @@ int perch_render(perch_ctx* ctx, const perch_obj* objs, int32_t n, float* depth_
  * states with g <= w * (smallest anchor key) are also expanded greedily by
  * each inadmissible heuristic in `heuristics` (bit 0: h_depth = K - |s|;
  * bit 1: h_overlap = observed points outside the assigned volumes,
- * Sec. IV-C; bit 2: the learned heuristic of perch_set_heuristic_net: each
- * expansion keeps the n_candidates cheapest valid placements of every
- * remaining type; a child's queue pool is ordered deepest first, then by g +
- * the sum of its remaining objects' cheapest exact costs at the parent, and
- * each round the front of the pool (max(16, 2 batch_states) states) is
- * re-ranked, within each depth, by g + h_cnn, h_cnn = sum over the remaining
+ * Sec. IV-C; bits 2 and 3, exclusive: the learned heuristic of
+ * perch_set_heuristic_net, PERCH_E_STATE without a network. Each expansion
+ * keeps the n_candidates cheapest valid placements of every remaining type.
+ * A child s' gets h_free = the sum over its remaining objects of their
+ * cheapest exact costs at the parent, and h_cnn = the sum over its remaining
  * objects of the smallest predicted edge cost exp(y) - 1 among the parent's
- * candidates of that type, predicted with the child as parent; PERCH_E_STATE
- * without a network), and the search returns a scene of cost <= w * OPT
+ * candidates of that type, predicted with s' as parent. Each round the
+ * learned queue takes a pool of its front states (max(16, 2 batch_states)),
+ * scores them, expands the best batch_states and returns the rest. Bit 2:
+ * the queue is ordered by g + h_free across depths (ties: deeper first) and
+ * the pool expanded in order of g + h_cnn. Bit 3: the queue is ordered
+ * deepest first, then by g + h_free, and the pool re-ranked by g + h_cnn
+ * within each depth), and the search returns a scene of cost <= w * OPT
  * (Theorem 2). mesh_multiset[K]: the types of the K objects (Sec. III: known
  * number and types). batch_states: states taken from each queue per device
  * launch (>= 1). Stops at the optimum / the bound, or at time_limit_s /
@@ -312,6 +316,27 @@ int perch_eval_graph(perch_ctx* ctx, const perch_obj* parents, int32_t parent_st
  * when the meshes, the pose grid or the camera change. Records are identical
  * with the shortcut on or off. on = 0 renders every hypothesis. */
 int perch_set_shortcut(perch_ctx* ctx, int32_t on);
+
+/* Shared renders (on by default; not in the paper). A successor's new-object
+ * render depends only on its mesh and pose, not on its parent, so a batch is
+ * grouped by pose: each distinct (mesh, x, y, yaw) is rasterised once into a
+ * tile store in device memory (one tile per pose of the grid, sized by the
+ * pose's screen box and allocated with the pose tables), and every
+ * hypothesis is then compared with its own parent render and costed from
+ * that tile. Records are identical with sharing on or off; on = 0 renders
+ * every hypothesis separately (one kernel per hypothesis, no tile store).
+ * Sharing also stays off when the tile store would take more than a quarter
+ * of the free device memory. */
+int perch_set_share_renders(perch_ctx* ctx, int32_t on);
+
+/* Device time of the four phases of the most recent evaluation (CUDA
+ * events on the context's stream): ms[0] parent z-buffers, residual sets and
+ * the exact shortcut; ms[1] grouping the hypotheses; ms[2] the render
+ * launches (with shared renders) or the per-hypothesis evaluation launches;
+ * ms[3] the cost launches (0 without shared renders). *shared (may be NULL)
+ * = 1 if the evaluation used shared renders. Waits for the events.
+ * PERCH_E_STATE if no evaluation has been issued yet. */
+int perch_last_phase_times(perch_ctx* ctx, float ms[4], int32_t* shared);
 
 /* Bound on the polls of the evaluation kernel's first wait for each of its
  * bulk copies into shared memory (default, and for polls < 0: 2^20 polls or
@@ -408,7 +433,7 @@ int perch_cnn_gradients(perch_cnn* net, const uint16_t* crops, const int32_t* on
                         float* grads, float* loss, float* pred);
 
 /* Use `net` (not owned; NULL detaches) for the learned heuristic of the
- * search (heuristics bit 2). n_candidates: placements per remaining object
+ * search (heuristics bits 2 and 3). n_candidates: placements per remaining object
  * type scored for a state (see perch_search). PERCH_E_ARG if the network's
  * one-hot is narrower than meshes x yaws. */
 int perch_set_heuristic_net(perch_ctx* ctx, perch_cnn* net, int32_t n_candidates);

@@ -149,7 +149,46 @@ int perch_ctx::ensure_tables() {
   if (!eval_tile_fits(device, tile_w, tile_h))
     return fail(PERCH_E_RANGE, "object screen box %dx%d does not fit in shared memory", tile_w, tile_h);
   if ((int)mesh_threads.size() != n_mesh) mesh_threads.assign(n_mesh, 256);
+  const int rc = ensure_tile_store();
+  if (rc != PERCH_OK) return rc;
   tables_valid = true;
+  return PERCH_OK;
+}
+
+// The tile store of shared renders: per pose, its screen box's 1/z bits
+// (rows of its width, rounded up to 16 bytes), at the offsets the scan of
+// the box areas gives. Left out (store_ok = false, every hypothesis rendered
+// by k_eval) when the pose grid is too large for int32 offsets or the store
+// would take more than a quarter of the free device memory.
+int perch_ctx::ensure_tile_store() {
+  perch_ctx* ctx = this;
+  store_ok = false;
+  const long long per_mesh = (long long)nx * ny * n_yaw, P = per_mesh * n_mesh;
+  long long bound = 0;  // 16-byte units, from the per-mesh tiles (each box fits its mesh's tile)
+  for (int m = 0; m < n_mesh; ++m) bound += per_mesh * (((long long)mesh_tile_w[m] * mesh_tile_h[m] + 3) / 4);
+  if (P > (1LL << 28) || bound >= (1LL << 31)) return PERCH_OK;
+  CK(tile_sizes.ensure(4 * (size_t)P), "alloc tile sizes");
+  CK(tile_off.ensure(4 * ((size_t)P + 1)), "alloc tile offsets");
+  CK(pg_tmp.ensure(4 * ((size_t)P / 1024 + 2)), "alloc");
+  CK(pose_flags.ensure((size_t)P), "alloc pose flags");
+  CK(launch_tile_offsets(geometry(), tile_sizes.as<int>(), tile_off.as<int>(), pg_tmp.as<int>(), stream),
+     "tile offsets");
+  int total = 0;
+  CK(cudaMemcpyAsync(&total, tile_off.as<int>() + P, 4, cudaMemcpyDeviceToHost, stream), "copy tile total");
+  CK(cudaStreamSynchronize(stream), "tile offsets");
+  const size_t bytes = 16 * (size_t)std::max(total, 1);
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+  if (bytes > tile_store.cap && bytes - tile_store.cap > free_b / 4) return PERCH_OK;
+  CK(tile_store.ensure(bytes), "alloc tile store");
+  store_ok = true;
+  return PERCH_OK;
+}
+
+int perch_ctx::create_events() {
+  perch_ctx* ctx = this;
+  if (!ev[0])
+    for (int k = 0; k < kEvents; ++k) CK(cudaEventCreate(&ev[k]), "cudaEventCreate");
   return PERCH_OK;
 }
 
@@ -340,7 +379,7 @@ int perch_destroy(perch_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (DevBuf* b : ctx->all_buffers()) b->release();
   for (SceneBufs& sc : ctx->scenes) sc.release();
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < perch_ctx::kEvents; ++k)
     if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -613,8 +652,10 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
   b.tile_h = tile_h;
   b.wait_polls = building_solo ? kWaitSpins : wait_polls;
   const Geometry g = geometry();
-  if (!ev[0])
-    for (int k = 0; k < 3; ++k) CK(cudaEventCreate(&ev[k]), "cudaEventCreate");
+  {
+    const int rc = create_events();
+    if (rc != PERCH_OK) return rc;
+  }
   if (!capturing) CK(cudaEventRecord(ev[0], stream), "event");
   CK(launch_fill_u32(parent_z.as<uint32_t>(), kInfBits, (long long)npx * n_par, stream), "clear parents");
   CK(cudaMemsetAsync(uset_count.p, 0, 4 * (size_t)std::max(n_par, 1), stream), "memset");
@@ -639,6 +680,50 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
   short_counted = use_short;
   last_total = n_hyp;
   if (!capturing) CK(cudaEventRecord(ev[1], stream), "event");
+  if (share_renders && store_ok) {
+    // shared renders: group by pose; per mesh one persistent launch renders
+    // its distinct poses into the tile store, then one costs its hypotheses
+    const int per_mesh = nx * ny * n_yaw, P = per_mesh * n_mesh;
+    CK(pg_cnt.ensure(4 * (size_t)P), "alloc");
+    CK(pg_start.ensure(4 * ((size_t)P + 1)), "alloc");
+    CK(pg_flag.ensure(4 * (size_t)P), "alloc");
+    CK(pg_gix.ensure(4 * ((size_t)P + 1)), "alloc");
+    CK(pg_gpose.ensure(4 * (size_t)P), "alloc");
+    CK(pg_tmp.ensure(4 * ((size_t)P / 1024 + 2)), "alloc");
+    CK(pg_ranges.ensure(16 * (size_t)n_mesh), "alloc");
+    CK(g_order.ensure(sizeof(int) * (size_t)std::max(n_hyp, 1LL)), "alloc");
+    CK(g_next.ensure(sizeof(int) * 2 * (size_t)n_mesh), "alloc");
+    PoseGroups pg{pg_cnt.as<int>(),   pg_start.as<int>(), pg_flag.as<int>(),   pg_gix.as<int>(),
+                  pg_gpose.as<int>(), pg_tmp.as<int>(),   pg_ranges.as<int>(), g_order.as<int>()};
+    CK(launch_group_by_pose(g, b, pg, stream), "group by pose");
+    CK(cudaMemsetAsync(g_next.p, 0, sizeof(int) * 2 * (size_t)n_mesh, stream), "memset");
+    if (!capturing) CK(cudaEventRecord(ev[2], stream), "event");
+    int* rg = pg.ranges;
+    for (int m = 0; m < n_mesh; ++m) {
+      Batch bm = b;
+      bm.tile_w = mesh_tile_w[m];
+      bm.tile_h = mesh_tile_h[m];
+      const RenderWork w{pg.gpose, rg + 4 * m + 2, rg + 4 * m + 3, g_next.as<int>() + m, tile_store.as<uint32_t>(),
+                         tile_off.as<int>(), pose_flags.as<uint8_t>()};
+      CK(launch_render_group(cam, g, bm, w, std::min<long long>(n_hyp, per_mesh), mesh_threads[m], sm_count, stream),
+         "render kernel");
+    }
+    if (!capturing) CK(cudaEventRecord(ev[3], stream), "event");
+    for (int m = 0; m < n_mesh; ++m) {
+      Batch bm = b;
+      bm.tile_w = mesh_tile_w[m];
+      bm.tile_h = mesh_tile_h[m];
+      const CostWork c{pg.order, rg + 4 * m, rg + 4 * m + 1, g_next.as<int>() + n_mesh + m, tile_store.as<uint32_t>(),
+                       tile_off.as<int>(), pose_flags.as<uint8_t>()};
+      CK(launch_cost_group(cam, g, obs, bm, c, n_hyp, cost_threads, sm_count, stream), "cost kernel");
+    }
+    last_path = 2;
+    if (!capturing) {
+      CK(cudaEventRecord(ev[4], stream), "event");
+      timed = true;
+    }
+    return PERCH_OK;
+  }
   // group by mesh; one persistent launch per mesh with its own tile and CTA width
   CK(g_hist.ensure(sizeof(int) * (size_t)n_mesh), "alloc");
   CK(g_off.ensure(sizeof(int) * ((size_t)n_mesh + 1)), "alloc");
@@ -650,6 +735,7 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
                           g_order.as<int>(), scan_tmp.as<int>(), stream, use_short ? skip.as<uint8_t>() : nullptr),
      "group by mesh");
   CK(cudaMemsetAsync(g_next.p, 0, sizeof(int) * (size_t)n_mesh, stream), "memset");
+  if (!capturing) CK(cudaEventRecord(ev[2], stream), "event");
   for (int m = 0; m < n_mesh; ++m) {
     Batch bm = b;
     bm.tile_w = mesh_tile_w[m];
@@ -658,8 +744,10 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
                          g_next.as<int>() + m, n_hyp, mesh_threads[m], sm_count, stream),
        "eval kernel");
   }
+  last_path = 1;
   if (!capturing) {
-    CK(cudaEventRecord(ev[2], stream), "event");
+    CK(cudaEventRecord(ev[3], stream), "event");
+    CK(cudaEventRecord(ev[4], stream), "event");
     timed = true;
   }
   return PERCH_OK;
@@ -746,12 +834,31 @@ int perch_last_timing(perch_ctx* ctx, float* prep_ms, float* eval_ms) {
   if (!ctx) return PERCH_E_ARG;
   ctx->err.clear();
   if (!ctx->timed) return ctx->fail(PERCH_E_STATE, "no evaluation issued yet");
-  CK(cudaEventSynchronize(ctx->ev[2]), "event sync");
+  CK(cudaEventSynchronize(ctx->ev[4]), "event sync");
   float a = 0.0f, b = 0.0f;
   CK(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]), "event time");
-  CK(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]), "event time");
+  CK(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[4]), "event time");
   if (prep_ms) *prep_ms = a;
   if (eval_ms) *eval_ms = b;
+  return PERCH_OK;
+}
+
+int perch_last_phase_times(perch_ctx* ctx, float* ms, int32_t* shared) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (!ctx->timed) return ctx->fail(PERCH_E_STATE, "no evaluation issued yet");
+  CK(cudaEventSynchronize(ctx->ev[4]), "event sync");
+  for (int k = 0; k < 4; ++k)
+    if (ms) CK(cudaEventElapsedTime(&ms[k], ctx->ev[k], ctx->ev[k + 1]), "event time");
+  if (shared) *shared = ctx->last_path == 2 ? 1 : 0;
+  return PERCH_OK;
+}
+
+int perch_set_share_renders(perch_ctx* ctx, int32_t on) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  ctx->share_renders = on != 0;
+  ctx->tables_version++;  // a captured graph holds the old path
   return PERCH_OK;
 }
 

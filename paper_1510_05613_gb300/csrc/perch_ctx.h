@@ -83,6 +83,17 @@ struct perch_ctx {
   // per-batch buffers
   DevBuf parent_z, uset, uset_count;
   DevBuf g_hist, g_off, g_cursor, g_order, g_next;  // hypotheses grouped by mesh
+
+  // shared renders (perch_set_share_renders, on by default): the tile store
+  // holds one render per pose, indexed by pose; it is sized once per
+  // geometry and camera (tile_off, built with the pose boxes). Without room
+  // for it, or with sharing off, every hypothesis is rendered by k_eval.
+  bool share_renders = true;
+  bool store_ok = false;
+  DevBuf tile_store, tile_off, tile_sizes, pose_flags;
+  DevBuf pg_cnt, pg_start, pg_flag, pg_gix, pg_gpose, pg_tmp, pg_ranges;  // hypotheses grouped by pose
+  int cost_threads = 128;  // CTA width of k_cost
+  int last_path = 0;       // last evaluation: 1 = one render per hypothesis, 2 = shared renders
   DevBuf b_parents, b_plen, b_hp, b_hyp, b_out;
 
   // captured evaluation graph (perch_eval_graph); `version` changes whenever
@@ -116,8 +127,11 @@ struct perch_ctx {
   // (perch_set_wait_limit); the solo table always uses the default
   int wait_polls = perch::kWaitSpins;
 
-  // events around the phases of the last evaluation
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  // events around the phases of the last evaluation: start, after parent
+  // prep (and shortcut), after grouping, after the render launches (or the
+  // per-hypothesis evaluation), after the cost launches
+  static constexpr int kEvents = 5;
+  cudaEvent_t ev[kEvents] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   bool timed = false;
 
   std::vector<DevBuf*> all_buffers() {
@@ -125,7 +139,9 @@ struct perch_ctx {
             &scan_tmp, &cam_pts, &world_pts, &keys, &counts, &cursor, &d_scenes, &d_scene_img,
             &scratch_small, &pose_bbox, &parent_z, &uset, &uset_count, &b_parents, &b_plen, &b_hp, &b_hyp,
             &b_out, &g_hist, &g_off, &g_cursor, &g_order, &g_next, &net_crops, &net_onehot, &net_pred,
-            &solo, &solo_rec, &solo_hyp, &solo_hp, &solo_parent, &ptile_counts, &ptile_sat, &skip, &n_short};
+            &solo, &solo_rec, &solo_hyp, &solo_hp, &solo_parent, &ptile_counts, &ptile_sat, &skip, &n_short,
+            &tile_store, &tile_off, &tile_sizes, &pose_flags, &pg_cnt, &pg_start, &pg_flag, &pg_gix, &pg_gpose,
+            &pg_tmp, &pg_ranges};
   }
 
   int fail(int code, const char* fmt, ...);
@@ -135,6 +151,8 @@ struct perch_ctx {
   int cuda(cudaError_t e, const char* what);
   perch::Geometry geometry() const;
   int ensure_tables();
+  int ensure_tile_store();
+  int create_events();
   int build_scene(int s, const float* depth_host);
   int ensure_solo();
   int enqueue_eval(const perch_obj* d_parents, int parent_stride, const int32_t* d_plen, int n_par,

@@ -113,6 +113,45 @@ struct Batch {
   int wait_polls;
 };
 
+// Shared renders (k_render, then k_cost): per-pose flags of the tile store
+constexpr uint8_t kPoseCulled = 1;  // a triangle of the render was culled
+constexpr uint8_t kPoseFailed = 2;  // the render's bounded wait gave up: no tile
+
+// k_render's work: the distinct poses of a batch (pose index = ((mesh * nx +
+// ix) * ny + iy) * n_yaw + iyaw), one mesh's range per launch
+struct RenderWork {
+  const int* gpose;     // distinct poses, in pose order
+  const int* offset;    // device scalar: this launch's first entry of gpose
+  const int* count;     // device scalar: its entries
+  int* next;            // device counter, zero before the launch
+  uint32_t* store;      // tile store: 1/z bits of each pose's screen box, rows of its width
+  const int* tile_off;  // per pose: offset of its tile in the store, in 16-byte units
+  uint8_t* pose_flags;  // per pose: kPoseCulled, kPoseFailed
+};
+
+// k_cost's work: hypotheses sorted by pose, one mesh's range per launch
+struct CostWork {
+  const int* order;
+  const int* offset;  // device scalar
+  const int* count;   // device scalar
+  int* next;          // device counter, zero before the launch
+  const uint32_t* store;
+  const int* tile_off;
+  const uint8_t* pose_flags;
+};
+
+// Hypotheses grouped by pose; P = n_mesh x nx x ny x n_yaw. All device arrays.
+struct PoseGroups {
+  int* cnt;     // P: hypotheses per pose (zero again after the grouping)
+  int* start;   // P + 1: exclusive scan of cnt
+  int* flag;    // P: cnt > 0
+  int* gix;     // P + 1: exclusive scan of flag
+  int* gpose;   // P: the distinct poses, in pose order
+  int* tmp;     // P / 1024 + 2: scan scratch
+  int* ranges;  // 4 per mesh: first hypothesis in order, hypotheses, first entry of gpose, entries
+  int* order;   // n_hyp: hypotheses sorted by pose
+};
+
 // kernels.cu launchers (all asynchronous on `s`)
 cudaError_t launch_fill_u32(uint32_t* p, uint32_t v, long long n, cudaStream_t s);
 cudaError_t launch_obs_count(const float* depth, int W, int H, int* block_counts, cudaStream_t s);
@@ -149,6 +188,19 @@ cudaError_t launch_eval_group(const Camera& cam, const Geometry& g, const ObsInd
                               const int* order, const int* offset, const int* count, int* next, long long max_items,
                               int threads, int sm_count, cudaStream_t s);
 size_t eval_smem_bytes(int tile_w, int tile_h);
+size_t render_smem_bytes(int tile_w, int tile_h);
+size_t cost_smem_bytes(int tile_w, int tile_h);
+// per pose: its tile's size in 16-byte units (screen box area rounded up to 4
+// pixels), exclusive scan into tile_off[P + 1]
+cudaError_t launch_tile_offsets(const Geometry& g, int* sizes, int* tile_off, int* tmp, cudaStream_t s);
+// hypotheses of the batch grouped by pose; writes the bad-index record of a
+// hypothesis with an out-of-range parent or pose (it joins no group) and
+// leaves out those the shortcut answered (b.skip)
+cudaError_t launch_group_by_pose(const Geometry& g, const Batch& b, const PoseGroups& pg, cudaStream_t s);
+cudaError_t launch_render_group(const Camera& cam, const Geometry& g, const Batch& b, const RenderWork& w,
+                                long long max_items, int threads, int sm_count, cudaStream_t s);
+cudaError_t launch_cost_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                              const CostWork& w, long long max_items, int threads, int sm_count, cudaStream_t s);
 // loads the kernels the allocation-free evaluation launches (a lazily loaded
 // module or function would otherwise be loaded, and may allocate, at its
 // first launch)

@@ -760,12 +760,67 @@ __device__ __forceinline__ void raster_box(int2 a, int2 b, int2 c, int A, int px
   }
 }
 
-// One CTA per hypothesis: render the new object into a shared-memory z tile
-// covering its screen box, test it against the parent render (Eq. (3)), and
-// count dJ_r, dJ_o and residual(K) (Sec. IV-A, Eq. (4)).
+struct EvalShared {
+  uint64_t* bar;   // [0]: vertex slice, [1]: triangle list
+  int* cnt;        // viol, n_new, culled, djr, djo, resid, n_vol
+  int* qn;         // queued larger triangles
+  unsigned char* dyn;
+  uint32_t pv, pt;  // parity of the next phase of each barrier
+};
+
+// Outcome of one render or evaluation: done; a bounded wait gave up but
+// every copy it was waiting for has landed since (the record carries
+// kFlagTimeout and the CTA may go on); or a copy may still be in flight (the
+// CTA must stop).
+enum EvalStatus { kEvalDone = 0, kEvalTimedOut = 1, kEvalStop = 2 };
+
+// Dynamic shared memory of a render: the chunk buffers (vertex-table slice,
+// triangle list, projected vertices, queue of larger triangles), then the
+// tile (rows of the pose's box width). Only vbuf and tbuf receive bulk
+// copies; threads never write them.
+struct RenderSmem {
+  float4* vbuf;
+  uint32_t* tbuf;
+  uint32_t* sXY;
+  float* sIZ;
+  uint32_t* queue;  // (triangle, box) pairs
+  uint32_t* tile;
+};
+
+__device__ __forceinline__ RenderSmem render_smem(unsigned char* smem) {
+  RenderSmem s;
+  s.vbuf = reinterpret_cast<float4*>(smem);
+  s.tbuf = reinterpret_cast<uint32_t*>(s.vbuf + kChunkMaxVerts);
+  s.sXY = s.tbuf + kChunkMaxTris;
+  s.sIZ = reinterpret_cast<float*>(s.sXY + kChunkMaxVerts);
+  s.queue = reinterpret_cast<uint32_t*>(s.sIZ + kChunkMaxVerts);
+  s.tile = s.queue + 2 * kBigQueue;
+  return s;
+}
+
+size_t render_smem_bytes(int tile_w, int tile_h) {
+  return (size_t)kChunkMaxVerts * 16 + (size_t)kChunkMaxTris * 4 + (size_t)kChunkMaxVerts * 8 +
+         (size_t)kBigQueue * 8 + (size_t)tile_w * tile_h * 4;
+}
+
+size_t cost_smem_bytes(int tile_w, int tile_h) { return (size_t)tile_w * tile_h * 4 + (size_t)(tile_w + tile_h) * 4; }
+
+// thread 0: start the bulk copies of the first chunk of mesh m at yaw iyaw
+__device__ __forceinline__ void render_start(const Geometry& g, const DevMesh& m, int iyaw, const RenderSmem& s,
+                                             uint64_t* bar) {
+  const float4* V = g.vtab + (size_t)iyaw * g.n_cverts;
+  const int4 ci = g.chunk_info[m.chunk_begin];
+  bulk_load(s.vbuf, V + ci.x, (uint32_t)ci.y * 16u, &bar[0]);
+  bulk_load(s.tbuf, g.chunk_tris + ci.z, (uint32_t)((ci.w + 3) & ~3) * 4u, &bar[1]);
+}
+
+// Render mesh m at pose o into the tile (1/z bits, 0 = empty) covering the
+// pose's screen box bb. The first chunk's copies must have been started
+// (render_start) and the tile cleared before the call; the first CTA barrier
+// inside orders those writes.
 //
-// Rendering walks the mesh in chunks of <= 512 vertices / 1024 triangles. A
-// chunk's camera-frame vertex table slice (M_yaw v) and its triangle list are
+// The mesh is walked in chunks of <= 512 vertices / 1024 triangles. A chunk's
+// camera-frame vertex table slice (M_yaw v) and its triangle list are
 // brought into shared memory by bulk asynchronous copies (TMA); the copy of
 // chunk c+1's vertices is issued as soon as chunk c's vertices are projected,
 // and the copy of its triangles as soon as chunk c's triangles are set up, so
@@ -775,79 +830,27 @@ __device__ __forceinline__ void raster_box(int2 a, int2 b, int2 c, int A, int px
 // are split across a warp. Edge arithmetic stays in int32: every object's
 // screen box is at most kMaxObjectPixels wide (checked at set-up), so
 // tile-relative coordinates (kept as int16 pairs) and all edge-function
-// values are far below 2^31.
-struct EvalShared {
-  uint64_t* bar;   // [0]: vertex slice, [1]: triangle list
-  int* cnt;        // viol, n_new, culled, djr, djo, resid, n_vol
-  int* qn;         // queued larger triangles
-  unsigned char* dyn;
-  uint32_t pv, pt;  // parity of the next phase of each barrier
-};
-
-// Outcome of one evaluation: done; a bounded wait gave up but every copy it
-// was waiting for has landed since (the record carries kFlagTimeout and the
-// CTA may go on); or a copy may still be in flight (the CTA must stop).
-enum EvalStatus { kEvalDone = 0, kEvalTimedOut = 1, kEvalStop = 2 };
-
-// Evaluate hypothesis h with a CTA of NT threads. The CTA's two mbarriers
-// persist across hypotheses (their phase parities are in sh).
-template <int NT, bool MULTI>
-__device__ int eval_one(long long h, const Camera& cam, const Geometry& g, const ObsIndex& obs0, const Batch& b,
-                         EvalShared& sh, ObsIndex* s_obs) {
+// values are far below 2^31. `culled` is set in the threads that dropped a
+// triangle. On kEvalTimedOut / kEvalStop the tile is incomplete; the caller
+// reports the failure and must pass a CTA barrier before reusing the tile.
+template <int NT>
+__device__ __forceinline__ int render_chunks(const Camera& cam, const Geometry& g, const Batch& b, const DevMesh& m,
+                                             const perch_obj& o, int4 bb, const RenderSmem& s, EvalShared& sh,
+                                             unsigned& culled) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint64_t* s_bar = sh.bar;
-  int* s_cnt = sh.cnt;
   int& s_qn = *sh.qn;
-  unsigned char* smem = sh.dyn;
-  const perch_obj o = b.hyp[h];
-  const int pid = b.hyp_parent[h];
-  bool badidx = pid < 0 || pid >= b.n_par || !obj_ok(g, o);
-  const int plen = badidx ? 0 : b.parent_len[pid];
-  badidx = badidx || plen < 0 || plen > b.parent_stride;
-  const int scene = (badidx || !b.parent_scene) ? 0 : b.parent_scene[pid];
-  const int K_total = (badidx || !b.parent_K) ? b.K_total : b.parent_K[pid];
-  badidx = badidx || (b.parent_scene && (scene < 0 || scene >= b.n_scenes));
-  const int4 bb = badidx ? make_int4(0, 0, 0, 0)
-                         : g.pose_bbox[(((long long)o.mesh * g.nx + o.ix) * g.ny + o.iy) * g.n_yaw + o.iyaw];
-  if (badidx || bb.z > b.tile_w || bb.w > b.tile_h) {
-    if (tid == 0) {
-      perch_cost r = {0, 0, 0, 0, 0, kFlagBadIndex, 0};
-      b.out[h] = r;
-    }
-    return kEvalDone;
-  }
-  if (MULTI && tid < (int)(sizeof(ObsIndex) / 4))  // this scene's index, read from shared memory below
-    reinterpret_cast<int*>(s_obs)[tid] = reinterpret_cast<const int*>(&b.scenes[scene])[tid];
-  const ObsIndex& obs = MULTI ? *s_obs : obs0;
-  float4* vbuf = reinterpret_cast<float4*>(smem);
-  uint32_t* tbuf = reinterpret_cast<uint32_t*>(vbuf + kChunkMaxVerts);
-  uint32_t* sXY = tbuf + kChunkMaxTris;
-  float* sIZ = reinterpret_cast<float*>(sXY + kChunkMaxVerts);
-  uint32_t* queue = reinterpret_cast<uint32_t*>(sIZ + kChunkMaxVerts);  // (triangle, box) pairs
-  uint32_t* tile = queue + 2 * kBigQueue;
-  float* rxs = reinterpret_cast<float*>(tile + b.tile_w * b.tile_h);
-  float* rys = rxs + b.tile_w;
+  float4* vbuf = s.vbuf;
+  uint32_t* tbuf = s.tbuf;
+  uint32_t* sXY = s.sXY;
+  float* sIZ = s.sIZ;
+  uint32_t* queue = s.queue;
+  uint32_t* tile = s.tile;
   const int tw = bb.z, th = bb.w;
-
-  const DevMesh m = g.meshes[o.mesh];
   const float4* V = g.vtab + (size_t)o.iyaw * g.n_cverts;
-  if (tid == 0) {  // first chunk
-    const int4 ci = g.chunk_info[m.chunk_begin];
-    bulk_load(vbuf, V + ci.x, (uint32_t)ci.y * 16u, &s_bar[0]);
-    bulk_load(tbuf, g.chunk_tris + ci.z, (uint32_t)((ci.w + 3) & ~3) * 4u, &s_bar[1]);
-  }
-  for (int ly = warp; ly < th; ly += NW)
-    for (int lx = lane; lx < tw; lx += 32) tile[ly * tw + lx] = 0u;  // 1/z = 0: empty
-  for (int i = tid; i < tw; i += NT) rxs[i] = g.rx[bb.x + i];
-  for (int i = tid; i < th; i += NT) rys[i] = g.ry[bb.y + i];
-  if (tid < 7) s_cnt[tid] = 0;
-
-  // ---- render the new object
-  const float ox = g.xs[o.ix], oy = g.ys[o.iy];
   const float4 bo = g.pose_off[o.ix * g.ny + o.iy];
   const int ox16 = 16 * bb.x, oy16 = 16 * bb.y;
-  unsigned culled = 0;
   uint32_t& pv = sh.pv;
   uint32_t& pt = sh.pt;
   bool v_pending = true, t_pending = true;  // a copy in flight on that barrier
@@ -949,11 +952,11 @@ __device__ int eval_one(long long h, const Camera& cam, const Geometry& g, const
     __syncthreads();  // the next chunk reuses sXY, sIZ and the queue
   }
   if (timed_out) {
-    // A wait gave up: report the failure instead of a cost, after draining
-    // every copy still in flight with the full bound (kWaitSpins polls or
-    // 2 s). Once both have landed the barriers' phases are known again and
-    // the CTA may take further work; if a drain also gives up, a copy may
-    // still be writing into this CTA's shared memory and it must stop.
+    // A wait gave up: drain every copy still in flight with the full bound
+    // (kWaitSpins polls or 2 s). Once both have landed the barriers' phases
+    // are known again and the CTA may take further work; if a drain also
+    // gives up, a copy may still be writing into this CTA's shared memory and
+    // it must stop.
     bool ok = true;
     if (v_pending) ok = mbar_wait(&s_bar[0], pv) && ok;
     if (t_pending) ok = mbar_wait(&s_bar[1], pt) && ok;
@@ -962,15 +965,28 @@ __device__ int eval_one(long long h, const Camera& cam, const Geometry& g, const
       if (v_pending) pv ^= 1u;
       if (t_pending) pt ^= 1u;
     }
-    if (tid == 0) {
-      perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout, 0};
-      b.out[h] = r;
-    }
-    __syncthreads();  // s_cnt and the tile are reused by the next hypothesis
     return ok ? kEvalTimedOut : kEvalStop;
   }
-  if (culled) s_cnt[2] = 1;
-  __syncthreads();
+  return kEvalDone;
+}
+
+// Cost of hypothesis h (Eq. (3), Eq. (4)) from its new object's render. src
+// holds the render as 1/z bits (0 = empty) over the pose's box bb, rows of
+// bb.z pixels: the shared tile itself (SRC_GLOBAL = false) or the pose's
+// entry in the tile store in global memory (SRC_GLOBAL = true). The shared
+// tile receives z on dR and +inf elsewhere. rxs / rys hold the ray slopes of
+// the box's columns and rows; s_cnt is zero except the culled flag s_cnt[2];
+// a CTA barrier must separate those writes from the call. Ends with a CTA
+// barrier (s_cnt and the tile may be reused after it).
+template <int NT, bool SRC_GLOBAL>
+__device__ __forceinline__ void cost_phase(long long h, int pid, int plen, int K_total, const perch_obj& o, int4 bb,
+                                           const DevMesh& m, const Camera& cam, const Geometry& g,
+                                           const ObsIndex& obs, const Batch& b, const uint32_t* src,
+                                           uint32_t* tile, const float* rxs, const float* rys, int* s_cnt) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tw = bb.z, th = bb.w;
+  const float ox = g.xs[o.ix], oy = g.ys[o.iy];
 
   // ---- monotone test against the parent render and dR (Eq. (3))
   int viol = 0, nnew = 0;
@@ -978,7 +994,7 @@ __device__ int eval_one(long long h, const Camera& cam, const Geometry& g, const
   for (int ly = warp; ly < th; ly += NW) {
     const float* prow = zp ? zp + (size_t)(bb.y + ly) * cam.W + bb.x : nullptr;
     for (int lx = lane; lx < tw; lx += 32) {
-      const uint32_t izb = tile[ly * tw + lx];
+      const uint32_t izb = SRC_GLOBAL ? __ldg(&src[ly * tw + lx]) : tile[ly * tw + lx];
       if (izb == 0u) {
         tile[ly * tw + lx] = kInfBits;
         continue;
@@ -1010,7 +1026,7 @@ __device__ int eval_one(long long h, const Camera& cam, const Geometry& g, const
       b.out[h] = r;
     }
     __syncthreads();  // s_cnt is reset by the next hypothesis
-    return kEvalDone;
+    return;
   }
 
   // ---- dJ_r: dR points with no observed point within delta
@@ -1080,6 +1096,78 @@ __device__ int eval_one(long long h, const Camera& cam, const Geometry& g, const
     b.out[h] = r;
   }
   __syncthreads();  // s_cnt and the tile are reused by the next hypothesis
+}
+
+// The checks every evaluation of hypothesis h makes before it touches its
+// parent or pose: false means the record is the bad-index record.
+struct HypArgs {
+  perch_obj o;
+  int pid, plen, scene, K_total;
+  long long pose;
+};
+
+__device__ __forceinline__ bool hyp_args(const Geometry& g, const Batch& b, long long h, HypArgs& a) {
+  a.o = b.hyp[h];
+  a.pid = b.hyp_parent[h];
+  bool bad = a.pid < 0 || a.pid >= b.n_par || !obj_ok(g, a.o);
+  a.plen = bad ? 0 : b.parent_len[a.pid];
+  bad = bad || a.plen < 0 || a.plen > b.parent_stride;
+  a.scene = (bad || !b.parent_scene) ? 0 : b.parent_scene[a.pid];
+  a.K_total = (bad || !b.parent_K) ? b.K_total : b.parent_K[a.pid];
+  bad = bad || (b.parent_scene && (a.scene < 0 || a.scene >= b.n_scenes));
+  a.pose = bad ? 0 : (((long long)a.o.mesh * g.nx + a.o.ix) * g.ny + a.o.iy) * g.n_yaw + a.o.iyaw;
+  return !bad;
+}
+
+// One CTA per hypothesis: render the new object into a shared-memory z tile
+// covering its screen box (render_chunks), test it against the parent render
+// (Eq. (3)), and count dJ_r, dJ_o and residual(K) (Sec. IV-A, Eq. (4))
+// (cost_phase). The CTA's two mbarriers persist across hypotheses (their
+// phase parities are in sh).
+template <int NT, bool MULTI>
+__device__ int eval_one(long long h, const Camera& cam, const Geometry& g, const ObsIndex& obs0, const Batch& b,
+                        EvalShared& sh, ObsIndex* s_obs) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int* s_cnt = sh.cnt;
+  HypArgs a;
+  const bool ok = hyp_args(g, b, h, a);
+  const int4 bb = ok ? g.pose_bbox[a.pose] : make_int4(0, 0, 0, 0);
+  if (!ok || bb.z > b.tile_w || bb.w > b.tile_h) {
+    if (tid == 0) {
+      perch_cost r = {0, 0, 0, 0, 0, kFlagBadIndex, 0};
+      b.out[h] = r;
+    }
+    return kEvalDone;
+  }
+  if (MULTI && tid < (int)(sizeof(ObsIndex) / 4))  // this scene's index, read from shared memory below
+    reinterpret_cast<int*>(s_obs)[tid] = reinterpret_cast<const int*>(&b.scenes[a.scene])[tid];
+  const ObsIndex& obs = MULTI ? *s_obs : obs0;
+  const RenderSmem s = render_smem(sh.dyn);
+  float* rxs = reinterpret_cast<float*>(s.tile + b.tile_w * b.tile_h);
+  float* rys = rxs + b.tile_w;
+  const int tw = bb.z, th = bb.w;
+  const DevMesh m = g.meshes[a.o.mesh];
+  if (tid == 0) render_start(g, m, a.o.iyaw, s, sh.bar);
+  for (int ly = warp; ly < th; ly += NW)
+    for (int lx = lane; lx < tw; lx += 32) s.tile[ly * tw + lx] = 0u;  // 1/z = 0: empty
+  for (int i = tid; i < tw; i += NT) rxs[i] = g.rx[bb.x + i];
+  for (int i = tid; i < th; i += NT) rys[i] = g.ry[bb.y + i];
+  if (tid < 7) s_cnt[tid] = 0;
+
+  unsigned culled = 0;
+  const int st = render_chunks<NT>(cam, g, b, m, a.o, bb, s, sh, culled);
+  if (st != kEvalDone) {
+    if (tid == 0) {
+      perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout, 0};
+      b.out[h] = r;
+    }
+    __syncthreads();  // s_cnt and the tile are reused by the next hypothesis
+    return st;
+  }
+  if (culled) s_cnt[2] = 1;
+  __syncthreads();
+  cost_phase<NT, false>(h, a.pid, a.plen, a.K_total, a.o, bb, m, cam, g, obs, b, s.tile, s.tile, rxs, rys, s_cnt);
   return kEvalDone;
 }
 
@@ -1117,6 +1205,118 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_eval(Camera cam, Geometry g, 
     if (item >= count) break;
     const long long h = grp.order ? grp.order[offset + item] : item;
     if (eval_one<NT, MULTI>(h, cam, g, obs, b, sh, &s_obs) == kEvalStop) break;
+  }
+}
+
+// ---- shared renders: one render per distinct pose of a batch, then one
+// cost per hypothesis. The new object's render depends on its mesh and pose
+// alone, not on its parent, so k_render rasterises each distinct (mesh,
+// pose) of the batch once into the tile store (global memory, 1/z bits of
+// the pose's screen box at 16-byte offset tile_off[pose]), and k_cost gives
+// every hypothesis its own comparison with its parent and its own costs
+// from that stored tile, read with plain coalesced loads.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_render(Camera cam, Geometry g, Batch b, RenderWork w) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int s_qn;
+  __shared__ int s_item;
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  EvalShared sh{s_bar, nullptr, &s_qn, smem, 0u, 0u};
+  const RenderSmem s = render_smem(smem);
+  const int count = *w.count, offset = *w.offset;
+  const long long per_x = (long long)g.ny * g.n_yaw, per_mesh = (long long)g.nx * per_x;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(w.next, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= count) break;
+    const long long p = w.gpose[offset + item];
+    perch_obj o;
+    o.mesh = (uint16_t)(p / per_mesh);
+    o.ix = (int16_t)((p / per_x) % g.nx);
+    o.iy = (int16_t)((p / g.n_yaw) % g.ny);
+    o.iyaw = (uint16_t)(p % g.n_yaw);
+    const int4 bb = g.pose_bbox[p];
+    if (bb.z > b.tile_w || bb.w > b.tile_h) {  // never for a valid pose: the mesh's tile is its largest box
+      if (tid == 0) w.pose_flags[p] = kPoseFailed;
+      continue;
+    }
+    const int tw = bb.z, th = bb.w;
+    const DevMesh m = g.meshes[o.mesh];
+    if (tid == 0) render_start(g, m, o.iyaw, s, sh.bar);
+    for (int ly = warp; ly < th; ly += NW)
+      for (int lx = lane; lx < tw; lx += 32) s.tile[ly * tw + lx] = 0u;  // 1/z = 0: empty
+    unsigned culled = 0;
+    const int st = render_chunks<NT>(cam, g, b, m, o, bb, s, sh, culled);
+    if (st != kEvalDone) {
+      if (tid == 0) w.pose_flags[p] = kPoseFailed;
+      __syncthreads();  // the tile is cleared by the next pose
+      if (st == kEvalStop) break;
+      continue;
+    }
+    const int any_culled = __syncthreads_or(culled != 0);
+    uint32_t* dst = w.store + 4 * (size_t)w.tile_off[p];
+    for (int i = tid; i < tw * th; i += NT) dst[i] = s.tile[i];
+    if (tid == 0) w.pose_flags[p] = any_culled ? kPoseCulled : 0;
+    __syncthreads();  // the tile is cleared by the next pose
+  }
+}
+
+template <int NT, bool MULTI>
+__global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex obs0, Batch b, CostWork w) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(16) ObsIndex s_obs;
+  __shared__ int s_cnt[7];
+  __shared__ int s_item;
+  const int tid = threadIdx.x;
+  uint32_t* tile = reinterpret_cast<uint32_t*>(smem);
+  float* rxs = reinterpret_cast<float*>(tile + b.tile_w * b.tile_h);
+  float* rys = rxs + b.tile_w;
+  const int count = *w.count, offset = *w.offset;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(w.next, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= count) break;
+    const long long h = w.order[offset + item];
+    HypArgs a;
+    const bool ok = hyp_args(g, b, h, a);
+    const int4 bb = ok ? g.pose_bbox[a.pose] : make_int4(0, 0, 0, 0);
+    if (!ok || bb.z > b.tile_w || bb.w > b.tile_h) {
+      if (tid == 0) {
+        perch_cost r = {0, 0, 0, 0, 0, kFlagBadIndex, 0};
+        b.out[h] = r;
+      }
+      continue;
+    }
+    const uint8_t pf = w.pose_flags[a.pose];
+    if (pf & kPoseFailed) {  // the render's bounded wait gave up
+      if (tid == 0) {
+        perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout, 0};
+        b.out[h] = r;
+      }
+      continue;
+    }
+    if (MULTI && tid < (int)(sizeof(ObsIndex) / 4))
+      reinterpret_cast<int*>(&s_obs)[tid] = reinterpret_cast<const int*>(&b.scenes[a.scene])[tid];
+    const ObsIndex& obs = MULTI ? s_obs : obs0;
+    for (int i = tid; i < bb.z; i += NT) rxs[i] = g.rx[bb.x + i];
+    for (int i = tid; i < bb.w; i += NT) rys[i] = g.ry[bb.y + i];
+    if (tid < 7) s_cnt[tid] = tid == 2 ? (int)(pf & kPoseCulled) : 0;
+    __syncthreads();
+    const DevMesh m = g.meshes[a.o.mesh];
+    cost_phase<NT, true>(h, a.pid, a.plen, a.K_total, a.o, bb, m, cam, g, obs, b,
+                         w.store + 4 * (size_t)w.tile_off[a.pose], tile, rxs, rys, s_cnt);
   }
 }
 
@@ -1158,6 +1358,82 @@ cudaError_t launch_group_by_mesh(const perch_obj* hyp, long long n, int n_mesh, 
     return e;
   k_group_scatter<<<blocks, 256, 0, s>>>(hyp, n, n_mesh, cursor, order, skip);
   return cudaGetLastError();
+}
+
+// ---- hypotheses grouped by pose, for shared renders: counts per pose ->
+// starts (exclusive scan) -> the distinct poses (scan of cnt > 0) -> each
+// mesh's ranges -> hypotheses placed in their pose's range
+__global__ void k_pose_count(Geometry g, Batch b, int* cnt) {
+  const long long h = blockIdx.x * 256LL + threadIdx.x;
+  if (h >= b.n_hyp || (b.skip && b.skip[h])) return;
+  HypArgs a;
+  if (!hyp_args(g, b, h, a)) {  // the record k_eval would write; joins no group
+    perch_cost r = {0, 0, 0, 0, 0, kFlagBadIndex, 0};
+    b.out[h] = r;
+    return;
+  }
+  atomicAdd(&cnt[a.pose], 1);
+}
+
+__global__ void k_pose_nonzero(const int* cnt, int P, int* flag) {
+  const int p = blockIdx.x * 256 + threadIdx.x;
+  if (p < P) flag[p] = cnt[p] > 0 ? 1 : 0;
+}
+
+__global__ void k_pose_list(const int* cnt, const int* gix, int P, int* gpose) {
+  const int p = blockIdx.x * 256 + threadIdx.x;
+  if (p < P && cnt[p] > 0) gpose[gix[p]] = p;
+}
+
+// mesh m owns poses [m * per_mesh, (m + 1) * per_mesh): its hypotheses are
+// order[start[m * per_mesh] ..) and its distinct poses gpose[gix[m * per_mesh] ..)
+__global__ void k_mesh_ranges(const int* start, const int* gix, int n_mesh, int per_mesh, int* ranges) {
+  const int m = blockIdx.x * 256 + threadIdx.x;
+  if (m >= n_mesh) return;
+  const int a = m * per_mesh, e = a + per_mesh;
+  ranges[4 * m + 0] = start[a];
+  ranges[4 * m + 1] = start[e] - start[a];
+  ranges[4 * m + 2] = gix[a];
+  ranges[4 * m + 3] = gix[e] - gix[a];
+}
+
+__global__ void k_pose_place(Geometry g, Batch b, const int* start, int* cnt, int* order) {
+  const long long h = blockIdx.x * 256LL + threadIdx.x;
+  if (h >= b.n_hyp || (b.skip && b.skip[h])) return;
+  HypArgs a;
+  if (!hyp_args(g, b, h, a)) return;
+  order[start[a.pose] + atomicSub(&cnt[a.pose], 1) - 1] = (int)h;
+}
+
+cudaError_t launch_group_by_pose(const Geometry& g, const Batch& b, const PoseGroups& pg, cudaStream_t s) {
+  const int per_mesh = g.nx * g.ny * g.n_yaw, P = g.n_mesh * per_mesh;
+  const unsigned pb = (unsigned)((P + 255) / 256), hb = (unsigned)((b.n_hyp + 255) / 256);
+  cudaError_t e = cudaMemsetAsync(pg.cnt, 0, sizeof(int) * (size_t)P, s);
+  if (e != cudaSuccess) return e;
+  if (b.n_hyp > 0) k_pose_count<<<hb, 256, 0, s>>>(g, b, pg.cnt);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_exclusive_scan(pg.cnt, pg.start, P, pg.tmp, s)) != cudaSuccess) return e;
+  k_pose_nonzero<<<pb, 256, 0, s>>>(pg.cnt, P, pg.flag);
+  if ((e = launch_exclusive_scan(pg.flag, pg.gix, P, pg.tmp, s)) != cudaSuccess) return e;
+  k_pose_list<<<pb, 256, 0, s>>>(pg.cnt, pg.gix, P, pg.gpose);
+  k_mesh_ranges<<<(unsigned)((g.n_mesh + 255) / 256), 256, 0, s>>>(pg.start, pg.gix, g.n_mesh, per_mesh, pg.ranges);
+  if (b.n_hyp > 0) k_pose_place<<<hb, 256, 0, s>>>(g, b, pg.start, pg.cnt, pg.order);
+  return cudaGetLastError();
+}
+
+__global__ void k_tile_sizes(Geometry g, int P, int* sizes) {
+  const int p = blockIdx.x * 256 + threadIdx.x;
+  if (p >= P) return;
+  const int4 bb = g.pose_bbox[p];
+  sizes[p] = (bb.z * bb.w + 3) >> 2;  // 16-byte units: every tile starts 16-byte aligned
+}
+
+cudaError_t launch_tile_offsets(const Geometry& g, int* sizes, int* tile_off, int* tmp, cudaStream_t s) {
+  const int P = g.n_mesh * g.nx * g.ny * g.n_yaw;
+  k_tile_sizes<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(g, P, sizes);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_exclusive_scan(sizes, tile_off, P, tmp, s);
 }
 
 // ------------------------------------------------------------ exact shortcut
@@ -1319,6 +1595,68 @@ static cudaError_t launch_group_t(const Camera& cam, const Geometry& g, const Ob
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, NT, smem, s>>>(cam, g, obs, b, grp);
   return cudaGetLastError();
+}
+
+template <int NT>
+static cudaError_t launch_render_t(const Camera& cam, const Geometry& g, const Batch& b, const RenderWork& w,
+                                   long long max_items, int sm_count, cudaStream_t s) {
+  const size_t smem = render_smem_bytes(b.tile_w, b.tile_h);
+  auto kern = k_render<NT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long grid = (long long)per_sm * sm_count;
+  if (grid > max_items) grid = max_items;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, NT, smem, s>>>(cam, g, b, w);
+  return cudaGetLastError();
+}
+
+// One persistent launch rendering one mesh's distinct poses of a batch into
+// the tile store, with CTAs of `threads` (128, 256 or 512) and the mesh's
+// tile (b.tile_w x b.tile_h).
+cudaError_t launch_render_group(const Camera& cam, const Geometry& g, const Batch& b, const RenderWork& w,
+                                long long max_items, int threads, int sm_count, cudaStream_t s) {
+  if (max_items <= 0) return cudaSuccess;
+  switch (threads) {
+    case 128: return launch_render_t<128>(cam, g, b, w, max_items, sm_count, s);
+    case 512: return launch_render_t<512>(cam, g, b, w, max_items, sm_count, s);
+    default: return launch_render_t<256>(cam, g, b, w, max_items, sm_count, s);
+  }
+}
+
+template <int NT, bool MULTI>
+static cudaError_t launch_cost_t(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                                 const CostWork& w, long long max_items, int sm_count, cudaStream_t s) {
+  const size_t smem = cost_smem_bytes(b.tile_w, b.tile_h);
+  auto kern = k_cost<NT, MULTI>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long grid = (long long)per_sm * sm_count;
+  if (grid > max_items) grid = max_items;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, NT, smem, s>>>(cam, g, obs, b, w);
+  return cudaGetLastError();
+}
+
+// One persistent launch costing one mesh's hypotheses of a batch from the
+// tile store, with CTAs of `threads` (128 or 256).
+cudaError_t launch_cost_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                              const CostWork& w, long long max_items, int threads, int sm_count, cudaStream_t s) {
+  if (max_items <= 0) return cudaSuccess;
+  const bool multi = b.parent_scene != nullptr;
+  if (threads == 256)
+    return multi ? launch_cost_t<256, true>(cam, g, obs, b, w, max_items, sm_count, s)
+                 : launch_cost_t<256, false>(cam, g, obs, b, w, max_items, sm_count, s);
+  return multi ? launch_cost_t<128, true>(cam, g, obs, b, w, max_items, sm_count, s)
+               : launch_cost_t<128, false>(cam, g, obs, b, w, max_items, sm_count, s);
 }
 
 // One persistent launch for one group of hypotheses with CTAs of `threads`

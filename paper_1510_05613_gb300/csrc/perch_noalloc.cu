@@ -62,12 +62,7 @@ int noalloc_prepare(perch_ctx* ctx) {
   if (e != cudaSuccess) return ctx->cuda(e, "cudaGetSymbolAddress(noalloc scratch)");
   e = preload_eval_kernels();
   if (e != cudaSuccess) return ctx->cuda(e, "load evaluation kernels");
-  if (!ctx->ev[0])
-    for (int k = 0; k < 3; ++k) {
-      e = cudaEventCreate(&ctx->ev[k]);
-      if (e != cudaSuccess) return ctx->cuda(e, "cudaEventCreate");
-    }
-  return PERCH_OK;
+  return ctx->create_events();
 }
 
 extern "C" int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride,
@@ -137,6 +132,8 @@ extern "C" int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* pa
   if (e != cudaSuccess) return ctx->cuda(e, "residual sets");
   e = cudaEventRecord(ctx->ev[1], ctx->stream);
   if (e != cudaSuccess) return ctx->cuda(e, "event");
+  e = cudaEventRecord(ctx->ev[2], ctx->stream);  // no grouping: every hypothesis in one launch
+  if (e != cudaSuccess) return ctx->cuda(e, "event");
   e = launch_fill_u32(reinterpret_cast<uint32_t*>(item_count), (uint32_t)n_hyp, 1, ctx->stream);
   if (e != cudaSuccess) return ctx->cuda(e, "item count");
   e = launch_fill_u32(reinterpret_cast<uint32_t*>(item_next), 0u, 1, ctx->stream);
@@ -144,8 +141,11 @@ extern "C" int perch_eval_successors_noalloc(perch_ctx* ctx, const perch_obj* pa
   e = launch_eval_group(ctx->cam, g, ctx->obs, b, nullptr, nullptr, item_count, item_next, n_hyp, 256,
                         ctx->sm_count, ctx->stream);
   if (e != cudaSuccess) return ctx->cuda(e, "eval kernel");
-  e = cudaEventRecord(ctx->ev[2], ctx->stream);
+  e = cudaEventRecord(ctx->ev[3], ctx->stream);
+  if (e != cudaSuccess) return ctx->cuda(e, "event");
+  e = cudaEventRecord(ctx->ev[4], ctx->stream);
   if (e != cudaSuccess) return ctx->cuda(e, "event");
   ctx->timed = true;  // perch_last_timing: prep = clears, parent renders, U sets; eval = the kernel
+  ctx->last_path = 1;
   return PERCH_OK;
 }

@@ -14,18 +14,25 @@
 // perch_search_multi runs one such search per scene and packs the expansions
 // of all unfinished scenes into shared evaluation launches.
 //
-// Learned queue (heuristics bit 2, not in the paper's experiments): every
-// expansion keeps, per remaining object type, its `n_candidates` cheapest valid
-// placements and their exact edge costs. A child s' gets the free estimate
-// h_free(s') = sum over its remaining objects of the cheapest exact cost of
-// that type at the parent; the queue's pool holds focal states ordered by
-// depth (deepest first, so its expansions have few remaining types and stay
-// cheap), then g + h_free. Each round the front of the pool is re-ranked,
-// within each depth, by g + h_cnn, where
+// Learned queue (heuristics bit 2 or 3, not in the paper's experiments):
+// every expansion keeps, per remaining object type, its `n_candidates`
+// cheapest valid placements and their exact edge costs. A child s' gets the
+// free estimate h_free(s') = sum over its remaining objects of the cheapest
+// exact cost of that type at the parent, and the learned estimate
 // h_cnn(s') = sum over the remaining objects of min over the parent's
 // candidates of that type of (exp(prediction) - 1), the network's edge-cost
-// estimate with s' itself as the parent (its z-buffer in the crop). States are
-// scored once, lazily, in one batch across scenes.
+// estimate with s' itself as the parent (its z-buffer in the crop). h_cnn
+// takes a forward pass, so states are scored lazily: each round the queue
+// takes a pool of its front states (max(16, 2 batch_states)), scores the
+// unscored ones in one batch across scenes, expands the pool's best
+// batch_states states and returns the rest.
+//   bit 2: the queue is ordered by g + h_free across depths (ties: deeper
+//          first) and the pool's states are expanded in order of g + h_cnn,
+//          both estimates of the cost of the whole scene, so the network's
+//          ranking decides between states of any depth.
+//   bit 3: the queue is ordered deepest first, then by g + h_free, and the
+//          pool is re-ranked by g + h_cnn only within a depth (a depth-first
+//          dive that the network steers among siblings).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -169,7 +176,7 @@ struct SceneSearch {
   bool done = false;
   double seconds = 0.0;
   double w = 1.0;
-  int heur = 0;                        // bit 0: h_depth, bit 1: h_overlap, bit 2: learned
+  int heur = 0;                        // bit 0: h_depth, bit 1: h_overlap, bit 2 / 3: learned
   std::vector<OpenEntry> pending;      // generated, not yet in the focal set (min g)
   std::vector<HEntry> hq[3];           // focal states ordered by each heuristic
   std::vector<ExpansionRecord> exps;   // learned queue: one per expanded state
@@ -177,10 +184,13 @@ struct SceneSearch {
   int T = 16;                          // learned queue: placements kept per type
   bool bad_record = false;             // a record carried no cost (flags bit 30 or 31)
   bool focal() const { return w > 1.0 || heur != 0; }
+  bool learned() const { return (heur & 12) != 0; }
+  bool dive() const { return (heur & 8) != 0; }  // the depth-first learned queue
   int64_t hval(int which, int idx) const {
-    if (which == 2) {  // deepest first, then g + the free estimate
+    if (which == 2) {
       const int64_t f = std::min<int64_t>(states[idx].g + states[idx].h_free, ((int64_t)1 << 40) - 1);
-      return ((int64_t)(K - (int)states[idx].depth) << 40) | f;
+      if (dive()) return ((int64_t)(K - (int)states[idx].depth) << 40) | f;  // deepest first, then g + h_free
+      return (f << 5) | (int64_t)(31 - std::min<int>(states[idx].depth, 31));  // g + h_free; ties: deeper first
     }
     return which == 0 ? (int64_t)(K - (int)states[idx].depth) : states[idx].h_overlap;
   }
@@ -263,7 +273,7 @@ struct SceneSearch {
       pending.pop_back();
       if (stale(e)) continue;
       for (int q = 0; q < 3; ++q)
-        if (heur & (1 << q)) {
+        if (q == 2 ? learned() : (heur & (1 << q)) != 0) {
           hq[q].push_back(HEntry{hval(q, e.idx), e.g, e.idx});
           std::push_heap(hq[q].begin(), hq[q].end(), hworse);
         }
@@ -290,7 +300,7 @@ struct SceneSearch {
         ++n;
       }
     }
-    if (heur & 4) {  // learned queue: gather the pool; the caller scores it and calls choose()
+    if (learned()) {  // learned queue: gather the pool; the caller scores it and calls choose()
       const int L = std::max(16, 2 * B);
       pool.clear();
       while ((int)pool.size() < L && !hq[2].empty()) {
@@ -310,11 +320,13 @@ struct SceneSearch {
     std::vector<int> live;
     for (int idx : pool)
       if (!states[idx].closed) live.push_back(idx);
-    std::sort(live.begin(), live.end(), [this](int a, int b) {
+    const bool by_depth = dive();
+    std::sort(live.begin(), live.end(), [this, by_depth](int a, int b) {
       const size_t da = states[a].depth, db = states[b].depth;
-      if (da != db) return da > db;  // deepest first, as the pool
+      if (by_depth && da != db) return da > db;  // deepest first, as the pool
       const double fa = (double)states[a].g + states[a].h_cnn, fb = (double)states[b].g + states[b].h_cnn;
       if (fa != fb) return fa < fb;
+      if (da != db) return da > db;
       return a < b;
     });
     for (size_t k = 0; k < live.size(); ++k) {
@@ -446,14 +458,14 @@ struct SceneSearch {
       c.depth = (uint8_t)(ps.depth + 1);
       states.push_back(c);
       index.insert(h0, idx);
-      if (heur & 4) set_parent(idx, pidx, h);
+      if (learned()) set_parent(idx, pidx, h);
       add_open(ng, idx);
     } else {
       State& s = states[found];
       if (ng < s.g) {
         s.g = ng;
         s.closed = false;  // a cheaper way in: reopen
-        if ((heur & 4) && s.parent != pidx) set_parent(found, pidx, h);
+        if (learned() && s.parent != pidx) set_parent(found, pidx, h);
         add_open(ng, found);
       }
     }
@@ -596,7 +608,7 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
       any_pool |= !s.pool.empty();
     }
     if (any_pool) {  // learned queue: score the pools, then take each scene's best
-      if (!ctx->net) return ctx->fail(PERCH_E_STATE, "search: heuristic bit 2 needs perch_set_heuristic_net");
+      if (!ctx->net) return ctx->fail(PERCH_E_STATE, "search: heuristic bits 2 and 3 need perch_set_heuristic_net");
       const auto ts = Clock::now();
       const int rc = score_pools(ctx, ss);
       ctx->net_seconds += std::chrono::duration<double>(Clock::now() - ts).count();
@@ -680,7 +692,7 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
         SceneSearch& s = ss[si];
         for (int w : by_scene[si]) {
           s.expansions++;
-          if (s.heur & 4)
+          if (s.learned())
             s.record_expansion(work[w].state, hyps.data() + hbeg[w], out.data() + hbeg[w],
                                (long long)(hbeg[w + 1] - hbeg[w]));
         }
@@ -722,9 +734,10 @@ int check_params(perch_ctx* ctx, const perch_search_params* prm) {
   if (!prm || prm->K < 1 || prm->K > 16 || !prm->mesh_multiset || prm->batch_states < 1)
     return ctx->fail(PERCH_E_ARG, "search: bad parameters");
   if (!(prm->w >= 1.0f)) return ctx->fail(PERCH_E_ARG, "search: w must be >= 1");
-  if (prm->heuristics & ~7) return ctx->fail(PERCH_E_ARG, "search: unknown heuristic bits %d", prm->heuristics);
-  if ((prm->heuristics & 4) && !ctx->net)
-    return ctx->fail(PERCH_E_STATE, "search: heuristic bit 2 needs perch_set_heuristic_net");
+  if (prm->heuristics & ~15) return ctx->fail(PERCH_E_ARG, "search: unknown heuristic bits %d", prm->heuristics);
+  if ((prm->heuristics & 12) == 12) return ctx->fail(PERCH_E_ARG, "search: heuristic bits 2 and 3 exclude each other");
+  if ((prm->heuristics & 12) && !ctx->net)
+    return ctx->fail(PERCH_E_STATE, "search: heuristic bits 2 and 3 need perch_set_heuristic_net");
   for (int i = 0; i < prm->K; ++i)
     if (prm->mesh_multiset[i] >= ctx->n_mesh) return ctx->fail(PERCH_E_ARG, "search: mesh %d out of range", i);
   return PERCH_OK;

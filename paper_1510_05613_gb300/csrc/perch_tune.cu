@@ -104,10 +104,11 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
           ctx->mesh_threads = saved;
           return rc;
         }
-        float a = 0.0f, b = 0.0f;
-        CK(cudaEventSynchronize(ctx->ev[2]), "event sync");
-        CK(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]), "event time");
-        CK(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]), "event time");
+        // the render phase: the per-mesh launches the width applies to (the
+        // shared-render k_render, or k_eval when every hypothesis is rendered)
+        float b = 0.0f;
+        CK(cudaEventSynchronize(ctx->ev[4]), "event sync");
+        CK(cudaEventElapsedTime(&b, ctx->ev[2], ctx->ev[3]), "event time");
         if (rep > 0) ms = std::min(ms, b);  // the first launch of a width also loads its code
       }
       if (ms < best_ms) {

@@ -32,7 +32,7 @@ EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_mesh
            "perch_cnn_forward", "perch_cnn_train_step", "perch_cnn_gradients", "perch_set_heuristic_net",
            "perch_cnn_set_tensor_path", "perch_cnn_tensor_status",
            "perch_set_shortcut", "perch_shortcut_stats", "perch_search_stats", "perch_search_times",
-           "perch_set_wait_limit")
+           "perch_set_wait_limit", "perch_set_share_renders", "perch_last_phase_times")
 
 
 class perch_mesh(ctypes.Structure):
@@ -109,6 +109,8 @@ def load(path: str = LIB_PATH):
         "perch_set_heuristic_net": ([P, P, I32], ctypes.c_int),
         "perch_set_shortcut": ([P, I32], ctypes.c_int),
         "perch_set_wait_limit": ([P, I32], ctypes.c_int),
+        "perch_set_share_renders": ([P, I32], ctypes.c_int),
+        "perch_last_phase_times": ([P, P, P], ctypes.c_int),
         "perch_search_stats": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "perch_search_times": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -298,6 +300,17 @@ class Perch:
         """Attach a PerchCNN (None detaches) for search heuristic bit 2."""
         self._net = net  # keep it alive while attached
         return self._check(self.lib.perch_set_heuristic_net(self.h, None if net is None else net.h, n_candidates))
+
+    def perch_set_share_renders(self, on: bool):
+        """One render per distinct pose of a batch (on by default)."""
+        return self._check(self.lib.perch_set_share_renders(self.h, 1 if on else 0))
+
+    def perch_last_phase_times(self):
+        """(ms per phase [prep, grouping, render, cost], shared renders used)."""
+        ms = np.zeros(4, np.float32)
+        shared = ctypes.c_int32(0)
+        self._check(self.lib.perch_last_phase_times(self.h, ms.ctypes.data, ctypes.byref(shared)))
+        return ms.astype(np.float64), bool(shared.value)
 
     def perch_set_wait_limit(self, polls: int):
         """Poll bound of the evaluation kernel's first wait per bulk copy

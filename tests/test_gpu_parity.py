@@ -135,6 +135,42 @@ def test_c2_bench_launch_sampled(c2):
     assert np.array_equal(got[idx], exp)
 
 
+def test_shared_renders_identical_to_per_hypothesis_renders(c2):
+    """A successor's new-object render depends on its mesh and pose alone
+    (Sec. III-A, R_j), so rendering each distinct pose of a batch once and
+    costing every hypothesis from that tile must give the records of
+    rendering every hypothesis: checked on a batch whose poses repeat over
+    four parents (root, middle level, last level), with the exact shortcut
+    off and on, and against the oracle on a sample."""
+    wl, p, w = c2
+    rng = np.random.default_rng(21)
+    parents = [wl.gt[:0], wl.gt[:1], wl.gt[:2], wl.gt[1:2]]
+    allh = synth.all_hypotheses(wl.grid, [0, 1, 2])
+    poses = allh[rng.choice(len(allh), 2500, replace=False)]
+    near = np.concatenate([wl.gt, allh[np.isin(allh["ix"], wl.gt["ix"]) & np.isin(allh["iy"], wl.gt["iy"])][:500]])
+    poses = np.concatenate([poses, near])
+    reps = rng.integers(1, 5, len(poses))  # 1-4 parents per pose
+    hyps = np.repeat(poses, reps)
+    hp = np.concatenate([rng.choice(4, r, replace=False) for r in reps]).astype(np.int32)
+    try:
+        for short in (False, True):
+            p.perch_set_shortcut(short)
+            p.perch_set_share_renders(True)
+            a = _recs(p.perch_eval_successors(parents, hp, hyps, wl.K))
+            assert p.perch_last_phase_times()[1]
+            p.perch_set_share_renders(False)
+            b = _recs(p.perch_eval_successors(parents, hp, hyps, wl.K))
+            assert not p.perch_last_phase_times()[1]
+            assert np.array_equal(a, b)
+    finally:
+        p.perch_set_shortcut(True)
+        p.perch_set_share_renders(True)
+    pick = rng.choice(len(hyps), 150, replace=False)
+    exp = oracle.eval_batch(w, wl.depth, parents, hp[pick], hyps[pick], wl.K)
+    assert np.array_equal(a[pick], exp)
+    assert (a[:, 3] > 0).any() and (a[:, 2] > 0).any() and (a[:, 1] > 0).any()
+
+
 def test_shortcut_records_identical_and_taken(c2):
     """The exact shortcut (hypotheses far from the observation and from the
     parent's render) gives the same records as rendering every hypothesis,

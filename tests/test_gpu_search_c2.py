@@ -1,0 +1,69 @@
+"""GPU tree search against the oracle's exact search at 640x480 (Sec. IV-B:
+uniform-cost search with h0 = 0 and w = 1 returns a minimum-cost scene;
+Sec. IV-D, Theorems 1 and 2 for Focal-MHA*).
+
+The oracle's answers on the three-object 640x480 workload with its pose grid
+reduced to 8 x 8 positions x 4 yaws are stored in
+tests/golden/search_c2_reduced.json, written by
+tests/golden/make_search_c2_reduced.py (it calls only oracle/; about five
+minutes per scene on eight cores). The GPU search must return the same cost
+and the same scene (ties broken by the smallest sorted key), with every batch
+size and with the exact shortcut off; Focal-MHA* must stay within w times
+that cost.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1510_05613_gb300 import perch, synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "search_c2_reduced.json")
+
+
+def _golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def _workload(g, scene):
+    gr = g["grid"]
+    return synth.workload_c2(scene=scene, grid=synth.pose_grid(gr["x0"], gr["step"], gr["n"], gr["n_yaw"]))
+
+
+@pytest.mark.parametrize("scene", [0, 1])
+def test_gpu_search_equals_oracle_search_c2_reduced(scene):
+    g = _golden()
+    exp = next(s for s in g["scenes"] if s["scene"] == scene)
+    wl = _workload(g, scene)
+    key = tuple(tuple(o) for o in exp["key"])
+    p = perch.Perch(0)
+    p.setup(wl)
+    try:
+        for B, short in ((1, True), (8, True), (64, False)):
+            p.perch_set_shortcut(short)
+            r = p.perch_search(wl.mesh_multiset, batch_states=B)
+            assert r["proven_optimal"]
+            assert (r["cost"], r["key"]) == (exp["cost"], key), (B, short, r["cost"], r["key"])
+        p.perch_set_shortcut(True)
+        for w in (1.5, 3.0):
+            r = p.perch_search(wl.mesh_multiset, w=w, batch_states=8, heuristics=3)
+            assert 0 <= r["cost"] <= w * exp["cost"]
+    finally:
+        p.close()
+    # the returned scene's cost, recomputed by the oracle along one valid order
+    w_or = oracle.World.of(wl)
+    objs = synth.objs(list(key))
+    for order in ([0, 1, 2], [2, 1, 0], [1, 0, 2], [0, 2, 1], [1, 2, 0], [2, 0, 1]):
+        seq = objs[order]
+        recs = [oracle.eval_batch(w_or, wl.depth, [seq[:j]], np.zeros(1, np.int32), seq[j:j + 1], 3)[0]
+                for j in range(3)]
+        if all(r[3] == 0 for r in recs):
+            assert sum(int(r[0] + r[1] + r[2]) for r in recs) == exp["cost"]
+            break
+    else:
+        raise AssertionError("no valid order of the returned scene")
