@@ -71,6 +71,33 @@ typedef struct {
   float vol_r, vol_zlo, vol_zhi;
 } perch_mesh;
 
+/* V(O) of one mesh in closed form (Sec. III-A: the set of points in the
+ * volume the object occupies; the inscribed cylinder of perch_mesh stands in
+ * where there is no closed form), in the object frame (z up, base on z = 0,
+ * yaw about the z axis):
+ *   kind 0: the inscribed cylinder of perch_mesh (the default);
+ *   kind 1: box |x| <= p[0], |y| <= p[1], zlo <= z <= zhi;
+ *   kind 2: regular prism of n sides (3..256): normals[k] . (x, y) <= p[1]
+ *           (the apothem) for every face k, zlo <= z <= zhi; normals = n
+ *           (cos, sin) pairs, the unit outward face normals in order of
+ *           angle, 2 pi / n apart (checked to 2e-7 rad); p[0] unused;
+ *   kind 3: superquadric with semi-axes p[0..2] and centre height p[3]:
+ *           n = 1: X^2 + Y^2 + Z^2 <= 1 (ellipsoid); n = 2:
+ *           (X^2 + Y^2)^2 + Z^4 <= 1 (eps1 = 0.5, eps2 = 1), where
+ *           X = x (1/p[0]), Y = y (1/p[1]), Z = (z - p[3]) (1/p[2]) with the
+ *           reciprocals computed in double and rounded to binary32;
+ *           t = fma(Y, Y, X X), F = fma(t, t, Z^2 Z^2) (n = 2) or t + Z^2.
+ * A world point enters the object frame through the pose table's (c, s):
+ * x = fma(s, dy, c dx), y = fma(c, dy, -(s dx)) with (dx, dy) its offset
+ * from the pose's (x, y); z is its world height. */
+typedef struct {
+  int32_t kind;
+  int32_t n;
+  float p[4];
+  float zlo, zhi;
+  const float* normals; /* kind 2: n x 2 */
+} perch_volume;
+
 /* One object state O = (ID, x, y, theta) of Sec. III-A, as indices into the
  * pose grid: x = xs[ix], y = ys[iy], (cos, sin) = cos_sin[iyaw]. 8 bytes. */
 typedef struct {
@@ -125,6 +152,25 @@ const char* perch_last_error(const perch_ctx* ctx);
  * vertices and 1024 triangles each). Errors: PERCH_E_ARG for empty meshes,
  * out-of-range indices or n < 1. */
 int perch_load_meshes(perch_ctx* ctx, const perch_mesh* meshes, int32_t n);
+
+/* V(O) of every mesh (volumes[n], n = the number of meshes loaded), used by
+ * dJ_o, the residual and n_vol from the next evaluation on; volumes = NULL
+ * restores the inscribed cylinders. Copied. perch_load_meshes resets to the
+ * cylinders. PERCH_E_ARG for a bad kind, side count, normal table or
+ * parameter; PERCH_E_STATE before perch_load_meshes. */
+int perch_set_volumes(perch_ctx* ctx, const perch_volume* volumes, int32_t n);
+
+/* Rotational symmetry of the meshes for the search (Sec. IV-E: for a
+ * rotationally symmetric object only (x, y) matters): sym[m] = s means mesh m
+ * is the same vertex set after a turn of 2 pi / s about its vertical axis
+ * (1 = no symmetry). The search then places mesh m only at the yaws of the
+ * pose grid that no smaller yaw index equals modulo 2 pi / s (compared in
+ * double from the yaw table), which removes the other yaws of each
+ * equivalence class from the tree: the returned scene is the optimum of that
+ * smaller tree (a rotated mesh's binary32 vertices, hence its render, can
+ * differ in the last bit). sym = NULL: no symmetry (the default, also after
+ * perch_load_meshes). Evaluation calls are unaffected. */
+int perch_set_symmetry(perch_ctx* ctx, const int32_t* sym, int32_t n);
 
 /* Discretised 3-DoF poses (Sec. III; Sec. V-B discretises x, y and yaw):
  * xs[nx], ys[ny] in metres, cos_sin[2 * n_yaw] = (cos, sin) per yaw. The
@@ -251,6 +297,8 @@ typedef struct {
   int64_t successors;   /* hypotheses evaluated */
   double seconds;
   int32_t proven_optimal;
+  double found_seconds;     /* when the returned scene was first found (its records absorbed) */
+  int64_t found_expansions; /* states expanded by then */
 } perch_result;
 
 int perch_search(perch_ctx* ctx, const perch_search_params* params, perch_result* result);
@@ -291,6 +339,12 @@ int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads_out);
 /* Set the CTA width (128, 256 or 512) used for one mesh (mesh = -1: all
  * meshes), overriding the default 256 or an autotuned choice. */
 int perch_set_threads(perch_ctx* ctx, int32_t mesh, int32_t threads);
+
+/* The launch configuration evaluations use now, per mesh (arrays of the
+ * number of meshes, either may be NULL): the CTA width of the render (or
+ * per-hypothesis evaluation) launch and of the cost launch. perch_autotune
+ * times both with shared renders on (the cost width among 128 and 256). */
+int perch_launch_config(perch_ctx* ctx, int32_t* render_threads, int32_t* cost_threads);
 
 /* Same work and arguments as perch_eval_successors_dev (device pointers), run
  * as a CUDA graph: the first call for a given argument set (and after any

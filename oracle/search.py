@@ -21,6 +21,7 @@ Readings where the paper is silent:
 from __future__ import annotations
 
 import heapq
+import math
 import itertools
 from collections import Counter
 
@@ -33,9 +34,34 @@ def key_of(objs) -> tuple:
     return tuple(sorted((int(o["mesh"]), int(o["ix"]), int(o["iy"]), int(o["iyaw"])) for o in objs))
 
 
-def _children(grid, remaining_types):
+def symmetric_yaws(grid, syms):
+    """Per mesh, the yaw indices a search over a symmetric mesh keeps: yaw k
+    is dropped when a smaller index j has theta_k - theta_j a multiple of
+    2 pi / sym (Sec. IV-E: a rotationally symmetric object needs only (x, y));
+    angles from the pose table's (cos, sin) in double, to 1e-6 of a period."""
+    th = [math.atan2(float(s), float(c)) for c, s in grid.cos_sin]
+    out = {}
+    for m, sym in enumerate(syms):
+        keep = []
+        for k in range(len(th)):
+            if not any(abs(t - round(t)) < 1e-6 for t in ((th[k] - th[j]) * max(int(sym), 1) / (2 * math.pi)
+                                                           for j in keep)):
+                keep.append(k)
+        out[m] = keep
+    return out
+
+
+def _children(grid, remaining_types, yaws=None):
+    """Every pose of every remaining type (yaws: per mesh the yaw indices to
+    keep, None = all)."""
     from paper_1510_05613_gb300.synth import all_hypotheses
-    return all_hypotheses(grid, sorted(set(remaining_types)))
+    h = all_hypotheses(grid, sorted(set(remaining_types)))
+    if yaws is None:
+        return h
+    keep = np.zeros(len(h), bool)
+    for m, ks in yaws.items():
+        keep |= (h["mesh"] == m) & np.isin(h["iyaw"], ks)
+    return h[keep]
 
 
 def _remaining(multiset, placed):
@@ -44,8 +70,10 @@ def _remaining(multiset, placed):
     return [m for m, n in c.items() for _ in range(n) if n > 0]
 
 
-def uniform_cost_search(world, depth, grid, multiset, threads: int = 0, max_expansions: int = 10 ** 7):
-    """Dijkstra (A* with h = 0) over set-keyed MSGT states.
+def uniform_cost_search(world, depth, grid, multiset, threads: int = 0, max_expansions: int = 10 ** 7,
+                        yaws=None):
+    """Dijkstra (A* with h = 0) over set-keyed MSGT states. yaws: per mesh
+    the yaw indices the tree places it at (symmetric_yaws), None = all.
 
     Returns (cost, goal_key, expansions)."""
     from paper_1510_05613_gb300.synth import OBJ_DTYPE
@@ -73,7 +101,7 @@ def uniform_cost_search(world, depth, grid, multiset, threads: int = 0, max_expa
         expansions += 1
         if expansions > max_expansions:
             raise RuntimeError("expansion limit")
-        hyps = _children(grid, _remaining(multiset, s))
+        hyps = _children(grid, _remaining(multiset, s), yaws)
         recs = eval_batch(world, depth, [s], np.zeros(len(hyps), np.int32), hyps, K, threads)
         for h, r in zip(hyps, recs):
             if r[3] > 0:

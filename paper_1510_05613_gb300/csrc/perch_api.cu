@@ -91,7 +91,14 @@ Geometry perch_ctx::geometry() const {
   g.pose_bbox = pose_bbox.as<int4>();
   g.rx = rx.as<float>();
   g.ry = ry.as<float>();
+  g.vol_normals = vol_normals.as<float2>();
   return g;
+}
+
+// radius of the footprint disk the exact shortcut and the dJ_o candidate
+// search use: it must hold every vertex and all of V(O)
+static float footprint_radius(double vert_r, double vol_rmax) {
+  return (float)(std::max(vert_r, vol_rmax) * (1.0 + 1e-6)) + 1e-6f;
 }
 
 #define CK(expr, what)                          \
@@ -149,6 +156,7 @@ int perch_ctx::ensure_tables() {
   if (!eval_tile_fits(device, tile_w, tile_h))
     return fail(PERCH_E_RANGE, "object screen box %dx%d does not fit in shared memory", tile_w, tile_h);
   if ((int)mesh_threads.size() != n_mesh) mesh_threads.assign(n_mesh, 256);
+  if ((int)mesh_cost_threads.size() != n_mesh) mesh_cost_threads.assign(n_mesh, 128);
   const int rc = ensure_tile_store();
   if (rc != PERCH_OK) return rc;
   tables_valid = true;
@@ -395,6 +403,7 @@ int perch_load_meshes(perch_ctx* ctx, const perch_mesh* meshes, int32_t n) {
   if (!meshes || n < 1 || n > 65535) return ctx->fail(PERCH_E_ARG, "need 1..65535 meshes, got %d", n);
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   std::vector<DevMesh> dm(n);
+  std::vector<double> vert_r(n, 0.0);
   std::vector<float4> verts;
   std::vector<int4> info;
   std::vector<uint32_t> tris;
@@ -415,10 +424,17 @@ int perch_load_meshes(perch_ctx* ctx, const perch_mesh* meshes, int32_t n) {
       d.lo[k] = INFINITY;
       d.hi[k] = -INFINITY;
     }
-    double fp2 = (double)m.vol_r * (double)m.vol_r;
+    double vr2 = 0.0;
     for (int v = 0; v < m.n_verts; ++v)
-      fp2 = std::max(fp2, (double)m.verts[3 * v] * m.verts[3 * v] + (double)m.verts[3 * v + 1] * m.verts[3 * v + 1]);
-    d.fp_r = (float)(std::sqrt(fp2) * (1.0 + 1e-6)) + 1e-6f;
+      vr2 = std::max(vr2, (double)m.verts[3 * v] * m.verts[3 * v] + (double)m.verts[3 * v + 1] * m.verts[3 * v + 1]);
+    vert_r[i] = std::sqrt(vr2);
+    d.vol_kind = 0;
+    d.vol_n = 0;
+    d.vol_nrm = 0;
+    d.vol_z0 = d.vol_z1 = 0.0f;
+    for (int k = 0; k < 4; ++k) d.vol_p[k] = 0.0f;
+    d.vol_rmax = m.vol_r;
+    d.fp_r = footprint_radius(vert_r[i], m.vol_r);
     for (int v = 0; v < m.n_verts; ++v)
       for (int k = 0; k < 3; ++k) {
         float x = m.verts[3 * v + k];
@@ -486,7 +502,11 @@ int perch_load_meshes(perch_ctx* ctx, const perch_mesh* meshes, int32_t n) {
                      ctx->stream), "copy");
   CK(cudaStreamSynchronize(ctx->stream), "load meshes");
   ctx->h_meshes = dm;
+  ctx->base_meshes = dm;
+  ctx->vert_r = vert_r;
   ctx->n_mesh = n;
+  ctx->mesh_sym.assign(n, 1);
+  ctx->update_search_yaws();
   ctx->max_chunks = max_ml;
   ctx->max_tris = max_tris;
   ctx->n_cverts = (int)verts.size();
@@ -494,6 +514,116 @@ int perch_load_meshes(perch_ctx* ctx, const perch_mesh* meshes, int32_t n) {
   ctx->tables_version++;
   ctx->geom_version++;
   return ctx->ensure_tables();
+}
+
+// Yaw k of a mesh with rotational symmetry order s is searched only if no
+// smaller index k' differs from it by a multiple of 2 pi / s (angles from the
+// pose table in double, to 1e-6 of a period): the mesh turned by that
+// difference is the same vertex set, so the two yaws are one pose.
+void perch_ctx::update_search_yaws() {
+  search_yaws.assign(n_mesh, {});
+  for (int m = 0; m < n_mesh; ++m) {
+    const int sym = m < (int)mesh_sym.size() ? std::max(mesh_sym[m], 1) : 1;
+    for (int k = 0; k < n_yaw; ++k) {
+      bool dup = false;
+      for (int j : search_yaws[m]) {
+        const double dk = std::atan2((double)h_cos_sin[2 * k + 1], (double)h_cos_sin[2 * k]);
+        const double dj = std::atan2((double)h_cos_sin[2 * j + 1], (double)h_cos_sin[2 * j]);
+        const double t = (dk - dj) * sym / (2.0 * M_PI);
+        if (std::fabs(t - std::nearbyint(t)) < 1e-6) {
+          dup = true;
+          break;
+        }
+      }
+      if (!dup) search_yaws[m].push_back(k);
+    }
+  }
+}
+
+int perch_set_symmetry(perch_ctx* ctx, const int32_t* sym, int32_t n) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (ctx->n_mesh == 0) return ctx->fail(PERCH_E_STATE, "load meshes first");
+  if (sym && n != ctx->n_mesh) return ctx->fail(PERCH_E_ARG, "%d symmetry orders for %d meshes", n, ctx->n_mesh);
+  for (int m = 0; sym && m < n; ++m)
+    if (sym[m] < 0 || sym[m] > (1 << 20)) return ctx->fail(PERCH_E_ARG, "mesh %d: bad symmetry order %d", m, sym[m]);
+  ctx->mesh_sym.assign(ctx->n_mesh, 1);
+  for (int m = 0; sym && m < n; ++m) ctx->mesh_sym[m] = std::max(sym[m], 1);
+  ctx->update_search_yaws();
+  return PERCH_OK;
+}
+
+int perch_set_volumes(perch_ctx* ctx, const perch_volume* volumes, int32_t n) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (ctx->n_mesh == 0) return ctx->fail(PERCH_E_STATE, "load meshes first");
+  if (volumes && n != ctx->n_mesh) return ctx->fail(PERCH_E_ARG, "%d volumes for %d meshes", n, ctx->n_mesh);
+  std::vector<DevMesh> dm = ctx->base_meshes;
+  std::vector<float2> normals;
+  auto fin = [](float x) { return std::isfinite(x); };
+  for (int i = 0; volumes && i < n; ++i) {
+    const perch_volume& v = volumes[i];
+    DevMesh& d = dm[i];
+    if (v.kind == 0) continue;
+    if (!fin(v.zlo) || !fin(v.zhi) || !(v.zlo <= v.zhi))
+      return ctx->fail(PERCH_E_ARG, "volume %d: bad height range", i);
+    double rmax = 0.0;
+    if (v.kind == 1) {
+      if (!(v.p[0] > 0.0f) || !(v.p[1] > 0.0f) || !fin(v.p[0]) || !fin(v.p[1]))
+        return ctx->fail(PERCH_E_ARG, "volume %d: box half extents must be finite and > 0", i);
+      d.vol_p[0] = v.p[0];
+      d.vol_p[1] = v.p[1];
+      rmax = std::hypot((double)v.p[0], (double)v.p[1]);
+    } else if (v.kind == 2) {
+      if (v.n < 3 || v.n > kMaxPrismSides || !v.normals)
+        return ctx->fail(PERCH_E_ARG, "volume %d: a prism needs 3..%d sides and their normals", i, kMaxPrismSides);
+      if (!(v.p[1] > 0.0f) || !fin(v.p[1])) return ctx->fail(PERCH_E_ARG, "volume %d: apothem must be > 0", i);
+      // the quick accept / reject circles of in_volume hold for a regular polygon:
+      // unit normals in order of angle, 2 pi / n apart
+      const double step = 2.0 * M_PI / v.n, a0 = std::atan2((double)v.normals[1], (double)v.normals[0]);
+      for (int k = 0; k < v.n; ++k) {
+        const double c = v.normals[2 * k], sn = v.normals[2 * k + 1];
+        const double da = std::remainder(std::atan2(sn, c) - (a0 + k * step), 2.0 * M_PI);
+        if (std::fabs(std::hypot(c, sn) - 1.0) > 1e-6 || std::fabs(da) > 2e-7)
+          return ctx->fail(PERCH_E_ARG, "volume %d: prism normal %d is not that of a regular %d-gon", i, k, v.n);
+      }
+      const double A = v.p[1], R = A / std::cos(M_PI / v.n);
+      d.vol_p[0] = v.p[1];
+      d.vol_p[1] = (float)(A * A * (1.0 - std::ldexp(1.0, -12)));
+      d.vol_p[2] = (float)(R * R * (1.0 + std::ldexp(1.0, -12)));
+      d.vol_n = v.n;
+      d.vol_nrm = (int)normals.size();
+      for (int k = 0; k < v.n; ++k) normals.push_back(make_float2(v.normals[2 * k], v.normals[2 * k + 1]));
+      rmax = R;
+    } else if (v.kind == 3) {
+      if (v.n != 1 && v.n != 2) return ctx->fail(PERCH_E_ARG, "volume %d: superquadric exponent pair must be 1 or 2", i);
+      for (int k = 0; k < 3; ++k)
+        if (!(v.p[k] > 0.0f) || !fin(v.p[k])) return ctx->fail(PERCH_E_ARG, "volume %d: bad semi-axis", i);
+      if (!fin(v.p[3])) return ctx->fail(PERCH_E_ARG, "volume %d: bad centre height", i);
+      for (int k = 0; k < 3; ++k) d.vol_p[k] = (float)(1.0 / (double)v.p[k]);
+      d.vol_p[3] = v.p[3];
+      d.vol_n = v.n;
+      rmax = std::max((double)v.p[0], (double)v.p[1]);
+    } else {
+      return ctx->fail(PERCH_E_ARG, "volume %d: unknown kind %d", i, v.kind);
+    }
+    d.vol_kind = v.kind;
+    d.vol_z0 = v.zlo;
+    d.vol_z1 = v.zhi;
+    d.vol_rmax = (float)(rmax * (1.0 + 1e-5));
+    d.fp_r = footprint_radius(ctx->vert_r[i], d.vol_rmax);
+  }
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(ctx->vol_normals.ensure(sizeof(float2) * std::max<size_t>(normals.size(), 1)), "alloc normals");
+  if (!normals.empty())
+    CK(cudaMemcpyAsync(ctx->vol_normals.p, normals.data(), sizeof(float2) * normals.size(), cudaMemcpyHostToDevice,
+                       ctx->stream), "copy normals");
+  CK(cudaMemcpyAsync(ctx->meshes.p, dm.data(), sizeof(DevMesh) * dm.size(), cudaMemcpyHostToDevice, ctx->stream),
+     "copy meshes");
+  CK(cudaStreamSynchronize(ctx->stream), "set volumes");
+  ctx->h_meshes = dm;
+  ctx->tables_version++;  // a captured graph holds the old geometry
+  return PERCH_OK;
 }
 
 int perch_set_pose_grid(perch_ctx* ctx, const float* xs, int32_t nx, const float* ys, int32_t ny,
@@ -513,6 +643,8 @@ int perch_set_pose_grid(perch_ctx* ctx, const float* xs, int32_t nx, const float
   ctx->nx = nx;
   ctx->ny = ny;
   ctx->n_yaw = n_yaw;
+  ctx->h_cos_sin.assign(cos_sin, cos_sin + 2 * (size_t)n_yaw);
+  ctx->update_search_yaws();
   ctx->tables_valid = false;
   ctx->tables_version++;
   ctx->geom_version++;
@@ -705,7 +837,8 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
       bm.tile_h = mesh_tile_h[m];
       const RenderWork w{pg.gpose, rg + 4 * m + 2, rg + 4 * m + 3, g_next.as<int>() + m, tile_store.as<uint32_t>(),
                          tile_off.as<int>(), pose_flags.as<uint8_t>()};
-      CK(launch_render_group(cam, g, bm, w, std::min<long long>(n_hyp, per_mesh), mesh_threads[m], sm_count, stream),
+      CK(launch_render_group(cam, g, obs, bm, w, std::min<long long>(n_hyp, per_mesh), mesh_threads[m], sm_count,
+                             stream),
          "render kernel");
     }
     if (!capturing) CK(cudaEventRecord(ev[3], stream), "event");
@@ -715,7 +848,7 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
       bm.tile_h = mesh_tile_h[m];
       const CostWork c{pg.order, rg + 4 * m, rg + 4 * m + 1, g_next.as<int>() + n_mesh + m, tile_store.as<uint32_t>(),
                        tile_off.as<int>(), pose_flags.as<uint8_t>()};
-      CK(launch_cost_group(cam, g, obs, bm, c, n_hyp, cost_threads, sm_count, stream), "cost kernel");
+      CK(launch_cost_group(cam, g, obs, bm, c, n_hyp, mesh_cost_threads[m], sm_count, stream), "cost kernel");
     }
     last_path = 2;
     if (!capturing) {

@@ -54,12 +54,20 @@ struct perch_ctx {
 
   // object meshes, split into chunks
   int n_mesh = 0, max_chunks = 0, max_tris = 0, n_cverts = 0;
-  std::vector<perch::DevMesh> h_meshes;
-  DevBuf meshes, chunk_verts, chunk_info, chunk_tris;
+  std::vector<perch::DevMesh> h_meshes;   // as on the device (with the current V(O))
+  std::vector<perch::DevMesh> base_meshes;  // as loaded (V(O) = the inscribed cylinders)
+  std::vector<double> vert_r;             // largest horizontal vertex radius per mesh
+  DevBuf meshes, chunk_verts, chunk_info, chunk_tris, vol_normals;
 
   // pose grid
   int nx = 0, ny = 0, n_yaw = 0;
   DevBuf xs, ys, cs;
+  std::vector<float> h_cos_sin;  // host copy of the yaw table
+  // the search's yaws per mesh: all of them, or with a rotational symmetry
+  // (perch_set_symmetry) the smallest index of each class of equivalent yaws
+  std::vector<int> mesh_sym;
+  std::vector<std::vector<int>> search_yaws;
+  void update_search_yaws();
 
   // camera, observation and its indices
   bool has_cam = false, has_obs = false;
@@ -92,7 +100,7 @@ struct perch_ctx {
   bool store_ok = false;
   DevBuf tile_store, tile_off, tile_sizes, pose_flags;
   DevBuf pg_cnt, pg_start, pg_flag, pg_gix, pg_gpose, pg_tmp, pg_ranges;  // hypotheses grouped by pose
-  int cost_threads = 128;  // CTA width of k_cost
+  std::vector<int> mesh_cost_threads;  // CTA width of k_cost per mesh (autotuned; 128 by default)
   int last_path = 0;       // last evaluation: 1 = one render per hypothesis, 2 = shared renders
   DevBuf b_parents, b_plen, b_hp, b_hyp, b_out;
 
@@ -135,7 +143,7 @@ struct perch_ctx {
   bool timed = false;
 
   std::vector<DevBuf*> all_buffers() {
-    return {&meshes, &chunk_verts, &chunk_info, &chunk_tris, &yaw_mats, &pose_off, &vtab, &xs, &ys, &cs, &depth, &rx, &ry, &blockcnt, &blockoff,
+    return {&meshes, &chunk_verts, &chunk_info, &chunk_tris, &vol_normals, &yaw_mats, &pose_off, &vtab, &xs, &ys, &cs, &depth, &rx, &ry, &blockcnt, &blockoff,
             &scan_tmp, &cam_pts, &world_pts, &keys, &counts, &cursor, &d_scenes, &d_scene_img,
             &scratch_small, &pose_bbox, &parent_z, &uset, &uset_count, &b_parents, &b_plen, &b_hp, &b_hyp,
             &b_out, &g_hist, &g_off, &g_cursor, &g_order, &g_next, &net_crops, &net_onehot, &net_pred,

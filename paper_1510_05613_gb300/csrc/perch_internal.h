@@ -38,10 +38,20 @@ struct Camera {
 struct DevMesh {
   int chunk_begin, chunk_count;
   int n_tris, n_verts;
-  float vol_r2, vol_zlo, vol_zhi;
+  float vol_r2, vol_zlo, vol_zhi;  // the inscribed cylinder (also the crops' reference height)
   float lo[3], hi[3];  // object-frame bounding box
   float fp_r;          // max(largest horizontal vertex radius, V(O) radius), rounded up
+  // V(O) (in_volume): kind 0 the inscribed cylinder; 1 box, p = (half x,
+  // half y); 2 regular prism of vol_n <= 256 sides, p = (apothem, quick
+  // accept r^2, quick reject r^2), normals at vol_normals[vol_nrm ..];
+  // 3 superquadric, p = (1/a1, 1/a2, 1/a3, centre height), vol_n = exponent
+  // pair (1: ellipsoid, 2: eps1 = 0.5, eps2 = 1)
+  int vol_kind, vol_n, vol_nrm;
+  float vol_p[4];
+  float vol_z0, vol_z1;  // kinds 1 and 2: height range
+  float vol_rmax;  // radius of a vertical cylinder about the origin that holds V(O)
 };
+constexpr int kMaxPrismSides = 256;
 
 // Observed cloud with its two spatial indices.
 struct ObsIndex {
@@ -77,6 +87,7 @@ struct Geometry {
   const int4* pose_bbox;  // per (mesh, ix, iy, iyaw): x0, y0, w, h in pixels
   const float* rx;        // ray slope per column
   const float* ry;        // ray slope per row
+  const float2* vol_normals;  // face normals of the prism volumes
 };
 
 struct Batch {
@@ -124,7 +135,8 @@ struct RenderWork {
   const int* offset;    // device scalar: this launch's first entry of gpose
   const int* count;     // device scalar: its entries
   int* next;            // device counter, zero before the launch
-  uint32_t* store;      // tile store: 1/z bits of each pose's screen box, rows of its width
+  uint32_t* store;      // tile store: z of each pose's screen box (+inf = empty), rows of its width; for a
+                        // single-scene batch the sign bit says the point is explained by I (Eq. (1))
   const int* tile_off;  // per pose: offset of its tile in the store, in 16-byte units
   uint8_t* pose_flags;  // per pose: kPoseCulled, kPoseFailed
 };
@@ -197,8 +209,9 @@ cudaError_t launch_tile_offsets(const Geometry& g, int* sizes, int* tile_off, in
 // hypothesis with an out-of-range parent or pose (it joins no group) and
 // leaves out those the shortcut answered (b.skip)
 cudaError_t launch_group_by_pose(const Geometry& g, const Batch& b, const PoseGroups& pg, cudaStream_t s);
-cudaError_t launch_render_group(const Camera& cam, const Geometry& g, const Batch& b, const RenderWork& w,
-                                long long max_items, int threads, int sm_count, cudaStream_t s);
+cudaError_t launch_render_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                                const RenderWork& w, long long max_items, int threads, int sm_count,
+                                cudaStream_t s);
 cudaError_t launch_cost_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
                               const CostWork& w, long long max_items, int threads, int sm_count, cudaStream_t s);
 // loads the kernels the allocation-free evaluation launches (a lazily loaded

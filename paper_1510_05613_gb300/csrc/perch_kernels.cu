@@ -31,11 +31,41 @@ __device__ __forceinline__ float dist2(float px, float py, float pz, float4 q) {
   return ffma(dz, dz, ffma(dy, dy, fmul(dx, dx)));
 }
 
-// V(O): the inscribed vertical cylinder of Sec. III-A at pose (ox, oy)
-__device__ __forceinline__ bool in_volume(float4 qw, float ox, float oy, float r2, float zlo, float zhi) {
+// V(O) of Sec. III-A for mesh m at pose (ox, oy, yaw iyaw): the inscribed
+// vertical cylinder (kind 0) or the closed-form solid (kinds 1-3), tested in
+// the object frame: x' = fma(s, dy, c dx), y' = fma(c, dy, -(s dx)) with the
+// pose table's (c, s); z is the world height.
+__device__ __forceinline__ bool in_volume(const Geometry& g, const DevMesh& m, float ox, float oy, int iyaw,
+                                          float4 qw) {
   const float dx = fsub(qw.x, ox), dy = fsub(qw.y, oy);
-  const float d2 = ffma(dy, dy, fmul(dx, dx));
-  return d2 <= r2 && zlo <= qw.z && qw.z <= zhi;
+  if (m.vol_kind == 0) {
+    const float d2 = ffma(dy, dy, fmul(dx, dx));
+    return d2 <= m.vol_r2 && m.vol_zlo <= qw.z && qw.z <= m.vol_zhi;
+  }
+  const float2 cs = g.cs[iyaw];
+  const float xo = ffma(cs.y, dy, fmul(cs.x, dx));
+  const float yo = ffma(cs.x, dy, -fmul(cs.y, dx));
+  if (m.vol_kind == 1)
+    return fabsf(xo) <= m.vol_p[0] && fabsf(yo) <= m.vol_p[1] && m.vol_z0 <= qw.z && qw.z <= m.vol_z1;
+  if (m.vol_kind == 2) {
+    if (!(m.vol_z0 <= qw.z && qw.z <= m.vol_z1)) return false;
+    // every face test passes inside the inscribed circle shrunk by 2^-12 in
+    // r^2, and one fails outside the circumscribed circle grown by 2^-12,
+    // whatever the binary32 rounding of the face tests (n <= 256 sides);
+    // only the thin annulus between them needs the faces
+    const float d2 = ffma(yo, yo, fmul(xo, xo));
+    if (d2 <= m.vol_p[1]) return true;
+    if (d2 >= m.vol_p[2]) return false;
+    const float2* nr = g.vol_normals + m.vol_nrm;
+    for (int k = 0; k < m.vol_n; ++k)
+      if (ffma(nr[k].y, yo, fmul(nr[k].x, xo)) > m.vol_p[0]) return false;
+    return true;
+  }
+  const float X = fmul(xo, m.vol_p[0]), Y = fmul(yo, m.vol_p[1]), Z = fmul(fsub(qw.z, m.vol_p[3]), m.vol_p[2]);
+  const float t = ffma(Y, Y, fmul(X, X));
+  const float z2 = fmul(Z, Z);
+  const float F = m.vol_n == 2 ? ffma(t, t, fmul(z2, z2)) : fadd(t, z2);
+  return F <= 1.0f;
 }
 
 struct Vtx {
@@ -619,7 +649,7 @@ __global__ void k_uset(Camera cam, Geometry g, ObsIndex obs0, Batch b) {
     const perch_obj o = b.parents[(long long)p * b.parent_stride + j];
     if (!obj_ok(g, o)) return;
     const DevMesh m = g.meshes[o.mesh];
-    if (in_volume(qw, g.xs[o.ix], g.ys[o.iy], m.vol_r2, m.vol_zlo, m.vol_zhi)) return;
+    if (in_volume(g, m, g.xs[o.ix], g.ys[o.iy], o.iyaw, qw)) return;
   }
   const float4 q = obs.cam2[k];
   if (plen > 0) {
@@ -803,7 +833,9 @@ size_t render_smem_bytes(int tile_w, int tile_h) {
          (size_t)kBigQueue * 8 + (size_t)tile_w * tile_h * 4;
 }
 
-size_t cost_smem_bytes(int tile_w, int tile_h) { return (size_t)tile_w * tile_h * 4 + (size_t)(tile_w + tile_h) * 4; }
+size_t cost_smem_bytes(int tile_w, int tile_h) {  // stage (16-byte multiple), tile, ray slopes
+  return (size_t)((tile_w * tile_h + 3) & ~3) * 4 + (size_t)tile_w * tile_h * 4 + (size_t)(tile_w + tile_h) * 4;
+}
 
 // thread 0: start the bulk copies of the first chunk of mesh m at yaw iyaw
 __device__ __forceinline__ void render_start(const Geometry& g, const DevMesh& m, int iyaw, const RenderSmem& s,
@@ -970,36 +1002,46 @@ __device__ __forceinline__ int render_chunks(const Camera& cam, const Geometry& 
   return kEvalDone;
 }
 
-// Cost of hypothesis h (Eq. (3), Eq. (4)) from its new object's render. src
-// holds the render as 1/z bits (0 = empty) over the pose's box bb, rows of
-// bb.z pixels: the shared tile itself (SRC_GLOBAL = false) or the pose's
-// entry in the tile store in global memory (SRC_GLOBAL = true). The shared
-// tile receives z on dR and +inf elsewhere. rxs / rys hold the ray slopes of
-// the box's columns and rows; s_cnt is zero except the culled flag s_cnt[2];
-// a CTA barrier must separate those writes from the call. Ends with a CTA
-// barrier (s_cnt and the tile may be reused after it).
-template <int NT, bool SRC_GLOBAL>
-__device__ __forceinline__ void cost_phase(long long h, int pid, int plen, int K_total, const perch_obj& o, int4 bb,
-                                           const DevMesh& m, const Camera& cam, const Geometry& g,
-                                           const ObsIndex& obs, const Batch& b, const uint32_t* src,
-                                           uint32_t* tile, const float* rxs, const float* rys, int* s_cnt) {
+// What a render source holds per pixel of the pose's box (shared memory,
+// rows of the box width): 1/z bits with 0 = empty (the per-hypothesis
+// kernel's own tile); z bits with +inf = empty (the tile store); or z bits
+// whose sign bit says the rendered point is explained by I (Eq. (1)), which
+// k_render decides once per pose for a single-scene batch.
+constexpr int kSrcInvZ = 0, kSrcZ = 1, kSrcZExplained = 2;
+constexpr uint32_t kExplainedBit = 0x80000000u;  // z > 0: the sign bit is free
+
+// The first part of cost_phase: the monotone test against the parent render
+// and dR (Eq. (3)). Reads the render from src, writes z on dR (+inf
+// elsewhere) into the tile, and sums violations and |dR| into s_cnt[0],
+// s_cnt[1] (with kSrcZExplained also dJ_r, the dR pixels not explained by I,
+// into s_cnt[3]); ends with a CTA barrier, after which src is no longer read.
+template <int NT, int SRC>
+__device__ __forceinline__ void compare_phase(int pid, int plen, int4 bb, const Camera& cam, const Batch& b,
+                                              const uint32_t* src, uint32_t* tile, int* s_cnt) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tw = bb.z, th = bb.w;
-  const float ox = g.xs[o.ix], oy = g.ys[o.iy];
-
-  // ---- monotone test against the parent render and dR (Eq. (3))
-  int viol = 0, nnew = 0;
+  int viol = 0, nnew = 0, djr = 0;
   const float* zp = plen > 0 ? b.parent_z + (size_t)pid * cam.W * cam.H : nullptr;
   for (int ly = warp; ly < th; ly += NW) {
     const float* prow = zp ? zp + (size_t)(bb.y + ly) * cam.W + bb.x : nullptr;
     for (int lx = lane; lx < tw; lx += 32) {
-      const uint32_t izb = SRC_GLOBAL ? __ldg(&src[ly * tw + lx]) : tile[ly * tw + lx];
-      if (izb == 0u) {
-        tile[ly * tw + lx] = kInfBits;
-        continue;
+      const uint32_t sv = src[ly * tw + lx];
+      uint32_t zb;
+      if (SRC == kSrcInvZ) {
+        if (sv == 0u) {
+          tile[ly * tw + lx] = kInfBits;
+          continue;
+        }
+        zb = __float_as_uint(__frcp_rn(__uint_as_float(sv)));
+      } else {
+        if (sv == kInfBits) {
+          tile[ly * tw + lx] = kInfBits;
+          continue;
+        }
+        zb = sv & ~kExplainedBit;
       }
-      const float z = __frcp_rn(__uint_as_float(izb));
+      const float z = __uint_as_float(zb);
       if (prow) {
         const float pz = __ldg(&prow[lx]);
         if (__float_as_uint(pz) != kInfBits) {
@@ -1008,17 +1050,35 @@ __device__ __forceinline__ void cost_phase(long long h, int pid, int plen, int K
           continue;
         }
       }
-      tile[ly * tw + lx] = __float_as_uint(z);
+      tile[ly * tw + lx] = zb;
       nnew++;
+      if (SRC == kSrcZExplained && !(sv & kExplainedBit)) djr++;
     }
   }
   viol = warp_sum(viol);
   nnew = warp_sum(nnew);
+  if (SRC == kSrcZExplained) djr = warp_sum(djr);
   if (lane == 0) {
     if (viol) atomicAdd(&s_cnt[0], viol);
     if (nnew) atomicAdd(&s_cnt[1], nnew);
+    if (djr) atomicAdd(&s_cnt[3], djr);
   }
   __syncthreads();
+}
+
+// The rest of cost_phase, after compare_phase: the record of an invalid
+// child, or dJ_r (unless DJR_DONE: compare_phase counted it), dJ_o,
+// residual(K) and n_vol from the tile (z on dR, +inf elsewhere). Ends with a
+// CTA barrier.
+template <int NT, bool DJR_DONE>
+__device__ __forceinline__ void finish_phase(long long h, int pid, int plen, int K_total, const perch_obj& o,
+                                             int4 bb, const DevMesh& m, const Camera& cam, const Geometry& g,
+                                             const ObsIndex& obs, const Batch& b, const uint32_t* tile,
+                                             const float* rxs, const float* rys, int* s_cnt) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tw = bb.z, th = bb.w;
+  const float ox = g.xs[o.ix], oy = g.ys[o.iy];
   const uint32_t flags = s_cnt[2] ? PERCH_FLAG_CULLED : 0u;
   if (s_cnt[0] > 0) {
     if (tid == 0) {
@@ -1031,7 +1091,7 @@ __device__ __forceinline__ void cost_phase(long long h, int pid, int plen, int K
 
   // ---- dJ_r: dR points with no observed point within delta
   int djr = 0;
-  for (int ly = warp; ly < th; ly += NW) {
+  for (int ly = warp; !DJR_DONE && ly < th; ly += NW) {
     const float ry = rys[ly];
     for (int lx = lane; lx < tw; lx += 32) {
       const uint32_t zb = tile[ly * tw + lx];
@@ -1044,7 +1104,7 @@ __device__ __forceinline__ void cost_phase(long long h, int pid, int plen, int K
   // ---- dJ_o: observed points inside V(O) with no dR point within delta
   int djo = 0, nvol = 0;
   if (obs.n > 0) {
-    const float r = sqrtf(m.vol_r2) * 1.001f + 1e-6f;
+    const float r = m.vol_rmax * 1.001f + 1e-6f;
     const int cx0 = max(cell_of(ox - r, obs.g2x, obs.inv2, obs.n2x) - 1, 0);
     const int cx1 = min(cell_of(ox + r, obs.g2x, obs.inv2, obs.n2x) + 1, obs.n2x - 1);
     const int cy0 = max(cell_of(oy - r, obs.g2y, obs.inv2, obs.n2y) - 1, 0);
@@ -1054,13 +1114,12 @@ __device__ __forceinline__ void cost_phase(long long h, int pid, int plen, int K
         const int s = obs.start2[cy * obs.n2x + cx0], e = obs.start2[cy * obs.n2x + cx1 + 1];
         for (int k = s + tid; k < e; k += NT) {
           const float4 qw = obs.world2[k];
-          if (!in_volume(qw, ox, oy, m.vol_r2, m.vol_zlo, m.vol_zhi)) continue;
+          if (!in_volume(g, m, ox, oy, o.iyaw, qw)) continue;
           if (!explained_by_tile(cam, obs.cam2[k], tile, rxs, rys, bb)) djo++;
           bool in_parent = false;  // already inside an assigned volume?
           for (int j = 0; j < plen && !in_parent; ++j) {
             const perch_obj po = b.parents[(long long)pid * b.parent_stride + j];
-            const DevMesh pm = g.meshes[po.mesh];
-            in_parent = in_volume(qw, g.xs[po.ix], g.ys[po.iy], pm.vol_r2, pm.vol_zlo, pm.vol_zhi);
+            in_parent = in_volume(g, g.meshes[po.mesh], g.xs[po.ix], g.ys[po.iy], po.iyaw, qw);
           }
           if (!in_parent) nvol++;
         }
@@ -1075,7 +1134,7 @@ __device__ __forceinline__ void cost_phase(long long h, int pid, int plen, int K
     const int* U = b.uset + (size_t)pid * b.uset_stride;
     for (int k = tid; k < nu; k += NT) {
       const int qi = U[k];
-      if (in_volume(obs.world2[qi], ox, oy, m.vol_r2, m.vol_zlo, m.vol_zhi)) continue;
+      if (in_volume(g, m, ox, oy, o.iyaw, obs.world2[qi])) continue;
       if (explained_by_tile(cam, obs.cam2[qi], tile, rxs, rys, bb)) continue;
       resid++;
     }
@@ -1096,6 +1155,22 @@ __device__ __forceinline__ void cost_phase(long long h, int pid, int plen, int K
     b.out[h] = r;
   }
   __syncthreads();  // s_cnt and the tile are reused by the next hypothesis
+}
+
+// Cost of hypothesis h (Eq. (3), Eq. (4)) from its new object's render,
+// which the shared tile holds as 1/z bits (0 = empty) over the pose's box bb,
+// rows of bb.z pixels; the tile then receives z on dR and +inf elsewhere.
+// rxs / rys hold the ray slopes of the box's columns and rows; s_cnt is zero
+// except the culled flag s_cnt[2]; a CTA barrier must separate those writes
+// from the call. Ends with a CTA barrier (s_cnt and the tile may be reused
+// after it).
+template <int NT>
+__device__ __forceinline__ void cost_phase(long long h, int pid, int plen, int K_total, const perch_obj& o, int4 bb,
+                                           const DevMesh& m, const Camera& cam, const Geometry& g,
+                                           const ObsIndex& obs, const Batch& b, uint32_t* tile, const float* rxs,
+                                           const float* rys, int* s_cnt) {
+  compare_phase<NT, kSrcInvZ>(pid, plen, bb, cam, b, tile, tile, s_cnt);
+  finish_phase<NT, false>(h, pid, plen, K_total, o, bb, m, cam, g, obs, b, tile, rxs, rys, s_cnt);
 }
 
 // The checks every evaluation of hypothesis h makes before it touches its
@@ -1167,7 +1242,7 @@ __device__ int eval_one(long long h, const Camera& cam, const Geometry& g, const
   }
   if (culled) s_cnt[2] = 1;
   __syncthreads();
-  cost_phase<NT, false>(h, a.pid, a.plen, a.K_total, a.o, bb, m, cam, g, obs, b, s.tile, s.tile, rxs, rys, s_cnt);
+  cost_phase<NT>(h, a.pid, a.plen, a.K_total, a.o, bb, m, cam, g, obs, b, s.tile, rxs, rys, s_cnt);
   return kEvalDone;
 }
 
@@ -1215,8 +1290,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_eval(Camera cam, Geometry g, 
 // the pose's screen box at 16-byte offset tile_off[pose]), and k_cost gives
 // every hypothesis its own comparison with its parent and its own costs
 // from that stored tile, read with plain coalesced loads.
-template <int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_render(Camera cam, Geometry g, Batch b, RenderWork w) {
+template <int NT, bool EXPL>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_render(Camera cam, Geometry g, ObsIndex obs, Batch b,
+                                                          RenderWork w) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ int s_qn;
@@ -1264,59 +1340,117 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_render(Camera cam, Geometry g
       continue;
     }
     const int any_culled = __syncthreads_or(culled != 0);
+    // the store gets z = 1/(1/z) (+inf where empty) and, for a single-scene
+    // batch (EXPL), the Eq. (1) test of each rendered point against I in the
+    // sign bit: it depends on the pose and the scene, not on the parent
     uint32_t* dst = w.store + 4 * (size_t)w.tile_off[p];
-    for (int i = tid; i < tw * th; i += NT) dst[i] = s.tile[i];
+    for (int ly = warp; ly < th; ly += NW) {
+      const float ry = EXPL ? g.ry[bb.y + ly] : 0.0f;
+      for (int lx = lane; lx < tw; lx += 32) {
+        const uint32_t izb = s.tile[ly * tw + lx];
+        uint32_t v = kInfBits;
+        if (izb != 0u) {
+          const float z = __frcp_rn(__uint_as_float(izb));
+          v = __float_as_uint(z);
+          if (EXPL && explained_by_obs(obs, fmul(g.rx[bb.x + lx], z), fmul(ry, z), z, cam.delta2))
+            v |= kExplainedBit;
+        }
+        dst[ly * tw + lx] = v;
+      }
+    }
     if (tid == 0) w.pose_flags[p] = any_culled ? kPoseCulled : 0;
     __syncthreads();  // the tile is cleared by the next pose
   }
 }
 
+// k_cost: one persistent CTA per SM slot costs hypotheses, sorted by pose,
+// from the tile store. A hypothesis's tile is brought into a shared stage
+// buffer by a 1D bulk copy (TMA), which threads only read; the copy of the
+// next hypothesis's tile is started as soon as the current one's compare
+// pass has read the stage, so it lands while dJ_r, dJ_o and the residual
+// run. The compare pass writes z (or +inf) into a separate shared tile, which
+// the delta windows of dJ_o and the residual scan.
 template <int NT, bool MULTI>
 __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex obs0, Batch b, CostWork w) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(16) ObsIndex s_obs;
+  __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_cnt[7];
   __shared__ int s_item;
   const int tid = threadIdx.x;
-  uint32_t* tile = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* stage = reinterpret_cast<uint32_t*>(smem);  // bulk-copy destination
+  uint32_t* tile = stage + ((b.tile_w * b.tile_h + 3) & ~3);
   float* rxs = reinterpret_cast<float*>(tile + b.tile_w * b.tile_h);
   float* rys = rxs + b.tile_w;
+  if (tid == 0) {
+    mbar_init(&s_bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
   const int count = *w.count, offset = *w.offset;
-  for (;;) {
-    if (tid == 0) s_item = atomicAdd(w.next, 1);
+  // Is there a stored tile to cost item `it` from? (the same answer in every thread)
+  auto has_tile = [&](int it, HypArgs& a, int4& bb) {
+    if (it >= count || !hyp_args(g, b, w.order[offset + it], a)) return false;
+    bb = g.pose_bbox[a.pose];
+    return bb.z <= b.tile_w && bb.w <= b.tile_h && !(w.pose_flags[a.pose] & kPoseFailed);
+  };
+  // claim the next item and start the copy of its tile (thread 0); a CTA barrier
+  auto claim = [&]() {
+    if (tid == 0) {
+      const int it = atomicAdd(w.next, 1);
+      s_item = it;
+      HypArgs a;
+      int4 bb;
+      if (has_tile(it, a, bb))
+        bulk_load(stage, w.store + 4 * (size_t)w.tile_off[a.pose], 16u * (uint32_t)((bb.z * bb.w + 3) >> 2),
+                  &s_bar);
+    }
     __syncthreads();
-    const int item = s_item;
-    __syncthreads();
-    if (item >= count) break;
+    return s_item;
+  };
+  uint32_t parity = 0;
+  int item = claim();
+  while (item < count) {
     const long long h = w.order[offset + item];
     HypArgs a;
-    const bool ok = hyp_args(g, b, h, a);
-    const int4 bb = ok ? g.pose_bbox[a.pose] : make_int4(0, 0, 0, 0);
-    if (!ok || bb.z > b.tile_w || bb.w > b.tile_h) {
+    int4 bb = make_int4(0, 0, 0, 0);
+    if (!has_tile(item, a, bb)) {  // no copy was started for it
       if (tid == 0) {
-        perch_cost r = {0, 0, 0, 0, 0, kFlagBadIndex, 0};
+        const bool failed = hyp_args(g, b, h, a) && (w.pose_flags[a.pose] & kPoseFailed);
+        perch_cost r = {0, 0, 0, 0, 0, failed ? kFlagTimeout : kFlagBadIndex, 0};
         b.out[h] = r;
       }
+      item = claim();
       continue;
     }
     const uint8_t pf = w.pose_flags[a.pose];
-    if (pf & kPoseFailed) {  // the render's bounded wait gave up
-      if (tid == 0) {
-        perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout, 0};
-        b.out[h] = r;
-      }
-      continue;
-    }
     if (MULTI && tid < (int)(sizeof(ObsIndex) / 4))
       reinterpret_cast<int*>(&s_obs)[tid] = reinterpret_cast<const int*>(&b.scenes[a.scene])[tid];
     const ObsIndex& obs = MULTI ? s_obs : obs0;
     for (int i = tid; i < bb.z; i += NT) rxs[i] = g.rx[bb.x + i];
     for (int i = tid; i < bb.w; i += NT) rys[i] = g.ry[bb.y + i];
     if (tid < 7) s_cnt[tid] = tid == 2 ? (int)(pf & kPoseCulled) : 0;
-    __syncthreads();
+    // wait for the stage (bounded); on give-up drain the copy with the full
+    // bound, report the hypothesis and go on, or stop if it is still in flight
+    if (!__syncthreads_and(mbar_wait(&s_bar, parity, b.wait_polls))) {
+      const bool drained = __syncthreads_and(mbar_wait(&s_bar, parity));
+      if (tid == 0) {
+        perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout, 0};
+        b.out[h] = r;
+      }
+      if (!drained) break;
+      parity ^= 1u;
+      item = claim();
+      continue;
+    }
+    parity ^= 1u;
+    // a single-scene store holds z with the explained flag (k_render); a
+    // multi-scene one plain z, and dJ_r is counted here against the scene
+    compare_phase<NT, MULTI ? kSrcZ : kSrcZExplained>(a.pid, a.plen, bb, cam, b, stage, tile, s_cnt);
+    const int next = claim();  // the stage is free: start the next copy
     const DevMesh m = g.meshes[a.o.mesh];
-    cost_phase<NT, true>(h, a.pid, a.plen, a.K_total, a.o, bb, m, cam, g, obs, b,
-                         w.store + 4 * (size_t)w.tile_off[a.pose], tile, rxs, rys, s_cnt);
+    finish_phase<NT, !MULTI>(h, a.pid, a.plen, a.K_total, a.o, bb, m, cam, g, obs, b, tile, rxs, rys, s_cnt);
+    item = next;
   }
 }
 
@@ -1597,11 +1731,11 @@ static cudaError_t launch_group_t(const Camera& cam, const Geometry& g, const Ob
   return cudaGetLastError();
 }
 
-template <int NT>
-static cudaError_t launch_render_t(const Camera& cam, const Geometry& g, const Batch& b, const RenderWork& w,
-                                   long long max_items, int sm_count, cudaStream_t s) {
+template <int NT, bool EXPL>
+static cudaError_t launch_render_t(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                                   const RenderWork& w, long long max_items, int sm_count, cudaStream_t s) {
   const size_t smem = render_smem_bytes(b.tile_w, b.tile_h);
-  auto kern = k_render<NT>;
+  auto kern = k_render<NT, EXPL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -1611,20 +1745,26 @@ static cudaError_t launch_render_t(const Camera& cam, const Geometry& g, const B
   long long grid = (long long)per_sm * sm_count;
   if (grid > max_items) grid = max_items;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, NT, smem, s>>>(cam, g, b, w);
+  kern<<<(unsigned)grid, NT, smem, s>>>(cam, g, obs, b, w);
   return cudaGetLastError();
 }
 
 // One persistent launch rendering one mesh's distinct poses of a batch into
 // the tile store, with CTAs of `threads` (128, 256 or 512) and the mesh's
-// tile (b.tile_w x b.tile_h).
-cudaError_t launch_render_group(const Camera& cam, const Geometry& g, const Batch& b, const RenderWork& w,
-                                long long max_items, int threads, int sm_count, cudaStream_t s) {
+// tile (b.tile_w x b.tile_h). A single-scene batch also stores each rendered
+// point's Eq. (1) test against `obs`.
+cudaError_t launch_render_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                                const RenderWork& w, long long max_items, int threads, int sm_count,
+                                cudaStream_t s) {
   if (max_items <= 0) return cudaSuccess;
+  const bool expl = b.parent_scene == nullptr;
   switch (threads) {
-    case 128: return launch_render_t<128>(cam, g, b, w, max_items, sm_count, s);
-    case 512: return launch_render_t<512>(cam, g, b, w, max_items, sm_count, s);
-    default: return launch_render_t<256>(cam, g, b, w, max_items, sm_count, s);
+    case 128: return expl ? launch_render_t<128, true>(cam, g, obs, b, w, max_items, sm_count, s)
+                          : launch_render_t<128, false>(cam, g, obs, b, w, max_items, sm_count, s);
+    case 512: return expl ? launch_render_t<512, true>(cam, g, obs, b, w, max_items, sm_count, s)
+                          : launch_render_t<512, false>(cam, g, obs, b, w, max_items, sm_count, s);
+    default: return expl ? launch_render_t<256, true>(cam, g, obs, b, w, max_items, sm_count, s)
+                         : launch_render_t<256, false>(cam, g, obs, b, w, max_items, sm_count, s);
   }
 }
 

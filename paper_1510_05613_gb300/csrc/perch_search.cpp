@@ -183,6 +183,9 @@ struct SceneSearch {
   std::vector<int> pool;               // learned queue: candidates of the current step
   int T = 16;                          // learned queue: placements kept per type
   bool bad_record = false;             // a record carried no cost (flags bit 30 or 31)
+  double now = 0.0;                    // seconds since the start, when the current records arrived
+  double found_seconds = 0.0;          // when best_key was last set
+  int64_t found_expansions = 0;
   bool focal() const { return w > 1.0 || heur != 0; }
   bool learned() const { return (heur & 12) != 0; }
   bool dive() const { return (heur & 8) != 0; }  // the depth-first learned queue
@@ -436,10 +439,16 @@ struct SceneSearch {
         best_g = ng;
         best_key = key_of(pidx);
         best_key.insert(std::upper_bound(best_key.begin(), best_key.end(), o), o);
+        found_seconds = now;
+        found_expansions = expansions;
       } else if (ng == best_g) {
         Key ck = key_of(pidx);
         ck.insert(std::upper_bound(ck.begin(), ck.end(), o), o);
-        if (ck < best_key) best_key = std::move(ck);
+        if (ck < best_key) {
+          best_key = std::move(ck);
+          found_seconds = now;
+          found_expansions = expansions;
+        }
       }
       return;
     }
@@ -637,7 +646,7 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
     // then the (independent) per-state fills in parallel
     std::vector<size_t> hbeg(work.size() + 1, 0);
     rem.resize(work.size());
-    const size_t poses = (size_t)ctx->nx * ctx->ny * ctx->n_yaw;
+    const size_t positions = (size_t)ctx->nx * ctx->ny;
     for (size_t w = 0; w < work.size(); ++w) {
       const SceneSearch& s = ss[work[w].scene_slot];
       const Key key = s.key_of(work[w].state);
@@ -646,20 +655,23 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
       pK[w] = s.K;
       for (size_t j = 0; j < key.size(); ++j) parents[w * stride + j] = unpack(key[j]);
       rem[w] = s.remaining(key);
-      hbeg[w + 1] = hbeg[w] + rem[w].size() * poses;
+      size_t n = 0;
+      for (int m : rem[w]) n += positions * ctx->search_yaws[m].size();
+      hbeg[w + 1] = hbeg[w] + n;
     }
     hyps.resize(hbeg[work.size()]);
     hparent.resize(hbeg[work.size()]);
-    const int nx = ctx->nx, ny = ctx->ny, nyaw = ctx->n_yaw;
+    const int nx = ctx->nx, ny = ctx->ny;
 #pragma omp parallel for schedule(dynamic, 1) if (hbeg[work.size()] >= kParallelMin)
     for (long long w = 0; w < (long long)work.size(); ++w) {
       size_t h = hbeg[w];
       for (int m : rem[w])
         for (int ix = 0; ix < nx; ++ix)
           for (int iy = 0; iy < ny; ++iy)
-            for (int k = 0; k < nyaw; ++k, ++h) {
+            for (int k : ctx->search_yaws[m]) {
               hyps[h] = perch_obj{(uint16_t)m, (uint16_t)k, (int16_t)ix, (int16_t)iy};
               hparent[h] = (int32_t)w;
+              ++h;
             }
     }
     out.resize(hyps.size());
@@ -687,6 +699,8 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
       v.push_back((int)w);
     }
     std::atomic<bool> failed{false};
+    const double now = elapsed();
+    for (int si : slots) ss[si].now = now;
     auto absorb_scene = [&](int si) {
       try {
         SceneSearch& s = ss[si];
@@ -721,6 +735,8 @@ void fill_result(const SceneSearch& s, int status, perch_result* res) {
   res->expansions = s.expansions;
   res->successors = s.successors;
   res->seconds = s.seconds;
+  res->found_seconds = s.found_seconds;
+  res->found_expansions = s.found_expansions;
   if (s.best_g != kInf) {
     res->cost = s.best_g;
     res->n_objs = (int32_t)s.best_key.size();

@@ -23,11 +23,12 @@ using namespace perch;
 
 namespace {
 
-using TuneKey = std::tuple<int, int, int, int, int>;  // device, tris, verts, tile_w, tile_h
+using TuneKey = std::tuple<int, int, int, int, int, int>;  // device, tris, verts, tile_w, tile_h, shared renders
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune_cache;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;  // (render or evaluation width, cost width)
 
 constexpr int kWidths[3] = {128, 256, 512};
+constexpr int kCostWidths[2] = {128, 256};
 
 }  // namespace
 
@@ -66,14 +67,17 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
     ~ShortcutOff() { c->shortcut = was; }
   } shortcut_off{ctx, ctx->shortcut};
   ctx->shortcut = false;
+  const bool shared = ctx->share_renders && ctx->store_ok;
+  const std::vector<int> saved_cost = ctx->mesh_cost_threads;
   for (int m = 0; m < n_mesh; ++m) {
-    const TuneKey key{ctx->device, ctx->h_meshes[m].n_tris, ctx->h_meshes[m].n_verts, ctx->mesh_tile_w[m],
-                      ctx->mesh_tile_h[m]};
+    const TuneKey key{ctx->device,          ctx->h_meshes[m].n_tris, ctx->h_meshes[m].n_verts,
+                      ctx->mesh_tile_w[m], ctx->mesh_tile_h[m],     shared ? 1 : 0};
     {
       std::lock_guard<std::mutex> lock(g_tune_mu);
       auto it = g_tune_cache.find(key);
       if (it != g_tune_cache.end()) {
-        ctx->mesh_threads[m] = it->second;
+        ctx->mesh_threads[m] = it->second.first;
+        ctx->mesh_cost_threads[m] = it->second.second;
         continue;
       }
     }
@@ -91,25 +95,34 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
     CK(cudaMemcpyAsync(ctx->b_hyp.p, hyps.data(), sizeof(perch_obj) * (size_t)n_sample, cudaMemcpyHostToDevice,
                        ctx->stream),
        "copy");
-    int best = 256;
-    float best_ms = 1e30f;
-    for (int w : kWidths) {
-      ctx->mesh_threads[m] = w;
+    // time one phase (ev[a] -> ev[a + 1]) of the sample's evaluation: the
+    // render launches (k_render, or k_eval when every hypothesis is
+    // rendered) or the cost launches (k_cost)
+    auto time_phase = [&](int a, float& out) -> int {
       float ms = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
         int rc = ctx->enqueue_eval(ctx->b_parents.as<perch_obj>(), 1, ctx->b_plen.as<int32_t>(), 1,
                                    ctx->b_hp.as<int32_t>(), ctx->b_hyp.as<perch_obj>(), n_sample, 1,
                                    ctx->b_out.as<perch_cost>());
-        if (rc != PERCH_OK) {
-          ctx->mesh_threads = saved;
-          return rc;
-        }
-        // the render phase: the per-mesh launches the width applies to (the
-        // shared-render k_render, or k_eval when every hypothesis is rendered)
+        if (rc != PERCH_OK) return rc;
         float b = 0.0f;
         CK(cudaEventSynchronize(ctx->ev[4]), "event sync");
-        CK(cudaEventElapsedTime(&b, ctx->ev[2], ctx->ev[3]), "event time");
+        CK(cudaEventElapsedTime(&b, ctx->ev[a], ctx->ev[a + 1]), "event time");
         if (rep > 0) ms = std::min(ms, b);  // the first launch of a width also loads its code
+      }
+      out = ms;
+      return PERCH_OK;
+    };
+    int best = 256, best_cost = ctx->mesh_cost_threads[m];
+    float best_ms = 1e30f;
+    for (int w : kWidths) {
+      ctx->mesh_threads[m] = w;
+      float ms = 0.0f;
+      const int rc = time_phase(2, ms);
+      if (rc != PERCH_OK) {
+        ctx->mesh_threads = saved;
+        ctx->mesh_cost_threads = saved_cost;
+        return rc;
       }
       if (ms < best_ms) {
         best_ms = ms;
@@ -117,8 +130,26 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
       }
     }
     ctx->mesh_threads[m] = best;
+    if (shared) {
+      best_ms = 1e30f;
+      for (int w : kCostWidths) {
+        ctx->mesh_cost_threads[m] = w;
+        float ms = 0.0f;
+        const int rc = time_phase(3, ms);
+        if (rc != PERCH_OK) {
+          ctx->mesh_threads = saved;
+          ctx->mesh_cost_threads = saved_cost;
+          return rc;
+        }
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_cost = w;
+        }
+      }
+      ctx->mesh_cost_threads[m] = best_cost;
+    }
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[key] = best;
+    g_tune_cache[key] = {best, best_cost};
   }
   if (threads_out)
     for (int m = 0; m < n_mesh; ++m) threads_out[m] = ctx->mesh_threads[m];
@@ -174,6 +205,18 @@ extern "C" int perch_eval_graph(perch_ctx* ctx, const perch_obj* parents, int32_
     ctx->graph_key = key;
   }
   CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream), "graph launch");
+  return PERCH_OK;
+}
+
+extern "C" int perch_launch_config(perch_ctx* ctx, int32_t* render_threads, int32_t* cost_threads) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if ((int)ctx->mesh_threads.size() != ctx->n_mesh || (int)ctx->mesh_cost_threads.size() != ctx->n_mesh)
+    return ctx->fail(PERCH_E_STATE, "no meshes and camera yet");
+  for (int m = 0; m < ctx->n_mesh; ++m) {
+    if (render_threads) render_threads[m] = ctx->mesh_threads[m];
+    if (cost_threads) cost_threads[m] = ctx->mesh_cost_threads[m];
+  }
   return PERCH_OK;
 }
 

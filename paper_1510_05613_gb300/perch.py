@@ -32,13 +32,19 @@ EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_mesh
            "perch_cnn_forward", "perch_cnn_train_step", "perch_cnn_gradients", "perch_set_heuristic_net",
            "perch_cnn_set_tensor_path", "perch_cnn_tensor_status",
            "perch_set_shortcut", "perch_shortcut_stats", "perch_search_stats", "perch_search_times",
-           "perch_set_wait_limit", "perch_set_share_renders", "perch_last_phase_times")
+           "perch_set_wait_limit", "perch_set_share_renders", "perch_last_phase_times", "perch_set_volumes",
+           "perch_launch_config", "perch_set_symmetry")
 
 
 class perch_mesh(ctypes.Structure):
     _fields_ = [("verts", ctypes.c_void_p), ("n_verts", ctypes.c_int32), ("tris", ctypes.c_void_p),
                 ("n_tris", ctypes.c_int32), ("vol_r", ctypes.c_float), ("vol_zlo", ctypes.c_float),
                 ("vol_zhi", ctypes.c_float)]
+
+
+class perch_volume(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("p", ctypes.c_float * 4),
+                ("zlo", ctypes.c_float), ("zhi", ctypes.c_float), ("normals", ctypes.c_void_p)]
 
 
 class perch_obj(ctypes.Structure):
@@ -54,7 +60,8 @@ class perch_search_params(ctypes.Structure):
 class perch_result(ctypes.Structure):
     _fields_ = [("objs", perch_obj * 16), ("n_objs", ctypes.c_int32), ("cost", ctypes.c_int64),
                 ("expansions", ctypes.c_int64), ("successors", ctypes.c_int64), ("seconds", ctypes.c_double),
-                ("proven_optimal", ctypes.c_int32)]
+                ("proven_optimal", ctypes.c_int32), ("found_seconds", ctypes.c_double),
+                ("found_expansions", ctypes.c_int64)]
 
 
 class PerchError(RuntimeError):
@@ -109,6 +116,9 @@ def load(path: str = LIB_PATH):
         "perch_set_heuristic_net": ([P, P, I32], ctypes.c_int),
         "perch_set_shortcut": ([P, I32], ctypes.c_int),
         "perch_set_wait_limit": ([P, I32], ctypes.c_int),
+        "perch_set_volumes": ([P, P, I32], ctypes.c_int),
+        "perch_launch_config": ([P, P, P], ctypes.c_int),
+        "perch_set_symmetry": ([P, P, I32], ctypes.c_int),
         "perch_set_share_renders": ([P, I32], ctypes.c_int),
         "perch_last_phase_times": ([P, P, P], ctypes.c_int),
         "perch_search_stats": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
@@ -183,10 +193,13 @@ class Perch:
         return self._check(self.lib.perch_set_observation(self.h, d.ctypes.data, W, H, k.ctypes.data, T.ctypes.data,
                                                           delta))
 
-    def setup(self, workload):
-        """Meshes, pose grid and observation of a synth.Workload."""
+    def setup(self, workload, exact_volumes: bool = False):
+        """Meshes, pose grid and observation of a synth.Workload; with
+        exact_volumes, V(O) is each mesh's closed form where it has one."""
         self.n_mesh = len(workload.meshes)
         self.perch_load_meshes(workload.meshes)
+        if exact_volumes:
+            self.perch_set_volumes(workload.meshes)
         self.perch_set_pose_grid(workload.grid)
         self.perch_set_observation(workload.depth, workload.cam.fxfycxcy, workload.cam.T_wc, workload.delta)
         self.H, self.W = workload.depth.shape
@@ -279,7 +292,8 @@ class Perch:
         key = tuple(sorted((int(o["mesh"]), int(o["ix"]), int(o["iy"]), int(o["iyaw"])) for o in objs))
         return {"cost": int(r.cost), "key": key, "objs": objs, "expansions": int(r.expansions),
                 "successors": int(r.successors), "seconds": float(r.seconds),
-                "proven_optimal": bool(r.proven_optimal), "status": rc}
+                "proven_optimal": bool(r.proven_optimal), "status": rc,
+                "found_seconds": float(r.found_seconds), "found_expansions": int(r.found_expansions)}
 
     def perch_cnn_crops(self, parents, hyp_parent, hyps, parent_scene=None):
         """Network inputs of the hypotheses: (crops, onehot) as torch device
@@ -311,6 +325,41 @@ class Perch:
         shared = ctypes.c_int32(0)
         self._check(self.lib.perch_last_phase_times(self.h, ms.ctypes.data, ctypes.byref(shared)))
         return ms.astype(np.float64), bool(shared.value)
+
+    def perch_set_symmetry(self, meshes):
+        """The search places each mesh only at yaws that are distinct modulo
+        its rotational symmetry (synth.Mesh.sym); None: every yaw."""
+        if meshes is None:
+            return self._check(self.lib.perch_set_symmetry(self.h, None, 0))
+        sym = np.array([int(getattr(m, "sym", 1)) for m in meshes], np.int32)
+        return self._check(self.lib.perch_set_symmetry(self.h, sym.ctypes.data, len(sym)))
+
+    def perch_launch_config(self):
+        """(render CTA width per mesh, cost CTA width per mesh) now in use."""
+        r = np.zeros(self.n_mesh, np.int32)
+        c = np.zeros(self.n_mesh, np.int32)
+        self._check(self.lib.perch_launch_config(self.h, r.ctypes.data, c.ctypes.data))
+        return r.tolist(), c.tolist()
+
+    def perch_set_volumes(self, meshes):
+        """V(O) per mesh from each synth.Mesh's closed-form `volume` (None:
+        the inscribed cylinder); meshes = None restores the cylinders."""
+        if meshes is None:
+            return self._check(self.lib.perch_set_volumes(self.h, None, 0))
+        arr = (perch_volume * len(meshes))()
+        keep = []
+        for i, m in enumerate(meshes):
+            v = getattr(m, "volume", None)
+            if v is None:
+                continue
+            nr = _c(v.normals, np.float32)
+            keep.append(nr)
+            arr[i].kind, arr[i].n = int(v.kind), int(v.n)
+            for k in range(4):
+                arr[i].p[k] = float(np.float32(v.p[k]))
+            arr[i].zlo, arr[i].zhi = float(v.zlo), float(v.zhi)
+            arr[i].normals = nr.ctypes.data if nr.size else None
+        return self._check(self.lib.perch_set_volumes(self.h, arr, len(meshes)))
 
     def perch_set_wait_limit(self, polls: int):
         """Poll bound of the evaluation kernel's first wait per bulk copy
@@ -363,7 +412,8 @@ class Perch:
         key = tuple(sorted((int(o["mesh"]), int(o["ix"]), int(o["iy"]), int(o["iyaw"])) for o in objs))
         return {"cost": int(r.cost), "key": key, "objs": objs, "expansions": int(r.expansions),
                 "successors": int(r.successors), "seconds": float(r.seconds),
-                "proven_optimal": bool(r.proven_optimal), "status": rc}
+                "proven_optimal": bool(r.proven_optimal), "status": rc,
+                "found_seconds": float(r.found_seconds), "found_expansions": int(r.found_expansions)}
 
 
 class PerchCNN:
