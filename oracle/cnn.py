@@ -126,6 +126,43 @@ def loss_and_grads(params, crops, onehot, target, bf16: bool = False):
     return loss, grads, pred
 
 
+def grad_magnitudes(params, crops, onehot, target, bf16: bool = False):
+    """Scales of the rounding error of every gradient element of
+    loss_and_grads, as (sums, rss):
+      sums: the sum of the absolute values of the terms the element adds up
+            (the same contractions taken on |a| |b|, with the forward pass's
+            ReLU masks); a relative perturbation e of every term moves the
+            element by at most e * sum, whatever the summation order;
+      rss:  the root of the sum of the squared terms; independent relative
+            roundings e of the terms move it by about e * rss (a random
+            walk), which is what a bfloat16 rounding of each stored operand
+            does."""
+    pred, (cache, feat, z1, h1, w1, w2) = forward(params, crops, onehot, bf16)
+    n = pred.shape[0]
+    err = (pred - np.asarray(target, np.float64)) / n
+    dpred = err[:, None]
+    sums, sq = [None] * len(params), [None] * len(params)
+    a = np.abs(dpred)
+    sums[10], sq[10] = a.T @ np.abs(h1), (a * a).T @ (h1 * h1)
+    sums[11], sq[11] = a.sum(0), (a * a).sum(0)
+    dz1 = (dpred @ w2) * (z1 > 0)
+    adz1 = (a @ np.abs(w2)) * (z1 > 0)
+    sums[8], sq[8] = adz1.T @ np.abs(feat), (dz1 * dz1).T @ (feat * feat)
+    sums[9], sq[9] = adz1.sum(0), (dz1 * dz1).sum(0)
+    last = cache[-1][3]
+    dx = (dz1 @ w1)[:, :last.size // n].reshape(last.shape)
+    adx = (adz1 @ np.abs(w1))[:, :last.size // n].reshape(last.shape)
+    for li in range(len(CONVS) - 1, -1, -1):
+        x, w, s, z = cache[li]
+        dz, adz = dx * (z > 0), adx * (z > 0)
+        dx, _, _ = conv_backward(x, w, s, dz)
+        adx, sw, sb = conv_backward(np.abs(x), np.abs(w), s, adz)
+        _, qw, qb = conv_backward(x * x, w, s, dz * dz)
+        sums[2 * li], sums[2 * li + 1] = sw, sb
+        sq[2 * li], sq[2 * li + 1] = qw, qb
+    return sums, [np.sqrt(q) for q in sq]
+
+
 # ---------------------------------------------------------------------------
 # network input: two crops centred on the projected hypothesis
 # ---------------------------------------------------------------------------

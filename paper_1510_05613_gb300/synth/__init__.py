@@ -77,6 +77,9 @@ class Mesh:
     vol_zhi: float
     # the closed-form solid the mesh describes, when it has one (see Volume)
     volume: "Volume | None" = None
+    # rotational symmetry order about the vertical axis: turning the mesh by
+    # 2 pi / sym maps its vertex set onto itself (1 = none)
+    sym: int = 1
 
     @property
     def n_verts(self) -> int:
@@ -187,7 +190,8 @@ def box_mesh(a: float, b: float, h: float, n: int, name: str = "box") -> Mesh:
     P, T = _weld(np.array(pts), np.array(tris, np.int64))
     T = _orient_outward(P, T, (0.0, 0.0, h / 2))
     r = 0.9 * min(a, b) / 2
-    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h, box_volume(a, b, h))
+    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h, box_volume(a, b, h),
+                4 if a == b else 2)
 
 
 def cylinder_mesh(R: float, h: float, n_seg: int, n_rings: int, name: str = "cylinder") -> Mesh:
@@ -214,7 +218,8 @@ def cylinder_mesh(R: float, h: float, n_seg: int, n_rings: int, name: str = "cyl
     P, T = np.array(pts), np.array(tris, np.int64)
     T = _orient_outward(P, T, (0.0, 0.0, h / 2))
     r = 0.9 * R * math.cos(math.pi / n_seg)
-    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h, prism_volume(R, n_seg, h))
+    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h, prism_volume(R, n_seg, h),
+                n_seg)
 
 
 def _spow(x, e):
@@ -257,8 +262,17 @@ def superquadric_mesh(a1: float, a2: float, a3: float, e1: float, e2: float,
     s = min(1.0, zb / a3)
     rho = max(0.0, 1.0 - s ** (2.0 / e1)) ** (e1 / 2.0)
     r = 0.9 * min(a1, a2) * rho * math.cos(math.pi / n_omega)
+    # the omega samples are n_omega equal steps: a half turn maps them onto
+    # themselves (n_omega even), a quarter turn too when a1 = a2 and 4 | n_omega,
+    # and every sample step when the cross-section is a circle (a1 = a2, e2 = 1)
+    if a1 == a2 and e2 == 1.0:
+        sym = n_omega
+    elif a1 == a2 and n_omega % 4 == 0:
+        sym = 4
+    else:
+        sym = 2 if n_omega % 2 == 0 else 1
     return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.2 * a3, 1.8 * a3,
-                superquadric_volume(a1, a2, a3, e1, e2))
+                superquadric_volume(a1, a2, a3, e1, e2), sym)
 
 
 # ---------------------------------------------------------------------------
@@ -567,13 +581,13 @@ def _ngon(k: int):
 def frustum_mesh(r_bot: float, r_top: float, h: float, n_seg: int, n_rings: int, name: str = "frustum") -> Mesh:
     P, T = prism_mesh(lambda t: (r_bot + (r_top - r_bot) * t, h * t), _ngon(n_seg), 1, n_rings, name)
     r = 0.9 * min(r_bot, r_top) * math.cos(math.pi / n_seg)
-    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h)
+    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h, None, n_seg)
 
 
 def hex_prism_mesh(R: float, h: float, sub: int, n_rings: int, name: str = "hexprism") -> Mesh:
     P, T = prism_mesh(lambda t: (R, h * t), _ngon(6), sub, n_rings, name)
     r = 0.9 * R * math.cos(math.pi / 6)
-    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h, prism_volume(R, 6, h))
+    return Mesh(name, P.astype(np.float32), T.astype(np.int32), r, 0.05 * h, 0.95 * h, prism_volume(R, 6, h), 6)
 
 
 def superquadric_general(a1, a2, a3, e1, e2, n_eta, n_omega, name):

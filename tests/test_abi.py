@@ -42,7 +42,13 @@ def test_struct_layouts():
     assert perch.COST.itemsize == 28
     assert ctypes.sizeof(perch.perch_mesh) == 40
     assert ctypes.sizeof(perch.perch_search_params) == 48
-    assert ctypes.sizeof(perch.perch_result) == 16 * 8 + 4 + 4 + 8 * 4 + 4 + 4
+    # objs, n_objs + pad, cost, expansions, successors, seconds, proven_optimal + pad, found_seconds,
+    # found_expansions
+    assert ctypes.sizeof(perch.perch_result) == 16 * 8 + 4 + 4 + 8 * 4 + 4 + 4 + 8 + 8
+    assert perch.perch_result.found_seconds.offset == 176
+    # kind, n, p[4], zlo, zhi, normals
+    assert ctypes.sizeof(perch.perch_volume) == 4 + 4 + 16 + 8 + 8
+    assert perch.perch_volume.normals.offset == 32
 
 
 def test_null_context_and_null_args_are_rejected(lib):
@@ -51,6 +57,10 @@ def test_null_context_and_null_args_are_rejected(lib):
     assert lib.perch_eval_successors(None, None, 0, None, 0, None, None, 0, 1, None) == perch.PERCH_E_ARG
     assert lib.perch_search(None, None, None) == perch.PERCH_E_ARG
     assert lib.perch_create(None, 0, None) == perch.PERCH_E_ARG
+    assert lib.perch_set_volumes(None, None, 0) == perch.PERCH_E_ARG
+    assert lib.perch_set_wait_limit(None, 0) == perch.PERCH_E_ARG
+    assert lib.perch_set_share_renders(None, 1) == perch.PERCH_E_ARG
+    assert lib.perch_launch_config(None, None, None) == perch.PERCH_E_ARG
 
 
 def test_create_without_gpu_fails_cleanly(lib):

@@ -5,9 +5,26 @@ centre and float/bfloat16 rounding). The network's forward and backward pass
 run in bfloat16 with FP32 accumulation and bfloat16 gradients between layers,
 against the oracle in float64 with the same bfloat16 rounding of inputs,
 activations and weights: predictions within 2e-2 (absolute, on targets of
-size ~1), every gradient tensor within a relative L2 error of 3e-2 (bfloat16
-carries 8 significant bits: 2^-9 relative per rounding, a few roundings deep,
-and sums of thousands of terms), and the loss within 1e-2 relative.
+size ~1) and the loss within 1e-2 relative. Gradients are compared element by
+element: the oracle's backward pass is given the GPU's own prediction error
+(its target shifted by pred_gpu - pred_oracle), so only the backward pass
+separates them. The GPU stores every gradient between layers in bfloat16
+(relative rounding 2^-9 per element) and the deepest weight gradient sits
+six such roundings below the loss; FP32 accumulation adds n 2^-24 relative
+per term. With S the root of the sum of the squared terms an element adds up
+(oracle.cnn.grad_magnitudes), independent roundings move it like a random
+walk over the fan-in, so each element must satisfy
+    |g - e| <= 8 2^-9 S + 2^-7 |e|      (8 standard widths).
+Exceptions have a known cause: where a pre-activation lies within the two
+sides' accumulation difference of zero, their ReLU masks differ, and that
+one position adds or drops a whole term, in the forward pass (an activation
+feeding every weight gradient of the next layer) or in the backward pass (a
+gradient feeding every weight gradient of its output channel). Measured:
+0.17% of conv4's 147k weight gradients; an FC1 gradient with one term
+doubled. So in a tensor of 1000 or more elements at most 0.5% may exceed the
+bound, and in a smaller tensor at most one element. A wrong sign or index on
+a slice of a tensor (one channel of 128 is 0.78%, one tap of nine 11%) moves
+its elements by about |e| or S and fails it.
 """
 import numpy as np
 import pytest
@@ -63,10 +80,6 @@ def _net_with(params, n_onehot, max_batch=64):
     return net
 
 
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-
-
 def test_gradients_match_oracle(c1):
     wl, p, w = c1
     n_onehot = len(wl.meshes) * wl.grid.n_yaw
@@ -81,15 +94,27 @@ def test_gradients_match_oracle(c1):
     g, loss, pred = net.perch_cnn_gradients(crops, onehot, target)
     # the parameters the network holds: round-trip of the set values
     assert np.array_equal(net.perch_cnn_get_params(), np.concatenate([a.astype(np.float32).ravel() for a in params]))
-    el, eg, ep = cnn.loss_and_grads(params, x, cnn.onehot(idx, n_onehot), y, bf16=True)
+    oh = cnn.onehot(idx, n_onehot)
+    el, _, ep = cnn.loss_and_grads(params, x, oh, y, bf16=True)
     assert np.max(np.abs(pred - ep)) < 2e-2
     assert abs(loss - el) <= 1e-2 * el
-    off = 0
-    for k, e in enumerate(eg):
-        got = g[off:off + e.size].reshape(e.shape)
+    # the oracle's backward pass from the GPU's prediction error
+    y_adj = y - (pred.astype(np.float64) - ep)
+    _, eg, _ = cnn.loss_and_grads(params, x, oh, y_adj, bf16=True)
+    _, rss = cnn.grad_magnitudes(params, x, oh, y_adj, bf16=True)
+    off, n_el, n_stat = 0, 0, 0
+    for k, (e, r) in enumerate(zip(eg, rss)):
+        got = g[off:off + e.size].reshape(e.shape).astype(np.float64)
         off += e.size
-        assert _rel(got, e) < 3e-2, (k, _rel(got, e))
-    assert off == net.n_params
+        err = np.abs(got - e)
+        stat = 8 * 2.0 ** -9 * r + 2.0 ** -7 * np.abs(e) + 1e-30
+        ok = err <= stat
+        worst = np.unravel_index(np.argmax(err / stat), e.shape)
+        allowed = int(0.005 * e.size) if e.size >= 1000 else 1
+        assert int((~ok).sum()) <= allowed, (k, ok.mean(), worst, got[worst], e[worst], r[worst])
+        n_el += e.size
+        n_stat += int(ok.sum())
+    assert off == net.n_params == n_el and n_stat >= 0.995 * n_el
 
 
 def test_forward_ragged_batch_matches_oracle(c1):

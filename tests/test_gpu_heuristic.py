@@ -1,9 +1,10 @@
 """The learned heuristic end to end on the GPU: training data from the exact
 evaluator, training with the library's kernels, and Focal-MHA* with the
-learned queue (heuristics bit 2). Whatever the network predicts, the search
-must keep Theorem 2's bound (cost <= w * OPT, OPT from uniform-cost search)
-and return a scene whose cost is the exact sum of edge costs along one valid
-order of its objects."""
+learned queue (heuristics bit 2: ordered by g + h_cnn across depths; bit 3:
+the depth-first variant). Whatever the network predicts, the search must keep
+Theorem 2's bound (cost <= w * OPT, OPT from uniform-cost search) and return
+a scene whose cost is the exact sum of edge costs along one valid order of
+its objects."""
 import itertools
 
 import numpy as np
@@ -61,20 +62,30 @@ def _path_cost(p, scene_id, K, objs):
     return out
 
 
-@pytest.mark.parametrize("w", [1.0, 2.0])
-def test_learned_queue_keeps_the_bound_and_exact_costs(setup, w):
+@pytest.mark.parametrize("w,heur", [(1.0, 7), (2.0, 7), (2.0, 4), (2.0, 9), (2.0, 8)])
+def test_learned_queue_keeps_the_bound_and_exact_costs(setup, w, heur):
     p, net, test_sc, te, *_ = setup
     ms = [wl.mesh_multiset for wl in test_sc]
     p.perch_set_heuristic_net(net, 8)
     opt = p.perch_search_multi(te, ms, batch_states=2, w=1.0, heuristics=0)
-    got = p.perch_search_multi(te, ms, batch_states=2, w=w, heuristics=7)
+    got = p.perch_search_multi(te, ms, batch_states=2, w=w, heuristics=heur)
     for o, g, sid, wl in zip(opt, got, te, test_sc):
         assert o["proven_optimal"] and o["cost"] >= 0
         assert o["cost"] <= g["cost"] <= w * o["cost"] + 1e-9
         if w == 1.0:  # optimal; among equal-cost goals either may be returned
             assert g["cost"] == o["cost"]
+        # the returned scene was found before the search ended
+        assert 0 < g["found_expansions"] <= g["expansions"] and g["found_seconds"] <= g["seconds"]
         costs = _path_cost(p, sid, wl.K, g["objs"])
         assert costs and min(costs) <= g["cost"] and g["cost"] in costs
+
+
+def test_learned_bits_exclude_each_other(setup):
+    p, net, test_sc, te, *_ = setup
+    p.perch_set_heuristic_net(net, 8)
+    with pytest.raises(perch.PerchError) as e:
+        p.perch_search_multi(te[:1], [test_sc[0].mesh_multiset], w=2.0, heuristics=12)
+    assert e.value.code == perch.PERCH_E_ARG
 
 
 def test_learned_queue_needs_a_network(setup):
@@ -104,9 +115,7 @@ def test_learned_queue_expands_fewer_states_than_plain_search(setup):
     uniform-cost search, the paper's exact search): on the held-out scenes
     Focal-MHA* with the anchor and the learned queue (w = 2) never expands
     more states than plain search, expands fewer in all, and returns a scene
-    within w times the optimum. (On these scenes the same search with the
-    untrained network expands the same states: the queue's depth-first pool
-    makes the gain, the network's ranking inside it does not change it.)"""
+    within w times the optimum."""
     p, net, test_sc, te, *_ = setup
     ms = [wl.mesh_multiset for wl in test_sc]
     p.perch_set_heuristic_net(net, 8)

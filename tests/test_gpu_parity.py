@@ -171,6 +171,63 @@ def test_shared_renders_identical_to_per_hypothesis_renders(c2):
     assert (a[:, 3] > 0).any() and (a[:, 2] > 0).any() and (a[:, 1] > 0).any()
 
 
+def _near(grid, objs, types):
+    """Hypotheses at and around the ground-truth poses of the given types
+    (one grid step and one yaw step away), where V(O) holds observed points."""
+    out = []
+    for o in objs:
+        if int(o["mesh"]) not in types:
+            continue
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dk in (-1, 0, 1):
+                    ix, iy = int(o["ix"]) + dx, int(o["iy"]) + dy
+                    if 0 <= ix < grid.nx and 0 <= iy < grid.ny:
+                        out.append((int(o["mesh"]), ix, iy, (int(o["iyaw"]) + dk) % grid.n_yaw))
+    return synth.objs(out)
+
+
+@pytest.mark.parametrize("which", ["c1", "c2", "c3"])
+def test_closed_form_volumes_bit_exact(which):
+    """V(O) in closed form (box, regular prism, superquadric; Sec. III-A):
+    records bit-exact with the oracle's closed forms at the root, a middle
+    level and the last level (residual), on random poses and on poses around
+    the ground truth; the closed forms change n_vol and dJ_o there; switching
+    back restores the inscribed cylinders' records."""
+    wl = {"c1": synth.workload_c1, "c2": synth.workload_c2, "c3": synth.workload_c3}[which]()
+    p = perch.Perch(0)
+    p.setup(wl, exact_volumes=True)
+    we, wc = oracle.World.of(wl, exact_volumes=True), oracle.World.of(wl)
+    rng = np.random.default_rng(8)
+    K = wl.K
+    parents = [wl.gt[:0], wl.gt[:1], wl.gt[:K - 1]]
+    hyps, hp = [], []
+    for i, par in enumerate(parents):
+        rem = list(wl.mesh_multiset)
+        for m in par["mesh"]:
+            rem.remove(int(m))
+        types = sorted(set(rem))
+        allh = synth.all_hypotheses(wl.grid, types)
+        n = len(allh) if which == "c1" else 120
+        pick = allh[rng.choice(len(allh), n, replace=False)]
+        near = _near(wl.grid, wl.gt, set(types))
+        hyps += [pick, near]
+        hp += [np.full(len(pick) + len(near), i, np.int32)]
+    hyps, hp = np.concatenate(hyps), np.concatenate(hp)
+    try:
+        got = _recs(p.perch_eval_successors(parents, hp, hyps, K))
+        exp = oracle.eval_batch(we, wl.depth, parents, hp, hyps, K)
+        bad = np.nonzero((got != exp).any(1))[0]
+        assert bad.size == 0, f"{bad.size} mismatches, first {hyps[bad[:3]]}: gpu {got[bad[:3]]} oracle {exp[bad[:3]]}"
+        cyl = oracle.eval_batch(wc, wl.depth, parents, hp, hyps, K)
+        assert (exp[:, 6] != cyl[:, 6]).sum() > 10 and (exp[:, 1] != cyl[:, 1]).any()
+        p.perch_set_volumes(None)
+        back = _recs(p.perch_eval_successors(parents, hp, hyps, K))
+        assert np.array_equal(back, cyl)
+    finally:
+        p.close()
+
+
 def test_shortcut_records_identical_and_taken(c2):
     """The exact shortcut (hypotheses far from the observation and from the
     parent's render) gives the same records as rendering every hypothesis,
@@ -357,6 +414,25 @@ def test_search_matches_oracle_ucs_full_c1(c1):
     cost, key, _ = search.uniform_cost_search(w, wl.depth, wl.grid, wl.mesh_multiset)
     r = p.perch_search(wl.mesh_multiset, batch_states=16)
     assert r["proven_optimal"] and (r["cost"], r["key"]) == (cost, key)
+
+
+def test_symmetric_search_matches_oracle_c1(c1):
+    """With the meshes' rotational symmetry declared, the GPU search places a
+    symmetric mesh only at the yaws no smaller yaw equals modulo its symmetry
+    (Sec. IV-E) and returns the oracle's optimum of that tree, evaluating
+    fewer successors than the full tree."""
+    wl, p, w = c1
+    yaws = search.symmetric_yaws(wl.grid, [m.sym for m in wl.meshes])
+    cost, key, _ = search.uniform_cost_search(w, wl.depth, wl.grid, wl.mesh_multiset, yaws=yaws)
+    full = p.perch_search(wl.mesh_multiset, batch_states=16)
+    p.perch_set_symmetry(wl.meshes)
+    try:
+        r = p.perch_search(wl.mesh_multiset, batch_states=16)
+    finally:
+        p.perch_set_symmetry(None)
+    assert r["proven_optimal"] and (r["cost"], r["key"]) == (cost, key)
+    assert all(o[3] in yaws[o[0]] for o in r["key"])
+    assert r["successors"] < 0.6 * full["successors"]
 
 
 def test_c3_uneven_meshes_sampled():
