@@ -91,15 +91,17 @@ def algorithmic_ops(wl, poses, covered, n_new):
     """Lower bound of the arithmetic one evaluation step must do, split by
     kernel. Render (k_render, once per distinct pose): 40 ops per mesh vertex
     (pose + camera transform, projection, snap, reciprocal depth), 20 per
-    triangle (edge setup, facing and extent tests, pixel box), 30 per covered
-    pixel (3 edge functions, depth interpolation, z-buffer max). Cost (k_cost,
-    per hypothesis): 20 per pixel of dR (back-projection and the first delta
-    probe). Returns (render ops, cost ops)."""
+    triangle (edge setup, facing and extent tests, pixel box), 50 per covered
+    pixel (3 edge functions, depth interpolation, z-buffer max, reciprocal,
+    back-projection and the first delta probe of Eq. (1), which k_render
+    decides once per pose). Cost (k_cost, per hypothesis): 10 per pixel of dR
+    (parent compare, classification, the counts). Returns (render ops, cost
+    ops)."""
     V = np.array([m.n_verts for m in wl.meshes], np.float64)
     T = np.array([m.n_tris for m in wl.meshes], np.float64)
     mi = poses["mesh"].astype(np.int64)
-    render = float((40.0 * V[mi] + 20.0 * T[mi]).sum() + 30.0 * np.asarray(covered, np.float64).sum())
-    return render, 20.0 * float(np.asarray(n_new, np.float64).sum())
+    render = float((40.0 * V[mi] + 20.0 * T[mi]).sum() + 50.0 * np.asarray(covered, np.float64).sum())
+    return render, 10.0 * float(np.asarray(n_new, np.float64).sum())
 
 
 class ClockSampler:
@@ -426,14 +428,26 @@ def run_ours(args):
                 "meaning": "exact shortcut on: hypotheses far from the observation and from the parent's render get "
                            "their record from a per-pose solo render table instead of being rasterised again"}
 
-    # time to the optimal scene (uniform-cost search, exact; shortcut on)
+    # time to the optimal scene (uniform-cost search, exact; shortcut on),
+    # over the full tree and over the tree with the meshes' rotational
+    # symmetry (Sec. IV-E), with the pose accuracy of both (Sec. V-D)
     search = None
     if not args.no_search:
-        r = p.perch_search(wl.mesh_multiset, batch_states=args.batch_states, time_limit_s=args.search_limit)
+        from paper_1510_05613_gb300 import accuracy
         gt_key = tuple(sorted((int(o["mesh"]), int(o["ix"]), int(o["iy"]), int(o["iyaw"])) for o in wl.gt))
-        search = {"seconds": r["seconds"], "proven_optimal": r["proven_optimal"], "cost": r["cost"],
-                  "expansions": r["expansions"], "successors": r["successors"],
-                  "found_ground_truth": r["key"] == gt_key, "batch_states": args.batch_states}
+
+        def one_search():
+            r = p.perch_search(wl.mesh_multiset, batch_states=args.batch_states, time_limit_s=args.search_limit)
+            return {"seconds": r["seconds"], "proven_optimal": r["proven_optimal"], "cost": r["cost"],
+                    "expansions": r["expansions"], "successors": r["successors"],
+                    "found_ground_truth": r["key"] == gt_key, "batch_states": args.batch_states,
+                    "pose_accuracy": accuracy.report([r], [wl], wl.meshes)}
+
+        search = one_search()
+        p.perch_set_symmetry(wl.meshes)
+        search["symmetric"] = one_search()
+        search["symmetric"]["symmetry_orders"] = [int(m.sym) for m in wl.meshes]
+        p.perch_set_symmetry(None)
 
     base = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -470,6 +484,7 @@ def run_ours(args):
             "e2e": e2e, "e2e_matches_device_records": consistent,
             "gpu_launches": ((14 + 2 * len(wl.meshes)) if shared else (8 + len(wl.meshes))) * args.steps,
             "launch": {"graph": not args.no_graph, "persistent_per_mesh": True, "autotuned_threads": widths,
+                       "config_in_use": dict(zip(("render_threads", "cost_threads"), p.perch_launch_config())),
                        "shared_renders": shared},
             "clocks": cl,
             "time_to_optimum": search,
@@ -529,7 +544,7 @@ def run_c5(args):
     into shared evaluation launches (perch_search_multi). Reports aggregate
     hypotheses/s over the whole run and per-scene time to the optimum."""
     import torch
-    from paper_1510_05613_gb300 import perch
+    from paper_1510_05613_gb300 import accuracy, perch
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
@@ -566,6 +581,7 @@ def run_c5(args):
             "time_to_optimum_p50_s": float(np.percentile(done, 50)) if done else None,
             "time_to_optimum_p99_s": float(np.percentile(done, 99)) if done else None,
             "successors": succ, "wall_s": wall, "host_peak_rss_gib": mem.peak / 2**30,
+            "pose_accuracy": accuracy.report(res, wls, wls[0].meshes),
             "hbm": hbm_fields(succ / wall, None), "paper_context": PAPER_CONTEXT, "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)
     p.close()
@@ -717,6 +733,7 @@ def run_c4(args):
     Every arm searches all scenes at once (perch_search_multi). Objects sit
     off the pose grid by up to half a step (--off-grid)."""
     import torch
+    from paper_1510_05613_gb300 import accuracy
     from paper_1510_05613_gb300 import heuristic as H
     from paper_1510_05613_gb300 import perch
 
@@ -786,6 +803,9 @@ def run_c4(args):
                 "time_to_scene_p50_s": float(np.percentile([x["seconds"] for x in fin], 50)) if fin else None,
                 "time_to_scene_mean_s": float(np.mean([x["seconds"] for x in fin])) if fin else None,
                 "expansions_mean": float(np.mean([x["expansions"] for x in r])),
+                "found_p50_s": float(np.percentile([x["found_seconds"] for x in r if x["cost"] >= 0], 50))
+                if any(x["cost"] >= 0 for x in r) else None,
+                "found_expansions_mean": float(np.mean([x["found_expansions"] for x in r])),
                 "successors_mean": float(np.mean([x["successors"] for x in r])),
                 "same_scene_as_plain": sum(a["key"] == b["key"] for a, b in both),
                 "compared_with_plain": len(both),
@@ -796,7 +816,9 @@ def run_c4(args):
                 "learned_crops": learned_cost[name][2],
                 "search_eval_s": learned_cost[name][3], "search_absorb_s": learned_cost[name][4],
                 "search_select_s": learned_cost[name][5],
+                "pose_accuracy": accuracy.report(r, test_sc, test_sc[0].meshes),
                 "per_scene": [{"cost": x["cost"], "expansions": x["expansions"], "seconds": round(x["seconds"], 3),
+                               "found_expansions": x["found_expansions"], "found_s": round(x["found_seconds"], 3),
                                "proven": x["proven_optimal"]} for x in r]}
 
     head = next((n for n in ("mha_depth+learned", "mha_learned", "mha+learned", "mha_depth", "plain") if n in out),
