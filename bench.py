@@ -368,7 +368,11 @@ def run_ours(args):
     # pixels each distinct pose covers: its record against the empty parent
     poses = distinct_poses(hyps)
     covered = perch.records(p.perch_eval_successors([wl.gt[:0]], np.zeros(len(poses), np.int32), poses, wl.K))[:, 4]
-    render_ops, cost_ops = algorithmic_ops(wl, poses, covered, rec[:, 4])
+    if not shared:  # one render per hypothesis (a batch of one parent): k_eval renders and costs each
+        covered = covered[np.searchsorted(poses, np.ascontiguousarray(hyps))]
+    render_ops, cost_ops = algorithmic_ops(wl, poses if shared else hyps, covered, rec[:, 4])
+    if not shared:  # both in the one kernel, timed as the render phase
+        render_ops, cost_ops = render_ops + cost_ops, 0.0
     peaks = _measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(dev)
@@ -484,7 +488,8 @@ def run_ours(args):
             "e2e": e2e, "e2e_matches_device_records": consistent,
             "gpu_launches": ((14 + 2 * len(wl.meshes)) if shared else (8 + len(wl.meshes))) * args.steps,
             "launch": {"graph": not args.no_graph, "persistent_per_mesh": True, "autotuned_threads": widths,
-                       "config_in_use": dict(zip(("render_threads", "cost_threads"), p.perch_launch_config())),
+                       "config_in_use": dict(zip(("render_threads", "render_inline_pixels", "cost_threads"),
+                                                 p.perch_launch_config())),
                        "shared_renders": shared},
             "clocks": cl,
             "time_to_optimum": search,
@@ -556,6 +561,8 @@ def run_c5(args):
     for s, wl in enumerate(wls[1:], 1):
         p.perch_set_scene(s, wl.depth)
     p.perch_autotune(args.tune_sample)
+    if args.symmetric:
+        p.perch_set_symmetry(wls[0].meshes)
     with ClockSampler(0) as clocks, MemoryGuard() as mem:
         t0 = time.perf_counter()
         res = p.perch_search_multi(list(range(len(wls))), [wl.mesh_multiset for wl in wls],
@@ -572,8 +579,9 @@ def run_c5(args):
                                    "search per scene, expansions of all scenes packed into shared launches",
                        "scenes": len(wls), "launch_hyps": args.launch_hyps, "batch_states": args.batch_states,
                        "time_limit_s": args.search_limit, "generation_s": gen_s},
-            "search": {"w": args.w, "heuristics": args.heuristics,
-                       "meaning": "cost <= w x optimum (Focal-MHA*, Theorem 2)" if args.w > 1 else "optimal"},
+            "search": {"w": args.w, "heuristics": args.heuristics, "symmetric": bool(args.symmetric),
+                       "meaning": ("cost <= w x optimum (Focal-MHA*, Theorem 2)" if args.w > 1 else "optimal") +
+                                  (" of the tree with each mesh's symmetric yaws merged" if args.symmetric else "")},
             "scenes_finished": len(done),
             "ground_truth_found": sum(
                 r["key"] == tuple(sorted((int(o["mesh"]), int(o["ix"]), int(o["iy"]), int(o["iyaw"])) for o in wl.gt))
@@ -747,6 +755,8 @@ def run_c4(args):
     tr = H.setup_scenes(p, train_sc)
     te = H.setup_scenes(p, test_sc, first_id=len(train_sc))
     p.perch_autotune(args.tune_sample)
+    if args.symmetric:
+        p.perch_set_symmetry(train_sc[0].meshes)
     stream = torch.cuda.Stream()
     n_onehot = len(train_sc[0].meshes) * grid.n_yaw
     data, dstats = H.make_dataset(p, train_sc, tr, per_parent=args.per_parent, seed=1)
@@ -835,6 +845,7 @@ def run_c4(args):
                                    f"on {dstats['pairs']} exact (crop, edge cost) pairs of {len(train_sc)} seeded "
                                    "2-5-object scenes",
                        "train_scenes": len(train_sc), "pairs": dstats["pairs"], "epochs": args.epochs, "batch": 256,
+                       "symmetric": bool(args.symmetric),
                        "candidates": args.candidates, "time_limit_s": args.search_limit, "generation_s": gen_s,
                        "dataset_s": dstats["seconds"]},
             "training": {"seconds": train_s, "steps": steps, "crops_per_s": steps * 256 / train_s,
@@ -887,6 +898,8 @@ def main():
                                                "mha_learned_untrained, mha_learned_dive, mha_learned_dive_untrained, "
                                                "mha, mha_depth+learned, mha_depth+learned_untrained, mha+learned "
                                                "(default: all)")
+    ap.add_argument("--symmetric", action="store_true",
+                    help="c4/c5: searches place each mesh only at yaws distinct modulo its rotational symmetry")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "cnn"],
                     help="c2: 640x480 three ~10k-triangle meshes (the headline); c3: heavy occlusion, 2k-50k triangles")
     args = ap.parse_args()

@@ -325,9 +325,10 @@ int perch_search_stats(perch_ctx* ctx, double* learned_seconds, int64_t* learned
  * may be NULL. */
 int perch_search_times(perch_ctx* ctx, double* eval_seconds, double* absorb_seconds, double* select_seconds);
 
-/* Launch tuning (not in the paper). The evaluation runs one persistent
- * launch per mesh with a shared-memory tile sized for that mesh; this call
- * times each CTA width the kernel is built for (128, 256, 512 threads) on
+/* Launch tuning (not in the paper). The evaluation runs persistent launches
+ * per mesh with a shared-memory tile sized for that mesh; this call times the
+ * launch parameters (see perch_launch_config: CTA widths 128, 256, 512 and
+ * the render's inline limit; the cost launch's width) on
  * max(n_sample, 32 x SM count) hypotheses of each mesh (a fixed spread of its poses, children of
  * the empty scene), keeps the fastest per mesh for all later evaluations on
  * this context, and writes them to threads_out[n_mesh] (may be NULL). Results
@@ -341,10 +342,19 @@ int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads_out);
 int perch_set_threads(perch_ctx* ctx, int32_t mesh, int32_t threads);
 
 /* The launch configuration evaluations use now, per mesh (arrays of the
- * number of meshes, either may be NULL): the CTA width of the render (or
- * per-hypothesis evaluation) launch and of the cost launch. perch_autotune
- * times both with shared renders on (the cost width among 128 and 256). */
-int perch_launch_config(perch_ctx* ctx, int32_t* render_threads, int32_t* cost_threads);
+ * number of meshes, any may be NULL): the CTA width of the render (or
+ * per-hypothesis evaluation) launch, the render's inline limit (a front-facing
+ * triangle with at most that many candidate pixel centres is rasterised by
+ * its own thread, a larger one by a warp through the CTA's queue) and the CTA
+ * width of the cost launch. With shared renders on, perch_autotune times
+ * every render width with every inline limit (8, 16, 32), then the cost
+ * widths 128 and 256. */
+int perch_launch_config(perch_ctx* ctx, int32_t* render_threads, int32_t* inline_pixels, int32_t* cost_threads);
+
+/* Set the render's inline limit (8, 16 or 32) for one mesh (mesh = -1: all),
+ * overriding the default 16 or an autotuned choice. Records do not depend on
+ * it (coverage resolves by an order-independent max). */
+int perch_set_inline_pixels(perch_ctx* ctx, int32_t mesh, int32_t inline_pixels);
 
 /* Same work and arguments as perch_eval_successors_dev (device pointers), run
  * as a CUDA graph: the first call for a given argument set (and after any
@@ -379,8 +389,9 @@ int perch_set_shortcut(perch_ctx* ctx, int32_t on);
  * hypothesis is then compared with its own parent render and costed from
  * that tile. Records are identical with sharing on or off; on = 0 renders
  * every hypothesis separately (one kernel per hypothesis, no tile store).
- * Sharing also stays off when the tile store would take more than a quarter
- * of the free device memory. */
+ * Sharing applies to batches of two or more parents (one parent repeats no
+ * pose), and stays off when the tile store would take more than a quarter of
+ * the free device memory. */
 int perch_set_share_renders(perch_ctx* ctx, int32_t on);
 
 /* Device time of the four phases of the most recent evaluation (CUDA

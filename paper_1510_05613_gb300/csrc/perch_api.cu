@@ -157,6 +157,7 @@ int perch_ctx::ensure_tables() {
     return fail(PERCH_E_RANGE, "object screen box %dx%d does not fit in shared memory", tile_w, tile_h);
   if ((int)mesh_threads.size() != n_mesh) mesh_threads.assign(n_mesh, 256);
   if ((int)mesh_cost_threads.size() != n_mesh) mesh_cost_threads.assign(n_mesh, 128);
+  if ((int)mesh_inline.size() != n_mesh) mesh_inline.assign(n_mesh, kInlinePixels);
   const int rc = ensure_tile_store();
   if (rc != PERCH_OK) return rc;
   tables_valid = true;
@@ -812,7 +813,9 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
   short_counted = use_short;
   last_total = n_hyp;
   if (!capturing) CK(cudaEventRecord(ev[1], stream), "event");
-  if (share_renders && store_ok) {
+  // a batch of one parent repeats no pose: rendering per hypothesis skips the
+  // tile store's round trip
+  if (share_renders && store_ok && n_par >= 2) {
     // shared renders: group by pose; per mesh one persistent launch renders
     // its distinct poses into the tile store, then one costs its hypotheses
     const int per_mesh = nx * ny * n_yaw, P = per_mesh * n_mesh;
@@ -837,8 +840,8 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
       bm.tile_h = mesh_tile_h[m];
       const RenderWork w{pg.gpose, rg + 4 * m + 2, rg + 4 * m + 3, g_next.as<int>() + m, tile_store.as<uint32_t>(),
                          tile_off.as<int>(), pose_flags.as<uint8_t>()};
-      CK(launch_render_group(cam, g, obs, bm, w, std::min<long long>(n_hyp, per_mesh), mesh_threads[m], sm_count,
-                             stream),
+      CK(launch_render_group(cam, g, obs, bm, w, std::min<long long>(n_hyp, per_mesh), mesh_threads[m],
+                             mesh_inline[m], sm_count, stream),
          "render kernel");
     }
     if (!capturing) CK(cudaEventRecord(ev[3], stream), "event");

@@ -101,6 +101,7 @@ struct perch_ctx {
   DevBuf tile_store, tile_off, tile_sizes, pose_flags;
   DevBuf pg_cnt, pg_start, pg_flag, pg_gix, pg_gpose, pg_tmp, pg_ranges;  // hypotheses grouped by pose
   std::vector<int> mesh_cost_threads;  // CTA width of k_cost per mesh (autotuned; 128 by default)
+  std::vector<int> mesh_inline;        // k_render's inline limit per mesh (autotuned; 16 by default)
   int last_path = 0;       // last evaluation: 1 = one render per hypothesis, 2 = shared renders
   DevBuf b_parents, b_plen, b_hp, b_hyp, b_out;
 

@@ -16,7 +16,8 @@ constexpr int kChunkMaxVerts = 512;   // vertices of one mesh chunk (10-bit loca
 constexpr int kChunkMaxTris = 1024;   // triangles of one mesh chunk (list padded to 4 entries)
 constexpr int kEvalThreads = 256;
 constexpr int kEvalWarps = kEvalThreads / 32;
-constexpr int kInlinePixels = 16;  // a lane tests at most this many pixel centres per triangle
+constexpr int kInlinePixels = 16;  // a lane tests at most this many pixel centres per triangle (k_eval;
+                                   // k_render takes 8, 16 or 32 per mesh from the autotuner)
 constexpr int kBigQueue = 128;     // per-chunk queue of larger triangles, shared by the CTA
 constexpr int kWaitSpins = 1 << 20;  // bound on mbarrier polls before a kernel gives up
 constexpr int kMaxObjectPixels = 1000;  // screen box limit that keeps edge arithmetic in int32
@@ -210,8 +211,8 @@ cudaError_t launch_tile_offsets(const Geometry& g, int* sizes, int* tile_off, in
 // leaves out those the shortcut answered (b.skip)
 cudaError_t launch_group_by_pose(const Geometry& g, const Batch& b, const PoseGroups& pg, cudaStream_t s);
 cudaError_t launch_render_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
-                                const RenderWork& w, long long max_items, int threads, int sm_count,
-                                cudaStream_t s);
+                                const RenderWork& w, long long max_items, int threads, int inline_px,
+                                int sm_count, cudaStream_t s);
 cudaError_t launch_cost_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
                               const CostWork& w, long long max_items, int threads, int sm_count, cudaStream_t s);
 // loads the kernels the allocation-free evaluation launches (a lazily loaded

@@ -857,15 +857,17 @@ __device__ __forceinline__ void render_start(const Geometry& g, const DevMesh& m
 // chunk c+1's vertices is issued as soon as chunk c's vertices are projected,
 // and the copy of its triangles as soon as chunk c's triangles are set up, so
 // the loads overlap the rasterisation. Each thread sets up triangles; a
-// front-facing triangle whose box holds at most kInlinePixels pixel centres
-// is rasterised by its thread, a larger one is queued and its pixel centres
-// are split across a warp. Edge arithmetic stays in int32: every object's
+// front-facing triangle whose box holds at most INL pixel centres (the inline
+// limit, a launch parameter the autotuner picks) is rasterised by its thread,
+// a larger one is queued and its pixel centres are split across a warp; a full
+// queue falls back to the thread. Coverage resolves by an order-independent
+// max, so the tile does not depend on INL. Edge arithmetic stays in int32: every object's
 // screen box is at most kMaxObjectPixels wide (checked at set-up), so
 // tile-relative coordinates (kept as int16 pairs) and all edge-function
 // values are far below 2^31. `culled` is set in the threads that dropped a
 // triangle. On kEvalTimedOut / kEvalStop the tile is incomplete; the caller
 // reports the failure and must pass a CTA barrier before reusing the tile.
-template <int NT>
+template <int NT, int INL>
 __device__ __forceinline__ int render_chunks(const Camera& cam, const Geometry& g, const Batch& b, const DevMesh& m,
                                              const perch_obj& o, int4 bb, const RenderSmem& s, EvalShared& sh,
                                              unsigned& culled) {
@@ -933,7 +935,7 @@ __device__ __forceinline__ int render_chunks(const Camera& cam, const Geometry& 
         const int py0 = max(ceil16(min(va.y, min(vb.y, vc.y))), 0);
         const int py1 = min(floor16(max(va.y, max(vb.y, vc.y))), th - 1);
         if (px0 > px1 || py0 > py1) continue;
-        if ((px1 - px0 + 1) * (py1 - py0 + 1) > kInlinePixels && px1 - px0 < 64 && py1 - py0 < 64) {
+        if ((px1 - px0 + 1) * (py1 - py0 + 1) > INL && px1 - px0 < 64 && py1 - py0 < 64) {
           const int slot = atomicAdd(&s_qn, 1);
           if (slot < kBigQueue) {  // (triangle, box): x0 10 bits, y0 10 bits, w-1 and h-1 6 bits each
             queue[2 * slot] = pk;
@@ -1231,7 +1233,7 @@ __device__ int eval_one(long long h, const Camera& cam, const Geometry& g, const
   if (tid < 7) s_cnt[tid] = 0;
 
   unsigned culled = 0;
-  const int st = render_chunks<NT>(cam, g, b, m, a.o, bb, s, sh, culled);
+  const int st = render_chunks<NT, kInlinePixels>(cam, g, b, m, a.o, bb, s, sh, culled);
   if (st != kEvalDone) {
     if (tid == 0) {
       perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout, 0};
@@ -1290,7 +1292,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_eval(Camera cam, Geometry g, 
 // the pose's screen box at 16-byte offset tile_off[pose]), and k_cost gives
 // every hypothesis its own comparison with its parent and its own costs
 // from that stored tile, read with plain coalesced loads.
-template <int NT, bool EXPL>
+template <int NT, bool EXPL, int INL>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_render(Camera cam, Geometry g, ObsIndex obs, Batch b,
                                                           RenderWork w) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1332,7 +1334,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_render(Camera cam, Geometry g
     for (int ly = warp; ly < th; ly += NW)
       for (int lx = lane; lx < tw; lx += 32) s.tile[ly * tw + lx] = 0u;  // 1/z = 0: empty
     unsigned culled = 0;
-    const int st = render_chunks<NT>(cam, g, b, m, o, bb, s, sh, culled);
+    const int st = render_chunks<NT, INL>(cam, g, b, m, o, bb, s, sh, culled);
     if (st != kEvalDone) {
       if (tid == 0) w.pose_flags[p] = kPoseFailed;
       __syncthreads();  // the tile is cleared by the next pose
@@ -1731,11 +1733,11 @@ static cudaError_t launch_group_t(const Camera& cam, const Geometry& g, const Ob
   return cudaGetLastError();
 }
 
-template <int NT, bool EXPL>
+template <int NT, bool EXPL, int INL>
 static cudaError_t launch_render_t(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
                                    const RenderWork& w, long long max_items, int sm_count, cudaStream_t s) {
   const size_t smem = render_smem_bytes(b.tile_w, b.tile_h);
-  auto kern = k_render<NT, EXPL>;
+  auto kern = k_render<NT, EXPL, INL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -1749,22 +1751,34 @@ static cudaError_t launch_render_t(const Camera& cam, const Geometry& g, const O
   return cudaGetLastError();
 }
 
+template <int NT, bool EXPL>
+static cudaError_t launch_render_i(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                                   const RenderWork& w, long long max_items, int inline_px, int sm_count,
+                                   cudaStream_t s) {
+  switch (inline_px) {
+    case 8: return launch_render_t<NT, EXPL, 8>(cam, g, obs, b, w, max_items, sm_count, s);
+    case 32: return launch_render_t<NT, EXPL, 32>(cam, g, obs, b, w, max_items, sm_count, s);
+    default: return launch_render_t<NT, EXPL, 16>(cam, g, obs, b, w, max_items, sm_count, s);
+  }
+}
+
 // One persistent launch rendering one mesh's distinct poses of a batch into
-// the tile store, with CTAs of `threads` (128, 256 or 512) and the mesh's
-// tile (b.tile_w x b.tile_h). A single-scene batch also stores each rendered
+// the tile store, with CTAs of `threads` (128, 256 or 512), the inline limit
+// `inline_px` (8, 16 or 32 candidate pixel centres) and the mesh's tile
+// (b.tile_w x b.tile_h). A single-scene batch also stores each rendered
 // point's Eq. (1) test against `obs`.
 cudaError_t launch_render_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
-                                const RenderWork& w, long long max_items, int threads, int sm_count,
-                                cudaStream_t s) {
+                                const RenderWork& w, long long max_items, int threads, int inline_px,
+                                int sm_count, cudaStream_t s) {
   if (max_items <= 0) return cudaSuccess;
   const bool expl = b.parent_scene == nullptr;
   switch (threads) {
-    case 128: return expl ? launch_render_t<128, true>(cam, g, obs, b, w, max_items, sm_count, s)
-                          : launch_render_t<128, false>(cam, g, obs, b, w, max_items, sm_count, s);
-    case 512: return expl ? launch_render_t<512, true>(cam, g, obs, b, w, max_items, sm_count, s)
-                          : launch_render_t<512, false>(cam, g, obs, b, w, max_items, sm_count, s);
-    default: return expl ? launch_render_t<256, true>(cam, g, obs, b, w, max_items, sm_count, s)
-                         : launch_render_t<256, false>(cam, g, obs, b, w, max_items, sm_count, s);
+    case 128: return expl ? launch_render_i<128, true>(cam, g, obs, b, w, max_items, inline_px, sm_count, s)
+                          : launch_render_i<128, false>(cam, g, obs, b, w, max_items, inline_px, sm_count, s);
+    case 512: return expl ? launch_render_i<512, true>(cam, g, obs, b, w, max_items, inline_px, sm_count, s)
+                          : launch_render_i<512, false>(cam, g, obs, b, w, max_items, inline_px, sm_count, s);
+    default: return expl ? launch_render_i<256, true>(cam, g, obs, b, w, max_items, inline_px, sm_count, s)
+                         : launch_render_i<256, false>(cam, g, obs, b, w, max_items, inline_px, sm_count, s);
   }
 }
 

@@ -25,9 +25,13 @@ namespace {
 
 using TuneKey = std::tuple<int, int, int, int, int, int>;  // device, tris, verts, tile_w, tile_h, shared renders
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;  // (render or evaluation width, cost width)
+struct TuneChoice {
+  int threads, inline_px, cost_threads;
+};
+std::map<TuneKey, TuneChoice> g_tune_cache;
 
 constexpr int kWidths[3] = {128, 256, 512};
+constexpr int kInline[3] = {8, 16, 32};  // k_render's inline limit (candidate pixel centres per lane)
 constexpr int kCostWidths[2] = {128, 256};
 
 }  // namespace
@@ -49,15 +53,18 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
   n_sample = std::max(n_sample, 32 * ctx->sm_count);
   const int n_mesh = ctx->n_mesh;
   const long long n_poses = (long long)ctx->nx * ctx->ny * ctx->n_yaw;
+  // children of two empty parents, alternating (a batch of two parents takes
+  // the shared-render path when it is on; every pose appears once)
   std::vector<perch_obj> hyps(n_sample);
   std::vector<int32_t> hp(n_sample, 0);
-  const int32_t plen = 0;
-  CK(ctx->b_parents.ensure(sizeof(perch_obj)), "alloc");
-  CK(ctx->b_plen.ensure(4), "alloc");
+  for (int i = 0; i < n_sample; ++i) hp[i] = i & 1;
+  const int32_t plen[2] = {0, 0};
+  CK(ctx->b_parents.ensure(2 * sizeof(perch_obj)), "alloc");
+  CK(ctx->b_plen.ensure(8), "alloc");
   CK(ctx->b_hp.ensure(4 * (size_t)n_sample), "alloc");
   CK(ctx->b_hyp.ensure(sizeof(perch_obj) * (size_t)n_sample), "alloc");
   CK(ctx->b_out.ensure(sizeof(perch_cost) * (size_t)n_sample), "alloc");
-  CK(cudaMemcpyAsync(ctx->b_plen.p, &plen, 4, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  CK(cudaMemcpyAsync(ctx->b_plen.p, plen, 8, cudaMemcpyHostToDevice, ctx->stream), "copy");
   CK(cudaMemcpyAsync(ctx->b_hp.p, hp.data(), 4 * (size_t)n_sample, cudaMemcpyHostToDevice, ctx->stream), "copy");
   const std::vector<int> saved = ctx->mesh_threads;
   // time the rasteriser itself: the exact shortcut would skip most root children
@@ -68,7 +75,12 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
   } shortcut_off{ctx, ctx->shortcut};
   ctx->shortcut = false;
   const bool shared = ctx->share_renders && ctx->store_ok;
-  const std::vector<int> saved_cost = ctx->mesh_cost_threads;
+  const std::vector<int> saved_cost = ctx->mesh_cost_threads, saved_inline = ctx->mesh_inline;
+  auto restore = [&]() {
+    ctx->mesh_threads = saved;
+    ctx->mesh_cost_threads = saved_cost;
+    ctx->mesh_inline = saved_inline;
+  };
   for (int m = 0; m < n_mesh; ++m) {
     const TuneKey key{ctx->device,          ctx->h_meshes[m].n_tris, ctx->h_meshes[m].n_verts,
                       ctx->mesh_tile_w[m], ctx->mesh_tile_h[m],     shared ? 1 : 0};
@@ -76,8 +88,9 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
       std::lock_guard<std::mutex> lock(g_tune_mu);
       auto it = g_tune_cache.find(key);
       if (it != g_tune_cache.end()) {
-        ctx->mesh_threads[m] = it->second.first;
-        ctx->mesh_cost_threads[m] = it->second.second;
+        ctx->mesh_threads[m] = it->second.threads;
+        ctx->mesh_inline[m] = it->second.inline_px;
+        ctx->mesh_cost_threads[m] = it->second.cost_threads;
         continue;
       }
     }
@@ -101,7 +114,7 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
     auto time_phase = [&](int a, float& out) -> int {
       float ms = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
-        int rc = ctx->enqueue_eval(ctx->b_parents.as<perch_obj>(), 1, ctx->b_plen.as<int32_t>(), 1,
+        int rc = ctx->enqueue_eval(ctx->b_parents.as<perch_obj>(), 1, ctx->b_plen.as<int32_t>(), 2,
                                    ctx->b_hp.as<int32_t>(), ctx->b_hyp.as<perch_obj>(), n_sample, 1,
                                    ctx->b_out.as<perch_cost>());
         if (rc != PERCH_OK) return rc;
@@ -113,23 +126,29 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
       out = ms;
       return PERCH_OK;
     };
-    int best = 256, best_cost = ctx->mesh_cost_threads[m];
+    // the render: CTA width x inline limit (the limit only applies to
+    // k_render; the per-hypothesis kernel keeps kInlinePixels)
+    int best = 256, best_inline = ctx->mesh_inline[m], best_cost = ctx->mesh_cost_threads[m];
     float best_ms = 1e30f;
-    for (int w : kWidths) {
-      ctx->mesh_threads[m] = w;
-      float ms = 0.0f;
-      const int rc = time_phase(2, ms);
-      if (rc != PERCH_OK) {
-        ctx->mesh_threads = saved;
-        ctx->mesh_cost_threads = saved_cost;
-        return rc;
+    for (int w : kWidths)
+      for (int il : kInline) {
+        if (!shared && il != kInlinePixels) continue;
+        ctx->mesh_threads[m] = w;
+        ctx->mesh_inline[m] = il;
+        float ms = 0.0f;
+        const int rc = time_phase(2, ms);
+        if (rc != PERCH_OK) {
+          restore();
+          return rc;
+        }
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = w;
+          best_inline = il;
+        }
       }
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = w;
-      }
-    }
     ctx->mesh_threads[m] = best;
+    ctx->mesh_inline[m] = best_inline;
     if (shared) {
       best_ms = 1e30f;
       for (int w : kCostWidths) {
@@ -137,8 +156,7 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
         float ms = 0.0f;
         const int rc = time_phase(3, ms);
         if (rc != PERCH_OK) {
-          ctx->mesh_threads = saved;
-          ctx->mesh_cost_threads = saved_cost;
+          restore();
           return rc;
         }
         if (ms < best_ms) {
@@ -149,7 +167,7 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
       ctx->mesh_cost_threads[m] = best_cost;
     }
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[key] = {best, best_cost};
+    g_tune_cache[key] = {best, best_inline, best_cost};
   }
   if (threads_out)
     for (int m = 0; m < n_mesh; ++m) threads_out[m] = ctx->mesh_threads[m];
@@ -208,15 +226,31 @@ extern "C" int perch_eval_graph(perch_ctx* ctx, const perch_obj* parents, int32_
   return PERCH_OK;
 }
 
-extern "C" int perch_launch_config(perch_ctx* ctx, int32_t* render_threads, int32_t* cost_threads) {
+extern "C" int perch_launch_config(perch_ctx* ctx, int32_t* render_threads, int32_t* inline_pixels,
+                                   int32_t* cost_threads) {
   if (!ctx) return PERCH_E_ARG;
   ctx->err.clear();
-  if ((int)ctx->mesh_threads.size() != ctx->n_mesh || (int)ctx->mesh_cost_threads.size() != ctx->n_mesh)
+  if ((int)ctx->mesh_threads.size() != ctx->n_mesh || (int)ctx->mesh_cost_threads.size() != ctx->n_mesh ||
+      (int)ctx->mesh_inline.size() != ctx->n_mesh)
     return ctx->fail(PERCH_E_STATE, "no meshes and camera yet");
   for (int m = 0; m < ctx->n_mesh; ++m) {
     if (render_threads) render_threads[m] = ctx->mesh_threads[m];
+    if (inline_pixels) inline_pixels[m] = ctx->mesh_inline[m];
     if (cost_threads) cost_threads[m] = ctx->mesh_cost_threads[m];
   }
+  return PERCH_OK;
+}
+
+extern "C" int perch_set_inline_pixels(perch_ctx* ctx, int32_t mesh, int32_t inline_pixels) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (inline_pixels != 8 && inline_pixels != 16 && inline_pixels != 32)
+    return ctx->fail(PERCH_E_ARG, "inline limit must be 8, 16 or 32");
+  if (mesh < -1 || mesh >= ctx->n_mesh) return ctx->fail(PERCH_E_ARG, "mesh %d out of range", mesh);
+  if ((int)ctx->mesh_inline.size() != ctx->n_mesh) ctx->mesh_inline.assign(ctx->n_mesh, kInlinePixels);
+  for (int m = 0; m < ctx->n_mesh; ++m)
+    if (mesh < 0 || m == mesh) ctx->mesh_inline[m] = inline_pixels;
+  ctx->tables_version++;  // a captured graph holds the old launch
   return PERCH_OK;
 }
 

@@ -33,7 +33,7 @@ EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_mesh
            "perch_cnn_set_tensor_path", "perch_cnn_tensor_status",
            "perch_set_shortcut", "perch_shortcut_stats", "perch_search_stats", "perch_search_times",
            "perch_set_wait_limit", "perch_set_share_renders", "perch_last_phase_times", "perch_set_volumes",
-           "perch_launch_config", "perch_set_symmetry")
+           "perch_launch_config", "perch_set_symmetry", "perch_set_inline_pixels")
 
 
 class perch_mesh(ctypes.Structure):
@@ -117,7 +117,8 @@ def load(path: str = LIB_PATH):
         "perch_set_shortcut": ([P, I32], ctypes.c_int),
         "perch_set_wait_limit": ([P, I32], ctypes.c_int),
         "perch_set_volumes": ([P, P, I32], ctypes.c_int),
-        "perch_launch_config": ([P, P, P], ctypes.c_int),
+        "perch_launch_config": ([P, P, P, P], ctypes.c_int),
+        "perch_set_inline_pixels": ([P, I32, I32], ctypes.c_int),
         "perch_set_symmetry": ([P, P, I32], ctypes.c_int),
         "perch_set_share_renders": ([P, I32], ctypes.c_int),
         "perch_last_phase_times": ([P, P, P], ctypes.c_int),
@@ -335,11 +336,16 @@ class Perch:
         return self._check(self.lib.perch_set_symmetry(self.h, sym.ctypes.data, len(sym)))
 
     def perch_launch_config(self):
-        """(render CTA width per mesh, cost CTA width per mesh) now in use."""
+        """(render CTA width, render inline limit, cost CTA width) per mesh, now in use."""
         r = np.zeros(self.n_mesh, np.int32)
+        i = np.zeros(self.n_mesh, np.int32)
         c = np.zeros(self.n_mesh, np.int32)
-        self._check(self.lib.perch_launch_config(self.h, r.ctypes.data, c.ctypes.data))
-        return r.tolist(), c.tolist()
+        self._check(self.lib.perch_launch_config(self.h, r.ctypes.data, i.ctypes.data, c.ctypes.data))
+        return r.tolist(), i.tolist(), c.tolist()
+
+    def perch_set_inline_pixels(self, inline_pixels: int, mesh: int = -1):
+        """The render's inline limit (8, 16 or 32) for one mesh or all."""
+        return self._check(self.lib.perch_set_inline_pixels(self.h, mesh, int(inline_pixels)))
 
     def perch_set_volumes(self, meshes):
         """V(O) per mesh from each synth.Mesh's closed-form `volume` (None:

@@ -416,6 +416,46 @@ def test_search_matches_oracle_ucs_full_c1(c1):
     assert r["proven_optimal"] and (r["cost"], r["key"]) == (cost, key)
 
 
+def test_render_launch_parameters_do_not_change_records():
+    """The render's CTA width and inline limit (which triangles a lane
+    rasterises itself and which a warp takes from the queue) change only who
+    writes a pixel's depth, never the depth: the same records for every
+    setting the autotuner can pick, on the uneven meshes of the heavy-occlusion
+    workload (2k-50k triangles), checked against the oracle on a sample."""
+    wl = synth.workload_c3()
+    p = perch.Perch(0)
+    p.setup(wl)
+    w = oracle.World.of(wl)
+    rng = np.random.default_rng(31)
+    parents = [wl.gt[:0], wl.gt[:2]]
+    hyps, hp = [], []
+    for i, par in enumerate(parents):
+        rem = list(wl.mesh_multiset)
+        for m in par["mesh"]:
+            rem.remove(int(m))
+        allh = synth.all_hypotheses(wl.grid, sorted(set(rem)))
+        pick = allh[rng.choice(len(allh), 1500, replace=False)]
+        near = _near(wl.grid, wl.gt, set(rem))
+        hyps += [pick, near]
+        hp += [np.full(len(pick) + len(near), i, np.int32)]
+    hyps, hp = np.concatenate(hyps), np.concatenate(hp)
+    ref = None
+    try:
+        p.perch_set_shortcut(False)
+        for threads, inl in ((256, 16), (128, 8), (512, 32), (256, 32), (128, 16)):
+            p.perch_set_threads(threads)
+            p.perch_set_inline_pixels(inl)
+            assert p.perch_launch_config()[:2] == ([threads] * len(wl.meshes), [inl] * len(wl.meshes))
+            got = _recs(p.perch_eval_successors(parents, hp, hyps, wl.K))
+            if ref is None:
+                ref = got
+            assert np.array_equal(got, ref), (threads, inl)
+    finally:
+        p.close()
+    pick = rng.choice(len(hyps), 60, replace=False)
+    assert np.array_equal(ref[pick], oracle.eval_batch(w, wl.depth, parents, hp[pick], hyps[pick], wl.K))
+
+
 def test_symmetric_search_matches_oracle_c1(c1):
     """With the meshes' rotational symmetry declared, the GPU search places a
     symmetric mesh only at the yaws no smaller yaw equals modulo its symmetry
