@@ -372,6 +372,30 @@ __device__ __forceinline__ int cell_of(float x, float g, float inv, int n) {
   return c;
 }
 
+__device__ __forceinline__ int sat_sum(const int* S, int cols, int r0, int r1, int c0, int c1) {  // inclusive
+  const int w = cols + 1;
+  return S[(r1 + 1) * w + c1 + 1] - S[r0 * w + c1 + 1] - S[(r1 + 1) * w + c0] + S[r0 * w + c0];
+}
+
+// Could some observed point lie within delta of a point that object o
+// renders? No, when the world (x, y) cells around its footprint disk (radius
+// fp_r, plus delta, plus 2 cm for the rounding of the back-projected depth,
+// plus a cell either side) hold no point: every rendered point lies within
+// that disk horizontally, and Eq. (1) bounds the 3D distance, hence the
+// horizontal one (the grid covers the whole cloud, so a disk beyond its
+// cells holds none).
+__device__ __forceinline__ bool obs_near(const Camera& cam, const Geometry& g, const ObsIndex& obs,
+                                         const perch_obj& o) {
+  if (obs.n == 0) return false;
+  const float R = g.meshes[o.mesh].fp_r + cam.delta + 0.02f;
+  const float ox = g.xs[o.ix], oy = g.ys[o.iy];
+  const int cx0 = max(cell_of(ox - R, obs.g2x, obs.inv2, obs.n2x) - 1, 0);
+  const int cx1 = min(cell_of(ox + R, obs.g2x, obs.inv2, obs.n2x) + 1, obs.n2x - 1);
+  const int cy0 = max(cell_of(oy - R, obs.g2y, obs.inv2, obs.n2y) - 1, 0);
+  const int cy1 = min(cell_of(oy + R, obs.g2y, obs.inv2, obs.n2y) + 1, obs.n2y - 1);
+  return cx0 <= cx1 && cy0 <= cy1 && sat_sum(obs.sat2, obs.n2x, cy0, cy1, cx0, cx1) != 0;
+}
+
 __global__ void k_grid3_keys(const float4* pts, int n, float gx, float gy, float gz, float inv, int nx, int ny,
                              int nz, int* keys, int* counts) {
   const int k = blockIdx.x * 256 + threadIdx.x;
@@ -1020,41 +1044,46 @@ constexpr uint32_t kExplainedBit = 0x80000000u;  // z > 0: the sign bit is free
 template <int NT, int SRC>
 __device__ __forceinline__ void compare_phase(int pid, int plen, int4 bb, const Camera& cam, const Batch& b,
                                               const uint32_t* src, uint32_t* tile, int* s_cnt) {
-  constexpr int NW = NT / 32;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tw = bb.z, th = bb.w;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int tw = bb.z, n = bb.z * bb.w;
   int viol = 0, nnew = 0, djr = 0;
   const float* zp = plen > 0 ? b.parent_z + (size_t)pid * cam.W * cam.H : nullptr;
-  for (int ly = warp; ly < th; ly += NW) {
-    const float* prow = zp ? zp + (size_t)(bb.y + ly) * cam.W + bb.x : nullptr;
-    for (int lx = lane; lx < tw; lx += 32) {
-      const uint32_t sv = src[ly * tw + lx];
-      uint32_t zb;
-      if (SRC == kSrcInvZ) {
-        if (sv == 0u) {
-          tile[ly * tw + lx] = kInfBits;
-          continue;
-        }
-        zb = __float_as_uint(__frcp_rn(__uint_as_float(sv)));
-      } else {
-        if (sv == kInfBits) {
-          tile[ly * tw + lx] = kInfBits;
-          continue;
-        }
-        zb = sv & ~kExplainedBit;
+  const uint32_t empty = SRC == kSrcInvZ ? 0u : kInfBits;
+  // pixel i of the box is (i mod tw, i div tw); i div tw = umulhi(i, ceil(2^32 / tw)),
+  // exact for i tw < 2^32 (the box is at most kMaxObjectPixels wide and high)
+  const uint32_t mg = tw > 1 ? 0xffffffffu / (uint32_t)tw + 1u : 0u;
+  // U pixels per thread at a time: their parent depths are loaded together
+  constexpr int U = 4;
+  for (int i0 = tid; i0 < n; i0 += NT * U) {
+    uint32_t sv[U];
+    float pz[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * NT;
+      sv[u] = i < n ? src[i] : empty;
+      pz[u] = __uint_as_float(kInfBits);
+      if (zp && sv[u] != empty) {
+        const int ly = tw > 1 ? (int)__umulhi((uint32_t)i, mg) : i;
+        pz[u] = __ldg(&zp[(size_t)(bb.y + ly) * cam.W + bb.x + (i - ly * tw)]);
       }
-      const float z = __uint_as_float(zb);
-      if (prow) {
-        const float pz = __ldg(&prow[lx]);
-        if (__float_as_uint(pz) != kInfBits) {
-          if (z < pz) viol++;
-          tile[ly * tw + lx] = kInfBits;  // hidden by (or hiding) the parent: not in dR
-          continue;
-        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * NT;
+      if (i >= n) break;
+      if (sv[u] == empty) {
+        tile[i] = kInfBits;
+        continue;
       }
-      tile[ly * tw + lx] = zb;
+      const uint32_t zb = SRC == kSrcInvZ ? __float_as_uint(__frcp_rn(__uint_as_float(sv[u]))) : (sv[u] & ~kExplainedBit);
+      if (__float_as_uint(pz[u]) != kInfBits) {  // hidden by (or hiding) the parent: not in dR
+        if (__uint_as_float(zb) < pz[u]) viol++;
+        tile[i] = kInfBits;
+        continue;
+      }
+      tile[i] = zb;
       nnew++;
-      if (SRC == kSrcZExplained && !(sv & kExplainedBit)) djr++;
+      if (SRC == kSrcZExplained && !(sv[u] & kExplainedBit)) djr++;
     }
   }
   viol = warp_sum(viol);
@@ -1344,7 +1373,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_render(Camera cam, Geometry g
     const int any_culled = __syncthreads_or(culled != 0);
     // the store gets z = 1/(1/z) (+inf where empty) and, for a single-scene
     // batch (EXPL), the Eq. (1) test of each rendered point against I in the
-    // sign bit: it depends on the pose and the scene, not on the parent
+    // sign bit: it depends on the pose and the scene, not on the parent. A
+    // pose with no observed point near its footprint explains no point.
+    const bool probe = EXPL && obs_near(cam, g, obs, o);
     uint32_t* dst = w.store + 4 * (size_t)w.tile_off[p];
     for (int ly = warp; ly < th; ly += NW) {
       const float ry = EXPL ? g.ry[bb.y + ly] : 0.0f;
@@ -1354,7 +1385,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_render(Camera cam, Geometry g
         if (izb != 0u) {
           const float z = __frcp_rn(__uint_as_float(izb));
           v = __float_as_uint(z);
-          if (EXPL && explained_by_obs(obs, fmul(g.rx[bb.x + lx], z), fmul(ry, z), z, cam.delta2))
+          if (probe && explained_by_obs(obs, fmul(g.rx[bb.x + lx], z), fmul(ry, z), z, cam.delta2))
             v |= kExplainedBit;
         }
         dst[ly * tw + lx] = v;
@@ -1367,18 +1398,30 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_render(Camera cam, Geometry g
 
 // k_cost: one persistent CTA per SM slot costs hypotheses, sorted by pose,
 // from the tile store. A hypothesis's tile is brought into a shared stage
-// buffer by a 1D bulk copy (TMA), which threads only read; the copy of the
-// next hypothesis's tile is started as soon as the current one's compare
-// pass has read the stage, so it lands while dJ_r, dJ_o and the residual
-// run. The compare pass writes z (or +inf) into a separate shared tile, which
-// the delta windows of dJ_o and the residual scan.
+// buffer by a 1D bulk copy (TMA), which threads only read. Thread 0 claims
+// the next hypothesis, looks up its arguments and box and starts the copy of
+// its tile as soon as the current one's compare pass has read the stage,
+// while the rest of the CTA runs dJ_r, dJ_o and the residual; the next
+// hypothesis reads what it found from shared memory. Hypotheses of the pose
+// whose tile the stage already holds (the batch is sorted by pose) take it
+// as it is, with no copy. The compare pass writes z (or +inf) into a
+// separate shared tile, which the delta windows of dJ_o and the residual
+// scan.
 template <int NT, bool MULTI>
 __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex obs0, Batch b, CostWork w) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(16) ObsIndex s_obs;
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_cnt[7];
-  __shared__ int s_item;
+  // the claimed item: its index, hypothesis, arguments, box, pose flags and
+  // how its tile reaches the stage (thread 0 writes it, everyone reads it)
+  enum { kItemBad = 0, kItemFailed = 1, kItemCopy = 2, kItemReuse = 3 };
+  __shared__ struct {
+    int item, state, pf;
+    long long h;
+    HypArgs a;
+    int4 bb;
+  } s_nx;
   const int tid = threadIdx.x;
   uint32_t* stage = reinterpret_cast<uint32_t*>(smem);  // bulk-copy destination
   uint32_t* tile = stage + ((b.tile_w * b.tile_h + 3) & ~3);
@@ -1390,69 +1433,90 @@ __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex ob
   }
   __syncthreads();
   const int count = *w.count, offset = *w.offset;
-  // Is there a stored tile to cost item `it` from? (the same answer in every thread)
-  auto has_tile = [&](int it, HypArgs& a, int4& bb) {
-    if (it >= count || !hyp_args(g, b, w.order[offset + it], a)) return false;
-    bb = g.pose_bbox[a.pose];
-    return bb.z <= b.tile_w && bb.w <= b.tile_h && !(w.pose_flags[a.pose] & kPoseFailed);
-  };
-  // claim the next item and start the copy of its tile (thread 0); a CTA barrier
+  long long stage_pose = -1;  // thread 0: the pose whose tile the stage holds or is receiving
+  // thread 0: claim the next item, look it up and start the copy of its tile
+  // unless the stage holds it; no barrier (the caller's next one publishes it)
   auto claim = [&]() {
-    if (tid == 0) {
-      const int it = atomicAdd(w.next, 1);
-      s_item = it;
-      HypArgs a;
-      int4 bb;
-      if (has_tile(it, a, bb))
-        bulk_load(stage, w.store + 4 * (size_t)w.tile_off[a.pose], 16u * (uint32_t)((bb.z * bb.w + 3) >> 2),
-                  &s_bar);
-    }
-    __syncthreads();
-    return s_item;
-  };
-  uint32_t parity = 0;
-  int item = claim();
-  while (item < count) {
-    const long long h = w.order[offset + item];
+    const int it = atomicAdd(w.next, 1);
+    s_nx.item = it;
+    if (it >= count) return;
+    const long long h = w.order[offset + it];
     HypArgs a;
+    int state = kItemBad, pf = 0;
     int4 bb = make_int4(0, 0, 0, 0);
-    if (!has_tile(item, a, bb)) {  // no copy was started for it
-      if (tid == 0) {
-        const bool failed = hyp_args(g, b, h, a) && (w.pose_flags[a.pose] & kPoseFailed);
-        perch_cost r = {0, 0, 0, 0, 0, failed ? kFlagTimeout : kFlagBadIndex, 0};
-        b.out[h] = r;
+    if (hyp_args(g, b, h, a)) {
+      bb = g.pose_bbox[a.pose];
+      pf = w.pose_flags[a.pose];
+      if (pf & kPoseFailed) {
+        state = kItemFailed;
+      } else if (bb.z <= b.tile_w && bb.w <= b.tile_h) {
+        state = a.pose == stage_pose ? kItemReuse : kItemCopy;
+        if (state == kItemCopy) {
+          bulk_load(stage, w.store + 4 * (size_t)w.tile_off[a.pose], 16u * (uint32_t)((bb.z * bb.w + 3) >> 2),
+                    &s_bar);
+          stage_pose = a.pose;
+        }
       }
-      item = claim();
+    }
+    s_nx.h = h;
+    s_nx.state = state;
+    s_nx.pf = pf;
+    s_nx.a = a;
+    s_nx.bb = bb;
+  };
+  if (tid == 0) claim();
+  __syncthreads();
+  uint32_t parity = 0;
+  for (;;) {
+    const int item = s_nx.item;
+    if (item >= count) break;
+    const long long h = s_nx.h;
+    const int state = s_nx.state, pf = s_nx.pf;
+    const HypArgs a = s_nx.a;
+    const int4 bb = s_nx.bb;
+    if (state == kItemBad || state == kItemFailed) {  // no copy was started for it
+      __syncthreads();  // every thread has read s_nx
+      if (tid == 0) {
+        perch_cost r = {0, 0, 0, 0, 0, state == kItemFailed ? kFlagTimeout : kFlagBadIndex, 0};
+        b.out[h] = r;
+        claim();
+      }
+      __syncthreads();
       continue;
     }
-    const uint8_t pf = w.pose_flags[a.pose];
     if (MULTI && tid < (int)(sizeof(ObsIndex) / 4))
       reinterpret_cast<int*>(&s_obs)[tid] = reinterpret_cast<const int*>(&b.scenes[a.scene])[tid];
     const ObsIndex& obs = MULTI ? s_obs : obs0;
     for (int i = tid; i < bb.z; i += NT) rxs[i] = g.rx[bb.x + i];
     for (int i = tid; i < bb.w; i += NT) rys[i] = g.ry[bb.y + i];
-    if (tid < 7) s_cnt[tid] = tid == 2 ? (int)(pf & kPoseCulled) : 0;
-    // wait for the stage (bounded); on give-up drain the copy with the full
-    // bound, report the hypothesis and go on, or stop if it is still in flight
-    if (!__syncthreads_and(mbar_wait(&s_bar, parity, b.wait_polls))) {
-      const bool drained = __syncthreads_and(mbar_wait(&s_bar, parity));
-      if (tid == 0) {
-        perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout, 0};
-        b.out[h] = r;
+    if (tid < 7) s_cnt[tid] = tid == 2 ? (pf & kPoseCulled) : 0;
+    if (state == kItemCopy) {
+      // wait for the stage (bounded); on give-up drain the copy with the
+      // full bound, report the hypothesis and go on, or stop if it is still
+      // in flight
+      if (!__syncthreads_and(mbar_wait(&s_bar, parity, b.wait_polls))) {
+        const bool drained = __syncthreads_and(mbar_wait(&s_bar, parity));
+        if (tid == 0) {
+          perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout, 0};
+          b.out[h] = r;
+          stage_pose = -1;
+          if (drained) claim();
+        }
+        if (!drained) break;
+        parity ^= 1u;
+        __syncthreads();
+        continue;
       }
-      if (!drained) break;
       parity ^= 1u;
-      item = claim();
-      continue;
+    } else {
+      __syncthreads();  // the stage holds this pose's tile already; rays and counters are written
     }
-    parity ^= 1u;
     // a single-scene store holds z with the explained flag (k_render); a
     // multi-scene one plain z, and dJ_r is counted here against the scene
     compare_phase<NT, MULTI ? kSrcZ : kSrcZExplained>(a.pid, a.plen, bb, cam, b, stage, tile, s_cnt);
-    const int next = claim();  // the stage is free: start the next copy
+    if (tid == 0) claim();  // the stage is read: start the next copy while the rest runs
     const DevMesh m = g.meshes[a.o.mesh];
     finish_phase<NT, !MULTI>(h, a.pid, a.plen, a.K_total, a.o, bb, m, cam, g, obs, b, tile, rxs, rys, s_cnt);
-    item = next;
   }
 }
 
@@ -1603,11 +1667,6 @@ __global__ void k_sat(const int* counts, int rows, int cols, int* sat) {
     for (int r = 1; r < rows; ++r) S[(size_t)(r + 1) * (cols + 1) + c + 1] += S[(size_t)r * (cols + 1) + c + 1];
 }
 
-__device__ __forceinline__ int sat_sum(const int* S, int cols, int r0, int r1, int c0, int c1) {  // inclusive
-  const int w = cols + 1;
-  return S[(r1 + 1) * w + c1 + 1] - S[r0 * w + c1 + 1] - S[(r1 + 1) * w + c0] + S[r0 * w + c0];
-}
-
 __global__ void k_cell_counts(const int* start2, int n, int* counts) {
   const int c = blockIdx.x * 256 + threadIdx.x;
   if (c < n) counts[c] = start2[c + 1] - start2[c];
@@ -1663,18 +1722,7 @@ __global__ void k_shortcut(Camera cam, Geometry g, ObsIndex obs0, Batch b) {
         ok = sat_sum(S, b.tiles_w, ty0, ty1, tx0, tx1) == 0;
       }
     }
-    if (ok) {  // no observed point near (x, y)?
-      const ObsIndex& obs = b.parent_scene ? b.scenes[scene] : obs0;
-      if (obs.n > 0) {
-        const float R = g.meshes[o.mesh].fp_r + cam.delta + 0.02f;
-        const float ox = g.xs[o.ix], oy = g.ys[o.iy];
-        const int cx0 = max(cell_of(ox - R, obs.g2x, obs.inv2, obs.n2x) - 1, 0);
-        const int cx1 = min(cell_of(ox + R, obs.g2x, obs.inv2, obs.n2x) + 1, obs.n2x - 1);
-        const int cy0 = max(cell_of(oy - R, obs.g2y, obs.inv2, obs.n2y) - 1, 0);
-        const int cy1 = min(cell_of(oy + R, obs.g2y, obs.inv2, obs.n2y) + 1, obs.n2y - 1);
-        if (cx0 <= cx1 && cy0 <= cy1) ok = sat_sum(obs.sat2, obs.n2x, cy0, cy1, cx0, cx1) == 0;
-      }
-    }
+    if (ok) ok = !obs_near(cam, g, b.parent_scene ? b.scenes[scene] : obs0, o);  // no observed point near (x, y)
     if (ok) {
       const int K_total = b.parent_K ? b.parent_K[pid] : b.K_total;
       const int2 so = b.solo[pose];
