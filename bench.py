@@ -452,6 +452,14 @@ def run_ours(args):
         search["symmetric"] = one_search()
         search["symmetric"]["symmetry_orders"] = [int(m.sym) for m in wl.meshes]
         p.perch_set_symmetry(None)
+        # the same search keeping each pose's render across expansions (the
+        # render cache: identical records, only poses not seen before rendered)
+        p.perch_set_render_cache(True)
+        search["render_cache"] = one_search()
+        p.perch_set_symmetry(wl.meshes)
+        search["render_cache_symmetric"] = one_search()
+        p.perch_set_symmetry(None)
+        p.perch_set_render_cache(False)
 
     base = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -563,6 +571,8 @@ def run_c5(args):
     p.perch_autotune(args.tune_sample)
     if args.symmetric:
         p.perch_set_symmetry(wls[0].meshes)
+    if args.render_cache:
+        p.perch_set_render_cache(True)
     with ClockSampler(0) as clocks, MemoryGuard() as mem:
         t0 = time.perf_counter()
         res = p.perch_search_multi(list(range(len(wls))), [wl.mesh_multiset for wl in wls],
@@ -580,6 +590,7 @@ def run_c5(args):
                        "scenes": len(wls), "launch_hyps": args.launch_hyps, "batch_states": args.batch_states,
                        "time_limit_s": args.search_limit, "generation_s": gen_s},
             "search": {"w": args.w, "heuristics": args.heuristics, "symmetric": bool(args.symmetric),
+                       "render_cache": bool(args.render_cache),
                        "meaning": ("cost <= w x optimum (Focal-MHA*, Theorem 2)" if args.w > 1 else "optimal") +
                                   (" of the tree with each mesh's symmetric yaws merged" if args.symmetric else "")},
             "scenes_finished": len(done),
@@ -757,6 +768,8 @@ def run_c4(args):
     p.perch_autotune(args.tune_sample)
     if args.symmetric:
         p.perch_set_symmetry(train_sc[0].meshes)
+    if args.render_cache:
+        p.perch_set_render_cache(True)
     stream = torch.cuda.Stream()
     n_onehot = len(train_sc[0].meshes) * grid.n_yaw
     data, dstats = H.make_dataset(p, train_sc, tr, per_parent=args.per_parent, seed=1)
@@ -845,7 +858,7 @@ def run_c4(args):
                                    f"on {dstats['pairs']} exact (crop, edge cost) pairs of {len(train_sc)} seeded "
                                    "2-5-object scenes",
                        "train_scenes": len(train_sc), "pairs": dstats["pairs"], "epochs": args.epochs, "batch": 256,
-                       "symmetric": bool(args.symmetric),
+                       "symmetric": bool(args.symmetric), "render_cache": bool(args.render_cache),
                        "candidates": args.candidates, "time_limit_s": args.search_limit, "generation_s": gen_s,
                        "dataset_s": dstats["seconds"]},
             "training": {"seconds": train_s, "steps": steps, "crops_per_s": steps * 256 / train_s,
@@ -898,6 +911,8 @@ def main():
                                                "mha_learned_untrained, mha_learned_dive, mha_learned_dive_untrained, "
                                                "mha, mha_depth+learned, mha_depth+learned_untrained, mha+learned "
                                                "(default: all)")
+    ap.add_argument("--render-cache", action="store_true",
+                    help="c4/c5: keep each pose's render across expansions (records unchanged)")
     ap.add_argument("--symmetric", action="store_true",
                     help="c4/c5: searches place each mesh only at yaws distinct modulo its rotational symmetry")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "cnn"],

@@ -394,6 +394,19 @@ int perch_set_shortcut(perch_ctx* ctx, int32_t on);
  * the free device memory. */
 int perch_set_share_renders(perch_ctx* ctx, int32_t on);
 
+/* Render cache (not in the paper; off by default). With on != 0 and shared
+ * renders in use, a pose's tile in the tile store stays valid after the
+ * batch that rendered it: later evaluations on this context cost their
+ * hypotheses of that pose from it and render only the poses they have not
+ * seen (any number of parents then takes the shared path). An object's
+ * render depends on its mesh and pose alone (and, for a single-scene batch,
+ * the explained flag of each rendered point on the observation), so records
+ * are identical with the cache on or off. Every change of the observation,
+ * of the scenes or of the pose tables empties the cache, and so does this
+ * call. perch_autotune turns it off while it times launches; a captured
+ * evaluation (perch_eval_graph) never uses it. */
+int perch_set_render_cache(perch_ctx* ctx, int32_t on);
+
 /* Device time of the four phases of the most recent evaluation (CUDA
  * events on the context's stream): ms[0] parent z-buffers, residual sets and
  * the exact shortcut; ms[1] grouping the hypotheses; ms[2] the render

@@ -180,6 +180,9 @@ int perch_ctx::ensure_tile_store() {
   CK(tile_off.ensure(4 * ((size_t)P + 1)), "alloc tile offsets");
   CK(pg_tmp.ensure(4 * ((size_t)P / 1024 + 2)), "alloc");
   CK(pose_flags.ensure((size_t)P), "alloc pose flags");
+  CK(pose_valid.ensure(4 * (size_t)P), "alloc render cache tags");
+  CK(cudaMemsetAsync(pose_valid.p, 0, 4 * (size_t)P, stream), "memset");  // no tag is 0
+  ++render_epoch;
   CK(launch_tile_offsets(geometry(), tile_sizes.as<int>(), tile_off.as<int>(), pg_tmp.as<int>(), stream),
      "tile offsets");
   int total = 0;
@@ -210,6 +213,7 @@ int perch_ctx::build_scene(int s, const float* depth_host) {
   const float delta = c.delta;
   if ((int)scenes.size() <= s) scenes.resize(s + 1);
   SceneBufs& sc = scenes[s];
+  ++render_epoch;  // stored renders with the explained bit belong to the old cloud
   const int npx = W * H;
   const int nblk = (npx + 255) / 256;
   CK(ctx->depth.ensure(4 * (size_t)npx), "alloc depth");
@@ -815,7 +819,8 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
   if (!capturing) CK(cudaEventRecord(ev[1], stream), "event");
   // a batch of one parent repeats no pose: rendering per hypothesis skips the
   // tile store's round trip
-  if (share_renders && store_ok && n_par >= 2) {
+  const bool cache = render_cache && !capturing;  // a captured graph would keep one epoch's tag
+  if (share_renders && store_ok && (n_par >= 2 || cache)) {
     // shared renders: group by pose; per mesh one persistent launch renders
     // its distinct poses into the tile store, then one costs its hypotheses
     const int per_mesh = nx * ny * n_yaw, P = per_mesh * n_mesh;
@@ -830,7 +835,9 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
     CK(g_next.ensure(sizeof(int) * 2 * (size_t)n_mesh), "alloc");
     PoseGroups pg{pg_cnt.as<int>(),   pg_start.as<int>(), pg_flag.as<int>(),   pg_gix.as<int>(),
                   pg_gpose.as<int>(), pg_tmp.as<int>(),   pg_ranges.as<int>(), g_order.as<int>()};
-    CK(launch_group_by_pose(g, b, pg, stream), "group by pose");
+    const uint32_t tag = 2u * render_epoch + (b.parent_scene ? 0u : 1u);
+    uint32_t* valid = cache ? pose_valid.as<uint32_t>() : nullptr;
+    CK(launch_group_by_pose(g, b, pg, valid, tag, stream), "group by pose");
     CK(cudaMemsetAsync(g_next.p, 0, sizeof(int) * 2 * (size_t)n_mesh, stream), "memset");
     if (!capturing) CK(cudaEventRecord(ev[2], stream), "event");
     int* rg = pg.ranges;
@@ -839,7 +846,7 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
       bm.tile_w = mesh_tile_w[m];
       bm.tile_h = mesh_tile_h[m];
       const RenderWork w{pg.gpose, rg + 4 * m + 2, rg + 4 * m + 3, g_next.as<int>() + m, tile_store.as<uint32_t>(),
-                         tile_off.as<int>(), pose_flags.as<uint8_t>()};
+                         tile_off.as<int>(), pose_flags.as<uint8_t>(), valid, tag};
       CK(launch_render_group(cam, g, obs, bm, w, std::min<long long>(n_hyp, per_mesh), mesh_threads[m],
                              mesh_inline[m], sm_count, stream),
          "render kernel");
@@ -987,6 +994,15 @@ int perch_last_phase_times(perch_ctx* ctx, float* ms, int32_t* shared) {
   for (int k = 0; k < 4; ++k)
     if (ms) CK(cudaEventElapsedTime(&ms[k], ctx->ev[k], ctx->ev[k + 1]), "event time");
   if (shared) *shared = ctx->last_path == 2 ? 1 : 0;
+  return PERCH_OK;
+}
+
+int perch_set_render_cache(perch_ctx* ctx, int32_t on) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  ctx->render_cache = on != 0;
+  ++ctx->render_epoch;    // what the store held before is not trusted
+  ctx->tables_version++;  // a captured graph holds the old path
   return PERCH_OK;
 }
 

@@ -103,6 +103,15 @@ struct perch_ctx {
   std::vector<int> mesh_cost_threads;  // CTA width of k_cost per mesh (autotuned; 128 by default)
   std::vector<int> mesh_inline;        // k_render's inline limit per mesh (autotuned; 16 by default)
   int last_path = 0;       // last evaluation: 1 = one render per hypothesis, 2 = shared renders
+  // render cache (perch_set_render_cache, off by default): a pose's tile in
+  // the store stays valid, with its pose flags, until the observation, the
+  // scenes or the pose tables change. pose_valid[p] holds the tag it was
+  // rendered under (2 render_epoch + 1 for the single-scene form with the
+  // explained bit, 2 render_epoch for plain z); the grouping leaves such
+  // poses out of a batch's render list
+  bool render_cache = false;
+  uint32_t render_epoch = 1;
+  DevBuf pose_valid;
   DevBuf b_parents, b_plen, b_hp, b_hyp, b_out;
 
   // captured evaluation graph (perch_eval_graph); `version` changes whenever
@@ -150,7 +159,7 @@ struct perch_ctx {
             &b_out, &g_hist, &g_off, &g_cursor, &g_order, &g_next, &net_crops, &net_onehot, &net_pred,
             &solo, &solo_rec, &solo_hyp, &solo_hp, &solo_parent, &ptile_counts, &ptile_sat, &skip, &n_short,
             &tile_store, &tile_off, &tile_sizes, &pose_flags, &pg_cnt, &pg_start, &pg_flag, &pg_gix, &pg_gpose,
-            &pg_tmp, &pg_ranges};
+            &pg_tmp, &pg_ranges, &pose_valid};
   }
 
   int fail(int code, const char* fmt, ...);

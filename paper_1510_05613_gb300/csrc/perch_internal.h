@@ -140,6 +140,8 @@ struct RenderWork {
                         // single-scene batch the sign bit says the point is explained by I (Eq. (1))
   const int* tile_off;  // per pose: offset of its tile in the store, in 16-byte units
   uint8_t* pose_flags;  // per pose: kPoseCulled, kPoseFailed
+  uint32_t* valid;      // render cache (or nullptr): per pose, the tag of its stored render
+  uint32_t tag;         // this batch's tag, written for every pose rendered in full
 };
 
 // k_cost's work: hypotheses sorted by pose, one mesh's range per launch
@@ -209,7 +211,8 @@ cudaError_t launch_tile_offsets(const Geometry& g, int* sizes, int* tile_off, in
 // hypotheses of the batch grouped by pose; writes the bad-index record of a
 // hypothesis with an out-of-range parent or pose (it joins no group) and
 // leaves out those the shortcut answered (b.skip)
-cudaError_t launch_group_by_pose(const Geometry& g, const Batch& b, const PoseGroups& pg, cudaStream_t s);
+cudaError_t launch_group_by_pose(const Geometry& g, const Batch& b, const PoseGroups& pg, const uint32_t* valid,
+                                 uint32_t tag, cudaStream_t s);
 cudaError_t launch_render_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
                                 const RenderWork& w, long long max_items, int threads, int inline_px,
                                 int sm_count, cudaStream_t s);

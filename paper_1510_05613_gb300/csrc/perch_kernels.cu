@@ -1391,7 +1391,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_render(Camera cam, Geometry g
         dst[ly * tw + lx] = v;
       }
     }
-    if (tid == 0) w.pose_flags[p] = any_culled ? kPoseCulled : 0;
+    if (tid == 0) {
+      w.pose_flags[p] = any_culled ? kPoseCulled : 0;
+      if (w.valid) w.valid[p] = w.tag;  // read by later launches only
+    }
     __syncthreads();  // the tile is cleared by the next pose
   }
 }
@@ -1575,14 +1578,16 @@ __global__ void k_pose_count(Geometry g, Batch b, int* cnt) {
   atomicAdd(&cnt[a.pose], 1);
 }
 
-__global__ void k_pose_nonzero(const int* cnt, int P, int* flag) {
+// a pose is rendered when some hypothesis has it and (with the render
+// cache) the store does not hold its render under this batch's tag already
+__global__ void k_pose_nonzero(const int* cnt, int P, const uint32_t* valid, uint32_t tag, int* flag) {
   const int p = blockIdx.x * 256 + threadIdx.x;
-  if (p < P) flag[p] = cnt[p] > 0 ? 1 : 0;
+  if (p < P) flag[p] = cnt[p] > 0 && !(valid && valid[p] == tag) ? 1 : 0;
 }
 
-__global__ void k_pose_list(const int* cnt, const int* gix, int P, int* gpose) {
+__global__ void k_pose_list(const int* flag, const int* gix, int P, int* gpose) {
   const int p = blockIdx.x * 256 + threadIdx.x;
-  if (p < P && cnt[p] > 0) gpose[gix[p]] = p;
+  if (p < P && flag[p]) gpose[gix[p]] = p;
 }
 
 // mesh m owns poses [m * per_mesh, (m + 1) * per_mesh): its hypotheses are
@@ -1605,7 +1610,8 @@ __global__ void k_pose_place(Geometry g, Batch b, const int* start, int* cnt, in
   order[start[a.pose] + atomicSub(&cnt[a.pose], 1) - 1] = (int)h;
 }
 
-cudaError_t launch_group_by_pose(const Geometry& g, const Batch& b, const PoseGroups& pg, cudaStream_t s) {
+cudaError_t launch_group_by_pose(const Geometry& g, const Batch& b, const PoseGroups& pg, const uint32_t* valid,
+                                 uint32_t tag, cudaStream_t s) {
   const int per_mesh = g.nx * g.ny * g.n_yaw, P = g.n_mesh * per_mesh;
   const unsigned pb = (unsigned)((P + 255) / 256), hb = (unsigned)((b.n_hyp + 255) / 256);
   cudaError_t e = cudaMemsetAsync(pg.cnt, 0, sizeof(int) * (size_t)P, s);
@@ -1613,9 +1619,9 @@ cudaError_t launch_group_by_pose(const Geometry& g, const Batch& b, const PoseGr
   if (b.n_hyp > 0) k_pose_count<<<hb, 256, 0, s>>>(g, b, pg.cnt);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_exclusive_scan(pg.cnt, pg.start, P, pg.tmp, s)) != cudaSuccess) return e;
-  k_pose_nonzero<<<pb, 256, 0, s>>>(pg.cnt, P, pg.flag);
+  k_pose_nonzero<<<pb, 256, 0, s>>>(pg.cnt, P, valid, tag, pg.flag);
   if ((e = launch_exclusive_scan(pg.flag, pg.gix, P, pg.tmp, s)) != cudaSuccess) return e;
-  k_pose_list<<<pb, 256, 0, s>>>(pg.cnt, pg.gix, P, pg.gpose);
+  k_pose_list<<<pb, 256, 0, s>>>(pg.flag, pg.gix, P, pg.gpose);
   k_mesh_ranges<<<(unsigned)((g.n_mesh + 255) / 256), 256, 0, s>>>(pg.start, pg.gix, g.n_mesh, per_mesh, pg.ranges);
   if (b.n_hyp > 0) k_pose_place<<<hb, 256, 0, s>>>(g, b, pg.start, pg.cnt, pg.order);
   return cudaGetLastError();

@@ -67,13 +67,18 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
   CK(cudaMemcpyAsync(ctx->b_plen.p, plen, 8, cudaMemcpyHostToDevice, ctx->stream), "copy");
   CK(cudaMemcpyAsync(ctx->b_hp.p, hp.data(), 4 * (size_t)n_sample, cudaMemcpyHostToDevice, ctx->stream), "copy");
   const std::vector<int> saved = ctx->mesh_threads;
-  // time the rasteriser itself: the exact shortcut would skip most root children
+  // time the rasteriser itself: the exact shortcut would skip most root
+  // children, and the render cache every render after the first
   struct ShortcutOff {
     perch_ctx* c;
-    bool was;
-    ~ShortcutOff() { c->shortcut = was; }
-  } shortcut_off{ctx, ctx->shortcut};
+    bool was, cache;
+    ~ShortcutOff() {
+      c->shortcut = was;
+      c->render_cache = cache;
+    }
+  } shortcut_off{ctx, ctx->shortcut, ctx->render_cache};
   ctx->shortcut = false;
+  ctx->render_cache = false;
   const bool shared = ctx->share_renders && ctx->store_ok;
   const std::vector<int> saved_cost = ctx->mesh_cost_threads, saved_inline = ctx->mesh_inline;
   auto restore = [&]() {

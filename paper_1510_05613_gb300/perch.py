@@ -32,7 +32,7 @@ EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_mesh
            "perch_cnn_forward", "perch_cnn_train_step", "perch_cnn_gradients", "perch_set_heuristic_net",
            "perch_cnn_set_tensor_path", "perch_cnn_tensor_status",
            "perch_set_shortcut", "perch_shortcut_stats", "perch_search_stats", "perch_search_times",
-           "perch_set_wait_limit", "perch_set_share_renders", "perch_last_phase_times", "perch_set_volumes",
+           "perch_set_wait_limit", "perch_set_share_renders", "perch_set_render_cache", "perch_last_phase_times", "perch_set_volumes",
            "perch_launch_config", "perch_set_symmetry", "perch_set_inline_pixels")
 
 
@@ -121,6 +121,7 @@ def load(path: str = LIB_PATH):
         "perch_set_inline_pixels": ([P, I32, I32], ctypes.c_int),
         "perch_set_symmetry": ([P, P, I32], ctypes.c_int),
         "perch_set_share_renders": ([P, I32], ctypes.c_int),
+        "perch_set_render_cache": ([P, I32], ctypes.c_int),
         "perch_last_phase_times": ([P, P, P], ctypes.c_int),
         "perch_search_stats": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -319,6 +320,11 @@ class Perch:
     def perch_set_share_renders(self, on: bool):
         """One render per distinct pose of a batch (on by default)."""
         return self._check(self.lib.perch_set_share_renders(self.h, 1 if on else 0))
+
+    def perch_set_render_cache(self, on: bool):
+        """Keep each pose's render across evaluations until the observation,
+        the scenes or the pose tables change (records unchanged)."""
+        return self._check(self.lib.perch_set_render_cache(self.h, 1 if on else 0))
 
     def perch_last_phase_times(self):
         """(ms per phase [prep, grouping, render, cost], shared renders used)."""

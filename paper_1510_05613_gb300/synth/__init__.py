@@ -710,6 +710,69 @@ def workload_c3(scene: int = 0, grid: PoseGrid | None = None, min_occlusion: flo
     raise RuntimeError("no heavily occluded scene found")
 
 
+def workload_c3_reduced(scene: int = 0, grid: PoseGrid | None = None, k: int = 3,
+                        min_occlusion: float = 0.3) -> Workload:
+    """The heavy-occlusion setting on a coarse pose grid, small enough for
+    the oracle's exact search: 640x480, k of the eight uneven meshes, the
+    tallest chosen one placed at a random cell and another one in the nearest
+    row behind it (as seen from the camera) whose footprint stays disjoint,
+    the rest anywhere disjoint; a scene is kept when some object is more than
+    min_occlusion (and less than 100%) occluded. Default grid 8 x 8 positions
+    (0.14 m apart) x 4 yaws; sigma 3 mm, 5% dropout, delta 1 cm."""
+    seed = 1000 * 3 + 500 + scene
+    cam, meshes = camera_c2(), meshes_c3()
+    grid = grid or pose_grid(-0.49, 0.14, 8, 4)
+    height = [float(m.verts[:, 2].max()) for m in meshes]
+    u = uniform(substream(seed, 7), 100000)
+    pos = 0
+
+    def take():
+        nonlocal pos
+        pos += 1
+        return u[pos - 1]
+
+    def disjoint(rows):
+        for i in range(len(rows)):
+            for j in range(i + 1, len(rows)):
+                dx = float(grid.xs[rows[i][1]]) - float(grid.xs[rows[j][1]])
+                dy = float(grid.ys[rows[i][2]]) - float(grid.ys[rows[j][2]])
+                rr = meshes[rows[i][0]].footprint_radius + meshes[rows[j][0]].footprint_radius + 0.005
+                if dx * dx + dy * dy < rr * rr:
+                    return False
+        return True
+
+    for _ in range(400):
+        ids = np.argsort(u[pos:pos + len(meshes)]).tolist()[:k]
+        pos += len(meshes)
+        front = max(ids, key=lambda m: height[m])
+        back = [m for m in ids if m != front][min(int(take() * (k - 1)), k - 2)]
+        fx_, fy_ = min(int(take() * grid.nx), grid.nx - 1), min(int(take() * (grid.ny - 1)), grid.ny - 2)
+        rows = [(front, fx_, fy_, min(int(take() * grid.n_yaw), grid.n_yaw - 1))]
+        for by in range(fy_ + 1, grid.ny):
+            cand = (back, fx_, by, min(int(take() * grid.n_yaw), grid.n_yaw - 1))
+            if disjoint(rows + [cand]):
+                rows.append(cand)
+                break
+        for m in ids:
+            if m in (front, back):
+                continue
+            for _ in range(50):
+                cand = (m, min(int(take() * grid.nx), grid.nx - 1), min(int(take() * grid.ny), grid.ny - 1),
+                        min(int(take() * grid.n_yaw), grid.n_yaw - 1))
+                if disjoint(rows + [cand]):
+                    rows.append(cand)
+                    break
+        if len(rows) < k:
+            continue
+        gt = objs(sorted(rows))
+        occ = occlusion_fractions(cam, meshes, grid, gt)
+        if min_occlusion < occ.max() < 1.0:
+            depth = observe(cam, meshes, grid, gt, 0.003, 0.05, seed)
+            return Workload("c3-reduced", cam, meshes, grid, 0.01, gt, depth, 0.003, 0.05, seed,
+                            extra={"occlusion": occ.tolist()})
+    raise RuntimeError("no occluded scene found")
+
+
 def workloads_c5(n_scenes: int = 256, grid: PoseGrid | None = None, cam: Camera | None = None, meshes=None,
                  k_range=(2, 6), seed_base: int = 5000, first: int = 0, off_grid: float = 0.0):
     """Many independent scenes for concurrent search: scene s draws K uniform

@@ -60,6 +60,7 @@ def test_null_context_and_null_args_are_rejected(lib):
     assert lib.perch_set_volumes(None, None, 0) == perch.PERCH_E_ARG
     assert lib.perch_set_wait_limit(None, 0) == perch.PERCH_E_ARG
     assert lib.perch_set_share_renders(None, 1) == perch.PERCH_E_ARG
+    assert lib.perch_set_render_cache(None, 1) == perch.PERCH_E_ARG
     assert lib.perch_launch_config(None, None, None, None) == perch.PERCH_E_ARG
     assert lib.perch_set_inline_pixels(None, -1, 16) == perch.PERCH_E_ARG
 

@@ -171,6 +171,71 @@ def test_shared_renders_identical_to_per_hypothesis_renders(c2):
     assert (a[:, 3] > 0).any() and (a[:, 2] > 0).any() and (a[:, 1] > 0).any()
 
 
+def test_render_cache_keeps_records(c2):
+    """With the render cache on, each pose's stored render is kept across
+    evaluations; a render depends on its mesh and pose (and its explained
+    flags on the observation), so batches that repeat and mix poses over
+    other parents, a single-parent batch and the first batch again give the
+    records of evaluating without it. A new observation empties the cache
+    (the explained flags change), checked against a cache-off evaluation of
+    that observation, and against the oracle on a sample."""
+    wl, p, w = c2
+    rng = np.random.default_rng(41)
+    wl2 = synth.workload_c2(scene=1)
+    allh = synth.all_hypotheses(wl.grid, [0, 1, 2])
+    near = np.concatenate([_near(wl.grid, wl.gt, {0, 1, 2}), _near(wl.grid, wl2.gt, {0, 1, 2})])
+    A = np.concatenate([allh[rng.choice(len(allh), 3000, replace=False)], near])
+    B = np.concatenate([A[::2], allh[rng.choice(len(allh), 1500, replace=False)]])
+    batches = [([wl.gt[:0], wl.gt[:1]], A), ([wl.gt[:2], wl.gt[:0], wl.gt[1:2]], B), ([wl.gt[:1]], B),
+               ([wl.gt[:0], wl.gt[:1]], A)]
+    hps = [rng.integers(0, len(par), len(h)).astype(np.int32) for par, h in batches]
+
+    def run():
+        return [_recs(p.perch_eval_successors(par, hp, h, wl.K)) for (par, h), hp in zip(batches, hps)]
+
+    try:
+        p.perch_set_shortcut(False)
+        ref = run()
+        p.perch_set_render_cache(True)
+        got = run()
+        for k, (a, b) in enumerate(zip(ref, got)):
+            assert np.array_equal(a, b), k
+        p.perch_eval_successors(batches[2][0], hps[2], batches[2][1], wl.K)
+        assert p.perch_last_phase_times()[1]  # one parent, yet shared renders (from the cache)
+        p.perch_set_observation(wl2.depth, wl2.cam.fxfycxcy, wl2.cam.T_wc, wl2.delta)
+        got2 = run()
+        p.perch_set_render_cache(False)
+        ref2 = run()
+        for k, (a, b) in enumerate(zip(ref2, got2)):
+            assert np.array_equal(a, b), k
+        assert any(not np.array_equal(a, b) for a, b in zip(ref, ref2))  # the observation matters
+    finally:
+        p.perch_set_render_cache(False)
+        p.perch_set_shortcut(True)
+        p.perch_set_observation(wl.depth, wl.cam.fxfycxcy, wl.cam.T_wc, wl.delta)
+    pick = rng.choice(len(A), 100, replace=False)
+    exp = oracle.eval_batch(w, wl.depth, batches[3][0], hps[3][pick], A[pick], wl.K)
+    assert np.array_equal(got[3][pick], exp)
+
+
+def test_render_cache_search_unchanged(c1):
+    """Uniform-cost search with the render cache on returns the same scene,
+    cost, expansions and successors as without it; with one state per batch
+    (single-parent batches, which the cache sends through shared renders)
+    the same scene and cost."""
+    wl, p, w = c1
+    base = p.perch_search(wl.mesh_multiset, batch_states=4)
+    p.perch_set_render_cache(True)
+    try:
+        r = p.perch_search(wl.mesh_multiset, batch_states=4)
+        r1 = p.perch_search(wl.mesh_multiset, batch_states=1)
+    finally:
+        p.perch_set_render_cache(False)
+    for k in ("cost", "key", "expansions", "successors", "proven_optimal"):
+        assert r[k] == base[k], k
+    assert (r1["cost"], r1["key"]) == (base["cost"], base["key"]) and r1["proven_optimal"]
+
+
 def _near(grid, objs, types):
     """Hypotheses at and around the ground-truth poses of the given types
     (one grid step and one yaw step away), where V(O) holds observed points."""
@@ -565,6 +630,10 @@ def test_multi_scene_eval_matches_oracle():
     hp = rng.integers(0, len(parents), 400).astype(np.int32)
     hyps = allh[rng.choice(len(allh), 400)]
     got = _recs(p.perch_eval_successors_multi(parents, pscene, pK, hp, hyps))
+    p.perch_set_render_cache(True)  # plain z kept across the two calls; the same records
+    for _ in range(2):
+        assert np.array_equal(_recs(p.perch_eval_successors_multi(parents, pscene, pK, hp, hyps)), got)
+    p.perch_set_render_cache(False)
     for s, wl in enumerate(wls):
         w = oracle.World.of(wl)
         for j in (2 * s, 2 * s + 1):

@@ -1,6 +1,7 @@
 """GPU tree search against the oracle's exact search at 640x480 (Sec. IV-B:
 uniform-cost search with h0 = 0 and w = 1 returns a minimum-cost scene;
-Sec. IV-D, Theorems 1 and 2 for Focal-MHA*).
+Sec. IV-D, Theorems 1 and 2 for Focal-MHA*), on the three-object workload
+and on the heavy-occlusion setting with the uneven meshes.
 
 The oracle's answers on the three-object 640x480 workload with its pose grid
 reduced to 8 x 8 positions x 4 yaws are stored in
@@ -67,3 +68,35 @@ def test_gpu_search_equals_oracle_search_c2_reduced(scene):
             break
     else:
         raise AssertionError("no valid order of the returned scene")
+
+
+GOLDEN_C3 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "search_c3_reduced.json")
+
+
+@pytest.mark.parametrize("scene", [0, 2])
+def test_gpu_search_equals_oracle_search_c3_reduced(scene):
+    """The heavy-occlusion setting (three of the uneven 2k-50k-triangle
+    meshes, one object 59-78% hidden behind a taller one) on an 8 x 8 x 4
+    grid: the GPU's exact search returns the oracle's cost and scene
+    (tests/golden/search_c3_reduced.json, written by
+    tests/golden/make_search_c3_reduced.py from oracle/ alone), with and
+    without the exact shortcut, the render cache, and the meshes' closed-form
+    volumes left at the inscribed cylinders the oracle used."""
+    with open(GOLDEN_C3) as f:
+        g = json.load(f)
+    exp = next(s for s in g["scenes"] if s["scene"] == scene)
+    gr = g["grid"]
+    wl = synth.workload_c3_reduced(scene=scene, grid=synth.pose_grid(gr["x0"], gr["step"], gr["n"], gr["n_yaw"]))
+    assert [round(float(x), 3) for x in wl.extra["occlusion"]] == exp["occlusion"]
+    key = tuple(tuple(o) for o in exp["key"])
+    p = perch.Perch(0)
+    p.setup(wl)
+    try:
+        for B, short, cache in ((1, True, False), (8, False, False), (8, True, True)):
+            p.perch_set_shortcut(short)
+            p.perch_set_render_cache(cache)
+            r = p.perch_search(wl.mesh_multiset, batch_states=B)
+            assert r["proven_optimal"]
+            assert (r["cost"], r["key"]) == (exp["cost"], key), (B, short, cache, r["cost"], r["key"])
+    finally:
+        p.close()
