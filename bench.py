@@ -470,7 +470,10 @@ def run_ours(args):
 
     if rank == 0:
         cl = clocks.summary()
-        traffic = (measured_traffic("perch_kernels.cu", f"k_eval_{args.workload}_launches.md")
+        # DRAM bytes per step of the dominant kernel (k_render with shared
+        # renders, else k_eval), from the committed summary of its ncu capture
+        traffic = (measured_traffic("perch_kernels.cu",
+                                    f"{'k_render' if shared else 'k_eval'}_{args.workload}_launches.md")
                    if not args.max_hyps else None)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
