@@ -500,7 +500,8 @@ def run_ours(args):
             "gpu_launches": ((14 + 2 * len(wl.meshes)) if shared else (8 + len(wl.meshes))) * args.steps,
             "launch": {"graph": not args.no_graph, "persistent_per_mesh": True, "autotuned_threads": widths,
                        "config_in_use": dict(zip(("render_threads", "render_inline_pixels", "cost_threads"),
-                                                 p.perch_launch_config())),
+                                                 p.perch_launch_config()),
+                                             render_bin_depth=p.perch_launch_bin_depths()),
                        "shared_renders": shared},
             "clocks": cl,
             "time_to_optimum": search,

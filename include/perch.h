@@ -356,6 +356,18 @@ int perch_launch_config(perch_ctx* ctx, int32_t* render_threads, int32_t* inline
  * it (coverage resolves by an order-independent max). */
 int perch_set_inline_pixels(perch_ctx* ctx, int32_t mesh, int32_t inline_pixels);
 
+/* The render's bin of larger triangles (the shared-memory queue each CTA
+ * fills with front faces whose box holds more than the inline limit's
+ * candidate centres, one warp per queued triangle): set its depth (32, 64 or
+ * 128 entries) for one mesh (mesh = -1: all), overriding the default 128 or
+ * an autotuned choice; a triangle that finds the bin full is rasterised by
+ * its own thread, so records do not depend on it. perch_autotune times the
+ * three depths per mesh after the CTA width and inline limit.
+ * perch_launch_bin_depths writes the depths in use to depths[n_mesh]
+ * (PERCH_E_STATE before meshes and pose grid are set). */
+int perch_set_bin_depth(perch_ctx* ctx, int32_t mesh, int32_t depth);
+int perch_launch_bin_depths(perch_ctx* ctx, int32_t* depths);
+
 /* Same work and arguments as perch_eval_successors_dev (device pointers), run
  * as a CUDA graph: the first call for a given argument set (and after any
  * change of meshes, pose grid or observation) runs the evaluation once and

@@ -158,6 +158,7 @@ int perch_ctx::ensure_tables() {
   if ((int)mesh_threads.size() != n_mesh) mesh_threads.assign(n_mesh, 256);
   if ((int)mesh_cost_threads.size() != n_mesh) mesh_cost_threads.assign(n_mesh, 128);
   if ((int)mesh_inline.size() != n_mesh) mesh_inline.assign(n_mesh, kInlinePixels);
+  if ((int)mesh_queue.size() != n_mesh) mesh_queue.assign(n_mesh, kBigQueue);
   const int rc = ensure_tile_store();
   if (rc != PERCH_OK) return rc;
   tables_valid = true;
@@ -845,6 +846,7 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
       Batch bm = b;
       bm.tile_w = mesh_tile_w[m];
       bm.tile_h = mesh_tile_h[m];
+      bm.queue_cap = mesh_queue[m];
       const RenderWork w{pg.gpose, rg + 4 * m + 2, rg + 4 * m + 3, g_next.as<int>() + m, tile_store.as<uint32_t>(),
                          tile_off.as<int>(), pose_flags.as<uint8_t>(), valid, tag};
       CK(launch_render_group(cam, g, obs, bm, w, std::min<long long>(n_hyp, per_mesh), mesh_threads[m],
@@ -883,6 +885,7 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
     Batch bm = b;
     bm.tile_w = mesh_tile_w[m];
     bm.tile_h = mesh_tile_h[m];
+    bm.queue_cap = mesh_queue[m];
     CK(launch_eval_group(cam, g, obs, bm, g_order.as<int>(), g_off.as<int>() + m, g_hist.as<int>() + m,
                          g_next.as<int>() + m, n_hyp, mesh_threads[m], sm_count, stream),
        "eval kernel");

@@ -123,6 +123,10 @@ struct Batch {
   // default); the wait that drains a copy after one gave up always uses
   // kWaitSpins
   int wait_polls;
+  // depth of the render's shared bin (queue) of larger triangles, per mesh
+  // (autotuned; <= 0 or above kBigQueue: kBigQueue); a triangle that finds
+  // the bin full is rasterised by its own thread
+  int queue_cap = 0;
 };
 
 // Shared renders (k_render, then k_cost): per-pose flags of the tile store

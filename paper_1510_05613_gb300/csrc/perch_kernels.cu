@@ -203,9 +203,21 @@ __device__ __forceinline__ void delta_window(const Camera& cam, float4 q, int& u
   }
 }
 
-// Eq. (1) against the new object's dR (the z tile, +inf off dR): is some
-// rendered point within delta of the observed point q?
-__device__ __forceinline__ bool explained_by_tile(const Camera& cam, float4 q, const uint32_t* tile,
+// The new object's dR over its pose's box (rows of the box width): either a
+// z tile with +inf off dR (mask == nullptr), or the staged render (z bits,
+// with the explained flag in the sign bit) and a bitmask of dR pixels.
+struct DRTile {
+  const uint32_t* z;
+  const uint32_t* mask;
+  __device__ __forceinline__ uint32_t at(int i) const {
+    if (!mask) return z[i];
+    return ((mask[i >> 5] >> (i & 31)) & 1u) ? (z[i] & 0x7fffffffu) : kInfBits;
+  }
+};
+
+// Eq. (1) against the new object's dR: is some rendered point within delta
+// of the observed point q?
+__device__ __forceinline__ bool explained_by_tile(const Camera& cam, float4 q, const DRTile& tile,
                                                   const float* rxs, const float* rys, int4 bb) {
   int u0, u1, v0, v1;
   delta_window(cam, q, u0, u1, v0, v1);
@@ -216,7 +228,7 @@ __device__ __forceinline__ bool explained_by_tile(const Camera& cam, float4 q, c
     const float ry = rys[ly];
     for (int u = u0; u <= u1; ++u) {
       const int lx = u - bb.x;
-      const uint32_t zb = tile[ly * bb.z + lx];
+      const uint32_t zb = tile.at(ly * bb.z + lx);
       if (zb == kInfBits) continue;
       const float z = __uint_as_float(zb);
       if (dist2(fmul(rxs[lx], z), fmul(ry, z), z, q) <= cam.delta2) return true;
@@ -857,8 +869,9 @@ size_t render_smem_bytes(int tile_w, int tile_h) {
          (size_t)kBigQueue * 8 + (size_t)tile_w * tile_h * 4;
 }
 
-size_t cost_smem_bytes(int tile_w, int tile_h) {  // stage (16-byte multiple), tile, ray slopes
-  return (size_t)((tile_w * tile_h + 3) & ~3) * 4 + (size_t)tile_w * tile_h * 4 + (size_t)(tile_w + tile_h) * 4;
+size_t cost_smem_bytes(int tile_w, int tile_h) {  // stage, dR bitmask (each a 16-byte multiple), ray slopes
+  return (size_t)((tile_w * tile_h + 3) & ~3) * 4 + (size_t)(((tile_w * tile_h + 31) / 32 + 3) & ~3) * 4 +
+         (size_t)(tile_w + tile_h) * 4;
 }
 
 // thread 0: start the bulk copies of the first chunk of mesh m at yaw iyaw
@@ -911,6 +924,7 @@ __device__ __forceinline__ int render_chunks(const Camera& cam, const Geometry& 
   const int ox16 = 16 * bb.x, oy16 = 16 * bb.y;
   uint32_t& pv = sh.pv;
   uint32_t& pt = sh.pt;
+  const int qcap = b.queue_cap > 0 && b.queue_cap < kBigQueue ? b.queue_cap : kBigQueue;
   bool v_pending = true, t_pending = true;  // a copy in flight on that barrier
   bool timed_out = false;
   for (int c = 0; c < m.chunk_count; ++c) {
@@ -961,7 +975,7 @@ __device__ __forceinline__ int render_chunks(const Camera& cam, const Geometry& 
         if (px0 > px1 || py0 > py1) continue;
         if ((px1 - px0 + 1) * (py1 - py0 + 1) > INL && px1 - px0 < 64 && py1 - py0 < 64) {
           const int slot = atomicAdd(&s_qn, 1);
-          if (slot < kBigQueue) {  // (triangle, box): x0 10 bits, y0 10 bits, w-1 and h-1 6 bits each
+          if (slot < qcap) {  // (triangle, box): x0 10 bits, y0 10 bits, w-1 and h-1 6 bits each
             queue[2 * slot] = pk;
             queue[2 * slot + 1] = (uint32_t)px0 | ((uint32_t)py0 << 10) | ((uint32_t)(px1 - px0) << 20) |
                                   ((uint32_t)(py1 - py0) << 26);
@@ -985,7 +999,7 @@ __device__ __forceinline__ int render_chunks(const Camera& cam, const Geometry& 
       t_pending = true;
     }
     // larger triangles: one warp per triangle, its pixel centres across lanes
-    const int nq = min(s_qn, kBigQueue);
+    const int nq = min(s_qn, qcap);
     for (int e = warp; e < nq; e += NW) {
       const uint32_t pk = queue[2 * e], box = queue[2 * e + 1];
       const int i0 = pk & 1023, i1 = (pk >> 10) & 1023, i2 = (pk >> 20) & 1023;
@@ -1097,6 +1111,63 @@ __device__ __forceinline__ void compare_phase(int pid, int plen, int4 bb, const 
   __syncthreads();
 }
 
+// compare_phase for a staged render that stays as it is (z bits, +inf =
+// empty, with kSrcZExplained the explained flag in the sign bit): the same
+// test and counts, but dR goes to a bitmask (bit i of mask[i / 32] = pixel i
+// is in dR) instead of a z tile. Warps take 32 consecutive pixels at a time
+// (NT is a multiple of 32, so every word is written by one ballot). Ends
+// with a CTA barrier.
+template <int NT, int SRC>
+__device__ __forceinline__ void compare_phase_mask(int pid, int plen, int4 bb, const Camera& cam, const Batch& b,
+                                                   const uint32_t* src, uint32_t* mask, int* s_cnt) {
+  static_assert(SRC != kSrcInvZ && NT % 32 == 0, "staged z source");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tw = bb.z, n = bb.z * bb.w;
+  int viol = 0, nnew = 0, djr = 0;
+  const float* zp = plen > 0 ? b.parent_z + (size_t)pid * cam.W * cam.H : nullptr;
+  const uint32_t mg = tw > 1 ? 0xffffffffu / (uint32_t)tw + 1u : 0u;  // i / tw, as in compare_phase
+  constexpr int U = 4;
+  for (int w0 = 32 * warp; w0 < n; w0 += NT * U) {  // warp-uniform
+    uint32_t sv[U];
+    float pz[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = w0 + u * NT + lane;
+      sv[u] = i < n ? src[i] : kInfBits;
+      pz[u] = __uint_as_float(kInfBits);
+      if (zp && sv[u] != kInfBits) {
+        const int ly = tw > 1 ? (int)__umulhi((uint32_t)i, mg) : i;
+        pz[u] = __ldg(&zp[(size_t)(bb.y + ly) * cam.W + bb.x + (i - ly * tw)]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      bool in_dr = false;
+      if (sv[u] != kInfBits) {
+        const uint32_t zb = sv[u] & ~kExplainedBit;
+        if (__float_as_uint(pz[u]) != kInfBits) {  // hidden by (or hiding) the parent: not in dR
+          if (__uint_as_float(zb) < pz[u]) viol++;
+        } else {
+          in_dr = true;
+          nnew++;
+          if (SRC == kSrcZExplained && !(sv[u] & kExplainedBit)) djr++;
+        }
+      }
+      const unsigned bits = __ballot_sync(0xffffffffu, in_dr);
+      if (lane == 0 && w0 + u * NT < n) mask[(w0 + u * NT) >> 5] = bits;
+    }
+  }
+  viol = warp_sum(viol);
+  nnew = warp_sum(nnew);
+  if (SRC == kSrcZExplained) djr = warp_sum(djr);
+  if (lane == 0) {
+    if (viol) atomicAdd(&s_cnt[0], viol);
+    if (nnew) atomicAdd(&s_cnt[1], nnew);
+    if (djr) atomicAdd(&s_cnt[3], djr);
+  }
+  __syncthreads();
+}
+
 // The rest of cost_phase, after compare_phase: the record of an invalid
 // child, or dJ_r (unless DJR_DONE: compare_phase counted it), dJ_o,
 // residual(K) and n_vol from the tile (z on dR, +inf elsewhere). Ends with a
@@ -1104,7 +1175,7 @@ __device__ __forceinline__ void compare_phase(int pid, int plen, int4 bb, const 
 template <int NT, bool DJR_DONE>
 __device__ __forceinline__ void finish_phase(long long h, int pid, int plen, int K_total, const perch_obj& o,
                                              int4 bb, const DevMesh& m, const Camera& cam, const Geometry& g,
-                                             const ObsIndex& obs, const Batch& b, const uint32_t* tile,
+                                             const ObsIndex& obs, const Batch& b, const DRTile& tile,
                                              const float* rxs, const float* rys, int* s_cnt) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1125,7 +1196,7 @@ __device__ __forceinline__ void finish_phase(long long h, int pid, int plen, int
   for (int ly = warp; !DJR_DONE && ly < th; ly += NW) {
     const float ry = rys[ly];
     for (int lx = lane; lx < tw; lx += 32) {
-      const uint32_t zb = tile[ly * tw + lx];
+      const uint32_t zb = tile.at(ly * tw + lx);
       if (zb == kInfBits) continue;
       const float z = __uint_as_float(zb);
       if (!explained_by_obs(obs, fmul(rxs[lx], z), fmul(ry, z), z, cam.delta2)) djr++;
@@ -1201,7 +1272,7 @@ __device__ __forceinline__ void cost_phase(long long h, int pid, int plen, int K
                                            const ObsIndex& obs, const Batch& b, uint32_t* tile, const float* rxs,
                                            const float* rys, int* s_cnt) {
   compare_phase<NT, kSrcInvZ>(pid, plen, bb, cam, b, tile, tile, s_cnt);
-  finish_phase<NT, false>(h, pid, plen, K_total, o, bb, m, cam, g, obs, b, tile, rxs, rys, s_cnt);
+  finish_phase<NT, false>(h, pid, plen, K_total, o, bb, m, cam, g, obs, b, DRTile{tile, nullptr}, rxs, rys, s_cnt);
 }
 
 // The checks every evaluation of hypothesis h makes before it touches its
@@ -1401,34 +1472,34 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_render(Camera cam, Geometry g
 
 // k_cost: one persistent CTA per SM slot costs hypotheses, sorted by pose,
 // from the tile store. A hypothesis's tile is brought into a shared stage
-// buffer by a 1D bulk copy (TMA), which threads only read. Thread 0 claims
-// the next hypothesis, looks up its arguments and box and starts the copy of
-// its tile as soon as the current one's compare pass has read the stage,
-// while the rest of the CTA runs dJ_r, dJ_o and the residual; the next
-// hypothesis reads what it found from shared memory. Hypotheses of the pose
-// whose tile the stage already holds (the batch is sorted by pose) take it
-// as it is, with no copy. The compare pass writes z (or +inf) into a
-// separate shared tile, which the delta windows of dJ_o and the residual
-// scan.
+// buffer by a 1D bulk copy (TMA), which threads only read: the compare pass
+// marks dR in a bitmask beside it, and dJ_r, dJ_o and the residual read z
+// from the stage through that mask. Thread 0 claims the next hypothesis and
+// looks up its arguments, box and tile while the rest of the CTA finishes the
+// current one; the copy starts once the stage is free. A hypothesis of the
+// pose whose tile the stage already holds (the batch is sorted by pose) takes
+// it as it is, with no copy. With one tile-sized buffer instead of two, twice
+// as many CTAs fit per SM to cover each other's copies.
 template <int NT, bool MULTI>
 __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex obs0, Batch b, CostWork w) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(16) ObsIndex s_obs;
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_cnt[7];
-  // the claimed item: its index, hypothesis, arguments, box, pose flags and
-  // how its tile reaches the stage (thread 0 writes it, everyone reads it)
+  // the claimed item: its index, hypothesis, arguments, box, pose flags, tile
+  // offset and how its tile reaches the stage (thread 0 writes it, everyone
+  // reads it)
   enum { kItemBad = 0, kItemFailed = 1, kItemCopy = 2, kItemReuse = 3 };
   __shared__ struct {
-    int item, state, pf;
+    int item, state, pf, off;
     long long h;
     HypArgs a;
     int4 bb;
   } s_nx;
   const int tid = threadIdx.x;
   uint32_t* stage = reinterpret_cast<uint32_t*>(smem);  // bulk-copy destination
-  uint32_t* tile = stage + ((b.tile_w * b.tile_h + 3) & ~3);
-  float* rxs = reinterpret_cast<float*>(tile + b.tile_w * b.tile_h);
+  uint32_t* mask = stage + ((b.tile_w * b.tile_h + 3) & ~3);
+  float* rxs = reinterpret_cast<float*>(mask + (((b.tile_w * b.tile_h + 31) / 32 + 3) & ~3));
   float* rys = rxs + b.tile_w;
   if (tid == 0) {
     mbar_init(&s_bar, 1);
@@ -1436,16 +1507,16 @@ __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex ob
   }
   __syncthreads();
   const int count = *w.count, offset = *w.offset;
-  long long stage_pose = -1;  // thread 0: the pose whose tile the stage holds or is receiving
-  // thread 0: claim the next item, look it up and start the copy of its tile
-  // unless the stage holds it; no barrier (the caller's next one publishes it)
+  long long stage_pose = -1;  // thread 0: the pose whose tile the stage holds or will receive
+  // thread 0: claim the next item and look it up; no barrier (the caller's
+  // next one publishes it)
   auto claim = [&]() {
     const int it = atomicAdd(w.next, 1);
     s_nx.item = it;
     if (it >= count) return;
     const long long h = w.order[offset + it];
     HypArgs a;
-    int state = kItemBad, pf = 0;
+    int state = kItemBad, pf = 0, off = 0;
     int4 bb = make_int4(0, 0, 0, 0);
     if (hyp_args(g, b, h, a)) {
       bb = g.pose_bbox[a.pose];
@@ -1455,8 +1526,7 @@ __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex ob
       } else if (bb.z <= b.tile_w && bb.w <= b.tile_h) {
         state = a.pose == stage_pose ? kItemReuse : kItemCopy;
         if (state == kItemCopy) {
-          bulk_load(stage, w.store + 4 * (size_t)w.tile_off[a.pose], 16u * (uint32_t)((bb.z * bb.w + 3) >> 2),
-                    &s_bar);
+          off = w.tile_off[a.pose];
           stage_pose = a.pose;
         }
       }
@@ -1464,6 +1534,7 @@ __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex ob
     s_nx.h = h;
     s_nx.state = state;
     s_nx.pf = pf;
+    s_nx.off = off;
     s_nx.a = a;
     s_nx.bb = bb;
   };
@@ -1477,7 +1548,7 @@ __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex ob
     const int state = s_nx.state, pf = s_nx.pf;
     const HypArgs a = s_nx.a;
     const int4 bb = s_nx.bb;
-    if (state == kItemBad || state == kItemFailed) {  // no copy was started for it
+    if (state == kItemBad || state == kItemFailed) {  // no copy for it
       __syncthreads();  // every thread has read s_nx
       if (tid == 0) {
         perch_cost r = {0, 0, 0, 0, 0, state == kItemFailed ? kFlagTimeout : kFlagBadIndex, 0};
@@ -1487,6 +1558,9 @@ __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex ob
       __syncthreads();
       continue;
     }
+    // the previous hypothesis's last barrier has passed: the stage is free
+    if (state == kItemCopy && tid == 0)
+      bulk_load(stage, w.store + 4 * (size_t)s_nx.off, 16u * (uint32_t)((bb.z * bb.w + 3) >> 2), &s_bar);
     if (MULTI && tid < (int)(sizeof(ObsIndex) / 4))
       reinterpret_cast<int*>(&s_obs)[tid] = reinterpret_cast<const int*>(&b.scenes[a.scene])[tid];
     const ObsIndex& obs = MULTI ? s_obs : obs0;
@@ -1516,10 +1590,11 @@ __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex ob
     }
     // a single-scene store holds z with the explained flag (k_render); a
     // multi-scene one plain z, and dJ_r is counted here against the scene
-    compare_phase<NT, MULTI ? kSrcZ : kSrcZExplained>(a.pid, a.plen, bb, cam, b, stage, tile, s_cnt);
-    if (tid == 0) claim();  // the stage is read: start the next copy while the rest runs
+    compare_phase_mask<NT, MULTI ? kSrcZ : kSrcZExplained>(a.pid, a.plen, bb, cam, b, stage, mask, s_cnt);
+    if (tid == 0) claim();  // look the next one up while the rest runs
     const DevMesh m = g.meshes[a.o.mesh];
-    finish_phase<NT, !MULTI>(h, a.pid, a.plen, a.K_total, a.o, bb, m, cam, g, obs, b, tile, rxs, rys, s_cnt);
+    finish_phase<NT, !MULTI>(h, a.pid, a.plen, a.K_total, a.o, bb, m, cam, g, obs, b, DRTile{stage, mask}, rxs, rys,
+                             s_cnt);
   }
 }
 

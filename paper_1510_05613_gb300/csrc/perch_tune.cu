@@ -26,13 +26,14 @@ namespace {
 using TuneKey = std::tuple<int, int, int, int, int, int>;  // device, tris, verts, tile_w, tile_h, shared renders
 std::mutex g_tune_mu;
 struct TuneChoice {
-  int threads, inline_px, cost_threads;
+  int threads, inline_px, cost_threads, bin_depth;
 };
 std::map<TuneKey, TuneChoice> g_tune_cache;
 
 constexpr int kWidths[3] = {128, 256, 512};
 constexpr int kInline[3] = {8, 16, 32};  // k_render's inline limit (candidate pixel centres per lane)
 constexpr int kCostWidths[2] = {128, 256};
+constexpr int kBinDepths[3] = {32, 64, 128};  // the render's shared bin of larger triangles
 
 }  // namespace
 
@@ -80,11 +81,13 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
   ctx->shortcut = false;
   ctx->render_cache = false;
   const bool shared = ctx->share_renders && ctx->store_ok;
-  const std::vector<int> saved_cost = ctx->mesh_cost_threads, saved_inline = ctx->mesh_inline;
+  const std::vector<int> saved_cost = ctx->mesh_cost_threads, saved_inline = ctx->mesh_inline,
+                         saved_bins = ctx->mesh_queue;
   auto restore = [&]() {
     ctx->mesh_threads = saved;
     ctx->mesh_cost_threads = saved_cost;
     ctx->mesh_inline = saved_inline;
+    ctx->mesh_queue = saved_bins;
   };
   for (int m = 0; m < n_mesh; ++m) {
     const TuneKey key{ctx->device,          ctx->h_meshes[m].n_tris, ctx->h_meshes[m].n_verts,
@@ -96,6 +99,7 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
         ctx->mesh_threads[m] = it->second.threads;
         ctx->mesh_inline[m] = it->second.inline_px;
         ctx->mesh_cost_threads[m] = it->second.cost_threads;
+        ctx->mesh_queue[m] = it->second.bin_depth;
         continue;
       }
     }
@@ -154,6 +158,23 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
       }
     ctx->mesh_threads[m] = best;
     ctx->mesh_inline[m] = best_inline;
+    // then the depth of the bin of larger triangles, at that width and limit
+    int best_bins = ctx->mesh_queue[m];
+    best_ms = 1e30f;
+    for (int d : kBinDepths) {
+      ctx->mesh_queue[m] = d;
+      float ms = 0.0f;
+      const int rc = time_phase(2, ms);
+      if (rc != PERCH_OK) {
+        restore();
+        return rc;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_bins = d;
+      }
+    }
+    ctx->mesh_queue[m] = best_bins;
     if (shared) {
       best_ms = 1e30f;
       for (int w : kCostWidths) {
@@ -172,7 +193,7 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
       ctx->mesh_cost_threads[m] = best_cost;
     }
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[key] = {best, best_inline, best_cost};
+    g_tune_cache[key] = {best, best_inline, best_cost, best_bins};
   }
   if (threads_out)
     for (int m = 0; m < n_mesh; ++m) threads_out[m] = ctx->mesh_threads[m];
@@ -256,6 +277,26 @@ extern "C" int perch_set_inline_pixels(perch_ctx* ctx, int32_t mesh, int32_t inl
   for (int m = 0; m < ctx->n_mesh; ++m)
     if (mesh < 0 || m == mesh) ctx->mesh_inline[m] = inline_pixels;
   ctx->tables_version++;  // a captured graph holds the old launch
+  return PERCH_OK;
+}
+
+extern "C" int perch_set_bin_depth(perch_ctx* ctx, int32_t mesh, int32_t depth) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (depth != 32 && depth != 64 && depth != 128) return ctx->fail(PERCH_E_ARG, "bin depth must be 32, 64 or 128");
+  if (mesh < -1 || mesh >= ctx->n_mesh) return ctx->fail(PERCH_E_ARG, "mesh %d out of range", mesh);
+  if ((int)ctx->mesh_queue.size() != ctx->n_mesh) ctx->mesh_queue.assign(ctx->n_mesh, kBigQueue);
+  for (int m = 0; m < ctx->n_mesh; ++m)
+    if (mesh < 0 || m == mesh) ctx->mesh_queue[m] = depth;
+  ctx->tables_version++;  // a captured graph holds the old launch
+  return PERCH_OK;
+}
+
+extern "C" int perch_launch_bin_depths(perch_ctx* ctx, int32_t* depths) {
+  if (!ctx || !depths) return PERCH_E_ARG;
+  ctx->err.clear();
+  if ((int)ctx->mesh_queue.size() != ctx->n_mesh) return ctx->fail(PERCH_E_STATE, "no geometry yet");
+  for (int m = 0; m < ctx->n_mesh; ++m) depths[m] = ctx->mesh_queue[m];
   return PERCH_OK;
 }
 

@@ -33,7 +33,8 @@ EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_mesh
            "perch_cnn_set_tensor_path", "perch_cnn_tensor_status",
            "perch_set_shortcut", "perch_shortcut_stats", "perch_search_stats", "perch_search_times",
            "perch_set_wait_limit", "perch_set_share_renders", "perch_set_render_cache", "perch_last_phase_times", "perch_set_volumes",
-           "perch_launch_config", "perch_set_symmetry", "perch_set_inline_pixels")
+           "perch_launch_config", "perch_set_symmetry", "perch_set_inline_pixels", "perch_set_bin_depth",
+           "perch_launch_bin_depths")
 
 
 class perch_mesh(ctypes.Structure):
@@ -119,6 +120,8 @@ def load(path: str = LIB_PATH):
         "perch_set_volumes": ([P, P, I32], ctypes.c_int),
         "perch_launch_config": ([P, P, P, P], ctypes.c_int),
         "perch_set_inline_pixels": ([P, I32, I32], ctypes.c_int),
+        "perch_set_bin_depth": ([P, I32, I32], ctypes.c_int),
+        "perch_launch_bin_depths": ([P, P], ctypes.c_int),
         "perch_set_symmetry": ([P, P, I32], ctypes.c_int),
         "perch_set_share_renders": ([P, I32], ctypes.c_int),
         "perch_set_render_cache": ([P, I32], ctypes.c_int),
@@ -352,6 +355,16 @@ class Perch:
     def perch_set_inline_pixels(self, inline_pixels: int, mesh: int = -1):
         """The render's inline limit (8, 16 or 32) for one mesh or all."""
         return self._check(self.lib.perch_set_inline_pixels(self.h, mesh, int(inline_pixels)))
+
+    def perch_set_bin_depth(self, depth: int, mesh: int = -1):
+        """Depth (32, 64 or 128) of the render's bin of larger triangles, for one mesh or all."""
+        return self._check(self.lib.perch_set_bin_depth(self.h, mesh, int(depth)))
+
+    def perch_launch_bin_depths(self):
+        """The bin depth in use per mesh."""
+        out = np.zeros(self.n_mesh, np.int32)
+        self._check(self.lib.perch_launch_bin_depths(self.h, out.ctypes.data))
+        return out.tolist()
 
     def perch_set_volumes(self, meshes):
         """V(O) per mesh from each synth.Mesh's closed-form `volume` (None:
