@@ -501,7 +501,8 @@ def run_ours(args):
             "launch": {"graph": not args.no_graph, "persistent_per_mesh": True, "autotuned_threads": widths,
                        "config_in_use": dict(zip(("render_threads", "render_inline_pixels", "cost_threads"),
                                                  p.perch_launch_config()),
-                                             render_bin_depth=p.perch_launch_bin_depths()),
+                                             render_bin_depth=p.perch_launch_bin_depths(),
+                                             cost_stages=p.perch_launch_cost_stages()),
                        "shared_renders": shared},
             "clocks": cl,
             "time_to_optimum": search,

@@ -368,6 +368,16 @@ int perch_set_inline_pixels(perch_ctx* ctx, int32_t mesh, int32_t inline_pixels)
 int perch_set_bin_depth(perch_ctx* ctx, int32_t mesh, int32_t depth);
 int perch_launch_bin_depths(perch_ctx* ctx, int32_t* depths);
 
+/* The cost launch's stage buffers for the stored tiles: 1 (default; the next
+ * tile is copied once the current hypothesis is done, and more CTAs fit per
+ * SM) or 2 (the next tile is copied while the current one is costed), for
+ * one mesh (mesh = -1: all). Two are used only where they fit in shared
+ * memory; records do not depend on it. perch_autotune times both with each
+ * cost CTA width. perch_launch_cost_stages writes the stages in use to
+ * stages[n_mesh] (PERCH_E_STATE before meshes and pose grid are set). */
+int perch_set_cost_stages(perch_ctx* ctx, int32_t mesh, int32_t stages);
+int perch_launch_cost_stages(perch_ctx* ctx, int32_t* stages);
+
 /* Same work and arguments as perch_eval_successors_dev (device pointers), run
  * as a CUDA graph: the first call for a given argument set (and after any
  * change of meshes, pose grid or observation) runs the evaluation once and

@@ -157,6 +157,7 @@ int perch_ctx::ensure_tables() {
     return fail(PERCH_E_RANGE, "object screen box %dx%d does not fit in shared memory", tile_w, tile_h);
   if ((int)mesh_threads.size() != n_mesh) mesh_threads.assign(n_mesh, 256);
   if ((int)mesh_cost_threads.size() != n_mesh) mesh_cost_threads.assign(n_mesh, 128);
+  if ((int)mesh_cost_stages.size() != n_mesh) mesh_cost_stages.assign(n_mesh, 1);
   if ((int)mesh_inline.size() != n_mesh) mesh_inline.assign(n_mesh, kInlinePixels);
   if ((int)mesh_queue.size() != n_mesh) mesh_queue.assign(n_mesh, kBigQueue);
   const int rc = ensure_tile_store();
@@ -860,7 +861,8 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
       bm.tile_h = mesh_tile_h[m];
       const CostWork c{pg.order, rg + 4 * m, rg + 4 * m + 1, g_next.as<int>() + n_mesh + m, tile_store.as<uint32_t>(),
                        tile_off.as<int>(), pose_flags.as<uint8_t>()};
-      CK(launch_cost_group(cam, g, obs, bm, c, n_hyp, mesh_cost_threads[m], sm_count, stream), "cost kernel");
+      CK(launch_cost_group(cam, g, obs, bm, c, n_hyp, mesh_cost_threads[m], mesh_cost_stages[m], sm_count, stream),
+         "cost kernel");
     }
     last_path = 2;
     if (!capturing) {

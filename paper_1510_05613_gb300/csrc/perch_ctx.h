@@ -101,6 +101,7 @@ struct perch_ctx {
   DevBuf tile_store, tile_off, tile_sizes, pose_flags;
   DevBuf pg_cnt, pg_start, pg_flag, pg_gix, pg_gpose, pg_tmp, pg_ranges;  // hypotheses grouped by pose
   std::vector<int> mesh_cost_threads;  // CTA width of k_cost per mesh (autotuned; 128 by default)
+  std::vector<int> mesh_cost_stages;   // stage buffers of k_cost per mesh (1 or 2; autotuned; 1 by default)
   std::vector<int> mesh_inline;        // k_render's inline limit per mesh (autotuned; 16 by default)
   std::vector<int> mesh_queue;         // depth of the render's bin of larger triangles per mesh (autotuned)
   int last_path = 0;       // last evaluation: 1 = one render per hypothesis, 2 = shared renders

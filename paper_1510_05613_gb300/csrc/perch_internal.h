@@ -208,7 +208,7 @@ cudaError_t launch_eval_group(const Camera& cam, const Geometry& g, const ObsInd
                               int threads, int sm_count, cudaStream_t s);
 size_t eval_smem_bytes(int tile_w, int tile_h);
 size_t render_smem_bytes(int tile_w, int tile_h);
-size_t cost_smem_bytes(int tile_w, int tile_h);
+size_t cost_smem_bytes(int tile_w, int tile_h, int stages);
 // per pose: its tile's size in 16-byte units (screen box area rounded up to 4
 // pixels), exclusive scan into tile_off[P + 1]
 cudaError_t launch_tile_offsets(const Geometry& g, int* sizes, int* tile_off, int* tmp, cudaStream_t s);
@@ -221,7 +221,9 @@ cudaError_t launch_render_group(const Camera& cam, const Geometry& g, const ObsI
                                 const RenderWork& w, long long max_items, int threads, int inline_px,
                                 int sm_count, cudaStream_t s);
 cudaError_t launch_cost_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
-                              const CostWork& w, long long max_items, int threads, int sm_count, cudaStream_t s);
+                              const CostWork& w, long long max_items, int threads, int stages, int sm_count,
+                              cudaStream_t s);
+bool cost_stages_fit(int device, int tile_w, int tile_h, int stages);
 // loads the kernels the allocation-free evaluation launches (a lazily loaded
 // module or function would otherwise be loaded, and may allocate, at its
 // first launch)

@@ -869,8 +869,8 @@ size_t render_smem_bytes(int tile_w, int tile_h) {
          (size_t)kBigQueue * 8 + (size_t)tile_w * tile_h * 4;
 }
 
-size_t cost_smem_bytes(int tile_w, int tile_h) {  // stage, dR bitmask (each a 16-byte multiple), ray slopes
-  return (size_t)((tile_w * tile_h + 3) & ~3) * 4 + (size_t)(((tile_w * tile_h + 31) / 32 + 3) & ~3) * 4 +
+size_t cost_smem_bytes(int tile_w, int tile_h, int stages) {  // stages, dR bitmask (16-byte multiples), rays
+  return (size_t)stages * ((tile_w * tile_h + 3) & ~3) * 4 + (size_t)(((tile_w * tile_h + 31) / 32 + 3) & ~3) * 4 +
          (size_t)(tile_w + tile_h) * 4;
 }
 
@@ -1471,52 +1471,65 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_render(Camera cam, Geometry g
 }
 
 // k_cost: one persistent CTA per SM slot costs hypotheses, sorted by pose,
-// from the tile store. A hypothesis's tile is brought into a shared stage
-// buffer by a 1D bulk copy (TMA), which threads only read: the compare pass
-// marks dR in a bitmask beside it, and dJ_r, dJ_o and the residual read z
-// from the stage through that mask. Thread 0 claims the next hypothesis and
+// from the tile store. A hypothesis's tile is brought into one of NS shared
+// stage buffers by a 1D bulk copy (TMA), which threads only read: the compare
+// pass marks dR in a bitmask beside it, and dJ_r, dJ_o and the residual read
+// z from the stage through that mask. Thread 0 claims the next hypothesis and
 // looks up its arguments, box and tile while the rest of the CTA finishes the
-// current one; the copy starts once the stage is free. A hypothesis of the
-// pose whose tile the stage already holds (the batch is sorted by pose) takes
-// it as it is, with no copy. With one tile-sized buffer instead of two, twice
-// as many CTAs fit per SM to cover each other's copies.
-template <int NT, bool MULTI>
+// current one. A hypothesis of a pose whose tile a stage already holds (the
+// batch is sorted by pose) takes it as it is, with no copy. With one stage
+// (NS = 1) the copy starts once the current hypothesis is done, and the
+// smaller footprint lets more CTAs share an SM to cover each other's copies;
+// with two (NS = 2, where the tiles are small) it starts into the other stage
+// as soon as the next hypothesis is claimed, and overlaps dJ_o and the
+// residual.
+template <int NT, bool MULTI, int NS>
 __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex obs0, Batch b, CostWork w) {
+  static_assert(NS == 1 || NS == 2, "one or two stages");
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(16) ObsIndex s_obs;
-  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(8) uint64_t s_bar[NS];
   __shared__ int s_cnt[7];
   // the claimed item: its index, hypothesis, arguments, box, pose flags, tile
-  // offset and how its tile reaches the stage (thread 0 writes it, everyone
-  // reads it)
+  // offset, stage and how its tile reaches the stage (thread 0 writes it,
+  // everyone reads it)
   enum { kItemBad = 0, kItemFailed = 1, kItemCopy = 2, kItemReuse = 3 };
   __shared__ struct {
-    int item, state, pf, off;
+    int item, state, pf, off, sidx;
     long long h;
     HypArgs a;
     int4 bb;
   } s_nx;
   const int tid = threadIdx.x;
-  uint32_t* stage = reinterpret_cast<uint32_t*>(smem);  // bulk-copy destination
-  uint32_t* mask = stage + ((b.tile_w * b.tile_h + 3) & ~3);
+  const int stage_words = (b.tile_w * b.tile_h + 3) & ~3;  // 16-byte multiples
+  uint32_t* mask = reinterpret_cast<uint32_t*>(smem) + NS * stage_words;
   float* rxs = reinterpret_cast<float*>(mask + (((b.tile_w * b.tile_h + 31) / 32 + 3) & ~3));
   float* rys = rxs + b.tile_w;
   if (tid == 0) {
-    mbar_init(&s_bar, 1);
+    for (int k = 0; k < NS; ++k) mbar_init(&s_bar[k], 1);
     fence_barrier_init();
   }
   __syncthreads();
   const int count = *w.count, offset = *w.offset;
-  long long stage_pose = -1;  // thread 0: the pose whose tile the stage holds or will receive
-  // thread 0: claim the next item and look it up; no barrier (the caller's
-  // next one publishes it)
+  // thread 0: the pose whose tile each stage holds or will receive, and the
+  // stage of the last claimed item
+  long long stage_pose[NS];
+  for (int k = 0; k < NS; ++k) stage_pose[k] = -1;
+  int cur = 0;
+  auto stage_of = [&](int k) { return reinterpret_cast<uint32_t*>(smem) + k * stage_words; };
+  auto copy = [&](int k, int off, int4 bb) {
+    bulk_load(stage_of(k), w.store + 4 * (size_t)off, 16u * (uint32_t)((bb.z * bb.w + 3) >> 2), &s_bar[k]);
+  };
+  // thread 0: claim the next item and look it up; with two stages also start
+  // its copy into the stage the current item does not use. No barrier (the
+  // caller's next one publishes it)
   auto claim = [&]() {
     const int it = atomicAdd(w.next, 1);
     s_nx.item = it;
     if (it >= count) return;
     const long long h = w.order[offset + it];
     HypArgs a;
-    int state = kItemBad, pf = 0, off = 0;
+    int state = kItemBad, pf = 0, off = 0, sidx = cur;
     int4 bb = make_int4(0, 0, 0, 0);
     if (hyp_args(g, b, h, a)) {
       bb = g.pose_bbox[a.pose];
@@ -1524,28 +1537,38 @@ __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex ob
       if (pf & kPoseFailed) {
         state = kItemFailed;
       } else if (bb.z <= b.tile_w && bb.w <= b.tile_h) {
-        state = a.pose == stage_pose ? kItemReuse : kItemCopy;
-        if (state == kItemCopy) {
+        if (a.pose == stage_pose[cur]) {
+          state = kItemReuse;
+        } else if (NS == 2 && a.pose == stage_pose[NS - 1 - cur]) {
+          state = kItemReuse;
+          sidx = NS - 1 - cur;
+        } else {
+          state = kItemCopy;
           off = w.tile_off[a.pose];
-          stage_pose = a.pose;
+          sidx = NS - 1 - cur;  // the other stage (the same one with NS = 1)
+          stage_pose[sidx] = a.pose;
+          if (NS == 2) copy(sidx, off, bb);  // the other stage's last reader has finished
         }
+        cur = sidx;
       }
     }
     s_nx.h = h;
     s_nx.state = state;
     s_nx.pf = pf;
     s_nx.off = off;
+    s_nx.sidx = sidx;
     s_nx.a = a;
     s_nx.bb = bb;
   };
   if (tid == 0) claim();
   __syncthreads();
-  uint32_t parity = 0;
+  uint32_t parity[NS];
+  for (int k = 0; k < NS; ++k) parity[k] = 0;
   for (;;) {
     const int item = s_nx.item;
     if (item >= count) break;
     const long long h = s_nx.h;
-    const int state = s_nx.state, pf = s_nx.pf;
+    const int state = s_nx.state, pf = s_nx.pf, sidx = s_nx.sidx;
     const HypArgs a = s_nx.a;
     const int4 bb = s_nx.bb;
     if (state == kItemBad || state == kItemFailed) {  // no copy for it
@@ -1558,9 +1581,8 @@ __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex ob
       __syncthreads();
       continue;
     }
-    // the previous hypothesis's last barrier has passed: the stage is free
-    if (state == kItemCopy && tid == 0)
-      bulk_load(stage, w.store + 4 * (size_t)s_nx.off, 16u * (uint32_t)((bb.z * bb.w + 3) >> 2), &s_bar);
+    // one stage: the previous hypothesis's last barrier has passed, the stage is free
+    if (NS == 1 && state == kItemCopy && tid == 0) copy(0, s_nx.off, bb);
     if (MULTI && tid < (int)(sizeof(ObsIndex) / 4))
       reinterpret_cast<int*>(&s_obs)[tid] = reinterpret_cast<const int*>(&b.scenes[a.scene])[tid];
     const ObsIndex& obs = MULTI ? s_obs : obs0;
@@ -1571,27 +1593,28 @@ __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex ob
       // wait for the stage (bounded); on give-up drain the copy with the
       // full bound, report the hypothesis and go on, or stop if it is still
       // in flight
-      if (!__syncthreads_and(mbar_wait(&s_bar, parity, b.wait_polls))) {
-        const bool drained = __syncthreads_and(mbar_wait(&s_bar, parity));
+      if (!__syncthreads_and(mbar_wait(&s_bar[sidx], parity[sidx], b.wait_polls))) {
+        const bool drained = __syncthreads_and(mbar_wait(&s_bar[sidx], parity[sidx]));
         if (tid == 0) {
           perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout, 0};
           b.out[h] = r;
-          stage_pose = -1;
+          for (int k = 0; k < NS; ++k) stage_pose[k] = -1;
           if (drained) claim();
         }
         if (!drained) break;
-        parity ^= 1u;
+        parity[sidx] ^= 1u;
         __syncthreads();
         continue;
       }
-      parity ^= 1u;
+      parity[sidx] ^= 1u;
     } else {
-      __syncthreads();  // the stage holds this pose's tile already; rays and counters are written
+      __syncthreads();  // a stage holds this pose's tile already; rays and counters are written
     }
+    const uint32_t* stage = stage_of(sidx);
     // a single-scene store holds z with the explained flag (k_render); a
     // multi-scene one plain z, and dJ_r is counted here against the scene
     compare_phase_mask<NT, MULTI ? kSrcZ : kSrcZExplained>(a.pid, a.plen, bb, cam, b, stage, mask, s_cnt);
-    if (tid == 0) claim();  // look the next one up while the rest runs
+    if (tid == 0) claim();  // look the next one up (and with two stages start its copy)
     const DevMesh m = g.meshes[a.o.mesh];
     finish_phase<NT, !MULTI>(h, a.pid, a.plen, a.K_total, a.o, bb, m, cam, g, obs, b, DRTile{stage, mask}, rxs, rys,
                              s_cnt);
@@ -1911,11 +1934,11 @@ cudaError_t launch_render_group(const Camera& cam, const Geometry& g, const ObsI
   }
 }
 
-template <int NT, bool MULTI>
+template <int NT, bool MULTI, int NS>
 static cudaError_t launch_cost_t(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
                                  const CostWork& w, long long max_items, int sm_count, cudaStream_t s) {
-  const size_t smem = cost_smem_bytes(b.tile_w, b.tile_h);
-  auto kern = k_cost<NT, MULTI>;
+  const size_t smem = cost_smem_bytes(b.tile_w, b.tile_h, NS);
+  auto kern = k_cost<NT, MULTI, NS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -1929,17 +1952,36 @@ static cudaError_t launch_cost_t(const Camera& cam, const Geometry& g, const Obs
   return cudaGetLastError();
 }
 
-// One persistent launch costing one mesh's hypotheses of a batch from the
-// tile store, with CTAs of `threads` (128 or 256).
-cudaError_t launch_cost_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
-                              const CostWork& w, long long max_items, int threads, int sm_count, cudaStream_t s) {
-  if (max_items <= 0) return cudaSuccess;
+template <int NS>
+static cudaError_t launch_cost_s(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                                 const CostWork& w, long long max_items, int threads, int sm_count, cudaStream_t s) {
   const bool multi = b.parent_scene != nullptr;
   if (threads == 256)
-    return multi ? launch_cost_t<256, true>(cam, g, obs, b, w, max_items, sm_count, s)
-                 : launch_cost_t<256, false>(cam, g, obs, b, w, max_items, sm_count, s);
-  return multi ? launch_cost_t<128, true>(cam, g, obs, b, w, max_items, sm_count, s)
-               : launch_cost_t<128, false>(cam, g, obs, b, w, max_items, sm_count, s);
+    return multi ? launch_cost_t<256, true, NS>(cam, g, obs, b, w, max_items, sm_count, s)
+                 : launch_cost_t<256, false, NS>(cam, g, obs, b, w, max_items, sm_count, s);
+  return multi ? launch_cost_t<128, true, NS>(cam, g, obs, b, w, max_items, sm_count, s)
+               : launch_cost_t<128, false, NS>(cam, g, obs, b, w, max_items, sm_count, s);
+}
+
+// One persistent launch costing one mesh's hypotheses of a batch from the
+// tile store, with CTAs of `threads` (128 or 256) and `stages` (1 or 2) stage
+// buffers; two stages fall back to one where they do not fit.
+bool cost_stages_fit(int device, int tile_w, int tile_h, int stages) {
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return false;
+  return cost_smem_bytes(tile_w, tile_h, stages) + 1024 <= (size_t)optin;  // 1024: static shared memory
+}
+
+cudaError_t launch_cost_group(const Camera& cam, const Geometry& g, const ObsIndex& obs, const Batch& b,
+                              const CostWork& w, long long max_items, int threads, int stages, int sm_count,
+                              cudaStream_t s) {
+  if (max_items <= 0) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (stages == 2 && cost_stages_fit(dev, b.tile_w, b.tile_h, 2))
+    return launch_cost_s<2>(cam, g, obs, b, w, max_items, threads, sm_count, s);
+  return launch_cost_s<1>(cam, g, obs, b, w, max_items, threads, sm_count, s);
 }
 
 // One persistent launch for one group of hypotheses with CTAs of `threads`

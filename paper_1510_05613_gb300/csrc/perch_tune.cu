@@ -26,7 +26,7 @@ namespace {
 using TuneKey = std::tuple<int, int, int, int, int, int>;  // device, tris, verts, tile_w, tile_h, shared renders
 std::mutex g_tune_mu;
 struct TuneChoice {
-  int threads, inline_px, cost_threads, bin_depth;
+  int threads, inline_px, cost_threads, bin_depth, cost_stages;
 };
 std::map<TuneKey, TuneChoice> g_tune_cache;
 
@@ -82,12 +82,13 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
   ctx->render_cache = false;
   const bool shared = ctx->share_renders && ctx->store_ok;
   const std::vector<int> saved_cost = ctx->mesh_cost_threads, saved_inline = ctx->mesh_inline,
-                         saved_bins = ctx->mesh_queue;
+                         saved_bins = ctx->mesh_queue, saved_stages = ctx->mesh_cost_stages;
   auto restore = [&]() {
     ctx->mesh_threads = saved;
     ctx->mesh_cost_threads = saved_cost;
     ctx->mesh_inline = saved_inline;
     ctx->mesh_queue = saved_bins;
+    ctx->mesh_cost_stages = saved_stages;
   };
   for (int m = 0; m < n_mesh; ++m) {
     const TuneKey key{ctx->device,          ctx->h_meshes[m].n_tris, ctx->h_meshes[m].n_verts,
@@ -100,6 +101,7 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
         ctx->mesh_inline[m] = it->second.inline_px;
         ctx->mesh_cost_threads[m] = it->second.cost_threads;
         ctx->mesh_queue[m] = it->second.bin_depth;
+        ctx->mesh_cost_stages[m] = it->second.cost_stages;
         continue;
       }
     }
@@ -175,25 +177,32 @@ extern "C" int perch_autotune(perch_ctx* ctx, int32_t n_sample, int32_t* threads
       }
     }
     ctx->mesh_queue[m] = best_bins;
+    int best_stages = ctx->mesh_cost_stages[m];
     if (shared) {
+      // the cost: CTA width x stage buffers (two only where they fit)
       best_ms = 1e30f;
-      for (int w : kCostWidths) {
-        ctx->mesh_cost_threads[m] = w;
-        float ms = 0.0f;
-        const int rc = time_phase(3, ms);
-        if (rc != PERCH_OK) {
-          restore();
-          return rc;
+      for (int w : kCostWidths)
+        for (int ns = 1; ns <= 2; ++ns) {
+          if (ns == 2 && !cost_stages_fit(ctx->device, ctx->mesh_tile_w[m], ctx->mesh_tile_h[m], 2)) continue;
+          ctx->mesh_cost_threads[m] = w;
+          ctx->mesh_cost_stages[m] = ns;
+          float ms = 0.0f;
+          const int rc = time_phase(3, ms);
+          if (rc != PERCH_OK) {
+            restore();
+            return rc;
+          }
+          if (ms < best_ms) {
+            best_ms = ms;
+            best_cost = w;
+            best_stages = ns;
+          }
         }
-        if (ms < best_ms) {
-          best_ms = ms;
-          best_cost = w;
-        }
-      }
       ctx->mesh_cost_threads[m] = best_cost;
+      ctx->mesh_cost_stages[m] = best_stages;
     }
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[key] = {best, best_inline, best_cost, best_bins};
+    g_tune_cache[key] = {best, best_inline, best_cost, best_bins, best_stages};
   }
   if (threads_out)
     for (int m = 0; m < n_mesh; ++m) threads_out[m] = ctx->mesh_threads[m];
@@ -289,6 +298,30 @@ extern "C" int perch_set_bin_depth(perch_ctx* ctx, int32_t mesh, int32_t depth) 
   for (int m = 0; m < ctx->n_mesh; ++m)
     if (mesh < 0 || m == mesh) ctx->mesh_queue[m] = depth;
   ctx->tables_version++;  // a captured graph holds the old launch
+  return PERCH_OK;
+}
+
+extern "C" int perch_set_cost_stages(perch_ctx* ctx, int32_t mesh, int32_t stages) {
+  if (!ctx) return PERCH_E_ARG;
+  ctx->err.clear();
+  if (stages != 1 && stages != 2) return ctx->fail(PERCH_E_ARG, "cost stages must be 1 or 2");
+  if (mesh < -1 || mesh >= ctx->n_mesh) return ctx->fail(PERCH_E_ARG, "mesh %d out of range", mesh);
+  if ((int)ctx->mesh_cost_stages.size() != ctx->n_mesh) ctx->mesh_cost_stages.assign(ctx->n_mesh, 1);
+  for (int m = 0; m < ctx->n_mesh; ++m)
+    if (mesh < 0 || m == mesh) ctx->mesh_cost_stages[m] = stages;
+  ctx->tables_version++;  // a captured graph holds the old launch
+  return PERCH_OK;
+}
+
+extern "C" int perch_launch_cost_stages(perch_ctx* ctx, int32_t* stages) {
+  if (!ctx || !stages) return PERCH_E_ARG;
+  ctx->err.clear();
+  if ((int)ctx->mesh_cost_stages.size() != ctx->n_mesh) return ctx->fail(PERCH_E_STATE, "no geometry yet");
+  for (int m = 0; m < ctx->n_mesh; ++m)
+    stages[m] = ctx->mesh_cost_stages[m] == 2 &&
+                        cost_stages_fit(ctx->device, ctx->mesh_tile_w[m], ctx->mesh_tile_h[m], 2)
+                    ? 2
+                    : 1;
   return PERCH_OK;
 }
 

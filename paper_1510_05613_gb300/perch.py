@@ -34,7 +34,7 @@ EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_mesh
            "perch_set_shortcut", "perch_shortcut_stats", "perch_search_stats", "perch_search_times",
            "perch_set_wait_limit", "perch_set_share_renders", "perch_set_render_cache", "perch_last_phase_times", "perch_set_volumes",
            "perch_launch_config", "perch_set_symmetry", "perch_set_inline_pixels", "perch_set_bin_depth",
-           "perch_launch_bin_depths")
+           "perch_launch_bin_depths", "perch_set_cost_stages", "perch_launch_cost_stages")
 
 
 class perch_mesh(ctypes.Structure):
@@ -122,6 +122,8 @@ def load(path: str = LIB_PATH):
         "perch_set_inline_pixels": ([P, I32, I32], ctypes.c_int),
         "perch_set_bin_depth": ([P, I32, I32], ctypes.c_int),
         "perch_launch_bin_depths": ([P, P], ctypes.c_int),
+        "perch_set_cost_stages": ([P, I32, I32], ctypes.c_int),
+        "perch_launch_cost_stages": ([P, P], ctypes.c_int),
         "perch_set_symmetry": ([P, P, I32], ctypes.c_int),
         "perch_set_share_renders": ([P, I32], ctypes.c_int),
         "perch_set_render_cache": ([P, I32], ctypes.c_int),
@@ -364,6 +366,16 @@ class Perch:
         """The bin depth in use per mesh."""
         out = np.zeros(self.n_mesh, np.int32)
         self._check(self.lib.perch_launch_bin_depths(self.h, out.ctypes.data))
+        return out.tolist()
+
+    def perch_set_cost_stages(self, stages: int, mesh: int = -1):
+        """Stage buffers (1 or 2) of the cost launch, for one mesh or all."""
+        return self._check(self.lib.perch_set_cost_stages(self.h, mesh, int(stages)))
+
+    def perch_launch_cost_stages(self):
+        """The cost launch's stage buffers in use per mesh."""
+        out = np.zeros(self.n_mesh, np.int32)
+        self._check(self.lib.perch_launch_cost_stages(self.h, out.ctypes.data))
         return out.tolist()
 
     def perch_set_volumes(self, meshes):

@@ -65,6 +65,8 @@ def test_null_context_and_null_args_are_rejected(lib):
     assert lib.perch_set_inline_pixels(None, -1, 16) == perch.PERCH_E_ARG
     assert lib.perch_set_bin_depth(None, -1, 64) == perch.PERCH_E_ARG
     assert lib.perch_launch_bin_depths(None, None) == perch.PERCH_E_ARG
+    assert lib.perch_set_cost_stages(None, -1, 2) == perch.PERCH_E_ARG
+    assert lib.perch_launch_cost_stages(None, None) == perch.PERCH_E_ARG
 
 
 def test_create_without_gpu_fails_cleanly(lib):

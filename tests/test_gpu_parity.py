@@ -485,9 +485,12 @@ def test_render_launch_parameters_do_not_change_records():
     """The render's CTA width, inline limit (which triangles a lane
     rasterises itself and which a warp takes from the queue) and bin depth
     (how many the queue holds before a lane rasterises one) change only who
-    writes a pixel's depth, never the depth: the same records for every
-    setting the autotuner can pick, on the uneven meshes of the heavy-occlusion
-    workload (2k-50k triangles), checked against the oracle on a sample."""
+    writes a pixel's depth, never the depth; the cost kernel's stage buffers
+    (one, or two so that the next tile is copied while the current one is
+    costed) change only when a tile arrives. The same records for every
+    setting the autotuner can pick, on the uneven meshes of the
+    heavy-occlusion workload (2k-50k triangles), checked against the oracle
+    on a sample."""
     wl = synth.workload_c3()
     p = perch.Perch(0)
     p.setup(wl)
@@ -508,16 +511,18 @@ def test_render_launch_parameters_do_not_change_records():
     ref = None
     try:
         p.perch_set_shortcut(False)
-        for threads, inl, bins in ((256, 16, 128), (128, 8, 32), (512, 32, 64), (256, 32, 32), (128, 16, 64)):
+        for threads, inl, bins, stages in ((256, 16, 128, 1), (128, 8, 32, 2), (512, 32, 64, 1), (256, 32, 32, 2),
+                                           (128, 16, 64, 2)):
             p.perch_set_threads(threads)
             p.perch_set_inline_pixels(inl)
             p.perch_set_bin_depth(bins)
+            p.perch_set_cost_stages(stages)
             assert p.perch_launch_config()[:2] == ([threads] * len(wl.meshes), [inl] * len(wl.meshes))
             assert p.perch_launch_bin_depths() == [bins] * len(wl.meshes)
             got = _recs(p.perch_eval_successors(parents, hp, hyps, wl.K))
             if ref is None:
                 ref = got
-            assert np.array_equal(got, ref), (threads, inl, bins)
+            assert np.array_equal(got, ref), (threads, inl, bins, stages)
     finally:
         p.close()
     pick = rng.choice(len(hyps), 60, replace=False)
