@@ -605,6 +605,7 @@ def run_c5(args):
             "time_to_optimum_p50_s": float(np.percentile(done, 50)) if done else None,
             "time_to_optimum_p99_s": float(np.percentile(done, 99)) if done else None,
             "successors": succ, "wall_s": wall, "host_peak_rss_gib": mem.peak / 2**30,
+            "search_seconds": dict(zip(("device_eval", "absorb_records", "select_states"), p.perch_search_times())),
             "pose_accuracy": accuracy.report(res, wls, wls[0].meshes),
             "hbm": hbm_fields(succ / wall, None), "paper_context": PAPER_CONTEXT, "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)

@@ -1191,9 +1191,12 @@ __device__ __forceinline__ void finish_phase(long long h, int pid, int plen, int
     return;
   }
 
-  // ---- dJ_r: dR points with no observed point within delta
+  // ---- dJ_r: dR points with no observed point within delta (with no
+  // observed point near the footprint, all |dR| of them, s_cnt[1])
   int djr = 0;
-  for (int ly = warp; !DJR_DONE && ly < th; ly += NW) {
+  const bool probe = !DJR_DONE && obs_near(cam, g, obs, o);
+  if (!DJR_DONE && !probe && tid == 0) djr = s_cnt[1];
+  for (int ly = warp; probe && ly < th; ly += NW) {
     const float ry = rys[ly];
     for (int lx = lane; lx < tw; lx += 32) {
       const uint32_t zb = tile.at(ly * tw + lx);
