@@ -182,6 +182,7 @@ int perch_ctx::ensure_tile_store() {
   CK(tile_off.ensure(4 * ((size_t)P + 1)), "alloc tile offsets");
   CK(pg_tmp.ensure(4 * ((size_t)P / 1024 + 2)), "alloc");
   CK(pose_flags.ensure((size_t)P), "alloc pose flags");
+  CK(tile_box.ensure(16 * (size_t)P), "alloc stored boxes");
   CK(pose_valid.ensure(4 * (size_t)P), "alloc render cache tags");
   CK(cudaMemsetAsync(pose_valid.p, 0, 4 * (size_t)P, stream), "memset");  // no tag is 0
   ++render_epoch;
@@ -849,7 +850,7 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
       bm.tile_h = mesh_tile_h[m];
       bm.queue_cap = mesh_queue[m];
       const RenderWork w{pg.gpose, rg + 4 * m + 2, rg + 4 * m + 3, g_next.as<int>() + m, tile_store.as<uint32_t>(),
-                         tile_off.as<int>(), pose_flags.as<uint8_t>(), valid, tag};
+                         tile_off.as<int>(), pose_flags.as<uint8_t>(), valid, tag, tile_box.as<int4>()};
       CK(launch_render_group(cam, g, obs, bm, w, std::min<long long>(n_hyp, per_mesh), mesh_threads[m],
                              mesh_inline[m], sm_count, stream),
          "render kernel");
@@ -860,7 +861,7 @@ int perch_ctx::enqueue_eval(const perch_obj* d_parents, int parent_stride, const
       bm.tile_w = mesh_tile_w[m];
       bm.tile_h = mesh_tile_h[m];
       const CostWork c{pg.order, rg + 4 * m, rg + 4 * m + 1, g_next.as<int>() + n_mesh + m, tile_store.as<uint32_t>(),
-                       tile_off.as<int>(), pose_flags.as<uint8_t>()};
+                       tile_off.as<int>(), pose_flags.as<uint8_t>(), tile_box.as<int4>()};
       CK(launch_cost_group(cam, g, obs, bm, c, n_hyp, mesh_cost_threads[m], mesh_cost_stages[m], sm_count, stream),
          "cost kernel");
     }

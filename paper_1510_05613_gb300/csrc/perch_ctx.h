@@ -98,7 +98,7 @@ struct perch_ctx {
   // for it, or with sharing off, every hypothesis is rendered by k_eval.
   bool share_renders = true;
   bool store_ok = false;
-  DevBuf tile_store, tile_off, tile_sizes, pose_flags;
+  DevBuf tile_store, tile_off, tile_sizes, pose_flags, tile_box;
   DevBuf pg_cnt, pg_start, pg_flag, pg_gix, pg_gpose, pg_tmp, pg_ranges;  // hypotheses grouped by pose
   std::vector<int> mesh_cost_threads;  // CTA width of k_cost per mesh (autotuned; 128 by default)
   std::vector<int> mesh_cost_stages;   // stage buffers of k_cost per mesh (1 or 2; autotuned; 1 by default)
@@ -161,7 +161,7 @@ struct perch_ctx {
             &b_out, &g_hist, &g_off, &g_cursor, &g_order, &g_next, &net_crops, &net_onehot, &net_pred,
             &solo, &solo_rec, &solo_hyp, &solo_hp, &solo_parent, &ptile_counts, &ptile_sat, &skip, &n_short,
             &tile_store, &tile_off, &tile_sizes, &pose_flags, &pg_cnt, &pg_start, &pg_flag, &pg_gix, &pg_gpose,
-            &pg_tmp, &pg_ranges, &pose_valid};
+            &pg_tmp, &pg_ranges, &pose_valid, &tile_box};
   }
 
   int fail(int code, const char* fmt, ...);

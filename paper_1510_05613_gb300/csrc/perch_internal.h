@@ -146,6 +146,7 @@ struct RenderWork {
   uint8_t* pose_flags;  // per pose: kPoseCulled, kPoseFailed
   uint32_t* valid;      // render cache (or nullptr): per pose, the tag of its stored render
   uint32_t tag;         // this batch's tag, written for every pose rendered in full
+  int4* tile_box;       // per pose: the stored box (x0, y0, width, height; the covered pixels' box)
 };
 
 // k_cost's work: hypotheses sorted by pose, one mesh's range per launch
@@ -157,6 +158,7 @@ struct CostWork {
   const uint32_t* store;
   const int* tile_off;
   const uint8_t* pose_flags;
+  const int4* tile_box;  // per pose: the stored box (k_render)
 };
 
 // Hypotheses grouped by pose; P = n_mesh x nx x ny x n_yaw. All device arrays.

@@ -907,7 +907,7 @@ __device__ __forceinline__ void render_start(const Geometry& g, const DevMesh& m
 template <int NT, int INL>
 __device__ __forceinline__ int render_chunks(const Camera& cam, const Geometry& g, const Batch& b, const DevMesh& m,
                                              const perch_obj& o, int4 bb, const RenderSmem& s, EvalShared& sh,
-                                             unsigned& culled) {
+                                             unsigned& culled, int4& cov) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint64_t* s_bar = sh.bar;
@@ -973,6 +973,10 @@ __device__ __forceinline__ int render_chunks(const Camera& cam, const Geometry& 
         const int py0 = max(ceil16(min(va.y, min(vb.y, vc.y))), 0);
         const int py1 = min(floor16(max(va.y, max(vb.y, vc.y))), th - 1);
         if (px0 > px1 || py0 > py1) continue;
+        cov.x = min(cov.x, px0);  // every pixel this triangle covers lies in its box
+        cov.y = max(cov.y, px1);
+        cov.z = min(cov.z, py0);
+        cov.w = max(cov.w, py1);
         if ((px1 - px0 + 1) * (py1 - py0 + 1) > INL && px1 - px0 < 64 && py1 - py0 < 64) {
           const int slot = atomicAdd(&s_qn, 1);
           if (slot < qcap) {  // (triangle, box): x0 10 bits, y0 10 bits, w-1 and h-1 6 bits each
@@ -1336,7 +1340,8 @@ __device__ int eval_one(long long h, const Camera& cam, const Geometry& g, const
   if (tid < 7) s_cnt[tid] = 0;
 
   unsigned culled = 0;
-  const int st = render_chunks<NT, kInlinePixels>(cam, g, b, m, a.o, bb, s, sh, culled);
+  int4 cov = make_int4(0x7fffffff, -1, 0x7fffffff, -1);  // not needed here
+  const int st = render_chunks<NT, kInlinePixels>(cam, g, b, m, a.o, bb, s, sh, culled, cov);
   if (st != kEvalDone) {
     if (tid == 0) {
       perch_cost r = {0, 0, 0, 0, 0, kFlagTimeout, 0};
@@ -1402,6 +1407,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_render(Camera cam, Geometry g
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ int s_qn;
   __shared__ int s_item;
+  __shared__ int s_box[4];  // the covered pixels' box within the pose's box: x0, x1, y0, y1
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
@@ -1436,37 +1442,55 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_render(Camera cam, Geometry g
     if (tid == 0) render_start(g, m, o.iyaw, s, sh.bar);
     for (int ly = warp; ly < th; ly += NW)
       for (int lx = lane; lx < tw; lx += 32) s.tile[ly * tw + lx] = 0u;  // 1/z = 0: empty
+    if (tid < 4) s_box[tid] = (tid & 1) ? -1 : 0x7fffffff;  // ordered by render_chunks' first barrier
     unsigned culled = 0;
-    const int st = render_chunks<NT, INL>(cam, g, b, m, o, bb, s, sh, culled);
+    int4 cov = make_int4(0x7fffffff, -1, 0x7fffffff, -1);  // x0, x1, y0, y1 of this thread's triangle boxes
+    const int st = render_chunks<NT, INL>(cam, g, b, m, o, bb, s, sh, culled, cov);
     if (st != kEvalDone) {
       if (tid == 0) w.pose_flags[p] = kPoseFailed;
       __syncthreads();  // the tile is cleared by the next pose
       if (st == kEvalStop) break;
       continue;
     }
-    const int any_culled = __syncthreads_or(culled != 0);
-    // the store gets z = 1/(1/z) (+inf where empty) and, for a single-scene
-    // batch (EXPL), the Eq. (1) test of each rendered point against I in the
-    // sign bit: it depends on the pose and the scene, not on the parent. A
-    // pose with no observed point near its footprint explains no point.
+    {  // the union of the front faces' candidate boxes holds every covered pixel:
+       // the store (and every cost of this pose) keeps only that box
+      const int x0 = __reduce_min_sync(0xffffffffu, cov.x), x1 = __reduce_max_sync(0xffffffffu, cov.y);
+      const int y0 = __reduce_min_sync(0xffffffffu, cov.z), y1 = __reduce_max_sync(0xffffffffu, cov.w);
+      if (lane == 0 && x1 >= 0) {
+        atomicMin(&s_box[0], x0);
+        atomicMax(&s_box[1], x1);
+        atomicMin(&s_box[2], y0);
+        atomicMax(&s_box[3], y1);
+      }
+    }
+    const int any_culled = __syncthreads_or(culled != 0);  // also publishes s_box
+    const bool empty = s_box[1] < 0;
+    const int cx0 = empty ? 0 : s_box[0], cy0 = empty ? 0 : s_box[2];
+    const int cw = empty ? 0 : s_box[1] - s_box[0] + 1, ch = empty ? 0 : s_box[3] - s_box[2] + 1;
+    // the store gets z = 1/(1/z) (+inf where empty) over that box, rows of
+    // its width, and, for a single-scene batch (EXPL), the Eq. (1) test of
+    // each rendered point against I in the sign bit: it depends on the pose
+    // and the scene, not on the parent. A pose with no observed point near
+    // its footprint explains no point.
     const bool probe = EXPL && obs_near(cam, g, obs, o);
     uint32_t* dst = w.store + 4 * (size_t)w.tile_off[p];
-    for (int ly = warp; ly < th; ly += NW) {
-      const float ry = EXPL ? g.ry[bb.y + ly] : 0.0f;
-      for (int lx = lane; lx < tw; lx += 32) {
-        const uint32_t izb = s.tile[ly * tw + lx];
+    for (int ly = warp; ly < ch; ly += NW) {
+      const float ry = EXPL ? g.ry[bb.y + cy0 + ly] : 0.0f;
+      for (int lx = lane; lx < cw; lx += 32) {
+        const uint32_t izb = s.tile[(cy0 + ly) * tw + cx0 + lx];
         uint32_t v = kInfBits;
         if (izb != 0u) {
           const float z = __frcp_rn(__uint_as_float(izb));
           v = __float_as_uint(z);
-          if (probe && explained_by_obs(obs, fmul(g.rx[bb.x + lx], z), fmul(ry, z), z, cam.delta2))
+          if (probe && explained_by_obs(obs, fmul(g.rx[bb.x + cx0 + lx], z), fmul(ry, z), z, cam.delta2))
             v |= kExplainedBit;
         }
-        dst[ly * tw + lx] = v;
+        dst[ly * cw + lx] = v;
       }
     }
     if (tid == 0) {
       w.pose_flags[p] = any_culled ? kPoseCulled : 0;
+      w.tile_box[p] = make_int4(bb.x + cx0, bb.y + cy0, cw, ch);
       if (w.valid) w.valid[p] = w.tag;  // read by later launches only
     }
     __syncthreads();  // the tile is cleared by the next pose
@@ -1535,12 +1559,14 @@ __global__ void __launch_bounds__(NT) k_cost(Camera cam, Geometry g, ObsIndex ob
     int state = kItemBad, pf = 0, off = 0, sidx = cur;
     int4 bb = make_int4(0, 0, 0, 0);
     if (hyp_args(g, b, h, a)) {
-      bb = g.pose_bbox[a.pose];
+      bb = w.tile_box[a.pose];  // the covered pixels' box (k_render)
       pf = w.pose_flags[a.pose];
       if (pf & kPoseFailed) {
         state = kItemFailed;
       } else if (bb.z <= b.tile_w && bb.w <= b.tile_h) {
-        if (a.pose == stage_pose[cur]) {
+        if (bb.z == 0 || bb.w == 0) {
+          state = kItemReuse;  // nothing rendered: no pixel to copy or compare
+        } else if (a.pose == stage_pose[cur]) {
           state = kItemReuse;
         } else if (NS == 2 && a.pose == stage_pose[NS - 1 - cur]) {
           state = kItemReuse;
