@@ -440,8 +440,9 @@ def run_ours(args):
         from paper_1510_05613_gb300 import accuracy
         gt_key = tuple(sorted((int(o["mesh"]), int(o["ix"]), int(o["iy"]), int(o["iyaw"])) for o in wl.gt))
 
-        def one_search():
-            r = p.perch_search(wl.mesh_multiset, batch_states=args.batch_states, time_limit_s=args.search_limit)
+        def one_search(heur=0):
+            r = p.perch_search(wl.mesh_multiset, batch_states=args.batch_states, time_limit_s=args.search_limit,
+                               heuristics=heur)
             return {"seconds": r["seconds"], "proven_optimal": r["proven_optimal"], "cost": r["cost"],
                     "expansions": r["expansions"], "successors": r["successors"],
                     "found_ground_truth": r["key"] == gt_key, "batch_states": args.batch_states,
@@ -459,6 +460,8 @@ def run_ours(args):
         p.perch_set_symmetry(wl.meshes)
         search["render_cache_symmetric"] = one_search()
         p.perch_set_symmetry(None)
+        # and with a greedy incumbent first (heuristics bit 4: the same optimum)
+        search["render_cache_incumbent"] = one_search(16)
         p.perch_set_render_cache(False)
 
     base = None
@@ -905,7 +908,8 @@ def main():
                     help="launch the evaluation directly instead of replaying its CUDA graph (same kernels)")
     ap.add_argument("--scenes", type=int, default=64, help="c5: number of scenes")
     ap.add_argument("--w", type=float, default=3.0, help="c5: suboptimality bound of Focal-MHA*")
-    ap.add_argument("--heuristics", type=int, default=3, help="c5: bit 0 h_depth, bit 1 h_overlap")
+    ap.add_argument("--heuristics", type=int, default=3,
+                    help="c5: bit 0 h_depth, bit 1 h_overlap, bit 4 a greedy incumbent first")
     ap.add_argument("--launch-hyps", type=int, default=1 << 22, help="c5: hypotheses per shared launch")
     ap.add_argument("--train-scenes", type=int, default=256, help="c4: training scenes")
     ap.add_argument("--per-parent", type=int, default=1536, help="c4: labelled hypotheses per training parent")

@@ -274,7 +274,14 @@ int perch_render(perch_ctx* ctx, const perch_obj* objs, int32_t n, float* depth_
  * the pool expanded in order of g + h_cnn. Bit 3: the queue is ordered
  * deepest first, then by g + h_free, and the pool re-ranked by g + h_cnn
  * within each depth), and the search returns a scene of cost <= w * OPT
- * (Theorem 2). mesh_multiset[K]: the types of the K objects (Sec. III: known
+ * (Theorem 2). Bit 4 (with any of the above or none; not in the paper): an
+ * incumbent first. A greedy completion from the root expands, one state per
+ * round, the cheapest valid child of the state it expanded last, down to a
+ * goal; that goal is the first best goal, so every later successor dearer
+ * than it is dropped as its record arrives instead of entering the open
+ * set. With w = 1 the returned scene is the same as without bit 4 (the
+ * optimum, ties broken by the smallest sorted key); with w > 1 it stays
+ * within w * OPT. The open set, host memory and time shrink. mesh_multiset[K]: the types of the K objects (Sec. III: known
  * number and types). batch_states: states taken from each queue per device
  * launch (>= 1). Stops at the optimum / the bound, or at time_limit_s /
  * max_expansions (0 = none) and then returns PERCH_E_TIMEOUT with the best

@@ -33,6 +33,16 @@
 //   bit 3: the queue is ordered deepest first, then by g + h_free, and the
 //          pool is re-ranked by g + h_cnn only within a depth (a depth-first
 //          dive that the network steers among siblings).
+//
+// Incumbent (heuristics bit 4, with any of the above or none): before the
+// search proper, a greedy completion from the root expands, at each depth,
+// the cheapest valid child of the state it expanded last (ties: the smallest
+// key), K expansions in all, one per round. Its goal is the first best goal:
+// from then on every successor dearer than it is dropped when its record is
+// absorbed, instead of entering the open set. Every state the greedy
+// completion expands is a state of the tree, expanded at its current g (a
+// cheaper way in later reopens it), so the search returns what it returns
+// without it; only the open set it has to hold shrinks.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -186,7 +196,12 @@ struct SceneSearch {
   double now = 0.0;                    // seconds since the start, when the current records arrived
   double found_seconds = 0.0;          // when best_key was last set
   int64_t found_expansions = 0;
-  bool focal() const { return w > 1.0 || heur != 0; }
+  // greedy completion (heuristics bit 4): the state it expands next, the
+  // state it expands this round, and that state's cheapest child so far
+  bool diving = false;
+  int dive_next = -1, dive_from = -1, dive_pick = -1;
+  int64_t dive_pick_g = kInf;
+  bool focal() const { return w > 1.0 || (heur & 15) != 0; }
   bool learned() const { return (heur & 12) != 0; }
   bool dive() const { return (heur & 8) != 0; }  // the depth-first learned queue
   int64_t hval(int which, int idx) const {
@@ -252,6 +267,21 @@ struct SceneSearch {
     states.push_back(root);
     index.init(1 << 16);  // the root is never looked up (no child has depth 0)
     add_open(0, 0);
+    diving = (heur & 16) != 0 && K > 1;
+    dive_next = diving ? 0 : -1;
+  }
+  // greedy completion: after a round's records, continue from the cheapest
+  // child of the state it expanded, or stop (a goal was reached, or no child
+  // was valid)
+  void end_round() {
+    if (dive_from < 0) return;
+    if (dive_pick >= 0 && best_g == kInf && (int)states[dive_pick].depth < K) {
+      dive_next = dive_pick;
+    } else {
+      diving = false;
+    }
+    dive_from = dive_pick = -1;
+    dive_pick_g = kInf;
   }
   // Focal-MHA* round: up to B states from the anchor and from each queue
   void pop_focal(int B, std::vector<int>& out) {
@@ -386,6 +416,13 @@ struct SceneSearch {
   // pop up to B expandable states; marks the search done when none is left
   void pop(int B, std::vector<int>& out) {
     out.clear();
+    if (diving && dive_next >= 0) {  // greedy completion: its one state this round
+      dive_from = dive_next;
+      dive_next = -1;
+      states[dive_from].closed = true;
+      out.push_back(dive_from);
+      return;
+    }
     if (focal()) {
       pop_focal(B, out);
       return;
@@ -423,6 +460,15 @@ struct SceneSearch {
     const size_t t = std::lower_bound(er.types.begin(), er.types.end(), (int)o.mesh) - er.types.begin();
     s.h_free = er.total - ((t < er.types.size() && er.best[t] != kInf) ? er.best[t] : (int64_t)1 << 40);
     s.h_cnn = -1.0;  // candidates changed: score again
+  }
+  // greedy completion: child idx of the state it expands; keep the cheapest
+  // (ties: the smallest key)
+  void dive_offer(int idx) {
+    const int64_t g = states[idx].g;
+    if (dive_pick < 0 || g < dive_pick_g || (g == dive_pick_g && key_of(idx) < key_of(dive_pick))) {
+      dive_pick = idx;
+      dive_pick_g = g;
+    }
   }
   void absorb(int pidx, const perch_obj& h, const perch_cost& r) {
     if (r.flags & kNoCost) {  // no cost was computed: the search cannot go on
@@ -469,6 +515,7 @@ struct SceneSearch {
       index.insert(h0, idx);
       if (learned()) set_parent(idx, pidx, h);
       add_open(ng, idx);
+      if (pidx == dive_from) dive_offer(idx);
     } else {
       State& s = states[found];
       if (ng < s.g) {
@@ -477,6 +524,7 @@ struct SceneSearch {
         if (learned() && s.parent != pidx) set_parent(found, pidx, h);
         add_open(ng, found);
       }
+      if (pidx == dive_from) dive_offer(found);
     }
   }
 };
@@ -715,6 +763,7 @@ int run_searches(perch_ctx* ctx, std::vector<SceneSearch>& ss, int batch_states,
             s.successors++;
             s.absorb(work[w].state, hyps[h], out[h]);
           }
+        s.end_round();
       } catch (...) {
         failed = true;
       }
@@ -750,7 +799,7 @@ int check_params(perch_ctx* ctx, const perch_search_params* prm) {
   if (!prm || prm->K < 1 || prm->K > 16 || !prm->mesh_multiset || prm->batch_states < 1)
     return ctx->fail(PERCH_E_ARG, "search: bad parameters");
   if (!(prm->w >= 1.0f)) return ctx->fail(PERCH_E_ARG, "search: w must be >= 1");
-  if (prm->heuristics & ~15) return ctx->fail(PERCH_E_ARG, "search: unknown heuristic bits %d", prm->heuristics);
+  if (prm->heuristics & ~31) return ctx->fail(PERCH_E_ARG, "search: unknown heuristic bits %d", prm->heuristics);
   if ((prm->heuristics & 12) == 12) return ctx->fail(PERCH_E_ARG, "search: heuristic bits 2 and 3 exclude each other");
   if ((prm->heuristics & 12) && !ctx->net)
     return ctx->fail(PERCH_E_STATE, "search: heuristic bits 2 and 3 need perch_set_heuristic_net");

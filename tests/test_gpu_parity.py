@@ -416,6 +416,9 @@ def test_argument_errors(c1):
     with pytest.raises(perch.PerchError):  # parent as long as the full scene
         p.perch_eval_successors([wl.gt], np.zeros(4, np.int32), hyps, 2)
     assert len(p.perch_eval_successors([wl.gt[:0]], np.zeros(0, np.int32), hyps[:0], 2)) == 0
+    with pytest.raises(perch.PerchError) as e:  # no heuristic bit 5
+        p.perch_search(wl.mesh_multiset, heuristics=32)
+    assert e.value.code == perch.PERCH_E_ARG
 
 
 def test_wait_limit_failure_path_reports_and_recovers(c1):
@@ -469,8 +472,9 @@ def test_search_matches_oracle_exhaustive_small_c1():
     w = oracle.World.of(wl)
     ex_cost, ex_key = search.exhaustive(w, wl.depth, wl.grid, wl.mesh_multiset)
     for B in (1, 3, 64):
-        r = p.perch_search(wl.mesh_multiset, batch_states=B)
-        assert r["proven_optimal"] and (r["cost"], r["key"]) == (ex_cost, ex_key)
+        for heur in (0, 16):  # 16: a greedy incumbent first; the same optimum
+            r = p.perch_search(wl.mesh_multiset, batch_states=B, heuristics=heur)
+            assert r["proven_optimal"] and (r["cost"], r["key"]) == (ex_cost, ex_key), (B, heur)
     p.close()
 
 
@@ -479,6 +483,9 @@ def test_search_matches_oracle_ucs_full_c1(c1):
     cost, key, _ = search.uniform_cost_search(w, wl.depth, wl.grid, wl.mesh_multiset)
     r = p.perch_search(wl.mesh_multiset, batch_states=16)
     assert r["proven_optimal"] and (r["cost"], r["key"]) == (cost, key)
+    # with the greedy incumbent first: the same optimum, and no more successors kept
+    ri = p.perch_search(wl.mesh_multiset, batch_states=16, heuristics=16)
+    assert ri["proven_optimal"] and (ri["cost"], ri["key"]) == (cost, key)
 
 
 def test_render_launch_parameters_do_not_change_records():
@@ -659,14 +666,17 @@ def test_multi_scene_search_matches_oracle():
         p.perch_set_scene(s, wl.depth)
     res = p.perch_search_multi(list(range(len(wls))), [wl.mesh_multiset for wl in wls], batch_states=2,
                                max_hyps_per_launch=300)
-    for wl, r in zip(wls, res):
+    inc = p.perch_search_multi(list(range(len(wls))), [wl.mesh_multiset for wl in wls], batch_states=2,
+                               max_hyps_per_launch=300, heuristics=16)
+    for wl, r, ri in zip(wls, res, inc):
         w = oracle.World.of(wl)
         cost, key = search.exhaustive(w, wl.depth, wl.grid, wl.mesh_multiset)
         assert r["proven_optimal"] and (r["cost"], r["key"]) == (cost, key)
+        assert ri["proven_optimal"] and (ri["cost"], ri["key"]) == (cost, key)
     p.close()
 
 
-@pytest.mark.parametrize("w,heur", [(1.0, 3), (1.5, 3), (3.0, 3), (3.0, 1), (3.0, 2)])
+@pytest.mark.parametrize("w,heur", [(1.0, 3), (1.5, 3), (3.0, 3), (3.0, 1), (3.0, 2), (3.0, 19), (1.0, 16)])
 def test_focal_mha_search_bound(w, heur):
     """Library Focal-MHA* on the reduced 2-object grid: cost within w times
     the exhaustive optimum (Theorem 2); with w = 1 exactly optimal."""

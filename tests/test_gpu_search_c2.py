@@ -45,11 +45,11 @@ def test_gpu_search_equals_oracle_search_c2_reduced(scene):
     p = perch.Perch(0)
     p.setup(wl)
     try:
-        for B, short in ((1, True), (8, True), (64, False)):
+        for B, short, heur in ((1, True, 0), (8, True, 0), (64, False, 0), (8, True, 16)):
             p.perch_set_shortcut(short)
-            r = p.perch_search(wl.mesh_multiset, batch_states=B)
+            r = p.perch_search(wl.mesh_multiset, batch_states=B, heuristics=heur)
             assert r["proven_optimal"]
-            assert (r["cost"], r["key"]) == (exp["cost"], key), (B, short, r["cost"], r["key"])
+            assert (r["cost"], r["key"]) == (exp["cost"], key), (B, short, heur, r["cost"], r["key"])
         p.perch_set_shortcut(True)
         for w in (1.5, 3.0):
             r = p.perch_search(wl.mesh_multiset, w=w, batch_states=8, heuristics=3)
@@ -92,11 +92,11 @@ def test_gpu_search_equals_oracle_search_c3_reduced(scene):
     p = perch.Perch(0)
     p.setup(wl)
     try:
-        for B, short, cache in ((1, True, False), (8, False, False), (8, True, True)):
+        for B, short, cache, heur in ((1, True, False, 0), (8, False, False, 0), (8, True, True, 0), (8, True, True, 16)):
             p.perch_set_shortcut(short)
             p.perch_set_render_cache(cache)
-            r = p.perch_search(wl.mesh_multiset, batch_states=B)
+            r = p.perch_search(wl.mesh_multiset, batch_states=B, heuristics=heur)
             assert r["proven_optimal"]
-            assert (r["cost"], r["key"]) == (exp["cost"], key), (B, short, cache, r["cost"], r["key"])
+            assert (r["cost"], r["key"]) == (exp["cost"], key), (B, short, cache, heur, r["cost"], r["key"])
     finally:
         p.close()
