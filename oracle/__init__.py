@@ -18,6 +18,12 @@ point-in-triangle coverage with exact rationals, exact-delta ties of Eq. (1),
 the K = 1 identity between the decomposed and undecomposed cost, the
 zero-cost ground-truth path on a noise-free observation, empty-observation and
 infinite-delta special cases, and search == exhaustive enumeration.
+The ICP refinement of Sec. IV-E-1 (tests/test_oracle_icp.py): the planar
+fit against known motions and an SVD fit, the correspondence rule against
+brute-force and k-d tree nearest neighbours, the model set against the edge
+cost's |dR|, the exact identity on an observation that is the object's own
+render, and off-grid objects of the ray-cast sensor brought to their true
+pose.
 """
 from __future__ import annotations
 
@@ -33,6 +39,11 @@ _LIB = os.path.join(_HERE, "libperch_oracle.so")
 
 REC_FIELDS = ("djr", "djo", "resid", "viol", "n_new", "flags", "n_vol")
 FLAG_CULLED, FLAG_INVALID = 1, 2
+# ICP record (Sec. IV-E-1): the planar motion (c, s, tx, ty), |M|, the last
+# matching's pairs, the fits made, and how the iteration stopped
+ICP_DTYPE = np.dtype([("c", "<f8"), ("s", "<f8"), ("tx", "<f8"), ("ty", "<f8"), ("n_model", "<i4"),
+                      ("n_corr", "<i4"), ("iters", "<i4"), ("status", "<i4")])
+ICP_CONVERGED, ICP_CAP, ICP_FEW, ICP_DEGENERATE = 0, 1, 2, 3
 
 
 def build() -> str:
@@ -90,6 +101,12 @@ def _load():
         lib.or_max_threads.restype = I32
         lib.or_in_volume.restype = I32
         lib.or_in_volume.argtypes = [P, _ObjArg, P, I64, P]
+        lib.or_icp_refine.restype = I32
+        lib.or_icp_refine.argtypes = [P, P, P, P, I32, I32, P, P, I64, ctypes.c_float, I32, P, I32]
+        lib.or_icp_fit.restype = I32
+        lib.or_icp_fit.argtypes = [P, P, I64, P]
+        lib.or_icp_match.restype = I32
+        lib.or_icp_match.argtypes = [P, P, P, I64, ctypes.c_float, P]
         _lib = lib
     return _lib
 
@@ -222,3 +239,63 @@ def in_volume(world: World, obj, pts):
 
 def max_threads() -> int:
     return int(_load().or_max_threads())
+
+
+def _parent_table(parents):
+    from paper_1510_05613_gb300.synth import OBJ_DTYPE
+    k_max = max([1] + [len(p) for p in parents])
+    P = np.zeros((max(1, len(parents)), k_max), OBJ_DTYPE)
+    plen = np.zeros(max(1, len(parents)), np.int32)
+    for i, p in enumerate(parents):
+        P[i, :len(p)] = p
+        plen[i] = len(p)
+    return P, plen, k_max
+
+
+def icp_refine(world: World, depth, parents, hyp_parent, hyps, radius: float = 0.02, max_iter: int = 20,
+               threads: int = 0):
+    """ICP refinement of each successor's new object (Sec. IV-E-1): one
+    ICP_DTYPE record per hypothesis. ``parents`` as in eval_batch."""
+    P, plen, k_max = _parent_table(parents)
+    hp = _c(hyp_parent, np.int32)
+    h = _objs(hyps)
+    d = _c(depth, np.float32)
+    out = np.zeros(len(h), ICP_DTYPE)
+    rc = _load().or_icp_refine(world.ptr(), d.ctypes.data, P.ctypes.data, plen.ctypes.data, len(parents), k_max,
+                               hp.ctypes.data, h.ctypes.data, len(h), float(radius), int(max_iter),
+                               out.ctypes.data, threads)
+    if rc:
+        raise MemoryError("oracle icp_refine")
+    return out
+
+
+def icp_fit(m, q):
+    """The closed-form planar fit on explicit pairs (world points (n, 3)):
+    ((c, s, tx, ty), status) with status 0 = fitted, 1 = no turn defined,
+    2 = fewer than 3 pairs."""
+    m, q = _c(m, np.float32).reshape(-1, 3), _c(q, np.float32).reshape(-1, 3)
+    out = np.zeros(4, np.float64)
+    st = _load().or_icp_fit(m.ctypes.data, q.ctypes.data, m.shape[0], out.ctypes.data)
+    return tuple(float(v) for v in out), int(st)
+
+
+def icp_match(world: World, depth, pts, radius: float):
+    """Index in I (pixel order) of each world point's correspondence, -1 if
+    none is within ``radius``."""
+    p = _c(pts, np.float32).reshape(-1, 3)
+    d = _c(depth, np.float32)
+    idx = np.empty(p.shape[0], np.int64)
+    if _load().or_icp_match(world.ptr(), d.ctypes.data, p.ctypes.data, p.shape[0], float(radius), idx.ctypes.data):
+        raise MemoryError("oracle icp_match")
+    return idx
+
+
+def icp_pose(grid, obj, rec):
+    """Refined (x, y, yaw) of a grid object moved by an ICP record's motion:
+    (x, y) turned and shifted, the yaw turned by atan2(s, c) (double)."""
+    import math
+    x, y = float(grid.xs[int(obj["ix"])]), float(grid.ys[int(obj["iy"])])
+    c0, s0 = (float(v) for v in grid.cos_sin[int(obj["iyaw"])])
+    c, s = float(rec["c"]), float(rec["s"])
+    return (c * x - s * y + float(rec["tx"]), s * x + c * y + float(rec["ty"]),
+            math.atan2(s0, c0) + math.atan2(s, c))

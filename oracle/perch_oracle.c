@@ -26,7 +26,9 @@
  *       resid= #{q in I - V_K unexplained by R_K}   (only when i = K)
  *   - monotone constraint R_{i-1} subset R_i of Eq. (3): the child is invalid
  *     when any of its pixels lies strictly in front of the parent's render;
- *   - undecomposed J = J_o + J_r of Sec. III-B (used to pin the K = 1 case).
+ *   - undecomposed J = J_o + J_r of Sec. III-B (used to pin the K = 1 case);
+ *   - ICP refinement of a successor's new object (Sec. IV-E-1, Sec. V-B),
+ *     each step fixed below (the section headed ICP).
  *
  * Readings where the paper is silent (it only says "render"):
  *   - pinhole with pixel centres at integer (u, v); depth = camera-frame Z;
@@ -404,6 +406,171 @@ static void edge_cost(const or_world* w, const or_cam* c, const or_cloud* I,
   }
 }
 
+/* ------------------------------------------------------------------ ICP */
+/* Local alignment of a successor's new object with the observed cloud
+ * (Sec. IV-E-1, compensating for discretization: each time a state is
+ * rendered with a new object, the object's non-occluded portion is aligned
+ * with I by ICP in the local vicinity; Sec. V-B: correspondences are sought
+ * only within 2 cm, half the grid step). The paper names ICP without fixing
+ * its variant; this restatement fixes every step, so the result is a
+ * function of the inputs alone:
+ *   model set M: the pixels where the object's own render z_O is finite and
+ *     lies strictly in front of the parent's render z_P (+inf where empty),
+ *     back-projected to the world frame exactly as the observed cloud is;
+ *   motion T = (c, s, t_x, t_y): a turn about the world's vertical axis and
+ *     a translation in the table plane (the pose's three degrees of
+ *     freedom), applied in binary32 from T's values rounded to binary32:
+ *     x' = (c x - s y) + t_x, y' = (s x + c y) + t_y, z' = z;
+ *   correspondence of m in M: the point q of I of smallest
+ *     d^2 = fma(dz, dz, fma(dy, dy, dx dx)) (d = T m - q) among those with
+ *     d^2 <= (float)(r^2); ties go to the smaller index of q in I (pixel
+ *     order); none: m is unmatched;
+ *   sums over the matched pairs, in fixed point (coordinates times 2^16,
+ *     rounded to the nearest integer, ties to even) so that they are exact
+ *     and independent of the order of summation: n, sum X_m, sum Y_m,
+ *     sum X_q, sum Y_q, sum X_m X_q, sum Y_m Y_q, sum X_m Y_q, sum Y_m X_q
+ *     (a pair with |x| or |y| >= 32 m for m or q is left out);
+ *   fit: the motion minimising sum |T m - q|^2 over the pairs' (x, y), in
+ *     closed form (icp_solve);
+ *   iteration k = 1 .. max_iter, from T = identity: match under the current
+ *     T; fewer than 3 pairs: stop (FEW); the same sums as the previous
+ *     iteration: stop (CONVERGED, the fit would repeat itself); no rotation
+ *     defined: stop (DEGENERATE); else T = fit of the pairs. After max_iter
+ *     fits: CAP. */
+typedef struct { double c, s, tx, ty; int32_t n_model, n_corr, iters, status; } or_icp_rec;
+enum { OR_ICP_CONVERGED = 0, OR_ICP_CAP = 1, OR_ICP_FEW = 2, OR_ICP_DEGENERATE = 3 };
+
+typedef struct { int64_t n, sx, sy, qx, qy, xx, yy, xy, yx; } or_icp_sums;
+
+static int64_t icp_fixed(float v) { return (int64_t)llrintf(v * 65536.0f); }
+
+/* a 128-bit integer as hi 2^64 + lo, each part rounded to double, then one
+ * rounded addition */
+static double i128_to_double(__int128 v) {
+  int64_t hi = (int64_t)(v >> 64);
+  uint64_t lo = (uint64_t)v;
+  return (double)hi * 18446744073709551616.0 + (double)lo;
+}
+
+static void icp_add_pair(or_icp_sums* S, or_pt m, or_pt q) {
+  if (!(fabsf(m.x) < 32.0f && fabsf(m.y) < 32.0f && fabsf(q.x) < 32.0f && fabsf(q.y) < 32.0f)) return;
+  int64_t X = icp_fixed(m.x), Y = icp_fixed(m.y), QX = icp_fixed(q.x), QY = icp_fixed(q.y);
+  S->n += 1;
+  S->sx += X; S->sy += Y; S->qx += QX; S->qy += QY;
+  S->xx += X * QX; S->yy += Y * QY; S->xy += X * QY; S->yx += Y * QX;
+}
+
+/* Planar Procrustes: with centred sums C = n sum(m . q) - sum m . sum q and
+ * S = n sum(m x q) - sum m x sum q (exact integers), the best turn has
+ * (cos, sin) = (C, S) / |(C, S)| and the best translation moves the turned
+ * centroid of M onto that of Q: t = (sum q - R sum m) / n. Returns 1 when
+ * C = S = 0 (no turn is better than another). */
+static int icp_solve(const or_icp_sums* S, double* c, double* s, double* tx, double* ty) {
+  const __int128 n = S->n;
+  const __int128 C = n * ((__int128)S->xx + S->yy) - ((__int128)S->sx * S->qx + (__int128)S->sy * S->qy);
+  const __int128 X = n * ((__int128)S->xy - S->yx) - ((__int128)S->sx * S->qy - (__int128)S->sy * S->qx);
+  if (C == 0 && X == 0) return 1;
+  const double Cd = i128_to_double(C), Xd = i128_to_double(X);
+  const double h = sqrt(Cd * Cd + Xd * Xd);
+  const double cc = Cd / h, ss = Xd / h;
+  const double nd = (double)S->n, sx = (double)S->sx, sy = (double)S->sy;
+  *c = cc;
+  *s = ss;
+  *tx = (((double)S->qx - (cc * sx - ss * sy)) / nd) * (1.0 / 65536.0);
+  *ty = (((double)S->qy - (ss * sx + cc * sy)) / nd) * (1.0 / 65536.0);
+  return 0;
+}
+
+/* observed world points ordered by x (then by index): a candidate whose x
+ * differs from the query's by more than 1.001 r cannot be within r (its
+ * rounded dx^2 alone already exceeds the rounded r^2), so the scan of the
+ * ordered list stops there; every other point is tested in full */
+static const or_pt* g_sort_pts;
+static int cmp_by_x(const void* a, const void* b) {
+  int64_t i = *(const int64_t*)a, j = *(const int64_t*)b;
+  float xi = g_sort_pts[i].x, xj = g_sort_pts[j].x;
+  if (xi < xj) return -1;
+  if (xi > xj) return 1;
+  return (i > j) - (i < j);
+}
+
+static int64_t* order_by_x(const or_cloud* I) {
+  int64_t* o = (int64_t*)malloc(sizeof(int64_t) * (size_t)(I->n > 0 ? I->n : 1));
+  if (!o) return NULL;
+  for (int64_t k = 0; k < I->n; ++k) o[k] = k;
+  g_sort_pts = I->world;
+  qsort(o, (size_t)I->n, sizeof(int64_t), cmp_by_x);
+  return o;
+}
+
+/* the correspondence of world point p (index into I, or -1) */
+static int64_t icp_match(const or_cloud* I, const int64_t* by_x, or_pt p, double r, float r2) {
+  const double lo = (double)p.x - 1.001 * r, hi = (double)p.x + 1.001 * r;
+  int64_t a = 0, b = I->n;
+  while (a < b) {  /* first point with x >= lo */
+    int64_t mid = a + (b - a) / 2;
+    if ((double)I->world[by_x[mid]].x < lo) a = mid + 1; else b = mid;
+  }
+  int64_t best = -1;
+  float bd = 0.0f;
+  for (int64_t k = a; k < I->n && (double)I->world[by_x[k]].x <= hi; ++k) {
+    const int64_t j = by_x[k];
+    const float d = dist2(p, I->world[j]);
+    if (!(d <= r2)) continue;
+    if (best < 0 || d < bd || (d == bd && j < best)) { best = j; bd = d; }
+  }
+  return best;
+}
+
+static or_pt icp_apply(float c, float s, float tx, float ty, or_pt m) {
+  or_pt p = {(c * m.x - s * m.y) + tx, (s * m.x + c * m.y) + ty, m.z};
+  return p;
+}
+
+/* ICP of one model set against I (the iteration stated above) */
+static void icp_run(const or_cloud* I, const int64_t* by_x, const or_pt* M, int64_t nm, double r,
+                    int32_t max_iter, or_icp_rec* out) {
+  const float r2 = (float)(r * r);
+  double c = 1.0, s = 0.0, tx = 0.0, ty = 0.0;
+  or_icp_sums prev;
+  int have_prev = 0;
+  out->status = OR_ICP_CAP;
+  out->iters = 0;
+  out->n_corr = 0;
+  out->n_model = (int32_t)nm;
+  for (int32_t k = 1; k <= max_iter; ++k) {
+    const float cf = (float)c, sf = (float)s, txf = (float)tx, tyf = (float)ty;
+    or_icp_sums S;
+    memset(&S, 0, sizeof S);
+    for (int64_t i = 0; i < nm; ++i) {
+      const int64_t j = icp_match(I, by_x, icp_apply(cf, sf, txf, tyf, M[i]), r, r2);
+      if (j >= 0) icp_add_pair(&S, M[i], I->world[j]);
+    }
+    out->n_corr = (int32_t)S.n;
+    if (S.n < 3) { out->status = OR_ICP_FEW; break; }
+    if (have_prev && memcmp(&S, &prev, sizeof S) == 0) { out->status = OR_ICP_CONVERGED; break; }
+    double c1, s1, tx1, ty1;
+    if (icp_solve(&S, &c1, &s1, &tx1, &ty1)) { out->status = OR_ICP_DEGENERATE; break; }
+    c = c1; s = s1; tx = tx1; ty = ty1;
+    prev = S;
+    have_prev = 1;
+    out->iters = k;
+  }
+  out->c = c; out->s = s; out->tx = tx; out->ty = ty;
+}
+
+/* model set of one successor: the new object's pixels in front of the
+ * parent's render, in the world frame */
+static int64_t icp_model(const or_world* w, const or_cam* c, const float* zo, const float* zp, or_pt* M) {
+  int64_t n = 0;
+  for (int v = 0; v < w->H; ++v)
+    for (int u = 0; u < w->W; ++u) {
+      const int64_t i = (int64_t)v * w->W + u;
+      if (isfinite(zo[i]) && zo[i] < zp[i]) M[n++] = cam_to_world(c, pixel_point(c, u, v, zo[i]));
+    }
+  return n;
+}
+
 /* ================================================================ exports */
 
 /* z-buffer render of n objects (min z; +inf where empty). Returns the
@@ -521,6 +688,86 @@ int32_t or_eval_batch(const or_world* w, const float* depth,
   }
   free(zp); free(I.cam); free(I.world); cam_free(&c);
   return err ? -1 : 0;
+}
+
+/* ICP refinement of n_hyp successors (the restatement above). parents,
+ * parent_len, hyp_parent, hyps as in or_eval_batch; radius = the
+ * correspondence distance r in metres; out[n_hyp]. */
+int32_t or_icp_refine(const or_world* w, const float* depth,
+                      const or_obj* parents, const int32_t* parent_len, int32_t n_par, int32_t k_max,
+                      const int32_t* hyp_parent, const or_obj* hyps, int64_t n_hyp,
+                      float radius, int32_t max_iter, or_icp_rec* out, int32_t n_threads) {
+  or_cam c;
+  if (cam_init(w, &c)) return -1;
+  or_cloud I;
+  if (observed_cloud(w, &c, depth, &I)) { cam_free(&c); return -1; }
+  int64_t* by_x = order_by_x(&I);
+  int64_t N = (int64_t)w->W * w->H;
+  float* zp = (float*)malloc(sizeof(float) * (size_t)N * (size_t)(n_par > 0 ? n_par : 1));
+  if (!zp || !by_x) { free(zp); free(by_x); free(I.cam); free(I.world); cam_free(&c); return -1; }
+  for (int32_t p = 0; p < n_par; ++p) {
+    int64_t culled = 0;
+    render_scene(w, &c, parents + (int64_t)p * k_max, parent_len[p], zp + (int64_t)p * N, &culled);
+  }
+  int err = 0;
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+  (void)n_threads;
+#endif
+#pragma omp parallel
+  {
+    float* zo = (float*)malloc(sizeof(float) * (size_t)N);
+    or_pt* M = (or_pt*)malloc(sizeof(or_pt) * (size_t)N);
+    if (!zo || !M) {
+#pragma omp atomic write
+      err = 1;
+    } else {
+#pragma omp for schedule(dynamic, 1)
+      for (int64_t h = 0; h < n_hyp; ++h) {
+        int64_t culled = 0;
+        render_scene(w, &c, hyps + h, 1, zo, &culled);
+        const int64_t nm = icp_model(w, &c, zo, zp + (int64_t)hyp_parent[h] * N, M);
+        icp_run(&I, by_x, M, nm, (double)radius, max_iter, out + h);
+      }
+    }
+    free(zo); free(M);
+  }
+  free(zp); free(by_x); free(I.cam); free(I.world); cam_free(&c);
+  return err ? -1 : 0;
+}
+
+/* The closed-form fit alone, on n explicit pairs (m[k], q[k]) (world
+ * frame, n x 3 floats): out = (c, s, t_x, t_y). Returns 0, 1 when no turn
+ * is defined, 2 with fewer than 3 pairs kept. */
+int32_t or_icp_fit(const float* m, const float* q, int64_t n, double* out) {
+  or_icp_sums S;
+  memset(&S, 0, sizeof S);
+  for (int64_t k = 0; k < n; ++k) {
+    or_pt a = {m[3 * k], m[3 * k + 1], m[3 * k + 2]}, b = {q[3 * k], q[3 * k + 1], q[3 * k + 2]};
+    icp_add_pair(&S, a, b);
+  }
+  if (S.n < 3) return 2;
+  return icp_solve(&S, out, out + 1, out + 2, out + 3);
+}
+
+/* The correspondence rule alone: idx[k] = index in I (pixel order) of the
+ * correspondence of world point p[k] within radius, or -1. */
+int32_t or_icp_match(const or_world* w, const float* depth, const float* p, int64_t n, float radius, int64_t* idx) {
+  or_cam c;
+  if (cam_init(w, &c)) return -1;
+  or_cloud I;
+  if (observed_cloud(w, &c, depth, &I)) { cam_free(&c); return -1; }
+  int64_t* by_x = order_by_x(&I);
+  if (!by_x) { free(I.cam); free(I.world); cam_free(&c); return -1; }
+  const double r = (double)radius;
+  const float r2 = (float)(r * r);
+  for (int64_t k = 0; k < n; ++k) {
+    or_pt a = {p[3 * k], p[3 * k + 1], p[3 * k + 2]};
+    idx[k] = icp_match(&I, by_x, a, r, r2);
+  }
+  free(by_x); free(I.cam); free(I.world); cam_free(&c);
+  return 0;
 }
 
 int32_t or_max_threads(void) {
