@@ -255,6 +255,75 @@ int perch_eval_successors_multi(perch_ctx* ctx, const perch_obj* parents, int32_
 int perch_render(perch_ctx* ctx, const perch_obj* objs, int32_t n, float* depth_out,
                  int64_t* n_culled);
 
+/* ICP refinement of successors (Sec. IV-E-1, compensating for
+ * discretization: each time a state is rendered with a new object, the
+ * object's non-occluded portion is aligned with the observed cloud by ICP in
+ * its local vicinity; Sec. V-B: correspondences only within 2 cm, half the
+ * grid step). The paper leaves the variant open; this one is fixed step by
+ * step, in exact arithmetic where order could matter, so that every record
+ * is bit-exact with the oracle:
+ *   model set M: the pixels where the new object's own render z_O is finite
+ *     and lies strictly in front of the parent's render z_P (+inf where
+ *     empty) -- for a valid child, dR of Eq. (3) -- back-projected to the
+ *     world frame as the observed cloud is;
+ *   motion T = (c, s, tx, ty): a turn about the world's vertical axis and a
+ *     shift in the table plane, applied in binary32 from T rounded to
+ *     binary32: x' = (c x - s y) + tx, y' = (s x + c y) + ty, z' = z;
+ *   correspondence of m: the observed point q of smallest
+ *     d^2 = fma(dz, dz, fma(dy, dy, dx dx)) (d = T m - q, world frame) with
+ *     d^2 <= (float)(radius^2); ties to the smaller index of q in I (pixel
+ *     order); none: m is unmatched;
+ *   sums over the pairs in fixed point (coordinates times 2^16, rounded to
+ *     the nearest integer, ties to even; a pair with |x| or |y| >= 32 m is
+ *     left out): n, sum X_m, sum Y_m, sum X_q, sum Y_q, sum X_m X_q,
+ *     sum Y_m Y_q, sum X_m Y_q, sum Y_m X_q -- exact, in any order;
+ *   fit (planar Procrustes, in closed form): with the exact integers
+ *     C = n sum(m . q) - sum m . sum q and S = n sum(m x q) - sum m x sum q,
+ *     each rounded to double as hi 2^64 + lo (hi, lo rounded, one rounded
+ *     sum), h = sqrt(C^2 + S^2), c = C / h, s = S / h,
+ *     tx = ((sum X_q - (c sum X_m - s sum Y_m)) / n) 2^-16, ty likewise with
+ *     (s sum X_m + c sum Y_m) (double, each operation rounded once);
+ *   iteration k = 1 .. max_iter from T = identity: match under T; fewer than
+ *     3 pairs: stop (PERCH_ICP_FEW); the same sums as at k - 1: stop
+ *     (PERCH_ICP_CONVERGED); C = S = 0: stop (PERCH_ICP_DEGENERATE); else T =
+ *     the fit. After max_iter fits: PERCH_ICP_CAP.
+ * The refined pose of the object at grid pose (x, y, yaw) is
+ * (c x - s y + tx, s x + c y + ty, yaw + atan2(s, c)). The search itself
+ * keeps the grid poses (its costs, renders and parity stay those of the
+ * grid MSGT); this call refines any batch of successors, such as the
+ * objects of a returned scene, each against the state it was added to. */
+typedef struct {
+  double c, s, tx, ty;  /* the motion T */
+  int32_t n_model;      /* |M| */
+  int32_t n_corr;       /* pairs of the last matching */
+  int32_t iters;        /* fits made */
+  int32_t status;       /* PERCH_ICP_*, or flags bit 30 / bit 31 as in perch_cost */
+} perch_icp;            /* 48 bytes */
+
+enum { PERCH_ICP_CONVERGED = 0, PERCH_ICP_CAP = 1, PERCH_ICP_FEW = 2, PERCH_ICP_DEGENERATE = 3 };
+
+/* Refine n_hyp successors against the observation of perch_set_observation
+ * (scene 0). parents, parent_stride, parent_len, n_par, hyp_parent, hyp as
+ * in perch_eval_successors (parent_len[i] <= parent_stride; no K_total);
+ * radius: the correspondence distance in metres (>= 0, finite); max_iter:
+ * the most fits per successor (0 .. 1000); out[n_hyp]. Host pointers; the
+ * call returns when out is written. Errors: PERCH_E_ARG (bad index, length,
+ * radius or max_iter), PERCH_E_STATE (no observation), PERCH_E_DEVICE (a
+ * record with bit 30 or 31). The first call after an observation builds
+ * the cloud's world-frame grid of cells >= 1.05 radius (one more set of
+ * device buffers, held by the context). */
+int perch_icp_refine(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride, const int32_t* parent_len,
+                     int32_t n_par, const int32_t* hyp_parent, const perch_obj* hyp, int64_t n_hyp, float radius,
+                     int32_t max_iter, perch_icp* out);
+
+/* Same, with parents, parent_len, hyp_parent, hyp and out as DEVICE pointers;
+ * the work is only enqueued on the context's stream (the grid, if it must
+ * be built, is built first, synchronously). Indices are checked on the
+ * device: a bad one gives a record with status bit 31 and the rest zero. */
+int perch_icp_refine_dev(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride,
+                         const int32_t* parent_len, int32_t n_par, const int32_t* hyp_parent, const perch_obj* hyp,
+                         int64_t n_hyp, float radius, int32_t max_iter, perch_icp* out);
+
 /* Tree search (Sec. IV-B, Alg. 1). With w = 1 and no heuristics:
  * uniform-cost search (A* with the admissible h0 = 0), which returns an
  * optimal scene. Otherwise Focal-MHA*: the anchor queue is keyed by g + h0,

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libperch.so")
 SOURCES = ["perch_kernels.cu", "perch_api.cu", "perch_search.cpp", "perch_noalloc.cu", "perch_tune.cu",
-           "perch_cnn.cu"]
+           "perch_cnn.cu", "perch_icp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

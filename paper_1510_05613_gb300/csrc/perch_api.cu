@@ -20,8 +20,11 @@
 using namespace perch;
 
 // ------------------------------------------------------------------ helpers
+long long DevBuf::reallocs = 0;
+
 cudaError_t DevBuf::ensure(size_t bytes) {
   if (bytes <= cap) return cudaSuccess;
+  ++reallocs;
   if (p) cudaFree(p);
   p = nullptr;
   cap = 0;
@@ -217,6 +220,7 @@ int perch_ctx::build_scene(int s, const float* depth_host) {
   if ((int)scenes.size() <= s) scenes.resize(s + 1);
   SceneBufs& sc = scenes[s];
   ++render_epoch;  // stored renders with the explained bit belong to the old cloud
+  if (s == 0) ++obs_serial;  // the ICP grid belongs to the old cloud
   const int npx = W * H;
   const int nblk = (npx + 255) / 256;
   CK(ctx->depth.ensure(4 * (size_t)npx), "alloc depth");

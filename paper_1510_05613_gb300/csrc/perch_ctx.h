@@ -10,6 +10,9 @@ struct DevBuf {
   void* p = nullptr;
   size_t cap = 0;
   cudaError_t ensure(size_t bytes);  // grow-only; contents are not preserved
+  // reallocations so far (every buffer of every context): a captured graph
+  // is replayed only while this is unchanged, since it holds the old addresses
+  static long long reallocs;
   void release();
   template <typename T>
   T* as() const {
@@ -31,6 +34,7 @@ struct GraphKey {
   const void* out;
   const void* out_host;
   long long version;
+  long long reallocs;  // DevBuf::reallocs when the graph was captured
 };
 
 // One scene's observed cloud and its indices (device buffers).
@@ -143,6 +147,14 @@ struct perch_ctx {
   // records, and in selecting states and building batches (learned scoring included)
   double search_eval_seconds = 0.0, search_absorb_seconds = 0.0, search_host_seconds = 0.0;
 
+  // ICP refinement (perch_icp_refine): scene 0's observed world points
+  // bucketed by a grid of cells >= 1.05 x the radius it was built for,
+  // rebuilt when the observation (obs_serial) or the radius changes
+  long long obs_serial = 0, icp_serial = -1;
+  float icp_radius = -1.0f;
+  perch::IcpGrid icp_grid{};
+  DevBuf icp_src, icp_pts, icp_start, icp_next, icp_out;
+
   // poll bound of the evaluation kernel's first wait for each bulk copy
   // (perch_set_wait_limit); the solo table always uses the default
   int wait_polls = perch::kWaitSpins;
@@ -161,7 +173,8 @@ struct perch_ctx {
             &b_out, &g_hist, &g_off, &g_cursor, &g_order, &g_next, &net_crops, &net_onehot, &net_pred,
             &solo, &solo_rec, &solo_hyp, &solo_hp, &solo_parent, &ptile_counts, &ptile_sat, &skip, &n_short,
             &tile_store, &tile_off, &tile_sizes, &pose_flags, &pg_cnt, &pg_start, &pg_flag, &pg_gix, &pg_gpose,
-            &pg_tmp, &pg_ranges, &pose_valid, &tile_box};
+            &pg_tmp, &pg_ranges, &pose_valid, &tile_box, &icp_src, &icp_pts, &icp_start, &icp_next,
+            &icp_out};
   }
 
   int fail(int code, const char* fmt, ...);
@@ -175,6 +188,10 @@ struct perch_ctx {
   int create_events();
   int build_scene(int s, const float* depth_host);
   int ensure_solo();
+  int ensure_icp_grid(float radius);
+  int enqueue_icp(const perch_obj* d_parents, int parent_stride, const int32_t* d_plen, int n_par,
+                  const int32_t* d_hp, const perch_obj* d_hyp, long long n_hyp, float radius, int max_iter,
+                  perch_icp* d_out);
   int enqueue_eval(const perch_obj* d_parents, int parent_stride, const int32_t* d_plen, int n_par,
                    const int32_t* d_hp, const perch_obj* d_hyp, long long n_hyp, int K_total, perch_cost* d_out,
                    const int32_t* d_parent_scene = nullptr, const int32_t* d_parent_K = nullptr);

@@ -173,6 +173,24 @@ struct PoseGroups {
   int* order;   // n_hyp: hypotheses sorted by pose
 };
 
+// ICP refinement (k_icp): the observed cloud's world points bucketed by a
+// 3D grid of cells no smaller than 1.05 x the correspondence radius, so
+// every point within the radius of a query lies in its 3 x 3 x 3 cells; cell
+// (ix, iy, iz) is key (iz ny + iy) nx + ix, so the three cells of a row in x
+// are one contiguous range of pts
+struct IcpGrid {
+  const float4* pts;  // world x, y, z; w = the point's index in I (pixel order, int bits)
+  const int* start;   // cells + 1
+  float gx, gy, gz, inv;
+  int nx, ny, nz;
+};
+
+struct IcpWork {
+  float r2;      // (float)(radius^2)
+  int max_iter;
+  perch_icp* out;
+};
+
 // kernels.cu launchers (all asynchronous on `s`)
 cudaError_t launch_fill_u32(uint32_t* p, uint32_t v, long long n, cudaStream_t s);
 cudaError_t launch_obs_count(const float* depth, int W, int H, int* block_counts, cudaStream_t s);
@@ -231,5 +249,14 @@ bool cost_stages_fit(int device, int tile_w, int tile_h, int stages);
 // first launch)
 cudaError_t preload_eval_kernels();
 bool eval_tile_fits(int device, int tile_w, int tile_h);
+// ICP: the observed world points with their pixel index, and their bounds
+// (ordered ints: x, y, z min, then x, y, z max)
+cudaError_t launch_icp_points(const float4* world2, const float4* cam2, int n, float4* pts, int* bounds,
+                              cudaStream_t s);
+// ICP of each hypothesis of the batch (one CTA per hypothesis at a time,
+// claimed from the device counter `next`, zero before the launch; the
+// parents' renders must be in b.parent_z)
+cudaError_t launch_icp(const Camera& cam, const Geometry& g, const Batch& b, const IcpGrid& q, const IcpWork& w,
+                       int* next, int sm_count, cudaStream_t s);
 
 }  // namespace perch

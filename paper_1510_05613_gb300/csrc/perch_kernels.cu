@@ -2031,4 +2031,277 @@ cudaError_t launch_eval_group(const Camera& cam, const Geometry& g, const ObsInd
   }
 }
 
+// -------------------------------------------------------------------- ICP
+// Local alignment of each successor's new object with the observed cloud
+// (Sec. IV-E-1: the object's non-occluded portion, aligned by ICP; Sec. V-B:
+// correspondences only within 2 cm), step by step as the public header
+// states it. The render, the model set and every distance are the binary32
+// arithmetic of the evaluation path; the pairs' sums are exact 64-bit
+// integers (coordinates in units of 2^-16 m), so the order in which the
+// warps add them does not matter; the fit from those sums is double
+// arithmetic in a fixed order, made by one thread.
+
+// the observed world points with their index in I, and their bounds
+__global__ void k_icp_points(const float4* world2, const float4* cam2, int n, float4* pts, int* bounds) {
+  const int k = blockIdx.x * 256 + threadIdx.x;
+  const bool ok = k < n;
+  const float4 w = ok ? world2[k] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (ok) pts[k] = make_float4(w.x, w.y, w.z, cam2[k].w);
+  const int lo[3] = {ok ? ford(w.x) : INT_MAX, ok ? ford(w.y) : INT_MAX, ok ? ford(w.z) : INT_MAX};
+  const int hi[3] = {ok ? ford(w.x) : INT_MIN, ok ? ford(w.y) : INT_MIN, ok ? ford(w.z) : INT_MIN};
+  for (int d = 0; d < 3; ++d) {
+    const int a = __reduce_min_sync(0xffffffffu, lo[d]), b = __reduce_max_sync(0xffffffffu, hi[d]);
+    if ((threadIdx.x & 31) == 0 && a <= b) {
+      atomicMin(&bounds[d], a);
+      atomicMax(&bounds[3 + d], b);
+    }
+  }
+}
+
+cudaError_t launch_icp_points(const float4* world2, const float4* cam2, int n, float4* pts, int* bounds,
+                              cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_icp_points<<<(n + 255) / 256, 256, 0, s>>>(world2, cam2, n, pts, bounds);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ long long icp_fixed(float v) { return __float2ll_rn(fmul(v, 65536.0f)); }
+
+// hi 2^64 + lo: each part rounded to double, then one rounded addition
+__device__ __forceinline__ double icp_i128_to_double(__int128 v) {
+  const long long hi = (long long)(v >> 64);
+  const unsigned long long lo = (unsigned long long)v;
+  return __dadd_rn(__dmul_rn(__ll2double_rn(hi), 18446744073709551616.0), __ull2double_rn(lo));
+}
+
+// one pair's terms: n, sum X_m, sum Y_m, sum X_q, sum Y_q, sum X_m X_q,
+// sum Y_m Y_q, sum X_m Y_q, sum Y_m X_q (|x|, |y| < 32 m: |X|, |Y| < 2^21)
+__device__ __forceinline__ void icp_add_pair(long long* L, float mx, float my, float qx, float qy) {
+  if (!(fabsf(mx) < 32.0f && fabsf(my) < 32.0f && fabsf(qx) < 32.0f && fabsf(qy) < 32.0f)) return;
+  const long long X = icp_fixed(mx), Y = icp_fixed(my), QX = icp_fixed(qx), QY = icp_fixed(qy);
+  L[0] += 1;
+  L[1] += X;
+  L[2] += Y;
+  L[3] += QX;
+  L[4] += QY;
+  L[5] += X * QX;
+  L[6] += Y * QY;
+  L[7] += X * QY;
+  L[8] += Y * QX;
+}
+
+// Planar Procrustes from the sums: C = n sum(m . q) - sum m . sum q and
+// S = n sum(m x q) - sum m x sum q (exact), (c, s) = (C, S) / |(C, S)|,
+// t = (sum q - R sum m) / n. False when C = S = 0.
+__device__ bool icp_solve(const long long* S, double* T) {
+  const __int128 n = S[0];
+  const __int128 C = n * ((__int128)S[5] + S[6]) - ((__int128)S[1] * S[3] + (__int128)S[2] * S[4]);
+  const __int128 X = n * ((__int128)S[7] - S[8]) - ((__int128)S[1] * S[4] - (__int128)S[2] * S[3]);
+  if (C == 0 && X == 0) return false;
+  const double Cd = icp_i128_to_double(C), Xd = icp_i128_to_double(X);
+  const double h = __dsqrt_rn(__dadd_rn(__dmul_rn(Cd, Cd), __dmul_rn(Xd, Xd)));
+  const double c = __ddiv_rn(Cd, h), s = __ddiv_rn(Xd, h);
+  const double nd = __ll2double_rn(S[0]), sx = __ll2double_rn(S[1]), sy = __ll2double_rn(S[2]);
+  T[0] = c;
+  T[1] = s;
+  T[2] = __dmul_rn(__ddiv_rn(__dsub_rn(__ll2double_rn(S[3]), __dsub_rn(__dmul_rn(c, sx), __dmul_rn(s, sy))), nd),
+                   1.0 / 65536.0);
+  T[3] = __dmul_rn(__ddiv_rn(__dsub_rn(__ll2double_rn(S[4]), __dadd_rn(__dmul_rn(s, sx), __dmul_rn(c, sy))), nd),
+                   1.0 / 65536.0);
+  return true;
+}
+
+struct IcpClaim {
+  int* next;  // device counter, zero before the launch
+};
+
+// One CTA per hypothesis at a time (claimed from a counter): render the new
+// object into the shared-memory tile over its screen box (render_chunks),
+// keep the pixels in front of the parent's render as the model set (z bits;
+// 0 elsewhere), then iterate. In each matching a warp takes one model pixel:
+// it back-projects and moves the point, and its lanes scan the nine x-rows of
+// the 3 x 3 x 3 grid cells around it; the lane holding the nearest point
+// (ties: smaller index) adds the pair to its own sums, which the warps reduce
+// into shared 64-bit counters. Thread 0 then decides and fits.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_icp(Camera cam, Geometry g, Batch b, IcpGrid q, IcpWork w, IcpClaim cl) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ __align__(8) unsigned long long s_sum[9];
+  __shared__ double s_T[4];
+  __shared__ int s_qn, s_item, s_stop, s_nm;
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  EvalShared sh{s_bar, nullptr, &s_qn, smem, 0u, 0u};
+  const RenderSmem s = render_smem(smem);
+  uint32_t* tile = s.tile;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(cl.next, 1);
+    __syncthreads();
+    const long long h = s_item;
+    __syncthreads();
+    if (h >= b.n_hyp) break;
+    HypArgs a;
+    const bool ok = hyp_args(g, b, h, a);
+    const int4 bb = ok ? g.pose_bbox[a.pose] : make_int4(0, 0, 0, 0);
+    if (!ok || bb.z > b.tile_w || bb.w > b.tile_h) {
+      if (tid == 0) w.out[h] = perch_icp{0.0, 0.0, 0.0, 0.0, 0, 0, 0, (int32_t)kFlagBadIndex};
+      continue;
+    }
+    const int tw = bb.z, area = bb.z * bb.w;
+    const DevMesh m = g.meshes[a.o.mesh];
+    if (tid == 0) render_start(g, m, a.o.iyaw, s, sh.bar);
+    for (int i = tid; i < area; i += NT) tile[i] = 0u;  // 1/z = 0: empty
+    if (tid == 0) {
+      s_nm = 0;
+      s_T[0] = 1.0;
+      s_T[1] = s_T[2] = s_T[3] = 0.0;
+    }
+    unsigned culled = 0;
+    int4 cov = make_int4(0x7fffffff, -1, 0x7fffffff, -1);  // not needed here
+    const int st = render_chunks<NT, kInlinePixels>(cam, g, b, m, a.o, bb, s, sh, culled, cov);
+    if (st != kEvalDone) {
+      if (tid == 0) w.out[h] = perch_icp{0.0, 0.0, 0.0, 0.0, 0, 0, 0, (int32_t)kFlagTimeout};
+      __syncthreads();  // the tile is cleared by the next hypothesis
+      if (st == kEvalStop) break;
+      continue;
+    }
+    // model set: z where the object lies strictly in front of the parent
+    const float* zp = b.parent_z + (size_t)a.pid * cam.W * cam.H;
+    int nm = 0;
+    for (int i = tid; i < area; i += NT) {
+      const uint32_t izb = tile[i];
+      uint32_t v = 0u;
+      if (izb != 0u) {
+        const int ly = i / tw, lx = i - ly * tw;
+        const float z = __frcp_rn(__uint_as_float(izb));
+        if (z < zp[(size_t)(bb.y + ly) * cam.W + bb.x + lx]) {
+          v = __float_as_uint(z);
+          ++nm;
+        }
+      }
+      tile[i] = v;
+    }
+    nm = __reduce_add_sync(0xffffffffu, nm);
+    if (lane == 0 && nm) atomicAdd(&s_nm, nm);
+    __syncthreads();  // |M| and the model set are complete
+    long long prev[9];  // thread 0: the previous matching's sums
+    bool have_prev = false;
+    int iters = 0, n_corr = 0, status = PERCH_ICP_CAP;
+    for (int k = 1; k <= w.max_iter; ++k) {
+      if (tid < 9) s_sum[tid] = 0ull;
+      __syncthreads();  // also publishes s_T
+      const float cf = __double2float_rn(s_T[0]), sf = __double2float_rn(s_T[1]);
+      const float txf = __double2float_rn(s_T[2]), tyf = __double2float_rn(s_T[3]);
+      long long L[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      for (int i = warp; i < area; i += NW) {
+        const uint32_t zb = tile[i];
+        if (zb == 0u) continue;  // the same pixel for the whole warp
+        const int ly = i / tw, lx = i - ly * tw;
+        const float z = __uint_as_float(zb);
+        const float xc = fmul(g.rx[bb.x + lx], z), yc = fmul(g.ry[bb.y + ly], z);
+        const float mx = fadd(ffma(cam.Rwc[2], z, ffma(cam.Rwc[1], yc, fmul(cam.Rwc[0], xc))), cam.twc[0]);
+        const float my = fadd(ffma(cam.Rwc[5], z, ffma(cam.Rwc[4], yc, fmul(cam.Rwc[3], xc))), cam.twc[1]);
+        const float mz = fadd(ffma(cam.Rwc[8], z, ffma(cam.Rwc[7], yc, fmul(cam.Rwc[6], xc))), cam.twc[2]);
+        const float px = fadd(fsub(fmul(cf, mx), fmul(sf, my)), txf);
+        const float py = fadd(fadd(fmul(sf, mx), fmul(cf, my)), tyf);
+        const int cx = cell_of(px, q.gx, q.inv, q.nx), cy = cell_of(py, q.gy, q.inv, q.ny);
+        const int cz = cell_of(mz, q.gz, q.inv, q.nz);
+        const int x0 = max(cx - 1, 0), x1 = min(cx + 1, q.nx - 1);
+        const int y0 = max(cy - 1, 0), y1 = min(cy + 1, q.ny - 1);
+        const int z0 = max(cz - 1, 0), z1 = min(cz + 1, q.nz - 1);
+        uint32_t bd = 0xffffffffu;  // no candidate (every d^2 <= r^2 has smaller bits)
+        int bj = INT_MAX;
+        float bqx = 0.0f, bqy = 0.0f;
+        if (x0 <= x1) {
+          for (int iz = z0; iz <= z1; ++iz)
+            for (int iy = y0; iy <= y1; ++iy) {
+              const int row = (iz * q.ny + iy) * q.nx;
+              const int end = q.start[row + x1 + 1];
+              for (int t = q.start[row + x0] + lane; t < end; t += 32) {
+                const float4 o = q.pts[t];
+                const float d = dist2(px, py, mz, o);
+                if (d <= w.r2) {
+                  const uint32_t db = __float_as_uint(d);
+                  const int j = __float_as_int(o.w);
+                  if (db < bd || (db == bd && j < bj)) {
+                    bd = db;
+                    bj = j;
+                    bqx = o.x;
+                    bqy = o.y;
+                  }
+                }
+              }
+            }
+        }
+        const uint32_t wd = __reduce_min_sync(0xffffffffu, bd);
+        if (wd == 0xffffffffu) continue;  // unmatched (uniform)
+        const uint32_t wj = __reduce_min_sync(0xffffffffu, bd == wd ? (uint32_t)bj : 0xffffffffu);
+        if (bd == wd && (uint32_t)bj == wj) icp_add_pair(L, mx, my, bqx, bqy);  // one lane: each point once
+      }
+      for (int t = 0; t < 9; ++t) {
+        long long v = L[t];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0 && v != 0) atomicAdd(&s_sum[t], (unsigned long long)v);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        long long S[9];
+        for (int t = 0; t < 9; ++t) S[t] = (long long)s_sum[t];
+        n_corr = (int)S[0];
+        int stop = 0;
+        bool same = have_prev;
+        for (int t = 0; t < 9 && same; ++t) same = S[t] == prev[t];
+        if (S[0] < 3) {
+          status = PERCH_ICP_FEW;
+          stop = 1;
+        } else if (same) {
+          status = PERCH_ICP_CONVERGED;
+          stop = 1;
+        } else {
+          double T[4];
+          if (!icp_solve(S, T)) {
+            status = PERCH_ICP_DEGENERATE;
+            stop = 1;
+          } else {
+            for (int t = 0; t < 4; ++t) s_T[t] = T[t];
+            for (int t = 0; t < 9; ++t) prev[t] = S[t];
+            have_prev = true;
+            iters = k;
+          }
+        }
+        s_stop = stop;
+      }
+      __syncthreads();
+      if (s_stop) break;
+    }
+    if (tid == 0) w.out[h] = perch_icp{s_T[0], s_T[1], s_T[2], s_T[3], s_nm, n_corr, iters, status};
+    __syncthreads();  // the tile, s_T and s_nm are reused by the next hypothesis
+  }
+}
+
+cudaError_t launch_icp(const Camera& cam, const Geometry& g, const Batch& b, const IcpGrid& q, const IcpWork& w,
+                       int* next, int sm_count, cudaStream_t s) {
+  if (b.n_hyp <= 0) return cudaSuccess;
+  const size_t smem = render_smem_bytes(b.tile_w, b.tile_h);
+  auto kern = k_icp<256>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long grid = (long long)per_sm * sm_count;
+  if (grid > b.n_hyp) grid = b.n_hyp;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, 256, smem, s>>>(cam, g, b, q, w, IcpClaim{next});
+  return cudaGetLastError();
+}
+
 }  // namespace perch

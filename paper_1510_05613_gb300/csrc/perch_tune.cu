@@ -223,8 +223,8 @@ extern "C" int perch_eval_graph(perch_ctx* ctx, const perch_obj* parents, int32_
   if (n_par > 65535 || (long long)n_par * std::max(parent_stride, 1) > 65535)
     return ctx->fail(PERCH_E_ARG, "too many parents in one batch (n_par x stride <= 65535)");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  const GraphKey key{parents, parent_stride, parent_len, n_par, hyp_parent, hyp, n_hyp, K_total, out, out_host,
-                     ctx->tables_version};
+  GraphKey key{parents, parent_stride, parent_len, n_par, hyp_parent, hyp, n_hyp, K_total, out, out_host,
+               ctx->tables_version, DevBuf::reallocs};
   if (!ctx->graph_exec || std::memcmp(&key, &ctx->graph_key, sizeof key) != 0) {
     if (ctx->graph_exec) {
       cudaGraphExecDestroy(ctx->graph_exec);
@@ -255,6 +255,7 @@ extern "C" int perch_eval_graph(perch_ctx* ctx, const perch_obj* parents, int32_
     cudaGraphDestroy(graph);
     CK(ei, "graph instantiate");
     ctx->graph_exec = exec;
+    key.reallocs = DevBuf::reallocs;  // the warm-up run may have grown buffers; the capture uses those
     ctx->graph_key = key;
   }
   CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream), "graph launch");

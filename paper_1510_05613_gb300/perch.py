@@ -21,6 +21,11 @@ FLAG_CULLED, FLAG_INVALID, FLAG_TIMEOUT, FLAG_BAD_INDEX = 1, 2, 1 << 30, 1 << 31
 OBJ = np.dtype([("mesh", np.uint16), ("iyaw", np.uint16), ("ix", np.int16), ("iy", np.int16)])
 COST = np.dtype([("djr", np.int32), ("djo", np.int32), ("resid", np.int32), ("viol", np.int32),
                  ("n_new", np.int32), ("flags", np.uint32), ("n_vol", np.int32)])
+# perch_icp (48 bytes): the planar motion, |M|, the last matching's pairs, the
+# fits made, and PERCH_ICP_* (or flags bit 30 / 31)
+ICP = np.dtype([("c", np.float64), ("s", np.float64), ("tx", np.float64), ("ty", np.float64),
+                ("n_model", np.int32), ("n_corr", np.int32), ("iters", np.int32), ("status", np.uint32)])
+PERCH_ICP_CONVERGED, PERCH_ICP_CAP, PERCH_ICP_FEW, PERCH_ICP_DEGENERATE = 0, 1, 2, 3
 
 # names exported by the library (include/perch.h)
 EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_meshes", "perch_set_pose_grid",
@@ -34,7 +39,8 @@ EXPORTS = ("perch_create", "perch_destroy", "perch_last_error", "perch_load_mesh
            "perch_set_shortcut", "perch_shortcut_stats", "perch_search_stats", "perch_search_times",
            "perch_set_wait_limit", "perch_set_share_renders", "perch_set_render_cache", "perch_last_phase_times", "perch_set_volumes",
            "perch_launch_config", "perch_set_symmetry", "perch_set_inline_pixels", "perch_set_bin_depth",
-           "perch_launch_bin_depths", "perch_set_cost_stages", "perch_launch_cost_stages")
+           "perch_launch_bin_depths", "perch_set_cost_stages", "perch_launch_cost_stages", "perch_icp_refine",
+           "perch_icp_refine_dev")
 
 
 class perch_mesh(ctypes.Structure):
@@ -124,6 +130,8 @@ def load(path: str = LIB_PATH):
         "perch_launch_bin_depths": ([P, P], ctypes.c_int),
         "perch_set_cost_stages": ([P, I32, I32], ctypes.c_int),
         "perch_launch_cost_stages": ([P, P], ctypes.c_int),
+        "perch_icp_refine": ([P, P, I32, P, I32, P, P, I64, F, I32, P], ctypes.c_int),
+        "perch_icp_refine_dev": ([P, P, I32, P, I32, P, P, I64, F, I32, P], ctypes.c_int),
         "perch_set_symmetry": ([P, P, I32], ctypes.c_int),
         "perch_set_share_renders": ([P, I32], ctypes.c_int),
         "perch_set_render_cache": ([P, I32], ctypes.c_int),
@@ -188,6 +196,7 @@ class Perch:
         return self._check(self.lib.perch_load_meshes(self.h, ctypes.addressof(arr), len(meshes)))
 
     def perch_set_pose_grid(self, grid):
+        self.grid = grid  # for refined_pose
         xs, ys, cs = _c(grid.xs, np.float32), _c(grid.ys, np.float32), _c(grid.cos_sin, np.float32)
         return self._check(self.lib.perch_set_pose_grid(self.h, xs.ctypes.data, len(xs), ys.ctypes.data, len(ys),
                                                         cs.ctypes.data, cs.shape[0]))
@@ -247,6 +256,34 @@ class Perch:
         return self._check(self.lib.perch_eval_successors_noalloc(
             self.h, parents_t.data_ptr(), stride, plen_t.data_ptr(), plen_t.numel(), hyp_parent_t.data_ptr(),
             hyps_t.data_ptr(), hyp_parent_t.numel(), K_total, out_t.data_ptr()))
+
+    def perch_icp_refine(self, parents, hyp_parent, hyps, radius: float = 0.02, max_iter: int = 20):
+        """ICP refinement of each hypothesis's new object against its parent
+        (host arrays in, structured ICP array out)."""
+        P, plen, stride = self.pack_parents(parents)
+        hp = _c(hyp_parent, np.int32)
+        h = _c(hyps, OBJ)
+        out = np.zeros(len(h), ICP)
+        self._check(self.lib.perch_icp_refine(self.h, P.ctypes.data, stride, plen.ctypes.data, len(plen), _ptr(hp),
+                                              _ptr(h), len(h), radius, max_iter, _ptr(out)))
+        return out
+
+    def perch_icp_refine_dev(self, parents_t, stride: int, plen_t, hyp_parent_t, hyps_t, radius: float,
+                             max_iter: int, out_t):
+        """Device buffers (torch tensors; out_t holds 48 bytes per hypothesis)
+        in and out; enqueued on the context's stream."""
+        return self._check(self.lib.perch_icp_refine_dev(
+            self.h, parents_t.data_ptr(), stride, plen_t.data_ptr(), plen_t.numel(), hyp_parent_t.data_ptr(),
+            hyps_t.data_ptr(), hyp_parent_t.numel(), radius, max_iter, out_t.data_ptr()))
+
+    def perch_refine_scene(self, objs, radius: float = 0.02, max_iter: int = 20):
+        """ICP of each object of a scene (in the order it was added) against
+        the objects before it: the refinement of every successor on the
+        path to that scene. Returns (records, [(mesh, x, y, yaw)])."""
+        objs = np.asarray(objs, OBJ)
+        recs = self.perch_icp_refine([objs[:k] for k in range(len(objs))], np.arange(len(objs)), objs, radius,
+                                     max_iter)
+        return recs, [refined_pose(self.grid, o, r) for o, r in zip(objs, recs)]
 
     def perch_autotune(self, n_sample: int = 2048):
         """Pick the CTA width per mesh by timing; returns the choices."""
@@ -540,6 +577,17 @@ class PerchCNN:
     def synchronize(self):
         import torch
         torch.cuda.synchronize()
+
+
+def refined_pose(grid, obj, rec):
+    """(mesh, x, y, yaw) of a grid object moved by an ICP record's motion:
+    (x, y) turned and shifted, the yaw turned by atan2(s, c)."""
+    import math
+    x, y = float(grid.xs[int(obj["ix"])]), float(grid.ys[int(obj["iy"])])
+    c0, s0 = (float(v) for v in grid.cos_sin[int(obj["iyaw"])])
+    c, s = float(rec["c"]), float(rec["s"])
+    return (int(obj["mesh"]), c * x - s * y + float(rec["tx"]), s * x + c * y + float(rec["ty"]),
+            math.atan2(s0, c0) + math.atan2(s, c))
 
 
 def records(out) -> np.ndarray:

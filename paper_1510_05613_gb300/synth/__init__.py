@@ -535,6 +535,24 @@ def workload_c2(scene: int = 0, grid: PoseGrid | None = None) -> Workload:
     return Workload("c2", cam, meshes, grid, 0.01, gt, depth, 0.003, 0.05, seed)
 
 
+def workload_c2_off_grid(scene: int = 0, off_grid: float = 1.0, grid: PoseGrid | None = None) -> Workload:
+    """The C2 camera, meshes and grid with the three objects observed off
+    the grid: each at its grid pose plus a uniform offset of up to off_grid/2
+    grid steps in x and y and off_grid/2 yaw steps (the recorded ground truth
+    stays the grid pose, extra["jitter"] the offsets; footprints 1.5 steps
+    further apart), sigma 3 mm, 5% dropout, delta 1 cm."""
+    seed = 1000 * 2 + 700 + scene
+    cam, meshes = camera_c2(), meshes_c2()
+    grid = grid or pose_grid(-0.49, 0.02, 50, 16)
+    step = float(grid.xs[1] - grid.xs[0])
+    gt = sample_scene(meshes, grid, [0, 1, 2], seed, margin=0.005 + 1.5 * step)
+    j = (uniform(substream(seed, 6), 9).reshape(3, 3) - 0.5) * float(off_grid)
+    jitter = j * np.array([step, step, 2.0 * math.pi / grid.n_yaw])
+    depth = observe(cam, meshes, grid, gt, 0.003, 0.05, seed, jitter)
+    return Workload("c2-off-grid", cam, meshes, grid, 0.01, gt, depth, 0.003, 0.05, seed,
+                    extra={"jitter": jitter.tolist()})
+
+
 # ---------------------------------------------------------------------------
 # heavy-occlusion workload: eight meshes of uneven size (2k to 50k triangles)
 # ---------------------------------------------------------------------------

@@ -49,6 +49,8 @@ def test_struct_layouts():
     # kind, n, p[4], zlo, zhi, normals
     assert ctypes.sizeof(perch.perch_volume) == 4 + 4 + 16 + 8 + 8
     assert perch.perch_volume.normals.offset == 32
+    # c, s, tx, ty (double), n_model, n_corr, iters, status
+    assert perch.ICP.itemsize == 48 and perch.ICP.fields["status"][1] == 44
 
 
 def test_null_context_and_null_args_are_rejected(lib):
@@ -67,6 +69,8 @@ def test_null_context_and_null_args_are_rejected(lib):
     assert lib.perch_launch_bin_depths(None, None) == perch.PERCH_E_ARG
     assert lib.perch_set_cost_stages(None, -1, 2) == perch.PERCH_E_ARG
     assert lib.perch_launch_cost_stages(None, None) == perch.PERCH_E_ARG
+    assert lib.perch_icp_refine(None, None, 0, None, 0, None, None, 0, 0.02, 20, None) == perch.PERCH_E_ARG
+    assert lib.perch_icp_refine_dev(None, None, 0, None, 0, None, None, 0, 0.02, 20, None) == perch.PERCH_E_ARG
 
 
 def test_create_without_gpu_fails_cleanly(lib):
