@@ -153,7 +153,7 @@ struct perch_ctx {
   long long obs_serial = 0, icp_serial = -1;
   float icp_radius = -1.0f;
   perch::IcpGrid icp_grid{};
-  DevBuf icp_src, icp_pts, icp_start, icp_next, icp_out;
+  DevBuf icp_src, icp_pts, icp_start, icp_next, icp_out, icp_prev;
 
   // poll bound of the evaluation kernel's first wait for each bulk copy
   // (perch_set_wait_limit); the solo table always uses the default
@@ -174,7 +174,7 @@ struct perch_ctx {
             &solo, &solo_rec, &solo_hyp, &solo_hp, &solo_parent, &ptile_counts, &ptile_sat, &skip, &n_short,
             &tile_store, &tile_off, &tile_sizes, &pose_flags, &pg_cnt, &pg_start, &pg_flag, &pg_gix, &pg_gpose,
             &pg_tmp, &pg_ranges, &pose_valid, &tile_box, &icp_src, &icp_pts, &icp_start, &icp_next,
-            &icp_out};
+            &icp_out, &icp_prev};
   }
 
   int fail(int code, const char* fmt, ...);

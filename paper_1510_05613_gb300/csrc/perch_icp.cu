@@ -23,11 +23,11 @@ static float icp_ordered_to_float(int i) {
   return f;
 }
 
-// Bucket scene 0's observed world points by a 3D grid of cells >= 1.05 x
-// radius (and >= 5 mm), grown by 1.25 until it has at most 16M cells: every
-// observed point within the radius of a query then lies in the query's
-// 3 x 3 x 3 cells (a cell is wider than the radius, and the rounding of the
-// cell index moves neither side by a cell).
+// Bucket scene 0's observed world points by a 3D grid of cells of half the
+// radius (at least 2.5 mm), grown by 1.25 until it has at most 16M cells.
+// The kernel scans the cells that meet its search cube, found with the same
+// monotone cell function, so any cell size gives the exact nearest point;
+// half the radius keeps the scanned volume close to the search ball.
 int perch_ctx::ensure_icp_grid(float radius) {
   perch_ctx* ctx = this;
   if (icp_serial == obs_serial && icp_radius == radius) return PERCH_OK;
@@ -58,7 +58,7 @@ int perch_ctx::ensure_icp_grid(float radius) {
       lo[k] = icp_ordered_to_float(hb[k]);
       hi[k] = icp_ordered_to_float(hb[3 + k]);
     }
-    double h = std::max(1.05 * (double)radius, 0.005);
+    double h = std::max(0.5 * (double)radius, 0.0025);
     long long cells;
     int dims[3];
     for (;;) {
@@ -110,6 +110,9 @@ int perch_ctx::enqueue_icp(const perch_obj* d_parents, int parent_stride, const 
   const size_t npx = (size_t)cam.W * cam.H;
   CK(parent_z.ensure(4 * npx * std::max(n_par, 1)), "alloc parent z-buffers");
   CK(icp_next.ensure(4), "alloc");
+  // each CTA's pair memory: 4 CTAs per SM at most (k_icp's registers)
+  const long long prev_elems = 4LL * sm_count * tile_w * tile_h;
+  CK(icp_prev.ensure(4 * (size_t)std::max(prev_elems, 1LL)), "alloc");
   Batch b;
   std::memset(&b, 0, sizeof b);
   b.parents = d_parents;
@@ -130,24 +133,29 @@ int perch_ctx::enqueue_icp(const perch_obj* d_parents, int parent_stride, const 
   CK(cudaMemsetAsync(icp_next.p, 0, 4, stream), "memset");
   IcpWork w;
   w.r2 = (float)((double)radius * (double)radius);
+  w.rwin = (float)(1.01 * (double)radius + 1e-6);
   w.max_iter = max_iter;
   w.out = d_out;
-  CK(launch_icp(cam, g, b, icp_grid, w, icp_next.as<int>(), sm_count, stream), "icp kernel");
+  w.prev = icp_prev.as<int>();
+  CK(launch_icp(cam, g, b, icp_grid, w, prev_elems, icp_next.as<int>(), sm_count, stream), "icp kernel");
   return PERCH_OK;
 }
+
+constexpr int kNothingToDo = 1;  // icp_check_args: a valid call with no hypothesis
 
 static int icp_check_args(perch_ctx* ctx, const perch_obj* parents, int32_t parent_stride, const int32_t* parent_len,
                           int32_t n_par, const int32_t* hyp_parent, const perch_obj* hyp, int64_t n_hyp,
                           float radius, int32_t max_iter, const perch_icp* out) {
   if (!ctx->has_obs) return ctx->fail(PERCH_E_STATE, "set an observation first");
   if (n_hyp < 0 || n_hyp > 0x7fffffffLL) return ctx->fail(PERCH_E_ARG, "n_hyp out of range");
+  if (!(radius >= 0.0f && radius <= 1.0f)) return ctx->fail(PERCH_E_ARG, "radius must lie in [0, 1] m");
+  if (max_iter < 0 || max_iter > 1000) return ctx->fail(PERCH_E_ARG, "max_iter must lie in [0, 1000]");
+  if (n_hyp == 0) return kNothingToDo;
   if (!parent_len || !hyp_parent || !hyp || !out || n_par < 1 || parent_stride < 0 ||
       (parent_stride > 0 && !parents))
     return ctx->fail(PERCH_E_ARG, "null pointer or bad sizes");
   if (n_par > 65535 || (long long)n_par * std::max(parent_stride, 1) > 65535)
     return ctx->fail(PERCH_E_ARG, "too many parents in one batch (n_par x stride <= 65535)");
-  if (!(radius >= 0.0f && radius <= 1.0f)) return ctx->fail(PERCH_E_ARG, "radius must lie in [0, 1] m");
-  if (max_iter < 0 || max_iter > 1000) return ctx->fail(PERCH_E_ARG, "max_iter must lie in [0, 1000]");
   return PERCH_OK;
 }
 
@@ -167,8 +175,8 @@ int perch_icp_refine(perch_ctx* ctx, const perch_obj* parents, int32_t parent_st
   ctx->err.clear();
   int rc = icp_check_args(ctx, parents, parent_stride, parent_len, n_par, hyp_parent, hyp, n_hyp, radius, max_iter,
                           out);
+  if (rc == kNothingToDo) return PERCH_OK;
   if (rc) return rc;
-  if (n_hyp == 0) return PERCH_OK;
   for (int i = 0; i < n_par; ++i) {
     if (parent_len[i] < 0 || parent_len[i] > parent_stride)
       return ctx->fail(PERCH_E_ARG, "parent %d: length %d outside [0, stride]", i, parent_len[i]);
@@ -224,8 +232,8 @@ int perch_icp_refine_dev(perch_ctx* ctx, const perch_obj* parents, int32_t paren
   ctx->err.clear();
   int rc = icp_check_args(ctx, parents, parent_stride, parent_len, n_par, hyp_parent, hyp, n_hyp, radius, max_iter,
                           out);
+  if (rc == kNothingToDo) return PERCH_OK;
   if (rc) return rc;
-  if (n_hyp == 0) return PERCH_OK;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   rc = ctx->ensure_tables();
   if (rc) return rc;

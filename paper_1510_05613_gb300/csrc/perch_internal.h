@@ -174,10 +174,8 @@ struct PoseGroups {
 };
 
 // ICP refinement (k_icp): the observed cloud's world points bucketed by a
-// 3D grid of cells no smaller than 1.05 x the correspondence radius, so
-// every point within the radius of a query lies in its 3 x 3 x 3 cells; cell
-// (ix, iy, iz) is key (iz ny + iy) nx + ix, so the three cells of a row in x
-// are one contiguous range of pts
+// 3D grid; cell (ix, iy, iz) is key (iz ny + iy) nx + ix, so the cells of a
+// row in x are one contiguous range of pts
 struct IcpGrid {
   const float4* pts;  // world x, y, z; w = the point's index in I (pixel order, int bits)
   const int* start;   // cells + 1
@@ -187,8 +185,10 @@ struct IcpGrid {
 
 struct IcpWork {
   float r2;      // (float)(radius^2)
+  float rwin;    // 1.01 radius + 1e-6 m: the search window before a pair is known
   int max_iter;
   perch_icp* out;
+  int* prev;     // per CTA, tile_w x tile_h entries: each model pixel's last paired point (grid order)
 };
 
 // kernels.cu launchers (all asynchronous on `s`)
@@ -255,8 +255,9 @@ cudaError_t launch_icp_points(const float4* world2, const float4* cam2, int n, f
                               cudaStream_t s);
 // ICP of each hypothesis of the batch (one CTA per hypothesis at a time,
 // claimed from the device counter `next`, zero before the launch; the
-// parents' renders must be in b.parent_z)
+// parents' renders must be in b.parent_z). The grid is capped so that every
+// CTA has its tile_w x tile_h slice of w.prev (prev_elems entries in all).
 cudaError_t launch_icp(const Camera& cam, const Geometry& g, const Batch& b, const IcpGrid& q, const IcpWork& w,
-                       int* next, int sm_count, cudaStream_t s);
+                       long long prev_elems, int* next, int sm_count, cudaStream_t s);
 
 }  // namespace perch

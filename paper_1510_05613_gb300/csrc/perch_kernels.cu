@@ -2118,11 +2118,14 @@ struct IcpClaim {
 // One CTA per hypothesis at a time (claimed from a counter): render the new
 // object into the shared-memory tile over its screen box (render_chunks),
 // keep the pixels in front of the parent's render as the model set (z bits;
-// 0 elsewhere), then iterate. In each matching a warp takes one model pixel:
-// it back-projects and moves the point, and its lanes scan the nine x-rows of
-// the 3 x 3 x 3 grid cells around it; the lane holding the nearest point
-// (ties: smaller index) adds the pair to its own sums, which the warps reduce
-// into shared 64-bit counters. Thread 0 then decides and fits.
+// 0 elsewhere), then iterate. In each matching a thread takes one model
+// pixel: it back-projects and moves the point and scans the grid cells that
+// meet a cube of half-width rho about it, where rho is the radius, or from
+// the second matching on the distance to the point the pixel was paired with
+// last time, when that point is still within the radius (the nearest point
+// can only be nearer). It keeps the nearest point (ties: smaller index),
+// adds the pair to its own sums, and the warps reduce those into shared
+// 64-bit counters. Thread 0 then decides and fits.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_icp(Camera cam, Geometry g, Batch b, IcpGrid q, IcpWork w, IcpClaim cl) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -2191,6 +2194,7 @@ __global__ void __launch_bounds__(NT) k_icp(Camera cam, Geometry g, Batch b, Icp
     nm = __reduce_add_sync(0xffffffffu, nm);
     if (lane == 0 && nm) atomicAdd(&s_nm, nm);
     __syncthreads();  // |M| and the model set are complete
+    int* prev_t = w.prev + (size_t)blockIdx.x * b.tile_w * b.tile_h;  // per model pixel: its last pair's point
     long long prev[9];  // thread 0: the previous matching's sums
     bool have_prev = false;
     int iters = 0, n_corr = 0, status = PERCH_ICP_CAP;
@@ -2200,9 +2204,9 @@ __global__ void __launch_bounds__(NT) k_icp(Camera cam, Geometry g, Batch b, Icp
       const float cf = __double2float_rn(s_T[0]), sf = __double2float_rn(s_T[1]);
       const float txf = __double2float_rn(s_T[2]), tyf = __double2float_rn(s_T[3]);
       long long L[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-      for (int i = warp; i < area; i += NW) {
+      for (int i = tid; i < area; i += NT) {
         const uint32_t zb = tile[i];
-        if (zb == 0u) continue;  // the same pixel for the whole warp
+        if (zb == 0u) continue;
         const int ly = i / tw, lx = i - ly * tw;
         const float z = __uint_as_float(zb);
         const float xc = fmul(g.rx[bb.x + lx], z), yc = fmul(g.ry[bb.y + ly], z);
@@ -2211,20 +2215,31 @@ __global__ void __launch_bounds__(NT) k_icp(Camera cam, Geometry g, Batch b, Icp
         const float mz = fadd(ffma(cam.Rwc[8], z, ffma(cam.Rwc[7], yc, fmul(cam.Rwc[6], xc))), cam.twc[2]);
         const float px = fadd(fsub(fmul(cf, mx), fmul(sf, my)), txf);
         const float py = fadd(fadd(fmul(sf, mx), fmul(cf, my)), tyf);
-        const int cx = cell_of(px, q.gx, q.inv, q.nx), cy = cell_of(py, q.gy, q.inv, q.ny);
-        const int cz = cell_of(mz, q.gz, q.inv, q.nz);
-        const int x0 = max(cx - 1, 0), x1 = min(cx + 1, q.nx - 1);
-        const int y0 = max(cy - 1, 0), y1 = min(cy + 1, q.ny - 1);
-        const int z0 = max(cz - 1, 0), z1 = min(cz + 1, q.nz - 1);
+        // Search window: the radius, or, when the previous matching's point
+        // is still within it, that point's distance (the nearest point is no
+        // farther). The margins cover the rounding of d^2 (relative 2^-22)
+        // and of the window's ends (1e-6 m), so every point whose d^2 can
+        // tie or beat the bound lies inside.
+        float rho = w.rwin;
+        if (k > 1) {
+          const int t0 = prev_t[i];
+          if (t0 >= 0) {
+            const float d0 = dist2(px, py, mz, q.pts[t0]);
+            if (d0 <= w.r2) rho = fminf(rho, __fsqrt_rn(d0) * 1.001f + 1e-6f);
+          }
+        }
+        const int x0 = max(cell_of(px - rho, q.gx, q.inv, q.nx), 0), x1 = min(cell_of(px + rho, q.gx, q.inv, q.nx), q.nx - 1);
+        const int y0 = max(cell_of(py - rho, q.gy, q.inv, q.ny), 0), y1 = min(cell_of(py + rho, q.gy, q.inv, q.ny), q.ny - 1);
+        const int z0 = max(cell_of(mz - rho, q.gz, q.inv, q.nz), 0), z1 = min(cell_of(mz + rho, q.gz, q.inv, q.nz), q.nz - 1);
         uint32_t bd = 0xffffffffu;  // no candidate (every d^2 <= r^2 has smaller bits)
-        int bj = INT_MAX;
+        int bj = INT_MAX, bt = -1;
         float bqx = 0.0f, bqy = 0.0f;
         if (x0 <= x1) {
           for (int iz = z0; iz <= z1; ++iz)
             for (int iy = y0; iy <= y1; ++iy) {
               const int row = (iz * q.ny + iy) * q.nx;
               const int end = q.start[row + x1 + 1];
-              for (int t = q.start[row + x0] + lane; t < end; t += 32) {
+              for (int t = q.start[row + x0]; t < end; ++t) {
                 const float4 o = q.pts[t];
                 const float d = dist2(px, py, mz, o);
                 if (d <= w.r2) {
@@ -2233,6 +2248,7 @@ __global__ void __launch_bounds__(NT) k_icp(Camera cam, Geometry g, Batch b, Icp
                   if (db < bd || (db == bd && j < bj)) {
                     bd = db;
                     bj = j;
+                    bt = t;
                     bqx = o.x;
                     bqy = o.y;
                   }
@@ -2240,10 +2256,8 @@ __global__ void __launch_bounds__(NT) k_icp(Camera cam, Geometry g, Batch b, Icp
               }
             }
         }
-        const uint32_t wd = __reduce_min_sync(0xffffffffu, bd);
-        if (wd == 0xffffffffu) continue;  // unmatched (uniform)
-        const uint32_t wj = __reduce_min_sync(0xffffffffu, bd == wd ? (uint32_t)bj : 0xffffffffu);
-        if (bd == wd && (uint32_t)bj == wj) icp_add_pair(L, mx, my, bqx, bqy);  // one lane: each point once
+        prev_t[i] = bt;
+        if (bt >= 0) icp_add_pair(L, mx, my, bqx, bqy);
       }
       for (int t = 0; t < 9; ++t) {
         long long v = L[t];
@@ -2287,7 +2301,7 @@ __global__ void __launch_bounds__(NT) k_icp(Camera cam, Geometry g, Batch b, Icp
 }
 
 cudaError_t launch_icp(const Camera& cam, const Geometry& g, const Batch& b, const IcpGrid& q, const IcpWork& w,
-                       int* next, int sm_count, cudaStream_t s) {
+                       long long prev_elems, int* next, int sm_count, cudaStream_t s) {
   if (b.n_hyp <= 0) return cudaSuccess;
   const size_t smem = render_smem_bytes(b.tile_w, b.tile_h);
   auto kern = k_icp<256>;
@@ -2299,7 +2313,9 @@ cudaError_t launch_icp(const Camera& cam, const Geometry& g, const Batch& b, con
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)per_sm * sm_count;
   if (grid > b.n_hyp) grid = b.n_hyp;
-  if (grid < 1) grid = 1;
+  const long long cap = (long long)b.tile_w * b.tile_h;  // each CTA's slice of w.prev
+  if (cap > 0 && grid > prev_elems / cap) grid = prev_elems / cap;
+  if (grid < 1) return cudaErrorInvalidValue;
   kern<<<(unsigned)grid, 256, smem, s>>>(cam, g, b, q, w, IcpClaim{next});
   return cudaGetLastError();
 }

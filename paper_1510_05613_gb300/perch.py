@@ -277,12 +277,14 @@ class Perch:
             hyps_t.data_ptr(), hyp_parent_t.numel(), radius, max_iter, out_t.data_ptr()))
 
     def perch_refine_scene(self, objs, radius: float = 0.02, max_iter: int = 20):
-        """ICP of each object of a scene (in the order it was added) against
-        the objects before it: the refinement of every successor on the
-        path to that scene. Returns (records, [(mesh, x, y, yaw)])."""
+        """ICP of each object of a scene against all the others: its model
+        set is then its visible part in the whole scene, which for a scene of
+        the MSGT is its non-occluded part when it was added (the objects
+        added after it lie behind it or beside it, Eq. (3)), in any order of
+        objs. Returns (records, [(mesh, x, y, yaw)])."""
         objs = np.asarray(objs, OBJ)
-        recs = self.perch_icp_refine([objs[:k] for k in range(len(objs))], np.arange(len(objs)), objs, radius,
-                                     max_iter)
+        others = [np.concatenate([objs[:k], objs[k + 1:]]) for k in range(len(objs))]
+        recs = self.perch_icp_refine(others, np.arange(len(objs)), objs, radius, max_iter)
         return recs, [refined_pose(self.grid, o, r) for o, r in zip(objs, recs)]
 
     def perch_autotune(self, n_sample: int = 2048):

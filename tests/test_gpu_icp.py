@@ -104,13 +104,14 @@ def test_icp_bit_exact_off_grid_c2_and_accuracy(off):
         assert after < 2e-3 and after < 0.25 * before, (k, before, after)
 
 
-def test_refine_scene_is_the_path_refinement(off):
+def test_refine_scene_against_the_other_objects(off):
     wl, p, w = off
-    recs, poses = p.perch_refine_scene(wl.gt)
-    exp = oracle.icp_refine(w, wl.depth, [wl.gt[:k] for k in range(len(wl.gt))], np.arange(len(wl.gt)), wl.gt,
-                            0.02, 20)
+    recs, poses = p.perch_refine_scene(wl.gt[::-1])
+    objs = wl.gt[::-1]
+    others = [np.concatenate([objs[:k], objs[k + 1:]]) for k in range(len(objs))]
+    exp = oracle.icp_refine(w, wl.depth, others, np.arange(len(objs)), objs, 0.02, 20)
     _compare(recs, exp)
-    assert [q[0] for q in poses] == [int(o["mesh"]) for o in wl.gt]
+    assert [q[0] for q in poses] == [int(o["mesh"]) for o in objs]
 
 
 def test_icp_full_size_sampled(off):
