@@ -913,6 +913,8 @@ def run_icp(args):
     p = perch.Perch(0, stream=stream.cuda_stream)
     p.setup(wl)
     hyps = synth.all_hypotheses(wl.grid, list(range(len(wl.meshes))))
+    if args.max_hyps and args.max_hyps < len(hyps):  # reduced batch (profiling case)
+        hyps = hyps[np.linspace(0, len(hyps) - 1, args.max_hyps).astype(np.int64)]
     n = len(hyps)
     hp = np.zeros(n, np.int32)
     P, plen, stride = perch.Perch.pack_parents([wl.gt[:0]])
