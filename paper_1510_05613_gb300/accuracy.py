@@ -53,11 +53,18 @@ def pose_errors(pred, truth, grid, syms):
     pairing predicted objects (OBJ records on `grid`) with true poses of the
     same mesh by the permutation of smallest total position error; a true
     object without a prediction of its type gets (mesh, inf, inf)."""
+    poses = [(int(o["mesh"]), float(grid.xs[o["ix"]]), float(grid.ys[o["iy"]]), yaw_angle(grid, o["iyaw"]))
+             for o in pred]
+    return pose_errors_of(poses, truth, syms)
+
+
+def pose_errors_of(poses, truth, syms):
+    """pose_errors for predicted poses given as (mesh, x, y, yaw) (off the
+    grid, e.g. refined by ICP)."""
     out = []
     for m in sorted({t[0] for t in truth}):
         T = [t for t in truth if t[0] == m]
-        P = [(float(grid.xs[o["ix"]]), float(grid.ys[o["iy"]]), yaw_angle(grid, o["iyaw"]))
-             for o in pred if int(o["mesh"]) == m]
+        P = [(x, y, yaw) for mm, x, y, yaw in poses if int(mm) == m]
         best, best_cost = None, math.inf
         n = min(len(T), len(P))
         for perm in itertools.permutations(range(len(P)), n):
