@@ -110,8 +110,8 @@ int perch_ctx::enqueue_icp(const perch_obj* d_parents, int parent_stride, const 
   const size_t npx = (size_t)cam.W * cam.H;
   CK(parent_z.ensure(4 * npx * std::max(n_par, 1)), "alloc parent z-buffers");
   CK(icp_next.ensure(4), "alloc");
-  // each CTA's pair memory: 4 CTAs per SM at most (k_icp's registers)
-  const long long prev_elems = 4LL * sm_count * tile_w * tile_h;
+  // each CTA's model list and pair memory: 4 CTAs per SM at most (k_icp's registers)
+  const long long prev_elems = 8LL * sm_count * tile_w * tile_h;
   CK(icp_prev.ensure(4 * (size_t)std::max(prev_elems, 1LL)), "alloc");
   Batch b;
   std::memset(&b, 0, sizeof b);

@@ -188,7 +188,7 @@ struct IcpWork {
   float rwin;    // 1.01 radius + 1e-6 m: the search window before a pair is known
   int max_iter;
   perch_icp* out;
-  int* prev;     // per CTA, tile_w x tile_h entries: each model pixel's last paired point (grid order)
+  int* prev;     // per CTA, 2 tile_w x tile_h entries: the model pixels, then each one's last paired point
 };
 
 // kernels.cu launchers (all asynchronous on `s`)
@@ -256,7 +256,7 @@ cudaError_t launch_icp_points(const float4* world2, const float4* cam2, int n, f
 // ICP of each hypothesis of the batch (one CTA per hypothesis at a time,
 // claimed from the device counter `next`, zero before the launch; the
 // parents' renders must be in b.parent_z). The grid is capped so that every
-// CTA has its tile_w x tile_h slice of w.prev (prev_elems entries in all).
+// CTA has its 2 tile_w x tile_h slice of w.prev (prev_elems entries in all).
 cudaError_t launch_icp(const Camera& cam, const Geometry& g, const Batch& b, const IcpGrid& q, const IcpWork& w,
                        long long prev_elems, int* next, int sm_count, cudaStream_t s);
 

@@ -2175,26 +2175,32 @@ __global__ void __launch_bounds__(NT) k_icp(Camera cam, Geometry g, Batch b, Icp
       if (st == kEvalStop) break;
       continue;
     }
-    // model set: z where the object lies strictly in front of the parent
+    // model set: z where the object lies strictly in front of the parent,
+    // and the list of those pixels (in any order: every sum is order-free)
     const float* zp = b.parent_z + (size_t)a.pid * cam.W * cam.H;
-    int nm = 0;
-    for (int i = tid; i < area; i += NT) {
-      const uint32_t izb = tile[i];
+    const size_t cap = (size_t)b.tile_w * b.tile_h;
+    int* list = w.prev + 2 * cap * blockIdx.x;  // this CTA's slice: model pixels, then their last pairs
+    int* prev_t = list + cap;
+    for (int i0 = 0; i0 < area; i0 += NT) {  // the same trip count in every lane (ballots below)
+      const int i = i0 + tid;
       uint32_t v = 0u;
-      if (izb != 0u) {
-        const int ly = i / tw, lx = i - ly * tw;
-        const float z = __frcp_rn(__uint_as_float(izb));
-        if (z < zp[(size_t)(bb.y + ly) * cam.W + bb.x + lx]) {
-          v = __float_as_uint(z);
-          ++nm;
+      if (i < area) {
+        const uint32_t izb = tile[i];
+        if (izb != 0u) {
+          const int ly = i / tw, lx = i - ly * tw;
+          const float z = __frcp_rn(__uint_as_float(izb));
+          if (z < zp[(size_t)(bb.y + ly) * cam.W + bb.x + lx]) v = __float_as_uint(z);
         }
+        tile[i] = v;
       }
-      tile[i] = v;
+      const unsigned mask = __ballot_sync(0xffffffffu, v != 0u);
+      int base = 0;
+      if (lane == 0 && mask) base = atomicAdd(&s_nm, __popc(mask));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (v != 0u) list[base + __popc(mask & ((1u << lane) - 1u))] = i;
     }
-    nm = __reduce_add_sync(0xffffffffu, nm);
-    if (lane == 0 && nm) atomicAdd(&s_nm, nm);
-    __syncthreads();  // |M| and the model set are complete
-    int* prev_t = w.prev + (size_t)blockIdx.x * b.tile_w * b.tile_h;  // per model pixel: its last pair's point
+    __syncthreads();  // |M|, the model set and its list are complete
+    const int nm = s_nm;
     long long prev[9];  // thread 0: the previous matching's sums
     bool have_prev = false;
     int iters = 0, n_corr = 0, status = PERCH_ICP_CAP;
@@ -2204,11 +2210,10 @@ __global__ void __launch_bounds__(NT) k_icp(Camera cam, Geometry g, Batch b, Icp
       const float cf = __double2float_rn(s_T[0]), sf = __double2float_rn(s_T[1]);
       const float txf = __double2float_rn(s_T[2]), tyf = __double2float_rn(s_T[3]);
       long long L[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-      for (int i = tid; i < area; i += NT) {
-        const uint32_t zb = tile[i];
-        if (zb == 0u) continue;
+      for (int e = tid; e < nm; e += NT) {
+        const int i = list[e];
         const int ly = i / tw, lx = i - ly * tw;
-        const float z = __uint_as_float(zb);
+        const float z = __uint_as_float(tile[i]);
         const float xc = fmul(g.rx[bb.x + lx], z), yc = fmul(g.ry[bb.y + ly], z);
         const float mx = fadd(ffma(cam.Rwc[2], z, ffma(cam.Rwc[1], yc, fmul(cam.Rwc[0], xc))), cam.twc[0]);
         const float my = fadd(ffma(cam.Rwc[5], z, ffma(cam.Rwc[4], yc, fmul(cam.Rwc[3], xc))), cam.twc[1]);
@@ -2222,7 +2227,7 @@ __global__ void __launch_bounds__(NT) k_icp(Camera cam, Geometry g, Batch b, Icp
         // tie or beat the bound lies inside.
         float rho = w.rwin;
         if (k > 1) {
-          const int t0 = prev_t[i];
+          const int t0 = prev_t[e];
           if (t0 >= 0) {
             const float d0 = dist2(px, py, mz, q.pts[t0]);
             if (d0 <= w.r2) rho = fminf(rho, __fsqrt_rn(d0) * 1.001f + 1e-6f);
@@ -2256,7 +2261,7 @@ __global__ void __launch_bounds__(NT) k_icp(Camera cam, Geometry g, Batch b, Icp
               }
             }
         }
-        prev_t[i] = bt;
+        prev_t[e] = bt;
         if (bt >= 0) icp_add_pair(L, mx, my, bqx, bqy);
       }
       for (int t = 0; t < 9; ++t) {
@@ -2313,7 +2318,7 @@ cudaError_t launch_icp(const Camera& cam, const Geometry& g, const Batch& b, con
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)per_sm * sm_count;
   if (grid > b.n_hyp) grid = b.n_hyp;
-  const long long cap = (long long)b.tile_w * b.tile_h;  // each CTA's slice of w.prev
+  const long long cap = 2LL * b.tile_w * b.tile_h;  // each CTA's slice of w.prev
   if (cap > 0 && grid > prev_elems / cap) grid = prev_elems / cap;
   if (grid < 1) return cudaErrorInvalidValue;
   kern<<<(unsigned)grid, 256, smem, s>>>(cam, g, b, q, w, IcpClaim{next});
