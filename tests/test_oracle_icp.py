@@ -208,3 +208,22 @@ def test_noisy_observation_still_converges_near_the_truth():
     o = gt[0]
     tx, ty = float(grid.xs[o["ix"]]) + jit[0], float(grid.ys[o["iy"]]) + jit[1]
     assert math.hypot(x - tx, y - ty) < 3e-3
+
+
+def test_refined_pose_of_binding_and_oracle_agree():
+    """The binding's pose arithmetic (perch.refined_pose) and the oracle's
+    (icp_pose) move a grid pose by a record's motion the same way; a pure
+    shift moves (x, y) only, a turn about the origin turns (x, y) and the yaw."""
+    from paper_1510_05613_gb300 import perch
+    grid = synth.pose_grid(-0.49, 0.02, 50, 16)
+    o = synth.objs([(0, 30, 10, 5)])[0]
+    for c, s, tx, ty in [(1.0, 0.0, 0.01, -0.02), (math.cos(0.3), math.sin(0.3), 0.0, 0.0),
+                         (math.cos(-1.2), math.sin(-1.2), 0.004, 0.003)]:
+        rec = np.zeros(1, perch.ICP)[0]
+        rec["c"], rec["s"], rec["tx"], rec["ty"] = c, s, tx, ty
+        _, x, y, yaw = perch.refined_pose(grid, o, rec)
+        assert np.allclose((x, y, yaw), oracle.icp_pose(grid, o, rec), atol=1e-15)
+        x0, y0 = float(grid.xs[o["ix"]]), float(grid.ys[o["iy"]])
+        assert np.allclose((x, y), (c * x0 - s * y0 + tx, s * x0 + c * y0 + ty))
+        th0 = math.atan2(float(grid.cos_sin[o["iyaw"], 1]), float(grid.cos_sin[o["iyaw"], 0]))
+        assert abs(yaw - th0 - math.atan2(s, c)) < 1e-12

@@ -78,3 +78,24 @@ def test_c3_workload_is_heavily_occluded():
     assert 0.7 < occ.max() < 1.0
     sizes = sorted(m.n_tris for m in wl.meshes)
     assert sizes[0] <= 2100 and sizes[-1] >= 49000
+
+
+def test_c2_off_grid_workload():
+    wl = synth.workload_c2_off_grid(1)
+    j = np.array(wl.extra["jitter"])
+    step = float(wl.grid.xs[1] - wl.grid.xs[0])
+    assert j.shape == (3, 3)
+    assert np.all(np.abs(j[:, :2]) <= 0.5 * step) and np.all(np.abs(j[:, 2]) <= 0.5 * 2 * np.pi / wl.grid.n_yaw)
+    assert np.abs(j).max() > 0  # really off the grid
+    # footprints stay apart with the offsets (1.5 steps of margin)
+    for a in range(3):
+        for b in range(a + 1, 3):
+            oa, ob = wl.gt[a], wl.gt[b]
+            d = np.hypot(float(wl.grid.xs[oa["ix"]] - wl.grid.xs[ob["ix"]]),
+                         float(wl.grid.ys[oa["iy"]] - wl.grid.ys[ob["iy"]]))
+            assert d > wl.meshes[oa["mesh"]].footprint_radius + wl.meshes[ob["mesh"]].footprint_radius + step
+    # the observation is made at the offset poses
+    on = synth.raycast_depth(wl.cam, wl.meshes, wl.grid, wl.gt)
+    off = synth.raycast_depth(wl.cam, wl.meshes, wl.grid, wl.gt, wl.extra["jitter"])
+    assert not np.array_equal(on > 0, off > 0)
+    assert np.array_equal(wl.depth, synth.workload_c2_off_grid(1).depth)
